@@ -1,0 +1,150 @@
+"""Seeded synthetic workloads for the coupled Allen–Cahn/Cahn–Hilliard time step.
+
+This module holds no arithmetic of the method.  It only says which grid,
+coefficients, solver settings and initial fields a run uses, and draws the
+initial fields from a seeded NumPy PCG64 generator.  Both the CPU oracle and the
+CUDA path are fed from here, so the two sides always see the same inputs.
+
+Initial fields follow the paper's random-perturbation recipe (Sec. 4.1 A and B:
+a constant state plus uniform noise on u and v); the amplitudes, seeds, grid
+sizes and coefficients are those of the five named workloads below.
+"""
+from __future__ import annotations
+
+import dataclasses
+from dataclasses import dataclass, field
+from typing import Tuple
+
+import numpy as np
+
+BC_PERIODIC = 0
+BC_NEUMANN = 1
+DT_FIXED = 0
+DT_ADAPTIVE = 1
+RAS_LEFT = 0
+RAS_AS = 1
+RAS_RIGHT = 2
+PREC_FP64 = 0
+PREC_MIXED = 1
+JAC_MATFREE = 0
+JAC_ASSEMBLED = 1
+
+
+@dataclass
+class Params:
+    """Problem and solver settings (field names follow the C struct acac_params)."""
+
+    dim: int = 2
+    n: Tuple[int, int, int] = (64, 64, 1)        # Nx, Ny, Nz
+    L: Tuple[float, float, float] = (1.0, 1.0, 1.0)
+    bc: int = BC_PERIODIC
+    alpha: float = 3.0
+    beta: float = 1.0
+    theta: float = 0.3
+    gamma: float = 1e-3
+    rho: float = 1.0
+    taylor_S: int = 10
+    dt_mode: int = DT_FIXED
+    dt0: float = 1e-3
+    dt_min: float = 1e-5
+    dt_max: float = 1e-1
+    eta0: float = 1e4
+    newton_rtol: float = 1e-8
+    newton_atol: float = 1e-13
+    newton_maxit: int = 20
+    gmres_rtol: float = 1e-6
+    gmres_atol: float = 1e-14
+    gmres_restart: int = 30
+    gmres_maxit: int = 500
+    ras_parts: Tuple[int, int, int] = (4, 4, 1)
+    ras_overlap: int = 1
+    ras_type: int = RAS_LEFT
+    ilu_reuse: int = 1
+    precision: int = PREC_FP64
+    jac_mode: int = JAC_MATFREE
+    batch: int = 1
+    cgs_refine: int = 1          # 1: CGS2 (two passes), 0: single classical pass
+
+    def replace(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
+
+    @property
+    def shape(self) -> Tuple[int, ...]:
+        """Array shape of one field, slowest axis first (x is the last axis)."""
+        nx, ny, nz = self.n
+        return (ny, nx) if self.dim == 2 else (nz, ny, nx)
+
+    @property
+    def ncells(self) -> int:
+        return int(np.prod(self.shape))
+
+
+def initial_fields(p: Params, seed: int, u_mean: float, amp: float):
+    """u = u_mean + amp*U(-1,1), v = amp*U(-1,1), drawn u then v from PCG64(seed)."""
+    rng = np.random.default_rng(seed)
+    noise = rng.uniform(-1.0, 1.0, size=(2,) + p.shape)
+    u = u_mean + amp * noise[0]
+    v = amp * noise[1]
+    return np.ascontiguousarray(u), np.ascontiguousarray(v)
+
+
+def perturbed_pair(p: Params, seed: int, u_mean: float = 0.5, amp: float = 0.05,
+                   step_amp: float = 1e-3):
+    """Two nearby admissible states (U1, U0) for residual / Jacobian parity checks.
+
+    U0 is drawn as initial_fields(seed); U1 = U0 + step_amp*U(-1,1) (seed+1).
+    """
+    u0, v0 = initial_fields(p, seed, u_mean, amp)
+    rng = np.random.default_rng(seed + 1)
+    d = rng.uniform(-1.0, 1.0, size=(2,) + p.shape)
+    return (u0 + step_amp * d[0], v0 + step_amp * d[1]), (u0, v0)
+
+
+def random_vector(p: Params, seed: int):
+    """A seeded direction (wu, wv) with entries U(-1,1)."""
+    rng = np.random.default_rng(seed)
+    w = rng.uniform(-1.0, 1.0, size=(2,) + p.shape)
+    return np.ascontiguousarray(w[0]), np.ascontiguousarray(w[1])
+
+
+@dataclass
+class Workload:
+    name: str
+    params: Params
+    steps: int
+    seed: int
+    u_mean: float
+    amp: float
+
+    def fields(self):
+        return initial_fields(self.params, self.seed, self.u_mean, self.amp)
+
+
+_COEF = dict(alpha=3.0, beta=1.0, theta=0.3, gamma=1e-3, rho=1.0)
+
+# 2D 64x64 periodic, FP64, fixed dt=1e-3, 10 steps, RAS 4x4 overlap 1, ILU(0).
+C1 = Workload(
+    "2d-64x64-periodic-fp64-fixed-dt1e-3",
+    Params(dim=2, n=(64, 64, 1), bc=BC_PERIODIC, dt_mode=DT_FIXED, dt0=1e-3,
+           ras_parts=(4, 4, 1), ras_overlap=1, **_COEF),
+    steps=10, seed=0, u_mean=0.5, amp=0.01)
+
+# 2D 1024x1024 periodic, FP64, adaptive dt from 1e-4 in [1e-5, 1e-1], 100 steps,
+# RAS 16x16 overlap 2, ILU(0).
+C2 = Workload(
+    "2d-1024x1024-periodic-fp64-adaptive",
+    Params(dim=2, n=(1024, 1024, 1), bc=BC_PERIODIC, dt_mode=DT_ADAPTIVE, dt0=1e-4,
+           dt_min=1e-5, dt_max=1e-1, eta0=1e4, ras_parts=(16, 16, 1), ras_overlap=2,
+           **_COEF),
+    steps=100, seed=1, u_mean=0.4, amp=0.05)
+
+# 2D 2048x2048 periodic, mixed precision (FP32 Krylov / Jacobian / RAS-ILU), adaptive,
+# 50 steps, RAS 16x16 overlap 2.
+C3 = Workload(
+    "2d-2048x2048-periodic-mixed-adaptive",
+    Params(dim=2, n=(2048, 2048, 1), bc=BC_PERIODIC, dt_mode=DT_ADAPTIVE, dt0=1e-4,
+           dt_min=1e-5, dt_max=1e-1, eta0=1e4, ras_parts=(16, 16, 1), ras_overlap=2,
+           precision=PREC_MIXED, **_COEF),
+    steps=50, seed=2, u_mean=0.4, amp=0.05)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3)}
