@@ -1,0 +1,198 @@
+/*
+ * acac.h — C ABI of the GB300 (sm_103a) solver for one implicit time step of the
+ * energy-stable discrete-variational-derivative (DVD) scheme for the coupled
+ * Allen–Cahn / Cahn–Hilliard system of Huang, Yang & Wei, "Parallel energy-stable
+ * solver for a coupled Allen–Cahn and Cahn–Hilliard system" (arXiv 2007.04560).
+ *
+ * The step solves F(X) = 0 of scheme (NSOA-1) (Sec. 2):
+ *     (U^{n+1} - U^n) / dt = -A~ G~^S,    A~ = diag(-div c grad, c / rho),
+ * with the Newton–Krylov–Schwarz method of Sec. 3.1 and the adaptive time step
+ * of Sec. 3.2 (Eq. sencondt).
+ *
+ * Conventions shared by every entry point:
+ *   - Grid: cell-centred, Nx x Ny (x Nz), spacing L/N per direction (Sec. 2).
+ *     A field is a contiguous array of N = Nx*Ny(*Nz) values, x fastest.
+ *   - A "state vector" is 2N contiguous values: the u field, then the v field.
+ *     Residuals, Newton directions and Krylov vectors use the same layout.
+ *   - Pointers named u, v, X, F, w, y, r, z, b, x, J are DEVICE pointers owned by
+ *     the caller unless the name ends in _host.  Scalar outputs (double*, int*)
+ *     are HOST pointers; NULL means "not wanted".
+ *   - "Krylov precision": double when params.precision == ACAC_FP64, float when
+ *     ACAC_MIXED.  Arguments typed void* below are in Krylov precision.
+ *   - All device work is enqueued on the stream given to acac_create.  Calls that
+ *     return host scalars or take decisions on device norms synchronise that
+ *     stream; the others only enqueue.
+ *   - Return value: ACAC_OK (0) or a negative ACAC_E_* code.  On error the
+ *     caller's fields are left unchanged by acac_step / acac_step_host.
+ *   - The handle owns all workspace (allocated in acac_create, freed in
+ *     acac_destroy).  A handle is not thread-safe.
+ */
+#ifndef ACAC_H
+#define ACAC_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define ACAC_OK               0
+#define ACAC_E_ARG           -1   /* bad size, coefficient, partition or pointer     */
+#define ACAC_E_CUDA          -2   /* a CUDA runtime call failed                      */
+#define ACAC_E_DOMAIN        -3   /* input state outside the admissible set (Sec. 2:
+                                     u+v and u-v in (0,1))                            */
+#define ACAC_E_DIVERGED      -4   /* NKS failed (Newton maxit, line search, GMRES
+                                     maxit, ILU pivot, non-finite norm)               */
+#define ACAC_E_DT_UNDERFLOW  -5   /* adaptive retry pushed dt below dt_min (Sec. 3.2) */
+#define ACAC_E_TIMEOUT       -6   /* a bounded device-side wait gave up              */
+#define ACAC_E_NOMEM         -7   /* device or host allocation failed                */
+
+/* ---- enumerations ---------------------------------------------------------- */
+#define ACAC_BC_PERIODIC     0
+#define ACAC_BC_NEUMANN      1    /* n.grad u = n.grad v = n.(c grad dE/du) = 0 (Sec. 1) */
+#define ACAC_DT_FIXED        0
+#define ACAC_DT_ADAPTIVE     1    /* Eq. sencondt with retry and eta doubling (Sec. 3.2)  */
+#define ACAC_RAS_LEFT        0    /* sum_k R_k^0T inv(A_k) R_k^delta   (Sec. 3.1)        */
+#define ACAC_RAS_AS          1    /* sum_k R_k^dT inv(A_k) R_k^delta   (Eq. invM)        */
+#define ACAC_RAS_RIGHT       2    /* sum_k R_k^dT inv(A_k) R_k^0       (Sec. 3.1)        */
+#define ACAC_FP64            0    /* every step of the solve in double                     */
+#define ACAC_MIXED           1    /* Jacobian, Krylov vectors and ILU in float; residual,
+                                     Newton update, energy, mass, dt estimator in double   */
+#define ACAC_JAC_MATFREE     0    /* GMRES products by the analytic Jacobian action      */
+#define ACAC_JAC_ASSEMBLED   1    /* GMRES products by the assembled stencil matrix      */
+
+/* Problem and solver settings.  Defaults: acac_default_params(). */
+typedef struct acac_params {
+    int    dim;                 /* 2 (3 is rejected by this build: ACAC_E_ARG)          */
+    int    n[3];                /* Nx, Ny, Nz; each >= 4                                */
+    double L[3];                /* domain lengths; dx = L[0]/n[0], ...                  */
+    int    bc;                  /* ACAC_BC_*                                             */
+    double alpha, beta, theta, gamma, rho;   /* > 0, Eq. 2 and Eq. 1                     */
+    int    taylor_S;            /* series terms of Lemma 2.2, 1..30 (paper: 10)          */
+    int    dt_mode;             /* ACAC_DT_*                                             */
+    double dt0, dt_min, dt_max, eta0;        /* first step, bounds, eta of Eq. sencondt  */
+    double newton_rtol, newton_atol;         /* eps_r, eps_a (Sec. 3.1)                  */
+    int    newton_maxit;
+    double gmres_rtol, gmres_atol;           /* xi_r, xi_a (Sec. 3.1)                    */
+    int    gmres_restart;       /* 1..64                                                 */
+    int    gmres_maxit;
+    int    ras_parts[3];        /* subdomain boxes per direction                        */
+    int    ras_overlap;         /* delta, mesh layers (Sec. 3.1)                        */
+    int    ras_type;            /* ACAC_RAS_*                                            */
+    int    ilu_reuse;           /* 1: factor at the first Newton iteration of each step
+                                   and reuse within the step (Sec. 4.2)                  */
+    int    precision;           /* ACAC_FP64 | ACAC_MIXED                                */
+    int    jac_mode;            /* ACAC_JAC_*                                            */
+    int    batch;               /* ensemble size; this build supports 1                  */
+    int    cgs_refine;          /* 1: Gram–Schmidt applied twice (CGS2), 0: once         */
+} acac_params;
+
+/* Per-step report. */
+typedef struct acac_step_info {
+    double t;                   /* time after the step                                  */
+    double dt;                  /* accepted dt                                          */
+    double eta;                 /* eta after the step (doubled on every divergence)     */
+    double energy;              /* discrete free energy E~ of the new state (Eq. freeenergy) */
+    double mass;                /* sum u dx dy (dz) of the new state                    */
+    double fnorm0, fnorm;       /* ||F(X_0)||, ||F(X_final)|| of the accepted solve      */
+    int    newton_its;          /* Newton iterations, all attempts of this step         */
+    int    gmres_its;           /* GMRES iterations, all attempts of this step          */
+    int    divergences;         /* NKS divergences retried in this step                 */
+    int    status;              /* ACAC_OK or the error returned                        */
+    int    line_search_cuts;    /* halvings of lambda, all attempts                     */
+    int    ilu_factorizations;  /* subdomain factorizations performed                   */
+} acac_step_info;
+
+typedef struct acac_handle acac_handle;
+
+/* Fill *p with the paper's solver defaults: S = 10, Newton rtol 1e-8 / atol 1e-13,
+ * GMRES rtol 1e-6 / atol 1e-14, restart 30, maxit 500, left-RAS, ILU(0) reuse,
+ * FP64, matrix-free products, CGS2, unit domain, 64x64 periodic, alpha=3,
+ * beta=1, theta=0.3, gamma=1e-3, rho=1, fixed dt 1e-3. */
+void acac_default_params(acac_params *p);
+
+/* Validate *p, allocate every workspace on the current CUDA device and build the
+ * subdomain tables (Sec. 3.1: boxes of near-equal size extended by delta layers,
+ * wrapped when periodic, clipped at Neumann walls).  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  *out receives the handle.
+ * Errors: ACAC_E_ARG (sizes < 4, non-positive coefficient, periodic box that
+ * would wrap onto itself, dim != 2, batch != 1), ACAC_E_NOMEM, ACAC_E_CUDA. */
+int acac_create(const acac_params *p, void *cuda_stream, acac_handle **out);
+
+/* One accepted time step, in place: u, v (device, N doubles each) hold U^n on
+ * entry and U^{n+1} on return.  The handle keeps U^{n-1}, dt_{n-1}, eta and t for
+ * the predictor of Eq. sencondt.  Synchronises the stream.  *info (host, may be
+ * NULL) receives the report.  Errors: ACAC_E_DOMAIN, ACAC_E_DIVERGED (fixed dt),
+ * ACAC_E_DT_UNDERFLOW (adaptive), ACAC_E_CUDA; fields unchanged on error. */
+int acac_step(acac_handle *h, double *u, double *v, acac_step_info *info);
+
+/* acac_step on HOST arrays: copies u_host, v_host to the device, steps, copies
+ * the result back.  Host arrays may be pageable or pinned. */
+int acac_step_host(acac_handle *h, double *u_host, double *v_host, acac_step_info *info);
+
+/* Discrete free energy E~ = <e~> (Eqs. relations, freeenergy, exact Phi with
+ * 0 ln 0 = 0) and mass sum u dx dy of the state (u, v) (device).  Host outputs;
+ * synchronises.  ACAC_E_DOMAIN if some u+v or u-v lies outside [0,1]. */
+int acac_energy(acac_handle *h, const double *u, const double *v, double *energy,
+                double *mass);
+
+/* Release every resource of h (NULL is ignored). */
+void acac_destroy(acac_handle *h);
+
+/* Static description of a status code. */
+const char *acac_status_string(int status);
+
+/* ---- component entry points (the pieces acac_step is made of) ---------------- */
+
+/* F(X1) of scheme (NSOA-1) with X0 = U^n and time step dt (Sec. 2, Eqs. dvds-2,
+ * D2-1, dvds-1, NSOA-1):  F_u = (u1-u0)/dt - [div c~ grad G_u],
+ * F_v = (v1-v0)/dt + c G_v / rho, mobility at the midpoint state.  X1, X0, F:
+ * device state vectors (double).  *fnorm (host, may be NULL) = ||F||_2, which
+ * synchronises.  ACAC_E_DOMAIN if a midpoint leaves the admissible set. */
+int acac_residual(acac_handle *h, const double *X1, const double *X0, double dt,
+                  double *F, double *fnorm);
+
+/* Assembled Jacobian dF/dX1 at (X1, X0, dt) in stencil-diagonal storage, Krylov
+ * precision: J[(b*4 + e)*N + cell], b = stencil slot 0..12 in the order
+ * (0,0),(-1,0),(1,0),(0,-1),(0,1),(-2,0),(2,0),(0,-2),(0,2),(-1,-1),(1,-1),(-1,1),(1,1)
+ * as (dx,dy); e = 0:(u-row,u-col) 1:(u,v) 2:(v,u) 3:(v,v).  Couplings to cells
+ * outside a Neumann domain are stored as 0.  J holds 52*N values (device). */
+int acac_jacobian(acac_handle *h, const double *X1, const double *X0, double dt, void *J);
+
+/* y = J w with J from acac_jacobian (Krylov precision, device). */
+int acac_spmv(acac_handle *h, const void *J, const void *w, void *y);
+
+/* y = J(X1) w by the analytic Jacobian action, without assembling J (Krylov
+ * precision w, y; double X1, X0). */
+int acac_jvp(acac_handle *h, const double *X1, const double *X0, double dt,
+             const void *w, void *y);
+
+/* Extract every subdomain matrix A_k = R_k J R_k^T (Eq. invM) from J (as stored by
+ * acac_jacobian) and factor it by ILU(0) on the 2x2-block stencil pattern, in the
+ * natural order of the box (x fastest, u before v).  ACAC_E_DIVERGED on a zero
+ * pivot (synchronises). */
+int acac_ras_factor(acac_handle *h, const void *J);
+
+/* z = H^{-1} r with the Schwarz preconditioner of params.ras_type and the factors
+ * of the last acac_ras_factor (Krylov precision, device). */
+int acac_ras_apply(acac_handle *h, const void *r, void *z);
+
+/* Solve J(X1) x = b by restarted right-preconditioned GMRES (Sec. 3.1, Eq.
+ * hjacobi) with the Schwarz/ILU(0) preconditioner factored from J(X1), x0 = 0,
+ * stopping when the residual estimate <= max(gmres_rtol ||b||, gmres_atol).
+ * b, x: double state vectors (device).  *its, *resid: host.  ACAC_E_DIVERGED if
+ * gmres_maxit is reached. */
+int acac_gmres(acac_handle *h, const double *X1, const double *X0, double dt,
+               const double *b, double *x, int *its, double *resid);
+
+/* One inexact-Newton solve of F(X) = 0 at fixed dt from X_0 = U0 (Sec. 3.1, Eq.
+ * newton), without time-step control.  U0, U1: double state vectors (device);
+ * U1 receives the root.  *info (host) receives fnorm0, fnorm, newton_its,
+ * gmres_its, line_search_cuts, ilu_factorizations and status (t, dt, eta,
+ * energy, mass are not filled). */
+int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
+                   acac_step_info *info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ACAC_H */

@@ -1,0 +1,276 @@
+"""Thin Python binding of the acac C ABI (include/acac.h).
+
+Argument marshalling only: every step of the solve runs in libacac.so's CUDA
+kernels.  Device arrays are torch CUDA tensors (contiguous float64 state vectors /
+fields, or Krylov-precision tensors where the C ABI takes void*); the handle
+enqueues all work on the torch stream that is current when it is created.
+
+The library must have been built (paper_2007_04560_gb300.build.build()); loading
+fails loudly otherwise — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libacac.so")
+
+OK = 0
+E_ARG = -1
+E_CUDA = -2
+E_DOMAIN = -3
+E_DIVERGED = -4
+E_DT_UNDERFLOW = -5
+E_TIMEOUT = -6
+E_NOMEM = -7
+
+
+class AcacError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = _lib().acac_status_string(status).decode() if _LIB is not None else str(status)
+        super().__init__("%s: %s (%d)" % (where or "acac", msg, status))
+
+
+class acac_params(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("L", ctypes.c_double * 3), ("bc", ctypes.c_int),
+        ("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("theta", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("rho", ctypes.c_double), ("taylor_S", ctypes.c_int),
+        ("dt_mode", ctypes.c_int), ("dt0", ctypes.c_double), ("dt_min", ctypes.c_double),
+        ("dt_max", ctypes.c_double), ("eta0", ctypes.c_double),
+        ("newton_rtol", ctypes.c_double), ("newton_atol", ctypes.c_double), ("newton_maxit", ctypes.c_int),
+        ("gmres_rtol", ctypes.c_double), ("gmres_atol", ctypes.c_double), ("gmres_restart", ctypes.c_int),
+        ("gmres_maxit", ctypes.c_int), ("ras_parts", ctypes.c_int * 3), ("ras_overlap", ctypes.c_int),
+        ("ras_type", ctypes.c_int), ("ilu_reuse", ctypes.c_int), ("precision", ctypes.c_int),
+        ("jac_mode", ctypes.c_int), ("batch", ctypes.c_int), ("cgs_refine", ctypes.c_int),
+    ]
+
+
+class acac_step_info(ctypes.Structure):
+    _fields_ = [
+        ("t", ctypes.c_double), ("dt", ctypes.c_double), ("eta", ctypes.c_double),
+        ("energy", ctypes.c_double), ("mass", ctypes.c_double), ("fnorm0", ctypes.c_double),
+        ("fnorm", ctypes.c_double), ("newton_its", ctypes.c_int), ("gmres_its", ctypes.c_int),
+        ("divergences", ctypes.c_int), ("status", ctypes.c_int), ("line_search_cuts", ctypes.c_int),
+        ("ilu_factorizations", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+# Every symbol declared in include/acac.h, with its ctypes signature.
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_PD = ctypes.POINTER(ctypes.c_double)
+_PI = ctypes.POINTER(ctypes.c_int)
+SIGNATURES = {
+    "acac_default_params": (None, [ctypes.POINTER(acac_params)]),
+    "acac_create": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, ctypes.POINTER(_P)]),
+    "acac_step": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(acac_step_info)]),
+    "acac_step_host": (ctypes.c_int, [_P, _P, _P, ctypes.POINTER(acac_step_info)]),
+    "acac_energy": (ctypes.c_int, [_P, _P, _P, _PD, _PD]),
+    "acac_destroy": (None, [_P]),
+    "acac_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "acac_residual": (ctypes.c_int, [_P, _P, _P, _D, _P, _PD]),
+    "acac_jacobian": (ctypes.c_int, [_P, _P, _P, _D, _P]),
+    "acac_spmv": (ctypes.c_int, [_P, _P, _P, _P]),
+    "acac_jvp": (ctypes.c_int, [_P, _P, _P, _D, _P, _P]),
+    "acac_ras_factor": (ctypes.c_int, [_P, _P]),
+    "acac_ras_apply": (ctypes.c_int, [_P, _P, _P]),
+    "acac_gmres": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _PI, _PD]),
+    "acac_nks_solve": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(acac_step_info)]),
+}
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libacac.so is not built (run paper_2007_04560_gb300.build.build()); "
+                               "there is no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load libacac.so (raises if it is missing) and return the ctypes handle."""
+    return _lib()
+
+
+def _check(st, where):
+    if st != OK:
+        raise AcacError(st, where)
+
+
+def to_c_params(p) -> acac_params:
+    """Marshal a workloads.Params (or any object with the same fields) into acac_params."""
+    c = acac_params()
+    _lib().acac_default_params(ctypes.byref(c))
+    for name, ctype in acac_params._fields_:
+        if not hasattr(p, name):
+            continue
+        val = getattr(p, name)
+        if name in ("n", "ras_parts"):
+            setattr(c, name, (ctypes.c_int * 3)(*[int(x) for x in val]))
+        elif name == "L":
+            setattr(c, name, (ctypes.c_double * 3)(*[float(x) for x in val]))
+        else:
+            setattr(c, name, val)
+    return c
+
+
+def _dev(t, dtype=None, numel=None, name="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("%s must be %s" % (name, dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements" % (name, numel))
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def acac_create(p, stream=None):
+    """acac_create on the current torch CUDA stream (or the given one)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    h = ctypes.c_void_p()
+    cp = to_c_params(p)
+    _check(_lib().acac_create(ctypes.byref(cp), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(h)),
+           "acac_create")
+    return h
+
+
+def acac_destroy(h):
+    _lib().acac_destroy(h)
+
+
+def acac_status_string(status: int) -> str:
+    return _lib().acac_status_string(status).decode()
+
+
+class Solver:
+    """Owns one acac handle.  Method names follow the C ABI without the prefix."""
+
+    def __init__(self, params, stream=None):
+        import torch
+        self.params = params
+        self.N = int(params.n[0]) * int(params.n[1]) * (int(params.n[2]) if params.dim == 3 else 1)
+        self.kdtype = torch.float32 if params.precision == 1 else torch.float64
+        self.h = acac_create(params, stream)
+
+    def close(self):
+        if self.h:
+            acac_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- time stepping
+    def step(self, u, v, check=True):
+        import torch
+        info = acac_step_info()
+        st = _lib().acac_step(self.h, _dev(u, torch.float64, self.N, "u"), _dev(v, torch.float64, self.N, "v"),
+                              ctypes.byref(info))
+        if check:
+            _check(st, "acac_step")
+        return info
+
+    def step_host(self, u, v, check=True):
+        """u, v: host (CPU) float64 contiguous tensors or numpy arrays, updated in place."""
+        import numpy as np
+        import torch
+        ptrs = []
+        for a in (u, v):
+            if isinstance(a, np.ndarray):
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.N
+                ptrs.append(ctypes.c_void_p(a.ctypes.data))
+            else:
+                assert a.device.type == "cpu" and a.dtype == torch.float64 and a.is_contiguous()
+                ptrs.append(ctypes.c_void_p(a.data_ptr()))
+        info = acac_step_info()
+        st = _lib().acac_step_host(self.h, ptrs[0], ptrs[1], ctypes.byref(info))
+        if check:
+            _check(st, "acac_step_host")
+        return info
+
+    def energy(self, u, v):
+        import torch
+        e, m = ctypes.c_double(), ctypes.c_double()
+        _check(_lib().acac_energy(self.h, _dev(u, torch.float64, self.N, "u"), _dev(v, torch.float64, self.N, "v"),
+                                  ctypes.byref(e), ctypes.byref(m)), "acac_energy")
+        return e.value, m.value
+
+    # -- components
+    def residual(self, X1, X0, dt, F):
+        import torch
+        fn = ctypes.c_double()
+        st = _lib().acac_residual(self.h, _dev(X1, torch.float64, 2 * self.N, "X1"),
+                                  _dev(X0, torch.float64, 2 * self.N, "X0"), float(dt),
+                                  _dev(F, torch.float64, 2 * self.N, "F"), ctypes.byref(fn))
+        _check(st, "acac_residual")
+        return fn.value
+
+    def jacobian(self, X1, X0, dt, J):
+        import torch
+        _check(_lib().acac_jacobian(self.h, _dev(X1, torch.float64, 2 * self.N), _dev(X0, torch.float64, 2 * self.N),
+                                    float(dt), _dev(J, self.kdtype, 52 * self.N, "J")), "acac_jacobian")
+
+    def spmv(self, J, w, y):
+        _check(_lib().acac_spmv(self.h, _dev(J, self.kdtype, 52 * self.N, "J"), _dev(w, self.kdtype, 2 * self.N, "w"),
+                                _dev(y, self.kdtype, 2 * self.N, "y")), "acac_spmv")
+
+    def jvp(self, X1, X0, dt, w, y):
+        import torch
+        _check(_lib().acac_jvp(self.h, _dev(X1, torch.float64, 2 * self.N), _dev(X0, torch.float64, 2 * self.N),
+                               float(dt), _dev(w, self.kdtype, 2 * self.N, "w"),
+                               _dev(y, self.kdtype, 2 * self.N, "y")), "acac_jvp")
+
+    def ras_factor(self, J):
+        _check(_lib().acac_ras_factor(self.h, _dev(J, self.kdtype, 52 * self.N, "J")), "acac_ras_factor")
+
+    def ras_apply(self, r, z):
+        _check(_lib().acac_ras_apply(self.h, _dev(r, self.kdtype, 2 * self.N, "r"),
+                                     _dev(z, self.kdtype, 2 * self.N, "z")), "acac_ras_apply")
+
+    def gmres(self, X1, X0, dt, b, x, check=True):
+        import torch
+        its, res = ctypes.c_int(), ctypes.c_double()
+        st = _lib().acac_gmres(self.h, _dev(X1, torch.float64, 2 * self.N), _dev(X0, torch.float64, 2 * self.N),
+                               float(dt), _dev(b, torch.float64, 2 * self.N, "b"),
+                               _dev(x, torch.float64, 2 * self.N, "x"), ctypes.byref(its), ctypes.byref(res))
+        if check:
+            _check(st, "acac_gmres")
+        return its.value, res.value, st
+
+    def nks_solve(self, U0, dt, U1, check=True):
+        import torch
+        info = acac_step_info()
+        st = _lib().acac_nks_solve(self.h, _dev(U0, torch.float64, 2 * self.N, "U0"), float(dt),
+                                   _dev(U1, torch.float64, 2 * self.N, "U1"), ctypes.byref(info))
+        if check:
+            _check(st, "acac_nks_solve")
+        return info

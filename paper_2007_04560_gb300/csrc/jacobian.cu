@@ -1,0 +1,193 @@
+// Jacobian of F (scheme NSOA-1, Sec. 2) at an iterate X1: analytic assembly into
+// stencil-diagonal 2x2-block storage, the assembled product y = J w, and the
+// matrix-free product y = J(X1) w from the per-cell linearisation cache.
+//
+// With the cache entries of cell k (c, cu, cv, Gu, Gv, du, xc; dv = du + (alpha-beta)/2):
+//   dG_u(k) = du w_u + xc w_v - gamma/2 [Delta w_u](k)
+//   dG_v(k) = xc w_u + dv w_v - gamma/2 [Delta w_v](k)
+//   dc(k)   = cu w_u + cv w_v
+//   (J w)_u(c) = w_u/dt - sum_f open_f/h_f^2 [ (dc_c+dc_n)/2 (Gu_n-Gu_c) + (c_c+c_n)/2 (dG_u(n)-dG_u(c)) ]
+//   (J w)_v(c) = w_v/dt + (dc_c Gv_c + c_c dG_v(c)) / rho
+#include "acac_internal.cuh"
+
+namespace acac {
+
+static int grid1(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < (1 << 30) ? (b < 1 ? 1 : b) : (1 << 30));
+}
+
+// ---------------------------------------------------------------- assembly
+template <typename T>
+__global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt, Cache<T> C, T* __restrict__ J) {
+    const int N = g.N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = c % g.nx, y = c / g.nx;
+    const double hg = 0.5 * k.gamma;
+    const double dvshift = 0.5 * (k.alpha - k.beta);
+    double Juu[NSLOT], Juv[NSLOT];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) { Juu[s] = 0.0; Juv[s] = 0.0; }
+    const double cc = C.c[c], cuc = C.cu[c], cvc = C.cv[c], gc = C.Gu[c], gvc = C.Gv[c];
+    const double duc = C.du[c], xcc = C.xc[c];
+    double lapc = 0.0;   // sum of open faces / h^2 at c
+    double eih2c[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        eih2c[f] = face_open(g, x, y, f) * (f < 2 ? g.ihx2 : g.ihy2);
+        lapc += eih2c[f];
+    }
+    Juu[0] = 1.0 / dt;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const int fx = face_dx(f), fy = face_dy(f);
+        const int sf = slot_of(fx, fy);
+        const int n = nb_index(g, x, y, fx, fy);
+        const double w = eih2c[f];
+        const double cn = C.c[n], dG = C.Gu[n] - gc, ct = 0.5 * (cc + cn);
+        // mobility variation of the face flux
+        Juu[0] -= w * 0.5 * cuc * dG;
+        Juv[0] -= w * 0.5 * cvc * dG;
+        Juu[sf] -= w * 0.5 * (double)C.cu[n] * dG;
+        Juv[sf] -= w * 0.5 * (double)C.cv[n] * dG;
+        // - ct * dG_u(n)/dX : pointwise part and Laplacian of the neighbour
+        Juu[sf] -= w * ct * (double)C.du[n];
+        Juv[sf] -= w * ct * (double)C.xc[n];
+        const int nx_ = x + fx, ny_ = y + fy;
+#pragma unroll
+        for (int f2 = 0; f2 < 4; ++f2) {
+            const double e2 = face_open(g, nx_, ny_, f2) * (f2 < 2 ? g.ihx2 : g.ihy2);
+            const int s2 = slot_of(fx + face_dx(f2), fy + face_dy(f2));
+            Juu[s2] += w * ct * hg * e2;
+            Juu[sf] -= w * ct * hg * e2;
+        }
+        // + ct * dG_u(c)/dX
+        Juu[0] += w * ct * duc;
+        Juv[0] += w * ct * xcc;
+#pragma unroll
+        for (int f2 = 0; f2 < 4; ++f2) {
+            const int s2 = slot_of(face_dx(f2), face_dy(f2));
+            Juu[s2] -= w * ct * hg * eih2c[f2];
+        }
+        Juu[0] += w * ct * hg * lapc;
+    }
+    const double irho = 1.0 / k.rho;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        double jvu = 0.0, jvv = 0.0;
+        if (s == 0) {
+            jvu = (cuc * gvc + cc * xcc) * irho;
+            jvv = 1.0 / dt + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
+        } else if (s <= 4) {
+            const int f = s - 1;   // slots 1..4 are faces -x, +x, -y, +y
+            jvv = -cc * hg * eih2c[f] * irho;
+        }
+        J[(size_t)(s * 4 + 0) * N + c] = (T)Juu[s];
+        J[(size_t)(s * 4 + 1) * N + c] = (T)Juv[s];
+        J[(size_t)(s * 4 + 2) * N + c] = (T)jvu;
+        J[(size_t)(s * 4 + 3) * N + c] = (T)jvv;
+    }
+}
+
+template <typename T>
+cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J,
+                            cudaStream_t s) {
+    assemble_kernel<T><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- assembled product
+template <typename T>
+__global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__ J, const T* __restrict__ w,
+                                                   T* __restrict__ y) {
+    const int N = g.N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = c % g.nx, yy = c / g.nx;
+    T au = 0, av = 0;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        const int n = nb_index(g, x, yy, slot_dx(s), slot_dy(s));
+        const T wu = w[n], wv = w[N + n];
+        au += J[(size_t)(s * 4 + 0) * N + c] * wu + J[(size_t)(s * 4 + 1) * N + c] * wv;
+        av += J[(size_t)(s * 4 + 2) * N + c] * wu + J[(size_t)(s * 4 + 3) * N + c] * wv;
+    }
+    y[c] = au;
+    y[N + c] = av;
+}
+
+template <typename T>
+cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s) {
+    spmv_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- matrix-free product
+// Pass 1: dG_u, dG_v, dc per cell into tmp = [dGu | dGv | dc].
+template <typename T>
+__global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, const T* __restrict__ w,
+                                                   T* __restrict__ tmp) {
+    const int N = g.N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = c % g.nx, y = c / g.nx;
+    const T wu = w[c], wv = w[N + c];
+    T lu = 0, lv = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
+        const T ih2 = (T)(f < 2 ? g.ihx2 : g.ihy2);
+        lu += (w[n] - wu) * ih2;
+        lv += (w[N + n] - wv) * ih2;
+    }
+    const T hg = (T)(0.5 * k.gamma);
+    const T du = C.du[c], xc = C.xc[c], dv = du + (T)(0.5 * (k.alpha - k.beta));
+    tmp[c] = du * wu + xc * wv - hg * lu;
+    tmp[N + c] = xc * wu + dv * wv - hg * lv;
+    tmp[2 * N + c] = C.cu[c] * wu + C.cv[c] * wv;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Cache<T> C,
+                                                   const T* __restrict__ w, const T* __restrict__ tmp,
+                                                   T* __restrict__ y) {
+    const int N = g.N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const int x = c % g.nx, yy = c / g.nx;
+    const T* dGu = tmp;
+    const T* dGv = tmp + N;
+    const T* dc = tmp + 2 * N;
+    const T cc = C.c[c], gc = C.Gu[c], dgc = dGu[c], dcc = dc[c];
+    T div = 0;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        const int n = nb_index(g, x, yy, face_dx(f), face_dy(f));
+        const T w_ = (T)(face_open(g, x, yy, f) * (f < 2 ? g.ihx2 : g.ihy2));
+        div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
+    }
+    const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho);
+    y[c] = w[c] * idt - div;
+    y[N + c] = w[N + c] * idt + (dcc * C.Gv[c] + cc * dGv[c]) * irho;
+}
+
+template <typename T>
+cudaError_t launch_jvp(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
+                       T* tmp, cudaStream_t s) {
+    jvp1_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
+    jvp2_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                   \
+    template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
+                                            cudaStream_t);                                        \
+    template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
+    template cudaError_t launch_jvp<T>(const Geom&, const Coef&, double, Cache<T>, const T*, T*,  \
+                                       T*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace acac

@@ -1,0 +1,259 @@
+// Vector kernels of the restarted GMRES of Sec. 3.1 (Eq. hjacobi): block dot
+// products against the Arnoldi basis with warp-shuffle reductions, the classical
+// Gram–Schmidt update, norms, scaling, the basis combination V y and the
+// precision boundary between the FP64 Newton vectors and the Krylov vectors.
+//
+// Reductions are two-stage and deterministic: every kernel writes one partial sum
+// per block (RED_BLOCKS blocks, grid-stride loops) and reduce_kernel adds the
+// partials of each vector in a fixed order.
+#include "acac_internal.cuh"
+
+namespace acac {
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block; result valid in thread 0.  sh: 32 doubles.
+__device__ __forceinline__ double block_sum_k(double v, double* sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        t = warp_sum(t);
+    }
+    return t;
+}
+
+__global__ void reduce_kernel(const double* __restrict__ partial, int nparts, double* __restrict__ out) {
+    __shared__ double sh[32];
+    const double* p = partial + (size_t)blockIdx.x * RED_BLOCKS;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += p[i];
+    const double t = block_sum_k(acc, sh);
+    if (threadIdx.x == 0) out[blockIdx.x] = t;
+}
+
+cudaError_t launch_reduce_partials(const double* partial, int nvec, int nparts, double* out,
+                                   cudaStream_t s) {
+    reduce_kernel<<<nvec, RED_THREADS, 0, s>>>(partial, nparts, out);
+    return cudaGetLastError();
+}
+
+// partial sums of (a - b - c) over n  (mass correction of the Newton direction)
+__global__ void sum_pair_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                const double* __restrict__ c, long long n, double* partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc += (a[i] - b[i]) - c[i];
+    const double t = block_sum_k(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n,
+                            double* partial, cudaStream_t s) {
+    sum_pair_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, c, n, partial);
+    return cudaGetLastError();
+}
+
+__global__ void norm2_double_kernel(const double* __restrict__ x, long long n, double* partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        acc = fma(x[i], x[i], acc);
+    const double t = block_sum_k(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+cudaError_t launch_norm2_double(const double* x, long long n, double* partial, cudaStream_t s) {
+    norm2_double_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, n, partial);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- V^T w
+// Vectors are processed in chunks of 8; each thread accumulates its share in the
+// Krylov precision, the block and global stages add in double.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
+                                                                const T* __restrict__ w, long long n,
+                                                                double* partial) {
+    __shared__ double sh[32];
+    for (int k0 = 0; k0 < nv; k0 += 8) {
+        const int cnt = nv - k0 < 8 ? nv - k0 : 8;
+        T acc[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[q] = 0;
+        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+             i += (long long)gridDim.x * blockDim.x) {
+            const T wi = w[i];
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (q < cnt) acc[q] += V[(size_t)(k0 + q) * ld + i] * wi;
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            if (q < cnt) {
+                const double t = block_sum_k((double)acc[q], sh);
+                if (threadIdx.x == 0) partial[(size_t)(k0 + q) * RED_BLOCKS + blockIdx.x] = t;
+            }
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n,
+                             double* partial, cudaStream_t s) {
+    multi_dot_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, w, n, partial);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- w -= V h  (+ ||w||^2)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __restrict__ V, long long ld, int nv,
+                                                                 const double* __restrict__ h, T* __restrict__ w,
+                                                                 long long n, int want_norm, double* partial) {
+    __shared__ double sh[32];
+    __shared__ T hs[MAX_RESTART + 1];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)h[k];
+    __syncthreads();
+    T acc = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = 0;
+        int k = 0;
+        for (; k + 4 <= nv; k += 4)
+            s += hs[k] * V[(size_t)k * ld + i] + hs[k + 1] * V[(size_t)(k + 1) * ld + i]
+               + hs[k + 2] * V[(size_t)(k + 2) * ld + i] + hs[k + 3] * V[(size_t)(k + 3) * ld + i];
+        for (; k < nv; ++k) s += hs[k] * V[(size_t)k * ld + i];
+        const T wn = w[i] - s;
+        w[i] = wn;
+        acc += wn * wn;
+    }
+    if (want_norm) {
+        const double t = block_sum_k((double)acc, sh);
+        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    }
+}
+
+template <typename T>
+cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w, long long n,
+                              int want_norm, double* partial, cudaStream_t s) {
+    cgs_update_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, partial);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- out = w / alpha (alpha on device)
+template <typename T>
+__global__ void scale_from_kernel(const T* __restrict__ w, const double* __restrict__ alpha,
+                                  T* __restrict__ out, long long n) {
+    const T inv = (T)(1.0 / sqrt(alpha[0]));   // alpha holds ||w||^2
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = w[i] * inv;
+}
+
+template <typename T>
+cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
+                              cudaStream_t s) {
+    scale_from_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w, alpha_dev, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* __restrict__ out,
+                                 long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = (T)(x[i] * scale);
+}
+
+template <typename T>
+cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s) {
+    to_krylov_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, scale, out, n);
+    return cudaGetLastError();
+}
+
+// out = sum_k y_k V_k
+template <typename T>
+__global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, const double* __restrict__ y,
+                               T* __restrict__ out, long long n) {
+    __shared__ T ys[MAX_RESTART + 1];
+    for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = (T)y[k];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        T s = 0;
+        for (int k = 0; k < nv; ++k) s += ys[k] * V[(size_t)k * ld + i];
+        out[i] = s;
+    }
+}
+
+template <typename T>
+cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T* out, long long n,
+                           cudaStream_t s) {
+    lincomb_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, y, out, n);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void axpy_to_double_kernel(double a, const T* __restrict__ x, double* __restrict__ y,
+                                      long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = fma(a, (double)x[i], y[i]);
+}
+
+template <typename T>
+cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s) {
+    axpy_to_double_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, x, y, n);
+    return cudaGetLastError();
+}
+
+// r = b - Ax (double), partial sums of ||r||^2
+template <typename T>
+__global__ void residual_restart_kernel(const double* __restrict__ b, const T* __restrict__ Ax,
+                                        double* __restrict__ r, long long n, double* partial) {
+    __shared__ double sh[32];
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double ri = b[i] - (double)Ax[i];
+        r[i] = ri;
+        acc = fma(ri, ri, acc);
+    }
+    const double t = block_sum_k(acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+
+template <typename T>
+cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n,
+                                    double* partial, cudaStream_t s) {
+    residual_restart_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, Ax, r, n, partial);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                     \
+    template cudaError_t launch_multi_dot<T>(const T*, long long, int, const T*, long long, double*, \
+                                             cudaStream_t);                                         \
+    template cudaError_t launch_cgs_update<T>(const T*, long long, int, const double*, T*, long long, \
+                                              int, double*, cudaStream_t);                          \
+    template cudaError_t launch_scale_from<T>(const T*, const double*, T*, long long, cudaStream_t); \
+    template cudaError_t launch_to_krylov<T>(const double*, double, T*, long long, cudaStream_t);   \
+    template cudaError_t launch_lincomb<T>(const T*, long long, int, const double*, T*, long long,  \
+                                           cudaStream_t);                                           \
+    template cudaError_t launch_axpy_to_double<T>(double, const T*, double*, long long, cudaStream_t); \
+    template cudaError_t launch_residual_restart<T>(const double*, const T*, double*, long long,    \
+                                                    double*, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace acac

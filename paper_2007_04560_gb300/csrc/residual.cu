@@ -1,0 +1,265 @@
+// Nonlinear residual F(X) of scheme (NSOA-1), its linearisation cache and the
+// discrete energy / mass reductions.  All in FP64 (Sec. 2).
+//
+// The residual is computed in two passes so that the expensive per-cell work
+// (two logarithms and the Lemma 2.2 series for p = u+v and q = u-v) is done exactly
+// once per cell; the FP64 pipe, not HBM, bounds both passes on GB300:
+//   pass A (g_kernel): G~^S = G1 + G2^S + G3 and the midpoint mobility c per cell;
+//   pass B (f_kernel): F_u = (u1-u0)/dt - [div c~ grad G_u], F_v = (v1-v0)/dt + c G_v/rho,
+//                      and per-block partial sums of ||F||^2.
+#include "acac_internal.cuh"
+
+namespace acac {
+
+__constant__ double c_taylor[MAX_S];   // 1 / ((2k)(2k+1)),  k = 1..S   (Lemma 2.2)
+__constant__ double c_rcoef[MAX_S];    // 1 / (2k+1),        k = 1..S   (its sigma/zeta derivative)
+
+static int g_taylor_S = -1;
+
+cudaError_t set_taylor_constants(int S) {
+    if (S == g_taylor_S) return cudaSuccess;
+    double a[MAX_S], b[MAX_S];
+    for (int k = 1; k <= MAX_S; ++k) {
+        a[k - 1] = 1.0 / ((2.0 * k) * (2.0 * k + 1.0));
+        b[k - 1] = 1.0 / (2.0 * k + 1.0);
+    }
+    cudaError_t e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef, b, sizeof(b));
+    if (e == cudaSuccess) g_taylor_S = S;
+    return e;
+}
+
+// sum_{k=1..S} r^k / ((2k)(2k+1)), Horner form.
+__device__ __forceinline__ double series_P(double r, int S) {
+    double acc = c_taylor[S - 1];
+    for (int k = S - 2; k >= 0; --k) acc = fma(acc, r, c_taylor[k]);
+    return acc * r;
+}
+// sum_{k=1..S} r^(k-1) / (2k+1), Horner form.
+__device__ __forceinline__ double series_R(double r, int S) {
+    double acc = c_rcoef[S - 1];
+    for (int k = S - 2; k >= 0; --k) acc = fma(acc, r, c_rcoef[k]);
+    return acc;
+}
+
+// phi^S(zeta, sigma): series form of [Phi(zeta+sigma) - Phi(zeta-sigma)] / (2 sigma)
+// (Lemma 2.2, Eq. D2-1, combination f_S(zeta,sigma) - f_S(1-zeta,sigma)):
+//   ln(zeta/(1-zeta)) - sum_k [(sigma/zeta)^{2k} - (sigma/(1-zeta))^{2k}] / ((2k)(2k+1)).
+__device__ __forceinline__ double phi_series(double zeta, double sigma, int S) {
+    const double om = 1.0 - zeta;
+    const double inv = 1.0 / (zeta * om);
+    const double a = sigma * om * inv;      // sigma / zeta
+    const double b = sigma * zeta * inv;    // sigma / (1 - zeta)
+    return log(zeta * zeta * inv) - (series_P(a * a, S) - series_P(b * b, S));
+}
+
+// d phi^S / d(end value) where zeta and sigma both move by 1/2:
+//   1/2 [ (1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta) ].
+__device__ __forceinline__ double dphi_series(double zeta, double sigma, int S) {
+    const double om = 1.0 - zeta;
+    const double iz = 1.0 / zeta, io = 1.0 / om;
+    const double a = sigma * iz, b = sigma * io;
+    const double Ra = series_R(a * a, S), Rb = series_R(b * b, S);
+    return 0.5 * ((1.0 + a * a * Ra - a * Ra) * iz + (1.0 + b * b * Rb + b * Rb) * io);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+    const unsigned full = 0xffffffffu;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        t = lane < nw ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(full, t, o);
+    }
+    return t;   // valid in thread 0
+}
+
+// ---------------------------------------------------------------- pass A
+__global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
+    const int N = g.N;
+    const double* __restrict__ Xu = a.X;
+    const double* __restrict__ Xv = a.X + N;
+    const double* __restrict__ Su = a.S;
+    const double* __restrict__ Sv = a.S ? a.S + N : nullptr;
+    const double* __restrict__ Pu = a.X0;
+    const double* __restrict__ Pv = a.X0 + N;
+    int flag = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int x = c % g.nx, y = c / g.nx;
+        int nbr[4];
+#pragma unroll
+        for (int f = 0; f < 4; ++f) nbr[f] = nb_index(g, x, y, face_dx(f), face_dy(f));
+        auto U1 = [&](int i) { return Su ? Xu[i] + a.lam * (Su[i] + a.shift) : Xu[i]; };
+        auto V1 = [&](int i) { return Sv ? Xv[i] + a.lam * Sv[i] : Xv[i]; };
+        const double u1 = U1(c), v1 = V1(c), u0 = Pu[c], v0 = Pv[c];
+        // Laplacians of u1 + u0 and v1 + v0 (G3): face differences, ghost = clamp
+        double lu = 0.0, lv = 0.0;
+        const double su = u1 + u0, sv = v1 + v0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const double ih2 = f < 2 ? g.ihx2 : g.ihy2;
+            const int n = nbr[f];
+            lu += (U1(n) + Pu[n] - su) * ih2;
+            lv += (V1(n) + Pv[n] - sv) * ih2;
+        }
+        // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma)
+        const double zp = 0.5 * ((u1 + v1) + (u0 + v0)), sp = 0.5 * ((u1 + v1) - (u0 + v0));
+        const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
+        if (!(zp > 0.0 && zp < 1.0 && zq > 0.0 && zq < 1.0)) flag |= 1;
+        double phi = 0.0, psi = 0.0;
+        if (!(flag & 1)) {
+            phi = phi_series(zp, sp, k.S);
+            psi = phi_series(zq, sq, k.S);
+        }
+        const double Gu = -0.5 * k.alpha * (su - 1.0) + k.theta * (phi + psi) - 0.5 * k.gamma * lu;
+        const double Gv = -0.5 * k.beta * sv + k.theta * (phi - psi) - 0.5 * k.gamma * lv;
+        const double ub = 0.5 * su, vb = 0.5 * sv;
+        a.G[c] = Gu;
+        a.G[N + c] = Gv;
+        a.G[2 * N + c] = ub * (1.0 - ub) * (0.25 - vb * vb);
+        if (Su) {
+            a.Xt[c] = u1;
+            a.Xt[N + c] = v1;
+            const double p1 = u1 + v1, q1 = u1 - v1;
+            if (!(p1 > 0.0 && p1 < 1.0 && q1 > 0.0 && q1 < 1.0)) flag |= 2;
+        }
+    }
+    if (flag) atomicOr(a.flags, flag);
+}
+
+// ---------------------------------------------------------------- pass B
+__global__ void __launch_bounds__(256) f_kernel(Geom g, Coef k, ResidualArgs a) {
+    __shared__ double sh[32];
+    const int N = g.N;
+    const double* __restrict__ X1 = a.S ? a.Xt : a.X;
+    const double* __restrict__ Gu = a.G;
+    const double* __restrict__ Gv = a.G + N;
+    const double* __restrict__ cm = a.G + 2 * N;
+    const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
+    double acc = 0.0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int x = c % g.nx, y = c / g.nx;
+        const double gc = Gu[c], cc = cm[c];
+        double div = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const double ih2 = f < 2 ? g.ihx2 : g.ihy2;
+            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
+            div += face_open(g, x, y, f) * ih2 * 0.5 * (cc + cm[n]) * (Gu[n] - gc);
+        }
+        const double Fu = (X1[c] - a.X0[c]) * idt - div;
+        const double Fv = (X1[N + c] - a.X0[N + c]) * idt + cc * Gv[c] * irho;
+        a.F[c] = Fu;
+        a.F[N + c] = Fv;
+        acc = fma(Fu, Fu, fma(Fv, Fv, acc));
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) a.partial[blockIdx.x] = t;
+}
+
+static int grid_for(long long n, int threads) {
+    long long b = (n + threads - 1) / threads;
+    return (int)(b < RED_BLOCKS ? (b < 1 ? 1 : b) : RED_BLOCKS);
+}
+
+cudaError_t launch_residual(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
+    cudaError_t e = set_taylor_constants(k.S);
+    if (e != cudaSuccess) return e;
+    const int nb = grid_for(g.N, 256);
+    g_kernel<<<nb, 256, 0, s>>>(g, k, a);
+    f_kernel<<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- energy / mass
+__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * log(z) : 0.0; }
+
+// E~ = sum [e1 + e2 + gamma/2 sum_d ((D+ phi)^2 + (D- phi)^2)/2] dx dy (Eqs. relations,
+// freeenergy) and sum u dx dy, as per-block partials [energy | mass].
+__global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const double* __restrict__ X,
+                                                     double* partial, int* flags) {
+    __shared__ double sh[32];
+    const int N = g.N;
+    const double* __restrict__ U = X;
+    const double* __restrict__ V = X + N;
+    const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy;
+    double e_acc = 0.0, m_acc = 0.0;
+    int flag = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const int x = c % g.nx, y = c / g.nx;
+        const double u = U[c], v = V[c];
+        const double p = u + v, q = u - v;
+        if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) flag |= 1;
+        double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v
+                 + k.theta * (xlogx(p) + xlogx(1.0 - p) + xlogx(q) + xlogx(1.0 - q));
+        double gr = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
+            const double ih = f < 2 ? ihx : ihy;
+            const double du = (U[n] - u) * ih, dv = (V[n] - v) * ih;
+            gr += du * du + dv * dv;
+        }
+        e += 0.25 * k.gamma * gr;   // gamma/2 * 1/2 * sum over D+ and D- of both fields
+        e_acc += e;
+        m_acc += u;
+    }
+    double t = block_sum(e_acc, sh);
+    if (threadIdx.x == 0) partial[blockIdx.x] = t * g.vol;
+    t = block_sum(m_acc, sh);
+    if (threadIdx.x == 0) partial[RED_BLOCKS + blockIdx.x] = t * g.vol;
+    if (flag) atomicOr(flags, flag);
+}
+
+cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
+                          int* flags, cudaStream_t s) {
+    energy_kernel<<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- linearisation
+// Per-cell derivative data of F at the accepted iterate X (G = [Gu | Gv | c] from
+// pass A at the same X):  cu = dc/du1, cv = dc/dv1 (c at the midpoint, so each picks
+// up a factor 1/2), du = -alpha/2 + theta (dphi/dp1 + dpsi/dq1), xc = theta (dphi/dp1 - dpsi/dq1).
+template <typename T>
+__global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const double* __restrict__ X,
+                                                        const double* __restrict__ X0,
+                                                        const double* __restrict__ G, Cache<T> C) {
+    const int N = g.N;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
+        const double ub = 0.5 * (u1 + u0), vb = 0.5 * (v1 + v0);
+        const double w = 0.25 - vb * vb;
+        const double zp = 0.5 * ((u1 + v1) + (u0 + v0)), sp = 0.5 * ((u1 + v1) - (u0 + v0));
+        const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
+        const double A = k.theta * dphi_series(zp, sp, k.S);
+        const double B = k.theta * dphi_series(zq, sq, k.S);
+        C.c[c] = (T)G[2 * N + c];
+        C.cu[c] = (T)(0.5 * (1.0 - 2.0 * ub) * w);
+        C.cv[c] = (T)(-ub * (1.0 - ub) * vb);
+        C.Gu[c] = (T)G[c];
+        C.Gv[c] = (T)G[N + c];
+        C.du[c] = (T)(-0.5 * k.alpha + A + B);
+        C.xc[c] = (T)(A - B);
+    }
+}
+
+template <typename T>
+cudaError_t launch_linearize(const Geom& g, const Coef& k, const double* X, const double* X0,
+                             const double* G, Cache<T> cache, cudaStream_t s) {
+    cudaError_t e = set_taylor_constants(k.S);
+    if (e != cudaSuccess) return e;
+    linearize_kernel<T><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, X, X0, G, cache);
+    return cudaGetLastError();
+}
+template cudaError_t launch_linearize<double>(const Geom&, const Coef&, const double*, const double*,
+                                              const double*, Cache<double>, cudaStream_t);
+template cudaError_t launch_linearize<float>(const Geom&, const Coef&, const double*, const double*,
+                                             const double*, Cache<float>, cudaStream_t);
+
+}  // namespace acac

@@ -1,0 +1,767 @@
+// Host side of the acac C ABI: handle and workspace, the inexact Newton iteration
+// with line search (Sec. 3.1, Eq. newton), restarted right-preconditioned GMRES
+// (Sec. 3.1, Eq. hjacobi; Hessenberg and Givens rotations on the host in double),
+// the subdomain tables of the Schwarz preconditioner, and the adaptive time step
+// of Sec. 3.2 (Eq. sencondt, with retry on divergence and eta doubling).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "acac_internal.cuh"
+
+using namespace acac;
+
+struct acac_handle {
+    acac_params p;
+    Geom g;
+    Coef k;
+    cudaStream_t stream;
+    bool mixed;
+    size_t N;
+    size_t ksz;                 // sizeof Krylov element
+    // FP64 state
+    double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
+    // Krylov precision buffers
+    void *V, *w, *z, *kt, *jtmp, *cache, *J, *coef, *gscratch;
+    size_t ldV;
+    // reductions
+    double* partial;            // RED_BLOCKS x (MAX_RESTART + 3)
+    double* red;                // device results
+    double* host;               // pinned host mirror of red
+    int* flags;
+    int* host_flags;
+    // Schwarz tables
+    std::vector<SubInfo> subs;
+    std::vector<int> lev;
+    SubInfo* subs_dev;
+    int* lev_dev;
+    int ras_threads;
+    size_t ras_smem;
+    long long coef_count;
+    // time stepping
+    double t, dt_prev, eta;
+    int nstep;
+    bool have_prev;
+    // counters of the current solve
+    int ls_cuts, n_factor;
+};
+
+namespace {
+
+struct Err {
+    int code;
+};
+
+#define CU(call)                                                                 \
+    do {                                                                         \
+        cudaError_t e_ = (call);                                                 \
+        if (e_ != cudaSuccess) throw Err{e_ == cudaErrorMemoryAllocation ? ACAC_E_NOMEM : ACAC_E_CUDA}; \
+    } while (0)
+
+template <typename T>
+Cache<T> cache_of(acac_handle* h) {
+    T* base = (T*)h->cache;
+    const size_t N = h->N;
+    return Cache<T>{base, base + N, base + 2 * N, base + 3 * N, base + 4 * N, base + 5 * N, base + 6 * N};
+}
+
+double read_scalars(acac_handle* h, int n) {
+    CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return h->host[0];
+}
+
+int read_flags(acac_handle* h) {
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    return *h->host_flags;
+}
+
+// ||F(X)|| (or of the trial point X + lam (S + shift e_u)) and the G buffer.
+double eval_residual(acac_handle* h, const double* X, const double* S, double lam, double shift,
+                     double dt, int* flags_out) {
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    ResidualArgs a;
+    a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
+    a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.partial = h->partial; a.flags = h->flags;
+    CU(launch_residual(h->g, h->k, a, h->stream));
+    CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    const double f2 = read_scalars(h, 1);
+    *flags_out = *h->host_flags;
+    return sqrt(f2);
+}
+
+template <typename T>
+void jac_action(acac_handle* h, double dt, const T* w, T* y) {
+    if (h->p.jac_mode == ACAC_JAC_ASSEMBLED)
+        CU(launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream));
+    else
+        CU(launch_jvp<T>(h->g, h->k, dt, cache_of<T>(h), w, y, (T*)h->jtmp, h->stream));
+}
+
+template <typename T>
+void precond(acac_handle* h, const T* r, T* z) {
+    CU(launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
+                           h->p.ras_type, h->ras_threads, h->ras_smem, (T*)h->gscratch, h->stream));
+}
+
+template <typename T>
+int factor(acac_handle* h) {
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    CU(launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J,
+                            (T*)h->coef, h->ras_threads, h->flags, h->stream));
+    h->n_factor++;
+    return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+}
+
+// Restarted GMRES for J x = b (b = h->b, double), x0 = 0, right preconditioning.
+// Returns ACAC_OK or ACAC_E_DIVERGED; x (double, 2N) receives the solution.
+template <typename T>
+int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out) {
+    const long long n = 2 * (long long)h->N;
+    const int m = h->p.gmres_restart;
+    T* V = (T*)h->V;
+    const long long ld = (long long)h->ldV;
+    T* w = (T*)h->w;
+    T* z = (T*)h->z;
+    T* tt = (T*)h->kt;
+    CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+    CU(launch_norm2_double(h->b, n, h->partial, h->stream));
+    CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+    const double bnorm = sqrt(read_scalars(h, 1));
+    const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
+    double beta = bnorm;
+    int its = 0;
+    double resid = beta;
+    *its_out = 0;
+    *resid_out = beta;
+    if (beta <= tol) return ACAC_OK;
+    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m + 1);
+    auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
+    const double* rsrc = h->b;
+    while (true) {
+        CU(launch_to_krylov<T>(rsrc, 1.0 / beta, V, n, h->stream));
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(gv.begin(), gv.end(), 0.0);
+        gv[0] = beta;
+        int k = 0;
+        bool done = false;
+        double hn = 0.0;
+        for (int j = 0; j < m; ++j) {
+            T* vj = V + (size_t)j * ld;
+            T* vn = V + (size_t)(j + 1) * ld;
+            precond<T>(h, vj, z);
+            jac_action<T>(h, dt, z, vn);
+            ++its;
+            // classical Gram–Schmidt, applied twice when cgs_refine
+            const int passes = h->p.cgs_refine ? 2 : 1;
+            for (int pass = 0; pass < passes; ++pass) {
+                CU(launch_multi_dot<T>(V, ld, j + 1, vn, n, h->partial, h->stream));
+                CU(launch_reduce_partials(h->partial, j + 1, RED_BLOCKS, h->red + pass * (MAX_RESTART + 1),
+                                          h->stream));
+                const bool last = pass == passes - 1;
+                CU(launch_cgs_update<T>(V, ld, j + 1, h->red + pass * (MAX_RESTART + 1), vn, n, last ? 1 : 0,
+                                        h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, h->stream));
+            }
+            CU(launch_reduce_partials(h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, 1, RED_BLOCKS,
+                                      h->red + 2 * (MAX_RESTART + 1), h->stream));
+            CU(launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
+            read_scalars(h, 3 * (MAX_RESTART + 1));
+            for (int i = 0; i <= j; ++i) {
+                double hij = h->host[i];
+                if (passes == 2) hij += h->host[(MAX_RESTART + 1) + i];
+                Hat(i, j) = hij;
+            }
+            hn = sqrt(h->host[2 * (MAX_RESTART + 1)]);
+            Hat(j + 1, j) = hn;
+            for (int i = 0; i < j; ++i) {
+                const double t0 = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
+                Hat(i + 1, j) = -sn[i] * Hat(i, j) + cs[i] * Hat(i + 1, j);
+                Hat(i, j) = t0;
+            }
+            const double rho = hypot(Hat(j, j), Hat(j + 1, j));
+            cs[j] = Hat(j, j) / rho;
+            sn[j] = Hat(j + 1, j) / rho;
+            Hat(j, j) = rho;
+            Hat(j + 1, j) = 0.0;
+            gv[j + 1] = -sn[j] * gv[j];
+            gv[j] = cs[j] * gv[j];
+            resid = fabs(gv[j + 1]);
+            k = j + 1;
+            if (!(resid == resid) || !isfinite(rho)) {
+                *its_out = its;
+                *resid_out = resid;
+                return ACAC_E_DIVERGED;
+            }
+            if (resid <= tol || its >= h->p.gmres_maxit || hn == 0.0) {
+                done = true;
+                break;
+            }
+        }
+        // y = H(1:k,1:k)^{-1} g(1:k);  x += M^{-1} (V y)
+        for (int i = k - 1; i >= 0; --i) {
+            double s = gv[i];
+            for (int jj = i + 1; jj < k; ++jj) s -= Hat(i, jj) * yv[jj];
+            yv[i] = s / Hat(i, i);
+        }
+        memcpy(h->host, yv.data(), sizeof(double) * k);
+        CU(cudaMemcpyAsync(h->red, h->host, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
+        CU(launch_lincomb<T>(V, ld, k, h->red, tt, n, h->stream));
+        precond<T>(h, tt, z);
+        CU(launch_axpy_to_double<T>(1.0, z, x, n, h->stream));
+        if (done) {
+            CU(cudaStreamSynchronize(h->stream));
+            *its_out = its;
+            *resid_out = resid;
+            return (resid <= tol || hn == 0.0) ? ACAC_OK : ACAC_E_DIVERGED;
+        }
+        // restart: r = b - J x
+        CU(launch_to_krylov<T>(x, 1.0, tt, n, h->stream));
+        jac_action<T>(h, dt, tt, w);
+        CU(launch_residual_restart<T>(h->b, w, h->r, n, h->partial, h->stream));
+        CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        beta = sqrt(read_scalars(h, 1));
+        rsrc = h->r;
+        if (beta <= tol) {
+            *its_out = its;
+            *resid_out = beta;
+            return ACAC_OK;
+        }
+    }
+}
+
+template <typename T>
+void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble) {
+    CU(launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
+    if (assemble) CU(launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
+}
+
+// Newton iteration from X_0 = X0 (device).  Root in h->X.
+template <typename T>
+int nks(acac_handle* h, double dt, acac_step_info* info) {
+    const size_t N = h->N;
+    const long long n = 2 * (long long)N;
+    CU(cudaMemcpyAsync(h->X, h->X0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    int fl = 0;
+    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl);
+    info->fnorm0 = info->fnorm = fnorm;
+    if (fl & 1) return ACAC_E_DOMAIN;
+    if (!isfinite(fnorm)) return ACAC_E_DIVERGED;
+    const double stop = std::max(h->p.newton_rtol * fnorm, h->p.newton_atol);
+    if (fnorm <= stop) return ACAC_OK;
+    int it = 0;
+    while (true) {
+        if (it >= h->p.newton_maxit) return ACAC_E_DIVERGED;
+        const bool refactor = (it == 0) || !h->p.ilu_reuse;
+        linearize_and_maybe_assemble<T>(h, h->X, dt, refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED);
+        if (refactor) {
+            int st = factor<T>(h);
+            if (st != ACAC_OK) return st;
+        }
+        // b = -F
+        CU(cudaMemsetAsync(h->b, 0, sizeof(double) * n, h->stream));
+        CU(launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
+        int gits = 0;
+        double gres = 0.0;
+        int st = gmres<T>(h, dt, h->S, &gits, &gres);
+        info->gmres_its += gits;
+        if (st != ACAC_OK) return st;
+        // shift S_u by a constant so that sum(u + S_u) = sum(u^n)
+        CU(launch_sum_pair(h->X0, h->X, h->S, (long long)N, h->partial, h->stream));
+        CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        const double shift = read_scalars(h, 1) / (double)N;
+        double lam = 1.0;
+        const double f2 = fnorm * fnorm;
+        double ft = 0.0;
+        while (true) {
+            ft = eval_residual(h, h->X, h->S, lam, shift, dt, &fl);
+            if (fl == 0 && isfinite(ft) && ft * ft <= (1.0 - 2e-4 * lam) * f2) break;
+            lam *= 0.5;
+            h->ls_cuts++;
+            if (lam < 1.0 / 1024.0) return ACAC_E_DIVERGED;
+        }
+        std::swap(h->X, h->Xt);
+        fnorm = ft;
+        ++it;
+        info->newton_its = it;
+        info->fnorm = fnorm;
+        if (fnorm <= stop) return ACAC_OK;
+    }
+}
+
+int nks_dispatch(acac_handle* h, double dt, acac_step_info* info) {
+    h->ls_cuts = 0;
+    h->n_factor = 0;
+    int st = h->mixed ? nks<float>(h, dt, info) : nks<double>(h, dt, info);
+    info->line_search_cuts += h->ls_cuts;
+    info->ilu_factorizations += h->n_factor;
+    return st;
+}
+
+// ---------------------------------------------------------------- Schwarz tables
+void partition_1d(int n, int P, std::vector<int>& s, std::vector<int>& e) {
+    int base = n / P, rem = n % P, pos = 0;
+    for (int k = 0; k < P; ++k) {
+        int w = base + (k < rem ? 1 : 0);
+        s.push_back(pos);
+        e.push_back(pos + w);
+        pos += w;
+    }
+}
+
+int build_subdomains(acac_handle* h) {
+    const acac_params& p = h->p;
+    const int d = p.ras_overlap;
+    std::vector<int> sx, ex, sy, ey;
+    partition_1d(p.n[0], p.ras_parts[0], sx, ex);
+    partition_1d(p.n[1], p.ras_parts[1], sy, ey);
+    h->subs.clear();
+    h->lev.clear();
+    long long coef = 0, vec = 0;
+    int maxcnt = 1;
+    size_t maxpad = 0;
+    for (int ky = 0; ky < p.ras_parts[1]; ++ky) {
+        for (int kx = 0; kx < p.ras_parts[0]; ++kx) {
+            SubInfo sd;
+            int lox, hix, loy, hiy;
+            if (p.bc == ACAC_BC_PERIODIC) {
+                lox = sx[kx] - d; hix = ex[kx] + d; loy = sy[ky] - d; hiy = ey[ky] + d;
+                if (hix - lox > p.n[0] - 2 || hiy - loy > p.n[1] - 2) return ACAC_E_ARG;
+            } else {
+                lox = std::max(0, sx[kx] - d); hix = std::min(p.n[0], ex[kx] + d);
+                loy = std::max(0, sy[ky] - d); hiy = std::min(p.n[1], ey[ky] + d);
+            }
+            sd.ox = lox; sd.oy = loy;
+            sd.W = hix - lox; sd.H = hiy - loy;
+            sd.own_x0 = sx[kx] - lox; sd.own_x1 = ex[kx] - lox;
+            sd.own_y0 = sy[ky] - loy; sd.own_y1 = ey[ky] - loy;
+            sd.nlev = (sd.W - 1) + 2 * (sd.H - 1) + 1;
+            sd.lev_base = (int)h->lev.size();
+            sd.coef_base = coef;
+            sd.vec_base = vec;
+            int acc = 0;
+            for (int l = 0; l < sd.nlev; ++l) {
+                h->lev.push_back(acc);
+                int cnt = 0;
+                for (int j = 0; j < sd.H; ++j) {
+                    int i = l - 2 * j;
+                    if (i >= 0 && i < sd.W) ++cnt;
+                }
+                maxcnt = std::max(maxcnt, cnt);
+                acc += cnt;
+            }
+            h->lev.push_back(acc);
+            coef += (long long)acc * NCOEF;
+            const size_t pad = (size_t)(sd.W + 4) * (sd.H + 4);
+            vec += (long long)pad;
+            maxpad = std::max(maxpad, pad);
+            h->subs.push_back(sd);
+        }
+    }
+    h->coef_count = coef;
+    h->ras_threads = std::max(64, ((maxcnt + 31) / 32) * 32);
+    if (h->ras_threads > 1024) h->ras_threads = 1024;
+    h->ras_smem = maxpad * 2 * h->ksz;
+    return ACAC_OK;
+}
+
+int validate(const acac_params* p) {
+    if (!p) return ACAC_E_ARG;
+    if (p->dim != 2) return ACAC_E_ARG;
+    if (p->n[0] < 4 || p->n[1] < 4) return ACAC_E_ARG;
+    if ((long long)p->n[0] * p->n[1] > (1LL << 30)) return ACAC_E_ARG;
+    if (!(p->L[0] > 0 && p->L[1] > 0)) return ACAC_E_ARG;
+    if (p->bc != ACAC_BC_PERIODIC && p->bc != ACAC_BC_NEUMANN) return ACAC_E_ARG;
+    if (!(p->alpha > 0 && p->beta > 0 && p->theta > 0 && p->gamma > 0 && p->rho > 0)) return ACAC_E_ARG;
+    if (p->taylor_S < 1 || p->taylor_S > MAX_S) return ACAC_E_ARG;
+    if (p->dt_mode != ACAC_DT_FIXED && p->dt_mode != ACAC_DT_ADAPTIVE) return ACAC_E_ARG;
+    if (!(p->dt0 > 0)) return ACAC_E_ARG;
+    if (p->dt_mode == ACAC_DT_ADAPTIVE && !(p->dt_min > 0 && p->dt_max >= p->dt_min && p->eta0 > 0))
+        return ACAC_E_ARG;
+    if (!(p->newton_rtol >= 0 && p->newton_atol >= 0) || p->newton_maxit < 1) return ACAC_E_ARG;
+    if (!(p->gmres_rtol >= 0 && p->gmres_atol >= 0) || p->gmres_maxit < 1) return ACAC_E_ARG;
+    if (p->gmres_restart < 1 || p->gmres_restart > MAX_RESTART) return ACAC_E_ARG;
+    if (p->ras_parts[0] < 1 || p->ras_parts[1] < 1 || p->ras_parts[0] > p->n[0] || p->ras_parts[1] > p->n[1])
+        return ACAC_E_ARG;
+    if (p->bc == ACAC_BC_PERIODIC && (p->ras_parts[0] < 2 || p->ras_parts[1] < 2)) return ACAC_E_ARG;
+    if (p->ras_overlap < 0) return ACAC_E_ARG;
+    if (p->ras_type < 0 || p->ras_type > 2) return ACAC_E_ARG;
+    if (p->precision != ACAC_FP64 && p->precision != ACAC_MIXED) return ACAC_E_ARG;
+    if (p->jac_mode != ACAC_JAC_MATFREE && p->jac_mode != ACAC_JAC_ASSEMBLED) return ACAC_E_ARG;
+    if (p->batch != 1) return ACAC_E_ARG;
+    return ACAC_OK;
+}
+
+template <typename P>
+void dmalloc(P** ptr, size_t bytes) {
+    void* q = nullptr;
+    CU(cudaMalloc(&q, bytes ? bytes : 16));
+    *ptr = (P*)q;
+}
+
+void free_all(acac_handle* h) {
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
+                    h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
+                    h->subs_dev, h->lev_dev};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (h->host) cudaFreeHost(h->host);
+    if (h->host_flags) cudaFreeHost(h->host_flags);
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+void acac_default_params(acac_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->dim = 2;
+    p->n[0] = 64; p->n[1] = 64; p->n[2] = 1;
+    p->L[0] = 1.0; p->L[1] = 1.0; p->L[2] = 1.0;
+    p->bc = ACAC_BC_PERIODIC;
+    p->alpha = 3.0; p->beta = 1.0; p->theta = 0.3; p->gamma = 1e-3; p->rho = 1.0;
+    p->taylor_S = 10;
+    p->dt_mode = ACAC_DT_FIXED;
+    p->dt0 = 1e-3; p->dt_min = 1e-5; p->dt_max = 1e-1; p->eta0 = 1e4;
+    p->newton_rtol = 1e-8; p->newton_atol = 1e-13; p->newton_maxit = 20;
+    p->gmres_rtol = 1e-6; p->gmres_atol = 1e-14; p->gmres_restart = 30; p->gmres_maxit = 500;
+    p->ras_parts[0] = 4; p->ras_parts[1] = 4; p->ras_parts[2] = 1;
+    p->ras_overlap = 1;
+    p->ras_type = ACAC_RAS_LEFT;
+    p->ilu_reuse = 1;
+    p->precision = ACAC_FP64;
+    p->jac_mode = ACAC_JAC_MATFREE;
+    p->batch = 1;
+    p->cgs_refine = 1;
+}
+
+const char* acac_status_string(int s) {
+    switch (s) {
+        case ACAC_OK: return "ok";
+        case ACAC_E_ARG: return "invalid argument";
+        case ACAC_E_CUDA: return "CUDA error";
+        case ACAC_E_DOMAIN: return "state outside the admissible set";
+        case ACAC_E_DIVERGED: return "Newton-Krylov-Schwarz solve diverged";
+        case ACAC_E_DT_UNDERFLOW: return "time step fell below dt_min";
+        case ACAC_E_TIMEOUT: return "device wait timed out";
+        case ACAC_E_NOMEM: return "out of memory";
+        default: return "unknown status";
+    }
+}
+
+int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
+    if (!out) return ACAC_E_ARG;
+    *out = nullptr;
+    int st = validate(p);
+    if (st != ACAC_OK) return st;
+    acac_handle* h = new (std::nothrow) acac_handle();
+    if (!h) return ACAC_E_NOMEM;
+    h->p = *p;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->mixed = p->precision == ACAC_MIXED;
+    h->ksz = h->mixed ? sizeof(float) : sizeof(double);
+    h->N = (size_t)p->n[0] * p->n[1];
+    Geom& g = h->g;
+    g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)h->N; g.bc = p->bc;
+    g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
+    g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
+    g.vol = g.hx * g.hy;
+    h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
+    h->eta = p->eta0;
+    st = build_subdomains(h);
+    if (st != ACAC_OK) {
+        delete h;
+        return st;
+    }
+    try {
+        const size_t N = h->N, n2 = 2 * N, ks = h->ksz;
+        dmalloc(&h->X, n2 * 8); dmalloc(&h->X0, n2 * 8); dmalloc(&h->Xprev, n2 * 8);
+        dmalloc(&h->Xt, n2 * 8); dmalloc(&h->F, n2 * 8); dmalloc(&h->S, n2 * 8);
+        dmalloc(&h->G, 3 * N * 8); dmalloc(&h->b, n2 * 8); dmalloc(&h->r, n2 * 8); dmalloc(&h->tmpd, n2 * 8);
+        dmalloc(&h->stage, n2 * 8);
+        h->ldV = (n2 + 63) / 64 * 64;
+        dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
+        dmalloc(&h->w, n2 * ks); dmalloc(&h->z, n2 * ks); dmalloc(&h->kt, n2 * ks);
+        dmalloc(&h->jtmp, 3 * N * ks);
+        dmalloc(&h->cache, 7 * N * ks);
+        dmalloc(&h->J, (size_t)NSLOT * 4 * N * ks);
+        dmalloc(&h->coef, (size_t)h->coef_count * ks);
+        int dev = 0;
+        CU(cudaGetDevice(&dev));
+        int optin = 0;
+        CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (h->ras_smem > (size_t)optin - 1024) {
+            size_t tot = 0;
+            for (auto& sd : h->subs) tot += (size_t)(sd.W + 4) * (sd.H + 4);
+            dmalloc(&h->gscratch, tot * 2 * ks);
+        }
+        dmalloc(&h->partial, (size_t)RED_BLOCKS * (MAX_RESTART + 3) * 8);
+        dmalloc(&h->red, (size_t)3 * (MAX_RESTART + 1) * 8);
+        dmalloc(&h->flags, 16);
+        CU(cudaMallocHost((void**)&h->host, (size_t)3 * (MAX_RESTART + 1) * 8));
+        CU(cudaMallocHost((void**)&h->host_flags, 16));
+        dmalloc(&h->subs_dev, h->subs.size() * sizeof(SubInfo));
+        dmalloc(&h->lev_dev, h->lev.size() * sizeof(int));
+        CU(cudaMemcpy(h->subs_dev, h->subs.data(), h->subs.size() * sizeof(SubInfo), cudaMemcpyHostToDevice));
+        CU(cudaMemcpy(h->lev_dev, h->lev.data(), h->lev.size() * sizeof(int), cudaMemcpyHostToDevice));
+        CU(set_taylor_constants(p->taylor_S));
+    } catch (Err e) {
+        free_all(h);
+        delete h;
+        return e.code;
+    }
+    *out = h;
+    return ACAC_OK;
+}
+
+void acac_destroy(acac_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    free_all(h);
+    delete h;
+}
+
+int acac_residual(acac_handle* h, const double* X1, const double* X0, double dt, double* F, double* fnorm) {
+    if (!h || !X1 || !X0 || !F || !(dt > 0)) return ACAC_E_ARG;
+    try {
+        const size_t n2 = 2 * h->N;
+        CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        int fl = 0;
+        double fn = eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
+        CU(cudaMemcpyAsync(F, h->F, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if (fnorm) *fnorm = fn;
+        return (fl & 1) ? ACAC_E_DOMAIN : ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+// Linearise at X1 (pass A of the residual fills G, then the cache).
+static int linearize_at(acac_handle* h, const double* X1, const double* X0, double dt) {
+    const size_t n2 = 2 * h->N;
+    CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+    int fl = 0;
+    eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
+    if (fl & 1) return ACAC_E_DOMAIN;
+    if (h->mixed)
+        CU(launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream));
+    else
+        CU(launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream));
+    return ACAC_OK;
+}
+
+int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt, void* J) {
+    if (!h || !X1 || !X0 || !J || !(dt > 0)) return ACAC_E_ARG;
+    try {
+        int st = linearize_at(h, X1, X0, dt);
+        if (st != ACAC_OK) return st;
+        if (h->mixed)
+            CU(launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)J, h->stream));
+        else
+            CU(launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)J, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
+    if (!h || !J || !w || !y) return ACAC_E_ARG;
+    cudaError_t e = h->mixed ? launch_spmv<float>(h->g, (const float*)J, (const float*)w, (float*)y, h->stream)
+                             : launch_spmv<double>(h->g, (const double*)J, (const double*)w, (double*)y, h->stream);
+    return e == cudaSuccess ? ACAC_OK : ACAC_E_CUDA;
+}
+
+int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, const void* w, void* y) {
+    if (!h || !X1 || !X0 || !w || !y || !(dt > 0)) return ACAC_E_ARG;
+    try {
+        int st = linearize_at(h, X1, X0, dt);
+        if (st != ACAC_OK) return st;
+        if (h->mixed)
+            CU(launch_jvp<float>(h->g, h->k, dt, cache_of<float>(h), (const float*)w, (float*)y,
+                                 (float*)h->jtmp, h->stream));
+        else
+            CU(launch_jvp<double>(h->g, h->k, dt, cache_of<double>(h), (const double*)w, (double*)y,
+                                  (double*)h->jtmp, h->stream));
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_ras_factor(acac_handle* h, const void* J) {
+    if (!h || !J) return ACAC_E_ARG;
+    try {
+        const size_t bytes = (size_t)NSLOT * 4 * h->N * h->ksz;
+        if (J != h->J) CU(cudaMemcpyAsync(h->J, J, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        return h->mixed ? factor<float>(h) : factor<double>(h);
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_ras_apply(acac_handle* h, const void* r, void* z) {
+    if (!h || !r || !z) return ACAC_E_ARG;
+    try {
+        if (h->mixed) precond<float>(h, (const float*)r, (float*)z);
+        else precond<double>(h, (const double*)r, (double*)z);
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, const double* b, double* x,
+               int* its, double* resid) {
+    if (!h || !X1 || !X0 || !b || !x || !(dt > 0)) return ACAC_E_ARG;
+    try {
+        int st = linearize_at(h, X1, X0, dt);
+        if (st != ACAC_OK) return st;
+        int gi = 0;
+        double gr = 0.0;
+        CU(cudaMemcpyAsync(h->b, b, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        if (h->mixed) {
+            CU(launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
+            st = factor<float>(h);
+            if (st == ACAC_OK) st = gmres<float>(h, dt, x, &gi, &gr);
+        } else {
+            CU(launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)h->J, h->stream));
+            st = factor<double>(h);
+            if (st == ACAC_OK) st = gmres<double>(h, dt, x, &gi, &gr);
+        }
+        if (its) *its = gi;
+        if (resid) *resid = gr;
+        return st;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac_step_info* info) {
+    if (!h || !U0 || !U1 || !(dt > 0)) return ACAC_E_ARG;
+    acac_step_info local;
+    memset(&local, 0, sizeof(local));
+    int st;
+    try {
+        CU(cudaMemcpyAsync(h->X0, U0, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        st = nks_dispatch(h, dt, &local);
+        if (st == ACAC_OK) CU(cudaMemcpyAsync(U1, h->X, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+    } catch (Err e) {
+        st = e.code;
+    }
+    local.status = st;
+    local.dt = dt;
+    if (info) *info = local;
+    return st;
+}
+
+static int energy_of(acac_handle* h, const double* X, double* e, double* m) {
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    CU(launch_energy(h->g, h->k, X, h->partial, h->flags, h->stream));
+    CU(launch_reduce_partials(h->partial, 2, RED_BLOCKS, h->red, h->stream));
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    read_scalars(h, 2);
+    if (e) *e = h->host[0];
+    if (m) *m = h->host[1];
+    return *h->host_flags ? ACAC_E_DOMAIN : ACAC_OK;
+}
+
+int acac_energy(acac_handle* h, const double* u, const double* v, double* energy, double* mass) {
+    if (!h || !u || !v) return ACAC_E_ARG;
+    try {
+        const size_t N = h->N;
+        CU(cudaMemcpyAsync(h->tmpd, u, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->tmpd + N, v, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        return energy_of(h, h->tmpd, energy, mass);
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
+    if (!h || !u || !v) return ACAC_E_ARG;
+    acac_step_info local;
+    memset(&local, 0, sizeof(local));
+    int st = ACAC_OK;
+    try {
+        const size_t N = h->N;
+        const long long n2 = 2 * (long long)N;
+        CU(cudaMemcpyAsync(h->X0, u, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->X0 + N, v, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        // predictor of Eq. sencondt
+        double dt = h->p.dt0;
+        if (h->p.dt_mode == ACAC_DT_ADAPTIVE && h->have_prev) {
+            CU(cudaMemsetAsync(h->tmpd, 0, n2 * 8, h->stream));
+            CU(launch_axpy_to_double<double>(1.0, h->X0, h->tmpd, n2, h->stream));
+            CU(launch_axpy_to_double<double>(-1.0, h->Xprev, h->tmpd, n2, h->stream));
+            CU(launch_norm2_double(h->tmpd, n2, h->partial, h->stream));
+            CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+            const double xd = sqrt(read_scalars(h, 1)) / h->dt_prev;
+            dt = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta * xd * xd));
+        }
+        while (true) {
+            st = nks_dispatch(h, dt, &local);
+            if (st == ACAC_OK) break;
+            if (st != ACAC_E_DIVERGED) break;
+            local.divergences++;
+            if (h->p.dt_mode == ACAC_DT_FIXED) break;
+            dt = dt / sqrt(2.0);
+            h->eta *= 2.0;
+            if (dt < h->p.dt_min) {
+                st = ACAC_E_DT_UNDERFLOW;
+                break;
+            }
+        }
+        if (st == ACAC_OK) {
+            CU(cudaMemcpyAsync(h->Xprev, h->X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+            CU(cudaMemcpyAsync(u, h->X, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+            CU(cudaMemcpyAsync(v, h->X + N, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+            h->dt_prev = dt;
+            h->t += dt;
+            h->nstep++;
+            h->have_prev = true;
+            double e = 0.0, m = 0.0;
+            energy_of(h, h->X, &e, &m);
+            local.energy = e;
+            local.mass = m;
+            local.dt = dt;
+            local.t = h->t;
+        }
+        local.eta = h->eta;
+    } catch (Err e) {
+        st = e.code;
+    }
+    local.status = st;
+    if (info) *info = local;
+    return st;
+}
+
+int acac_step_host(acac_handle* h, double* u_host, double* v_host, acac_step_info* info) {
+    if (!h || !u_host || !v_host) return ACAC_E_ARG;
+    try {
+        const size_t N = h->N;
+        CU(cudaMemcpyAsync(h->stage, u_host, N * 8, cudaMemcpyHostToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->stage + N, v_host, N * 8, cudaMemcpyHostToDevice, h->stream));
+        int st = acac_step(h, h->stage, h->stage + N, info);
+        if (st == ACAC_OK) {
+            CU(cudaMemcpyAsync(u_host, h->stage, N * 8, cudaMemcpyDeviceToHost, h->stream));
+            CU(cudaMemcpyAsync(v_host, h->stage + N, N * 8, cudaMemcpyDeviceToHost, h->stream));
+        }
+        CU(cudaStreamSynchronize(h->stream));
+        return st;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+}  // extern "C"
