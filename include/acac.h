@@ -192,6 +192,43 @@ int acac_gmres(acac_handle *h, const double *X1, const double *X0, double dt,
 int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
                    acac_step_info *info);
 
+/* ---- instrumentation ---------------------------------------------------------- */
+
+/* Kernel classes counted and timed by the handle (one __global__ each, except
+ * ACAC_K_VECTOR, which gathers the small vector kernels of GMRES and Newton). */
+#define ACAC_K_RESIDUAL_G    0    /* G~^S and mobility per cell (pass A of F)        */
+#define ACAC_K_RESIDUAL_F    1    /* F and ||F||^2 partials (pass B of F)             */
+#define ACAC_K_LINEARIZE     2    /* per-cell derivative cache                        */
+#define ACAC_K_ASSEMBLE      3    /* stencil-diagonal Jacobian                        */
+#define ACAC_K_SPMV          4    /* assembled y = J w                                */
+#define ACAC_K_JVP_G         5    /* matrix-free J w, pass 1                          */
+#define ACAC_K_JVP_F         6    /* matrix-free J w, pass 2                          */
+#define ACAC_K_RAS_FACTOR    7    /* batched subdomain ILU(0)                         */
+#define ACAC_K_RAS_APPLY     8    /* batched restriction, triangular sweeps, extension */
+#define ACAC_K_DOT           9    /* Gram–Schmidt block dot products                  */
+#define ACAC_K_CGS_UPDATE   10    /* Gram–Schmidt update (and norm)                   */
+#define ACAC_K_REDUCE       11    /* final stage of the reductions                    */
+#define ACAC_K_VECTOR       12    /* other vector kernels                             */
+#define ACAC_K_ENERGY       13    /* energy and mass                                  */
+#define ACAC_NKERNEL        14
+
+/* Reset the per-kernel counters; enable != 0 also brackets every launch with CUDA
+ * events on the handle's stream (durations are collected at the next
+ * synchronisation).  Launch counts are kept whether or not timing is enabled.
+ * Synchronises the stream. */
+int acac_profile(acac_handle *h, int enable);
+
+/* Since the last acac_profile: launches of kernel class `kernel`, their summed
+ * event-timed duration in ms (0 unless timing was enabled), and their summed
+ * algorithmic HBM bytes and floating-point operations (the minimum traffic and
+ * arithmetic of the operation, from the launch sizes; 0 where not modelled).
+ * Any output pointer may be NULL.  Synchronises. */
+int acac_kernel_stats(acac_handle *h, int kernel, long long *launches, double *total_ms,
+                      double *bytes, double *flops);
+
+/* Static name of a kernel class. */
+const char *acac_kernel_name(int kernel);
+
 #ifdef __cplusplus
 }
 #endif

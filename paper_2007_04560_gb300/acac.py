@@ -82,7 +82,12 @@ SIGNATURES = {
     "acac_ras_apply": (ctypes.c_int, [_P, _P, _P]),
     "acac_gmres": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _PI, _PD]),
     "acac_nks_solve": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(acac_step_info)]),
+    "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
+    "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
 }
+
+NKERNEL = 14
 
 _LIB = None
 
@@ -265,6 +270,20 @@ class Solver:
         if check:
             _check(st, "acac_gmres")
         return its.value, res.value, st
+
+    # -- instrumentation
+    def profile(self, enable=True):
+        _check(_lib().acac_profile(self.h, 1 if enable else 0), "acac_profile")
+
+    def kernel_stats(self):
+        """{name: (launches, total_ms, algorithmic_bytes, algorithmic_flops)} per kernel class."""
+        out = {}
+        for k in range(NKERNEL):
+            n, ms, b, f = ctypes.c_longlong(), ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+            _check(_lib().acac_kernel_stats(self.h, k, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(b),
+                                            ctypes.byref(f)), "acac_kernel_stats")
+            out[_lib().acac_kernel_name(k).decode()] = (n.value, ms.value, b.value, f.value)
+        return out
 
     def nks_solve(self, U0, dt, U1, check=True):
         import torch

@@ -21,11 +21,13 @@
 namespace acac {
 
 constexpr int NSLOT = 13;          // radius-2 stencil (|o|_1 <= 2) in 2D
-constexpr int NCOEF = 52;          // 6 lower 2x2 blocks, inverse pivot block, 6 upper blocks
+constexpr int NCOEF = 56;          // stored per cell: forward record + backward record
+constexpr int CREC = 28;           // record: 6 lower 2x2 blocks (+4 pad) | inverse pivot + 6 upper blocks
 constexpr int MAX_S = 30;          // Lemma 2.2 series terms accepted
 constexpr int MAX_RESTART = 64;
 constexpr int RED_BLOCKS = 1216;   // 152 SMs x 8: partial-sum blocks of the reductions
 constexpr int RED_THREADS = 256;
+constexpr int RAS_MAXBUF = 16;    // coefficient stages of the Schwarz apply ring
 
 // Stencil slot order (dx, dy); mirrored in include/acac.h for acac_jacobian.
 __host__ __device__ constexpr int slot_dx(int s) {
@@ -112,6 +114,20 @@ struct SubInfo {
     long long vec_base;  // first padded-vector element in the global scratch
 };
 
+// Row pitch (in cells) of a padded box vector: W + 4, made odd so that the cells of
+// one wavefront level (row stride pitch - 2) fall into distinct shared-memory banks.
+__host__ __device__ constexpr int ras_pitch(int W) { return (W + 4) | 1; }
+
+// Shared-memory plan of the Schwarz apply kernel (bytes / elements).
+struct RasLaunch {
+    int nbuf;            // coefficient stages in flight
+    int threads;         // consumer warps (2 threads per cell of the widest level) + 1 producer warp
+    int stage_elems;     // elements per stage (>= 28 x the largest level)
+    int stage_off;       // byte offset of the stages (after mbarriers and level table)
+    int vec_off;         // byte offset of the box vector when it is in shared memory
+    size_t smem_bytes;   // dynamic shared memory per CTA
+};
+
 // ---------------------------------------------------------------- kernels (launchers)
 // residual.cu
 cudaError_t set_taylor_constants(int S);
@@ -127,7 +143,8 @@ struct ResidualArgs {
     double* partial;     // RED_BLOCKS partial sums of F^2
     int* flags;          // bit 0: midpoint inadmissible, bit 1: trial state inadmissible
 };
-cudaError_t launch_residual(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
                           int* flags, cudaStream_t s);
 template <typename T>
@@ -141,8 +158,11 @@ cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> ca
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
 template <typename T>
-cudaError_t launch_jvp(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w,
-                       T* y, T* tmp, cudaStream_t s);
+cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp,
+                         cudaStream_t s);
+template <typename T>
+cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w,
+                         const T* tmp, T* y, cudaStream_t s);
 
 // krylov.cu
 cudaError_t launch_reduce_partials(const double* partial, int nvec, int nparts, double* out,
@@ -177,6 +197,6 @@ cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, cons
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             size_t smem_bytes, T* gscratch, cudaStream_t s);
+                             const RasLaunch& L, T* gscratch, int* err, cudaStream_t s);
 
 }  // namespace acac

@@ -173,9 +173,14 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Ca
 }
 
 template <typename T>
-cudaError_t launch_jvp(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
-                       T* tmp, cudaStream_t s) {
+cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
     jvp1_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, const T* tmp,
+                         T* y, cudaStream_t s) {
     jvp2_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
     return cudaGetLastError();
 }
@@ -184,8 +189,10 @@ cudaError_t launch_jvp(const Geom& g, const Coef& k, double dt, Cache<T> cache, 
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
                                             cudaStream_t);                                        \
     template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
-    template cudaError_t launch_jvp<T>(const Geom&, const Coef&, double, Cache<T>, const T*, T*,  \
-                                       T*, cudaStream_t);
+    template cudaError_t launch_jvp_g<T>(const Geom&, const Coef&, Cache<T>, const T*, T*,         \
+                                         cudaStream_t);                                           \
+    template cudaError_t launch_jvp_f<T>(const Geom&, const Coef&, double, Cache<T>, const T*,     \
+                                         const T*, T*, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

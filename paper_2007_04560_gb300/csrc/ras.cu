@@ -35,12 +35,22 @@ __device__ __forceinline__ int box_cell(const Geom& g, const SubInfo& sd, int i,
     return gy * g.nx + gx;
 }
 
-// Address of coefficient q of box cell (i, j) in the level-major storage.
-__device__ __forceinline__ long long coef_addr(const SubInfo& sd, const int* lo, int i, int j, int q) {
+// Coefficient storage of one level with cnt cells (offset lo[l] * NCOEF in the
+// subdomain): a forward block of cnt records [L blocks q=0..5, row-major 2x2; 4 pad]
+// and then a backward block of cnt records [D^-1 (4) | U blocks q=0..5 (24)], each
+// record CREC values.  A record per cell keeps one thread's coefficients contiguous
+// (wide shared loads, no per-coefficient address arithmetic); CREC = 28 makes the
+// records of neighbouring threads fall into distinct shared-memory banks.
+__device__ __forceinline__ long long fwd_addr(const SubInfo& sd, const int* lo, int i, int j) {
+    const int l = i + 2 * j;
+    const int t = j - level_jmin(l, sd.W);
+    return sd.coef_base + (long long)lo[l] * NCOEF + (long long)t * CREC;
+}
+__device__ __forceinline__ long long bwd_addr(const SubInfo& sd, const int* lo, int i, int j) {
     const int l = i + 2 * j;
     const int cnt = lo[l + 1] - lo[l];
     const int t = j - level_jmin(l, sd.W);
-    return sd.coef_base + (long long)lo[l] * NCOEF + (long long)q * cnt + t;
+    return sd.coef_base + (long long)lo[l] * NCOEF + (long long)(cnt + t) * CREC;
 }
 
 template <typename T>
@@ -73,16 +83,18 @@ __global__ void ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs, cons
 #pragma unroll
                 for (int e = 0; e < 4; ++e) A[s][e] = in ? J[(size_t)(s * 4 + e) * N + gc] : (T)0;
             }
-            const long long base = (long long)lo[l] * NCOEF + sd.coef_base;
+            T* fw = coef + fwd_addr(sd, lo, i, j);
+            T* bw = coef + bwd_addr(sd, lo, i, j);
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 const int dx1 = lower_dx(a), dy1 = lower_dy(a);
                 const int ki = i + dx1, kj = j + dy1;
                 T L[4] = {0, 0, 0, 0};
                 if (ki >= 0 && ki < sd.W && kj >= 0 && kj < sd.H) {
+                    const T* kb = coef + bwd_addr(sd, lo, ki, kj);
                     T Dk[4];
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) Dk[e] = coef[coef_addr(sd, lo, ki, kj, 24 + e)];
+                    for (int e = 0; e < 4; ++e) Dk[e] = kb[e];
                     mul22(A[slot_of(dx1, dy1)], Dk, L);
 #pragma unroll
                     for (int b = 0; b < 6; ++b) {
@@ -90,7 +102,7 @@ __global__ void ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs, cons
                         if (s2 >= 0) {
                             T U[4], P[4];
 #pragma unroll
-                            for (int e = 0; e < 4; ++e) U[e] = coef[coef_addr(sd, lo, ki, kj, 28 + 4 * b + e)];
+                            for (int e = 0; e < 4; ++e) U[e] = kb[4 + 4 * b + e];
                             mul22(L, U, P);
 #pragma unroll
                             for (int e = 0; e < 4; ++e) A[s2][e] -= P[e];
@@ -98,22 +110,23 @@ __global__ void ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs, cons
                     }
                 }
 #pragma unroll
-                for (int e = 0; e < 4; ++e) coef[base + (long long)(4 * a + e) * cnt + t] = L[e];
+                for (int e = 0; e < 4; ++e) fw[4 * a + e] = L[e];
             }
+#pragma unroll
+            for (int e = 24; e < CREC; ++e) fw[e] = (T)0;
             const T* D = A[0];
             const T det = D[0] * D[3] - D[1] * D[2];
             if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
             const T id = (T)1 / det;
-            coef[base + (long long)24 * cnt + t] = D[3] * id;
-            coef[base + (long long)25 * cnt + t] = -D[1] * id;
-            coef[base + (long long)26 * cnt + t] = -D[2] * id;
-            coef[base + (long long)27 * cnt + t] = D[0] * id;
+            bw[0] = D[3] * id;
+            bw[1] = -D[1] * id;
+            bw[2] = -D[2] * id;
+            bw[3] = D[0] * id;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
                 const int s = slot_of(upper_dx(b), upper_dy(b));
 #pragma unroll
-                for (int e = 0; e < 4; ++e)
-                    coef[base + (long long)(28 + 4 * b + e) * cnt + t] = A[s][e];
+                for (int e = 0; e < 4; ++e) bw[4 + 4 * b + e] = A[s][e];
             }
         }
         __syncthreads();
@@ -132,73 +145,240 @@ cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, cons
 // z = sum_k E_k inv(L_k U_k) R_k r with E_k the restricted (left-RAS) or full
 // (AS, right-RAS) extension and R_k the full (left-RAS, AS) or restricted
 // (right-RAS) restriction.  The box vector lives in a zero-padded (W+4)x(H+4)
-// array (shared memory when it fits, else the subdomain's global scratch).
+// array: shared memory when it fits, else the subdomain's global scratch.
+//
+// The sweeps are latency bound (2 x nlev dependent levels), so the coefficients of
+// each level, stored contiguously (forward part [24][cnt], backward part
+// [28][cnt]), are streamed into a ring of NBUF shared-memory stages by one thread
+// with cp.async.bulk (TMA) and an mbarrier per stage, NBUF levels ahead of the
+// level being solved.  Stage k of the 2*nlev stages is forward level k for
+// k < nlev and backward level 2*nlev-1-k after that.  Every mbarrier wait is bounded
+// by the global timer; on expiry the CTA records ACAC_E_TIMEOUT in *err, drains the
+// copies it issued (again bounded) and returns without writing z.
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Bounded wait: false after ~0.5 s without completion.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 500000000ull) return false;
+    }
+}
+
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Producer / consumer pipeline.  The last warp is the producer: its lane 0 streams
+// level stages into the ring (full[b] completes when a stage has landed) and reuses
+// buffer b only after the consumers released it (empty[b]).  The other warps are
+// the consumers: two threads per cell, thread (m, rr) solving row rr of the m-th
+// cell of the level, synchronised level by level by a named barrier.
 template <typename T>
-__global__ void ras_apply_kernel(Geom g, const SubInfo* __restrict__ subs, const int* __restrict__ lev_off,
-                                 const T* __restrict__ coef, const T* __restrict__ r, T* __restrict__ z,
-                                 int ras_type, T* gscratch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+__global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                        const int* __restrict__ lev_off,
+                                                        const T* __restrict__ coef, const T* __restrict__ r,
+                                                        T* __restrict__ z, int ras_type, T* gscratch,
+                                                        RasLaunch L, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_cabort, s_pabort;   // consumer / producer gave up on a wait
+    __shared__ int s_issued, s_consumed;
     const SubInfo sd = subs[blockIdx.x];
-    const int* lo = lev_off + sd.lev_base;
     const int N = g.N;
-    const int PW = sd.W + 4, PH = sd.H + 4;
+    const int PW = ras_pitch(sd.W), PH = sd.H + 4;
+    const int nlev = sd.nlev;
+    const int nst = 2 * nlev;
+    const int nbuf = L.nbuf;
+    const int ncons = blockDim.x - 32;          // consumer threads (a multiple of 32)
+    const bool producer = threadIdx.x >= ncons;
+    // shared layout: full[RAS_MAXBUF] | empty[RAS_MAXBUF] | level table | stages | (box vector)
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + RAS_MAXBUF;
+    int* lo = reinterpret_cast<int*>(smem_raw + 16 * RAS_MAXBUF);
+    T* stages = reinterpret_cast<T*>(smem_raw + L.stage_off);
     V2<T>* yv = gscratch ? reinterpret_cast<V2<T>*>(gscratch) + sd.vec_base
-                         : reinterpret_cast<V2<T>*>(smem_raw);
+                         : reinterpret_cast<V2<T>*>(smem_raw + L.vec_off);
+    T* ys = reinterpret_cast<T*>(yv);        // component view: ys[2 * cell + row]
+    const T* cbase = coef + sd.coef_base;
+
+    for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
+    if (threadIdx.x == 0) {
+        s_cabort = 0;
+        s_pabort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(smem_addr(&full[b]), 1);
+            mbar_init(smem_addr(&empty[b]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int k) {   // stage k into buffer k % nbuf (producer lane only)
+        const bool fwd = k < nlev;
+        const int l = fwd ? k : nst - 1 - k;
+        const int cnt = lo[l + 1] - lo[l];
+        const T* src = cbase + (long long)lo[l] * NCOEF + (fwd ? 0 : (long long)cnt * CREC);
+        const uint32_t bytes = (uint32_t)(CREC * cnt * sizeof(T));
+        const int b = k % nbuf;
+        const uint32_t bar = smem_addr(&full[b]);
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(stages + (size_t)b * L.stage_elems), src, bytes, bar);
+    };
+    if (threadIdx.x == ncons) {
+        const int first = nbuf < nst ? nbuf : nst;
+        for (int k = 0; k < first; ++k) issue(k);
+        s_issued = first;
+    }
+
+    // restriction: gather r over the box (padding stays zero); loads are batched
+    // GATHER at a time per thread so that their latencies overlap
     for (int idx = threadIdx.x; idx < PW * PH; idx += blockDim.x) yv[idx] = V2<T>{(T)0, (T)0};
     __syncthreads();
-    for (int idx = threadIdx.x; idx < sd.W * sd.H; idx += blockDim.x) {
-        const int i = idx % sd.W, j = idx / sd.W;
-        const int gc = box_cell(g, sd, i, j);
-        const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1;
-        V2<T> val{r[gc], r[N + gc]};
-        if (ras_type == ACAC_RAS_RIGHT && !own) val = V2<T>{(T)0, (T)0};
-        yv[(j + 2) * PW + i + 2] = val;
+    constexpr int GATHER = 8;
+    const int ncell = sd.W * sd.H;
+    for (int base = 0; base < ncell; base += GATHER * blockDim.x) {
+        V2<T> val[GATHER];
+        int dst[GATHER];
+#pragma unroll
+        for (int q = 0; q < GATHER; ++q) {
+            const int idx = base + q * blockDim.x + threadIdx.x;
+            dst[q] = -1;
+            if (idx < ncell) {
+                const int i = idx % sd.W, j = idx / sd.W;
+                const int gc = box_cell(g, sd, i, j);
+                const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1;
+                val[q] = V2<T>{r[gc], r[N + gc]};
+                if (ras_type == ACAC_RAS_RIGHT && !own) val[q] = V2<T>{(T)0, (T)0};
+                dst[q] = (j + 2) * PW + i + 2;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < GATHER; ++q)
+            if (dst[q] >= 0) yv[dst[q]] = val[q];
     }
     __syncthreads();
-    // forward: y_c -= sum_lower L_c,o y_{c+o}
-    for (int l = 0; l < sd.nlev; ++l) {
-        const int cnt = lo[l + 1] - lo[l];
-        const int jmin = level_jmin(l, sd.W);
-        const T* cf = coef + sd.coef_base + (long long)lo[l] * NCOEF;
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int j = jmin + t, i = l - 2 * j;
-            const int pc = (j + 2) * PW + i + 2;
-            V2<T> a = yv[pc];
-#pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                const V2<T> nb = yv[pc + lower_dy(b) * PW + lower_dx(b)];
-                const T l0 = cf[(4 * b + 0) * cnt + t], l1 = cf[(4 * b + 1) * cnt + t];
-                const T l2 = cf[(4 * b + 2) * cnt + t], l3 = cf[(4 * b + 3) * cnt + t];
-                a.x -= l0 * nb.x + l1 * nb.y;
-                a.y -= l2 * nb.x + l3 * nb.y;
+
+    if (producer) {
+        if (threadIdx.x == ncons) {
+            for (int k = nbuf; k < nst; ++k) {
+                const int b = k % nbuf;
+                if (!mbar_wait_bounded(smem_addr(&empty[b]), (uint32_t)(((k / nbuf) - 1) & 1))) {
+                    s_pabort = 1;
+                    break;
+                }
+                issue(k);
+                s_issued = k + 1;
             }
-            yv[pc] = a;
         }
-        __syncthreads();
-    }
-    // backward: y_c = D^-1 (y_c - sum_upper U_c,o y_{c+o})
-    for (int l = sd.nlev - 1; l >= 0; --l) {
-        const int cnt = lo[l + 1] - lo[l];
-        const int jmin = level_jmin(l, sd.W);
-        const T* cf = coef + sd.coef_base + (long long)lo[l] * NCOEF;
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int j = jmin + t, i = l - 2 * j;
-            const int pc = (j + 2) * PW + i + 2;
-            V2<T> a = yv[pc];
+    } else {
+        const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+        // neighbour offsets in the padded box (cells)
+        int offL[6], offU[6];
 #pragma unroll
-            for (int b = 0; b < 6; ++b) {
-                const V2<T> nb = yv[pc + upper_dy(b) * PW + upper_dx(b)];
-                const T u0 = cf[(28 + 4 * b + 0) * cnt + t], u1 = cf[(28 + 4 * b + 1) * cnt + t];
-                const T u2 = cf[(28 + 4 * b + 2) * cnt + t], u3 = cf[(28 + 4 * b + 3) * cnt + t];
-                a.x -= u0 * nb.x + u1 * nb.y;
-                a.y -= u2 * nb.x + u3 * nb.y;
-            }
-            const T d0 = cf[24 * cnt + t], d1 = cf[25 * cnt + t], d2 = cf[26 * cnt + t], d3 = cf[27 * cnt + t];
-            yv[pc] = V2<T>{d0 * a.x + d1 * a.y, d2 * a.x + d3 * a.y};
+        for (int q = 0; q < 6; ++q) {
+            offL[q] = lower_dy(q) * PW + lower_dx(q);
+            offU[q] = upper_dy(q) * PW + upper_dx(q);
         }
-        __syncthreads();
+        int k = 0;
+        for (; k < nst; ++k) {
+            const int b = k % nbuf;
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
+            const bool fwd = k < nlev;
+            const int l = fwd ? k : nst - 1 - k;
+            const int cnt = lo[l + 1] - lo[l];
+            const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+            const int pc = (j + 2) * PW + i + 2;
+            const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
+            const bool act = m < cnt && landed;
+            if (fwd) {
+                if (act) {
+                    // row rr: y_c -= sum_lower L_c,o y_{c+o}  (two independent chains)
+                    T a0 = ys[2 * pc + rr], a1 = (T)0;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = yv[pc + offL[q]];
+                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                    ys[2 * pc + rr] = a0 + a1;
+                }
+            } else {
+                // row rr of s = y_c - sum_upper U_c,o y_{c+o}; then y_c = D^-1 s
+                T a0 = (T)0, a1 = (T)0;
+                if (act) {
+                    a0 = ys[2 * pc + rr];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = yv[pc + offU[q]];
+                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                }
+                const T s_me = a0 + a1;
+                const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
+                if (act) {
+                    const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
+                    ys[2 * pc + rr] = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
+                }
+            }
+            // all consumers done with this level and with stage b; the barrier also
+            // ORs "a wait gave up" over the consumers so that all of them agree
+            uint32_t gave_up;
+            asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
+            if (gave_up) {
+                if (threadIdx.x == 0) s_cabort = 1;
+                break;
+            }
+            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[b]));
+        }
+        if (threadIdx.x == 0) s_consumed = k;
     }
-    for (int idx = threadIdx.x; idx < sd.W * sd.H; idx += blockDim.x) {
+    __syncthreads();
+    if (s_cabort || s_pabort) {
+        // drain the copies issued but not consumed (bounded), then leave without writing z
+        if (threadIdx.x == 0) {
+            for (int kk = s_consumed; kk < s_issued; ++kk)
+                mbar_wait_bounded(smem_addr(&full[kk % nbuf]), (uint32_t)((kk / nbuf) & 1));
+            atomicOr(err, 8);
+        }
+        return;
+    }
+    // extension
+    for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
         const int i = idx % sd.W, j = idx / sd.W;
         const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1;
         const int gc = box_cell(g, sd, i, j);
@@ -215,21 +395,21 @@ __global__ void ras_apply_kernel(Geom g, const SubInfo* __restrict__ subs, const
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             size_t smem_bytes, T* gscratch, cudaStream_t s) {
-    static bool attr_set[2] = {false, false};
+                             const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
+    static size_t attr_bytes[2] = {0, 0};
     const int which = sizeof(T) == 8 ? 0 : 1;
-    if (!gscratch && smem_bytes > 48 * 1024 && !attr_set[which]) {
+    if (L.smem_bytes > attr_bytes[which]) {
         cudaError_t e = cudaFuncSetAttribute(ras_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             227 * 1024);
+                                             (int)L.smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_set[which] = true;
+        attr_bytes[which] = L.smem_bytes;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
         if (e != cudaSuccess) return e;
     }
-    ras_apply_kernel<T><<<nsub, threads, gscratch ? 0 : smem_bytes, s>>>(g, subs, lev_off, coef, r, z,
-                                                                         ras_type, gscratch);
+    ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
+                                                            err);
     return cudaGetLastError();
 }
 
@@ -237,7 +417,8 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                               T*, int, int*, cudaStream_t);                         \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
-                                             const T*, T*, int, int, size_t, T*, cudaStream_t);
+                                             const T*, T*, int, int, const RasLaunch&, T*, int*,       \
+                                             cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -167,11 +167,14 @@ static int grid_for(long long n, int threads) {
     return (int)(b < RED_BLOCKS ? (b < 1 ? 1 : b) : RED_BLOCKS);
 }
 
-cudaError_t launch_residual(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
+cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
-    const int nb = grid_for(g.N, 256);
-    g_kernel<<<nb, 256, 0, s>>>(g, k, a);
+    g_kernel<<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     f_kernel<<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
     return cudaGetLastError();
 }

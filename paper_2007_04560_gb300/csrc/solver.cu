@@ -41,13 +41,26 @@ struct acac_handle {
     int* lev_dev;
     int ras_threads;
     size_t ras_smem;
+    RasLaunch ras_launch;
     long long coef_count;
+    double nbox;                // cells of all subdomain boxes (overlap counted)
+    int ras_maxlev, ras_maxcnt;
+    size_t ras_maxpad;
     // time stepping
     double t, dt_prev, eta;
     int nstep;
     bool have_prev;
     // counters of the current solve
     int ls_cuts, n_factor;
+    // kernel launch counts and (when enabled) CUDA-event timings per kernel
+    bool prof_on;
+    long long launches[ACAC_NKERNEL];
+    double kernel_ms[ACAC_NKERNEL];
+    double kernel_bytes[ACAC_NKERNEL];   // algorithmic HBM bytes of the counted launches
+    double kernel_flops[ACAC_NKERNEL];   // algorithmic floating-point operations
+    struct Pending { int id; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace {
@@ -62,6 +75,61 @@ struct Err {
         if (e_ != cudaSuccess) throw Err{e_ == cudaErrorMemoryAllocation ? ACAC_E_NOMEM : ACAC_E_CUDA}; \
     } while (0)
 
+cudaEvent_t take_event(acac_handle* h) {
+    if (!h->pool.empty()) {
+        cudaEvent_t e = h->pool.back();
+        h->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e;
+    CU(cudaEventCreate(&e));
+    return e;
+}
+
+// Adds the durations of completed timed launches (call after a stream sync).
+void prof_collect(acac_handle* h) {
+    for (auto& p : h->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->kernel_ms[p.id] += ms;
+        h->pool.push_back(p.a);
+        h->pool.push_back(p.b);
+    }
+    h->pending.clear();
+}
+
+// Brackets one kernel launch: counts it and, when profiling, records CUDA events
+// around it on the handle's stream.
+struct KScope {
+    acac_handle* h;
+    cudaEvent_t b;
+    KScope(acac_handle* h_, int id, double bytes = 0.0, double flops = 0.0) : h(h_), b(nullptr) {
+        h->launches[id]++;
+        h->kernel_bytes[id] += bytes;
+        h->kernel_flops[id] += flops;
+        if (h->prof_on) {
+            cudaEvent_t a = take_event(h);
+            b = take_event(h);
+            CU(cudaEventRecord(a, h->stream));
+            h->pending.push_back({id, a, b});
+        }
+    }
+    ~KScope() {
+        if (b) cudaEventRecord(b, h->stream);
+    }
+};
+
+#define KL(id, call)                 \
+    do {                             \
+        KScope ks_(h, id);           \
+        CU(call);                    \
+    } while (0)
+// Same, with the launch's algorithmic HBM bytes and floating-point operations.
+#define KLA(id, bytes, flops, call)          \
+    do {                                     \
+        KScope ks_(h, id, (bytes), (flops)); \
+        CU(call);                            \
+    } while (0)
+
 template <typename T>
 Cache<T> cache_of(acac_handle* h) {
     T* base = (T*)h->cache;
@@ -72,12 +140,14 @@ Cache<T> cache_of(acac_handle* h) {
 double read_scalars(acac_handle* h, int n) {
     CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
     return h->host[0];
 }
 
 int read_flags(acac_handle* h) {
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
     return *h->host_flags;
 }
 
@@ -88,8 +158,9 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     ResidualArgs a;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
     a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.partial = h->partial; a.flags = h->flags;
-    CU(launch_residual(h->g, h->k, a, h->stream));
-    CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * (S ? 11 : 7), 0.0, launch_residual_g(h->g, h->k, a, h->stream));
+    KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
+    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double f2 = read_scalars(h, 1);
     *flags_out = *h->host_flags;
@@ -97,23 +168,31 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
 }
 
 template <typename T>
+void jvp_action(acac_handle* h, double dt, const T* w, T* y) {
+    KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N, launch_jvp_g<T>(h->g, h->k, cache_of<T>(h), w, (T*)h->jtmp, h->stream));
+    KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N, launch_jvp_f<T>(h->g, h->k, dt, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream));
+}
+
+template <typename T>
 void jac_action(acac_handle* h, double dt, const T* w, T* y) {
     if (h->p.jac_mode == ACAC_JAC_ASSEMBLED)
-        CU(launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream));
+        KLA(ACAC_K_SPMV, (double)sizeof(T) * h->N * 56, 104.0 * h->N, launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream));
     else
-        CU(launch_jvp<T>(h->g, h->k, dt, cache_of<T>(h), w, y, (T*)h->jtmp, h->stream));
+        jvp_action<T>(h, dt, w, y);
 }
 
 template <typename T>
 void precond(acac_handle* h, const T* r, T* z) {
-    CU(launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
-                           h->p.ras_type, h->ras_threads, h->ras_smem, (T*)h->gscratch, h->stream));
+    KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
+        launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
+                            h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch, h->flags + 1,
+                            h->stream));
 }
 
 template <typename T>
 int factor(acac_handle* h) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-    CU(launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J,
+    KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox, launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J,
                             (T*)h->coef, h->ras_threads, h->flags, h->stream));
     h->n_factor++;
     return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
@@ -131,8 +210,8 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
     T* z = (T*)h->z;
     T* tt = (T*)h->kt;
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
-    CU(launch_norm2_double(h->b, n, h->partial, h->stream));
-    CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+    KL(ACAC_K_VECTOR, launch_norm2_double(h->b, n, h->partial, h->stream));
+    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
     const double bnorm = sqrt(read_scalars(h, 1));
     const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
     double beta = bnorm;
@@ -145,7 +224,7 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
     auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
     const double* rsrc = h->b;
     while (true) {
-        CU(launch_to_krylov<T>(rsrc, 1.0 / beta, V, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_to_krylov<T>(rsrc, 1.0 / beta, V, n, h->stream));
         std::fill(H.begin(), H.end(), 0.0);
         std::fill(gv.begin(), gv.end(), 0.0);
         gv[0] = beta;
@@ -161,16 +240,16 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
             // classical Gram–Schmidt, applied twice when cgs_refine
             const int passes = h->p.cgs_refine ? 2 : 1;
             for (int pass = 0; pass < passes; ++pass) {
-                CU(launch_multi_dot<T>(V, ld, j + 1, vn, n, h->partial, h->stream));
-                CU(launch_reduce_partials(h->partial, j + 1, RED_BLOCKS, h->red + pass * (MAX_RESTART + 1),
+                KLA(ACAC_K_DOT, (double)sizeof(T) * n * (j + 2), 2.0 * n * (j + 1), launch_multi_dot<T>(V, ld, j + 1, vn, n, h->partial, h->stream));
+                KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, j + 1, RED_BLOCKS, h->red + pass * (MAX_RESTART + 1),
                                           h->stream));
                 const bool last = pass == passes - 1;
-                CU(launch_cgs_update<T>(V, ld, j + 1, h->red + pass * (MAX_RESTART + 1), vn, n, last ? 1 : 0,
+                KLA(ACAC_K_CGS_UPDATE, (double)sizeof(T) * n * (j + 3), 2.0 * n * (j + 2), launch_cgs_update<T>(V, ld, j + 1, h->red + pass * (MAX_RESTART + 1), vn, n, last ? 1 : 0,
                                         h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, h->stream));
             }
-            CU(launch_reduce_partials(h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, 1, RED_BLOCKS,
+            KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, 1, RED_BLOCKS,
                                       h->red + 2 * (MAX_RESTART + 1), h->stream));
-            CU(launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
+            KL(ACAC_K_VECTOR, launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
             read_scalars(h, 3 * (MAX_RESTART + 1));
             for (int i = 0; i <= j; ++i) {
                 double hij = h->host[i];
@@ -211,20 +290,22 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
         }
         memcpy(h->host, yv.data(), sizeof(double) * k);
         CU(cudaMemcpyAsync(h->red, h->host, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-        CU(launch_lincomb<T>(V, ld, k, h->red, tt, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_lincomb<T>(V, ld, k, h->red, tt, n, h->stream));
         precond<T>(h, tt, z);
-        CU(launch_axpy_to_double<T>(1.0, z, x, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, z, x, n, h->stream));
         if (done) {
+            CU(cudaMemcpyAsync(h->host_flags + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
             CU(cudaStreamSynchronize(h->stream));
             *its_out = its;
             *resid_out = resid;
+            if (h->host_flags[1]) return ACAC_E_TIMEOUT;
             return (resid <= tol || hn == 0.0) ? ACAC_OK : ACAC_E_DIVERGED;
         }
         // restart: r = b - J x
-        CU(launch_to_krylov<T>(x, 1.0, tt, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_to_krylov<T>(x, 1.0, tt, n, h->stream));
         jac_action<T>(h, dt, tt, w);
-        CU(launch_residual_restart<T>(h->b, w, h->r, n, h->partial, h->stream));
-        CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, h->partial, h->stream));
+        KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
         beta = sqrt(read_scalars(h, 1));
         rsrc = h->r;
         if (beta <= tol) {
@@ -237,8 +318,8 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
 
 template <typename T>
 void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble) {
-    CU(launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
-    if (assemble) CU(launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
+    KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0, launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
+    if (assemble) KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0, launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
 }
 
 // Newton iteration from X_0 = X0 (device).  Root in h->X.
@@ -265,15 +346,15 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         }
         // b = -F
         CU(cudaMemsetAsync(h->b, 0, sizeof(double) * n, h->stream));
-        CU(launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
         int gits = 0;
         double gres = 0.0;
         int st = gmres<T>(h, dt, h->S, &gits, &gres);
         info->gmres_its += gits;
         if (st != ACAC_OK) return st;
         // shift S_u by a constant so that sum(u + S_u) = sum(u^n)
-        CU(launch_sum_pair(h->X0, h->X, h->S, (long long)N, h->partial, h->stream));
-        CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, h->partial, h->stream));
+        KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
         const double shift = read_scalars(h, 1) / (double)N;
         double lam = 1.0;
         const double f2 = fnorm * fnorm;
@@ -340,6 +421,7 @@ int build_subdomains(acac_handle* h) {
             sd.W = hix - lox; sd.H = hiy - loy;
             sd.own_x0 = sx[kx] - lox; sd.own_x1 = ex[kx] - lox;
             sd.own_y0 = sy[ky] - loy; sd.own_y1 = ey[ky] - loy;
+            if (sd.W > 500 || sd.H > 500) return ACAC_E_ARG;
             sd.nlev = (sd.W - 1) + 2 * (sd.H - 1) + 1;
             sd.lev_base = (int)h->lev.size();
             sd.coef_base = coef;
@@ -357,13 +439,19 @@ int build_subdomains(acac_handle* h) {
             }
             h->lev.push_back(acc);
             coef += (long long)acc * NCOEF;
-            const size_t pad = (size_t)(sd.W + 4) * (sd.H + 4);
+            const size_t pad = (size_t)ras_pitch(sd.W) * (sd.H + 4);
             vec += (long long)pad;
             maxpad = std::max(maxpad, pad);
             h->subs.push_back(sd);
         }
     }
     h->coef_count = coef;
+    int maxlev = 0;
+    for (auto& sd : h->subs) maxlev = std::max(maxlev, sd.nlev);
+    h->ras_maxlev = maxlev;
+    h->ras_maxcnt = maxcnt;
+    h->ras_maxpad = maxpad;
+    h->nbox = (double)(coef / NCOEF);
     h->ras_threads = std::max(64, ((maxcnt + 31) / 32) * 32);
     if (h->ras_threads > 1024) h->ras_threads = 1024;
     h->ras_smem = maxpad * 2 * h->ksz;
@@ -497,14 +585,44 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         CU(cudaGetDevice(&dev));
         int optin = 0;
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-        if (h->ras_smem > (size_t)optin - 1024) {
-            size_t tot = 0;
-            for (auto& sd : h->subs) tot += (size_t)(sd.W + 4) * (sd.H + 4);
-            dmalloc(&h->gscratch, tot * 2 * ks);
+        // shared-memory plan of the Schwarz apply: mbarriers | level table | coefficient
+        // stages | box vector.  Prefer a plan with two CTAs per SM.
+        {
+            auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
+            RasLaunch& L = h->ras_launch;
+            L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
+            L.stage_elems = (CREC * h->ras_maxcnt + 31) / 32 * 32;
+            L.threads = 32 * ((2 * h->ras_maxcnt + 31) / 32) + 32;
+            const size_t vec_bytes = r128(h->ras_maxpad * 2 * ks);
+            const size_t stage_bytes = (size_t)L.stage_elems * ks;
+            const size_t cap = (size_t)optin - 2048;
+            // The sweeps stream every level's coefficients once: keep as many stages in
+            // flight per SM as shared memory allows (TMA latency is several us).  With
+            // the box vector in shared memory, take two CTAs per SM when at least 3 stages
+            // fit per CTA, else one CTA per SM with up to RAS_MAXBUF stages.
+            bool vec_in_smem = false;
+            const size_t half = 113 * 1024;
+            if (L.stage_off + vec_bytes + 3 * stage_bytes <= half) {
+                L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (half - L.stage_off - vec_bytes) / stage_bytes);
+                vec_in_smem = true;
+            } else if (L.stage_off + vec_bytes + 4 * stage_bytes <= cap) {
+                L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (cap - L.stage_off - vec_bytes) / stage_bytes);
+                vec_in_smem = true;
+            } else {
+                L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (cap - L.stage_off) / stage_bytes);
+            }
+            L.vec_off = (int)(L.stage_off + (size_t)L.nbuf * L.stage_elems * ks);
+            L.smem_bytes = L.vec_off + (vec_in_smem ? vec_bytes : 0);
+            if (!vec_in_smem) {
+                size_t tot = 0;
+                for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
+                dmalloc(&h->gscratch, tot * 2 * ks);
+            }
         }
         dmalloc(&h->partial, (size_t)RED_BLOCKS * (MAX_RESTART + 3) * 8);
         dmalloc(&h->red, (size_t)3 * (MAX_RESTART + 1) * 8);
         dmalloc(&h->flags, 16);
+        CU(cudaMemset(h->flags, 0, 16));
         CU(cudaMallocHost((void**)&h->host, (size_t)3 * (MAX_RESTART + 1) * 8));
         CU(cudaMallocHost((void**)&h->host_flags, 16));
         dmalloc(&h->subs_dev, h->subs.size() * sizeof(SubInfo));
@@ -524,8 +642,54 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
 void acac_destroy(acac_handle* h) {
     if (!h) return;
     cudaStreamSynchronize(h->stream);
+    for (auto& p : h->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : h->pool) cudaEventDestroy(e);
     free_all(h);
     delete h;
+}
+
+int acac_profile(acac_handle* h, int enable) {
+    if (!h) return ACAC_E_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
+    try {
+        prof_collect(h);
+    } catch (Err e) {
+        return e.code;
+    }
+    h->prof_on = enable != 0;
+    for (int i = 0; i < ACAC_NKERNEL; ++i) {
+        h->launches[i] = 0;
+        h->kernel_ms[i] = 0.0;
+        h->kernel_bytes[i] = 0.0;
+        h->kernel_flops[i] = 0.0;
+    }
+    return ACAC_OK;
+}
+
+int acac_kernel_stats(acac_handle* h, int kernel, long long* launches, double* total_ms, double* bytes,
+                      double* flops) {
+    if (!h || kernel < 0 || kernel >= ACAC_NKERNEL) return ACAC_E_ARG;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
+    try {
+        prof_collect(h);
+    } catch (Err e) {
+        return e.code;
+    }
+    if (launches) *launches = h->launches[kernel];
+    if (total_ms) *total_ms = h->kernel_ms[kernel];
+    if (bytes) *bytes = h->kernel_bytes[kernel];
+    if (flops) *flops = h->kernel_flops[kernel];
+    return ACAC_OK;
+}
+
+const char* acac_kernel_name(int kernel) {
+    static const char* names[ACAC_NKERNEL] = {
+        "residual_g", "residual_f", "linearize", "assemble", "spmv", "jvp_g", "jvp_f",
+        "ras_factor", "ras_apply", "gs_dot", "gs_update", "reduce", "vector", "energy"};
+    return (kernel >= 0 && kernel < ACAC_NKERNEL) ? names[kernel] : "unknown";
 }
 
 int acac_residual(acac_handle* h, const double* X1, const double* X0, double dt, double* F, double* fnorm) {
@@ -552,9 +716,9 @@ static int linearize_at(acac_handle* h, const double* X1, const double* X0, doub
     eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
     if (fl & 1) return ACAC_E_DOMAIN;
     if (h->mixed)
-        CU(launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream));
+        KL(ACAC_K_LINEARIZE, launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream));
     else
-        CU(launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream));
+        KL(ACAC_K_LINEARIZE, launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream));
     return ACAC_OK;
 }
 
@@ -564,9 +728,9 @@ int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt,
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
         if (h->mixed)
-            CU(launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)J, h->stream));
         else
-            CU(launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)J, h->stream));
         CU(cudaStreamSynchronize(h->stream));
         return ACAC_OK;
     } catch (Err e) {
@@ -576,9 +740,15 @@ int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt,
 
 int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
     if (!h || !J || !w || !y) return ACAC_E_ARG;
-    cudaError_t e = h->mixed ? launch_spmv<float>(h->g, (const float*)J, (const float*)w, (float*)y, h->stream)
-                             : launch_spmv<double>(h->g, (const double*)J, (const double*)w, (double*)y, h->stream);
-    return e == cudaSuccess ? ACAC_OK : ACAC_E_CUDA;
+    try {
+        if (h->mixed)
+            KL(ACAC_K_SPMV, launch_spmv<float>(h->g, (const float*)J, (const float*)w, (float*)y, h->stream));
+        else
+            KL(ACAC_K_SPMV, launch_spmv<double>(h->g, (const double*)J, (const double*)w, (double*)y, h->stream));
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
 }
 
 int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, const void* w, void* y) {
@@ -586,12 +756,8 @@ int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, cons
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
-        if (h->mixed)
-            CU(launch_jvp<float>(h->g, h->k, dt, cache_of<float>(h), (const float*)w, (float*)y,
-                                 (float*)h->jtmp, h->stream));
-        else
-            CU(launch_jvp<double>(h->g, h->k, dt, cache_of<double>(h), (const double*)w, (double*)y,
-                                  (double*)h->jtmp, h->stream));
+        if (h->mixed) jvp_action<float>(h, dt, (const float*)w, (float*)y);
+        else jvp_action<double>(h, dt, (const double*)w, (double*)y);
         return ACAC_OK;
     } catch (Err e) {
         return e.code;
@@ -630,11 +796,11 @@ int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, co
         double gr = 0.0;
         CU(cudaMemcpyAsync(h->b, b, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
         if (h->mixed) {
-            CU(launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
             st = factor<float>(h);
             if (st == ACAC_OK) st = gmres<float>(h, dt, x, &gi, &gr);
         } else {
-            CU(launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)h->J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)h->J, h->stream));
             st = factor<double>(h);
             if (st == ACAC_OK) st = gmres<double>(h, dt, x, &gi, &gr);
         }
@@ -667,8 +833,8 @@ int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac
 
 static int energy_of(acac_handle* h, const double* X, double* e, double* m) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-    CU(launch_energy(h->g, h->k, X, h->partial, h->flags, h->stream));
-    CU(launch_reduce_partials(h->partial, 2, RED_BLOCKS, h->red, h->stream));
+    KLA(ACAC_K_ENERGY, 16.0 * h->N, 0.0, launch_energy(h->g, h->k, X, h->partial, h->flags, h->stream));
+    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 2, RED_BLOCKS, h->red, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     read_scalars(h, 2);
     if (e) *e = h->host[0];
@@ -702,10 +868,10 @@ int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
         double dt = h->p.dt0;
         if (h->p.dt_mode == ACAC_DT_ADAPTIVE && h->have_prev) {
             CU(cudaMemsetAsync(h->tmpd, 0, n2 * 8, h->stream));
-            CU(launch_axpy_to_double<double>(1.0, h->X0, h->tmpd, n2, h->stream));
-            CU(launch_axpy_to_double<double>(-1.0, h->Xprev, h->tmpd, n2, h->stream));
-            CU(launch_norm2_double(h->tmpd, n2, h->partial, h->stream));
-            CU(launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+            KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(1.0, h->X0, h->tmpd, n2, h->stream));
+            KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->Xprev, h->tmpd, n2, h->stream));
+            KL(ACAC_K_VECTOR, launch_norm2_double(h->tmpd, n2, h->partial, h->stream));
+            KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
             const double xd = sqrt(read_scalars(h, 1)) / h->dt_prev;
             dt = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta * xd * xd));
         }
