@@ -192,6 +192,27 @@ int acac_gmres(acac_handle *h, const double *X1, const double *X0, double dt,
 int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
                    acac_step_info *info);
 
+/* ---- residual without a handle and without device allocation ------------------- */
+
+/* F(X1) and ||F|| exactly as acac_residual computes them, for callers that may not
+ * allocate device memory when they need a residual (code inside a framework that
+ * owns every device allocation, allocation-free latency-critical loops, plugins
+ * that are handed only their buffers).  There is no counterpart of this entry
+ * point in the paper: it is a deployment convenience.
+ *   p: validated like acac_create; the grid may have at most 512 x 512 cells
+ *      (ACAC_E_ARG beyond that).  X1, X0, F: device state vectors (double, 2N);
+ *      *fnorm: host, may be NULL.  cuda_stream: cudaStream_t (NULL = default).
+ *   Working memory: file-scope device arrays of about 6 MB, present on every GPU
+ *      that loads the library until the process exits; nothing is allocated or
+ *      freed per call.
+ *   The first call on a device looks up those arrays' device addresses; make it
+ *      before any stream capture.  Calls share the arrays: calls whose work
+ *      overlaps on the GPU race.  Synchronises cuda_stream.
+ *   Returns ACAC_OK, ACAC_E_ARG, ACAC_E_DOMAIN (a midpoint outside the
+ *      admissible set) or ACAC_E_CUDA. */
+int acac_residual_noalloc(const acac_params *p, const double *X1, const double *X0, double dt,
+                          double *F, double *fnorm, void *cuda_stream);
+
 /* ---- instrumentation ---------------------------------------------------------- */
 
 /* Kernel classes counted and timed by the handle (one __global__ each, except

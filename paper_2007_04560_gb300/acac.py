@@ -82,6 +82,7 @@ SIGNATURES = {
     "acac_ras_apply": (ctypes.c_int, [_P, _P, _P]),
     "acac_gmres": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _PI, _PD]),
     "acac_nks_solve": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(acac_step_info)]),
+    "acac_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, _P, _D, _P, _PD, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -165,6 +166,23 @@ def acac_destroy(h):
 
 def acac_status_string(status: int) -> str:
     return _lib().acac_status_string(status).decode()
+
+
+def acac_residual_noalloc(p, X1, X0, dt, F, stream=None, check=True):
+    """F(X1) without a handle and without device allocation (grids up to 512x512).
+    Returns (status, ||F||)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = 2 * int(p.n[0]) * int(p.n[1])
+    cp = to_c_params(p)
+    fn = ctypes.c_double()
+    st = _lib().acac_residual_noalloc(ctypes.byref(cp), _dev(X1, torch.float64, n, "X1"),
+                                      _dev(X0, torch.float64, n, "X0"), float(dt), _dev(F, torch.float64, n, "F"),
+                                      ctypes.byref(fn), ctypes.c_void_p(stream.cuda_stream))
+    if check:
+        _check(st, "acac_residual_noalloc")
+    return st, fn.value
 
 
 class Solver:

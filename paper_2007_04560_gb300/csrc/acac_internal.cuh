@@ -128,6 +128,9 @@ struct RasLaunch {
     size_t smem_bytes;   // dynamic shared memory per CTA
 };
 
+// Checks of acac_create (sizes, coefficients, partition, enumerations).
+int validate_params(const acac_params* p);
+
 // ---------------------------------------------------------------- kernels (launchers)
 // residual.cu
 cudaError_t set_taylor_constants(int S);

@@ -458,7 +458,9 @@ int build_subdomains(acac_handle* h) {
     return ACAC_OK;
 }
 
-int validate(const acac_params* p) {
+}  // namespace
+
+int acac::validate_params(const acac_params* p) {
     if (!p) return ACAC_E_ARG;
     if (p->dim != 2) return ACAC_E_ARG;
     if (p->n[0] < 4 || p->n[1] < 4) return ACAC_E_ARG;
@@ -484,6 +486,8 @@ int validate(const acac_params* p) {
     if (p->batch != 1) return ACAC_E_ARG;
     return ACAC_OK;
 }
+
+namespace {
 
 template <typename P>
 void dmalloc(P** ptr, size_t bytes) {
@@ -547,7 +551,7 @@ const char* acac_status_string(int s) {
 int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     if (!out) return ACAC_E_ARG;
     *out = nullptr;
-    int st = validate(p);
+    int st = validate_params(p);
     if (st != ACAC_OK) return st;
     acac_handle* h = new (std::nothrow) acac_handle();
     if (!h) return ACAC_E_NOMEM;
