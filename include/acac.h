@@ -213,6 +213,11 @@ int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
 int acac_residual_noalloc(const acac_params *p, const double *X1, const double *X0, double dt,
                           double *F, double *fnorm, void *cuda_stream);
 
+/* y[i] = ln x[i] (device arrays, n values) with the logarithm the residual and energy
+ * kernels use (a table-driven reduction: Tang, ACM TOMS 1990).  Enqueued on
+ * cuda_stream; exposed so that its accuracy can be checked against a reference. */
+int acac_log(const double *x, double *y, long long n, void *cuda_stream);
+
 /* ---- instrumentation ---------------------------------------------------------- */
 
 /* Kernel classes counted and timed by the handle (one __global__ each, except

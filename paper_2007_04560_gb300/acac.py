@@ -83,6 +83,7 @@ SIGNATURES = {
     "acac_gmres": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _PI, _PD]),
     "acac_nks_solve": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(acac_step_info)]),
     "acac_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, _P, _D, _P, _PD, _P]),
+    "acac_log": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
@@ -183,6 +184,15 @@ def acac_residual_noalloc(p, X1, X0, dt, F, stream=None, check=True):
     if check:
         _check(st, "acac_residual_noalloc")
     return st, fn.value
+
+
+def acac_log(x, y, stream=None):
+    """y = ln x with the library's device logarithm (float64 CUDA tensors)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    _check(_lib().acac_log(_dev(x, torch.float64, None, "x"), _dev(y, torch.float64, x.numel(), "y"),
+                           x.numel(), ctypes.c_void_p(stream.cuda_stream)), "acac_log")
 
 
 class Solver:

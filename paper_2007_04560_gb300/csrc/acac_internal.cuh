@@ -62,6 +62,7 @@ struct Geom {
     double hx, hy;
     double ihx2, ihy2;   // 1/hx^2, 1/hy^2
     double vol;          // hx*hy
+    float ihx2f, ihy2f;  // the same in float, for the FP32 Jacobian kernels
 };
 
 struct Coef {
@@ -88,6 +89,21 @@ __device__ __forceinline__ double face_open(const Geom& g, int x, int y, int f) 
     if (g.bc == ACAC_BC_PERIODIC) return 1.0;
     int xx = x + face_dx(f), yy = y + face_dy(f);
     return (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny) ? 1.0 : 0.0;
+}
+// 1/h^2 of face f of cell (x, y) if it carries flux, else 0, in precision T.
+template <typename T>
+__device__ __forceinline__ T face_w(const Geom& g, int x, int y, int f);
+template <>
+__device__ __forceinline__ double face_w<double>(const Geom& g, int x, int y, int f) {
+    int xx = x + face_dx(f), yy = y + face_dy(f);
+    const bool open = g.bc == ACAC_BC_PERIODIC || (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny);
+    return open ? (f < 2 ? g.ihx2 : g.ihy2) : 0.0;
+}
+template <>
+__device__ __forceinline__ float face_w<float>(const Geom& g, int x, int y, int f) {
+    int xx = x + face_dx(f), yy = y + face_dy(f);
+    const bool open = g.bc == ACAC_BC_PERIODIC || (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny);
+    return open ? (f < 2 ? g.ihx2f : g.ihy2f) : 0.0f;
 }
 __device__ __forceinline__ bool in_domain(const Geom& g, int x, int y) {
     return g.bc == ACAC_BC_PERIODIC || (x >= 0 && x < g.nx && y >= 0 && y < g.ny);
@@ -121,7 +137,8 @@ __host__ __device__ constexpr int ras_pitch(int W) { return (W + 4) | 1; }
 // Shared-memory plan of the Schwarz apply kernel (bytes / elements).
 struct RasLaunch {
     int nbuf;            // coefficient stages in flight
-    int threads;         // consumer warps (2 threads per cell of the widest level) + 1 producer warp
+    int tpc;             // consumer threads per cell (2 or 4)
+    int threads;         // consumer warps (tpc threads per cell of the widest level) + 1 producer warp
     int stage_elems;     // elements per stage (>= 28 x the largest level)
     int stage_off;       // byte offset of the stages (after mbarriers and level table)
     int vec_off;         // byte offset of the box vector when it is in shared memory
@@ -148,6 +165,7 @@ struct ResidualArgs {
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
                           int* flags, cudaStream_t s);
 template <typename T>
@@ -196,7 +214,8 @@ cudaError_t launch_norm2_double(const double* x, long long n, double* partial, c
 // ras.cu
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
-                              const T* J, T* coef, int threads, int* flags, cudaStream_t s);
+                              const T* J, T* coef, int threads, int ring_cells, size_t smem_bytes,
+                              int* flags, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,

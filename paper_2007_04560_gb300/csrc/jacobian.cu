@@ -24,40 +24,42 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
     const int x = c % g.nx, y = c / g.nx;
-    const double hg = 0.5 * k.gamma;
-    const double dvshift = 0.5 * (k.alpha - k.beta);
-    double Juu[NSLOT], Juv[NSLOT];
+    // arithmetic in the Jacobian's precision T
+    const T hg = (T)(0.5 * k.gamma);
+    const T dvshift = (T)(0.5 * (k.alpha - k.beta));
+    const T half = (T)0.5;
+    T Juu[NSLOT], Juv[NSLOT];
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) { Juu[s] = 0.0; Juv[s] = 0.0; }
-    const double cc = C.c[c], cuc = C.cu[c], cvc = C.cv[c], gc = C.Gu[c], gvc = C.Gv[c];
-    const double duc = C.du[c], xcc = C.xc[c];
-    double lapc = 0.0;   // sum of open faces / h^2 at c
-    double eih2c[4];
+    for (int s = 0; s < NSLOT; ++s) { Juu[s] = (T)0; Juv[s] = (T)0; }
+    const T cc = C.c[c], cuc = C.cu[c], cvc = C.cv[c], gc = C.Gu[c], gvc = C.Gv[c];
+    const T duc = C.du[c], xcc = C.xc[c];
+    T lapc = (T)0;   // sum of open faces / h^2 at c
+    T eih2c[4];
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
-        eih2c[f] = face_open(g, x, y, f) * (f < 2 ? g.ihx2 : g.ihy2);
+        eih2c[f] = face_w<T>(g, x, y, f);
         lapc += eih2c[f];
     }
-    Juu[0] = 1.0 / dt;
+    Juu[0] = (T)(1.0 / dt);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int fx = face_dx(f), fy = face_dy(f);
         const int sf = slot_of(fx, fy);
         const int n = nb_index(g, x, y, fx, fy);
-        const double w = eih2c[f];
-        const double cn = C.c[n], dG = C.Gu[n] - gc, ct = 0.5 * (cc + cn);
+        const T w = eih2c[f];
+        const T cn = C.c[n], dG = C.Gu[n] - gc, ct = half * (cc + cn);
         // mobility variation of the face flux
-        Juu[0] -= w * 0.5 * cuc * dG;
-        Juv[0] -= w * 0.5 * cvc * dG;
-        Juu[sf] -= w * 0.5 * (double)C.cu[n] * dG;
-        Juv[sf] -= w * 0.5 * (double)C.cv[n] * dG;
+        Juu[0] -= w * half * cuc * dG;
+        Juv[0] -= w * half * cvc * dG;
+        Juu[sf] -= w * half * C.cu[n] * dG;
+        Juv[sf] -= w * half * C.cv[n] * dG;
         // - ct * dG_u(n)/dX : pointwise part and Laplacian of the neighbour
-        Juu[sf] -= w * ct * (double)C.du[n];
-        Juv[sf] -= w * ct * (double)C.xc[n];
+        Juu[sf] -= w * ct * C.du[n];
+        Juv[sf] -= w * ct * C.xc[n];
         const int nx_ = x + fx, ny_ = y + fy;
 #pragma unroll
         for (int f2 = 0; f2 < 4; ++f2) {
-            const double e2 = face_open(g, nx_, ny_, f2) * (f2 < 2 ? g.ihx2 : g.ihy2);
+            const T e2 = face_w<T>(g, nx_, ny_, f2);
             const int s2 = slot_of(fx + face_dx(f2), fy + face_dy(f2));
             Juu[s2] += w * ct * hg * e2;
             Juu[sf] -= w * ct * hg * e2;
@@ -72,13 +74,13 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
         }
         Juu[0] += w * ct * hg * lapc;
     }
-    const double irho = 1.0 / k.rho;
+    const T irho = (T)(1.0 / k.rho);
 #pragma unroll
     for (int s = 0; s < NSLOT; ++s) {
-        double jvu = 0.0, jvv = 0.0;
+        T jvu = (T)0, jvv = (T)0;
         if (s == 0) {
             jvu = (cuc * gvc + cc * xcc) * irho;
-            jvv = 1.0 / dt + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
+            jvv = (T)(1.0 / dt) + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
         } else if (s <= 4) {
             const int f = s - 1;   // slots 1..4 are faces -x, +x, -y, +y
             jvv = -cc * hg * eih2c[f] * irho;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, c
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
-        const T ih2 = (T)(f < 2 ? g.ihx2 : g.ihy2);
+        const T ih2 = f < 2 ? (T)g.ihx2 : (T)g.ihy2;
         lu += (w[n] - wu) * ih2;
         lv += (w[N + n] - wv) * ih2;
     }
@@ -164,7 +166,7 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Ca
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         const int n = nb_index(g, x, yy, face_dx(f), face_dy(f));
-        const T w_ = (T)(face_open(g, x, yy, f) * (f < 2 ? g.ihx2 : g.ihy2));
+        const T w_ = face_w<T>(g, x, yy, f);
         div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
     }
     const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho);

@@ -41,92 +41,111 @@ __device__ __forceinline__ int box_cell(const Geom& g, const SubInfo& sd, int i,
 // record CREC values.  A record per cell keeps one thread's coefficients contiguous
 // (wide shared loads, no per-coefficient address arithmetic); CREC = 28 makes the
 // records of neighbouring threads fall into distinct shared-memory banks.
-__device__ __forceinline__ long long fwd_addr(const SubInfo& sd, const int* lo, int i, int j) {
-    const int l = i + 2 * j;
-    const int t = j - level_jmin(l, sd.W);
-    return sd.coef_base + (long long)lo[l] * NCOEF + (long long)t * CREC;
-}
-__device__ __forceinline__ long long bwd_addr(const SubInfo& sd, const int* lo, int i, int j) {
-    const int l = i + 2 * j;
-    const int cnt = lo[l + 1] - lo[l];
-    const int t = j - level_jmin(l, sd.W);
-    return sd.coef_base + (long long)lo[l] * NCOEF + (long long)(cnt + t) * CREC;
-}
-
-template <typename T>
-__device__ __forceinline__ void mul22(const T* a, const T* b, T* c) {
-    c[0] = a[0] * b[0] + a[1] * b[2];
-    c[1] = a[0] * b[1] + a[1] * b[3];
-    c[2] = a[2] * b[0] + a[3] * b[2];
-    c[3] = a[2] * b[1] + a[3] * b[3];
-}
-
 // ---------------------------------------------------------------- factorization
+// Block ILU(0) row by row in wavefront order.  Row c: for every lower neighbour k in
+// increasing natural order, L_ck = A_ck D_k^-1 and A_cj -= L_ck U_kj for every upper
+// block U_kj of row k whose column j is in the pattern of row c; then D_c = A_cc.
+// Both steps act on one block row at a time, so two threads share a cell, thread rr
+// owning row rr of every 2x2 block; D_c^-1 needs both rows (one shuffle).
+//
+// The records of the last RING levels (every lower neighbour lies 1..4 levels back)
+// are kept in shared memory for the neighbour lookups; the Jacobian rows of the next
+// level are loaded into registers while the current level is computed.
+constexpr int FACTOR_RING = 5;
+
 template <typename T>
-__global__ void ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs, const int* __restrict__ lev_off,
-                                  const T* __restrict__ J, T* coef, int* flags) {
+__device__ __forceinline__ void fetch_rows(const Geom& g, const SubInfo& sd, const int* lo, const T* __restrict__ J,
+                                           int l, int m, int rr, T (&dst)[NSLOT][2]) {
+    const int cnt = lo[l + 1] - lo[l];
+    if (m >= cnt) return;
+    const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+    const int gc = box_cell(g, sd, i, j);
+    const size_t N = (size_t)g.N;
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s) {
+        const int ii = i + slot_dx(s), jj = j + slot_dy(s);
+        const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H;
+        dst[s][0] = in ? J[(size_t)(s * 4 + 2 * rr) * N + gc] : (T)0;
+        dst[s][1] = in ? J[(size_t)(s * 4 + 2 * rr + 1) * N + gc] : (T)0;
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                         const int* __restrict__ lev_off, const T* __restrict__ J,
+                                                         T* __restrict__ coef, int ring_cells, int* flags) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubInfo sd = subs[blockIdx.x];
-    const int* lo = lev_off + sd.lev_base;
-    const int N = g.N;
+    int* lo = reinterpret_cast<int*>(smem_raw);
+    const int lev_words = (sd.nlev + 1 + 3) & ~3;
+    T* ring = reinterpret_cast<T*>(smem_raw + sizeof(int) * ((lev_words + 3) & ~3));
+    for (int l = threadIdx.x; l <= sd.nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
+    __syncthreads();
+    const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
     int bad = 0;
+    T Jn[NSLOT][2];
+    fetch_rows<T>(g, sd, lo, J, 0, m, rr, Jn);
     for (int l = 0; l < sd.nlev; ++l) {
+        T A[NSLOT][2];
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) { A[s][0] = Jn[s][0]; A[s][1] = Jn[s][1]; }
+        if (l + 1 < sd.nlev) fetch_rows<T>(g, sd, lo, J, l + 1, m, rr, Jn);
         const int cnt = lo[l + 1] - lo[l];
-        const int jmin = level_jmin(l, sd.W);
-        for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-            const int j = jmin + t, i = l - 2 * j;
-            const int gc = box_cell(g, sd, i, j);
-            T A[NSLOT][4];
-#pragma unroll
-            for (int s = 0; s < NSLOT; ++s) {
-                const int ii = i + slot_dx(s), jj = j + slot_dy(s);
-                const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H;
-#pragma unroll
-                for (int e = 0; e < 4; ++e) A[s][e] = in ? J[(size_t)(s * 4 + e) * N + gc] : (T)0;
-            }
-            T* fw = coef + fwd_addr(sd, lo, i, j);
-            T* bw = coef + bwd_addr(sd, lo, i, j);
+        const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+        const bool act = m < cnt;
+        T* fw = coef + sd.coef_base + (long long)lo[l] * NCOEF + (long long)m * CREC;
+        T* bw = fw + (long long)cnt * CREC;
+        T* rb = ring + ((size_t)(l % FACTOR_RING) * ring_cells + m) * CREC;
+        if (act) {
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 const int dx1 = lower_dx(a), dy1 = lower_dy(a);
                 const int ki = i + dx1, kj = j + dy1;
-                T L[4] = {0, 0, 0, 0};
+                T L0 = (T)0, L1 = (T)0;
                 if (ki >= 0 && ki < sd.W && kj >= 0 && kj < sd.H) {
-                    const T* kb = coef + bwd_addr(sd, lo, ki, kj);
-                    T Dk[4];
-#pragma unroll
-                    for (int e = 0; e < 4; ++e) Dk[e] = kb[e];
-                    mul22(A[slot_of(dx1, dy1)], Dk, L);
+                    const int lk = l + dx1 + 2 * dy1;
+                    const T* kr = ring + ((size_t)(lk % FACTOR_RING) * ring_cells + (kj - level_jmin(lk, sd.W))) * CREC;
+                    const T* As = A[slot_of(dx1, dy1)];
+                    L0 = As[0] * kr[0] + As[1] * kr[2];
+                    L1 = As[0] * kr[1] + As[1] * kr[3];
 #pragma unroll
                     for (int b = 0; b < 6; ++b) {
                         const int s2 = slot_of(dx1 + upper_dx(b), dy1 + upper_dy(b));
                         if (s2 >= 0) {
-                            T U[4], P[4];
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) U[e] = kb[4 + 4 * b + e];
-                            mul22(L, U, P);
-#pragma unroll
-                            for (int e = 0; e < 4; ++e) A[s2][e] -= P[e];
+                            const T* U = kr + 4 + 4 * b;
+                            A[s2][0] -= L0 * U[0] + L1 * U[2];
+                            A[s2][1] -= L0 * U[1] + L1 * U[3];
                         }
                     }
                 }
-#pragma unroll
-                for (int e = 0; e < 4; ++e) fw[4 * a + e] = L[e];
+                fw[4 * a + 2 * rr] = L0;
+                fw[4 * a + 2 * rr + 1] = L1;
             }
-#pragma unroll
-            for (int e = 24; e < CREC; ++e) fw[e] = (T)0;
-            const T* D = A[0];
-            const T det = D[0] * D[3] - D[1] * D[2];
+            fw[24 + 2 * rr] = (T)0;
+            fw[25 + 2 * rr] = (T)0;
+        }
+        // pivot block D = A[0]: row rr here, the other row in the partner lane
+        const T o0 = __shfl_xor_sync(0xffffffffu, A[0][0], 1);
+        const T o1 = __shfl_xor_sync(0xffffffffu, A[0][1], 1);
+        if (act) {
+            const T d00 = rr ? o0 : A[0][0], d01 = rr ? o1 : A[0][1];
+            const T d10 = rr ? A[0][0] : o0, d11 = rr ? A[0][1] : o1;
+            const T det = d00 * d11 - d01 * d10;
             if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
             const T id = (T)1 / det;
-            bw[0] = D[3] * id;
-            bw[1] = -D[1] * id;
-            bw[2] = -D[2] * id;
-            bw[3] = D[0] * id;
+            const T i0 = rr ? -d10 * id : d11 * id;    // row rr of D^-1
+            const T i1 = rr ? d00 * id : -d01 * id;
+            bw[2 * rr] = i0;
+            bw[2 * rr + 1] = i1;
+            rb[2 * rr] = i0;
+            rb[2 * rr + 1] = i1;
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
                 const int s = slot_of(upper_dx(b), upper_dy(b));
-#pragma unroll
-                for (int e = 0; e < 4; ++e) bw[4 + 4 * b + e] = A[s][e];
+                bw[4 + 4 * b + 2 * rr] = A[s][0];
+                bw[4 + 4 * b + 2 * rr + 1] = A[s][1];
+                rb[4 + 4 * b + 2 * rr] = A[s][0];
+                rb[4 + 4 * b + 2 * rr + 1] = A[s][1];
             }
         }
         __syncthreads();
@@ -136,8 +155,17 @@ __global__ void ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs, cons
 
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
-                              const T* J, T* coef, int threads, int* flags, cudaStream_t s) {
-    ras_factor_kernel<T><<<nsub, threads, 0, s>>>(g, subs, lev_off, J, coef, flags);
+                              const T* J, T* coef, int threads, int ring_cells, size_t smem_bytes, int* flags,
+                              cudaStream_t s) {
+    static size_t attr_bytes[2] = {0, 0};
+    const int which = sizeof(T) == 8 ? 0 : 1;
+    if (smem_bytes > 48 * 1024 && smem_bytes > attr_bytes[which]) {
+        cudaError_t e = cudaFuncSetAttribute(ras_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_bytes[which] = smem_bytes;
+    }
+    ras_factor_kernel<T><<<nsub, threads, smem_bytes, s>>>(g, subs, lev_off, J, coef, ring_cells, flags);
     return cudaGetLastError();
 }
 
@@ -198,9 +226,10 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Producer / consumer pipeline.  The last warp is the producer: its lane 0 streams
 // level stages into the ring (full[b] completes when a stage has landed) and reuses
 // buffer b only after the consumers released it (empty[b]).  The other warps are
-// the consumers: two threads per cell, thread (m, rr) solving row rr of the m-th
-// cell of the level, synchronised level by level by a named barrier.
-template <typename T>
+// the consumers, TPC (2 or 4) threads per cell: thread (m, hh, rr) sums, for row rr
+// of the m-th cell of the level, the neighbour blocks of half hh (all six when
+// TPC = 2); the halves meet by a shuffle.  Levels are separated by a named barrier.
+template <typename T, int TPC>
 __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                         const int* __restrict__ lev_off,
                                                         const T* __restrict__ coef, const T* __restrict__ r,
@@ -299,13 +328,16 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             }
         }
     } else {
-        const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
-        // neighbour offsets in the padded box (cells)
-        int offL[6], offU[6];
+        const int m = threadIdx.x / TPC, rr = threadIdx.x & 1, hh = TPC == 4 ? (threadIdx.x >> 1) & 1 : 0;
+        constexpr int QN = TPC == 4 ? 3 : 6;    // neighbour blocks per thread
+        const int q0 = hh * 3;
+        // this thread's neighbour blocks q0 .. q0+QN-1: offsets in the padded box
+        int offF[QN], offB[QN];
 #pragma unroll
-        for (int q = 0; q < 6; ++q) {
-            offL[q] = lower_dy(q) * PW + lower_dx(q);
-            offU[q] = upper_dy(q) * PW + upper_dx(q);
+        for (int qq = 0; qq < QN; ++qq) {
+            const int q = q0 + qq;
+            offF[qq] = lower_dy(q) * PW + lower_dx(q);
+            offB[qq] = upper_dy(q) * PW + upper_dx(q);
         }
         int k = 0;
         for (; k < nst; ++k) {
@@ -318,37 +350,27 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             const int pc = (j + 2) * PW + i + 2;
             const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
             const bool act = m < cnt && landed;
+            // row rr, blocks q0 .. q0+QN-1: a0 (+ a1) = partial of sum_o C_c,o y_{c+o}
+            const T* cq = rec + (fwd ? 0 : 4) + 4 * q0 + 2 * rr;
+            T a0 = (T)0, a1 = (T)0;
+            if (act) {
+#pragma unroll
+                for (int qq = 0; qq < QN; ++qq) {
+                    const V2<T> nb = yv[pc + (fwd ? offF[qq] : offB[qq])];
+                    T& acc = (qq < QN / 2) ? a0 : a1;
+                    acc = fma(cq[4 * qq], nb.x, acc);
+                    acc = fma(cq[4 * qq + 1], nb.y, acc);
+                }
+            }
+            T part = a0 + a1;
+            if (TPC == 4) part += __shfl_xor_sync(0xffffffffu, part, 2);
+            const T s_me = (act ? ys[2 * pc + rr] : (T)0) - part;     // row rr of y_c - sum
             if (fwd) {
-                if (act) {
-                    // row rr: y_c -= sum_lower L_c,o y_{c+o}  (two independent chains)
-                    T a0 = ys[2 * pc + rr], a1 = (T)0;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = yv[pc + offL[q]];
-                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
-                        T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
-                    }
-                    ys[2 * pc + rr] = a0 + a1;
-                }
+                if (act && hh == 0) ys[2 * pc + rr] = s_me;
             } else {
-                // row rr of s = y_c - sum_upper U_c,o y_{c+o}; then y_c = D^-1 s
-                T a0 = (T)0, a1 = (T)0;
-                if (act) {
-                    a0 = ys[2 * pc + rr];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = yv[pc + offU[q]];
-                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
-                        T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
-                    }
-                }
-                const T s_me = a0 + a1;
+                // y_c = D^-1 s, the other row from the partner thread
                 const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
-                if (act) {
+                if (act && hh == 0) {
                     const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
                     ys[2 * pc + rr] = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
                 }
@@ -396,26 +418,26 @@ template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
-    static size_t attr_bytes[2] = {0, 0};
+    static size_t attr_bytes[2][2] = {{0, 0}, {0, 0}};
     const int which = sizeof(T) == 8 ? 0 : 1;
-    if (L.smem_bytes > attr_bytes[which]) {
-        cudaError_t e = cudaFuncSetAttribute(ras_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L.smem_bytes);
+    const int t4 = L.tpc == 4 ? 1 : 0;
+    auto kern = t4 ? ras_apply_kernel<T, 4> : ras_apply_kernel<T, 2>;
+    if (L.smem_bytes > attr_bytes[which][t4]) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes[which] = L.smem_bytes;
+        attr_bytes[which][t4] = L.smem_bytes;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
         if (e != cudaSuccess) return e;
     }
-    ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
-                                                            err);
+    kern<<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L, err);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                    \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
-                                              T*, int, int*, cudaStream_t);                         \
+                                              T*, int, int, size_t, int*, cudaStream_t);            \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, int*,       \
                                              cudaStream_t);

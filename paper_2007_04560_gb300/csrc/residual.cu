@@ -13,20 +13,82 @@ namespace acac {
 
 __constant__ double c_taylor[MAX_S];   // 1 / ((2k)(2k+1)),  k = 1..S   (Lemma 2.2)
 __constant__ double c_rcoef[MAX_S];    // 1 / (2k+1),        k = 1..S   (its sigma/zeta derivative)
+__constant__ float c_rcoef_f[MAX_S];   // the same in float, for the FP32 Jacobian of the mixed form
+
+// Table of the logarithm below: for F_j = 1 + j/128, j = 0..128, 1/F_j and ln F_j as an
+// unevaluated sum hi + lo.
+constexpr int LOG_TABLE = 129;
+__constant__ double c_log_invF[LOG_TABLE];
+__constant__ double c_log_hi[LOG_TABLE];
+__constant__ double c_log_lo[LOG_TABLE];
 
 static int g_taylor_S = -1;
+static bool g_log_ready = false;
 
 cudaError_t set_taylor_constants(int S) {
+    cudaError_t e = cudaSuccess;
+    if (!g_log_ready) {
+        double inv[LOG_TABLE], hi[LOG_TABLE], lo[LOG_TABLE];
+        for (int j = 0; j < LOG_TABLE; ++j) {
+            const long double F = 1.0L + (long double)j / 128.0L;
+            const long double L = logl(F);
+            inv[j] = (double)(1.0L / F);
+            hi[j] = (double)L;
+            lo[j] = (double)(L - (long double)hi[j]);
+        }
+        e = cudaMemcpyToSymbol(c_log_invF, inv, sizeof(inv));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_hi, hi, sizeof(hi));
+        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_lo, lo, sizeof(lo));
+        if (e != cudaSuccess) return e;
+        g_log_ready = true;
+    }
     if (S == g_taylor_S) return cudaSuccess;
     double a[MAX_S], b[MAX_S];
     for (int k = 1; k <= MAX_S; ++k) {
         a[k - 1] = 1.0 / ((2.0 * k) * (2.0 * k + 1.0));
         b[k - 1] = 1.0 / (2.0 * k + 1.0);
     }
-    cudaError_t e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
+    float bf[MAX_S];
+    for (int k = 0; k < MAX_S; ++k) bf[k] = (float)b[k];
+    e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef, b, sizeof(b));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef_f, bf, sizeof(bf));
     if (e == cudaSuccess) g_taylor_S = S;
     return e;
+}
+
+// Natural logarithm in double by the table-driven reduction of P. T. P. Tang, "Table-
+// driven implementation of the logarithm function in IEEE floating-point arithmetic"
+// (ACM TOMS 16, 1990), written from the mathematics: x = 2^e m, m in [1, 2); F = 1 + j/128
+// is the table point nearest to m, so f = m - F is exact and |f| <= 2^-8; with
+// u = f / F (one multiplication by the tabulated 1/F),
+//     ln x = e ln 2 + ln F + ln(1 + u),
+//     ln(1 + u) = u - u^2/2 + u^3/3 - ... (terms to u^7; the next is below 2^-67 |u|).
+// ln 2 is split into a 42-bit head (so that e * head is exact) and a tail.  Arguments
+// that are not positive normal numbers go to the library logarithm.  The GPU tests
+// compare it with the library logarithm over the arguments the kernels use.
+__device__ __forceinline__ double table_log(double x) {
+    if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) return log(x);
+    const long long bits = __double_as_longlong(x);
+    const int e = (int)((bits >> 52) & 0x7ff) - 1023;
+    const long long mb = (bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL;
+    const double m = __longlong_as_double(mb);
+    const int j = (int)((mb >> 45) & 0x7f) + (int)((mb >> 44) & 1);      // nearest j/128
+    const double F = 1.0 + (double)j * 0.0078125;
+    const double u = (m - F) * c_log_invF[j];
+    const double u2 = u * u;
+    // -1/2 + u (1/3 + u (-1/4 + u (1/5 + u (-1/6 + u / 7))))
+    double q = fma(u, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(u, q, 0.2);
+    q = fma(u, q, -0.25);
+    q = fma(u, q, 1.0 / 3.0);
+    q = fma(u, q, -0.5);
+    const double ln2_hi = 6.93147180559890330187045037746429443359375e-1;   // 42 significant bits
+    const double ln2_lo = 5.497923018708371174712471233040e-14;
+    const double ed = (double)e;
+    const double hi = fma(ed, ln2_hi, c_log_hi[j]);
+    const double lo = fma(ed, ln2_lo, c_log_lo[j]);
+    return hi + (u + fma(u2, q, lo));
 }
 
 // sum_{k=1..S} r^k / ((2k)(2k+1)), Horner form.
@@ -35,10 +97,19 @@ __device__ __forceinline__ double series_P(double r, int S) {
     for (int k = S - 2; k >= 0; --k) acc = fma(acc, r, c_taylor[k]);
     return acc * r;
 }
-// sum_{k=1..S} r^(k-1) / (2k+1), Horner form.
-__device__ __forceinline__ double series_R(double r, int S) {
+// sum_{k=1..S} r^(k-1) / (2k+1), Horner form (in the precision T of the Jacobian).
+template <typename T>
+__device__ __forceinline__ T series_R(T r, int S);
+template <>
+__device__ __forceinline__ double series_R<double>(double r, int S) {
     double acc = c_rcoef[S - 1];
     for (int k = S - 2; k >= 0; --k) acc = fma(acc, r, c_rcoef[k]);
+    return acc;
+}
+template <>
+__device__ __forceinline__ float series_R<float>(float r, int S) {
+    float acc = c_rcoef_f[S - 1];
+    for (int k = S - 2; k >= 0; --k) acc = fmaf(acc, r, c_rcoef_f[k]);
     return acc;
 }
 
@@ -50,17 +121,19 @@ __device__ __forceinline__ double phi_series(double zeta, double sigma, int S) {
     const double inv = 1.0 / (zeta * om);
     const double a = sigma * om * inv;      // sigma / zeta
     const double b = sigma * zeta * inv;    // sigma / (1 - zeta)
-    return log(zeta * zeta * inv) - (series_P(a * a, S) - series_P(b * b, S));
+    return table_log(zeta * zeta * inv) - (series_P(a * a, S) - series_P(b * b, S));
 }
 
 // d phi^S / d(end value) where zeta and sigma both move by 1/2:
-//   1/2 [ (1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta) ].
-__device__ __forceinline__ double dphi_series(double zeta, double sigma, int S) {
-    const double om = 1.0 - zeta;
-    const double iz = 1.0 / zeta, io = 1.0 / om;
-    const double a = sigma * iz, b = sigma * io;
-    const double Ra = series_R(a * a, S), Rb = series_R(b * b, S);
-    return 0.5 * ((1.0 + a * a * Ra - a * Ra) * iz + (1.0 + b * b * Rb + b * Rb) * io);
+//   1/2 [ (1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta) ],
+// evaluated in the Jacobian's precision T (zeta, 1 - zeta and sigma formed in double).
+template <typename T>
+__device__ __forceinline__ T dphi_series(double zeta_d, double sigma_d, int S) {
+    const T zeta = (T)zeta_d, om = (T)(1.0 - zeta_d), sigma = (T)sigma_d;
+    const T iz = (T)1 / zeta, io = (T)1 / om;
+    const T a = sigma * iz, b = sigma * io;
+    const T Ra = series_R<T>(a * a, S), Rb = series_R<T>(b * b, S);
+    return (T)0.5 * (((T)1 + a * a * Ra - a * Ra) * iz + ((T)1 + b * b * Rb + b * Rb) * io);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -180,7 +253,7 @@ cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& 
 }
 
 // ---------------------------------------------------------------- energy / mass
-__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * log(z) : 0.0; }
+__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_log(z) : 0.0; }
 
 // E~ = sum [e1 + e2 + gamma/2 sum_d ((D+ phi)^2 + (D- phi)^2)/2] dx dy (Eqs. relations,
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
@@ -229,26 +302,29 @@ cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double*
 // Per-cell derivative data of F at the accepted iterate X (G = [Gu | Gv | c] from
 // pass A at the same X):  cu = dc/du1, cv = dc/dv1 (c at the midpoint, so each picks
 // up a factor 1/2), du = -alpha/2 + theta (dphi/dp1 + dpsi/dq1), xc = theta (dphi/dp1 - dpsi/dq1).
+// The midpoint sums are formed in double; the derivative arithmetic runs in the
+// Jacobian's precision T (double, or float in the mixed form).
 template <typename T>
 __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const double* __restrict__ X,
                                                         const double* __restrict__ X0,
                                                         const double* __restrict__ G, Cache<T> C) {
     const int N = g.N;
+    const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
-        const double ub = 0.5 * (u1 + u0), vb = 0.5 * (v1 + v0);
-        const double w = 0.25 - vb * vb;
         const double zp = 0.5 * ((u1 + v1) + (u0 + v0)), sp = 0.5 * ((u1 + v1) - (u0 + v0));
         const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
-        const double A = k.theta * dphi_series(zp, sp, k.S);
-        const double B = k.theta * dphi_series(zq, sq, k.S);
+        const T ub = (T)(0.5 * (u1 + u0)), vb = (T)(0.5 * (v1 + v0));
+        const T w = (T)0.25 - vb * vb;
+        const T A = theta * dphi_series<T>(zp, sp, k.S);
+        const T B = theta * dphi_series<T>(zq, sq, k.S);
         C.c[c] = (T)G[2 * N + c];
-        C.cu[c] = (T)(0.5 * (1.0 - 2.0 * ub) * w);
-        C.cv[c] = (T)(-ub * (1.0 - ub) * vb);
+        C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ub) * w;
+        C.cv[c] = -ub * ((T)1 - ub) * vb;
         C.Gu[c] = (T)G[c];
         C.Gv[c] = (T)G[N + c];
-        C.du[c] = (T)(-0.5 * k.alpha + A + B);
-        C.xc[c] = (T)(A - B);
+        C.du[c] = -halpha + A + B;
+        C.xc[c] = A - B;
     }
 }
 
@@ -260,6 +336,18 @@ cudaError_t launch_linearize(const Geom& g, const Coef& k, const double* X, cons
     linearize_kernel<T><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, X, X0, G, cache);
     return cudaGetLastError();
 }
+__global__ void table_log_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = table_log(x[i]);
+}
+
+cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s) {
+    cudaError_t e = set_taylor_constants(1);
+    if (e != cudaSuccess) return e;
+    table_log_kernel<<<RED_BLOCKS, 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_linearize<double>(const Geom&, const Coef&, const double*, const double*,
                                               const double*, Cache<double>, cudaStream_t);
 template cudaError_t launch_linearize<float>(const Geom&, const Coef&, const double*, const double*,

@@ -192,8 +192,12 @@ void precond(acac_handle* h, const T* r, T* z) {
 template <typename T>
 int factor(acac_handle* h) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-    KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox, launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J,
-                            (T*)h->coef, h->ras_threads, h->flags, h->stream));
+    const int ring_cells = h->ras_maxcnt;
+    const size_t smem = sizeof(int) * (size_t)(((h->ras_maxlev + 1 + 3) & ~3) + 3 & ~3) +
+                        sizeof(T) * 5 * (size_t)ring_cells * CREC;
+    KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox,
+        launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J, (T*)h->coef,
+                             h->ras_threads, ring_cells, smem, h->flags, h->stream));
     h->n_factor++;
     return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
 }
@@ -421,7 +425,7 @@ int build_subdomains(acac_handle* h) {
             sd.W = hix - lox; sd.H = hiy - loy;
             sd.own_x0 = sx[kx] - lox; sd.own_x1 = ex[kx] - lox;
             sd.own_y0 = sy[ky] - loy; sd.own_y1 = ey[ky] - loy;
-            if (sd.W > 500 || sd.H > 500) return ACAC_E_ARG;
+            if (sd.W > 250 || sd.H > 250) return ACAC_E_ARG;   // 2 threads per cell of a level
             sd.nlev = (sd.W - 1) + 2 * (sd.H - 1) + 1;
             sd.lev_base = (int)h->lev.size();
             sd.coef_base = coef;
@@ -452,7 +456,7 @@ int build_subdomains(acac_handle* h) {
     h->ras_maxcnt = maxcnt;
     h->ras_maxpad = maxpad;
     h->nbox = (double)(coef / NCOEF);
-    h->ras_threads = std::max(64, ((maxcnt + 31) / 32) * 32);
+    h->ras_threads = std::max(64, ((2 * maxcnt + 31) / 32) * 32);
     if (h->ras_threads > 1024) h->ras_threads = 1024;
     h->ras_smem = maxpad * 2 * h->ksz;
     return ACAC_OK;
@@ -564,6 +568,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)h->N; g.bc = p->bc;
     g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
     g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
+    g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
     g.vol = g.hx * g.hy;
     h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
     h->eta = p->eta0;
@@ -596,7 +601,8 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             RasLaunch& L = h->ras_launch;
             L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
             L.stage_elems = (CREC * h->ras_maxcnt + 31) / 32 * 32;
-            L.threads = 32 * ((2 * h->ras_maxcnt + 31) / 32) + 32;
+            L.tpc = 2;   // measured: 2 threads per cell beats 4 in both precisions
+            L.threads = 32 * ((L.tpc * h->ras_maxcnt + 31) / 32) + 32;
             const size_t vec_bytes = r128(h->ras_maxpad * 2 * ks);
             const size_t stage_bytes = (size_t)L.stage_elems * ks;
             const size_t cap = (size_t)optin - 2048;
@@ -653,6 +659,12 @@ void acac_destroy(acac_handle* h) {
     for (auto e : h->pool) cudaEventDestroy(e);
     free_all(h);
     delete h;
+}
+
+int acac_log(const double* x, double* y, long long n, void* cuda_stream) {
+    if (!x || !y || n < 0) return ACAC_E_ARG;
+    if (launch_table_log(x, y, n, (cudaStream_t)cuda_stream) != cudaSuccess) return ACAC_E_CUDA;
+    return ACAC_OK;
 }
 
 int acac_profile(acac_handle* h, int enable) {

@@ -51,6 +51,28 @@ def test_residual(P, bc, grid):
     assert fn == pytest.approx(np.linalg.norm(Fo), rel=1e-12)
 
 
+def test_table_log_accuracy(P):
+    """The residual / energy logarithm against the library log: within 2 ulp over
+    (1e-300, 1e300), and within 2 ulp of ln 2 absolute on (1/2, 2)."""
+    import torch
+    from paper_2007_04560_gb300.acac import acac_log
+    rng = np.random.default_rng(0)
+    xs = np.concatenate([10.0 ** rng.uniform(-300, 300, 200000), rng.uniform(0.0, 1.0, 200000),
+                         1.0 + rng.uniform(-1e-3, 1e-3, 100000), rng.uniform(0.5, 2.0, 100000),
+                         np.array([1.0, 2.0, 0.5, 1e-308, 3.0, 1.0 - 2 ** -53, 1.0 + 2 ** -52])])
+    xs = xs[xs > 0]
+    x = torch.tensor(xs, dtype=torch.float64, device="cuda")
+    y = torch.empty_like(x)
+    acac_log(x, y)
+    ref = torch.log(x)
+    torch.cuda.synchronize()
+    err = (y - ref).abs()
+    ulp = torch.abs(torch.nextafter(ref, torch.full_like(ref, float("inf"))) - ref)
+    assert float((err / ulp).max()) <= 2.0
+    near1 = (x > 0.5) & (x < 2.0)
+    assert float(err[near1].max()) <= 2.3e-16
+
+
 def test_residual_domain_error(P):
     import torch
     p = Params(n=(16, 16, 1))
