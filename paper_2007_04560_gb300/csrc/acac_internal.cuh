@@ -137,8 +137,7 @@ __host__ __device__ constexpr int ras_pitch(int W) { return (W + 4) | 1; }
 // Shared-memory plan of the Schwarz apply kernel (bytes / elements).
 struct RasLaunch {
     int nbuf;            // coefficient stages in flight
-    int tpc;             // consumer threads per cell (2 or 4)
-    int threads;         // consumer warps (tpc threads per cell of the widest level) + 1 producer warp
+    int threads;         // consumer warps (2 threads per cell of the widest level) + 1 producer warp
     int stage_elems;     // elements per stage (>= 28 x the largest level)
     int stage_off;       // byte offset of the stages (after mbarriers and level table)
     int vec_off;         // byte offset of the box vector when it is in shared memory
@@ -152,12 +151,12 @@ int validate_params(const acac_params* p);
 // residual.cu
 cudaError_t set_taylor_constants(int S);
 struct ResidualArgs {
-    const double* X;     // iterate (state vector)
-    const double* S;     // direction or nullptr
+    const double* X;     // state at which F is evaluated (the trial state in a line search)
+    const double* S;     // direction (trial_kernel only)
     double lam, shift;   // trial u = X_u + lam (S_u + shift), v = X_v + lam S_v
     const double* X0;
     double dt;
-    double* Xt;          // trial state written here when S != nullptr
+    double* Xt;          // trial state written by trial_kernel
     double* G;           // [Gu | Gv | c], 3N
     double* F;           // residual
     double* partial;     // RED_BLOCKS partial sums of F^2
@@ -165,6 +164,7 @@ struct ResidualArgs {
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
                           int* flags, cudaStream_t s);

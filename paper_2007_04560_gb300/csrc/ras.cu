@@ -226,10 +226,9 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // Producer / consumer pipeline.  The last warp is the producer: its lane 0 streams
 // level stages into the ring (full[b] completes when a stage has landed) and reuses
 // buffer b only after the consumers released it (empty[b]).  The other warps are
-// the consumers, TPC (2 or 4) threads per cell: thread (m, hh, rr) sums, for row rr
-// of the m-th cell of the level, the neighbour blocks of half hh (all six when
-// TPC = 2); the halves meet by a shuffle.  Levels are separated by a named barrier.
-template <typename T, int TPC>
+// the consumers: two threads per cell, thread (m, rr) solving row rr of the m-th
+// cell of the level, synchronised level by level by a named barrier.
+template <typename T>
 __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                         const int* __restrict__ lev_off,
                                                         const T* __restrict__ coef, const T* __restrict__ r,
@@ -328,16 +327,13 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             }
         }
     } else {
-        const int m = threadIdx.x / TPC, rr = threadIdx.x & 1, hh = TPC == 4 ? (threadIdx.x >> 1) & 1 : 0;
-        constexpr int QN = TPC == 4 ? 3 : 6;    // neighbour blocks per thread
-        const int q0 = hh * 3;
-        // this thread's neighbour blocks q0 .. q0+QN-1: offsets in the padded box
-        int offF[QN], offB[QN];
+        const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+        // neighbour offsets in the padded box (cells)
+        int offL[6], offU[6];
 #pragma unroll
-        for (int qq = 0; qq < QN; ++qq) {
-            const int q = q0 + qq;
-            offF[qq] = lower_dy(q) * PW + lower_dx(q);
-            offB[qq] = upper_dy(q) * PW + upper_dx(q);
+        for (int q = 0; q < 6; ++q) {
+            offL[q] = lower_dy(q) * PW + lower_dx(q);
+            offU[q] = upper_dy(q) * PW + upper_dx(q);
         }
         int k = 0;
         for (; k < nst; ++k) {
@@ -350,27 +346,37 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             const int pc = (j + 2) * PW + i + 2;
             const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
             const bool act = m < cnt && landed;
-            // row rr, blocks q0 .. q0+QN-1: a0 (+ a1) = partial of sum_o C_c,o y_{c+o}
-            const T* cq = rec + (fwd ? 0 : 4) + 4 * q0 + 2 * rr;
-            T a0 = (T)0, a1 = (T)0;
-            if (act) {
-#pragma unroll
-                for (int qq = 0; qq < QN; ++qq) {
-                    const V2<T> nb = yv[pc + (fwd ? offF[qq] : offB[qq])];
-                    T& acc = (qq < QN / 2) ? a0 : a1;
-                    acc = fma(cq[4 * qq], nb.x, acc);
-                    acc = fma(cq[4 * qq + 1], nb.y, acc);
-                }
-            }
-            T part = a0 + a1;
-            if (TPC == 4) part += __shfl_xor_sync(0xffffffffu, part, 2);
-            const T s_me = (act ? ys[2 * pc + rr] : (T)0) - part;     // row rr of y_c - sum
             if (fwd) {
-                if (act && hh == 0) ys[2 * pc + rr] = s_me;
+                if (act) {
+                    // row rr: y_c -= sum_lower L_c,o y_{c+o}  (two independent chains)
+                    T a0 = ys[2 * pc + rr], a1 = (T)0;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = yv[pc + offL[q]];
+                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                    ys[2 * pc + rr] = a0 + a1;
+                }
             } else {
-                // y_c = D^-1 s, the other row from the partner thread
+                // row rr of s = y_c - sum_upper U_c,o y_{c+o}; then y_c = D^-1 s
+                T a0 = (T)0, a1 = (T)0;
+                if (act) {
+                    a0 = ys[2 * pc + rr];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = yv[pc + offU[q]];
+                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                }
+                const T s_me = a0 + a1;
                 const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
-                if (act && hh == 0) {
+                if (act) {
                     const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
                     ys[2 * pc + rr] = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
                 }
@@ -418,20 +424,20 @@ template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
-    static size_t attr_bytes[2][2] = {{0, 0}, {0, 0}};
+    static size_t attr_bytes[2] = {0, 0};
     const int which = sizeof(T) == 8 ? 0 : 1;
-    const int t4 = L.tpc == 4 ? 1 : 0;
-    auto kern = t4 ? ras_apply_kernel<T, 4> : ras_apply_kernel<T, 2>;
-    if (L.smem_bytes > attr_bytes[which][t4]) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.smem_bytes);
+    if (L.smem_bytes > attr_bytes[which]) {
+        cudaError_t e = cudaFuncSetAttribute(ras_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)L.smem_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes[which][t4] = L.smem_bytes;
+        attr_bytes[which] = L.smem_bytes;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
         if (e != cudaSuccess) return e;
     }
-    kern<<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L, err);
+    ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
+                                                            err);
     return cudaGetLastError();
 }
 

@@ -91,11 +91,26 @@ __device__ __forceinline__ double table_log(double x) {
     return hi + (u + fma(u2, q, lo));
 }
 
-// sum_{k=1..S} r^k / ((2k)(2k+1)), Horner form.
-__device__ __forceinline__ double series_P(double r, int S) {
-    double acc = c_taylor[S - 1];
-    for (int k = S - 2; k >= 0; --k) acc = fma(acc, r, c_taylor[k]);
+// sum_{k=1..K} r^k / ((2k)(2k+1)), Horner form.
+__device__ __forceinline__ double series_P(double r, int K) {
+    double acc = c_taylor[K - 1];
+    for (int k = K - 2; k >= 0; --k) acc = fma(acc, r, c_taylor[k]);
     return acc * r;
+}
+
+// Number of series terms K <= S, uniform over the warp, such that the terms K+1..S
+// of every lane add up to less than 2^-60 of that lane's first term (the
+// coefficients decrease, and r^K <= 2^-60 bounds the tail by a geometric series):
+// the K-term sum then equals the S-term sum of Lemma 2.2 up to FP64 rounding.
+__device__ __forceinline__ int series_terms(double rmax_lane, int S) {
+    // non-negative floats order like their bit patterns
+    const unsigned bits = __float_as_uint((float)fmin(rmax_lane, 0.5));
+    const float r = __uint_as_float(__reduce_max_sync(0xffffffffu, bits));
+    if (r <= 0.0f) return 1;
+    if (r >= 0.25f) return S;
+    // smallest K with r^K * (1 + r + r^2 + ...) <= 2^-60, i.e. K >= (60 + log2(1/(1-r))) / log2(1/r)
+    const int K = (int)ceilf((60.0f + 0.5f) / -log2f(r));
+    return K < 1 ? 1 : (K > S ? S : K);
 }
 // sum_{k=1..S} r^(k-1) / (2k+1), Horner form (in the precision T of the Jacobian).
 template <typename T>
@@ -116,12 +131,20 @@ __device__ __forceinline__ float series_R<float>(float r, int S) {
 // phi^S(zeta, sigma): series form of [Phi(zeta+sigma) - Phi(zeta-sigma)] / (2 sigma)
 // (Lemma 2.2, Eq. D2-1, combination f_S(zeta,sigma) - f_S(1-zeta,sigma)):
 //   ln(zeta/(1-zeta)) - sum_k [(sigma/zeta)^{2k} - (sigma/(1-zeta))^{2k}] / ((2k)(2k+1)).
-__device__ __forceinline__ double phi_series(double zeta, double sigma, int S) {
+// The squares ra = (sigma/zeta)^2, rb = (sigma/(1-zeta))^2 and the log argument are
+// returned first so that the caller can pick the warp-uniform term count.
+struct SeriesArgs {
+    double ra, rb, ratio;
+};
+__device__ __forceinline__ SeriesArgs series_args(double zeta, double sigma) {
     const double om = 1.0 - zeta;
     const double inv = 1.0 / (zeta * om);
     const double a = sigma * om * inv;      // sigma / zeta
     const double b = sigma * zeta * inv;    // sigma / (1 - zeta)
-    return table_log(zeta * zeta * inv) - (series_P(a * a, S) - series_P(b * b, S));
+    return SeriesArgs{a * a, b * b, zeta * zeta * inv};
+}
+__device__ __forceinline__ double phi_series(const SeriesArgs& s, int K) {
+    return table_log(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
 }
 
 // d phi^S / d(end value) where zeta and sigma both move by 1/2:
@@ -153,54 +176,72 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 }
 
 // ---------------------------------------------------------------- pass A
+// x in (0, 1) on the IEEE bit pattern: positive doubles order like their bits, and
+// every negative number, NaN or value >= 1 falls outside (0, bits(1.0)).
+__device__ __forceinline__ bool in_unit(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x3ff0000000000000LL;
+}
+
 __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
     const int N = g.N;
     const double* __restrict__ Xu = a.X;
     const double* __restrict__ Xv = a.X + N;
-    const double* __restrict__ Su = a.S;
-    const double* __restrict__ Sv = a.S ? a.S + N : nullptr;
     const double* __restrict__ Pu = a.X0;
     const double* __restrict__ Pv = a.X0 + N;
     int flag = 0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int x = c % g.nx, y = c / g.nx;
-        int nbr[4];
-#pragma unroll
-        for (int f = 0; f < 4; ++f) nbr[f] = nb_index(g, x, y, face_dx(f), face_dy(f));
-        auto U1 = [&](int i) { return Su ? Xu[i] + a.lam * (Su[i] + a.shift) : Xu[i]; };
-        auto V1 = [&](int i) { return Sv ? Xv[i] + a.lam * Sv[i] : Xv[i]; };
-        const double u1 = U1(c), v1 = V1(c), u0 = Pu[c], v0 = Pv[c];
+    // uniform trip count so that every lane of a warp takes part in the term-count vote
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (N + stride - 1) / stride;
+    for (int it = 0; it < iters; ++it) {
+        const int c = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool live = c < N;
+        const int cc = live ? c : N - 1;
+        const int x = cc % g.nx, y = cc / g.nx;
+        const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
         // Laplacians of u1 + u0 and v1 + v0 (G3): face differences, ghost = clamp
         double lu = 0.0, lv = 0.0;
         const double su = u1 + u0, sv = v1 + v0;
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const double ih2 = f < 2 ? g.ihx2 : g.ihy2;
-            const int n = nbr[f];
-            lu += (U1(n) + Pu[n] - su) * ih2;
-            lv += (V1(n) + Pv[n] - sv) * ih2;
+            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
+            lu = fma(Xu[n] + Pu[n] - su, ih2, lu);
+            lv = fma(Xv[n] + Pv[n] - sv, ih2, lv);
         }
         // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma)
-        const double zp = 0.5 * ((u1 + v1) + (u0 + v0)), sp = 0.5 * ((u1 + v1) - (u0 + v0));
-        const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
-        if (!(zp > 0.0 && zp < 1.0 && zq > 0.0 && zq < 1.0)) flag |= 1;
-        double phi = 0.0, psi = 0.0;
-        if (!(flag & 1)) {
-            phi = phi_series(zp, sp, k.S);
-            psi = phi_series(zq, sq, k.S);
-        }
+        const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
+        const double zp = 0.5 * (p1 + p0), sp = 0.5 * (p1 - p0);
+        const double zq = 0.5 * (q1 + q0), sq = 0.5 * (q1 - q0);
+        const bool ok = in_unit(zp) && in_unit(zq);
+        if (live && !ok) flag |= 1;
+        const SeriesArgs ap = series_args(ok ? zp : 0.5, sp);
+        const SeriesArgs aq = series_args(ok ? zq : 0.5, sq);
+        const int K = series_terms(fmax(fmax(ap.ra, ap.rb), fmax(aq.ra, aq.rb)), k.S);
+        double phi = phi_series(ap, K), psi = phi_series(aq, K);
+        if (!ok) { phi = 0.0; psi = 0.0; }
         const double Gu = -0.5 * k.alpha * (su - 1.0) + k.theta * (phi + psi) - 0.5 * k.gamma * lu;
         const double Gv = -0.5 * k.beta * sv + k.theta * (phi - psi) - 0.5 * k.gamma * lv;
         const double ub = 0.5 * su, vb = 0.5 * sv;
-        a.G[c] = Gu;
-        a.G[N + c] = Gv;
-        a.G[2 * N + c] = ub * (1.0 - ub) * (0.25 - vb * vb);
-        if (Su) {
-            a.Xt[c] = u1;
-            a.Xt[N + c] = v1;
-            const double p1 = u1 + v1, q1 = u1 - v1;
-            if (!(p1 > 0.0 && p1 < 1.0 && q1 > 0.0 && q1 < 1.0)) flag |= 2;
+        if (live) {
+            a.G[c] = Gu;
+            a.G[N + c] = Gv;
+            a.G[2 * N + c] = ub * (1.0 - ub) * (0.25 - vb * vb);
         }
+    }
+    if (flag) atomicOr(a.flags, flag);
+}
+
+// Trial state of the line search: Xt_u = X_u + lam (S_u + shift), Xt_v = X_v + lam S_v,
+// with flag bit 1 when some u+v or u-v leaves (0, 1).
+__global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
+    int flag = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        const double u = fma(a.lam, a.S[c] + a.shift, a.X[c]);
+        const double v = fma(a.lam, a.S[N + c], a.X[N + c]);
+        a.Xt[c] = u;
+        a.Xt[N + c] = v;
+        if (!(in_unit(u + v) && in_unit(u - v))) flag |= 2;
     }
     if (flag) atomicOr(a.flags, flag);
 }
@@ -209,7 +250,7 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
 __global__ void __launch_bounds__(256) f_kernel(Geom g, Coef k, ResidualArgs a) {
     __shared__ double sh[32];
     const int N = g.N;
-    const double* __restrict__ X1 = a.S ? a.Xt : a.X;
+    const double* __restrict__ X1 = a.X;
     const double* __restrict__ Gu = a.G;
     const double* __restrict__ Gv = a.G + N;
     const double* __restrict__ cm = a.G + 2 * N;
@@ -244,6 +285,11 @@ cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& 
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
     g_kernel<<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
+    trial_kernel<<<grid_for(g.N, 256), 256, 0, s>>>(g.N, a);
     return cudaGetLastError();
 }
 

@@ -158,7 +158,13 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     ResidualArgs a;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
     a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.partial = h->partial; a.flags = h->flags;
-    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * (S ? 11 : 7), 0.0, launch_residual_g(h->g, h->k, a, h->stream));
+    if (S) {
+        // the line search's trial state X + lam (S + shift e_u), then F there
+        KLA(ACAC_K_VECTOR, 40.0 * h->N, 0.0, launch_trial(h->g, a, h->stream));
+        a.X = h->Xt;
+        a.S = nullptr;
+    }
+    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 0.0, launch_residual_g(h->g, h->k, a, h->stream));
     KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
     KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -601,8 +607,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             RasLaunch& L = h->ras_launch;
             L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
             L.stage_elems = (CREC * h->ras_maxcnt + 31) / 32 * 32;
-            L.tpc = 2;   // measured: 2 threads per cell beats 4 in both precisions
-            L.threads = 32 * ((L.tpc * h->ras_maxcnt + 31) / 32) + 32;
+            L.threads = 32 * ((2 * h->ras_maxcnt + 31) / 32) + 32;
             const size_t vec_bytes = r128(h->ras_maxpad * 2 * ks);
             const size_t stage_bytes = (size_t)L.stage_elems * ks;
             const size_t cap = (size_t)optin - 2048;
