@@ -62,7 +62,7 @@ extern "C" {
 
 /* Problem and solver settings.  Defaults: acac_default_params(). */
 typedef struct acac_params {
-    int    dim;                 /* 2 (3 is rejected by this build: ACAC_E_ARG)          */
+    int    dim;                 /* 2 or 3                                                */
     int    n[3];                /* Nx, Ny, Nz; each >= 4                                */
     double L[3];                /* domain lengths; dx = L[0]/n[0], ...                  */
     int    bc;                  /* ACAC_BC_*                                             */
@@ -115,7 +115,8 @@ void acac_default_params(acac_params *p);
  * wrapped when periodic, clipped at Neumann walls).  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  *out receives the handle.
  * Errors: ACAC_E_ARG (sizes < 4, non-positive coefficient, periodic box that
- * would wrap onto itself, dim != 2, batch != 1), ACAC_E_NOMEM, ACAC_E_CUDA. */
+ * would wrap onto itself, subdomain box under 4 or over 250 cells in some
+ * direction, dim not 2 or 3, batch != 1), ACAC_E_NOMEM, ACAC_E_CUDA. */
 int acac_create(const acac_params *p, void *cuda_stream, acac_handle **out);
 
 /* One accepted time step, in place: u, v (device, N doubles each) hold U^n on
@@ -152,10 +153,13 @@ int acac_residual(acac_handle *h, const double *X1, const double *X0, double dt,
                   double *F, double *fnorm);
 
 /* Assembled Jacobian dF/dX1 at (X1, X0, dt) in stencil-diagonal storage, Krylov
- * precision: J[(b*4 + e)*N + cell], b = stencil slot 0..12 in the order
- * (0,0),(-1,0),(1,0),(0,-1),(0,1),(-2,0),(2,0),(0,-2),(0,2),(-1,-1),(1,-1),(-1,1),(1,1)
- * as (dx,dy); e = 0:(u-row,u-col) 1:(u,v) 2:(v,u) 3:(v,v).  Couplings to cells
- * outside a Neumann domain are stored as 0.  J holds 52*N values (device). */
+ * precision: J[(b*4 + e)*N + cell], e = 0:(u-row,u-col) 1:(u,v) 2:(v,u) 3:(v,v).
+ * 2D, b = slot 0..12 in the order (dx,dy) = (0,0),(-1,0),(1,0),(0,-1),(0,1),(-2,0),
+ * (2,0),(0,-2),(0,2),(-1,-1),(1,-1),(-1,1),(1,1): J holds 52*N values.
+ * 3D, b = slot 0..24: centre; faces -x,+x,-y,+y,-z,+z; two steps -2x,+2x,-2y,+2y,-2z,+2z;
+ * edge diagonals (dx,dy,dz) = (-1,-1,0),(1,-1,0),(-1,1,0),(1,1,0),(-1,0,-1),(1,0,-1),
+ * (-1,0,1),(1,0,1),(0,-1,-1),(0,1,-1),(0,-1,1),(0,1,1): J holds 100*N values.
+ * Couplings to cells outside a Neumann domain are stored as 0 (device). */
 int acac_jacobian(acac_handle *h, const double *X1, const double *X0, double dt, void *J);
 
 /* y = J w with J from acac_jacobian (Krylov precision, device). */

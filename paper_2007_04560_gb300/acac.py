@@ -175,7 +175,7 @@ def acac_residual_noalloc(p, X1, X0, dt, F, stream=None, check=True):
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = 2 * int(p.n[0]) * int(p.n[1])
+    n = 2 * int(p.n[0]) * int(p.n[1]) * (int(p.n[2]) if p.dim == 3 else 1)
     cp = to_c_params(p)
     fn = ctypes.c_double()
     st = _lib().acac_residual_noalloc(ctypes.byref(cp), _dev(X1, torch.float64, n, "X1"),
@@ -203,6 +203,7 @@ class Solver:
         self.params = params
         self.N = int(params.n[0]) * int(params.n[1]) * (int(params.n[2]) if params.dim == 3 else 1)
         self.kdtype = torch.float32 if params.precision == 1 else torch.float64
+        self.nslot = 13 if params.dim == 2 else 25
         self.h = acac_create(params, stream)
 
     def close(self):
@@ -270,10 +271,10 @@ class Solver:
     def jacobian(self, X1, X0, dt, J):
         import torch
         _check(_lib().acac_jacobian(self.h, _dev(X1, torch.float64, 2 * self.N), _dev(X0, torch.float64, 2 * self.N),
-                                    float(dt), _dev(J, self.kdtype, 52 * self.N, "J")), "acac_jacobian")
+                                    float(dt), _dev(J, self.kdtype, 4 * self.nslot * self.N, "J")), "acac_jacobian")
 
     def spmv(self, J, w, y):
-        _check(_lib().acac_spmv(self.h, _dev(J, self.kdtype, 52 * self.N, "J"), _dev(w, self.kdtype, 2 * self.N, "w"),
+        _check(_lib().acac_spmv(self.h, _dev(J, self.kdtype, 4 * self.nslot * self.N, "J"), _dev(w, self.kdtype, 2 * self.N, "w"),
                                 _dev(y, self.kdtype, 2 * self.N, "y")), "acac_spmv")
 
     def jvp(self, X1, X0, dt, w, y):
@@ -283,7 +284,7 @@ class Solver:
                                _dev(y, self.kdtype, 2 * self.N, "y")), "acac_jvp")
 
     def ras_factor(self, J):
-        _check(_lib().acac_ras_factor(self.h, _dev(J, self.kdtype, 52 * self.N, "J")), "acac_ras_factor")
+        _check(_lib().acac_ras_factor(self.h, _dev(J, self.kdtype, 4 * self.nslot * self.N, "J")), "acac_ras_factor")
 
     def ras_apply(self, r, z):
         _check(_lib().acac_ras_apply(self.h, _dev(r, self.kdtype, 2 * self.N, "r"),

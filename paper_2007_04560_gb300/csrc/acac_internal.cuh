@@ -61,9 +61,70 @@ struct Geom {
     int bc;              // ACAC_BC_*
     double hx, hy;
     double ihx2, ihy2;   // 1/hx^2, 1/hy^2
-    double vol;          // hx*hy
+    double vol;          // hx*hy (*hz)
     float ihx2f, ihy2f;  // the same in float, for the FP32 Jacobian kernels
+    int nz, dim;         // 3D: z extent (1 in 2D)
+    double hz, ihz2;
+    float ihz2f;
 };
+
+// ---------------------------------------------------------------- 3D stencil
+// 25 slots of the radius-2 stencil in 3D: 0 centre; 1..6 faces -x,+x,-y,+y,-z,+z;
+// 7..12 two steps along an axis; 13..24 edge diagonals (xy, xz, yz).
+constexpr int NSLOT3 = 25;
+constexpr int CREC3 = 52;          // 3D record: 12 lower 2x2 blocks (+4 pad) | inverse pivot + 12 upper blocks
+constexpr int NCOEF3 = 2 * CREC3;
+__host__ __device__ constexpr int s3_dx(int s) {
+    return (s == 1 || s == 13 || s == 15 || s == 17 || s == 19) ? -1 : (s == 2 || s == 14 || s == 16 || s == 18 || s == 20) ? 1
+         : s == 7 ? -2 : s == 8 ? 2 : 0;
+}
+__host__ __device__ constexpr int s3_dy(int s) {
+    return (s == 3 || s == 13 || s == 14 || s == 21 || s == 23) ? -1 : (s == 4 || s == 15 || s == 16 || s == 22 || s == 24) ? 1
+         : s == 9 ? -2 : s == 10 ? 2 : 0;
+}
+__host__ __device__ constexpr int s3_dz(int s) {
+    return (s == 5 || s == 17 || s == 18 || s == 21 || s == 22) ? -1 : (s == 6 || s == 19 || s == 20 || s == 23 || s == 24) ? 1
+         : s == 11 ? -2 : s == 12 ? 2 : 0;
+}
+__host__ __device__ constexpr int slot3_of(int dx, int dy, int dz) {
+    for (int s = 0; s < NSLOT3; ++s)
+        if (s3_dx(s) == dx && s3_dy(s) == dy && s3_dz(s) == dz) return s;
+    return -1;
+}
+// the 12 lower neighbours in increasing natural order (x fastest, then y, then z);
+// the upper ones are their negatives in reverse order
+__host__ __device__ constexpr int l3_dx(int k) { return (k == 2 || k == 7 || k == 11) ? -1 : (k == 4 || k == 9) ? 1 : k == 10 ? -2 : 0; }
+__host__ __device__ constexpr int l3_dy(int k) { return (k == 1 || k == 7 || k == 8 || k == 9) ? -1 : k == 5 ? 1 : k == 6 ? -2 : 0; }
+__host__ __device__ constexpr int l3_dz(int k) { return k == 0 ? -2 : (k >= 1 && k <= 5) ? -1 : 0; }
+__host__ __device__ constexpr int u3_dx(int k) { return -l3_dx(11 - k); }
+__host__ __device__ constexpr int u3_dy(int k) { return -l3_dy(11 - k); }
+__host__ __device__ constexpr int u3_dz(int k) { return -l3_dz(11 - k); }
+// faces in 3D: f = 0..5 is -x, +x, -y, +y, -z, +z
+__host__ __device__ constexpr int f3_dx(int f) { return f == 0 ? -1 : f == 1 ? 1 : 0; }
+__host__ __device__ constexpr int f3_dy(int f) { return f == 2 ? -1 : f == 3 ? 1 : 0; }
+__host__ __device__ constexpr int f3_dz(int f) { return f == 4 ? -1 : f == 5 ? 1 : 0; }
+
+__device__ __forceinline__ int wrap_or_clamp(int v, int n, bool periodic) {
+    if (periodic) return v < 0 ? v + n : (v >= n ? v - n : v);
+    return v < 0 ? 0 : (v >= n ? n - 1 : v);
+}
+// Neighbour index in 3D (wrapped or clamped per axis, as nb_index in 2D).
+__device__ __forceinline__ int nb_index3(const Geom& g, int x, int y, int z, int dx, int dy, int dz) {
+    const bool per = g.bc == ACAC_BC_PERIODIC;
+    const int xx = wrap_or_clamp(x + dx, g.nx, per), yy = wrap_or_clamp(y + dy, g.ny, per);
+    const int zz = wrap_or_clamp(z + dz, g.nz, per);
+    return (zz * g.ny + yy) * g.nx + xx;
+}
+// 1/h^2 of face f of cell (x, y, z) if it carries flux, else 0.
+template <typename T>
+__device__ __forceinline__ T face_w3(const Geom& g, int x, int y, int z, int f) {
+    const int xx = x + f3_dx(f), yy = y + f3_dy(f), zz = z + f3_dz(f);
+    const bool open = g.bc == ACAC_BC_PERIODIC ||
+                      (xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny && zz >= 0 && zz < g.nz);
+    if (!open) return (T)0;
+    if (sizeof(T) == 8) return (T)(f < 2 ? g.ihx2 : f < 4 ? g.ihy2 : g.ihz2);
+    return (T)(f < 2 ? g.ihx2f : f < 4 ? g.ihy2f : g.ihz2f);
+}
 
 struct Coef {
     double alpha, beta, theta, gamma, rho;
@@ -109,6 +170,44 @@ __device__ __forceinline__ bool in_domain(const Geom& g, int x, int y) {
     return g.bc == ACAC_BC_PERIODIC || (x >= 0 && x < g.nx && y >= 0 && y < g.ny);
 }
 
+// Dimension-generic cell helpers (faces 0..3 are -x, +x, -y, +y in both 2D and 3D).
+template <int DIM>
+__device__ __forceinline__ void decode_cell(const Geom& g, int c, int& x, int& y, int& z) {
+    x = c % g.nx;
+    if (DIM == 2) {
+        y = c / g.nx;
+        z = 0;
+    } else {
+        const int t = c / g.nx;
+        y = t % g.ny;
+        z = t / g.ny;
+    }
+}
+template <int DIM>
+__device__ __forceinline__ int face_nb(const Geom& g, int x, int y, int z, int f) {
+    return DIM == 2 ? nb_index(g, x, y, face_dx(f), face_dy(f)) : nb_index3(g, x, y, z, f3_dx(f), f3_dy(f), f3_dz(f));
+}
+template <int DIM, typename T>
+__device__ __forceinline__ T face_weight(const Geom& g, int x, int y, int z, int f) {
+    return DIM == 2 ? face_w<T>(g, x, y, f) : face_w3<T>(g, x, y, z, f);
+}
+__device__ __forceinline__ double face_ih2(const Geom& g, int f) { return f < 2 ? g.ihx2 : f < 4 ? g.ihy2 : g.ihz2; }
+// Generic stencil slots (2D: 13, 3D: 25; slot f+1 is face f in both).
+template <int DIM> __host__ __device__ constexpr int nslot() { return DIM == 2 ? NSLOT : NSLOT3; }
+template <int DIM> __host__ __device__ constexpr int sl_dx(int s) { return DIM == 2 ? slot_dx(s) : s3_dx(s); }
+template <int DIM> __host__ __device__ constexpr int sl_dy(int s) { return DIM == 2 ? slot_dy(s) : s3_dy(s); }
+template <int DIM> __host__ __device__ constexpr int sl_dz(int s) { return DIM == 2 ? 0 : s3_dz(s); }
+template <int DIM> __host__ __device__ constexpr int sl_of(int dx, int dy, int dz) {
+    return DIM == 2 ? (dz == 0 ? slot_of(dx, dy) : -1) : slot3_of(dx, dy, dz);
+}
+template <int DIM> __host__ __device__ constexpr int fc_dx(int f) { return DIM == 2 ? face_dx(f) : f3_dx(f); }
+template <int DIM> __host__ __device__ constexpr int fc_dy(int f) { return DIM == 2 ? face_dy(f) : f3_dy(f); }
+template <int DIM> __host__ __device__ constexpr int fc_dz(int f) { return DIM == 2 ? 0 : f3_dz(f); }
+template <int DIM>
+__device__ __forceinline__ int slot_nb(const Geom& g, int x, int y, int z, int s) {
+    return DIM == 2 ? nb_index(g, x, y, slot_dx(s), slot_dy(s)) : nb_index3(g, x, y, z, s3_dx(s), s3_dy(s), s3_dz(s));
+}
+
 // Linearisation cache (Krylov precision T).  For cell k:
 //   c, cu = dc/du1, cv = dc/dv1, Gu, Gv, du = dG_u/du1 pointwise part
 //   (-alpha/2 + theta dphi/dp1 + theta dpsi/dq1), xc = theta (dphi/dp1 - dpsi/dq1).
@@ -124,6 +223,9 @@ struct SubInfo {
     int W, H;            // box size
     int own_x0, own_x1;  // owned (non-overlapping) range, box-local
     int own_y0, own_y1;
+    int oz, D;           // 3D: z corner and depth (0, 1 in 2D)
+    int own_z0, own_z1;
+    long long cell_base; // 3D: first entry in the level-ordered cell list / position map
     int nlev;            // wavefront levels = (W-1) + 2(H-1) + 1
     int lev_base;        // first entry of this subdomain in the level-offset table
     long long coef_base; // first coefficient of this subdomain
@@ -148,6 +250,13 @@ struct RasLaunch {
 int validate_params(const acac_params* p);
 
 // ---------------------------------------------------------------- kernels (launchers)
+template <typename T>
+cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                               const int* pos, const T* J, T* coef, int threads, int* flags, cudaStream_t s);
+template <typename T>
+cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                              const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
+                              T* gscratch, cudaStream_t s);
 // residual.cu
 cudaError_t set_taylor_constants(int S);
 struct ResidualArgs {

@@ -18,34 +18,37 @@ static int grid1(long long n, int threads) {
 }
 
 // ---------------------------------------------------------------- assembly
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt, Cache<T> C, T* __restrict__ J) {
+    constexpr int NS = nslot<DIM>();
+    constexpr int NF = 2 * DIM;
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int x = c % g.nx, y = c / g.nx;
+    int x, y, z;
+    decode_cell<DIM>(g, c, x, y, z);
     // arithmetic in the Jacobian's precision T
     const T hg = (T)(0.5 * k.gamma);
     const T dvshift = (T)(0.5 * (k.alpha - k.beta));
     const T half = (T)0.5;
-    T Juu[NSLOT], Juv[NSLOT];
+    T Juu[NS], Juv[NS];
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) { Juu[s] = (T)0; Juv[s] = (T)0; }
+    for (int s = 0; s < NS; ++s) { Juu[s] = (T)0; Juv[s] = (T)0; }
     const T cc = C.c[c], cuc = C.cu[c], cvc = C.cv[c], gc = C.Gu[c], gvc = C.Gv[c];
     const T duc = C.du[c], xcc = C.xc[c];
     T lapc = (T)0;   // sum of open faces / h^2 at c
-    T eih2c[4];
+    T eih2c[NF];
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        eih2c[f] = face_w<T>(g, x, y, f);
+    for (int f = 0; f < NF; ++f) {
+        eih2c[f] = face_weight<DIM, T>(g, x, y, z, f);
         lapc += eih2c[f];
     }
     Juu[0] = (T)(1.0 / dt);
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int fx = face_dx(f), fy = face_dy(f);
-        const int sf = slot_of(fx, fy);
-        const int n = nb_index(g, x, y, fx, fy);
+    for (int f = 0; f < NF; ++f) {
+        const int fx = fc_dx<DIM>(f), fy = fc_dy<DIM>(f), fz = fc_dz<DIM>(f);
+        const int sf = sl_of<DIM>(fx, fy, fz);
+        const int n = face_nb<DIM>(g, x, y, z, f);
         const T w = eih2c[f];
         const T cn = C.c[n], dG = C.Gu[n] - gc, ct = half * (cc + cn);
         // mobility variation of the face flux
@@ -56,11 +59,11 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
         // - ct * dG_u(n)/dX : pointwise part and Laplacian of the neighbour
         Juu[sf] -= w * ct * C.du[n];
         Juv[sf] -= w * ct * C.xc[n];
-        const int nx_ = x + fx, ny_ = y + fy;
+        const int nx_ = x + fx, ny_ = y + fy, nz_ = z + fz;
 #pragma unroll
-        for (int f2 = 0; f2 < 4; ++f2) {
-            const T e2 = face_w<T>(g, nx_, ny_, f2);
-            const int s2 = slot_of(fx + face_dx(f2), fy + face_dy(f2));
+        for (int f2 = 0; f2 < NF; ++f2) {
+            const T e2 = face_weight<DIM, T>(g, nx_, ny_, nz_, f2);
+            const int s2 = sl_of<DIM>(fx + fc_dx<DIM>(f2), fy + fc_dy<DIM>(f2), fz + fc_dz<DIM>(f2));
             Juu[s2] += w * ct * hg * e2;
             Juu[sf] -= w * ct * hg * e2;
         }
@@ -68,21 +71,21 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
         Juu[0] += w * ct * duc;
         Juv[0] += w * ct * xcc;
 #pragma unroll
-        for (int f2 = 0; f2 < 4; ++f2) {
-            const int s2 = slot_of(face_dx(f2), face_dy(f2));
+        for (int f2 = 0; f2 < NF; ++f2) {
+            const int s2 = sl_of<DIM>(fc_dx<DIM>(f2), fc_dy<DIM>(f2), fc_dz<DIM>(f2));
             Juu[s2] -= w * ct * hg * eih2c[f2];
         }
         Juu[0] += w * ct * hg * lapc;
     }
     const T irho = (T)(1.0 / k.rho);
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
+    for (int s = 0; s < NS; ++s) {
         T jvu = (T)0, jvv = (T)0;
         if (s == 0) {
             jvu = (cuc * gvc + cc * xcc) * irho;
             jvv = (T)(1.0 / dt) + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
-        } else if (s <= 4) {
-            const int f = s - 1;   // slots 1..4 are faces -x, +x, -y, +y
+        } else if (s <= NF) {
+            const int f = s - 1;   // slots 1..2*DIM are the faces
             jvv = -cc * hg * eih2c[f] * irho;
         }
         J[(size_t)(s * 4 + 0) * N + c] = (T)Juu[s];
@@ -95,22 +98,24 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
 template <typename T>
 cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J,
                             cudaStream_t s) {
-    assemble_kernel<T><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
+    if (g.dim == 3) assemble_kernel<T, 3><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
+    else assemble_kernel<T, 2><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- assembled product
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__ J, const T* __restrict__ w,
                                                    T* __restrict__ y) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int x = c % g.nx, yy = c / g.nx;
+    int x, yy, zz;
+    decode_cell<DIM>(g, c, x, yy, zz);
     T au = 0, av = 0;
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s) {
-        const int n = nb_index(g, x, yy, slot_dx(s), slot_dy(s));
+    for (int s = 0; s < nslot<DIM>(); ++s) {
+        const int n = slot_nb<DIM>(g, x, yy, zz, s);
         const T wu = w[n], wv = w[N + n];
         au += J[(size_t)(s * 4 + 0) * N + c] * wu + J[(size_t)(s * 4 + 1) * N + c] * wv;
         av += J[(size_t)(s * 4 + 2) * N + c] * wu + J[(size_t)(s * 4 + 3) * N + c] * wv;
@@ -121,25 +126,27 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__
 
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s) {
-    spmv_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
+    if (g.dim == 3) spmv_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
+    else spmv_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- matrix-free product
 // Pass 1: dG_u, dG_v, dc per cell into tmp = [dGu | dGv | dc].
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, const T* __restrict__ w,
                                                    T* __restrict__ tmp) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int x = c % g.nx, y = c / g.nx;
+    int x, y, z;
+    decode_cell<DIM>(g, c, x, y, z);
     const T wu = w[c], wv = w[N + c];
     T lu = 0, lv = 0;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
-        const T ih2 = f < 2 ? (T)g.ihx2 : (T)g.ihy2;
+    for (int f = 0; f < 2 * DIM; ++f) {
+        const int n = face_nb<DIM>(g, x, y, z, f);
+        const T ih2 = sizeof(T) == 8 ? (T)face_ih2(g, f) : (T)(f < 2 ? g.ihx2f : f < 4 ? g.ihy2f : g.ihz2f);
         lu += (w[n] - wu) * ih2;
         lv += (w[N + n] - wv) * ih2;
     }
@@ -150,23 +157,24 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, c
     tmp[2 * N + c] = C.cu[c] * wu + C.cv[c] * wv;
 }
 
-template <typename T>
+template <typename T, int DIM>
 __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Cache<T> C,
                                                    const T* __restrict__ w, const T* __restrict__ tmp,
                                                    T* __restrict__ y) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    const int x = c % g.nx, yy = c / g.nx;
+    int x, yy, zz;
+    decode_cell<DIM>(g, c, x, yy, zz);
     const T* dGu = tmp;
     const T* dGv = tmp + N;
     const T* dc = tmp + 2 * N;
     const T cc = C.c[c], gc = C.Gu[c], dgc = dGu[c], dcc = dc[c];
     T div = 0;
 #pragma unroll
-    for (int f = 0; f < 4; ++f) {
-        const int n = nb_index(g, x, yy, face_dx(f), face_dy(f));
-        const T w_ = face_w<T>(g, x, yy, f);
+    for (int f = 0; f < 2 * DIM; ++f) {
+        const int n = face_nb<DIM>(g, x, yy, zz, f);
+        const T w_ = face_weight<DIM, T>(g, x, yy, zz, f);
         div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
     }
     const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho);
@@ -176,14 +184,16 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Ca
 
 template <typename T>
 cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
-    jvp1_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
+    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
+    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, const T* tmp,
                          T* y, cudaStream_t s) {
-    jvp2_kernel<T><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
+    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
+    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
     return cudaGetLastError();
 }
 

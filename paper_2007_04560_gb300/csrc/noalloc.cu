@@ -16,6 +16,7 @@
 // make that first call before any stream capture.  All calls share the arrays, so
 // calls whose work overlaps on the GPU (other streams, other host threads) race.
 #include <mutex>
+#include <string.h>
 
 #include "acac_internal.cuh"
 
@@ -62,7 +63,7 @@ extern "C" int acac_residual_noalloc(const acac_params* p, const double* X1, con
     if (!p || !X1 || !X0 || !F || !(dt > 0)) return ACAC_E_ARG;
     int st = validate_params(p);
     if (st != ACAC_OK) return st;
-    const long long ncell = (long long)p->n[0] * p->n[1];
+    const long long ncell = (long long)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
     if (ncell > NOALLOC_MAX_CELLS) return ACAC_E_ARG;
     double* scratch = nullptr;
     int* flags = nullptr;
@@ -71,7 +72,13 @@ extern "C" int acac_residual_noalloc(const acac_params* p, const double* X1, con
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
     Geom g;
+    memset(&g, 0, sizeof(g));
     g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)ncell; g.bc = p->bc;
+    g.dim = p->dim;
+    g.nz = p->dim == 3 ? p->n[2] : 1;
+    g.hz = p->dim == 3 ? p->L[2] / p->n[2] : 1.0;
+    g.ihz2 = p->dim == 3 ? 1.0 / (g.hz * g.hz) : 0.0;
+    g.ihz2f = (float)g.ihz2;
     g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
     g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
     g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;

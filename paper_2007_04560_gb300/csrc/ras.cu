@@ -441,12 +441,233 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
     return cudaGetLastError();
 }
 
+
+// ================================================================ 3D
+// Same factorization and sweeps on 3D boxes: wavefront level l = i + 2j + 3k, 12 lower and
+// 12 upper 2x2 blocks per cell, records of CREC3 values.  The cells of each level come from
+// a per-subdomain list (packed i | j << 10 | k << 20, in level order) and a map from the
+// box-local cell index to its position in its level.  One CTA per subdomain, two threads per
+// cell (one per block row); records are read from global memory.
+__device__ __forceinline__ void unpack3(int p, int& i, int& j, int& k) {
+    i = p & 1023;
+    j = (p >> 10) & 1023;
+    k = p >> 20;
+}
+__device__ __forceinline__ int box_cell3(const Geom& g, const SubInfo& sd, int i, int j, int k) {
+    const bool per = g.bc == ACAC_BC_PERIODIC;
+    const int gx = wrap_or_clamp(sd.ox + i, g.nx, per), gy = wrap_or_clamp(sd.oy + j, g.ny, per);
+    const int gz = wrap_or_clamp(sd.oz + k, g.nz, per);
+    return (gz * g.ny + gy) * g.nx + gx;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                          const int* __restrict__ lev_off, const int* __restrict__ cells,
+                                                          const int* __restrict__ pos, const T* __restrict__ J, T* coef,
+                                                          int* flags) {
+    const SubInfo sd = subs[blockIdx.x];
+    const int* lo = lev_off + sd.lev_base;
+    const int* cl = cells + sd.cell_base;
+    const int* ps = pos + sd.cell_base;
+    const size_t N = (size_t)g.N;
+    const int rr = threadIdx.x & 1;
+    int bad = 0;
+    for (int l = 0; l < sd.nlev; ++l) {
+        const int cnt = lo[l + 1] - lo[l];
+        T* lvl = coef + sd.coef_base + (long long)lo[l] * NCOEF3;
+        for (int m = threadIdx.x >> 1; m < (cnt + 15) / 16 * 16; m += blockDim.x >> 1) {
+            const bool act = m < cnt;
+            int i = 0, j = 0, k = 0;
+            if (act) unpack3(cl[lo[l] + m], i, j, k);
+            T A[NSLOT3][2];
+            if (act) {
+                const int gc = box_cell3(g, sd, i, j, k);
+#pragma unroll
+                for (int s = 0; s < NSLOT3; ++s) {
+                    const int ii = i + s3_dx(s), jj = j + s3_dy(s), kk = k + s3_dz(s);
+                    const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H && kk >= 0 && kk < sd.D;
+                    A[s][0] = in ? J[(size_t)(s * 4 + 2 * rr) * N + gc] : (T)0;
+                    A[s][1] = in ? J[(size_t)(s * 4 + 2 * rr + 1) * N + gc] : (T)0;
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < NSLOT3; ++s) { A[s][0] = (T)0; A[s][1] = (T)0; }
+            }
+            T* fw = lvl + (long long)m * CREC3;
+            T* bw = lvl + (long long)(cnt + m) * CREC3;
+            if (act) {
+#pragma unroll
+                for (int a = 0; a < 12; ++a) {
+                    const int dx1 = l3_dx(a), dy1 = l3_dy(a), dz1 = l3_dz(a);
+                    const int ki = i + dx1, kj = j + dy1, kk = k + dz1;
+                    T L0 = (T)0, L1 = (T)0;
+                    if (ki >= 0 && ki < sd.W && kj >= 0 && kj < sd.H && kk >= 0 && kk < sd.D) {
+                        const int lk = l + dx1 + 2 * dy1 + 3 * dz1;
+                        const int tk = ps[(kk * sd.H + kj) * sd.W + ki];
+                        const int ck = lo[lk + 1] - lo[lk];
+                        const T* kr = coef + sd.coef_base + (long long)lo[lk] * NCOEF3 + (long long)(ck + tk) * CREC3;
+                        const T* As = A[slot3_of(dx1, dy1, dz1)];
+                        L0 = As[0] * kr[0] + As[1] * kr[2];
+                        L1 = As[0] * kr[1] + As[1] * kr[3];
+#pragma unroll
+                        for (int b = 0; b < 12; ++b) {
+                            const int s2 = slot3_of(dx1 + u3_dx(b), dy1 + u3_dy(b), dz1 + u3_dz(b));
+                            if (s2 >= 0) {
+                                const T* U = kr + 4 + 4 * b;
+                                A[s2][0] -= L0 * U[0] + L1 * U[2];
+                                A[s2][1] -= L0 * U[1] + L1 * U[3];
+                            }
+                        }
+                    }
+                    fw[4 * a + 2 * rr] = L0;
+                    fw[4 * a + 2 * rr + 1] = L1;
+                }
+                fw[48 + 2 * rr] = (T)0;
+                fw[49 + 2 * rr] = (T)0;
+            }
+            const T o0 = __shfl_xor_sync(0xffffffffu, A[0][0], 1);
+            const T o1 = __shfl_xor_sync(0xffffffffu, A[0][1], 1);
+            if (act) {
+                const T d00 = rr ? o0 : A[0][0], d01 = rr ? o1 : A[0][1];
+                const T d10 = rr ? A[0][0] : o0, d11 = rr ? A[0][1] : o1;
+                const T det = d00 * d11 - d01 * d10;
+                if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
+                const T id = (T)1 / det;
+                bw[2 * rr] = rr ? -d10 * id : d11 * id;
+                bw[2 * rr + 1] = rr ? d00 * id : -d01 * id;
+#pragma unroll
+                for (int b = 0; b < 12; ++b) {
+                    const int s = slot3_of(u3_dx(b), u3_dy(b), u3_dz(b));
+                    bw[4 + 4 * b + 2 * rr] = A[s][0];
+                    bw[4 + 4 * b + 2 * rr + 1] = A[s][1];
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(flags, 4);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512) ras_apply3_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                         const int* __restrict__ lev_off, const int* __restrict__ cells,
+                                                         const T* __restrict__ coef, const T* __restrict__ r,
+                                                         T* __restrict__ z, int ras_type, T* gscratch) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const SubInfo sd = subs[blockIdx.x];
+    const int* lo = lev_off + sd.lev_base;
+    const int* cl = cells + sd.cell_base;
+    const int N = g.N;
+    const int PW = sd.W + 4, PH = sd.H + 4, PD = sd.D + 4;
+    const int plane = PW * PH;
+    V2<T>* yv = gscratch ? reinterpret_cast<V2<T>*>(gscratch) + sd.vec_base : reinterpret_cast<V2<T>*>(smem_raw);
+    T* ys = reinterpret_cast<T*>(yv);
+    const int rr = threadIdx.x & 1;
+    for (int idx = threadIdx.x; idx < plane * PD; idx += blockDim.x) yv[idx] = V2<T>{(T)0, (T)0};
+    __syncthreads();
+    const int ncell = sd.W * sd.H * sd.D;
+    for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
+        const int i = idx % sd.W, j = (idx / sd.W) % sd.H, k = idx / (sd.W * sd.H);
+        const int gc = box_cell3(g, sd, i, j, k);
+        const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1 &&
+                         k >= sd.own_z0 && k < sd.own_z1;
+        V2<T> val{r[gc], r[N + gc]};
+        if (ras_type == ACAC_RAS_RIGHT && !own) val = V2<T>{(T)0, (T)0};
+        yv[((k + 2) * PH + j + 2) * PW + i + 2] = val;
+    }
+    __syncthreads();
+    for (int pass = 0; pass < 2; ++pass) {
+        const bool fwd = pass == 0;
+        for (int s = 0; s < sd.nlev; ++s) {
+            const int l = fwd ? s : sd.nlev - 1 - s;
+            const int cnt = lo[l + 1] - lo[l];
+            const T* lvl = coef + sd.coef_base + (long long)lo[l] * NCOEF3;
+            for (int m = threadIdx.x >> 1; m < (cnt + 15) / 16 * 16; m += blockDim.x >> 1) {
+                const bool act = m < cnt;
+                int i = 0, j = 0, k = 0;
+                if (act) unpack3(cl[lo[l] + m], i, j, k);
+                const int pc = ((k + 2) * PH + j + 2) * PW + i + 2;
+                const T* rec = lvl + (long long)(fwd ? m : cnt + m) * CREC3 + (fwd ? 0 : 4) + 2 * rr;
+                T a0 = (T)0, a1 = (T)0;
+                if (act) {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) {
+                        const int off = fwd ? (l3_dz(q) * plane + l3_dy(q) * PW + l3_dx(q))
+                                            : (u3_dz(q) * plane + u3_dy(q) * PW + u3_dx(q));
+                        const V2<T> nb = yv[pc + off];
+                        T& acc = q < 6 ? a0 : a1;
+                        acc = fma(rec[4 * q], nb.x, acc);
+                        acc = fma(rec[4 * q + 1], nb.y, acc);
+                    }
+                }
+                const T s_me = (act ? ys[2 * pc + rr] : (T)0) - (a0 + a1);
+                if (fwd) {
+                    if (act) ys[2 * pc + rr] = s_me;
+                } else {
+                    const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
+                    if (act) {
+                        const T* di = lvl + (long long)(cnt + m) * CREC3 + 2 * rr;
+                        const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
+                        ys[2 * pc + rr] = fma(di[0], sx, di[1] * sy);
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
+        const int i = idx % sd.W, j = (idx / sd.W) % sd.H, k = idx / (sd.W * sd.H);
+        const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1 &&
+                         k >= sd.own_z0 && k < sd.own_z1;
+        const int gc = box_cell3(g, sd, i, j, k);
+        const V2<T> val = yv[((k + 2) * PH + j + 2) * PW + i + 2];
+        if (ras_type == ACAC_RAS_LEFT) {
+            if (own) { z[gc] = val.x; z[N + gc] = val.y; }
+        } else {
+            atomicAdd(&z[gc], val.x);
+            atomicAdd(&z[N + gc], val.y);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                               const int* pos, const T* J, T* coef, int threads, int* flags, cudaStream_t s) {
+    ras_factor3_kernel<T><<<nsub, threads, 0, s>>>(g, subs, lev_off, cells, pos, J, coef, flags);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                              const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
+                              T* gscratch, cudaStream_t s) {
+    static size_t attr_bytes[2] = {0, 0};
+    const int which = sizeof(T) == 8 ? 0 : 1;
+    if (!gscratch && smem_bytes > 48 * 1024 && smem_bytes > attr_bytes[which]) {
+        cudaError_t e = cudaFuncSetAttribute(ras_apply3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes);
+        if (e != cudaSuccess) return e;
+        attr_bytes[which] = smem_bytes;
+    }
+    if (ras_type != ACAC_RAS_LEFT) {
+        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
+        if (e != cudaSuccess) return e;
+    }
+    ras_apply3_kernel<T><<<nsub, threads, gscratch ? 0 : smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z,
+                                                                          ras_type, gscratch);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                    \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                               T*, int, int, size_t, int*, cudaStream_t);            \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, int*,       \
-                                             cudaStream_t);
+                                             cudaStream_t);                                           \
+    template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*, \
+                                               const int*, const T*, T*, int, int*, cudaStream_t);      \
+    template cudaError_t launch_ras_apply3<T>(const Geom&, int, const SubInfo*, const int*, const int*,  \
+                                              const T*, const T*, T*, int, int, size_t, T*, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -183,6 +183,7 @@ __device__ __forceinline__ bool in_unit(double x) {
     return b > 0 && b < 0x3ff0000000000000LL;
 }
 
+template <int DIM>
 __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
     const int N = g.N;
     const double* __restrict__ Xu = a.X;
@@ -197,15 +198,16 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         const int c = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
         const bool live = c < N;
         const int cc = live ? c : N - 1;
-        const int x = cc % g.nx, y = cc / g.nx;
+        int x, y, z;
+        decode_cell<DIM>(g, cc, x, y, z);
         const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
         // Laplacians of u1 + u0 and v1 + v0 (G3): face differences, ghost = clamp
         double lu = 0.0, lv = 0.0;
         const double su = u1 + u0, sv = v1 + v0;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const double ih2 = f < 2 ? g.ihx2 : g.ihy2;
-            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const double ih2 = face_ih2(g, f);
+            const int n = face_nb<DIM>(g, x, y, z, f);
             lu = fma(Xu[n] + Pu[n] - su, ih2, lu);
             lv = fma(Xv[n] + Pv[n] - sv, ih2, lv);
         }
@@ -247,6 +249,7 @@ __global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
 }
 
 // ---------------------------------------------------------------- pass B
+template <int DIM>
 __global__ void __launch_bounds__(256) f_kernel(Geom g, Coef k, ResidualArgs a) {
     __shared__ double sh[32];
     const int N = g.N;
@@ -257,14 +260,14 @@ __global__ void __launch_bounds__(256) f_kernel(Geom g, Coef k, ResidualArgs a) 
     const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int x = c % g.nx, y = c / g.nx;
+        int x, y, z;
+        decode_cell<DIM>(g, c, x, y, z);
         const double gc = Gu[c], cc = cm[c];
         double div = 0.0;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const double ih2 = f < 2 ? g.ihx2 : g.ihy2;
-            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
-            div += face_open(g, x, y, f) * ih2 * 0.5 * (cc + cm[n]) * (Gu[n] - gc);
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, y, z, f);
+            div += face_weight<DIM, double>(g, x, y, z, f) * 0.5 * (cc + cm[n]) * (Gu[n] - gc);
         }
         const double Fu = (X1[c] - a.X0[c]) * idt - div;
         const double Fv = (X1[N + c] - a.X0[N + c]) * idt + cc * Gv[c] * irho;
@@ -284,7 +287,8 @@ static int grid_for(long long n, int threads) {
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
-    g_kernel<<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
+    if (g.dim == 3) g_kernel<3><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
+    else g_kernel<2><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
     return cudaGetLastError();
 }
 
@@ -294,7 +298,8 @@ cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
-    f_kernel<<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
+    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
+    else f_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
     return cudaGetLastError();
 }
 
@@ -303,17 +308,18 @@ __device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_l
 
 // E~ = sum [e1 + e2 + gamma/2 sum_d ((D+ phi)^2 + (D- phi)^2)/2] dx dy (Eqs. relations,
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
+template <int DIM>
 __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const double* __restrict__ X,
                                                      double* partial, int* flags) {
     __shared__ double sh[32];
     const int N = g.N;
     const double* __restrict__ U = X;
     const double* __restrict__ V = X + N;
-    const double ihx = 1.0 / g.hx, ihy = 1.0 / g.hy;
     double e_acc = 0.0, m_acc = 0.0;
     int flag = 0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const int x = c % g.nx, y = c / g.nx;
+        int x, y, z;
+        decode_cell<DIM>(g, c, x, y, z);
         const double u = U[c], v = V[c];
         const double p = u + v, q = u - v;
         if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) flag |= 1;
@@ -321,13 +327,12 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
                  + k.theta * (xlogx(p) + xlogx(1.0 - p) + xlogx(q) + xlogx(1.0 - q));
         double gr = 0.0;
 #pragma unroll
-        for (int f = 0; f < 4; ++f) {
-            const int n = nb_index(g, x, y, face_dx(f), face_dy(f));
-            const double ih = f < 2 ? ihx : ihy;
-            const double du = (U[n] - u) * ih, dv = (V[n] - v) * ih;
-            gr += du * du + dv * dv;
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, y, z, f);
+            const double du = U[n] - u, dv = V[n] - v;
+            gr = fma(du * du + dv * dv, face_ih2(g, f), gr);
         }
-        e += 0.25 * k.gamma * gr;   // gamma/2 * 1/2 * sum over D+ and D- of both fields
+        e += 0.25 * k.gamma * gr;   // gamma/2 * 1/2 * sum over D+ and D- of both fields and all axes
         e_acc += e;
         m_acc += u;
     }
@@ -340,7 +345,8 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
 
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
                           int* flags, cudaStream_t s) {
-    energy_kernel<<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
+    if (g.dim == 3) energy_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
+    else energy_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
     return cudaGetLastError();
 }
 

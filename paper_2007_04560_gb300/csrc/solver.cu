@@ -37,8 +37,10 @@ struct acac_handle {
     // Schwarz tables
     std::vector<SubInfo> subs;
     std::vector<int> lev;
+    std::vector<int> cells3, pos3;   // 3D: level-ordered packed cells, position map
     SubInfo* subs_dev;
     int* lev_dev;
+    int *cells3_dev, *pos3_dev;
     int ras_threads;
     size_t ras_smem;
     RasLaunch ras_launch;
@@ -189,6 +191,13 @@ void jac_action(acac_handle* h, double dt, const T* w, T* y) {
 
 template <typename T>
 void precond(acac_handle* h, const T* r, T* z) {
+    if (h->g.dim == 3) {
+        KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (100.0 * h->nbox + 2.0 * h->N), 200.0 * h->nbox,
+            launch_ras_apply3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev,
+                                 (const T*)h->coef, r, z, h->p.ras_type, h->ras_threads, h->ras_smem,
+                                 (T*)h->gscratch, h->stream));
+        return;
+    }
     KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
         launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
                             h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch, h->flags + 1,
@@ -198,6 +207,13 @@ void precond(acac_handle* h, const T* r, T* z) {
 template <typename T>
 int factor(acac_handle* h) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    if (h->g.dim == 3) {
+        KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 200.0 * h->nbox, 1200.0 * h->nbox,
+            launch_ras_factor3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev,
+                                  (const T*)h->J, (T*)h->coef, h->ras_threads, h->flags, h->stream));
+        h->n_factor++;
+        return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+    }
     const int ring_cells = h->ras_maxcnt;
     const size_t smem = sizeof(int) * (size_t)(((h->ras_maxlev + 1 + 3) & ~3) + 3 & ~3) +
                         sizeof(T) * 5 * (size_t)ring_cells * CREC;
@@ -408,51 +424,89 @@ void partition_1d(int n, int P, std::vector<int>& s, std::vector<int>& e) {
 int build_subdomains(acac_handle* h) {
     const acac_params& p = h->p;
     const int d = p.ras_overlap;
-    std::vector<int> sx, ex, sy, ey;
-    partition_1d(p.n[0], p.ras_parts[0], sx, ex);
-    partition_1d(p.n[1], p.ras_parts[1], sy, ey);
+    const int dim = p.dim;
+    std::vector<int> st[3], en[3];
+    for (int a = 0; a < dim; ++a) partition_1d(p.n[a], p.ras_parts[a], st[a], en[a]);
+    if (dim == 2) { st[2] = {0}; en[2] = {1}; }
+    const int pz = dim == 3 ? p.ras_parts[2] : 1;
     h->subs.clear();
     h->lev.clear();
+    h->cells3.clear();
+    h->pos3.clear();
     long long coef = 0, vec = 0;
     int maxcnt = 1;
     size_t maxpad = 0;
-    for (int ky = 0; ky < p.ras_parts[1]; ++ky) {
-        for (int kx = 0; kx < p.ras_parts[0]; ++kx) {
-            SubInfo sd;
-            int lox, hix, loy, hiy;
-            if (p.bc == ACAC_BC_PERIODIC) {
-                lox = sx[kx] - d; hix = ex[kx] + d; loy = sy[ky] - d; hiy = ey[ky] + d;
-                if (hix - lox > p.n[0] - 2 || hiy - loy > p.n[1] - 2) return ACAC_E_ARG;
-            } else {
-                lox = std::max(0, sx[kx] - d); hix = std::min(p.n[0], ex[kx] + d);
-                loy = std::max(0, sy[ky] - d); hiy = std::min(p.n[1], ey[ky] + d);
-            }
-            sd.ox = lox; sd.oy = loy;
-            sd.W = hix - lox; sd.H = hiy - loy;
-            sd.own_x0 = sx[kx] - lox; sd.own_x1 = ex[kx] - lox;
-            sd.own_y0 = sy[ky] - loy; sd.own_y1 = ey[ky] - loy;
-            if (sd.W > 250 || sd.H > 250) return ACAC_E_ARG;   // 2 threads per cell of a level
-            sd.nlev = (sd.W - 1) + 2 * (sd.H - 1) + 1;
-            sd.lev_base = (int)h->lev.size();
-            sd.coef_base = coef;
-            sd.vec_base = vec;
-            int acc = 0;
-            for (int l = 0; l < sd.nlev; ++l) {
-                h->lev.push_back(acc);
-                int cnt = 0;
-                for (int j = 0; j < sd.H; ++j) {
-                    int i = l - 2 * j;
-                    if (i >= 0 && i < sd.W) ++cnt;
+    for (int kz = 0; kz < pz; ++kz) {
+        for (int ky = 0; ky < p.ras_parts[1]; ++ky) {
+            for (int kx = 0; kx < p.ras_parts[0]; ++kx) {
+                const int kk[3] = {kx, ky, kz};
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    const int s0 = st[a][kk[a]], e0 = en[a][kk[a]];
+                    if (a >= dim) { lo[a] = 0; hi[a] = 1; continue; }
+                    if (p.bc == ACAC_BC_PERIODIC) {
+                        lo[a] = s0 - d; hi[a] = e0 + d;
+                        if (hi[a] - lo[a] > p.n[a] - 2) return ACAC_E_ARG;   // box would wrap onto itself
+                    } else {
+                        lo[a] = std::max(0, s0 - d); hi[a] = std::min(p.n[a], e0 + d);
+                    }
                 }
-                maxcnt = std::max(maxcnt, cnt);
-                acc += cnt;
+                SubInfo sd;
+                memset(&sd, 0, sizeof(sd));
+                sd.ox = lo[0]; sd.oy = lo[1]; sd.oz = lo[2];
+                sd.W = hi[0] - lo[0]; sd.H = hi[1] - lo[1]; sd.D = hi[2] - lo[2];
+                sd.own_x0 = st[0][kx] - lo[0]; sd.own_x1 = en[0][kx] - lo[0];
+                sd.own_y0 = st[1][ky] - lo[1]; sd.own_y1 = en[1][ky] - lo[1];
+                sd.own_z0 = st[2][kz] - lo[2]; sd.own_z1 = en[2][kz] - lo[2];
+                // the stencil's offsets keep their natural order only in boxes of >= 4 cells
+                if (sd.W < 4 || sd.H < 4 || (dim == 3 && sd.D < 4)) return ACAC_E_ARG;
+                if (sd.W > 250 || sd.H > 250 || sd.D > 250) return ACAC_E_ARG;
+                sd.nlev = (sd.W - 1) + 2 * (sd.H - 1) + (dim == 3 ? 3 * (sd.D - 1) : 0) + 1;
+                sd.lev_base = (int)h->lev.size();
+                sd.coef_base = coef;
+                sd.vec_base = vec;
+                sd.cell_base = (long long)h->cells3.size();
+                int acc = 0;
+                if (dim == 2) {
+                    for (int l = 0; l < sd.nlev; ++l) {
+                        h->lev.push_back(acc);
+                        int cnt = 0;
+                        for (int j = 0; j < sd.H; ++j) {
+                            int i = l - 2 * j;
+                            if (i >= 0 && i < sd.W) ++cnt;
+                        }
+                        maxcnt = std::max(maxcnt, cnt);
+                        acc += cnt;
+                    }
+                } else {
+                    // level-ordered cell list and the position of every cell in its level
+                    const size_t ncell = (size_t)sd.W * sd.H * sd.D;
+                    const size_t base = h->cells3.size();
+                    h->cells3.resize(base + ncell);
+                    h->pos3.resize(base + ncell);
+                    for (int l = 0; l < sd.nlev; ++l) {
+                        h->lev.push_back(acc);
+                        int cnt = 0;
+                        for (int k = 0; k < sd.D; ++k)
+                            for (int j = 0; j < sd.H; ++j) {
+                                const int i = l - 2 * j - 3 * k;
+                                if (i < 0 || i >= sd.W) continue;
+                                h->cells3[base + acc + cnt] = i | (j << 10) | (k << 20);
+                                h->pos3[base + (size_t)(k * sd.H + j) * sd.W + i] = cnt;
+                                ++cnt;
+                            }
+                        maxcnt = std::max(maxcnt, cnt);
+                        acc += cnt;
+                    }
+                }
+                h->lev.push_back(acc);
+                coef += (long long)acc * (dim == 2 ? NCOEF : NCOEF3);
+                const size_t pad = dim == 2 ? (size_t)ras_pitch(sd.W) * (sd.H + 4)
+                                            : (size_t)(sd.W + 4) * (sd.H + 4) * (sd.D + 4);
+                vec += (long long)pad;
+                maxpad = std::max(maxpad, pad);
+                h->subs.push_back(sd);
             }
-            h->lev.push_back(acc);
-            coef += (long long)acc * NCOEF;
-            const size_t pad = (size_t)ras_pitch(sd.W) * (sd.H + 4);
-            vec += (long long)pad;
-            maxpad = std::max(maxpad, pad);
-            h->subs.push_back(sd);
         }
     }
     h->coef_count = coef;
@@ -461,8 +515,9 @@ int build_subdomains(acac_handle* h) {
     h->ras_maxlev = maxlev;
     h->ras_maxcnt = maxcnt;
     h->ras_maxpad = maxpad;
-    h->nbox = (double)(coef / NCOEF);
+    h->nbox = (double)(coef / (dim == 2 ? NCOEF : NCOEF3));
     h->ras_threads = std::max(64, ((2 * maxcnt + 31) / 32) * 32);
+    if (dim == 3) h->ras_threads = std::min(h->ras_threads, 512);
     if (h->ras_threads > 1024) h->ras_threads = 1024;
     h->ras_smem = maxpad * 2 * h->ksz;
     return ACAC_OK;
@@ -472,10 +527,12 @@ int build_subdomains(acac_handle* h) {
 
 int acac::validate_params(const acac_params* p) {
     if (!p) return ACAC_E_ARG;
-    if (p->dim != 2) return ACAC_E_ARG;
-    if (p->n[0] < 4 || p->n[1] < 4) return ACAC_E_ARG;
-    if ((long long)p->n[0] * p->n[1] > (1LL << 30)) return ACAC_E_ARG;
-    if (!(p->L[0] > 0 && p->L[1] > 0)) return ACAC_E_ARG;
+    if (p->dim != 2 && p->dim != 3) return ACAC_E_ARG;
+    if (p->n[0] < 4 || p->n[1] < 4 || (p->dim == 3 && p->n[2] < 4)) return ACAC_E_ARG;
+    if ((long long)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1) > (1LL << 30)) return ACAC_E_ARG;
+    if (!(p->L[0] > 0 && p->L[1] > 0 && (p->dim == 2 || p->L[2] > 0))) return ACAC_E_ARG;
+    if (p->dim == 3 && (p->ras_parts[2] < 1 || p->ras_parts[2] > p->n[2])) return ACAC_E_ARG;
+    if (p->dim == 3 && p->bc == ACAC_BC_PERIODIC && p->ras_parts[2] < 2) return ACAC_E_ARG;
     if (p->bc != ACAC_BC_PERIODIC && p->bc != ACAC_BC_NEUMANN) return ACAC_E_ARG;
     if (!(p->alpha > 0 && p->beta > 0 && p->theta > 0 && p->gamma > 0 && p->rho > 0)) return ACAC_E_ARG;
     if (p->taylor_S < 1 || p->taylor_S > MAX_S) return ACAC_E_ARG;
@@ -509,7 +566,7 @@ void dmalloc(P** ptr, size_t bytes) {
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
-                    h->subs_dev, h->lev_dev};
+                    h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->host) cudaFreeHost(h->host);
@@ -569,13 +626,18 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     h->stream = (cudaStream_t)cuda_stream;
     h->mixed = p->precision == ACAC_MIXED;
     h->ksz = h->mixed ? sizeof(float) : sizeof(double);
-    h->N = (size_t)p->n[0] * p->n[1];
+    h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
     Geom& g = h->g;
     g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)h->N; g.bc = p->bc;
+    g.dim = p->dim;
+    g.nz = p->dim == 3 ? p->n[2] : 1;
+    g.hz = p->dim == 3 ? p->L[2] / p->n[2] : 1.0;
+    g.ihz2 = p->dim == 3 ? 1.0 / (g.hz * g.hz) : 0.0;
+    g.ihz2f = (float)g.ihz2;
     g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
     g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
     g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
-    g.vol = g.hx * g.hy;
+    g.vol = g.hx * g.hy * (p->dim == 3 ? g.hz : 1.0);
     h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
     h->eta = p->eta0;
     st = build_subdomains(h);
@@ -594,15 +656,22 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         dmalloc(&h->w, n2 * ks); dmalloc(&h->z, n2 * ks); dmalloc(&h->kt, n2 * ks);
         dmalloc(&h->jtmp, 3 * N * ks);
         dmalloc(&h->cache, 7 * N * ks);
-        dmalloc(&h->J, (size_t)NSLOT * 4 * N * ks);
+        dmalloc(&h->J, (size_t)(p->dim == 3 ? NSLOT3 : NSLOT) * 4 * N * ks);
         dmalloc(&h->coef, (size_t)h->coef_count * ks);
         int dev = 0;
         CU(cudaGetDevice(&dev));
         int optin = 0;
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        if (p->dim == 3) {
+            // 3D apply: the padded box vector in shared memory when it fits, else global
+            if (h->ras_smem > (size_t)optin - 2048) {
+                size_t tot = 0;
+                for (auto& sd : h->subs) tot += (size_t)(sd.W + 4) * (sd.H + 4) * (sd.D + 4);
+                dmalloc(&h->gscratch, tot * 2 * ks);
+            }
+        } else {
         // shared-memory plan of the Schwarz apply: mbarriers | level table | coefficient
         // stages | box vector.  Prefer a plan with two CTAs per SM.
-        {
             auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
             RasLaunch& L = h->ras_launch;
             L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
@@ -642,6 +711,12 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         CU(cudaMallocHost((void**)&h->host_flags, 16));
         dmalloc(&h->subs_dev, h->subs.size() * sizeof(SubInfo));
         dmalloc(&h->lev_dev, h->lev.size() * sizeof(int));
+        dmalloc(&h->cells3_dev, std::max<size_t>(1, h->cells3.size()) * sizeof(int));
+        dmalloc(&h->pos3_dev, std::max<size_t>(1, h->pos3.size()) * sizeof(int));
+        if (!h->cells3.empty()) {
+            CU(cudaMemcpy(h->cells3_dev, h->cells3.data(), h->cells3.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CU(cudaMemcpy(h->pos3_dev, h->pos3.data(), h->pos3.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
         CU(cudaMemcpy(h->subs_dev, h->subs.data(), h->subs.size() * sizeof(SubInfo), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(h->lev_dev, h->lev.data(), h->lev.size() * sizeof(int), cudaMemcpyHostToDevice));
         CU(set_taylor_constants(p->taylor_S));
@@ -788,7 +863,7 @@ int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, cons
 int acac_ras_factor(acac_handle* h, const void* J) {
     if (!h || !J) return ACAC_E_ARG;
     try {
-        const size_t bytes = (size_t)NSLOT * 4 * h->N * h->ksz;
+        const size_t bytes = (size_t)(h->g.dim == 3 ? NSLOT3 : NSLOT) * 4 * h->N * h->ksz;
         if (J != h->J) CU(cudaMemcpyAsync(h->J, J, bytes, cudaMemcpyDeviceToDevice, h->stream));
         return h->mixed ? factor<float>(h) : factor<double>(h);
     } catch (Err e) {

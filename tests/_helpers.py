@@ -51,24 +51,32 @@ SLOTS = [(0, 0), (-1, 0), (1, 0), (0, -1), (0, 1), (-2, 0), (2, 0), (0, -2), (0,
          (-1, -1), (1, -1), (-1, 1), (1, 1)]
 
 
+SLOTS3 = [(0, 0, 0), (-1, 0, 0), (1, 0, 0), (0, -1, 0), (0, 1, 0), (0, 0, -1), (0, 0, 1),
+          (-2, 0, 0), (2, 0, 0), (0, -2, 0), (0, 2, 0), (0, 0, -2), (0, 0, 2),
+          (-1, -1, 0), (1, -1, 0), (-1, 1, 0), (1, 1, 0), (-1, 0, -1), (1, 0, -1), (-1, 0, 1), (1, 0, 1),
+          (0, -1, -1), (0, 1, -1), (0, -1, 1), (0, 1, 1)]
+
+
 def stencil_J_to_csr(J, p):
     """Stencil-diagonal storage J[(slot*4+e)*N + cell] -> CSR in interleaved order
     (e = 0: uu, 1: uv, 2: vu, 3: vv).  Slots leaving a Neumann domain are dropped."""
     import scipy.sparse as sp
     nx, ny = p.n[0], p.n[1]
-    N = nx * ny
-    J = np.asarray(J, dtype=np.float64).reshape(13, 4, N)
+    nz = p.n[2] if p.dim == 3 else 1
+    N = nx * ny * nz
+    slots = SLOTS3 if p.dim == 3 else [(a, b, 0) for a, b in SLOTS]
+    J = np.asarray(J, dtype=np.float64).reshape(len(slots), 4, N)
     cell = np.arange(N)
-    x, y = cell % nx, cell // nx
+    x, y, z = cell % nx, (cell // nx) % ny, cell // (nx * ny)
     rows, cols, vals = [], [], []
-    for s, (dx, dy) in enumerate(SLOTS):
-        xx, yy = x + dx, y + dy
+    for s, (dx, dy, dz) in enumerate(slots):
+        xx, yy, zz = x + dx, y + dy, z + dz
         if p.bc == 0:
             ok = np.ones(N, bool)
-            xx, yy = xx % nx, yy % ny
+            xx, yy, zz = xx % nx, yy % ny, zz % nz
         else:
-            ok = (xx >= 0) & (xx < nx) & (yy >= 0) & (yy < ny)
-        nb = yy * nx + xx
+            ok = (xx >= 0) & (xx < nx) & (yy >= 0) & (yy < ny) & (zz >= 0) & (zz < nz)
+        nb = (zz * ny + yy) * nx + xx
         for e in range(4):
             a, b = divmod(e, 2)
             rows.append(2 * cell[ok] + a)

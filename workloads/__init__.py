@@ -156,6 +156,18 @@ C3 = Workload(
            precision=PREC_MIXED, **_COEF),
     steps=50, seed=2, u_mean=0.4, amp=0.05)
 
+# 3D 128^3 homogeneous Neumann on the unit cube (the paper's 3D test, Sec. 4.1 B), FP64
+# residual with FP32 Krylov / Jacobian / ILU, RAS 8x8x8 overlap 1 (boxes truncated at the
+# walls), adaptive dt from 1e-4 in [1e-5, 1e-1], seed 3, initial state as the 2D runs.
+C4 = Workload(
+    "3d-128x128x128-neumann-mixed-adaptive",
+    Params(dim=3, n=(128, 128, 128), L=(1.0, 1.0, 1.0), bc=BC_NEUMANN, dt_mode=DT_ADAPTIVE, dt0=1e-4,
+           dt_min=1e-5, dt_max=1e-1, eta0=100.0, ras_parts=(8, 8, 8), ras_overlap=1,
+           precision=PREC_MIXED, **_COEF),
+    steps=50, seed=3, u_mean=0.4, amp=0.05)
+C4_FP64 = Workload("3d-128x128x128-neumann-fp64-adaptive", C4.params.replace(precision=PREC_FP64),
+                   steps=50, seed=3, u_mean=0.4, amp=0.05)
+
 # Unit-square variants of C2 and C3 (see the note above H64).
 C2_UNIT = Workload("2d-1024x1024-unit-square-periodic-fp64-adaptive",
                    C2.params.replace(L=(1.0, 1.0, 1.0)), steps=100, seed=1, u_mean=0.4, amp=0.05)
@@ -166,4 +178,4 @@ C3_UNIT = Workload("2d-2048x2048-unit-square-periodic-mixed-adaptive",
 C3_FP64 = Workload("2d-2048x2048-periodic-fp64-adaptive", C3.params.replace(precision=PREC_FP64),
                    steps=50, seed=2, u_mean=0.4, amp=0.05)
 
-WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C2_UNIT, C3_UNIT)}
+WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C4, C4_FP64, C2_UNIT, C3_UNIT)}
