@@ -288,6 +288,9 @@ cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> ca
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
 template <typename T>
+cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
+                            cudaStream_t s);
+template <typename T>
 cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp,
                          cudaStream_t s);
 template <typename T>

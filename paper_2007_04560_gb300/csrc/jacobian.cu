@@ -197,6 +197,86 @@ cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache
     return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------- fused tiled product (2D)
+// y = J(X1) w in one pass over a JT_X x JT_Y tile of output cells: w is staged with a
+// 2-cell halo and c, G_u with a 1-cell halo in shared memory; dG_u and dc are formed on
+// the 1-cell ring, dG_v on the tile; then the face fluxes.  Block coordinates give (x, y)
+// without division; neighbours outside the grid are wrapped (periodic) or clamped
+// (Neumann: their face weight is 0).  Algorithmic traffic: w (2), the cache (7) and y (2)
+// per cell.
+constexpr int JT_X = 64, JT_Y = 8, JT_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, Coef k, double dt, Cache<T> C,
+                                                              const T* __restrict__ w, T* __restrict__ y) {
+    constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
+    constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1
+    __shared__ T swu[WY][WX], swv[WY][WX];
+    __shared__ T sc[RY][RX], sg[RY][RX], sdg[RY][RX], sdc[RY][RX];
+    __shared__ T sdgv[JT_Y][JT_X];
+    const int N = g.N;
+    const int x0 = blockIdx.x * JT_X, y0 = blockIdx.y * JT_Y;
+    const bool per = g.bc == ACAC_BC_PERIODIC;
+    for (int idx = threadIdx.x; idx < WX * WY; idx += JT_THREADS) {
+        const int lx = idx % WX, ly = idx / WX;
+        const int gx = wrap_or_clamp(x0 + lx - 2, g.nx, per), gy = wrap_or_clamp(y0 + ly - 2, g.ny, per);
+        const int gc = gy * g.nx + gx;
+        swu[ly][lx] = w[gc];
+        swv[ly][lx] = w[N + gc];
+    }
+    __syncthreads();
+    const T hg = (T)(0.5 * k.gamma);
+    const T ihx2 = sizeof(T) == 8 ? (T)g.ihx2 : (T)g.ihx2f, ihy2 = sizeof(T) == 8 ? (T)g.ihy2 : (T)g.ihy2f;
+    const T dvs = (T)(0.5 * (k.alpha - k.beta));
+    for (int idx = threadIdx.x; idx < RX * RY; idx += JT_THREADS) {
+        const int lx = idx % RX, ly = idx / RX;
+        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
+        const int cx = wrap_or_clamp(gx, g.nx, per), cy = wrap_or_clamp(gy, g.ny, per);
+        const int gc = cy * g.nx + cx;
+        const int wx = lx + 1, wy = ly + 1;             // position in the w tile
+        const T wu = swu[wy][wx], wv = swv[wy][wx];
+        // Laplacians with the ghost rule (clamped neighbours give zero differences)
+        const T lu = (swu[wy][wx - 1] + swu[wy][wx + 1] - (T)2 * wu) * ihx2 + (swu[wy - 1][wx] + swu[wy + 1][wx] - (T)2 * wu) * ihy2;
+        const T du = C.du[gc], xc = C.xc[gc];
+        sc[ly][lx] = C.c[gc];
+        sg[ly][lx] = C.Gu[gc];
+        sdg[ly][lx] = du * wu + xc * wv - hg * lu;
+        sdc[ly][lx] = C.cu[gc] * wu + C.cv[gc] * wv;
+        if (lx >= 1 && lx <= JT_X && ly >= 1 && ly <= JT_Y) {
+            const T lv = (swv[wy][wx - 1] + swv[wy][wx + 1] - (T)2 * wv) * ihx2 + (swv[wy - 1][wx] + swv[wy + 1][wx] - (T)2 * wv) * ihy2;
+            sdgv[ly - 1][lx - 1] = xc * wu + (du + dvs) * wv - hg * lv;
+        }
+    }
+    __syncthreads();
+    const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho), half = (T)0.5;
+    for (int idx = threadIdx.x; idx < JT_X * JT_Y; idx += JT_THREADS) {
+        const int tx = idx % JT_X, ty = idx / JT_X;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= g.nx || gy >= g.ny) continue;
+        const int rx = tx + 1, ry = ty + 1;
+        const T cc = sc[ry][rx], gc_ = sg[ry][rx], dgc = sdg[ry][rx], dcc = sdc[ry][rx];
+        T div = (T)0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const int nx_ = rx + face_dx(f), ny_ = ry + face_dy(f);
+            const T wf = face_w<T>(g, gx, gy, f);
+            div += wf * (half * (dcc + sdc[ny_][nx_]) * (sg[ny_][nx_] - gc_) + half * (cc + sc[ny_][nx_]) * (sdg[ny_][nx_] - dgc));
+        }
+        const int c = gy * g.nx + gx;
+        y[c] = swu[ty + 2][tx + 2] * idt - div;
+        y[N + c] = swv[ty + 2][tx + 2] * idt + (dcc * C.Gv[c] + cc * sdgv[ty][tx]) * irho;
+    }
+}
+
+template <typename T>
+cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
+                            cudaStream_t s) {
+    dim3 grid((g.nx + JT_X - 1) / JT_X, (g.ny + JT_Y - 1) / JT_Y);
+    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, k, dt, cache, w, y);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                   \
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
                                             cudaStream_t);                                        \
@@ -204,7 +284,9 @@ cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache
     template cudaError_t launch_jvp_g<T>(const Geom&, const Coef&, Cache<T>, const T*, T*,         \
                                          cudaStream_t);                                           \
     template cudaError_t launch_jvp_f<T>(const Geom&, const Coef&, double, Cache<T>, const T*,     \
-                                         const T*, T*, cudaStream_t);
+                                         const T*, T*, cudaStream_t);                               \
+    template cudaError_t launch_jvp_tile<T>(const Geom&, const Coef&, double, Cache<T>, const T*, T*, \
+                                            cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

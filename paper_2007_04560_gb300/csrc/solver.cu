@@ -177,6 +177,13 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
 
 template <typename T>
 void jvp_action(acac_handle* h, double dt, const T* w, T* y) {
+    if (h->g.dim == 2 && sizeof(T) == 4) {
+        // FP32: one tiled pass (HBM bound); FP64 keeps the two passes (FP64-pipe bound,
+        // no halo recomputation)
+        KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 11, 80.0 * h->N,
+            launch_jvp_tile<T>(h->g, h->k, dt, cache_of<T>(h), w, y, h->stream));
+        return;
+    }
     KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N, launch_jvp_g<T>(h->g, h->k, cache_of<T>(h), w, (T*)h->jtmp, h->stream));
     KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N, launch_jvp_f<T>(h->g, h->k, dt, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream));
 }

@@ -122,6 +122,26 @@ def test_jacobian_spmv_jvp(P, bc, grid):
     assert _rel(host(y2), yo) <= 1e-12
 
 
+@pytest.mark.parametrize("bc", [BC_PERIODIC, BC_NEUMANN])
+@pytest.mark.parametrize("grid", GRIDS + [((130, 17, 1), (4, 2, 1))])
+def test_jvp_fp32(P, bc, grid):
+    """Mixed form: the fused tiled FP32 Jacobian action against the FP64 oracle J w.
+    FP32 arithmetic on O(1) inputs: 1e-5 of max |J w|."""
+    import torch
+    n, parts = grid
+    p = Params(n=n, bc=bc, ras_parts=parts, precision=PREC_MIXED)
+    X1, X0 = perturbed_pair(p, 29, u_mean=0.45, amp=0.05, step_amp=2e-3)
+    dt = 2e-3
+    Jo = O.jacobian(p, X1, X0, dt)
+    w = soa(*random_vector(p, 31))
+    yo = interleaved_to_soa(Jo @ soa_to_interleaved(w))
+    with P.Solver(p) as s:
+        y = torch.empty(2 * p.ncells, dtype=torch.float32, device="cuda")
+        s.jvp(dev(soa(*X1)), dev(soa(*X0)), dt, dev(w, torch.float32), y)
+        torch.cuda.synchronize()
+    assert _rel(host(y), yo) <= 1e-5
+
+
 @pytest.mark.parametrize("ras_type", [0, 1, 2])
 @pytest.mark.parametrize("bc", [BC_PERIODIC, BC_NEUMANN])
 @pytest.mark.parametrize("grid", GRIDS)
