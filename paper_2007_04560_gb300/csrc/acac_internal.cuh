@@ -217,6 +217,19 @@ struct Cache {
     T* c; T* cu; T* cv; T* Gu; T* Gv; T* du; T* xc;
 };
 
+// Scalars of the Jacobian in precision T, formed once on the host: a double division
+// or conversion per thread runs on the FP64 pipe, which on sm_103 issues at 1/64 of
+// the FP32 rate and would dominate the FP32 kernels.  The values are the correctly
+// rounded ones a kernel would form.
+template <typename T>
+struct JacK {
+    T idt, irho, hg, dvs;   // 1/dt, 1/rho, gamma/2, (alpha - beta)/2
+};
+template <typename T>
+inline JacK<T> jac_consts(const Coef& k, double dt) {
+    return JacK<T>{(T)(1.0 / dt), (T)(1.0 / k.rho), (T)(0.5 * k.gamma), (T)(0.5 * (k.alpha - k.beta))};
+}
+
 // One subdomain of the Schwarz decomposition (Sec. 3.1).
 struct SubInfo {
     int ox, oy;          // global coordinates of the box corner (may be < 0 when periodic)

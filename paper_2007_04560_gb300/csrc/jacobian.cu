@@ -19,7 +19,7 @@ static int grid1(long long n, int threads) {
 
 // ---------------------------------------------------------------- assembly
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt, Cache<T> C, T* __restrict__ J) {
+__global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<T> C, T* __restrict__ J) {
     constexpr int NS = nslot<DIM>();
     constexpr int NF = 2 * DIM;
     const int N = g.N;
@@ -28,8 +28,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
     int x, y, z;
     decode_cell<DIM>(g, c, x, y, z);
     // arithmetic in the Jacobian's precision T
-    const T hg = (T)(0.5 * k.gamma);
-    const T dvshift = (T)(0.5 * (k.alpha - k.beta));
+    const T hg = k.hg, dvshift = k.dvs;
     const T half = (T)0.5;
     T Juu[NS], Juv[NS];
 #pragma unroll
@@ -43,7 +42,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
         eih2c[f] = face_weight<DIM, T>(g, x, y, z, f);
         lapc += eih2c[f];
     }
-    Juu[0] = (T)(1.0 / dt);
+    Juu[0] = k.idt;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const int fx = fc_dx<DIM>(f), fy = fc_dy<DIM>(f), fz = fc_dz<DIM>(f);
@@ -77,13 +76,13 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
         }
         Juu[0] += w * ct * hg * lapc;
     }
-    const T irho = (T)(1.0 / k.rho);
+    const T irho = k.irho;
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         T jvu = (T)0, jvv = (T)0;
         if (s == 0) {
             jvu = (cuc * gvc + cc * xcc) * irho;
-            jvv = (T)(1.0 / dt) + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
+            jvv = k.idt + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
         } else if (s <= NF) {
             const int f = s - 1;   // slots 1..2*DIM are the faces
             jvv = -cc * hg * eih2c[f] * irho;
@@ -98,8 +97,9 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, Coef k, double dt
 template <typename T>
 cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J,
                             cudaStream_t s) {
-    if (g.dim == 3) assemble_kernel<T, 3><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
-    else assemble_kernel<T, 2><<<grid1(g.N, 128), 128, 0, s>>>(g, k, dt, cache, J);
+    const JacK<T> kk = jac_consts<T>(k, dt);
+    if (g.dim == 3) assemble_kernel<T, 3><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J);
+    else assemble_kernel<T, 2><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J);
     return cudaGetLastError();
 }
 
@@ -134,7 +134,7 @@ cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_
 // ---------------------------------------------------------------- matrix-free product
 // Pass 1: dG_u, dG_v, dc per cell into tmp = [dGu | dGv | dc].
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, const T* __restrict__ w,
+__global__ void __launch_bounds__(256) jvp1_kernel(Geom g, JacK<T> k, Cache<T> C, const T* __restrict__ w,
                                                    T* __restrict__ tmp) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -150,15 +150,15 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, Coef k, Cache<T> C, c
         lu += (w[n] - wu) * ih2;
         lv += (w[N + n] - wv) * ih2;
     }
-    const T hg = (T)(0.5 * k.gamma);
-    const T du = C.du[c], xc = C.xc[c], dv = du + (T)(0.5 * (k.alpha - k.beta));
+    const T hg = k.hg;
+    const T du = C.du[c], xc = C.xc[c], dv = du + k.dvs;
     tmp[c] = du * wu + xc * wv - hg * lu;
     tmp[N + c] = xc * wu + dv * wv - hg * lv;
     tmp[2 * N + c] = C.cu[c] * wu + C.cv[c] * wv;
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Cache<T> C,
+__global__ void __launch_bounds__(256) jvp2_kernel(Geom g, JacK<T> k, Cache<T> C,
                                                    const T* __restrict__ w, const T* __restrict__ tmp,
                                                    T* __restrict__ y) {
     const int N = g.N;
@@ -177,23 +177,25 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, Coef k, double dt, Ca
         const T w_ = face_weight<DIM, T>(g, x, yy, zz, f);
         div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
     }
-    const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho);
+    const T idt = k.idt, irho = k.irho;
     y[c] = w[c] * idt - div;
     y[N + c] = w[N + c] * idt + (dcc * C.Gv[c] + cc * dGv[c]) * irho;
 }
 
 template <typename T>
 cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
-    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
-    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, k, cache, w, tmp);
+    const JacK<T> kk = jac_consts<T>(k, 1.0);
+    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp);
+    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, const T* tmp,
                          T* y, cudaStream_t s) {
-    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
-    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, k, dt, cache, w, tmp, y);
+    const JacK<T> kk = jac_consts<T>(k, dt);
+    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp, y);
+    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp, y);
     return cudaGetLastError();
 }
 
@@ -208,7 +210,7 @@ cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache
 constexpr int JT_X = 64, JT_Y = 8, JT_THREADS = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, Coef k, double dt, Cache<T> C,
+__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, JacK<T> k, Cache<T> C,
                                                               const T* __restrict__ w, T* __restrict__ y) {
     constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
     constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1
@@ -226,9 +228,8 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, Coef k, do
         swv[ly][lx] = w[N + gc];
     }
     __syncthreads();
-    const T hg = (T)(0.5 * k.gamma);
+    const T hg = k.hg, dvs = k.dvs;
     const T ihx2 = sizeof(T) == 8 ? (T)g.ihx2 : (T)g.ihx2f, ihy2 = sizeof(T) == 8 ? (T)g.ihy2 : (T)g.ihy2f;
-    const T dvs = (T)(0.5 * (k.alpha - k.beta));
     for (int idx = threadIdx.x; idx < RX * RY; idx += JT_THREADS) {
         const int lx = idx % RX, ly = idx / RX;
         const int gx = x0 + lx - 1, gy = y0 + ly - 1;
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, Coef k, do
         }
     }
     __syncthreads();
-    const T idt = (T)(1.0 / dt), irho = (T)(1.0 / k.rho), half = (T)0.5;
+    const T idt = k.idt, irho = k.irho, half = (T)0.5;
     for (int idx = threadIdx.x; idx < JT_X * JT_Y; idx += JT_THREADS) {
         const int tx = idx % JT_X, ty = idx / JT_X;
         const int gx = x0 + tx, gy = y0 + ty;
@@ -273,7 +274,7 @@ template <typename T>
 cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
                             cudaStream_t s) {
     dim3 grid((g.nx + JT_X - 1) / JT_X, (g.ny + JT_Y - 1) / JT_Y);
-    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, k, dt, cache, w, y);
+    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, jac_consts<T>(k, dt), cache, w, y);
     return cudaGetLastError();
 }
 

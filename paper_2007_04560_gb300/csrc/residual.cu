@@ -250,14 +250,13 @@ __global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
 
 // ---------------------------------------------------------------- pass B
 template <int DIM>
-__global__ void __launch_bounds__(256) f_kernel(Geom g, Coef k, ResidualArgs a) {
+__global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho, ResidualArgs a) {
     __shared__ double sh[32];
     const int N = g.N;
     const double* __restrict__ X1 = a.X;
     const double* __restrict__ Gu = a.G;
     const double* __restrict__ Gv = a.G + N;
     const double* __restrict__ cm = a.G + 2 * N;
-    const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
     double acc = 0.0;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int x, y, z;
@@ -298,8 +297,10 @@ cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
-    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
-    else f_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, k, a);
+    // 1/dt and 1/rho on the host (correctly rounded, as a kernel division would be)
+    const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
+    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, idt, irho, a);
+    else f_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, idt, irho, a);
     return cudaGetLastError();
 }
 
