@@ -59,6 +59,7 @@ extern "C" {
                                      Newton update, energy, mass, dt estimator in double   */
 #define ACAC_JAC_MATFREE     0    /* GMRES products by the analytic Jacobian action      */
 #define ACAC_JAC_ASSEMBLED   1    /* GMRES products by the assembled stencil matrix      */
+#define ACAC_MAX_BATCH       1024 /* largest ensemble (params.batch)                      */
 
 /* Problem and solver settings.  Defaults: acac_default_params(). */
 typedef struct acac_params {
@@ -82,8 +83,13 @@ typedef struct acac_params {
                                    and reuse within the step (Sec. 4.2)                  */
     int    precision;           /* ACAC_FP64 | ACAC_MIXED                                */
     int    jac_mode;            /* ACAC_JAC_*                                            */
-    int    batch;               /* ensemble size; this build supports 1                  */
+    int    batch;               /* ensemble size B, 1..ACAC_MAX_BATCH: B independent
+                                   problems of this size and these settings, each with
+                                   its own coefficients (acac_set_coeffs), time step,
+                                   eta and history                                       */
     int    cgs_refine;          /* 1: Gram–Schmidt applied twice (CGS2), 0: once         */
+    int    graphs;              /* 1: replay each GMRES iteration from a captured CUDA
+                                   graph (same kernels and results as 0: direct launches) */
 } acac_params;
 
 /* Per-step report. */
@@ -116,23 +122,42 @@ void acac_default_params(acac_params *p);
  * cudaStream_t (NULL = legacy default stream).  *out receives the handle.
  * Errors: ACAC_E_ARG (sizes < 4, non-positive coefficient, periodic box that
  * would wrap onto itself, subdomain box under 4 or over 250 cells in some
- * direction, dim not 2 or 3, batch != 1), ACAC_E_NOMEM, ACAC_E_CUDA. */
+ * direction, dim not 2 or 3, batch outside 1..ACAC_MAX_BATCH), ACAC_E_NOMEM,
+ * ACAC_E_CUDA.
+ * Ensembles (batch B > 1): the handle holds B member solvers, each with its own
+ * workspace and its own CUDA stream (ordered after cuda_stream at the start of each
+ * call and before it at the end), and a pool of host threads that drives the
+ * members' solves concurrently so that their kernels share the GPU.  Every member
+ * starts with the coefficients of *p. */
 int acac_create(const acac_params *p, void *cuda_stream, acac_handle **out);
+
+/* Coefficients alpha, beta, theta, gamma, rho (all > 0, Eq. 2 and Eq. 1) of ensemble
+ * member `member` (0..batch-1; 0 for a batch-1 handle) from the next step on.  The
+ * member's time-step history is kept.  ACAC_E_ARG on a bad member or value. */
+int acac_set_coeffs(acac_handle *h, int member, double alpha, double beta, double theta,
+                    double gamma, double rho);
 
 /* One accepted time step, in place: u, v (device, N doubles each) hold U^n on
  * entry and U^{n+1} on return.  The handle keeps U^{n-1}, dt_{n-1}, eta and t for
  * the predictor of Eq. sencondt.  Synchronises the stream.  *info (host, may be
  * NULL) receives the report.  Errors: ACAC_E_DOMAIN, ACAC_E_DIVERGED (fixed dt),
- * ACAC_E_DT_UNDERFLOW (adaptive), ACAC_E_CUDA; fields unchanged on error. */
+ * ACAC_E_DT_UNDERFLOW (adaptive), ACAC_E_CUDA; fields unchanged on error.
+ * Ensembles: u and v hold the B members' fields one after another (B*N doubles
+ * each, member-major), info is an array of B reports (or NULL), and every member
+ * takes one accepted step with its own dt.  Returns ACAC_OK when every member
+ * succeeded, else the status of the first member that failed (each report carries
+ * its member's status; a failed member's fields are unchanged). */
 int acac_step(acac_handle *h, double *u, double *v, acac_step_info *info);
 
 /* acac_step on HOST arrays: copies u_host, v_host to the device, steps, copies
- * the result back.  Host arrays may be pageable or pinned. */
+ * the result back.  Host arrays may be pageable or pinned (B*N doubles each for an
+ * ensemble). */
 int acac_step_host(acac_handle *h, double *u_host, double *v_host, acac_step_info *info);
 
 /* Discrete free energy E~ = <e~> (Eqs. relations, freeenergy, exact Phi with
  * 0 ln 0 = 0) and mass sum u dx dy of the state (u, v) (device).  Host outputs;
- * synchronises.  ACAC_E_DOMAIN if some u+v or u-v lies outside [0,1]. */
+ * synchronises.  ACAC_E_DOMAIN if some u+v or u-v lies outside [0,1].
+ * Ensembles: u, v member-major as in acac_step; energy and mass are arrays of B. */
 int acac_energy(acac_handle *h, const double *u, const double *v, double *energy,
                 double *mass);
 
@@ -143,6 +168,7 @@ void acac_destroy(acac_handle *h);
 const char *acac_status_string(int status);
 
 /* ---- component entry points (the pieces acac_step is made of) ---------------- */
+/* These act on one problem: they return ACAC_E_ARG on an ensemble handle. */
 
 /* F(X1) of scheme (NSOA-1) with X0 = U^n and time step dt (Sec. 2, Eqs. dvds-2,
  * D2-1, dvds-1, NSOA-1):  F_u = (u1-u0)/dt - [div c~ grad G_u],

@@ -45,6 +45,7 @@ class acac_params(ctypes.Structure):
         ("gmres_maxit", ctypes.c_int), ("ras_parts", ctypes.c_int * 3), ("ras_overlap", ctypes.c_int),
         ("ras_type", ctypes.c_int), ("ilu_reuse", ctypes.c_int), ("precision", ctypes.c_int),
         ("jac_mode", ctypes.c_int), ("batch", ctypes.c_int), ("cgs_refine", ctypes.c_int),
+        ("graphs", ctypes.c_int),
     ]
 
 
@@ -87,6 +88,7 @@ SIGNATURES = {
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
+    "acac_set_coeffs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
 }
 
 NKERNEL = 14
@@ -196,11 +198,16 @@ def acac_log(x, y, stream=None):
 
 
 class Solver:
-    """Owns one acac handle.  Method names follow the C ABI without the prefix."""
+    """Owns one acac handle.  Method names follow the C ABI without the prefix.
+
+    With params.batch = B > 1 the handle is an ensemble: step / step_host / energy
+    take the B members' fields one after another (B*N values per field) and return
+    one report (or energy, mass) per member."""
 
     def __init__(self, params, stream=None):
         import torch
         self.params = params
+        self.B = int(getattr(params, "batch", 1))
         self.N = int(params.n[0]) * int(params.n[1]) * (int(params.n[2]) if params.dim == 3 else 1)
         self.kdtype = torch.float32 if params.precision == 1 else torch.float64
         self.nslot = 13 if params.dim == 2 else 25
@@ -224,39 +231,53 @@ class Solver:
         self.close()
 
     # -- time stepping
+    def _infos(self):
+        return (acac_step_info * self.B)()
+
+    def _out(self, infos):
+        return infos[0] if self.B == 1 else list(infos)
+
     def step(self, u, v, check=True):
+        """One accepted step in place; returns the report (a list of B for an ensemble)."""
         import torch
-        info = acac_step_info()
-        st = _lib().acac_step(self.h, _dev(u, torch.float64, self.N, "u"), _dev(v, torch.float64, self.N, "v"),
-                              ctypes.byref(info))
+        infos = self._infos()
+        nb = self.B * self.N
+        st = _lib().acac_step(self.h, _dev(u, torch.float64, nb, "u"), _dev(v, torch.float64, nb, "v"), infos)
         if check:
             _check(st, "acac_step")
-        return info
+        return self._out(infos)
+
+    def set_coeffs(self, member, alpha, beta, theta, gamma, rho):
+        _check(_lib().acac_set_coeffs(self.h, int(member), float(alpha), float(beta), float(theta), float(gamma),
+                                      float(rho)), "acac_set_coeffs")
 
     def step_host(self, u, v, check=True):
         """u, v: host (CPU) float64 contiguous tensors or numpy arrays, updated in place."""
         import numpy as np
         import torch
         ptrs = []
+        nb = self.B * self.N
         for a in (u, v):
             if isinstance(a, np.ndarray):
-                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == self.N
+                assert a.dtype == np.float64 and a.flags.c_contiguous and a.size == nb
                 ptrs.append(ctypes.c_void_p(a.ctypes.data))
             else:
-                assert a.device.type == "cpu" and a.dtype == torch.float64 and a.is_contiguous()
+                assert a.device.type == "cpu" and a.dtype == torch.float64 and a.is_contiguous() and a.numel() == nb
                 ptrs.append(ctypes.c_void_p(a.data_ptr()))
-        info = acac_step_info()
-        st = _lib().acac_step_host(self.h, ptrs[0], ptrs[1], ctypes.byref(info))
+        infos = self._infos()
+        st = _lib().acac_step_host(self.h, ptrs[0], ptrs[1], infos)
         if check:
             _check(st, "acac_step_host")
-        return info
+        return self._out(infos)
 
     def energy(self, u, v):
+        """(energy, mass) of the state; lists of B values for an ensemble."""
         import torch
-        e, m = ctypes.c_double(), ctypes.c_double()
-        _check(_lib().acac_energy(self.h, _dev(u, torch.float64, self.N, "u"), _dev(v, torch.float64, self.N, "v"),
-                                  ctypes.byref(e), ctypes.byref(m)), "acac_energy")
-        return e.value, m.value
+        e, m = (ctypes.c_double * self.B)(), (ctypes.c_double * self.B)()
+        nb = self.B * self.N
+        _check(_lib().acac_energy(self.h, _dev(u, torch.float64, nb, "u"), _dev(v, torch.float64, nb, "v"),
+                                  e, m), "acac_energy")
+        return (e[0], m[0]) if self.B == 1 else (list(e), list(m))
 
     # -- components
     def residual(self, X1, X0, dt, F):

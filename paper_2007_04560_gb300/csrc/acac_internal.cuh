@@ -270,6 +270,53 @@ template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
                               T* gscratch, cudaStream_t s);
+// Deterministic two-stage reductions.  A reducing kernel runs at most RED_BLOCKS
+// blocks of RED_THREADS threads; each block writes one partial sum per reduced
+// quantity v to partial[v * RED_BLOCKS + block], and the block that finishes last
+// adds the partials of each quantity in a fixed order (so the result does not
+// depend on which block finishes when) and writes out[v].  The counter is zero
+// between launches (the last block re-arms it); kernels that share one counter must
+// not overlap in time (they are issued on one stream).
+struct Red {
+    double* partial;
+    double* out;
+    unsigned* counter;
+};
+
+// Sum of v over the block (blockDim.x a multiple of 32), valid in thread 0.  sh: 32 doubles.
+__device__ __forceinline__ double block_sum_red(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (warp == 0) {
+        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    }
+    return t;
+}
+
+// Called by every thread of every block after the block's partials are written.
+__device__ __forceinline__ void finish_reduction(const Red& r, int nv, double* sh) {
+    __shared__ int s_last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) s_last = atomicAdd(r.counter, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int v = 0; v < nv; ++v) {
+        double acc = 0.0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
+            acc += __ldcg(r.partial + (size_t)v * RED_BLOCKS + i);
+        const double t = block_sum_red(acc, sh);
+        if (threadIdx.x == 0) r.out[v] = t;
+    }
+    if (threadIdx.x == 0) *r.counter = 0u;
+}
+
 // residual.cu
 cudaError_t set_taylor_constants(int S);
 struct ResidualArgs {
@@ -281,15 +328,15 @@ struct ResidualArgs {
     double* Xt;          // trial state written by trial_kernel
     double* G;           // [Gu | Gv | c], 3N
     double* F;           // residual
-    double* partial;     // RED_BLOCKS partial sums of F^2
+    Red red;             // ||F||^2 (one quantity)
     int* flags;          // bit 0: midpoint inadmissible, bit 1: trial state inadmissible
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);
-cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
-                          int* flags, cudaStream_t s);
+// energy and mass: two quantities
+cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s);
 template <typename T>
 cudaError_t launch_linearize(const Geom& g, const Coef& k, const double* X, const double* X0,
                              const double* G, Cache<T> cache, cudaStream_t s);
@@ -300,27 +347,29 @@ cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> ca
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
+// The matrix-free products read their scalars (JacK) from device memory, written by
+// launch_set_jac whenever dt or the coefficients change, so that a captured CUDA
+// graph of a GMRES iteration stays valid across time steps.
 template <typename T>
-cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
-                            cudaStream_t s);
+cudaError_t launch_set_jac(JacK<T>* dst, const Coef& k, double dt, cudaStream_t s);
 template <typename T>
-cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp,
+cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_jvp_g(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* tmp,
                          cudaStream_t s);
 template <typename T>
-cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w,
-                         const T* tmp, T* y, cudaStream_t s);
+cudaError_t launch_jvp_f(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, const T* tmp, T* y,
+                         cudaStream_t s);
 
 // krylov.cu
-cudaError_t launch_reduce_partials(const double* partial, int nvec, int nparts, double* out,
-                                   cudaStream_t s);
-cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n,
-                            double* partial, cudaStream_t s);
+cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
+                            cudaStream_t s);
 template <typename T>
-cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n,
-                             double* partial, cudaStream_t s);
+cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
+                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w,
-                              long long n, int want_dots, double* partial, cudaStream_t s);
+                              long long n, int want_norm, Red red, cudaStream_t s);
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
                               cudaStream_t s);
@@ -332,9 +381,10 @@ cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T*
 template <typename T>
 cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s);
 template <typename T>
-cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n,
-                                    double* partial, cudaStream_t s);
-cudaError_t launch_norm2_double(const double* x, long long n, double* partial, cudaStream_t s);
+cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
+                                    cudaStream_t s);
+// ||a - b||^2 (b may be NULL)
+cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s);
 
 // ras.cu
 template <typename T>

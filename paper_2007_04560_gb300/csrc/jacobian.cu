@@ -134,8 +134,8 @@ cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_
 // ---------------------------------------------------------------- matrix-free product
 // Pass 1: dG_u, dG_v, dc per cell into tmp = [dGu | dGv | dc].
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) jvp1_kernel(Geom g, JacK<T> k, Cache<T> C, const T* __restrict__ w,
-                                                   T* __restrict__ tmp) {
+__global__ void __launch_bounds__(256) jvp1_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
+                                                   const T* __restrict__ w, T* __restrict__ tmp) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
@@ -150,6 +150,7 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, JacK<T> k, Cache<T> C
         lu += (w[n] - wu) * ih2;
         lv += (w[N + n] - wv) * ih2;
     }
+    const JacK<T> k = *kp;
     const T hg = k.hg;
     const T du = C.du[c], xc = C.xc[c], dv = du + k.dvs;
     tmp[c] = du * wu + xc * wv - hg * lu;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, JacK<T> k, Cache<T> C
 }
 
 template <typename T, int DIM>
-__global__ void __launch_bounds__(256) jvp2_kernel(Geom g, JacK<T> k, Cache<T> C,
+__global__ void __launch_bounds__(256) jvp2_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
                                                    const T* __restrict__ w, const T* __restrict__ tmp,
                                                    T* __restrict__ y) {
     const int N = g.N;
@@ -177,25 +178,34 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, JacK<T> k, Cache<T> C
         const T w_ = face_weight<DIM, T>(g, x, yy, zz, f);
         div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
     }
-    const T idt = k.idt, irho = k.irho;
+    const T idt = kp->idt, irho = kp->irho;
     y[c] = w[c] * idt - div;
     y[N + c] = w[N + c] * idt + (dcc * C.Gv[c] + cc * dGv[c]) * irho;
 }
 
 template <typename T>
-cudaError_t launch_jvp_g(const Geom& g, const Coef& k, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
-    const JacK<T> kk = jac_consts<T>(k, 1.0);
-    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp);
-    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp);
+cudaError_t launch_jvp_g(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
+    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp);
+    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp);
     return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, const T* tmp,
-                         T* y, cudaStream_t s) {
-    const JacK<T> kk = jac_consts<T>(k, dt);
-    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp, y);
-    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kk, cache, w, tmp, y);
+cudaError_t launch_jvp_f(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, const T* tmp, T* y,
+                         cudaStream_t s) {
+    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp, y);
+    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp, y);
+    return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void set_jac_kernel(JacK<T>* dst, JacK<T> v) {
+    *dst = v;
+}
+
+template <typename T>
+cudaError_t launch_set_jac(JacK<T>* dst, const Coef& k, double dt, cudaStream_t s) {
+    set_jac_kernel<T><<<1, 1, 0, s>>>(dst, jac_consts<T>(k, dt));
     return cudaGetLastError();
 }
 
@@ -210,7 +220,7 @@ cudaError_t launch_jvp_f(const Geom& g, const Coef& k, double dt, Cache<T> cache
 constexpr int JT_X = 64, JT_Y = 8, JT_THREADS = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, JacK<T> k, Cache<T> C,
+__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
                                                               const T* __restrict__ w, T* __restrict__ y) {
     constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
     constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1
@@ -228,6 +238,7 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, JacK<T> k,
         swv[ly][lx] = w[N + gc];
     }
     __syncthreads();
+    const JacK<T> k = *kp;
     const T hg = k.hg, dvs = k.dvs;
     const T ihx2 = sizeof(T) == 8 ? (T)g.ihx2 : (T)g.ihx2f, ihy2 = sizeof(T) == 8 ? (T)g.ihy2 : (T)g.ihy2f;
     for (int idx = threadIdx.x; idx < RX * RY; idx += JT_THREADS) {
@@ -271,10 +282,9 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, JacK<T> k,
 }
 
 template <typename T>
-cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> cache, const T* w, T* y,
-                            cudaStream_t s) {
+cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s) {
     dim3 grid((g.nx + JT_X - 1) / JT_X, (g.ny + JT_Y - 1) / JT_Y);
-    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, jac_consts<T>(k, dt), cache, w, y);
+    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, kp, cache, w, y);
     return cudaGetLastError();
 }
 
@@ -282,12 +292,13 @@ cudaError_t launch_jvp_tile(const Geom& g, const Coef& k, double dt, Cache<T> ca
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
                                             cudaStream_t);                                        \
     template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
-    template cudaError_t launch_jvp_g<T>(const Geom&, const Coef&, Cache<T>, const T*, T*,         \
+    template cudaError_t launch_jvp_g<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,      \
                                          cudaStream_t);                                           \
-    template cudaError_t launch_jvp_f<T>(const Geom&, const Coef&, double, Cache<T>, const T*,     \
-                                         const T*, T*, cudaStream_t);                               \
-    template cudaError_t launch_jvp_tile<T>(const Geom&, const Coef&, double, Cache<T>, const T*, T*, \
-                                            cudaStream_t);
+    template cudaError_t launch_jvp_f<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, const T*, \
+                                         T*, cudaStream_t);                                         \
+    template cudaError_t launch_jvp_tile<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,    \
+                                            cudaStream_t);                                          \
+    template cudaError_t launch_set_jac<T>(JacK<T>*, const Coef&, double, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

@@ -4,77 +4,47 @@
 // precision boundary between the FP64 Newton vectors and the Krylov vectors.
 //
 // Reductions are two-stage and deterministic: every kernel writes one partial sum
-// per block (RED_BLOCKS blocks, grid-stride loops) and reduce_kernel adds the
-// partials of each vector in a fixed order.
+// per block (RED_BLOCKS blocks, grid-stride loops) and its last block to finish adds
+// the partials of each quantity in a fixed order (finish_reduction).
 #include "acac_internal.cuh"
 
 namespace acac {
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Sum of v over the block; result valid in thread 0.  sh: 32 doubles.
-__device__ __forceinline__ double block_sum_k(double v, double* sh) {
-    v = warp_sum(v);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0.0;
-        t = warp_sum(t);
-    }
-    return t;
-}
-
-__global__ void reduce_kernel(const double* __restrict__ partial, int nparts, double* __restrict__ out) {
-    __shared__ double sh[32];
-    const double* p = partial + (size_t)blockIdx.x * RED_BLOCKS;
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += p[i];
-    const double t = block_sum_k(acc, sh);
-    if (threadIdx.x == 0) out[blockIdx.x] = t;
-}
-
-cudaError_t launch_reduce_partials(const double* partial, int nvec, int nparts, double* out,
-                                   cudaStream_t s) {
-    reduce_kernel<<<nvec, RED_THREADS, 0, s>>>(partial, nparts, out);
-    return cudaGetLastError();
-}
-
 // partial sums of (a - b - c) over n  (mass correction of the Newton direction)
 __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                const double* __restrict__ c, long long n, double* partial) {
+                                const double* __restrict__ c, long long n, Red red) {
     __shared__ double sh[32];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         acc += (a[i] - b[i]) - c[i];
-    const double t = block_sum_k(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    const double t = block_sum_red(acc, sh);
+    if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
+    finish_reduction(red, 1, sh);
 }
 
-cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n,
-                            double* partial, cudaStream_t s) {
-    sum_pair_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, c, n, partial);
+cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
+                            cudaStream_t s) {
+    sum_pair_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, c, n, red);
     return cudaGetLastError();
 }
 
-__global__ void norm2_double_kernel(const double* __restrict__ x, long long n, double* partial) {
+__global__ void norm2_double_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                                    Red red) {
     __shared__ double sh[32];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        acc = fma(x[i], x[i], acc);
-    const double t = block_sum_k(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = b ? a[i] - b[i] : a[i];
+        acc = fma(x, x, acc);
+    }
+    const double t = block_sum_red(acc, sh);
+    if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
+    finish_reduction(red, 1, sh);
 }
 
-cudaError_t launch_norm2_double(const double* x, long long n, double* partial, cudaStream_t s) {
-    norm2_double_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, n, partial);
+cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s) {
+    norm2_double_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, red);
     return cudaGetLastError();
 }
 
@@ -84,7 +54,7 @@ cudaError_t launch_norm2_double(const double* x, long long n, double* partial, c
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                 const T* __restrict__ w, long long n,
-                                                                double* partial) {
+                                                                Red red) {
     __shared__ double sh[32];
     for (int k0 = 0; k0 < nv; k0 += 8) {
         const int cnt = nv - k0 < 8 ? nv - k0 : 8;
@@ -101,17 +71,18 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             if (q < cnt) {
-                const double t = block_sum_k((double)acc[q], sh);
-                if (threadIdx.x == 0) partial[(size_t)(k0 + q) * RED_BLOCKS + blockIdx.x] = t;
+                const double t = block_sum_red((double)acc[q], sh);
+                if (threadIdx.x == 0) red.partial[(size_t)(k0 + q) * RED_BLOCKS + blockIdx.x] = t;
             }
         }
     }
+    finish_reduction(red, nv, sh);
 }
 
 template <typename T>
-cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n,
-                             double* partial, cudaStream_t s) {
-    multi_dot_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, w, n, partial);
+cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
+                             cudaStream_t s) {
+    multi_dot_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, w, n, red);
     return cudaGetLastError();
 }
 
@@ -119,7 +90,7 @@ cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                  const double* __restrict__ h, T* __restrict__ w,
-                                                                 long long n, int want_norm, double* partial) {
+                                                                 long long n, int want_norm, Red red) {
     __shared__ double sh[32];
     __shared__ T hs[MAX_RESTART + 1];
     for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)h[k];
@@ -138,15 +109,16 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __rest
         acc += wn * wn;
     }
     if (want_norm) {
-        const double t = block_sum_k((double)acc, sh);
-        if (threadIdx.x == 0) partial[blockIdx.x] = t;
+        const double t = block_sum_red((double)acc, sh);
+        if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
+        finish_reduction(red, 1, sh);
     }
 }
 
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w, long long n,
-                              int want_norm, double* partial, cudaStream_t s) {
-    cgs_update_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, partial);
+                              int want_norm, Red red, cudaStream_t s) {
+    cgs_update_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red);
     return cudaGetLastError();
 }
 
@@ -154,7 +126,12 @@ cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h,
 template <typename T>
 __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restrict__ alpha,
                                   T* __restrict__ out, long long n) {
-    const T inv = (T)(1.0 / sqrt(alpha[0]));   // alpha holds ||w||^2
+    // alpha holds ||w||^2; one thread per block forms 1/||w|| (an FP64 square root
+    // and division per thread would cost more than the scaling itself)
+    __shared__ T s_inv;
+    if (threadIdx.x == 0) s_inv = (T)(1.0 / sqrt(alpha[0]));
+    __syncthreads();
+    const T inv = s_inv;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = w[i] * inv;
@@ -220,7 +197,7 @@ cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, 
 // r = b - Ax (double), partial sums of ||r||^2
 template <typename T>
 __global__ void residual_restart_kernel(const double* __restrict__ b, const T* __restrict__ Ax,
-                                        double* __restrict__ r, long long n, double* partial) {
+                                        double* __restrict__ r, long long n, Red red) {
     __shared__ double sh[32];
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -229,29 +206,30 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
         r[i] = ri;
         acc = fma(ri, ri, acc);
     }
-    const double t = block_sum_k(acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t;
+    const double t = block_sum_red(acc, sh);
+    if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
+    finish_reduction(red, 1, sh);
 }
 
 template <typename T>
-cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n,
-                                    double* partial, cudaStream_t s) {
-    residual_restart_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, Ax, r, n, partial);
+cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
+                                    cudaStream_t s) {
+    residual_restart_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, Ax, r, n, red);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                     \
-    template cudaError_t launch_multi_dot<T>(const T*, long long, int, const T*, long long, double*, \
+    template cudaError_t launch_multi_dot<T>(const T*, long long, int, const T*, long long, Red,    \
                                              cudaStream_t);                                         \
     template cudaError_t launch_cgs_update<T>(const T*, long long, int, const double*, T*, long long, \
-                                              int, double*, cudaStream_t);                          \
+                                              int, Red, cudaStream_t);                              \
     template cudaError_t launch_scale_from<T>(const T*, const double*, T*, long long, cudaStream_t); \
     template cudaError_t launch_to_krylov<T>(const double*, double, T*, long long, cudaStream_t);   \
     template cudaError_t launch_lincomb<T>(const T*, long long, int, const double*, T*, long long,  \
                                            cudaStream_t);                                           \
     template cudaError_t launch_axpy_to_double<T>(double, const T*, double*, long long, cudaStream_t); \
     template cudaError_t launch_residual_restart<T>(const double*, const T*, double*, long long,    \
-                                                    double*, cudaStream_t);
+                                                    Red, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

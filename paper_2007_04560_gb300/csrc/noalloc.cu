@@ -85,15 +85,17 @@ extern "C" int acac_residual_noalloc(const acac_params* p, const double* X1, con
     g.vol = g.hx * g.hy;
     const Coef k{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
 
-    // the flags accumulate with atomicOr: clear them for this call
-    if (cudaMemsetAsync(flags, 0, sizeof(int), s) != cudaSuccess) return ACAC_E_CUDA;
+    // the flags accumulate with atomicOr: clear them for this call (flags[4] is the
+    // reduction counter: zero between calls, re-armed by the kernel; clearing it too
+    // recovers from an earlier call that failed mid-way)
+    if (cudaMemsetAsync(flags, 0, 8 * sizeof(int), s) != cudaSuccess) return ACAC_E_CUDA;
     ResidualArgs a;
     a.X = X1; a.S = nullptr; a.lam = 0.0; a.shift = 0.0; a.X0 = X0; a.dt = dt;
-    a.Xt = nullptr; a.G = scratch; a.F = F; a.partial = scratch + NOALLOC_G; a.flags = flags;
     double* result = scratch + NOALLOC_G + RED_BLOCKS;
+    a.Xt = nullptr; a.G = scratch; a.F = F; a.flags = flags;
+    a.red = Red{scratch + NOALLOC_G, result, reinterpret_cast<unsigned*>(flags + 4)};
     if (launch_residual_g(g, k, a, s) != cudaSuccess) return ACAC_E_CUDA;
     if (launch_residual_f(g, k, a, s) != cudaSuccess) return ACAC_E_CUDA;
-    if (launch_reduce_partials(a.partial, 1, RED_BLOCKS, result, s) != cudaSuccess) return ACAC_E_CUDA;
     double f2 = 0.0;
     int fl = 0;
     if (cudaMemcpyAsync(&f2, result, sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess) return ACAC_E_CUDA;

@@ -14,9 +14,25 @@
 // same updates, so both give the same preconditioner (L unit block-lower, U block-
 // upper with pivot blocks D).  Stored per cell: the 6 lower blocks of L, D^-1, and
 // the 6 upper blocks of U (52 values, zero where the neighbour is outside the box).
+#include <atomic>
+#include <mutex>
+
 #include "acac_internal.cuh"
 
 namespace acac {
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`; `done` caches the
+// largest limit set so far.  Several host threads (the members of an ensemble) may
+// launch the same kernel at once.
+static std::mutex g_attr_mu;
+static cudaError_t ensure_smem_limit(const void* func, size_t bytes, std::atomic<size_t>* done) {
+    if (bytes <= done->load(std::memory_order_acquire)) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_attr_mu);
+    if (bytes <= done->load(std::memory_order_relaxed)) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done->store(bytes, std::memory_order_release);
+    return e;
+}
 
 template <typename T> struct V2 { T x, y; };
 template <> struct __align__(16) V2<double> { double x, y; };
@@ -74,7 +90,7 @@ template <typename T>
 __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                          const int* __restrict__ lev_off, const T* __restrict__ J,
                                                          T* __restrict__ coef, int ring_cells, int* flags) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubInfo sd = subs[blockIdx.x];
     int* lo = reinterpret_cast<int*>(smem_raw);
     const int lev_words = (sd.nlev + 1 + 3) & ~3;
@@ -157,13 +173,10 @@ template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                               const T* J, T* coef, int threads, int ring_cells, size_t smem_bytes, int* flags,
                               cudaStream_t s) {
-    static size_t attr_bytes[2] = {0, 0};
-    const int which = sizeof(T) == 8 ? 0 : 1;
-    if (smem_bytes > 48 * 1024 && smem_bytes > attr_bytes[which]) {
-        cudaError_t e = cudaFuncSetAttribute(ras_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes);
+    static std::atomic<size_t> attr_bytes{0};
+    if (smem_bytes > 48 * 1024) {
+        cudaError_t e = ensure_smem_limit((const void*)ras_factor_kernel<T>, smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes[which] = smem_bytes;
     }
     ras_factor_kernel<T><<<nsub, threads, smem_bytes, s>>>(g, subs, lev_off, J, coef, ring_cells, flags);
     return cudaGetLastError();
@@ -424,13 +437,10 @@ template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
-    static size_t attr_bytes[2] = {0, 0};
-    const int which = sizeof(T) == 8 ? 0 : 1;
-    if (L.smem_bytes > attr_bytes[which]) {
-        cudaError_t e = cudaFuncSetAttribute(ras_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)L.smem_bytes);
+    static std::atomic<size_t> attr_bytes{0};
+    {
+        cudaError_t e = ensure_smem_limit((const void*)ras_apply_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes[which] = L.smem_bytes;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
@@ -553,7 +563,7 @@ __global__ void __launch_bounds__(512) ras_apply3_kernel(Geom g, const SubInfo* 
                                                          const int* __restrict__ lev_off, const int* __restrict__ cells,
                                                          const T* __restrict__ coef, const T* __restrict__ r,
                                                          T* __restrict__ z, int ras_type, T* gscratch) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubInfo sd = subs[blockIdx.x];
     const int* lo = lev_off + sd.lev_base;
     const int* cl = cells + sd.cell_base;
@@ -641,13 +651,10 @@ template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
                               T* gscratch, cudaStream_t s) {
-    static size_t attr_bytes[2] = {0, 0};
-    const int which = sizeof(T) == 8 ? 0 : 1;
-    if (!gscratch && smem_bytes > 48 * 1024 && smem_bytes > attr_bytes[which]) {
-        cudaError_t e = cudaFuncSetAttribute(ras_apply3_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes);
+    static std::atomic<size_t> attr_bytes{0};
+    if (!gscratch && smem_bytes > 48 * 1024) {
+        cudaError_t e = ensure_smem_limit((const void*)ras_apply3_kernel<T>, smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
-        attr_bytes[which] = smem_bytes;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);

@@ -7,6 +7,9 @@
 //   pass A (g_kernel): G~^S = G1 + G2^S + G3 and the midpoint mobility c per cell;
 //   pass B (f_kernel): F_u = (u1-u0)/dt - [div c~ grad G_u], F_v = (v1-v0)/dt + c G_v/rho,
 //                      and per-block partial sums of ||F||^2.
+#include <atomic>
+#include <mutex>
+
 #include "acac_internal.cuh"
 
 namespace acac {
@@ -22,38 +25,41 @@ __constant__ double c_log_invF[LOG_TABLE];
 __constant__ double c_log_hi[LOG_TABLE];
 __constant__ double c_log_lo[LOG_TABLE];
 
-static int g_taylor_S = -1;
-static bool g_log_ready = false;
+// The constant tables do not depend on S (S only selects how many terms a kernel
+// sums), so they are uploaded once per device; several host threads may race here.
+static std::mutex g_const_mu;
+static std::atomic<unsigned long long> g_const_ready{0};   // bit d: device d holds the tables
 
-cudaError_t set_taylor_constants(int S) {
-    cudaError_t e = cudaSuccess;
-    if (!g_log_ready) {
-        double inv[LOG_TABLE], hi[LOG_TABLE], lo[LOG_TABLE];
-        for (int j = 0; j < LOG_TABLE; ++j) {
-            const long double F = 1.0L + (long double)j / 128.0L;
-            const long double L = logl(F);
-            inv[j] = (double)(1.0L / F);
-            hi[j] = (double)L;
-            lo[j] = (double)(L - (long double)hi[j]);
-        }
-        e = cudaMemcpyToSymbol(c_log_invF, inv, sizeof(inv));
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_hi, hi, sizeof(hi));
-        if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_lo, lo, sizeof(lo));
-        if (e != cudaSuccess) return e;
-        g_log_ready = true;
+cudaError_t set_taylor_constants(int) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ULL << (dev & 63);
+    if (g_const_ready.load(std::memory_order_acquire) & bit) return cudaSuccess;
+    std::lock_guard<std::mutex> lock(g_const_mu);
+    if (g_const_ready.load(std::memory_order_relaxed) & bit) return cudaSuccess;
+    double inv[LOG_TABLE], hi[LOG_TABLE], lo[LOG_TABLE];
+    for (int j = 0; j < LOG_TABLE; ++j) {
+        const long double F = 1.0L + (long double)j / 128.0L;
+        const long double L = logl(F);
+        inv[j] = (double)(1.0L / F);
+        hi[j] = (double)L;
+        lo[j] = (double)(L - (long double)hi[j]);
     }
-    if (S == g_taylor_S) return cudaSuccess;
     double a[MAX_S], b[MAX_S];
+    float bf[MAX_S];
     for (int k = 1; k <= MAX_S; ++k) {
         a[k - 1] = 1.0 / ((2.0 * k) * (2.0 * k + 1.0));
         b[k - 1] = 1.0 / (2.0 * k + 1.0);
+        bf[k - 1] = (float)b[k - 1];
     }
-    float bf[MAX_S];
-    for (int k = 0; k < MAX_S; ++k) bf[k] = (float)b[k];
-    e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
+    e = cudaMemcpyToSymbol(c_log_invF, inv, sizeof(inv));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_hi, hi, sizeof(hi));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_lo, lo, sizeof(lo));
+    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef, b, sizeof(b));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef_f, bf, sizeof(bf));
-    if (e == cudaSuccess) g_taylor_S = S;
+    if (e == cudaSuccess) g_const_ready.fetch_or(bit, std::memory_order_release);
     return e;
 }
 
@@ -159,22 +165,6 @@ __device__ __forceinline__ T dphi_series(double zeta_d, double sigma_d, int S) {
     return (T)0.5 * (((T)1 + a * a * Ra - a * Ra) * iz + ((T)1 + b * b * Rb + b * Rb) * io);
 }
 
-__device__ __forceinline__ double block_sum(double v, double* sh) {
-    const unsigned full = 0xffffffffu;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(full, v, o);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __syncthreads();
-    if (lane == 0) sh[warp] = v;
-    __syncthreads();
-    double t = 0.0;
-    if (warp == 0) {
-        const int nw = (blockDim.x + 31) >> 5;
-        t = lane < nw ? sh[lane] : 0.0;
-        for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(full, t, o);
-    }
-    return t;   // valid in thread 0
-}
-
 // ---------------------------------------------------------------- pass A
 // x in (0, 1) on the IEEE bit pattern: positive doubles order like their bits, and
 // every negative number, NaN or value >= 1 falls outside (0, bits(1.0)).
@@ -274,8 +264,9 @@ __global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho,
         a.F[N + c] = Fv;
         acc = fma(Fu, Fu, fma(Fv, Fv, acc));
     }
-    const double t = block_sum(acc, sh);
-    if (threadIdx.x == 0) a.partial[blockIdx.x] = t;
+    const double t = block_sum_red(acc, sh);
+    if (threadIdx.x == 0) a.red.partial[blockIdx.x] = t;
+    finish_reduction(a.red, 1, sh);
 }
 
 static int grid_for(long long n, int threads) {
@@ -299,8 +290,8 @@ cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     // 1/dt and 1/rho on the host (correctly rounded, as a kernel division would be)
     const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
-    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, idt, irho, a);
-    else f_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, idt, irho, a);
+    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, idt, irho, a);
+    else f_kernel<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, idt, irho, a);
     return cudaGetLastError();
 }
 
@@ -311,7 +302,7 @@ __device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_l
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
 template <int DIM>
 __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const double* __restrict__ X,
-                                                     double* partial, int* flags) {
+                                                     Red red, int* flags) {
     __shared__ double sh[32];
     const int N = g.N;
     const double* __restrict__ U = X;
@@ -337,17 +328,17 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
         e_acc += e;
         m_acc += u;
     }
-    double t = block_sum(e_acc, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = t * g.vol;
-    t = block_sum(m_acc, sh);
-    if (threadIdx.x == 0) partial[RED_BLOCKS + blockIdx.x] = t * g.vol;
     if (flag) atomicOr(flags, flag);
+    double t = block_sum_red(e_acc, sh);
+    if (threadIdx.x == 0) red.partial[blockIdx.x] = t * g.vol;
+    t = block_sum_red(m_acc, sh);
+    if (threadIdx.x == 0) red.partial[RED_BLOCKS + blockIdx.x] = t * g.vol;
+    finish_reduction(red, 2, sh);
 }
 
-cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, double* partial,
-                          int* flags, cudaStream_t s) {
-    if (g.dim == 3) energy_kernel<3><<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
-    else energy_kernel<2><<<RED_BLOCKS, 256, 0, s>>>(g, k, X, partial, flags);
+cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s) {
+    if (g.dim == 3) energy_kernel<3><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, k, X, red, flags);
+    else energy_kernel<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, k, X, red, flags);
     return cudaGetLastError();
 }
 

@@ -8,18 +8,114 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "acac_internal.cuh"
 
 using namespace acac;
 
+// Fixed set of host threads that runs fn(0..count-1) concurrently (the calling thread
+// takes part).  The members of an ensemble each drive their own solve from the host
+// (Newton control, GMRES Givens rotations, scalar read-backs), so stepping them from
+// separate threads lets their kernels, issued on separate streams, share the GPU.
+class MemberPool {
+public:
+    MemberPool(int nthreads, int device) : device_(device) {
+        for (int i = 0; i < nthreads; ++i) threads_.emplace_back([this] { worker(); });
+    }
+    ~MemberPool() {
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            stop_ = true;
+        }
+        cv_.notify_all();
+        for (auto& t : threads_) t.join();
+    }
+    void run(int count, const std::function<void(int)>& fn) {
+        {
+            std::lock_guard<std::mutex> lock(mu_);
+            fn_ = &fn;
+            count_ = count;
+            next_.store(0);
+            busy_ = (int)threads_.size();
+            ++gen_;
+        }
+        cv_.notify_all();
+        drain(fn, count);
+        std::unique_lock<std::mutex> lock(mu_);
+        done_cv_.wait(lock, [this] { return busy_ == 0; });
+        fn_ = nullptr;
+    }
+
+private:
+    void drain(const std::function<void(int)>& fn, int count) {
+        for (int i = next_.fetch_add(1); i < count; i = next_.fetch_add(1)) fn(i);
+    }
+    void worker() {
+        cudaSetDevice(device_);
+        long seen = 0;
+        while (true) {
+            const std::function<void(int)>* fn;
+            int count;
+            {
+                std::unique_lock<std::mutex> lock(mu_);
+                cv_.wait(lock, [&] { return stop_ || gen_ != seen; });
+                if (stop_) return;
+                seen = gen_;
+                fn = fn_;
+                count = count_;
+            }
+            drain(*fn, count);
+            {
+                std::lock_guard<std::mutex> lock(mu_);
+                --busy_;
+            }
+            done_cv_.notify_all();
+        }
+    }
+    int device_;
+    std::vector<std::thread> threads_;
+    std::mutex mu_;
+    std::condition_variable cv_, done_cv_;
+    const std::function<void(int)>* fn_ = nullptr;
+    int count_ = 0;
+    std::atomic<int> next_{0};
+    int busy_ = 0;
+    long gen_ = 0;
+    bool stop_ = false;
+};
+
+// One captured GMRES (Arnoldi) iteration: the graph and, per kernel node, the
+// launch accounting (and, when profiling, the event pair recorded around it).
+struct GraphRec {
+    int id;
+    double bytes, flops;
+    cudaEvent_t a, b;
+};
+struct IterGraph {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<GraphRec> recs;
+};
+
 struct acac_handle {
     acac_params p;
     Geom g;
     Coef k;
-    cudaStream_t stream;
+    cudaStream_t stream;        // private stream of all the handle's work
+    cudaStream_t user_stream;   // the caller's stream (ordered with `stream` at entry and exit)
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    void* jk_dev = nullptr;     // JacK<T> of the current linearisation
+    // CUDA graphs of the Arnoldi iterations (index j), captured on first use
+    std::vector<IterGraph> graphs;
+    bool graphs_prof = false;   // profiling state the graphs were captured with
+    std::vector<GraphRec>* capture = nullptr;   // non-null while capturing
+    int gmres_calls = 0;
     bool mixed;
     size_t N;
     size_t ksz;                 // sizeof Krylov element
@@ -34,6 +130,7 @@ struct acac_handle {
     double* host;               // pinned host mirror of red
     int* flags;
     int* host_flags;
+    unsigned* counter;          // reduction counter (zero between launches)
     // Schwarz tables
     std::vector<SubInfo> subs;
     std::vector<int> lev;
@@ -60,9 +157,16 @@ struct acac_handle {
     double kernel_ms[ACAC_NKERNEL];
     double kernel_bytes[ACAC_NKERNEL];   // algorithmic HBM bytes of the counted launches
     double kernel_flops[ACAC_NKERNEL];   // algorithmic floating-point operations
-    struct Pending { int id; cudaEvent_t a, b; };
+    struct Pending { int id; cudaEvent_t a, b; bool owned_by_graph; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
+    // ensemble (batch > 1): independent member problems, each a batch-1 handle on its
+    // own stream; this handle then only owns them, the staging buffer and the pool
+    std::vector<acac_handle*> members;
+    std::vector<cudaStream_t> member_streams;
+    std::vector<cudaEvent_t> member_done;
+    cudaEvent_t member_start = nullptr;
+    MemberPool* member_pool = nullptr;
 };
 
 namespace {
@@ -93,6 +197,7 @@ void prof_collect(acac_handle* h) {
     for (auto& p : h->pending) {
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) h->kernel_ms[p.id] += ms;
+        if (p.owned_by_graph) continue;
         h->pool.push_back(p.a);
         h->pool.push_back(p.b);
     }
@@ -105,6 +210,23 @@ struct KScope {
     acac_handle* h;
     cudaEvent_t b;
     KScope(acac_handle* h_, int id, double bytes = 0.0, double flops = 0.0) : h(h_), b(nullptr) {
+        if (h->capture) {
+            // inside a graph capture: the accounting happens at every replay, and the
+            // events (when profiling) become event-record nodes of the graph
+            GraphRec r{id, bytes, flops, nullptr, nullptr};
+            if (h->prof_on) {
+                // events come from the pool, stocked before the capture began
+                if (h->pool.size() < 2) throw Err{ACAC_E_CUDA};
+                r.a = h->pool.back();
+                h->pool.pop_back();
+                r.b = h->pool.back();
+                h->pool.pop_back();
+                CU(cudaEventRecordWithFlags(r.a, h->stream, cudaEventRecordExternal));
+                b = r.b;
+            }
+            h->capture->push_back(r);
+            return;
+        }
         h->launches[id]++;
         h->kernel_bytes[id] += bytes;
         h->kernel_flops[id] += flops;
@@ -112,13 +234,43 @@ struct KScope {
             cudaEvent_t a = take_event(h);
             b = take_event(h);
             CU(cudaEventRecord(a, h->stream));
-            h->pending.push_back({id, a, b});
+            h->pending.push_back({id, a, b, false});
         }
     }
     ~KScope() {
-        if (b) cudaEventRecord(b, h->stream);
+        if (!b) return;
+        if (h->capture) cudaEventRecordWithFlags(b, h->stream, cudaEventRecordExternal);
+        else cudaEventRecord(b, h->stream);
     }
 };
+
+// Orders the handle's private stream after the caller's stream on entry to a C-ABI
+// call and the caller's stream after the private stream on exit.  (An ensemble
+// handle works on the caller's stream itself and has no join events.)
+struct Join {
+    acac_handle* h;
+    explicit Join(acac_handle* h_) : h(h_) {
+        if (!h->ev_in) return;
+        cudaEventRecord(h->ev_in, h->user_stream);
+        cudaStreamWaitEvent(h->stream, h->ev_in, 0);
+    }
+    ~Join() {
+        if (!h->ev_in) return;
+        cudaEventRecord(h->ev_out, h->stream);
+        cudaStreamWaitEvent(h->user_stream, h->ev_out, 0);
+    }
+};
+
+void free_graphs(acac_handle* h) {
+    for (auto& G : h->graphs) {
+        if (G.exec) cudaGraphExecDestroy(G.exec);
+        for (auto& r : G.recs) {
+            if (r.a) cudaEventDestroy(r.a);
+            if (r.b) cudaEventDestroy(r.b);
+        }
+    }
+    h->graphs.clear();
+}
 
 #define KL(id, call)                 \
     do {                             \
@@ -138,6 +290,9 @@ Cache<T> cache_of(acac_handle* h) {
     const size_t N = h->N;
     return Cache<T>{base, base + N, base + 2 * N, base + 3 * N, base + 4 * N, base + 5 * N, base + 6 * N};
 }
+
+// Reduction target: partials at h->partial + poff, results at out.
+Red red_to(acac_handle* h, double* out, size_t poff = 0) { return Red{h->partial + poff, out, h->counter}; }
 
 double read_scalars(acac_handle* h, int n) {
     CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
@@ -159,7 +314,7 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     ResidualArgs a;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
-    a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.partial = h->partial; a.flags = h->flags;
+    a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.red = red_to(h, h->red); a.flags = h->flags;
     if (S) {
         // the line search's trial state X + lam (S + shift e_u), then F there
         KLA(ACAC_K_VECTOR, 40.0 * h->N, 0.0, launch_trial(h->g, a, h->stream));
@@ -168,32 +323,38 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     }
     KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 0.0, launch_residual_g(h->g, h->k, a, h->stream));
     KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
-    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double f2 = read_scalars(h, 1);
     *flags_out = *h->host_flags;
     return sqrt(f2);
 }
 
+// Scalars of the Jacobian action for the current (dt, coefficients), on the device.
 template <typename T>
-void jvp_action(acac_handle* h, double dt, const T* w, T* y) {
+void set_jac(acac_handle* h, double dt) {
+    KL(ACAC_K_VECTOR, launch_set_jac<T>((JacK<T>*)h->jk_dev, h->k, dt, h->stream));
+}
+
+template <typename T>
+void jvp_action(acac_handle* h, const T* w, T* y) {
+    const JacK<T>* kp = (const JacK<T>*)h->jk_dev;
     if (h->g.dim == 2 && sizeof(T) == 4) {
         // FP32: one tiled pass (HBM bound); FP64 keeps the two passes (FP64-pipe bound,
         // no halo recomputation)
         KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 11, 80.0 * h->N,
-            launch_jvp_tile<T>(h->g, h->k, dt, cache_of<T>(h), w, y, h->stream));
+            launch_jvp_tile<T>(h->g, kp, cache_of<T>(h), w, y, h->stream));
         return;
     }
-    KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N, launch_jvp_g<T>(h->g, h->k, cache_of<T>(h), w, (T*)h->jtmp, h->stream));
-    KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N, launch_jvp_f<T>(h->g, h->k, dt, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream));
+    KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N, launch_jvp_g<T>(h->g, kp, cache_of<T>(h), w, (T*)h->jtmp, h->stream));
+    KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N, launch_jvp_f<T>(h->g, kp, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream));
 }
 
 template <typename T>
-void jac_action(acac_handle* h, double dt, const T* w, T* y) {
+void jac_action(acac_handle* h, const T* w, T* y) {
     if (h->p.jac_mode == ACAC_JAC_ASSEMBLED)
         KLA(ACAC_K_SPMV, (double)sizeof(T) * h->N * 56, 104.0 * h->N, launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream));
     else
-        jvp_action<T>(h, dt, w, y);
+        jvp_action<T>(h, w, y);
 }
 
 template <typename T>
@@ -231,10 +392,96 @@ int factor(acac_handle* h) {
     return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
 }
 
+// One Arnoldi step of GMRES: v_{j+1} = J M^{-1} v_j orthogonalised against v_0..v_j
+// by classical Gram–Schmidt (twice when cgs_refine) and normalised; the Hessenberg
+// column and ||w||^2 are copied to h->host.  The caller synchronises.
+template <typename T>
+void arnoldi_step(acac_handle* h, int j) {
+    const long long n = 2 * (long long)h->N;
+    T* V = (T*)h->V;
+    const long long ld = (long long)h->ldV;
+    T* vj = V + (size_t)j * ld;
+    T* vn = V + (size_t)(j + 1) * ld;
+    precond<T>(h, vj, (T*)h->z);
+    jac_action<T>(h, (const T*)h->z, vn);
+    const int passes = h->p.cgs_refine ? 2 : 1;
+    for (int pass = 0; pass < passes; ++pass) {
+        double* hcol = h->red + pass * (MAX_RESTART + 1);
+        KLA(ACAC_K_DOT, (double)sizeof(T) * n * (j + 2), 2.0 * n * (j + 1),
+            launch_multi_dot<T>(V, ld, j + 1, vn, n, red_to(h, hcol), h->stream));
+        const bool last = pass == passes - 1;
+        KLA(ACAC_K_CGS_UPDATE, (double)sizeof(T) * n * (j + 3), 2.0 * n * (j + 2),
+            launch_cgs_update<T>(V, ld, j + 1, hcol, vn, n, last ? 1 : 0,
+                                 red_to(h, h->red + 2 * (MAX_RESTART + 1)), h->stream));
+    }
+    KL(ACAC_K_VECTOR, launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
+    CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * 3 * (MAX_RESTART + 1), cudaMemcpyDeviceToHost,
+                       h->stream));
+}
+
+// arnoldi_step(j), replayed from a CUDA graph captured on its first use (one graph per
+// j; every pointer and scalar the step's kernels take is fixed for the handle's
+// lifetime), or launched directly.  Synchronises and collects timings.
+template <typename T>
+void arnoldi_step_sync(acac_handle* h, int j) {
+    const bool use_graph = h->p.graphs && h->gmres_calls > 0;
+    if (!use_graph) {
+        arnoldi_step<T>(h, j);
+        CU(cudaStreamSynchronize(h->stream));
+        prof_collect(h);
+        return;
+    }
+    if (h->graphs_prof != h->prof_on) {
+        free_graphs(h);
+        h->graphs_prof = h->prof_on;
+    }
+    if ((int)h->graphs.size() <= j) h->graphs.resize(j + 1);
+    IterGraph& G = h->graphs[j];
+    if (!G.exec) {
+        if (h->prof_on)
+            while (h->pool.size() < 32) {
+                cudaEvent_t e;
+                CU(cudaEventCreate(&e));
+                h->pool.push_back(e);
+            }
+        cudaGraph_t graph = nullptr;
+        CU(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        h->capture = &G.recs;
+        try {
+            arnoldi_step<T>(h, j);
+        } catch (Err e) {
+            h->capture = nullptr;
+            cudaStreamEndCapture(h->stream, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            throw;
+        }
+        h->capture = nullptr;
+        CU(cudaStreamEndCapture(h->stream, &graph));
+        const cudaError_t e = cudaGraphInstantiate(&G.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        CU(e);
+    }
+    CU(cudaGraphLaunch(G.exec, h->stream));
+    for (const GraphRec& r : G.recs) {
+        h->launches[r.id]++;
+        h->kernel_bytes[r.id] += r.bytes;
+        h->kernel_flops[r.id] += r.flops;
+        if (r.a) h->pending.push_back({r.id, r.a, r.b, true});
+    }
+    CU(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+}
+
 // Restarted GMRES for J x = b (b = h->b, double), x0 = 0, right preconditioning.
 // Returns ACAC_OK or ACAC_E_DIVERGED; x (double, 2N) receives the solution.
 template <typename T>
-int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out) {
+int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
+    // the first call runs eagerly (it also sets the kernels' shared-memory limits);
+    // later calls replay captured graphs
+    struct Count {
+        acac_handle* h;
+        ~Count() { h->gmres_calls++; }
+    } count{h};
     const long long n = 2 * (long long)h->N;
     const int m = h->p.gmres_restart;
     T* V = (T*)h->V;
@@ -243,8 +490,7 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
     T* z = (T*)h->z;
     T* tt = (T*)h->kt;
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
-    KL(ACAC_K_VECTOR, launch_norm2_double(h->b, n, h->partial, h->stream));
-    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+    KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
     const double bnorm = sqrt(read_scalars(h, 1));
     const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
     double beta = bnorm;
@@ -265,25 +511,9 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
         bool done = false;
         double hn = 0.0;
         for (int j = 0; j < m; ++j) {
-            T* vj = V + (size_t)j * ld;
-            T* vn = V + (size_t)(j + 1) * ld;
-            precond<T>(h, vj, z);
-            jac_action<T>(h, dt, z, vn);
+            arnoldi_step_sync<T>(h, j);
             ++its;
-            // classical Gram–Schmidt, applied twice when cgs_refine
             const int passes = h->p.cgs_refine ? 2 : 1;
-            for (int pass = 0; pass < passes; ++pass) {
-                KLA(ACAC_K_DOT, (double)sizeof(T) * n * (j + 2), 2.0 * n * (j + 1), launch_multi_dot<T>(V, ld, j + 1, vn, n, h->partial, h->stream));
-                KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, j + 1, RED_BLOCKS, h->red + pass * (MAX_RESTART + 1),
-                                          h->stream));
-                const bool last = pass == passes - 1;
-                KLA(ACAC_K_CGS_UPDATE, (double)sizeof(T) * n * (j + 3), 2.0 * n * (j + 2), launch_cgs_update<T>(V, ld, j + 1, h->red + pass * (MAX_RESTART + 1), vn, n, last ? 1 : 0,
-                                        h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, h->stream));
-            }
-            KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial + (size_t)(MAX_RESTART + 1) * RED_BLOCKS, 1, RED_BLOCKS,
-                                      h->red + 2 * (MAX_RESTART + 1), h->stream));
-            KL(ACAC_K_VECTOR, launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
-            read_scalars(h, 3 * (MAX_RESTART + 1));
             for (int i = 0; i <= j; ++i) {
                 double hij = h->host[i];
                 if (passes == 2) hij += h->host[(MAX_RESTART + 1) + i];
@@ -336,9 +566,8 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
         }
         // restart: r = b - J x
         KL(ACAC_K_VECTOR, launch_to_krylov<T>(x, 1.0, tt, n, h->stream));
-        jac_action<T>(h, dt, tt, w);
-        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, h->partial, h->stream));
-        KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        jac_action<T>(h, tt, w);
+        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, red_to(h, h->red), h->stream));
         beta = sqrt(read_scalars(h, 1));
         rsrc = h->r;
         if (beta <= tol) {
@@ -351,6 +580,7 @@ int gmres(acac_handle* h, double dt, double* x, int* its_out, double* resid_out)
 
 template <typename T>
 void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble) {
+    set_jac<T>(h, dt);
     KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0, launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
     if (assemble) KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0, launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
 }
@@ -382,12 +612,11 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
         int gits = 0;
         double gres = 0.0;
-        int st = gmres<T>(h, dt, h->S, &gits, &gres);
+        int st = gmres<T>(h, h->S, &gits, &gres);
         info->gmres_its += gits;
         if (st != ACAC_OK) return st;
         // shift S_u by a constant so that sum(u + S_u) = sum(u^n)
-        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, h->partial, h->stream));
-        KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->red), h->stream));
         const double shift = read_scalars(h, 1) / (double)N;
         double lam = 1.0;
         const double f2 = fnorm * fnorm;
@@ -557,7 +786,8 @@ int acac::validate_params(const acac_params* p) {
     if (p->ras_type < 0 || p->ras_type > 2) return ACAC_E_ARG;
     if (p->precision != ACAC_FP64 && p->precision != ACAC_MIXED) return ACAC_E_ARG;
     if (p->jac_mode != ACAC_JAC_MATFREE && p->jac_mode != ACAC_JAC_ASSEMBLED) return ACAC_E_ARG;
-    if (p->batch != 1) return ACAC_E_ARG;
+    if (p->batch < 1 || p->batch > ACAC_MAX_BATCH) return ACAC_E_ARG;
+    if (p->graphs != 0 && p->graphs != 1) return ACAC_E_ARG;
     return ACAC_OK;
 }
 
@@ -573,12 +803,107 @@ void dmalloc(P** ptr, size_t bytes) {
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
-                    h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev};
+                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->host) cudaFreeHost(h->host);
     if (h->host_flags) cudaFreeHost(h->host_flags);
+    if (h->jk_dev) cudaFree(h->jk_dev);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->stream) cudaStreamDestroy(h->stream);
 }
+
+}  // namespace
+
+// ---------------------------------------------------------------- ensembles
+extern "C" int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out);
+extern "C" void acac_destroy(acac_handle* h);
+
+namespace {
+
+void destroy_ensemble(acac_handle* h) {
+    cudaStreamSynchronize(h->stream);
+    delete h->member_pool;
+    for (acac_handle* m : h->members)
+        if (m) acac_destroy(m);
+    for (cudaStream_t s : h->member_streams) cudaStreamDestroy(s);
+    for (cudaEvent_t e : h->member_done) cudaEventDestroy(e);
+    if (h->member_start) cudaEventDestroy(h->member_start);
+    if (h->stage) cudaFree(h->stage);
+    delete h;
+}
+
+int create_ensemble(const acac_params* p, void* cuda_stream, acac_handle** out) {
+    acac_handle* h = new (std::nothrow) acac_handle();
+    if (!h) return ACAC_E_NOMEM;
+    h->p = *p;
+    h->stream = h->user_stream = (cudaStream_t)cuda_stream;
+    h->mixed = p->precision == ACAC_MIXED;
+    h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
+    acac_params q = *p;
+    q.batch = 1;
+    const int B = p->batch;
+    int st = ACAC_OK;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) st = ACAC_E_CUDA;
+    h->members.assign(B, nullptr);
+    for (int m = 0; m < B && st == ACAC_OK; ++m) {
+        cudaStream_t s = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+            st = ACAC_E_CUDA;
+            break;
+        }
+        h->member_streams.push_back(s);
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            st = ACAC_E_CUDA;
+            break;
+        }
+        h->member_done.push_back(e);
+        st = acac_create(&q, s, &h->members[m]);
+    }
+    if (st == ACAC_OK && cudaEventCreateWithFlags(&h->member_start, cudaEventDisableTiming) != cudaSuccess)
+        st = ACAC_E_CUDA;
+    if (st == ACAC_OK && cudaMalloc((void**)&h->stage, 2 * h->N * B * sizeof(double)) != cudaSuccess)
+        st = ACAC_E_NOMEM;
+    if (st != ACAC_OK) {
+        destroy_ensemble(h);
+        return st;
+    }
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int workers = std::min<int>(B, (int)hw) - 1;   // the calling thread takes part
+    try {
+        h->member_pool = new MemberPool(std::max(0, workers), dev);
+    } catch (...) {
+        destroy_ensemble(h);
+        return ACAC_E_NOMEM;
+    }
+    *out = h;
+    return ACAC_OK;
+}
+
+// Runs fn(member) for every member concurrently, with the members' streams ordered
+// after the caller's stream on entry and before it on exit.  Returns the first
+// failing status in member order.
+int for_members(acac_handle* h, const std::function<int(int)>& fn) {
+    const int B = (int)h->members.size();
+    if (cudaEventRecord(h->member_start, h->stream) != cudaSuccess) return ACAC_E_CUDA;
+    for (int m = 0; m < B; ++m)
+        if (cudaStreamWaitEvent(h->member_streams[m], h->member_start, 0) != cudaSuccess) return ACAC_E_CUDA;
+    std::vector<int> st(B, ACAC_OK);
+    h->member_pool->run(B, [&](int m) { st[m] = fn(m); });
+    int first = ACAC_OK;
+    for (int m = 0; m < B; ++m) {
+        if (cudaEventRecord(h->member_done[m], h->member_streams[m]) != cudaSuccess ||
+            cudaStreamWaitEvent(h->stream, h->member_done[m], 0) != cudaSuccess)
+            return ACAC_E_CUDA;
+        if (first == ACAC_OK && st[m] != ACAC_OK) first = st[m];
+    }
+    return first;
+}
+
+bool is_ensemble(const acac_handle* h) { return h && !h->members.empty(); }
 
 }  // namespace
 
@@ -606,6 +931,7 @@ void acac_default_params(acac_params* p) {
     p->jac_mode = ACAC_JAC_MATFREE;
     p->batch = 1;
     p->cgs_refine = 1;
+    p->graphs = 1;
 }
 
 const char* acac_status_string(int s) {
@@ -627,10 +953,15 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     *out = nullptr;
     int st = validate_params(p);
     if (st != ACAC_OK) return st;
+    if (p->batch > 1) return create_ensemble(p, cuda_stream, out);
     acac_handle* h = new (std::nothrow) acac_handle();
     if (!h) return ACAC_E_NOMEM;
     h->p = *p;
-    h->stream = (cudaStream_t)cuda_stream;
+    h->user_stream = (cudaStream_t)cuda_stream;
+    if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete h;
+        return ACAC_E_CUDA;
+    }
     h->mixed = p->precision == ACAC_MIXED;
     h->ksz = h->mixed ? sizeof(float) : sizeof(double);
     h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
@@ -649,6 +980,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     h->eta = p->eta0;
     st = build_subdomains(h);
     if (st != ACAC_OK) {
+        cudaStreamDestroy(h->stream);
         delete h;
         return st;
     }
@@ -714,6 +1046,11 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         dmalloc(&h->red, (size_t)3 * (MAX_RESTART + 1) * 8);
         dmalloc(&h->flags, 16);
         CU(cudaMemset(h->flags, 0, 16));
+        dmalloc(&h->counter, 16);
+        CU(cudaMemset(h->counter, 0, 16));
+        dmalloc(&h->jk_dev, sizeof(JacK<double>));
+        CU(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        CU(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
         CU(cudaMallocHost((void**)&h->host, (size_t)3 * (MAX_RESTART + 1) * 8));
         CU(cudaMallocHost((void**)&h->host_flags, 16));
         dmalloc(&h->subs_dev, h->subs.size() * sizeof(SubInfo));
@@ -738,12 +1075,18 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
 
 void acac_destroy(acac_handle* h) {
     if (!h) return;
+    if (!h->members.empty()) {
+        destroy_ensemble(h);
+        return;
+    }
     cudaStreamSynchronize(h->stream);
     for (auto& p : h->pending) {
+        if (p.owned_by_graph) continue;
         cudaEventDestroy(p.a);
         cudaEventDestroy(p.b);
     }
     for (auto e : h->pool) cudaEventDestroy(e);
+    free_graphs(h);
     free_all(h);
     delete h;
 }
@@ -756,6 +1099,13 @@ int acac_log(const double* x, double* y, long long n, void* cuda_stream) {
 
 int acac_profile(acac_handle* h, int enable) {
     if (!h) return ACAC_E_ARG;
+    if (is_ensemble(h)) {
+        for (acac_handle* m : h->members) {
+            const int st = acac_profile(m, enable);
+            if (st != ACAC_OK) return st;
+        }
+        return ACAC_OK;
+    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
     try {
         prof_collect(h);
@@ -775,6 +1125,24 @@ int acac_profile(acac_handle* h, int enable) {
 int acac_kernel_stats(acac_handle* h, int kernel, long long* launches, double* total_ms, double* bytes,
                       double* flops) {
     if (!h || kernel < 0 || kernel >= ACAC_NKERNEL) return ACAC_E_ARG;
+    if (is_ensemble(h)) {
+        // sums over the members (their kernels overlap in time: the sum of the
+        // durations exceeds the wall time)
+        long long n = 0;
+        double ms = 0.0, b = 0.0, f = 0.0;
+        for (acac_handle* m : h->members) {
+            long long n1 = 0;
+            double ms1 = 0.0, b1 = 0.0, f1 = 0.0;
+            const int st = acac_kernel_stats(m, kernel, &n1, &ms1, &b1, &f1);
+            if (st != ACAC_OK) return st;
+            n += n1; ms += ms1; b += b1; f += f1;
+        }
+        if (launches) *launches = n;
+        if (total_ms) *total_ms = ms;
+        if (bytes) *bytes = b;
+        if (flops) *flops = f;
+        return ACAC_OK;
+    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
     try {
         prof_collect(h);
@@ -788,6 +1156,21 @@ int acac_kernel_stats(acac_handle* h, int kernel, long long* launches, double* t
     return ACAC_OK;
 }
 
+int acac_set_coeffs(acac_handle* h, int member, double alpha, double beta, double theta, double gamma,
+                    double rho) {
+    if (!h) return ACAC_E_ARG;
+    if (!(alpha > 0 && beta > 0 && theta > 0 && gamma > 0 && rho > 0)) return ACAC_E_ARG;
+    if (is_ensemble(h)) {
+        if (member < 0 || member >= (int)h->members.size()) return ACAC_E_ARG;
+        h = h->members[member];
+    } else if (member != 0) {
+        return ACAC_E_ARG;
+    }
+    h->p.alpha = alpha; h->p.beta = beta; h->p.theta = theta; h->p.gamma = gamma; h->p.rho = rho;
+    h->k = Coef{alpha, beta, theta, gamma, rho, h->p.taylor_S};
+    return ACAC_OK;
+}
+
 const char* acac_kernel_name(int kernel) {
     static const char* names[ACAC_NKERNEL] = {
         "residual_g", "residual_f", "linearize", "assemble", "spmv", "jvp_g", "jvp_f",
@@ -796,7 +1179,9 @@ const char* acac_kernel_name(int kernel) {
 }
 
 int acac_residual(acac_handle* h, const double* X1, const double* X0, double dt, double* F, double* fnorm) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !F || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
     try {
         const size_t n2 = 2 * h->N;
         CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
@@ -818,15 +1203,20 @@ static int linearize_at(acac_handle* h, const double* X1, const double* X0, doub
     int fl = 0;
     eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
     if (fl & 1) return ACAC_E_DOMAIN;
-    if (h->mixed)
+    if (h->mixed) {
+        set_jac<float>(h, dt);
         KL(ACAC_K_LINEARIZE, launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream));
-    else
+    } else {
+        set_jac<double>(h, dt);
         KL(ACAC_K_LINEARIZE, launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream));
+    }
     return ACAC_OK;
 }
 
 int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt, void* J) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !J || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
@@ -842,7 +1232,9 @@ int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt,
 }
 
 int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !J || !w || !y) return ACAC_E_ARG;
+    Join join(h);
     try {
         if (h->mixed)
             KL(ACAC_K_SPMV, launch_spmv<float>(h->g, (const float*)J, (const float*)w, (float*)y, h->stream));
@@ -855,12 +1247,14 @@ int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
 }
 
 int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, const void* w, void* y) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !w || !y || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
-        if (h->mixed) jvp_action<float>(h, dt, (const float*)w, (float*)y);
-        else jvp_action<double>(h, dt, (const double*)w, (double*)y);
+        if (h->mixed) jvp_action<float>(h, (const float*)w, (float*)y);
+        else jvp_action<double>(h, (const double*)w, (double*)y);
         return ACAC_OK;
     } catch (Err e) {
         return e.code;
@@ -868,7 +1262,9 @@ int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, cons
 }
 
 int acac_ras_factor(acac_handle* h, const void* J) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !J) return ACAC_E_ARG;
+    Join join(h);
     try {
         const size_t bytes = (size_t)(h->g.dim == 3 ? NSLOT3 : NSLOT) * 4 * h->N * h->ksz;
         if (J != h->J) CU(cudaMemcpyAsync(h->J, J, bytes, cudaMemcpyDeviceToDevice, h->stream));
@@ -879,7 +1275,9 @@ int acac_ras_factor(acac_handle* h, const void* J) {
 }
 
 int acac_ras_apply(acac_handle* h, const void* r, void* z) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !r || !z) return ACAC_E_ARG;
+    Join join(h);
     try {
         if (h->mixed) precond<float>(h, (const float*)r, (float*)z);
         else precond<double>(h, (const double*)r, (double*)z);
@@ -891,7 +1289,9 @@ int acac_ras_apply(acac_handle* h, const void* r, void* z) {
 
 int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, const double* b, double* x,
                int* its, double* resid) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !b || !x || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
@@ -901,11 +1301,11 @@ int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, co
         if (h->mixed) {
             KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
             st = factor<float>(h);
-            if (st == ACAC_OK) st = gmres<float>(h, dt, x, &gi, &gr);
+            if (st == ACAC_OK) st = gmres<float>(h, x, &gi, &gr);
         } else {
             KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)h->J, h->stream));
             st = factor<double>(h);
-            if (st == ACAC_OK) st = gmres<double>(h, dt, x, &gi, &gr);
+            if (st == ACAC_OK) st = gmres<double>(h, x, &gi, &gr);
         }
         if (its) *its = gi;
         if (resid) *resid = gr;
@@ -916,7 +1316,9 @@ int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, co
 }
 
 int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac_step_info* info) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
     if (!h || !U0 || !U1 || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
     acac_step_info local;
     memset(&local, 0, sizeof(local));
     int st;
@@ -936,8 +1338,7 @@ int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac
 
 static int energy_of(acac_handle* h, const double* X, double* e, double* m) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-    KLA(ACAC_K_ENERGY, 16.0 * h->N, 0.0, launch_energy(h->g, h->k, X, h->partial, h->flags, h->stream));
-    KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 2, RED_BLOCKS, h->red, h->stream));
+    KLA(ACAC_K_ENERGY, 16.0 * h->N, 0.0, launch_energy(h->g, h->k, X, red_to(h, h->red), h->flags, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     read_scalars(h, 2);
     if (e) *e = h->host[0];
@@ -947,6 +1348,14 @@ static int energy_of(acac_handle* h, const double* X, double* e, double* m) {
 
 int acac_energy(acac_handle* h, const double* u, const double* v, double* energy, double* mass) {
     if (!h || !u || !v) return ACAC_E_ARG;
+    if (is_ensemble(h)) {
+        const size_t N = h->N;
+        return for_members(h, [&](int m) {
+            return acac_energy(h->members[m], u + m * N, v + m * N, energy ? energy + m : nullptr,
+                               mass ? mass + m : nullptr);
+        });
+    }
+    Join join(h);
     try {
         const size_t N = h->N;
         CU(cudaMemcpyAsync(h->tmpd, u, N * 8, cudaMemcpyDeviceToDevice, h->stream));
@@ -959,6 +1368,13 @@ int acac_energy(acac_handle* h, const double* u, const double* v, double* energy
 
 int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
     if (!h || !u || !v) return ACAC_E_ARG;
+    if (is_ensemble(h)) {
+        const size_t N = h->N;
+        return for_members(h, [&](int m) {
+            return acac_step(h->members[m], u + m * N, v + m * N, info ? info + m : nullptr);
+        });
+    }
+    Join join(h);
     acac_step_info local;
     memset(&local, 0, sizeof(local));
     int st = ACAC_OK;
@@ -970,11 +1386,7 @@ int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
         // predictor of Eq. sencondt
         double dt = h->p.dt0;
         if (h->p.dt_mode == ACAC_DT_ADAPTIVE && h->have_prev) {
-            CU(cudaMemsetAsync(h->tmpd, 0, n2 * 8, h->stream));
-            KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(1.0, h->X0, h->tmpd, n2, h->stream));
-            KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->Xprev, h->tmpd, n2, h->stream));
-            KL(ACAC_K_VECTOR, launch_norm2_double(h->tmpd, n2, h->partial, h->stream));
-            KL(ACAC_K_REDUCE, launch_reduce_partials(h->partial, 1, RED_BLOCKS, h->red, h->stream));
+            KL(ACAC_K_VECTOR, launch_norm2_double(h->X0, h->Xprev, n2, red_to(h, h->red), h->stream));
             const double xd = sqrt(read_scalars(h, 1)) / h->dt_prev;
             dt = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta * xd * xd));
         }
@@ -1017,12 +1429,14 @@ int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
 
 int acac_step_host(acac_handle* h, double* u_host, double* v_host, acac_step_info* info) {
     if (!h || !u_host || !v_host) return ACAC_E_ARG;
+    Join join(h);
     try {
-        const size_t N = h->N;
+        const size_t N = h->N * (is_ensemble(h) ? h->members.size() : 1);
         CU(cudaMemcpyAsync(h->stage, u_host, N * 8, cudaMemcpyHostToDevice, h->stream));
         CU(cudaMemcpyAsync(h->stage + N, v_host, N * 8, cudaMemcpyHostToDevice, h->stream));
         int st = acac_step(h, h->stage, h->stage + N, info);
-        if (st == ACAC_OK) {
+        // an ensemble copies every member back: a failed member's fields are unchanged
+        if (st == ACAC_OK || is_ensemble(h)) {
             CU(cudaMemcpyAsync(u_host, h->stage, N * 8, cudaMemcpyDeviceToHost, h->stream));
             CU(cudaMemcpyAsync(v_host, h->stage + N, N * 8, cudaMemcpyDeviceToHost, h->stream));
         }

@@ -79,7 +79,8 @@ def test_defaults_and_validation_without_gpu(lib):
     assert lib.acac_status_string(-5).decode() == "time step fell below dt_min"
     h = ctypes.c_void_p()
     # argument errors are detected before any CUDA call
-    for field, bad in (("dim", 3), ("taylor_S", 0), ("gamma", -1.0), ("batch", 2), ("gmres_restart", 99)):
+    for field, bad in (("dim", 4), ("taylor_S", 0), ("gamma", -1.0), ("batch", 0), ("batch", 1025),
+                       ("gmres_restart", 99)):
         q = A.acac_params()
         lib.acac_default_params(ctypes.byref(q))
         setattr(q, field, bad)

@@ -64,6 +64,7 @@ class Params:
     jac_mode: int = JAC_MATFREE
     batch: int = 1
     cgs_refine: int = 1          # 1: CGS2 (two passes), 0: single classical pass
+    graphs: int = 1              # 1: GMRES iterations replayed from captured CUDA graphs
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
@@ -178,4 +179,44 @@ C3_UNIT = Workload("2d-2048x2048-unit-square-periodic-mixed-adaptive",
 C3_FP64 = Workload("2d-2048x2048-periodic-fp64-adaptive", C3.params.replace(precision=PREC_FP64),
                    steps=50, seed=2, u_mean=0.4, amp=0.05)
 
-WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C4, C4_FP64, C2_UNIT, C3_UNIT)}
+
+
+@dataclass
+class EnsembleWorkload(Workload):
+    """B independent members of one grid: member m starts from
+    initial_fields(seed * 1000 + m) and has theta_m = lo + (hi - lo) * U(0, 1), the B
+    values drawn from PCG64(seed); the other coefficients are shared."""
+
+    theta_range: Tuple[float, float] = (0.25, 0.35)
+
+    @property
+    def members(self) -> int:
+        return self.params.batch
+
+    def member_params(self, m: int) -> Params:
+        return self.params.replace(batch=1, theta=float(self.thetas()[m]))
+
+    def thetas(self) -> np.ndarray:
+        lo, hi = self.theta_range
+        return lo + (hi - lo) * np.random.default_rng(self.seed).uniform(0.0, 1.0, size=self.members)
+
+    def member_fields(self, m: int):
+        one = self.params.replace(batch=1)
+        return initial_fields(one, self.seed * 1000 + m, self.u_mean, self.amp)
+
+    def fields(self):
+        """(u, v) of shape (B,) + grid shape, member-major."""
+        us, vs = zip(*(self.member_fields(m) for m in range(self.members)))
+        return np.ascontiguousarray(np.stack(us)), np.ascontiguousarray(np.stack(vs))
+
+
+# 32 members of 256^2 periodic (h = 1/64, so [0, 4]^2), theta ~ U(0.25, 0.35) per member,
+# FP64 residual with FP32 Krylov / Jacobian / ILU, adaptive dt from 1e-4, RAS 4x4 overlap 2.
+E32 = EnsembleWorkload(
+    "2d-ensemble-32x256x256-periodic-mixed-adaptive",
+    Params(dim=2, n=(256, 256, 1), L=(256 * H64, 256 * H64, 1.0), bc=BC_PERIODIC, dt_mode=DT_ADAPTIVE,
+           dt0=1e-4, dt_min=1e-5, dt_max=1e-1, eta0=1e4, ras_parts=(4, 4, 1), ras_overlap=2,
+           precision=PREC_MIXED, batch=32, **_COEF),
+    steps=50, seed=3, u_mean=0.4, amp=0.05)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C4, C4_FP64, C2_UNIT, C3_UNIT, E32)}
