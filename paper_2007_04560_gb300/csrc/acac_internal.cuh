@@ -298,6 +298,14 @@ __device__ __forceinline__ double block_sum_red(double v, double* sh) {
     return t;
 }
 
+// Grid of a reducing (or plain vector) kernel over n elements: about four elements per
+// thread, at most RED_BLOCKS blocks.  Small problems (ensemble members) then leave
+// most of the GPU to the kernels of other members instead of occupying every SM.
+inline int red_grid(long long n) {
+    const long long b = (n + 4LL * RED_THREADS - 1) / (4LL * RED_THREADS);
+    return (int)(b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b));
+}
+
 // Called by every thread of every block after the block's partials are written.
 __device__ __forceinline__ void finish_reduction(const Red& r, int nv, double* sh) {
     __shared__ int s_last;

@@ -25,7 +25,7 @@ __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __re
 
 cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
                             cudaStream_t s) {
-    sum_pair_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, c, n, red);
+    sum_pair_kernel<<<red_grid(n), RED_THREADS, 0, s>>>(a, b, c, n, red);
     return cudaGetLastError();
 }
 
@@ -44,7 +44,7 @@ __global__ void norm2_double_kernel(const double* __restrict__ a, const double* 
 }
 
 cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s) {
-    norm2_double_kernel<<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, b, n, red);
+    norm2_double_kernel<<<red_grid(n), RED_THREADS, 0, s>>>(a, b, n, red);
     return cudaGetLastError();
 }
 
@@ -82,7 +82,7 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
 template <typename T>
 cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
                              cudaStream_t s) {
-    multi_dot_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, w, n, red);
+    multi_dot_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red);
     return cudaGetLastError();
 }
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __rest
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w, long long n,
                               int want_norm, Red red, cudaStream_t s) {
-    cgs_update_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red);
+    cgs_update_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red);
     return cudaGetLastError();
 }
 
@@ -140,7 +140,7 @@ __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restr
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
                               cudaStream_t s) {
-    scale_from_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(w, alpha_dev, out, n);
+    scale_from_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(w, alpha_dev, out, n);
     return cudaGetLastError();
 }
 
@@ -154,7 +154,7 @@ __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* 
 
 template <typename T>
 cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s) {
-    to_krylov_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(x, scale, out, n);
+    to_krylov_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(x, scale, out, n);
     return cudaGetLastError();
 }
 
@@ -176,7 +176,7 @@ __global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, co
 template <typename T>
 cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T* out, long long n,
                            cudaStream_t s) {
-    lincomb_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(V, ld, nv, y, out, n);
+    lincomb_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n);
     return cudaGetLastError();
 }
 
@@ -190,7 +190,7 @@ __global__ void axpy_to_double_kernel(double a, const T* __restrict__ x, double*
 
 template <typename T>
 cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s) {
-    axpy_to_double_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(a, x, y, n);
+    axpy_to_double_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(a, x, y, n);
     return cudaGetLastError();
 }
 
@@ -214,7 +214,7 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
 template <typename T>
 cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
                                     cudaStream_t s) {
-    residual_restart_kernel<T><<<RED_BLOCKS, RED_THREADS, 0, s>>>(b, Ax, r, n, red);
+    residual_restart_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(b, Ax, r, n, red);
     return cudaGetLastError();
 }
 

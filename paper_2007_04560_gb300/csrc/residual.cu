@@ -290,8 +290,8 @@ cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     // 1/dt and 1/rho on the host (correctly rounded, as a kernel division would be)
     const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
-    if (g.dim == 3) f_kernel<3><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, idt, irho, a);
-    else f_kernel<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, idt, irho, a);
+    if (g.dim == 3) f_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, idt, irho, a);
+    else f_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, idt, irho, a);
     return cudaGetLastError();
 }
 
@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
 }
 
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s) {
-    if (g.dim == 3) energy_kernel<3><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, k, X, red, flags);
-    else energy_kernel<2><<<RED_BLOCKS, RED_THREADS, 0, s>>>(g, k, X, red, flags);
+    if (g.dim == 3) energy_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, red, flags);
+    else energy_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, red, flags);
     return cudaGetLastError();
 }
 
