@@ -222,6 +222,50 @@ int acac_gmres(acac_handle *h, const double *X1, const double *X0, double dt,
 int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
                    acac_step_info *info);
 
+/* ---- adjoint of the implicit step (FP64 handles) -------------------------------- */
+/* There is no adjoint in the paper; these entry points differentiate its fixed-dt
+ * scheme (NSOA-1, Sec. 2) in reverse mode.  With F(U^{n+1}, U^n; p) = 0 per step and
+ * J1 = dF/dU^{n+1}, J0 = dF/dU^n:
+ *     J1^T mu = lambda^{n+1},   lambda^n = -J0^T mu,   dL/dp += -mu^T dF/dp,
+ * for p = (alpha, beta, theta, gamma).  J1^T mu = lambda is solved by GMRES on the
+ * transposed assembled Jacobian, preconditioned by the Schwarz/ILU(0) preconditioner
+ * of params.ras_type factored from the subdomain blocks of J1^T, to relative residual
+ * rtol.  Vectors are double state vectors [u | v] on the device.  ACAC_E_ARG on an
+ * ensemble or mixed-precision handle. */
+
+/* dF/dX0 at (X1, X0, dt) in the storage of acac_jacobian (Krylov precision). */
+int acac_jacobian_x0(acac_handle *h, const double *X1, const double *X0, double dt, void *J);
+
+/* y = J^T w for J in the storage of acac_jacobian (Krylov precision, device). */
+int acac_spmv_t(acac_handle *h, const void *J, const void *w, void *y);
+
+/* Loss L = w_energy E~(X) + (w_misfit / 2) sum ((u - u*)^2 + (v - v*)^2) dx dy of a
+ * state X against target = [u* | v*]: *loss (host), dX = dL/dX (device, 2N) and
+ * grad[0..3] (host, may be NULL) = dL/d(alpha, beta, theta, gamma) at fixed X.
+ * ACAC_E_DOMAIN if some u+v or u-v of X lies outside (0, 1).  Synchronises. */
+int acac_loss(acac_handle *h, const double *X, const double *target, double w_energy,
+              double w_misfit, double *loss, double *dX, double *grad);
+
+/* One adjoint step at (X1, X0, dt): lam0 = -J0^T mu with J1^T mu = lam1 (lam0 may
+ * alias lam1), grad[0..3] (host, may be NULL) = -mu^T dF/d(alpha, beta, theta, gamma),
+ * *gmres_its (host, may be NULL).  Synchronises. */
+int acac_adjoint_step(acac_handle *h, const double *X1, const double *X0, double dt,
+                      const double *lam1, double *lam0, double *grad, double rtol,
+                      int *gmres_its);
+
+/* Gradient of L(U^K) (as acac_loss) after nsteps fixed-dt steps from (u0, v0), by the
+ * adjoint recursion with a checkpoint every checkpoint_every steps: the forward run
+ * keeps those states (and U^K), the backward run recomputes each segment from its
+ * checkpoint.  Device: u0, v0, u_target, v_target (N each), du0, dv0 (N each,
+ * receive dL/du0, dL/dv0).  Host: *loss, grad[0..3] = dL/d(alpha, beta, theta,
+ * gamma), *gmres_its (may be NULL).  Working memory: (nsteps/checkpoint_every + 2 +
+ * checkpoint_every) states, allocated for the call.  The handle's time-step history
+ * is not used or changed.  Errors as acac_nks_solve and acac_loss.  Synchronises. */
+int acac_adjoint(acac_handle *h, const double *u0, const double *v0, int nsteps, double dt,
+                 int checkpoint_every, const double *u_target, const double *v_target,
+                 double w_energy, double w_misfit, double rtol, double *loss, double *du0,
+                 double *dv0, double *grad, int *gmres_its);
+
 /* ---- residual without a handle and without device allocation ------------------- */
 
 /* F(X1) and ||F|| exactly as acac_residual computes them, for callers that may not

@@ -89,6 +89,12 @@ SIGNATURES = {
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "acac_set_coeffs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
+    "acac_jacobian_x0": (ctypes.c_int, [_P, _P, _P, _D, _P]),
+    "acac_spmv_t": (ctypes.c_int, [_P, _P, _P, _P]),
+    "acac_loss": (ctypes.c_int, [_P, _P, _P, _D, _D, _PD, _P, _PD]),
+    "acac_adjoint_step": (ctypes.c_int, [_P, _P, _P, _D, _P, _P, _PD, _D, _PI]),
+    "acac_adjoint": (ctypes.c_int, [_P, _P, _P, ctypes.c_int, _D, ctypes.c_int, _P, _P, _D, _D, _D, _PD, _P, _P,
+                                    _PD, _PI]),
 }
 
 NKERNEL = 14
@@ -320,6 +326,53 @@ class Solver:
         if check:
             _check(st, "acac_gmres")
         return its.value, res.value, st
+
+    # -- adjoint (FP64 handles)
+    def jacobian_x0(self, X1, X0, dt, J):
+        import torch
+        _check(_lib().acac_jacobian_x0(self.h, _dev(X1, torch.float64, 2 * self.N), _dev(X0, torch.float64, 2 * self.N),
+                                       float(dt), _dev(J, self.kdtype, 4 * self.nslot * self.N, "J")),
+               "acac_jacobian_x0")
+
+    def spmv_t(self, J, w, y):
+        _check(_lib().acac_spmv_t(self.h, _dev(J, self.kdtype, 4 * self.nslot * self.N, "J"),
+                                  _dev(w, self.kdtype, 2 * self.N, "w"), _dev(y, self.kdtype, 2 * self.N, "y")),
+               "acac_spmv_t")
+
+    def loss(self, X, target, w_energy, w_misfit, dX):
+        """Returns (L, [dL/dalpha, dL/dbeta, dL/dtheta, dL/dgamma]); dX receives dL/dX."""
+        import torch
+        L, g = ctypes.c_double(), (ctypes.c_double * 4)()
+        _check(_lib().acac_loss(self.h, _dev(X, torch.float64, 2 * self.N, "X"),
+                                _dev(target, torch.float64, 2 * self.N, "target"), float(w_energy), float(w_misfit),
+                                ctypes.byref(L), _dev(dX, torch.float64, 2 * self.N, "dX"), g), "acac_loss")
+        return L.value, list(g)
+
+    def adjoint_step(self, X1, X0, dt, lam1, lam0, rtol=1e-10):
+        """lam0 = -J0^T mu with J1^T mu = lam1; returns (grad[4], gmres_its)."""
+        import torch
+        g, its = (ctypes.c_double * 4)(), ctypes.c_int()
+        n = 2 * self.N
+        _check(_lib().acac_adjoint_step(self.h, _dev(X1, torch.float64, n, "X1"), _dev(X0, torch.float64, n, "X0"),
+                                        float(dt), _dev(lam1, torch.float64, n, "lam1"),
+                                        _dev(lam0, torch.float64, n, "lam0"), g, float(rtol), ctypes.byref(its)),
+               "acac_adjoint_step")
+        return list(g), its.value
+
+    def adjoint(self, u0, v0, nsteps, dt, u_target, v_target, w_energy=1.0, w_misfit=1.0, every=5, rtol=1e-10,
+                du0=None, dv0=None):
+        """Loss of the state after nsteps fixed-dt steps and its gradient.  Returns
+        (L, du0, dv0, [dL/dalpha, dL/dbeta, dL/dtheta, dL/dgamma], gmres_its)."""
+        import torch
+        du0 = torch.empty_like(u0) if du0 is None else du0
+        dv0 = torch.empty_like(v0) if dv0 is None else dv0
+        L, g, its = ctypes.c_double(), (ctypes.c_double * 4)(), ctypes.c_int()
+        _check(_lib().acac_adjoint(self.h, _dev(u0, torch.float64, self.N, "u0"), _dev(v0, torch.float64, self.N, "v0"),
+                                   int(nsteps), float(dt), int(every), _dev(u_target, torch.float64, self.N, "u_target"),
+                                   _dev(v_target, torch.float64, self.N, "v_target"), float(w_energy), float(w_misfit),
+                                   float(rtol), ctypes.byref(L), _dev(du0, torch.float64, self.N, "du0"),
+                                   _dev(dv0, torch.float64, self.N, "dv0"), g, ctypes.byref(its)), "acac_adjoint")
+        return L.value, du0, dv0, list(g), its.value
 
     # -- instrumentation
     def profile(self, enable=True):

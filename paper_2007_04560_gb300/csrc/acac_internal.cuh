@@ -345,9 +345,19 @@ cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);
 // energy and mass: two quantities
 cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s);
+// wrt_x0 = 0: the cache of dF/dX1; 1: of dF/dX0 (the series derivative taken with -sigma;
+// c, cu, cv, Gu, Gv are the same, and assembling with -dt gives the -1/dt diagonal).
 template <typename T>
 cudaError_t launch_linearize(const Geom& g, const Coef& k, const double* X, const double* X0,
-                             const double* G, Cache<T> cache, cudaStream_t s);
+                             const double* G, Cache<T> cache, cudaStream_t s, int wrt_x0 = 0);
+// Adjoint: per-cell -mu^T dF/d(alpha, beta, theta, gamma) at (X1, X0) with G = [Gu | Gv | c]
+// of pass A there, reduced to 4 sums (red.out[0..3]).
+cudaError_t launch_param_grad(const Geom& g, const Coef& k, const double* X1, const double* X0,
+                              const double* G, const double* mu, Red red, int* flags, cudaStream_t s);
+// Loss L = wE E~(X) + wM/2 sum((u-u*)^2 + (v-v*)^2) dx dy: dL/dX into lam (2N) and the sums
+// [L, dL/dalpha, dL/dbeta, dL/dtheta, dL/dgamma] into red.out[0..4].
+cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, const double* target, double wE,
+                             double wM, double* lam, Red red, int* flags, cudaStream_t s);
 
 // jacobian.cu
 template <typename T>
@@ -355,6 +365,8 @@ cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> ca
                             cudaStream_t s);
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
+template <typename T>
+cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s);
 // The matrix-free products read their scalars (JacK) from device memory, written by
 // launch_set_jac whenever dt or the coefficients change, so that a captured CUDA
 // graph of a GMRES iteration stays valid across time steps.

@@ -288,6 +288,48 @@ cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, co
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- transpose
+// JT = J^T in the same stencil-diagonal storage.  The block of JT at row c, slot s
+// (column c + o_s) is the transpose of J's block at row r = c + o_s, slot s' with
+// o_s' = -o_s (the slot set is symmetric).  Slots that leave a Neumann domain are 0
+// in both.  Used by the adjoint: GMRES on J^T with the Schwarz/ILU(0) preconditioner
+// factored from J^T's own subdomain blocks, and the products J0^T mu.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) transpose_kernel(Geom g, const T* __restrict__ J, T* __restrict__ JT) {
+    const int N = g.N;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    int x, y, z;
+    decode_cell<DIM>(g, c, x, y, z);
+    const bool per = g.bc == ACAC_BC_PERIODIC;
+#pragma unroll
+    for (int s = 0; s < nslot<DIM>(); ++s) {
+        const int dx = sl_dx<DIM>(s), dy = sl_dy<DIM>(s), dz = sl_dz<DIM>(s);
+        const bool inside = per || (x + dx >= 0 && x + dx < g.nx && y + dy >= 0 && y + dy < g.ny &&
+                                    z + dz >= 0 && z + dz < g.nz);
+        T b0 = 0, b1 = 0, b2 = 0, b3 = 0;
+        if (inside) {
+            const int r = slot_nb<DIM>(g, x, y, z, s);
+            const int s2 = sl_of<DIM>(-dx, -dy, -dz);
+            b0 = J[(size_t)(s2 * 4 + 0) * N + r];
+            b1 = J[(size_t)(s2 * 4 + 2) * N + r];
+            b2 = J[(size_t)(s2 * 4 + 1) * N + r];
+            b3 = J[(size_t)(s2 * 4 + 3) * N + r];
+        }
+        JT[(size_t)(s * 4 + 0) * N + c] = b0;
+        JT[(size_t)(s * 4 + 1) * N + c] = b1;
+        JT[(size_t)(s * 4 + 2) * N + c] = b2;
+        JT[(size_t)(s * 4 + 3) * N + c] = b3;
+    }
+}
+
+template <typename T>
+cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s) {
+    if (g.dim == 3) transpose_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, J, JT);
+    else transpose_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, J, JT);
+    return cudaGetLastError();
+}
+
 #define INST(T)                                                                                   \
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
                                             cudaStream_t);                                        \
@@ -298,7 +340,8 @@ cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, co
                                          T*, cudaStream_t);                                         \
     template cudaError_t launch_jvp_tile<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,    \
                                             cudaStream_t);                                          \
-    template cudaError_t launch_set_jac<T>(JacK<T>*, const Coef&, double, cudaStream_t);
+    template cudaError_t launch_set_jac<T>(JacK<T>*, const Coef&, double, cudaStream_t);             \
+    template cudaError_t launch_transpose<T>(const Geom&, const T*, T*, cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

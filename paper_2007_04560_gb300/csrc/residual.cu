@@ -351,7 +351,8 @@ cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red
 template <typename T>
 __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const double* __restrict__ X,
                                                         const double* __restrict__ X0,
-                                                        const double* __restrict__ G, Cache<T> C) {
+                                                        const double* __restrict__ G, Cache<T> C,
+                                                        double ssign) {
     const int N = g.N;
     const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
@@ -360,8 +361,9 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
         const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
         const T ub = (T)(0.5 * (u1 + u0)), vb = (T)(0.5 * (v1 + v0));
         const T w = (T)0.25 - vb * vb;
-        const T A = theta * dphi_series<T>(zp, sp, k.S);
-        const T B = theta * dphi_series<T>(zq, sq, k.S);
+        // ssign = -1: derivative in the start value (phi^S is even in sigma)
+        const T A = theta * dphi_series<T>(zp, ssign * sp, k.S);
+        const T B = theta * dphi_series<T>(zq, ssign * sq, k.S);
         C.c[c] = (T)G[2 * N + c];
         C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ub) * w;
         C.cv[c] = -ub * ((T)1 - ub) * vb;
@@ -374,10 +376,142 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
 
 template <typename T>
 cudaError_t launch_linearize(const Geom& g, const Coef& k, const double* X, const double* X0,
-                             const double* G, Cache<T> cache, cudaStream_t s) {
+                             const double* G, Cache<T> cache, cudaStream_t s, int wrt_x0) {
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
-    linearize_kernel<T><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, X, X0, G, cache);
+    linearize_kernel<T><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, X, X0, G, cache, wrt_x0 ? -1.0 : 1.0);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- adjoint
+// -mu^T dF/dp for p = alpha, beta, theta, gamma at (X1, X0).  The coefficients enter
+// only G~ (linearly), so with A(g) = -div(c~ grad g) (symmetric) and
+// q_u = A(mu_u), q_v = c mu_v / rho:
+//   -mu^T dF/dp = -sum_cells [dG_u/dp q_u + dG_v/dp q_v],
+//   dG/dalpha = (-(u1+u0-1)/2, 0), dG/dbeta = (0, -(v1+v0)/2),
+//   dG/dtheta = (phi + psi, phi - psi), dG/dgamma = -(Delta(u1+u0), Delta(v1+v0))/2.
+template <int DIM>
+__global__ void __launch_bounds__(256) param_grad_kernel(Geom g, Coef k, const double* __restrict__ X1,
+                                                         const double* __restrict__ X0,
+                                                         const double* __restrict__ G,
+                                                         const double* __restrict__ mu, Red red, int* flags) {
+    __shared__ double sh[32];
+    const int N = g.N;
+    const double* __restrict__ cm = G + 2 * N;
+    const double irho = 1.0 / k.rho;   // once per thread: this kernel runs once per adjoint step
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    int flag = 0;
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (N + stride - 1) / stride;
+    for (int it = 0; it < iters; ++it) {
+        const int c = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool live = c < N;
+        const int cc = live ? c : N - 1;
+        int x, y, z;
+        decode_cell<DIM>(g, cc, x, y, z);
+        const double u1 = X1[cc], v1 = X1[N + cc], u0 = X0[cc], v0 = X0[N + cc];
+        const double su = u1 + u0, sv = v1 + v0;
+        const double c0 = cm[cc], mu_u = mu[cc];
+        double lu = 0.0, lv = 0.0, qu = 0.0;
+#pragma unroll
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, y, z, f);
+            const double w = face_weight<DIM, double>(g, x, y, z, f);
+            lu = fma(X1[n] + X0[n] - su, w, lu);
+            lv = fma(X1[N + n] + X0[N + n] - sv, w, lv);
+            qu -= w * 0.5 * (c0 + cm[n]) * (mu[n] - mu_u);
+        }
+        const double qv = c0 * mu[N + cc] * irho;
+        const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
+        const double zp = 0.5 * (p1 + p0), sp = 0.5 * (p1 - p0);
+        const double zq = 0.5 * (q1 + q0), sq = 0.5 * (q1 - q0);
+        const bool ok = in_unit(zp) && in_unit(zq);
+        if (live && !ok) flag |= 1;
+        const SeriesArgs ap = series_args(ok ? zp : 0.5, sp);
+        const SeriesArgs aq = series_args(ok ? zq : 0.5, sq);
+        const int K = series_terms(fmax(fmax(ap.ra, ap.rb), fmax(aq.ra, aq.rb)), k.S);
+        const double phi = phi_series(ap, K), psi = phi_series(aq, K);
+        if (live && ok) {
+            acc[0] += 0.5 * (su - 1.0) * qu;
+            acc[1] += 0.5 * sv * qv;
+            acc[2] -= (phi + psi) * qu + (phi - psi) * qv;
+            acc[3] += 0.5 * (lu * qu + lv * qv);
+        }
+    }
+    if (flag) atomicOr(flags, flag);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+        const double t = block_sum_red(acc[v], sh);
+        if (threadIdx.x == 0) red.partial[(size_t)v * RED_BLOCKS + blockIdx.x] = t;
+    }
+    finish_reduction(red, 4, sh);
+}
+
+cudaError_t launch_param_grad(const Geom& g, const Coef& k, const double* X1, const double* X0,
+                              const double* G, const double* mu, Red red, int* flags, cudaStream_t s) {
+    cudaError_t e = set_taylor_constants(k.S);
+    if (e != cudaSuccess) return e;
+    if (g.dim == 3) param_grad_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X1, X0, G, mu, red, flags);
+    else param_grad_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X1, X0, G, mu, red, flags);
+    return cudaGetLastError();
+}
+
+// Loss of the final state and its gradient.  E~ as in energy_kernel; its derivative in
+// u at a cell is dx dy [alpha/2 (1 - 2u) + theta Phi'(u+v) + theta Phi'(u-v) - gamma Delta u]
+// (every face difference enters E~ once as a D+ and once as a D- term), in v
+// dx dy [-beta v + theta Phi'(u+v) - theta Phi'(u-v) - gamma Delta v], Phi'(z) = ln z - ln(1-z).
+template <int DIM>
+__global__ void __launch_bounds__(256) loss_grad_kernel(Geom g, Coef k, const double* __restrict__ X,
+                                                        const double* __restrict__ T, double wE, double wM,
+                                                        double* __restrict__ lam, Red red, int* flags) {
+    __shared__ double sh[32];
+    const int N = g.N;
+    double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    int flag = 0;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        int x, y, z;
+        decode_cell<DIM>(g, c, x, y, z);
+        const double u = X[c], v = X[N + c];
+        const double p = u + v, q = u - v;
+        if (!(in_unit(p) && in_unit(q))) flag |= 1;
+        const double lp = table_log(p), lp1 = table_log(1.0 - p), lq = table_log(q), lq1 = table_log(1.0 - q);
+        double lapu = 0.0, lapv = 0.0, gr = 0.0;
+#pragma unroll
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, y, z, f);
+            const double du = X[n] - u, dv = X[N + n] - v, ih2 = face_ih2(g, f);
+            lapu = fma(du, ih2, lapu);
+            lapv = fma(dv, ih2, lapv);
+            gr = fma(du * du + dv * dv, ih2, gr);
+        }
+        const double eu = u - T[c], ev = v - T[N + c];
+        const double dEu = 0.5 * k.alpha * (1.0 - 2.0 * u) + k.theta * ((lp - lp1) + (lq - lq1)) - k.gamma * lapu;
+        const double dEv = -k.beta * v + k.theta * ((lp - lp1) - (lq - lq1)) - k.gamma * lapv;
+        lam[c] = g.vol * (wE * dEu + wM * eu);
+        lam[N + c] = g.vol * (wE * dEv + wM * ev);
+        const double xl = p * lp + (1.0 - p) * lp1 + q * lq + (1.0 - q) * lq1;
+        const double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v + k.theta * xl + 0.25 * k.gamma * gr;
+        acc[0] += wE * e + 0.5 * wM * (eu * eu + ev * ev);
+        acc[1] += wE * 0.5 * u * (1.0 - u);
+        acc[2] -= wE * 0.5 * v * v;
+        acc[3] += wE * xl;
+        acc[4] += wE * 0.25 * gr;
+    }
+    if (flag) atomicOr(flags, flag);
+#pragma unroll
+    for (int v = 0; v < 5; ++v) {
+        const double t = block_sum_red(acc[v], sh);
+        if (threadIdx.x == 0) red.partial[(size_t)v * RED_BLOCKS + blockIdx.x] = t * g.vol;
+    }
+    finish_reduction(red, 5, sh);
+}
+
+cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, const double* target, double wE,
+                             double wM, double* lam, Red red, int* flags, cudaStream_t s) {
+    cudaError_t e = set_taylor_constants(k.S);
+    if (e != cudaSuccess) return e;
+    if (g.dim == 3) loss_grad_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, target, wE, wM, lam, red, flags);
+    else loss_grad_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, target, wE, wM, lam, red, flags);
     return cudaGetLastError();
 }
 __global__ void table_log_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
@@ -393,8 +527,8 @@ cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream
 }
 
 template cudaError_t launch_linearize<double>(const Geom&, const Coef&, const double*, const double*,
-                                              const double*, Cache<double>, cudaStream_t);
+                                              const double*, Cache<double>, cudaStream_t, int);
 template cudaError_t launch_linearize<float>(const Geom&, const Coef&, const double*, const double*,
-                                             const double*, Cache<float>, cudaStream_t);
+                                             const double*, Cache<float>, cudaStream_t, int);
 
 }  // namespace acac

@@ -160,6 +160,10 @@ struct acac_handle {
     struct Pending { int id; cudaEvent_t a, b; bool owned_by_graph; };
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> pool;
+    // adjoint workspace (allocated on first use): mu, lam, lam2, target (2N doubles each)
+    // and one stencil matrix in the Krylov precision
+    double* adj = nullptr;
+    void* adjJ = nullptr;
     // ensemble (batch > 1): independent member problems, each a batch-1 handle on its
     // own stream; this handle then only owns them, the staging buffer and the pool
     std::vector<acac_handle*> members;
@@ -180,6 +184,13 @@ struct Err {
         cudaError_t e_ = (call);                                                 \
         if (e_ != cudaSuccess) throw Err{e_ == cudaErrorMemoryAllocation ? ACAC_E_NOMEM : ACAC_E_CUDA}; \
     } while (0)
+
+template <typename P>
+void dmalloc(P** ptr, size_t bytes) {
+    void* q = nullptr;
+    CU(cudaMalloc(&q, bytes ? bytes : 16));
+    *ptr = (P*)q;
+}
 
 cudaEvent_t take_event(acac_handle* h) {
     if (!h->pool.empty()) {
@@ -646,6 +657,90 @@ int nks_dispatch(acac_handle* h, double dt, acac_step_info* info) {
     return st;
 }
 
+// ---------------------------------------------------------------- adjoint
+// Reverse-mode derivative of the fixed-dt implicit step F(U^{n+1}, U^n; p) = 0:
+//   J1^T mu = lambda^{n+1},  lambda^n = -J0^T mu,  dL/dp += -mu^T dF/dp,
+// J1 = dF/dU^{n+1}, J0 = dF/dU^n at (U^{n+1}, U^n).  J1^T is formed by transposing the
+// assembled stencil matrix, so GMRES uses the assembled product and the Schwarz/ILU(0)
+// preconditioner factored from the subdomain blocks of J1^T.  FP64 handles only.
+
+size_t stencil_values(const acac_handle* h) { return (size_t)(h->g.dim == 3 ? NSLOT3 : NSLOT) * 4 * h->N; }
+
+void adjoint_buffers(acac_handle* h) {
+    if (!h->adj) dmalloc(&h->adj, 8 * 2 * h->N * 4);
+    if (!h->adjJ) dmalloc(&h->adjJ, stencil_values(h) * h->ksz);
+}
+
+// Linearisation at (X1, h->X0): pass A into G (flags: domain) and the cache of
+// dF/dX1 (wrt_x0 = 0) or dF/dX0 (1), then the assembled matrix into h->adjJ and its
+// transpose into h->J.
+void assemble_transposed(acac_handle* h, const double* X1, double dt, int wrt_x0) {
+    double* J = (double*)h->adjJ;
+    KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 56.0 * h->N, 0.0,
+        launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream, wrt_x0));
+    // -dt puts -1/dt on the diagonal of dF/dX0
+    KLA(ACAC_K_ASSEMBLE, 8.0 * 59.0 * h->N, 0.0,
+        launch_assemble<double>(h->g, h->k, wrt_x0 ? -dt : dt, cache_of<double>(h), J, h->stream));
+    KLA(ACAC_K_VECTOR, 8.0 * 2.0 * stencil_values(h), 0.0, launch_transpose<double>(h->g, J, (double*)h->J, h->stream));
+}
+
+// One adjoint step at (X1, X0) (device, 2N each).  lam_in = lambda^{n+1}; lam_out
+// (may alias lam_in) receives lambda^n; grad[0..3] += -mu^T dF/d(alpha, beta, theta, gamma).
+int adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, const double* lam_in,
+                 double* lam_out, double* grad, double rtol, int* its) {
+    const long long n2 = 2 * (long long)h->N;
+    double* mu = h->adj;
+    CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+    int fl = 0;
+    eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
+    if (fl & 1) return ACAC_E_DOMAIN;
+    // J1^T mu = lambda^{n+1}
+    assemble_transposed(h, X1, dt, 0);
+    int st = factor<double>(h);
+    if (st != ACAC_OK) return st;
+    CU(cudaMemcpyAsync(h->b, lam_in, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+    const acac_params saved = h->p;
+    h->p.jac_mode = ACAC_JAC_ASSEMBLED;   // products with the transposed matrix in h->J
+    h->p.graphs = 0;                      // the captured iterations use the forward product
+    h->p.gmres_rtol = rtol;
+    h->p.gmres_atol = 0.0;
+    int gi = 0;
+    double gr = 0.0;
+    try {
+        st = gmres<double>(h, mu, &gi, &gr);
+    } catch (Err e) {
+        h->p = saved;
+        throw;
+    }
+    h->p = saved;
+    if (its) *its += gi;
+    if (st != ACAC_OK) return st;
+    // -mu^T dF/dp
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    KLA(ACAC_K_VECTOR, 8.0 * 7.0 * h->N, 0.0,
+        launch_param_grad(h->g, h->k, X1, h->X0, h->G, mu, red_to(h, h->red), h->flags, h->stream));
+    read_scalars(h, 4);
+    for (int i = 0; i < 4; ++i) grad[i] += h->host[i];
+    // lambda^n = -J0^T mu
+    assemble_transposed(h, X1, dt, 1);
+    KLA(ACAC_K_SPMV, 8.0 * h->N * 56, 104.0 * h->N, launch_spmv<double>(h->g, (const double*)h->J, mu, h->tmpd, h->stream));
+    KL(ACAC_K_VECTOR, launch_to_krylov<double>(h->tmpd, -1.0, lam_out, n2, h->stream));
+    return ACAC_OK;
+}
+
+// L(X) and dL/dX (into lam), dL/dp explicit part into grad[0..3].
+int loss_and_grad(acac_handle* h, const double* X, const double* target, double wE, double wM, double* loss,
+                  double* lam, double* grad) {
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    KLA(ACAC_K_ENERGY, 8.0 * 6.0 * h->N, 0.0,
+        launch_loss_grad(h->g, h->k, X, target, wE, wM, lam, red_to(h, h->red), h->flags, h->stream));
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    read_scalars(h, 5);
+    if (loss) *loss = h->host[0];
+    for (int i = 0; i < 4; ++i) grad[i] = h->host[1 + i];
+    return *h->host_flags ? ACAC_E_DOMAIN : ACAC_OK;
+}
+
 // ---------------------------------------------------------------- Schwarz tables
 void partition_1d(int n, int P, std::vector<int>& s, std::vector<int>& e) {
     int base = n / P, rem = n % P, pos = 0;
@@ -793,12 +888,6 @@ int acac::validate_params(const acac_params* p) {
 
 namespace {
 
-template <typename P>
-void dmalloc(P** ptr, size_t bytes) {
-    void* q = nullptr;
-    CU(cudaMalloc(&q, bytes ? bytes : 16));
-    *ptr = (P*)q;
-}
 
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
@@ -809,6 +898,8 @@ void free_all(acac_handle* h) {
     if (h->host) cudaFreeHost(h->host);
     if (h->host_flags) cudaFreeHost(h->host_flags);
     if (h->jk_dev) cudaFree(h->jk_dev);
+    if (h->adj) cudaFree(h->adj);
+    if (h->adjJ) cudaFree(h->adjJ);
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->stream) cudaStreamDestroy(h->stream);
@@ -1334,6 +1425,160 @@ int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac
     local.dt = dt;
     if (info) *info = local;
     return st;
+}
+
+int acac_jacobian_x0(acac_handle* h, const double* X1, const double* X0, double dt, void* J) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (!h || !X1 || !X0 || !J || !(dt > 0)) return ACAC_E_ARG;
+    Join join(h);
+    try {
+        int st = linearize_at(h, X1, X0, dt);
+        if (st != ACAC_OK) return st;
+        if (h->mixed) {
+            KL(ACAC_K_LINEARIZE, launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream, 1));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, -dt, cache_of<float>(h), (float*)J, h->stream));
+        } else {
+            KL(ACAC_K_LINEARIZE, launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream, 1));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, -dt, cache_of<double>(h), (double*)J, h->stream));
+        }
+        CU(cudaStreamSynchronize(h->stream));
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_spmv_t(acac_handle* h, const void* J, const void* w, void* y) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (!h || !J || !w || !y) return ACAC_E_ARG;
+    Join join(h);
+    try {
+        adjoint_buffers(h);
+        if (h->mixed) {
+            KL(ACAC_K_VECTOR, launch_transpose<float>(h->g, (const float*)J, (float*)h->adjJ, h->stream));
+            KL(ACAC_K_SPMV, launch_spmv<float>(h->g, (const float*)h->adjJ, (const float*)w, (float*)y, h->stream));
+        } else {
+            KL(ACAC_K_VECTOR, launch_transpose<double>(h->g, (const double*)J, (double*)h->adjJ, h->stream));
+            KL(ACAC_K_SPMV, launch_spmv<double>(h->g, (const double*)h->adjJ, (const double*)w, (double*)y, h->stream));
+        }
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_loss(acac_handle* h, const double* X, const double* target, double w_energy, double w_misfit,
+              double* loss, double* dX, double* grad) {
+    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (!h || !X || !target || !dX) return ACAC_E_ARG;
+    Join join(h);
+    try {
+        double gl[4];
+        const int st = loss_and_grad(h, X, target, w_energy, w_misfit, loss, dX, gl);
+        if (grad)
+            for (int i = 0; i < 4; ++i) grad[i] = gl[i];
+        return st;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, const double* lam1,
+                      double* lam0, double* grad, double rtol, int* gmres_its) {
+    if (is_ensemble(h) || (h && h->mixed)) return ACAC_E_ARG;
+    if (!h || !X1 || !X0 || !lam1 || !lam0 || !(dt > 0) || !(rtol > 0)) return ACAC_E_ARG;
+    Join join(h);
+    try {
+        adjoint_buffers(h);
+        double gl[4] = {0.0, 0.0, 0.0, 0.0};
+        int its = 0;
+        const int st = adjoint_step(h, X1, X0, dt, lam1, lam0, gl, rtol, &its);
+        CU(cudaStreamSynchronize(h->stream));
+        if (grad)
+            for (int i = 0; i < 4; ++i) grad[i] = gl[i];
+        if (gmres_its) *gmres_its = its;
+        return st;
+    } catch (Err e) {
+        return e.code;
+    }
+}
+
+int acac_adjoint(acac_handle* h, const double* u0, const double* v0, int nsteps, double dt, int checkpoint_every,
+                 const double* u_target, const double* v_target, double w_energy, double w_misfit, double rtol,
+                 double* loss, double* du0, double* dv0, double* grad, int* gmres_its) {
+    if (is_ensemble(h) || (h && h->mixed)) return ACAC_E_ARG;
+    if (!h || !u0 || !v0 || !u_target || !v_target || !du0 || !dv0 || nsteps < 1 || !(dt > 0) ||
+        checkpoint_every < 1 || !(rtol > 0))
+        return ACAC_E_ARG;
+    Join join(h);
+    const size_t N = h->N, n2 = 2 * N;
+    const int every = std::min(checkpoint_every, nsteps);
+    const int nckpt = (nsteps + every - 1) / every;
+    double* store = nullptr;   // nckpt checkpoints and U^K, then every + 1 states of one segment
+    struct Free {
+        double** p;
+        ~Free() {
+            if (*p) cudaFree(*p);
+        }
+    } free_store{&store};
+    try {
+        adjoint_buffers(h);
+        dmalloc(&store, 8 * n2 * (size_t)(nckpt + 1 + every + 1));
+        double* seg = store + n2 * (nckpt + 1);
+        double* lam = h->adj + n2;
+        double* tgt = h->adj + 3 * n2;
+        CU(cudaMemcpyAsync(tgt, u_target, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(tgt + N, v_target, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        // forward, keeping every `every`-th state
+        CU(cudaMemcpyAsync(h->X0, u0, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(h->X0 + N, v0, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        int its = 0;
+        auto step_from_X0 = [&](acac_step_info* info) {
+            memset(info, 0, sizeof(*info));
+            return nks_dispatch(h, dt, info);
+        };
+        for (int k = 0; k < nsteps; ++k) {
+            if (k % every == 0)
+                CU(cudaMemcpyAsync(store + n2 * (k / every), h->X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+            acac_step_info info;
+            const int st = step_from_X0(&info);
+            if (st != ACAC_OK) return st;
+            CU(cudaMemcpyAsync(h->X0, h->X, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        }
+        CU(cudaMemcpyAsync(store + n2 * nckpt, h->X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+        double g[4];
+        int st = loss_and_grad(h, h->X0, tgt, w_energy, w_misfit, loss, lam, g);
+        if (st != ACAC_OK) return st;
+        // backward, one segment at a time from its checkpoint
+        for (int c = nckpt - 1; c >= 0; --c) {
+            const int k0 = c * every, k1 = std::min(k0 + every, nsteps);
+            CU(cudaMemcpyAsync(seg, store + n2 * c, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+            CU(cudaMemcpyAsync(h->X0, seg, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+            for (int k = k0; k < k1 - 1; ++k) {
+                acac_step_info info;
+                st = step_from_X0(&info);
+                if (st != ACAC_OK) return st;
+                CU(cudaMemcpyAsync(seg + n2 * (k + 1 - k0), h->X, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+                CU(cudaMemcpyAsync(h->X0, h->X, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
+            }
+            // the segment ends at the next checkpoint (U^K for the last segment)
+            CU(cudaMemcpyAsync(seg + n2 * (k1 - k0), store + n2 * (c + 1), n2 * 8, cudaMemcpyDeviceToDevice,
+                               h->stream));
+            for (int k = k1 - 1; k >= k0; --k) {
+                st = adjoint_step(h, seg + n2 * (k + 1 - k0), seg + n2 * (k - k0), dt, lam, lam, g, rtol, &its);
+                if (st != ACAC_OK) return st;
+            }
+        }
+        CU(cudaMemcpyAsync(du0, lam, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaMemcpyAsync(dv0, lam + N, N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        CU(cudaStreamSynchronize(h->stream));
+        if (grad)
+            for (int i = 0; i < 4; ++i) grad[i] = g[i];
+        if (gmres_its) *gmres_its = its;
+        return ACAC_OK;
+    } catch (Err e) {
+        return e.code;
+    }
 }
 
 static int energy_of(acac_handle* h, const double* X, double* e, double* m) {

@@ -219,4 +219,32 @@ E32 = EnsembleWorkload(
            precision=PREC_MIXED, batch=32, **_COEF),
     steps=50, seed=3, u_mean=0.4, amp=0.05)
 
-WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C4, C4_FP64, C2_UNIT, C3_UNIT, E32)}
+
+
+@dataclass
+class AdjointWorkload(Workload):
+    """K fixed-dt steps from initial_fields(seed), then the loss
+    L = w_energy E~(U^K) + (w_misfit/2) sum |U^K - U*|^2 dx dy against the target
+    U* = initial_fields(target_seed) (same mean and amplitude); checkpoint every
+    `every` steps."""
+
+    target_seed: int = 0
+    every: int = 5
+    w_energy: float = 1.0
+    w_misfit: float = 1.0
+
+    def target(self):
+        return initial_fields(self.params, self.target_seed, self.u_mean, self.amp)
+
+
+# 2D 512x512 periodic, FP64, 20 steps at dt = 1e-3, checkpoint every 5; loss = final
+# energy + misfit to the seeded target; gradients in u0, v0, alpha..gamma.  Mesh spacing
+# h = 1/64 as the other large workloads ([0, 8]^2): on the unit square the forward GMRES
+# stagnates at the first step (the same ILU(0) instability as the *_UNIT workloads).
+C5 = AdjointWorkload(
+    "2d-512x512-periodic-fp64-adjoint",
+    Params(dim=2, n=(512, 512, 1), L=(512 * H64, 512 * H64, 1.0), bc=BC_PERIODIC, dt_mode=DT_FIXED, dt0=1e-3,
+           ras_parts=(8, 8, 1), ras_overlap=1, **_COEF),
+    steps=20, seed=4, u_mean=0.4, amp=0.05, target_seed=104, every=5)
+
+WORKLOADS = {w.name: w for w in (C1, C2, C3, C3_FP64, C4, C4_FP64, C2_UNIT, C3_UNIT, E32, C5)}
