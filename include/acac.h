@@ -222,6 +222,23 @@ int acac_gmres(acac_handle *h, const double *X1, const double *X0, double dt,
 int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
                    acac_step_info *info);
 
+/* ---- autotuning of the Schwarz partition ---------------------------------------- */
+
+/* Time acac_step for candidate Schwarz partitions of the problem *p and return the
+ * fastest in *best (a copy of *p with ras_parts and ras_overlap replaced).  The
+ * candidates are *p itself and near-cubic boxes of owned width 12, 16, 24, 32, 48, 64,
+ * 96, 128, 192 or 240 cells per direction, each with overlap 1 and 2, that acac_create
+ * accepts.  The box shape trades the preconditioner's strength (GMRES iterations)
+ * against the length of the triangular sweeps and the parallelism across boxes, so
+ * each candidate is timed end to end: one untimed step from (u, v) (device, N doubles
+ * each, not modified), then trial_steps timed steps continuing from it.
+ * *best_ms_per_step and *ncandidates (host, may be NULL) report the best time and
+ * the number of candidates tried.  ACAC_E_ARG on bad arguments or batch != 1,
+ * ACAC_E_DIVERGED when no candidate completes its steps.  Synchronises. */
+int acac_autotune(const acac_params *p, const double *u, const double *v, int trial_steps,
+                  void *cuda_stream, acac_params *best, double *best_ms_per_step,
+                  int *ncandidates);
+
 /* ---- adjoint of the implicit step (FP64 handles) -------------------------------- */
 /* There is no adjoint in the paper; these entry points differentiate its fixed-dt
  * scheme (NSOA-1, Sec. 2) in reverse mode.  With F(U^{n+1}, U^n; p) = 0 per step and

@@ -89,6 +89,8 @@ SIGNATURES = {
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "acac_set_coeffs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
+    "acac_autotune": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, _P, ctypes.c_int, _P,
+                                     ctypes.POINTER(acac_params), _PD, _PI]),
     "acac_jacobian_x0": (ctypes.c_int, [_P, _P, _P, _D, _P]),
     "acac_spmv_t": (ctypes.c_int, [_P, _P, _P, _P]),
     "acac_loss": (ctypes.c_int, [_P, _P, _P, _D, _D, _PD, _P, _PD]),
@@ -201,6 +203,26 @@ def acac_log(x, y, stream=None):
         stream = torch.cuda.current_stream()
     _check(_lib().acac_log(_dev(x, torch.float64, None, "x"), _dev(y, torch.float64, x.numel(), "y"),
                            x.numel(), ctypes.c_void_p(stream.cuda_stream)), "acac_log")
+
+
+def acac_autotune(p, u, v, trial_steps=3, stream=None):
+    """Fastest Schwarz partition for the problem p (a workloads.Params) from the state
+    (u, v) (float64 CUDA tensors, not modified).  Returns (params, ms_per_step,
+    ncandidates) with params a copy of p with ras_parts / ras_overlap replaced."""
+    import dataclasses
+
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    n = int(p.n[0]) * int(p.n[1]) * (int(p.n[2]) if p.dim == 3 else 1)
+    cp = to_c_params(p)
+    best = acac_params()
+    ms, nc = ctypes.c_double(), ctypes.c_int()
+    _check(_lib().acac_autotune(ctypes.byref(cp), _dev(u, torch.float64, n, "u"), _dev(v, torch.float64, n, "v"),
+                                int(trial_steps), ctypes.c_void_p(stream.cuda_stream), ctypes.byref(best),
+                                ctypes.byref(ms), ctypes.byref(nc)), "acac_autotune")
+    out = dataclasses.replace(p, ras_parts=tuple(best.ras_parts), ras_overlap=best.ras_overlap)
+    return out, ms.value, nc.value
 
 
 class Solver:

@@ -9,6 +9,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <condition_variable>
 #include <functional>
 #include <mutex>
@@ -1579,6 +1580,73 @@ int acac_adjoint(acac_handle* h, const double* u0, const double* v0, int nsteps,
     } catch (Err e) {
         return e.code;
     }
+}
+
+int acac_autotune(const acac_params* p, const double* u, const double* v, int trial_steps, void* cuda_stream,
+                  acac_params* best, double* best_ms_per_step, int* ncandidates) {
+    if (!p || !u || !v || !best || trial_steps < 1) return ACAC_E_ARG;
+    int st = validate_params(p);
+    if (st != ACAC_OK) return st;
+    if (p->batch != 1) return ACAC_E_ARG;
+    const int dim = p->dim;
+    const size_t N = (size_t)p->n[0] * p->n[1] * (dim == 3 ? p->n[2] : 1);
+    // candidates: the given partition, and near-cubic boxes of owned width W in every
+    // direction for W in a ladder, each with overlap 1 and 2
+    std::vector<acac_params> cand;
+    auto add = [&](const acac_params& q) {
+        if (validate_params(&q) != ACAC_OK) return;
+        for (const acac_params& c : cand)
+            if (c.ras_overlap == q.ras_overlap && c.ras_parts[0] == q.ras_parts[0] &&
+                c.ras_parts[1] == q.ras_parts[1] && (dim == 2 || c.ras_parts[2] == q.ras_parts[2]))
+                return;
+        for (int a = 0; a < dim; ++a) {
+            const int w = (p->n[a] + q.ras_parts[a] - 1) / q.ras_parts[a] + 2 * q.ras_overlap;
+            if (w < 4 || w > 250 || (p->bc == ACAC_BC_PERIODIC && w > p->n[a] - 2)) return;
+        }
+        cand.push_back(q);
+    };
+    add(*p);
+    const int ladder[] = {12, 16, 24, 32, 48, 64, 96, 128, 192, 240};
+    for (int W : ladder)
+        for (int d = 1; d <= 2; ++d) {
+            acac_params q = *p;
+            q.ras_overlap = d;
+            for (int a = 0; a < dim; ++a) q.ras_parts[a] = std::max(1, (p->n[a] + W - 1) / W);
+            add(q);
+        }
+    if (ncandidates) *ncandidates = (int)cand.size();
+    double* X = nullptr;
+    if (cudaMalloc((void**)&X, 2 * N * sizeof(double)) != cudaSuccess) return ACAC_E_NOMEM;
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    double best_ms = -1.0;
+    int rc = ACAC_E_DIVERGED;   // when no candidate completes its trial steps
+    for (const acac_params& q : cand) {
+        acac_handle* h = nullptr;
+        if (acac_create(&q, cuda_stream, &h) != ACAC_OK) continue;
+        // one untimed step from (u, v) (first-use costs: shared-memory limits, graph
+        // capture), then trial_steps timed steps continuing from it: every candidate
+        // follows the same trajectory
+        bool ok = cudaMemcpyAsync(X, u, N * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+                  cudaMemcpyAsync(X + N, v, N * 8, cudaMemcpyDeviceToDevice, s) == cudaSuccess &&
+                  acac_step(h, X, X + N, nullptr) == ACAC_OK && cudaStreamSynchronize(s) == cudaSuccess;
+        double ms = -1.0;
+        if (ok) {
+            const auto t0 = std::chrono::steady_clock::now();
+            for (int k = 0; ok && k < trial_steps; ++k) ok = acac_step(h, X, X + N, nullptr) == ACAC_OK;
+            ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+            ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count() /
+                 trial_steps;
+        }
+        acac_destroy(h);
+        if (ok && (best_ms < 0 || ms < best_ms)) {
+            best_ms = ms;
+            *best = q;
+            rc = ACAC_OK;
+        }
+    }
+    cudaFree(X);
+    if (best_ms_per_step) *best_ms_per_step = best_ms;
+    return rc;
 }
 
 static int energy_of(acac_handle* h, const double* X, double* e, double* m) {

@@ -172,3 +172,26 @@ def test_graph_replay_matches_direct_launches(precision):
     for k in ("ras_apply", "gs_dot", "gs_update"):
         assert out[0][3][k][0] == out[1][3][k][0] > 0, k
         assert out[1][3][k][1] > 0, k
+
+
+def test_autotune_picks_a_valid_partition():
+    """acac_autotune returns one of its candidates (valid for acac_create), the time of
+    its trial steps, and leaves the input state unchanged; the tuned solver then steps
+    to the oracle's result."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    from paper_2007_04560_gb300.acac import acac_autotune
+    p = Params(n=(96, 80, 1), ras_parts=(2, 2, 1), ras_overlap=1, newton_rtol=1e-12)
+    u, v = initial_fields(p, 61, 0.4, 0.05)
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    best, ms, nc = acac_autotune(p, ug, vg, trial_steps=2)
+    torch.cuda.synchronize()
+    assert nc >= 4 and ms > 0
+    assert np.array_equal(host(ug), u.ravel()) and np.array_equal(host(vg), v.ravel())
+    assert best.ras_overlap in (1, 2)
+    with P.Solver(best) as s:
+        s.step(ug, vg)
+    (uo, vo), _ = O.Stepper(p).step(u, v)
+    xo = soa(uo, vo)
+    assert np.linalg.norm(soa(host(ug), host(vg)) - xo) <= 1e-9 * np.linalg.norm(xo)
