@@ -126,8 +126,9 @@ def cpu_baseline(workload_name, precision, steps=1):
         "from workloads import WORKLOADS\n"
         "from oracle import acac_oracle as O\n"
         "w = WORKLOADS[%r]\n"
-        "p = w.params.replace(precision=0)\n"
-        "u, v = w.fields()\n"
+        "one = hasattr(w, 'member_params')  # an ensemble: time member 0\n"
+        "p = (w.member_params(0) if one else w.params).replace(precision=0)\n"
+        "u, v = w.member_fields(0) if one else w.fields()\n"
         "st = O.Stepper(p)\n"
         "t = time.perf_counter()\n"
         "for k in range(%d):\n"
@@ -185,6 +186,17 @@ def run_mine(args, rank, world):
     stream = torch.cuda.current_stream()
     u0, v0 = w.fields()
     N = p.ncells
+    B = int(p.batch)                       # ensemble members (1: one problem)
+
+    def set_member_coeffs(solver):
+        if B > 1:
+            th = w.thetas()
+            for m in range(B):
+                solver.set_coeffs(m, p.alpha, p.beta, float(th[m]), p.gamma, p.rho)
+
+    def report(info):
+        """Per-step report; an ensemble reports member 0's iterations and dt."""
+        return (info[0] if isinstance(info, list) else info).as_dict()
 
     def barrier():
         if world > 1:
@@ -201,6 +213,7 @@ def run_mine(args, rank, world):
 
     # ---- device-resident timed region
     s = P.Solver(p, stream)
+    set_member_coeffs(s)
     u = torch.tensor(u0.ravel(), device=dev)
     v = torch.tensor(v0.ravel(), device=dev)
     for _ in range(args.warmup):
@@ -214,7 +227,7 @@ def run_mine(args, rank, world):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        infos.append(s.step(u, v).as_dict())
+        infos.append(report(s.step(u, v)))
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -229,6 +242,7 @@ def run_mine(args, rank, world):
     e2e = None
     if not args.no_e2e:
         s2 = P.Solver(p, stream)
+        set_member_coeffs(s2)
         uh = torch.tensor(u0.ravel()).pin_memory()
         vh = torch.tensor(v0.ravel()).pin_memory()
         for _ in range(args.warmup):
@@ -242,17 +256,18 @@ def run_mine(args, rank, world):
         el = max_over_ranks(time.perf_counter() - t0)
         barrier()
         s2.close()
-        e2e = {"value": world * args.steps / el, "unit": "steps/s", "h2d_bytes_per_step": 16 * N,
-               "d2h_bytes_per_step": 16 * N}
+        e2e = {"value": world * B * args.steps / el, "unit": "steps/s" if B == 1 else "member-steps/s",
+               "h2d_bytes_per_step": 16 * N * B, "d2h_bytes_per_step": 16 * N * B}
 
     if rank != 0:
         return None
     hbm, src = peaks()
-    steps_per_s = world * args.steps / (ms * 1e-3)
+    steps_per_s = world * B * args.steps / (ms * 1e-3)
     out = {
-        "metric": "NKS time steps/s (one accepted implicit time step per step)",
+        "metric": "NKS time steps/s (one accepted implicit time step per step)" if B == 1 else
+                  "ensemble member time steps/s (every member takes one accepted implicit step per step)",
         "value": steps_per_s,
-        "unit": "steps/s",
+        "unit": "steps/s" if B == 1 else "member-steps/s",
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
@@ -264,11 +279,11 @@ def run_mine(args, rank, world):
         "data": "synthetic (seeded uniform perturbation of a constant state)",
         "config": {"workload": w.name, "grid": list(p.shape[::-1]), "bc": "periodic" if p.bc == 0 else "neumann",
                    "precision": "fp64" if prec == PREC_FP64 else "mixed",
-                   "unknowns": 2 * N, "ras": "%dx%d overlap %d ILU(0) left-RAS" % (p.ras_parts[0], p.ras_parts[1],
+                   "unknowns": 2 * N * B, "members": B, "ras": "%dx%d overlap %d ILU(0) left-RAS" % (p.ras_parts[0], p.ras_parts[1],
                                                                                  p.ras_overlap),
                    "dt_mode": "adaptive" if p.dt_mode == 1 else "fixed",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "1 GPU"},
-        "unknowns_steps_per_s": steps_per_s * 2 * N,
+        "unknowns_steps_per_s": steps_per_s * 2 * N,   # per member for an ensemble
         "iterations": {"newton_per_step": sum(i["newton_its"] for i in infos) / len(infos),
                        "gmres_per_newton": sum(i["gmres_its"] for i in infos) / max(1, sum(i["newton_its"] for i in infos)),
                        "dt_first": infos[0]["dt"], "dt_last": infos[-1]["dt"], "t_end": infos[-1]["t"]},
@@ -306,8 +321,9 @@ def run_reference(args, rank, world):
         "from workloads import WORKLOADS\n"
         "from oracle import acac_oracle as O\n"
         "w = WORKLOADS[%r]\n"
-        "p = w.params.replace(precision=0)\n"
-        "u, v = w.fields()\n"
+        "one = hasattr(w, 'member_params')  # an ensemble: time member 0\n"
+        "p = (w.member_params(0) if one else w.params).replace(precision=0)\n"
+        "u, v = w.member_fields(0) if one else w.fields()\n"
         "st = O.Stepper(p)\n"
         "for k in range(%d):\n"
         "    X, info = st.step(u, v); u, v = X\n"
