@@ -324,7 +324,7 @@ int acac_log(const double *x, double *y, long long n, void *cuda_stream);
 #define ACAC_K_RAS_APPLY     8    /* batched restriction, triangular sweeps, extension */
 #define ACAC_K_DOT           9    /* Gram–Schmidt block dot products                  */
 #define ACAC_K_CGS_UPDATE   10    /* Gram–Schmidt update (and norm)                   */
-#define ACAC_K_REDUCE       11    /* final stage of the reductions                    */
+#define ACAC_K_REDUCE       11    /* unused: reductions finish inside their kernels   */
 #define ACAC_K_VECTOR       12    /* other vector kernels                             */
 #define ACAC_K_ENERGY       13    /* energy and mass                                  */
 #define ACAC_NKERNEL        14
@@ -334,6 +334,11 @@ int acac_log(const double *x, double *y, long long n, void *cuda_stream);
  * synchronisation).  Launch counts are kept whether or not timing is enabled.
  * Synchronises the stream. */
 int acac_profile(acac_handle *h, int enable);
+
+/* As acac_profile, timing only the launches of the kernel classes whose bit
+ * (1 << ACAC_K_*) is set in mask (0: no timing).  Two events per timed launch cost host
+ * time; a mask with only the class of interest keeps that cost off the other launches. */
+int acac_profile_mask(acac_handle *h, unsigned mask);
 
 /* Since the last acac_profile: launches of kernel class `kernel`, their summed
  * event-timed duration in ms (0 unless timing was enabled), and their summed

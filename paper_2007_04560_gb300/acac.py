@@ -86,6 +86,7 @@ SIGNATURES = {
     "acac_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, _P, _D, _P, _PD, _P]),
     "acac_log": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
+    "acac_profile_mask": (ctypes.c_int, [_P, ctypes.c_uint]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "acac_set_coeffs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
@@ -397,8 +398,17 @@ class Solver:
         return L.value, du0, dv0, list(g), its.value
 
     # -- instrumentation
-    def profile(self, enable=True):
-        _check(_lib().acac_profile(self.h, 1 if enable else 0), "acac_profile")
+    def profile(self, enable=True, kernels=None):
+        """Reset the counters; time every launch (enable), or only the named kernel
+        classes (kernels = iterable of names as kernel_stats reports them)."""
+        if kernels is None:
+            _check(_lib().acac_profile(self.h, 1 if enable else 0), "acac_profile")
+            return
+        names = [_lib().acac_kernel_name(k).decode() for k in range(NKERNEL)]
+        mask = 0
+        for k in kernels:
+            mask |= 1 << names.index(k)
+        _check(_lib().acac_profile_mask(self.h, mask if enable else 0), "acac_profile_mask")
 
     def kernel_stats(self):
         """{name: (launches, total_ms, algorithmic_bytes, algorithmic_flops)} per kernel class."""

@@ -114,7 +114,7 @@ struct acac_handle {
     void* jk_dev = nullptr;     // JacK<T> of the current linearisation
     // CUDA graphs of the Arnoldi iterations (index j), captured on first use
     std::vector<IterGraph> graphs;
-    bool graphs_prof = false;   // profiling state the graphs were captured with
+    unsigned graphs_prof = 0;   // timing mask the graphs were captured with
     std::vector<GraphRec>* capture = nullptr;   // non-null while capturing
     int gmres_calls = 0;
     bool mixed;
@@ -154,6 +154,7 @@ struct acac_handle {
     int ls_cuts, n_factor;
     // kernel launch counts and (when enabled) CUDA-event timings per kernel
     bool prof_on;
+    unsigned prof_mask = 0;     // kernel classes timed with events (bit = ACAC_K_*)
     long long launches[ACAC_NKERNEL];
     double kernel_ms[ACAC_NKERNEL];
     double kernel_bytes[ACAC_NKERNEL];   // algorithmic HBM bytes of the counted launches
@@ -226,7 +227,7 @@ struct KScope {
             // inside a graph capture: the accounting happens at every replay, and the
             // events (when profiling) become event-record nodes of the graph
             GraphRec r{id, bytes, flops, nullptr, nullptr};
-            if (h->prof_on) {
+            if (h->prof_on && (h->prof_mask >> id & 1u)) {
                 // events come from the pool, stocked before the capture began
                 if (h->pool.size() < 2) throw Err{ACAC_E_CUDA};
                 r.a = h->pool.back();
@@ -242,7 +243,7 @@ struct KScope {
         h->launches[id]++;
         h->kernel_bytes[id] += bytes;
         h->kernel_flops[id] += flops;
-        if (h->prof_on) {
+        if (h->prof_on && (h->prof_mask >> id & 1u)) {
             cudaEvent_t a = take_event(h);
             b = take_event(h);
             CU(cudaEventRecord(a, h->stream));
@@ -443,9 +444,10 @@ void arnoldi_step_sync(acac_handle* h, int j) {
         prof_collect(h);
         return;
     }
-    if (h->graphs_prof != h->prof_on) {
+    const unsigned timing = h->prof_on ? h->prof_mask : 0u;
+    if (h->graphs_prof != timing) {
         free_graphs(h);
-        h->graphs_prof = h->prof_on;
+        h->graphs_prof = timing;
     }
     if ((int)h->graphs.size() <= j) h->graphs.resize(j + 1);
     IterGraph& G = h->graphs[j];
@@ -1189,11 +1191,13 @@ int acac_log(const double* x, double* y, long long n, void* cuda_stream) {
     return ACAC_OK;
 }
 
-int acac_profile(acac_handle* h, int enable) {
+int acac_profile(acac_handle* h, int enable) { return acac_profile_mask(h, enable ? 0xffffffffu : 0u); }
+
+int acac_profile_mask(acac_handle* h, unsigned mask) {
     if (!h) return ACAC_E_ARG;
     if (is_ensemble(h)) {
         for (acac_handle* m : h->members) {
-            const int st = acac_profile(m, enable);
+            const int st = acac_profile_mask(m, mask);
             if (st != ACAC_OK) return st;
         }
         return ACAC_OK;
@@ -1204,7 +1208,8 @@ int acac_profile(acac_handle* h, int enable) {
     } catch (Err e) {
         return e.code;
     }
-    h->prof_on = enable != 0;
+    h->prof_on = mask != 0;
+    h->prof_mask = mask;
     for (int i = 0; i < ACAC_NKERNEL; ++i) {
         h->launches[i] = 0;
         h->kernel_ms[i] = 0.0;
