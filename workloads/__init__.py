@@ -108,6 +108,25 @@ def random_vector(p: Params, seed: int):
     return np.ascontiguousarray(w[0]), np.ascontiguousarray(w[1])
 
 
+def sinusoidal_fields(p: Params):
+    """The smooth initial state of the paper's 2D convergence test (Sec. 4.1 A):
+    u = 0.4 (sin^2(2 pi x) + cos^2(2 pi y)) + 0.1, v = 0.4 (sin^2(2 pi x) - cos^2(2 pi y)),
+    at the cell centres x_i = (i + 1/2) dx, y_j = (j + 1/2) dy."""
+    nx, ny = p.n[0], p.n[1]
+    x = (np.arange(nx) + 0.5) * (p.L[0] / nx)
+    y = (np.arange(ny) + 0.5) * (p.L[1] / ny)
+    sx = np.sin(2.0 * np.pi * x)[None, :] ** 2
+    cy = np.cos(2.0 * np.pi * y)[:, None] ** 2
+    return np.ascontiguousarray(0.4 * (sx + cy) + 0.1), np.ascontiguousarray(0.4 * (sx - cy))
+
+
+# Coefficients and solver tolerances of the paper's numerical section (Sec. 4: S = 10,
+# eps_r = 1e-6, eps_a = 1e-13, xi_r = 1e-8, xi_a = 1e-14; Sec. 4.1: alpha = 4, beta = 2,
+# gamma = 0.005, theta = 0.1, rho = 0.001).
+PAPER_COEF = dict(alpha=4.0, beta=2.0, gamma=0.005, theta=0.1, rho=0.001, taylor_S=10)
+PAPER_TOL = dict(newton_rtol=1e-6, newton_atol=1e-13, gmres_rtol=1e-8, gmres_atol=1e-14)
+
+
 @dataclass
 class Workload:
     name: str
