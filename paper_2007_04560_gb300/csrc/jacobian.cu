@@ -216,53 +216,103 @@ cudaError_t launch_set_jac(JacK<T>* dst, const Coef& k, double dt, cudaStream_t 
 // the 1-cell ring, dG_v on the tile; then the face fluxes.  Block coordinates give (x, y)
 // without division; neighbours outside the grid are wrapped (periodic) or clamped
 // (Neumann: their face weight is 0).  Algorithmic traffic: w (2), the cache (7) and y (2)
-// per cell.
-constexpr int JT_X = 64, JT_Y = 8, JT_THREADS = 256;
+// per cell.  Each staging phase first issues all of a thread's loads into registers and
+// only then uses them, so that ~30 loads per thread are in flight (the kernel is bound
+// by load latency otherwise).
+constexpr int JT_X = 64, JT_Y = 16, JT_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
                                                               const T* __restrict__ w, T* __restrict__ y) {
     constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
     constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1
+    constexpr int NW = (WX * WY + JT_THREADS - 1) / JT_THREADS;
+    constexpr int NR = (RX * RY + JT_THREADS - 1) / JT_THREADS;
+    constexpr int NO = JT_X * JT_Y / JT_THREADS;
     __shared__ T swu[WY][WX], swv[WY][WX];
     __shared__ T sc[RY][RX], sg[RY][RX], sdg[RY][RX], sdc[RY][RX];
     __shared__ T sdgv[JT_Y][JT_X];
     const int N = g.N;
     const int x0 = blockIdx.x * JT_X, y0 = blockIdx.y * JT_Y;
     const bool per = g.bc == ACAC_BC_PERIODIC;
-    for (int idx = threadIdx.x; idx < WX * WY; idx += JT_THREADS) {
-        const int lx = idx % WX, ly = idx / WX;
-        const int gx = wrap_or_clamp(x0 + lx - 2, g.nx, per), gy = wrap_or_clamp(y0 + ly - 2, g.ny, per);
-        const int gc = gy * g.nx + gx;
-        swu[ly][lx] = w[gc];
-        swv[ly][lx] = w[N + gc];
+    const int tid = threadIdx.x;
+    // G_v of this thread's output cells, needed only at the end
+    T gv[NO];
+#pragma unroll
+    for (int k = 0; k < NO; ++k) {
+        const int idx = tid + k * JT_THREADS;
+        const int gx = x0 + idx % JT_X, gy = y0 + idx / JT_X;
+        gv[k] = (gx < g.nx && gy < g.ny) ? C.Gv[gy * g.nx + gx] : (T)0;
+    }
+    // phase 1: w with a 2-cell halo
+    {
+        T au[NW], av[NW];
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int idx = tid + k * JT_THREADS;
+            au[k] = av[k] = (T)0;
+            if (idx < WX * WY) {
+                const int lx = idx % WX, ly = idx / WX;
+                const int gx = wrap_or_clamp(x0 + lx - 2, g.nx, per), gy = wrap_or_clamp(y0 + ly - 2, g.ny, per);
+                const int gc = gy * g.nx + gx;
+                au[k] = w[gc];
+                av[k] = w[N + gc];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NW; ++k) {
+            const int idx = tid + k * JT_THREADS;
+            if (idx < WX * WY) {
+                swu[idx / WX][idx % WX] = au[k];
+                swv[idx / WX][idx % WX] = av[k];
+            }
+        }
+    }
+    // phase 2 loads (independent of w): the cache on the 1-cell ring
+    T rc[NR], rg[NR], rdu[NR], rxc[NR], rcu[NR], rcv[NR];
+#pragma unroll
+    for (int k = 0; k < NR; ++k) {
+        const int idx = tid + k * JT_THREADS;
+        rc[k] = rg[k] = rdu[k] = rxc[k] = rcu[k] = rcv[k] = (T)0;
+        if (idx < RX * RY) {
+            const int lx = idx % RX, ly = idx / RX;
+            const int cx = wrap_or_clamp(x0 + lx - 1, g.nx, per), cy = wrap_or_clamp(y0 + ly - 1, g.ny, per);
+            const int gc = cy * g.nx + cx;
+            rc[k] = C.c[gc];
+            rg[k] = C.Gu[gc];
+            rdu[k] = C.du[gc];
+            rxc[k] = C.xc[gc];
+            rcu[k] = C.cu[gc];
+            rcv[k] = C.cv[gc];
+        }
     }
     __syncthreads();
     const JacK<T> k = *kp;
     const T hg = k.hg, dvs = k.dvs;
     const T ihx2 = sizeof(T) == 8 ? (T)g.ihx2 : (T)g.ihx2f, ihy2 = sizeof(T) == 8 ? (T)g.ihy2 : (T)g.ihy2f;
-    for (int idx = threadIdx.x; idx < RX * RY; idx += JT_THREADS) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        const int idx = tid + q * JT_THREADS;
+        if (idx >= RX * RY) continue;
         const int lx = idx % RX, ly = idx / RX;
-        const int gx = x0 + lx - 1, gy = y0 + ly - 1;
-        const int cx = wrap_or_clamp(gx, g.nx, per), cy = wrap_or_clamp(gy, g.ny, per);
-        const int gc = cy * g.nx + cx;
         const int wx = lx + 1, wy = ly + 1;             // position in the w tile
         const T wu = swu[wy][wx], wv = swv[wy][wx];
         // Laplacians with the ghost rule (clamped neighbours give zero differences)
         const T lu = (swu[wy][wx - 1] + swu[wy][wx + 1] - (T)2 * wu) * ihx2 + (swu[wy - 1][wx] + swu[wy + 1][wx] - (T)2 * wu) * ihy2;
-        const T du = C.du[gc], xc = C.xc[gc];
-        sc[ly][lx] = C.c[gc];
-        sg[ly][lx] = C.Gu[gc];
-        sdg[ly][lx] = du * wu + xc * wv - hg * lu;
-        sdc[ly][lx] = C.cu[gc] * wu + C.cv[gc] * wv;
+        sc[ly][lx] = rc[q];
+        sg[ly][lx] = rg[q];
+        sdg[ly][lx] = rdu[q] * wu + rxc[q] * wv - hg * lu;
+        sdc[ly][lx] = rcu[q] * wu + rcv[q] * wv;
         if (lx >= 1 && lx <= JT_X && ly >= 1 && ly <= JT_Y) {
             const T lv = (swv[wy][wx - 1] + swv[wy][wx + 1] - (T)2 * wv) * ihx2 + (swv[wy - 1][wx] + swv[wy + 1][wx] - (T)2 * wv) * ihy2;
-            sdgv[ly - 1][lx - 1] = xc * wu + (du + dvs) * wv - hg * lv;
+            sdgv[ly - 1][lx - 1] = rxc[q] * wu + (rdu[q] + dvs) * wv - hg * lv;
         }
     }
     __syncthreads();
     const T idt = k.idt, irho = k.irho, half = (T)0.5;
-    for (int idx = threadIdx.x; idx < JT_X * JT_Y; idx += JT_THREADS) {
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+        const int idx = tid + q * JT_THREADS;
         const int tx = idx % JT_X, ty = idx / JT_X;
         const int gx = x0 + tx, gy = y0 + ty;
         if (gx >= g.nx || gy >= g.ny) continue;
@@ -277,7 +327,7 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK
         }
         const int c = gy * g.nx + gx;
         y[c] = swu[ty + 2][tx + 2] * idt - div;
-        y[N + c] = swv[ty + 2][tx + 2] * idt + (dcc * C.Gv[c] + cc * sdgv[ty][tx]) * irho;
+        y[N + c] = swv[ty + 2][tx + 2] * idt + (dcc * gv[q] + cc * sdgv[ty][tx]) * irho;
     }
 }
 

@@ -72,15 +72,18 @@ cudaError_t set_taylor_constants(int) {
 //     ln(1 + u) = u - u^2/2 + u^3/3 - ... (terms to u^7; the next is below 2^-67 |u|).
 // ln 2 is split into a 42-bit head (so that e * head is exact) and a tail.  Arguments
 // that are not positive normal numbers go to the library logarithm.  The GPU tests
-// compare it with the library logarithm over the arguments the kernels use.
+// compare it with the library logarithm over the arguments the kernels use.  The range
+// test and F are formed on the bit patterns (integer instructions): on this GPU every
+// FP64 instruction costs an FP64-pipe slot, and those bound the kernels that call this.
 __device__ __forceinline__ double table_log(double x) {
-    if (!(x >= 2.2250738585072014e-308 && x <= 1.7976931348623157e308)) return log(x);
     const long long bits = __double_as_longlong(x);
+    // positive normal numbers: bits in [bits(DBL_MIN), bits(DBL_MAX)]
+    if ((unsigned long long)(bits - 0x0010000000000000LL) >= 0x7fe0000000000000ULL) return log(x);
     const int e = (int)((bits >> 52) & 0x7ff) - 1023;
     const long long mb = (bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL;
     const double m = __longlong_as_double(mb);
     const int j = (int)((mb >> 45) & 0x7f) + (int)((mb >> 44) & 1);      // nearest j/128
-    const double F = 1.0 + (double)j * 0.0078125;
+    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 45));   // 1 + j/128
     const double u = (m - F) * c_log_invF[j];
     const double u2 = u * u;
     // -1/2 + u (1/3 + u (-1/4 + u (1/5 + u (-1/6 + u / 7))))
@@ -110,7 +113,7 @@ __device__ __forceinline__ double series_P(double r, int K) {
 // the K-term sum then equals the S-term sum of Lemma 2.2 up to FP64 rounding.
 __device__ __forceinline__ int series_terms(double rmax_lane, int S) {
     // non-negative floats order like their bit patterns
-    const unsigned bits = __float_as_uint((float)fmin(rmax_lane, 0.5));
+    const unsigned bits = __float_as_uint((float)rmax_lane < 0.5f ? (float)rmax_lane : 0.5f);
     const float r = __uint_as_float(__reduce_max_sync(0xffffffffu, bits));
     if (r <= 0.0f) return 1;
     if (r >= 0.25f) return S;
@@ -138,27 +141,52 @@ __device__ __forceinline__ float series_R<float>(float r, int S) {
 // (Lemma 2.2, Eq. D2-1, combination f_S(zeta,sigma) - f_S(1-zeta,sigma)):
 //   ln(zeta/(1-zeta)) - sum_k [(sigma/zeta)^{2k} - (sigma/(1-zeta))^{2k}] / ((2k)(2k+1)).
 // The squares ra = (sigma/zeta)^2, rb = (sigma/(1-zeta))^2 and the log argument are
-// returned first so that the caller can pick the warp-uniform term count.
+// formed first (series_args2) so that the caller can pick the warp-uniform term count.
 struct SeriesArgs {
     double ra, rb, ratio;
 };
-__device__ __forceinline__ SeriesArgs series_args(double zeta, double sigma) {
-    const double om = 1.0 - zeta;
-    const double inv = 1.0 / (zeta * om);
-    const double a = sigma * om * inv;      // sigma / zeta
-    const double b = sigma * zeta * inv;    // sigma / (1 - zeta)
-    return SeriesArgs{a * a, b * b, zeta * zeta * inv};
-}
 __device__ __forceinline__ double phi_series(const SeriesArgs& s, int K) {
     return table_log(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
+}
+
+// series_args for p and q with one division: 1/(zp(1-zp)) and 1/(zq(1-zq)) from the
+// reciprocal of their product (which stays far above the underflow threshold for any
+// state that is not within 1e-140 of a pure phase; such states take two divisions).
+__device__ __forceinline__ void series_args2(double zp, double sp, double zq, double sq, SeriesArgs& ap,
+                                             SeriesArgs& aq) {
+    const double omp = 1.0 - zp, omq = 1.0 - zq;
+    const double Pp = zp * omp, Pq = zq * omq;
+    const double PP = Pp * Pq;
+    double invp, invq;
+    if (PP > 1e-280) {
+        const double D = 1.0 / PP;
+        invp = Pq * D;
+        invq = Pp * D;
+    } else {
+        invp = 1.0 / Pp;
+        invq = 1.0 / Pq;
+    }
+    const double tp = zp * invp, up = omp * invp;      // 1/(1-zp), 1/zp
+    const double tq = zq * invq, uq = omq * invq;
+    const double a1 = sp * up, b1 = sp * tp, a2 = sq * uq, b2 = sq * tq;
+    ap = SeriesArgs{a1 * a1, b1 * b1, zp * tp};
+    aq = SeriesArgs{a2 * a2, b2 * b2, zq * tq};
+}
+
+// max of non-negative doubles (their bit patterns order like the values)
+__device__ __forceinline__ double max_nonneg(double a, double b, double c, double d) {
+    long long x = __double_as_longlong(a), y = __double_as_longlong(b);
+    const long long z = __double_as_longlong(c), w = __double_as_longlong(d);
+    x = x > y ? x : y;
+    x = x > z ? x : z;
+    return __longlong_as_double(x > w ? x : w);
 }
 
 // d phi^S / d(end value) where zeta and sigma both move by 1/2:
 //   1/2 [ (1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta) ],
 // evaluated in the Jacobian's precision T (zeta, 1 - zeta and sigma formed in double).
 template <typename T>
-__device__ __forceinline__ T dphi_series(double zeta_d, double sigma_d, int S) {
-    const T zeta = (T)zeta_d, om = (T)(1.0 - zeta_d), sigma = (T)sigma_d;
+__device__ __forceinline__ T dphi_series(T zeta, T om, T sigma, int S) {
     const T iz = (T)1 / zeta, io = (T)1 / om;
     const T a = sigma * iz, b = sigma * io;
     const T Ra = series_R<T>(a * a, S), Rb = series_R<T>(b * b, S);
@@ -191,29 +219,31 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         int x, y, z;
         decode_cell<DIM>(g, cc, x, y, z);
         const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
-        // Laplacians of u1 + u0 and v1 + v0 (G3): face differences, ghost = clamp
+        const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
+        // Laplacians of u1 + u0 and v1 + v0 (G3), per axis (S_- + S_+ - 2 S) / h^2; a
+        // clamped (Neumann ghost) neighbour is the cell itself and adds nothing
         double lu = 0.0, lv = 0.0;
-        const double su = u1 + u0, sv = v1 + v0;
 #pragma unroll
-        for (int f = 0; f < 2 * DIM; ++f) {
-            const double ih2 = face_ih2(g, f);
-            const int n = face_nb<DIM>(g, x, y, z, f);
-            lu = fma(Xu[n] + Pu[n] - su, ih2, lu);
-            lv = fma(Xv[n] + Pv[n] - sv, ih2, lv);
+        for (int d = 0; d < DIM; ++d) {
+            const double ih2 = face_ih2(g, 2 * d);
+            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+            lu = fma(fma(-2.0, su, (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np])), ih2, lu);
+            lv = fma(fma(-2.0, sv, (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np])), ih2, lv);
         }
-        // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma)
-        const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
-        const double zp = 0.5 * (p1 + p0), sp = 0.5 * (p1 - p0);
-        const double zq = 0.5 * (q1 + q0), sq = 0.5 * (q1 - q0);
+        // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma);
+        // the increments come from the differences du, dv (exact for nearby states)
+        const double zp = 0.5 * (su + sv), sp = 0.5 * (du + dv);
+        const double zq = 0.5 * (su - sv), sq = 0.5 * (du - dv);
         const bool ok = in_unit(zp) && in_unit(zq);
         if (live && !ok) flag |= 1;
-        const SeriesArgs ap = series_args(ok ? zp : 0.5, sp);
-        const SeriesArgs aq = series_args(ok ? zq : 0.5, sq);
-        const int K = series_terms(fmax(fmax(ap.ra, ap.rb), fmax(aq.ra, aq.rb)), k.S);
+        SeriesArgs ap, aq;
+        series_args2(ok ? zp : 0.5, sp, ok ? zq : 0.5, sq, ap, aq);
+        const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
         double phi = phi_series(ap, K), psi = phi_series(aq, K);
         if (!ok) { phi = 0.0; psi = 0.0; }
-        const double Gu = -0.5 * k.alpha * (su - 1.0) + k.theta * (phi + psi) - 0.5 * k.gamma * lu;
-        const double Gv = -0.5 * k.beta * sv + k.theta * (phi - psi) - 0.5 * k.gamma * lv;
+        const double ha = 0.5 * k.alpha, hgn = -0.5 * k.gamma;
+        const double Gu = fma(hgn, lu, fma(k.theta, phi + psi, fma(-ha, su, ha)));
+        const double Gv = fma(hgn, lv, fma(k.theta, phi - psi, -0.5 * k.beta * sv));
         const double ub = 0.5 * su, vb = 0.5 * sv;
         if (live) {
             a.G[c] = Gu;
@@ -355,15 +385,23 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
                                                         double ssign) {
     const int N = g.N;
     const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
+    const T sgn = (T)ssign;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
-        const double zp = 0.5 * ((u1 + v1) + (u0 + v0)), sp = 0.5 * ((u1 + v1) - (u0 + v0));
-        const double zq = 0.5 * ((u1 - v1) + (u0 - v0)), sq = 0.5 * ((u1 - v1) - (u0 - v0));
-        const T ub = (T)(0.5 * (u1 + u0)), vb = (T)(0.5 * (v1 + v0));
+        // sums and differences in double (the increments cancel), then precision T:
+        // 2 zeta_p = su + sv, 2 (1 - zeta_p) = 2 - (su + sv), 2 sigma_p = du + dv, and for q
+        // the same with -sv, -dv
+        const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
+        const double zp2 = su + sv, zq2 = su - sv;
+        const T half = (T)0.5;
+        const T zp = half * (T)zp2, omp = half * (T)(2.0 - zp2), zq = half * (T)zq2, omq = half * (T)(2.0 - zq2);
+        const T duT = (T)du, dvT = (T)dv;
+        const T sp = half * (duT + dvT), sq = half * (duT - dvT);
+        const T ub = half * (T)su, vb = half * (T)sv;
         const T w = (T)0.25 - vb * vb;
         // ssign = -1: derivative in the start value (phi^S is even in sigma)
-        const T A = theta * dphi_series<T>(zp, ssign * sp, k.S);
-        const T B = theta * dphi_series<T>(zq, ssign * sq, k.S);
+        const T A = theta * dphi_series<T>(zp, omp, sgn * sp, k.S);
+        const T B = theta * dphi_series<T>(zq, omq, sgn * sq, k.S);
         C.c[c] = (T)G[2 * N + c];
         C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ub) * w;
         C.cv[c] = -ub * ((T)1 - ub) * vb;
@@ -427,9 +465,9 @@ __global__ void __launch_bounds__(256) param_grad_kernel(Geom g, Coef k, const d
         const double zq = 0.5 * (q1 + q0), sq = 0.5 * (q1 - q0);
         const bool ok = in_unit(zp) && in_unit(zq);
         if (live && !ok) flag |= 1;
-        const SeriesArgs ap = series_args(ok ? zp : 0.5, sp);
-        const SeriesArgs aq = series_args(ok ? zq : 0.5, sq);
-        const int K = series_terms(fmax(fmax(ap.ra, ap.rb), fmax(aq.ra, aq.rb)), k.S);
+        SeriesArgs ap, aq;
+        series_args2(ok ? zp : 0.5, sp, ok ? zq : 0.5, sq, ap, aq);
+        const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
         const double phi = phi_series(ap, K), psi = phi_series(aq, K);
         if (live && ok) {
             acc[0] += 0.5 * (su - 1.0) * qu;
