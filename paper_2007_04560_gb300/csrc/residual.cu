@@ -111,15 +111,20 @@ __device__ __forceinline__ double series_P(double r, int K) {
 // of every lane add up to less than 2^-60 of that lane's first term (the
 // coefficients decrease, and r^K <= 2^-60 bounds the tail by a geometric series):
 // the K-term sum then equals the S-term sum of Lemma 2.2 up to FP64 rounding.
-__device__ __forceinline__ int series_terms(double rmax_lane, int S) {
+// The same with a tail below 2^-bits (60 for double; 26 for the float Jacobian of the
+// mixed form).  Every lane of the warp must call it.
+__device__ __forceinline__ int series_terms_bits(float rmax_lane, int S, float bits) {
     // non-negative floats order like their bit patterns
-    const unsigned bits = __float_as_uint((float)rmax_lane < 0.5f ? (float)rmax_lane : 0.5f);
-    const float r = __uint_as_float(__reduce_max_sync(0xffffffffu, bits));
+    const unsigned ub = __float_as_uint(rmax_lane < 0.5f ? rmax_lane : 0.5f);
+    const float r = __uint_as_float(__reduce_max_sync(0xffffffffu, ub));
     if (r <= 0.0f) return 1;
     if (r >= 0.25f) return S;
-    // smallest K with r^K * (1 + r + r^2 + ...) <= 2^-60, i.e. K >= (60 + log2(1/(1-r))) / log2(1/r)
-    const int K = (int)ceilf((60.0f + 0.5f) / -log2f(r));
+    // smallest K with r^K * (1 + r + r^2 + ...) <= 2^-bits, i.e. K >= (bits + log2(1/(1-r))) / log2(1/r)
+    const int K = (int)ceilf((bits + 0.5f) / -log2f(r));
     return K < 1 ? 1 : (K > S ? S : K);
+}
+__device__ __forceinline__ int series_terms(double rmax_lane, int S) {
+    return series_terms_bits((float)rmax_lane, S, 60.0f);
 }
 // sum_{k=1..S} r^(k-1) / (2k+1), Horner form (in the precision T of the Jacobian).
 template <typename T>
@@ -182,15 +187,35 @@ __device__ __forceinline__ double max_nonneg(double a, double b, double c, doubl
     return __longlong_as_double(x > w ? x : w);
 }
 
-// d phi^S / d(end value) where zeta and sigma both move by 1/2:
+// d phi^S / d(end value) where zeta and sigma both move by 1/2, for p and q at once:
 //   1/2 [ (1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta) ],
-// evaluated in the Jacobian's precision T (zeta, 1 - zeta and sigma formed in double).
+// a = sigma/zeta, b = sigma/(1-zeta), in the Jacobian's precision T.  The four
+// reciprocals come from one division; in double R is summed to a warp-uniform K terms
+// whose omitted tail is below 2^-60 of its first term (every lane of the warp must call
+// it), in float to all S terms.
 template <typename T>
-__device__ __forceinline__ T dphi_series(T zeta, T om, T sigma, int S) {
-    const T iz = (T)1 / zeta, io = (T)1 / om;
-    const T a = sigma * iz, b = sigma * io;
-    const T Ra = series_R<T>(a * a, S), Rb = series_R<T>(b * b, S);
-    return (T)0.5 * (((T)1 + a * a * Ra - a * Ra) * iz + ((T)1 + b * b * Rb + b * Rb) * io);
+__device__ __forceinline__ void dphi_pair(T zp, T omp, T sp, T zq, T omq, T sq, int S, T& dp, T& dq) {
+    const T Pp = zp * omp, Pq = zq * omq, PP = Pp * Pq;
+    T invp, invq;
+    if (PP > (sizeof(T) == 8 ? (T)1e-280 : (T)1e-30)) {
+        const T D = (T)1 / PP;
+        invp = Pq * D;
+        invq = Pp * D;
+    } else {
+        invp = (T)1 / Pp;
+        invq = (T)1 / Pq;
+    }
+    const T izp = omp * invp, iop = zp * invp, izq = omq * invq, ioq = zq * invq;
+    const T a1 = sp * izp, b1 = sp * iop, a2 = sq * izq, b2 = sq * ioq;
+    const T ra1 = a1 * a1, rb1 = b1 * b1, ra2 = a2 * a2, rb2 = b2 * b2;
+    // FP32 sums all S terms: its FMAs cost less than the vote
+    const int K = sizeof(T) == 8 ? series_terms_bits((float)max_nonneg((double)ra1, (double)rb1, (double)ra2,
+                                                                       (double)rb2), S, 60.0f)
+                                 : S;
+    const T R1 = series_R<T>(ra1, K), R2 = series_R<T>(rb1, K), R3 = series_R<T>(ra2, K), R4 = series_R<T>(rb2, K);
+    const T one = (T)1, half = (T)0.5;
+    dp = half * ((one + ra1 * R1 - a1 * R1) * izp + (one + rb1 * R2 + b1 * R2) * iop);
+    dq = half * ((one + ra2 * R3 - a2 * R3) * izq + (one + rb2 * R4 + b2 * R4) * ioq);
 }
 
 // ---------------------------------------------------------------- pass A
@@ -386,7 +411,13 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
     const int N = g.N;
     const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
     const T sgn = (T)ssign;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+    // uniform trip count: every lane of a warp takes part in the term-count vote
+    const int stride = gridDim.x * blockDim.x;
+    const int iters = (N + stride - 1) / stride;
+    for (int it = 0; it < iters; ++it) {
+        const int c0 = it * stride + blockIdx.x * blockDim.x + threadIdx.x;
+        const bool live = c0 < N;
+        const int c = live ? c0 : N - 1;
         const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
         // sums and differences in double (the increments cancel), then precision T:
         // 2 zeta_p = su + sv, 2 (1 - zeta_p) = 2 - (su + sv), 2 sigma_p = du + dv, and for q
@@ -400,8 +431,10 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
         const T ub = half * (T)su, vb = half * (T)sv;
         const T w = (T)0.25 - vb * vb;
         // ssign = -1: derivative in the start value (phi^S is even in sigma)
-        const T A = theta * dphi_series<T>(zp, omp, sgn * sp, k.S);
-        const T B = theta * dphi_series<T>(zq, omq, sgn * sq, k.S);
+        T dp, dq;
+        dphi_pair<T>(zp, omp, sgn * sp, zq, omq, sgn * sq, k.S, dp, dq);
+        if (!live) continue;
+        const T A = theta * dp, B = theta * dq;
         C.c[c] = (T)G[2 * N + c];
         C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ub) * w;
         C.cv[c] = -ub * ((T)1 - ub) * vb;
