@@ -90,6 +90,10 @@ typedef struct acac_params {
     int    cgs_refine;          /* 1: Gram–Schmidt applied twice (CGS2), 0: once         */
     int    graphs;              /* 1: replay each GMRES iteration from a captured CUDA
                                    graph (same kernels and results as 0: direct launches) */
+    int    ras_window;          /* 2D Schwarz apply: 0 choose, 1 keep only the last wavefront
+                                   levels in shared memory (forward result in global
+                                   scratch), 2 keep the whole box vector (shared memory when
+                                   it fits, else global); same results                    */
 } acac_params;
 
 /* Per-step report. */

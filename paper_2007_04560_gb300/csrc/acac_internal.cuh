@@ -255,8 +255,10 @@ struct RasLaunch {
     int threads;         // consumer warps (2 threads per cell of the widest level) + 1 producer warp
     int stage_elems;     // elements per stage (>= 28 x the largest level)
     int stage_off;       // byte offset of the stages (after mbarriers and level table)
-    int vec_off;         // byte offset of the box vector when it is in shared memory
+    int vec_off;         // byte offset of the box vector (or of the level window) in shared memory
     size_t smem_bytes;   // dynamic shared memory per CTA
+    int window;          // 1: windowed apply (last levels in shared memory, forward result in global)
+    int win_cells;       // cells per window level (the widest level)
 };
 
 // Checks of acac_create (sizes, coefficients, partition, enumerations).

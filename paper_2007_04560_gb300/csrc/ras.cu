@@ -433,18 +433,205 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
     }
 }
 
+// Windowed variant for boxes whose vector does not fit shared memory at two CTAs per SM
+// (e.g. 132 x 132 boxes): every lower neighbour of a level-l cell lies on levels l-1..l-4
+// and every upper neighbour on l+1..l+4, so shared memory keeps only the last RAS_WIN
+// levels of the sweep's values (slot (l mod RAS_WIN), position j - jmin(l)).  The forward
+// sweep also writes its result level-major to global scratch (coalesced), where the
+// backward sweep reads it back one level ahead; r is gathered per level, one level
+// ahead, and z written per level.  Same pipeline, barrier and bounded waits as above.
+constexpr int RAS_WIN = 5;
+
+template <typename T>
+__global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                            const int* __restrict__ lev_off,
+                                                            const T* __restrict__ coef, const T* __restrict__ r,
+                                                            T* __restrict__ z, int ras_type, T* __restrict__ gscratch,
+                                                            RasLaunch L, int* err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_cabort, s_pabort;
+    __shared__ int s_issued, s_consumed;
+    const SubInfo sd = subs[blockIdx.x];
+    const int N = g.N;
+    const int W = sd.W, H = sd.H;
+    const int nlev = sd.nlev;
+    const int nst = 2 * nlev;
+    const int nbuf = L.nbuf;
+    const int mc = L.win_cells;
+    const int ncons = blockDim.x - 32;
+    const bool producer = threadIdx.x >= ncons;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + RAS_MAXBUF;
+    int* lo = reinterpret_cast<int*>(smem_raw + 16 * RAS_MAXBUF);
+    T* stages = reinterpret_cast<T*>(smem_raw + L.stage_off);
+    T* win = reinterpret_cast<T*>(smem_raw + L.vec_off);          // [RAS_WIN][mc][2]
+    T* yg = gscratch + 2 * (size_t)sd.vec_base;                   // level-major forward result
+    const T* cbase = coef + sd.coef_base;
+
+    for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
+    if (threadIdx.x == 0) {
+        s_cabort = 0;
+        s_pabort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(smem_addr(&full[b]), 1);
+            mbar_init(smem_addr(&empty[b]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int k) {
+        const bool fwd = k < nlev;
+        const int l = fwd ? k : nst - 1 - k;
+        const int cnt = lo[l + 1] - lo[l];
+        const T* src = cbase + (long long)lo[l] * NCOEF + (fwd ? 0 : (long long)cnt * CREC);
+        const uint32_t bytes = (uint32_t)(CREC * cnt * sizeof(T));
+        const int b = k % nbuf;
+        const uint32_t bar = smem_addr(&full[b]);
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(stages + (size_t)b * L.stage_elems), src, bytes, bar);
+    };
+    if (threadIdx.x == ncons) {
+        const int first = nbuf < nst ? nbuf : nst;
+        for (int k = 0; k < first; ++k) issue(k);
+        s_issued = first;
+    }
+
+    if (producer) {
+        if (threadIdx.x == ncons) {
+            for (int k = nbuf; k < nst; ++k) {
+                const int b = k % nbuf;
+                if (!mbar_wait_bounded(smem_addr(&empty[b]), (uint32_t)(((k / nbuf) - 1) & 1))) {
+                    s_pabort = 1;
+                    break;
+                }
+                issue(k);
+                s_issued = k + 1;
+            }
+        }
+    } else {
+        const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+        // value of the neighbour (i2, j2) of the current sweep: the window slot of its level,
+        // zero outside the box
+        auto nbv = [&](int i2, int j2) -> V2<T> {
+            if (i2 < 0 || i2 >= W || j2 < 0 || j2 >= H) return V2<T>{(T)0, (T)0};
+            const int l2 = i2 + 2 * j2;
+            const int m2 = j2 - level_jmin(l2, W);
+            return reinterpret_cast<const V2<T>*>(win)[(l2 % RAS_WIN) * mc + m2];
+        };
+        // this thread's row of the restricted r at cell m of level l (0 if none)
+        auto r_at = [&](int l) -> T {
+            if (l >= nlev || m >= lo[l + 1] - lo[l]) return (T)0;
+            const int j = level_jmin(l, W) + m, i = l - 2 * j;
+            if (ras_type == ACAC_RAS_RIGHT &&
+                !(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1))
+                return (T)0;
+            return r[(size_t)rr * N + box_cell(g, sd, i, j)];
+        };
+        T pre = r_at(0);   // operand prefetched for the next level: r (forward), y (backward)
+        int k = 0;
+        for (; k < nst; ++k) {
+            const int b = k % nbuf;
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
+            const bool fwd = k < nlev;
+            const int l = fwd ? k : nst - 1 - k;
+            const int cnt = lo[l + 1] - lo[l];
+            const int j = level_jmin(l, W) + m, i = l - 2 * j;
+            const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
+            const bool act = m < cnt && landed;
+            const int slot = (l % RAS_WIN) * mc + m;
+            const T cur = pre;
+            if (fwd) {
+                if (l + 1 < nlev) pre = r_at(l + 1);
+                T y = (T)0;
+                if (act) {
+                    T a0 = cur, a1 = (T)0;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = nbv(i + lower_dx(q), j + lower_dy(q));
+                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                    y = a0 + a1;
+                    win[2 * slot + rr] = y;
+                    yg[2 * (size_t)(lo[l] + m) + rr] = y;
+                }
+                if (l + 1 == nlev) pre = y;   // the first backward level is this one
+            } else {
+                if (l > 0) pre = m < lo[l] - lo[l - 1] ? yg[2 * (size_t)(lo[l - 1] + m) + rr] : (T)0;
+                T a0 = (T)0, a1 = (T)0;
+                if (act) {
+                    a0 = cur;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const V2<T> nb = nbv(i + upper_dx(q), j + upper_dy(q));
+                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
+                        T& acc = q < 3 ? a0 : a1;
+                        acc = fma(-c0, nb.x, acc);
+                        acc = fma(-c1, nb.y, acc);
+                    }
+                }
+                const T s_me = a0 + a1;
+                const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
+                if (act) {
+                    const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
+                    const T zc = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
+                    win[2 * slot + rr] = zc;
+                    const int gc = box_cell(g, sd, i, j);
+                    if (ras_type == ACAC_RAS_LEFT) {
+                        if (i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)
+                            z[(size_t)rr * N + gc] = zc;
+                    } else {
+                        atomicAdd(&z[(size_t)rr * N + gc], zc);
+                    }
+                }
+            }
+            uint32_t gave_up;
+            asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
+            if (gave_up) {
+                if (threadIdx.x == 0) s_cabort = 1;
+                break;
+            }
+            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[b]));
+        }
+        if (threadIdx.x == 0) s_consumed = k;
+    }
+    __syncthreads();
+    if (s_cabort || s_pabort) {
+        if (threadIdx.x == 0) {
+            for (int kk = s_consumed; kk < s_issued; ++kk)
+                mbar_wait_bounded(smem_addr(&full[kk % nbuf]), (uint32_t)((kk / nbuf) & 1));
+            atomicOr(err, 8);
+        }
+    }
+}
+
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
     static std::atomic<size_t> attr_bytes{0};
-    {
+    if (!L.window) {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
         if (e != cudaSuccess) return e;
+    }
+    if (L.window) {
+        static std::atomic<size_t> win_bytes{0};
+        cudaError_t e = ensure_smem_limit((const void*)ras_apply_win_kernel<T>, L.smem_bytes, &win_bytes);
+        if (e != cudaSuccess) return e;
+        ras_apply_win_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch,
+                                                                    L, err);
+        return cudaGetLastError();
     }
     ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
                                                             err);

@@ -886,6 +886,7 @@ int acac::validate_params(const acac_params* p) {
     if (p->jac_mode != ACAC_JAC_MATFREE && p->jac_mode != ACAC_JAC_ASSEMBLED) return ACAC_E_ARG;
     if (p->batch < 1 || p->batch > ACAC_MAX_BATCH) return ACAC_E_ARG;
     if (p->graphs != 0 && p->graphs != 1) return ACAC_E_ARG;
+    if (p->ras_window < 0 || p->ras_window > 2) return ACAC_E_ARG;
     return ACAC_OK;
 }
 
@@ -1119,7 +1120,23 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             // fit per CTA, else one CTA per SM with up to RAS_MAXBUF stages.
             bool vec_in_smem = false;
             const size_t half = 113 * 1024;
-            if (L.stage_off + vec_bytes + 3 * stage_bytes <= half) {
+            const bool full_fits2 = L.stage_off + vec_bytes + 3 * stage_bytes <= half;
+            // windowed apply (the last 5 levels in shared memory, the forward result in
+            // global scratch) when the box vector does not fit two CTAs per SM, or on request
+            L.window = p->ras_window == 1 || (p->ras_window == 0 && !full_fits2);
+            L.win_cells = h->ras_maxcnt;
+            if (L.window) {
+                // aim at three CTAs per SM with at least 4 stages each
+                const size_t win_bytes = r128((size_t)5 * h->ras_maxcnt * 2 * ks);
+                const size_t third = 74 * 1024;
+                const size_t room = third > L.stage_off + win_bytes ? third - L.stage_off - win_bytes : 0;
+                L.nbuf = (int)std::max<size_t>(4, std::min<size_t>(RAS_MAXBUF, room / stage_bytes));
+                L.vec_off = (int)(L.stage_off + (size_t)L.nbuf * L.stage_elems * ks);
+                L.smem_bytes = L.vec_off + win_bytes;
+                size_t tot = 0;
+                for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
+                dmalloc(&h->gscratch, tot * 2 * ks);
+            } else if (L.stage_off + vec_bytes + 3 * stage_bytes <= half) {
                 L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (half - L.stage_off - vec_bytes) / stage_bytes);
                 vec_in_smem = true;
             } else if (L.stage_off + vec_bytes + 4 * stage_bytes <= cap) {
@@ -1128,12 +1145,14 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             } else {
                 L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (cap - L.stage_off) / stage_bytes);
             }
-            L.vec_off = (int)(L.stage_off + (size_t)L.nbuf * L.stage_elems * ks);
-            L.smem_bytes = L.vec_off + (vec_in_smem ? vec_bytes : 0);
-            if (!vec_in_smem) {
-                size_t tot = 0;
-                for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
-                dmalloc(&h->gscratch, tot * 2 * ks);
+            if (!L.window) {
+                L.vec_off = (int)(L.stage_off + (size_t)L.nbuf * L.stage_elems * ks);
+                L.smem_bytes = L.vec_off + (vec_in_smem ? vec_bytes : 0);
+                if (!vec_in_smem) {
+                    size_t tot = 0;
+                    for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
+                    dmalloc(&h->gscratch, tot * 2 * ks);
+                }
             }
         }
         dmalloc(&h->partial, (size_t)RED_BLOCKS * (MAX_RESTART + 3) * 8);

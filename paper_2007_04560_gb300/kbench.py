@@ -45,12 +45,16 @@ def main(argv=None):
     ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
     ap.add_argument("--reps", type=int, default=5)
     ap.add_argument("--components", default=",".join(COMPONENTS))
+    ap.add_argument("--ras-window", type=int, default=None, choices=[0, 1, 2],
+                    help="2D Schwarz apply variant (params.ras_window)")
     args = ap.parse_args(argv)
     build.build()
     w = WORKLOADS[args.workload]
     p = w.params.replace(batch=1)
     if args.precision:
         p = p.replace(precision=PREC_MIXED if args.precision == "mixed" else PREC_FP64)
+    if args.ras_window is not None:
+        p = p.replace(ras_window=args.ras_window)
     comps = [c for c in args.components.split(",") if c]
     for c in comps:
         if c not in COMPONENTS:

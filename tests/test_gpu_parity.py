@@ -142,14 +142,17 @@ def test_jvp_fp32(P, bc, grid):
     assert _rel(host(y), yo) <= 1e-5
 
 
+@pytest.mark.parametrize("window", [2, 1])
 @pytest.mark.parametrize("ras_type", [0, 1, 2])
 @pytest.mark.parametrize("bc", [BC_PERIODIC, BC_NEUMANN])
 @pytest.mark.parametrize("grid", GRIDS)
-def test_ras_apply(P, bc, grid, ras_type):
-    """ILU(0) of every A_k and the Schwarz sum (left-RAS, AS, right-RAS)."""
+def test_ras_apply(P, bc, grid, ras_type, window):
+    """ILU(0) of every A_k and the Schwarz sum (left-RAS, AS, right-RAS), with the whole box
+    vector in shared memory (window = 2) and with the level-window kernel (window = 1)."""
     import torch
     n, parts = grid
-    p = Params(n=n, bc=bc, ras_parts=parts, ras_overlap=2 if n[0] == 64 else 1, ras_type=ras_type)
+    p = Params(n=n, bc=bc, ras_parts=parts, ras_overlap=2 if n[0] == 64 else 1, ras_type=ras_type,
+               ras_window=window)
     X1, X0 = perturbed_pair(p, 13, u_mean=0.45, amp=0.05, step_amp=2e-3)
     dt = 2e-3
     Jo = O.jacobian(p, X1, X0, dt)
@@ -336,3 +339,22 @@ def test_step_host_matches_device():
             s2.step_host(uh, vh)
         torch.cuda.synchronize()
         assert np.array_equal(host(ug), uh) and np.array_equal(host(vg), vh)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_window_apply_steps_match_whole_box(P, precision):
+    """Time steps with the level-window apply equal those with the whole-box apply up to
+    rounding (the two sum the same products in the same order: bit-identical)."""
+    import torch
+    p = Params(n=(96, 80, 1), ras_parts=(3, 2, 1), ras_overlap=2, dt_mode=DT_ADAPTIVE, dt0=1e-4, dt_min=1e-5,
+               dt_max=1e-1, eta0=1e4, precision=precision)
+    u, v = initial_fields(p, 9, 0.4, 0.05)
+    out = []
+    for window in (2, 1):
+        ug, vg = dev(u.ravel()), dev(v.ravel())
+        with P.Solver(p.replace(ras_window=window)) as s:
+            infos = [s.step(ug, vg) for _ in range(3)]
+        torch.cuda.synchronize()
+        out.append((host(ug), host(vg), [(i.dt, i.gmres_its) for i in infos]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]

@@ -65,6 +65,7 @@ class Params:
     batch: int = 1
     cgs_refine: int = 1          # 1: CGS2 (two passes), 0: single classical pass
     graphs: int = 1              # 1: GMRES iterations replayed from captured CUDA graphs
+    ras_window: int = 0          # 2D Schwarz apply: 0 choose, 1 level window, 2 whole box vector
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
