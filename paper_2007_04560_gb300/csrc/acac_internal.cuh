@@ -258,7 +258,7 @@ struct RasLaunch {
     int vec_off;         // byte offset of the box vector (or of the level window) in shared memory
     size_t smem_bytes;   // dynamic shared memory per CTA
     int window;          // 1: windowed apply (last levels in shared memory, forward result in global)
-    int win_cells;       // cells per window level (the widest level)
+    int win_cells;       // rows per window slot (the tallest box + 4)
 };
 
 // Checks of acac_create (sizes, coefficients, partition, enumerations).

@@ -436,10 +436,14 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
 // Windowed variant for boxes whose vector does not fit shared memory at two CTAs per SM
 // (e.g. 132 x 132 boxes): every lower neighbour of a level-l cell lies on levels l-1..l-4
 // and every upper neighbour on l+1..l+4, so shared memory keeps only the last RAS_WIN
-// levels of the sweep's values (slot (l mod RAS_WIN), position j - jmin(l)).  The forward
-// sweep also writes its result level-major to global scratch (coalesced), where the
-// backward sweep reads it back one level ahead; r is gathered per level, one level
-// ahead, and z written per level.  Same pipeline, barrier and bounded waits as above.
+// levels of the sweep's values, slot (l mod RAS_WIN), indexed by the row j (+2 padding
+// rows on each side).  Every slot position that its level does not cover holds zero --
+// the stale rows a slot's previous level left are cleared when the slot is reused, and
+// the window is cleared between the sweeps -- so neighbour reads need no bounds tests.
+// The forward sweep also writes its result level-major to global scratch (coalesced),
+// where the backward sweep reads it back one level ahead; r is gathered per level, one
+// level ahead, and z written per level.  Same pipeline, barrier and bounded waits as
+// above.
 constexpr int RAS_WIN = 5;
 
 template <typename T>
@@ -457,18 +461,20 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
     const int nlev = sd.nlev;
     const int nst = 2 * nlev;
     const int nbuf = L.nbuf;
-    const int mc = L.win_cells;
+    const int hp = L.win_cells;                 // rows per window slot (>= H + 4)
     const int ncons = blockDim.x - 32;
     const bool producer = threadIdx.x >= ncons;
     uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
     uint64_t* empty = full + RAS_MAXBUF;
     int* lo = reinterpret_cast<int*>(smem_raw + 16 * RAS_MAXBUF);
     T* stages = reinterpret_cast<T*>(smem_raw + L.stage_off);
-    T* win = reinterpret_cast<T*>(smem_raw + L.vec_off);          // [RAS_WIN][mc][2]
-    T* yg = gscratch + 2 * (size_t)sd.vec_base;                   // level-major forward result
+    V2<T>* win = reinterpret_cast<V2<T>*>(smem_raw + L.vec_off);  // [RAS_WIN][hp]
+    T* wins = reinterpret_cast<T*>(win);                            // component view
+    T* yg = gscratch + 2 * (size_t)sd.vec_base;                     // level-major forward result
     const T* cbase = coef + sd.coef_base;
 
     for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
+    for (int t = threadIdx.x; t < RAS_WIN * hp; t += blockDim.x) win[t] = V2<T>{(T)0, (T)0};
     if (threadIdx.x == 0) {
         s_cabort = 0;
         s_pabort = 0;
@@ -513,14 +519,7 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
         }
     } else {
         const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
-        // value of the neighbour (i2, j2) of the current sweep: the window slot of its level,
-        // zero outside the box
-        auto nbv = [&](int i2, int j2) -> V2<T> {
-            if (i2 < 0 || i2 >= W || j2 < 0 || j2 >= H) return V2<T>{(T)0, (T)0};
-            const int l2 = i2 + 2 * j2;
-            const int m2 = j2 - level_jmin(l2, W);
-            return reinterpret_cast<const V2<T>*>(win)[(l2 % RAS_WIN) * mc + m2];
-        };
+        auto jmax_of = [&](int l) { const int t = l >> 1; return t < H - 1 ? t : H - 1; };
         // this thread's row of the restricted r at cell m of level l (0 if none)
         auto r_at = [&](int l) -> T {
             if (l >= nlev || m >= lo[l + 1] - lo[l]) return (T)0;
@@ -531,44 +530,74 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
             return r[(size_t)rr * N + box_cell(g, sd, i, j)];
         };
         T pre = r_at(0);   // operand prefetched for the next level: r (forward), y (backward)
+        int lm = 0;        // l mod RAS_WIN
         int k = 0;
         for (; k < nst; ++k) {
             const int b = k % nbuf;
-            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
             const bool fwd = k < nlev;
+            if (k == nlev) {
+                // between the sweeps: clear the window (the backward sweep reads only its own
+                // results and zeros), then start from the last level
+                for (int t = threadIdx.x; t < RAS_WIN * hp; t += ncons) win[t] = V2<T>{(T)0, (T)0};
+                asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
+                lm = (nlev - 1) % RAS_WIN;
+            }
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
             const int l = fwd ? k : nst - 1 - k;
             const int cnt = lo[l + 1] - lo[l];
-            const int j = level_jmin(l, W) + m, i = l - 2 * j;
+            const int jmin = level_jmin(l, W);
+            const int j = jmin + m, i = l - 2 * j;
             const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
             const bool act = m < cnt && landed;
-            const int slot = (l % RAS_WIN) * mc + m;
+            // slot bases of the levels l -+ d, d = 1..4 (in V2 elements), and the row offset
+            int sb[5];
+#pragma unroll
+            for (int d = 1; d <= 4; ++d) {
+                int t = fwd ? lm - d : lm + d;
+                t = t < 0 ? t + RAS_WIN : (t >= RAS_WIN ? t - RAS_WIN : t);
+                sb[d] = t * hp + 2;
+            }
+            V2<T>* own = win + lm * hp + 2;
             const T cur = pre;
             if (fwd) {
                 if (l + 1 < nlev) pre = r_at(l + 1);
+                // clear the rows the slot's previous level (l - 5) covered below this level's
+                if (l >= RAS_WIN && m < 3 && rr == 0) {
+                    const int jz = level_jmin(l - RAS_WIN, W) + m;
+                    if (jz < jmin) own[jz] = V2<T>{(T)0, (T)0};
+                }
                 T y = (T)0;
                 if (act) {
                     T a0 = cur, a1 = (T)0;
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = nbv(i + lower_dx(q), j + lower_dy(q));
+                        const int dl = -(lower_dx(q) + 2 * lower_dy(q));   // 1..4 levels back
+                        const V2<T> nb = win[sb[dl] + j + lower_dy(q)];
                         const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
                         T& acc = q < 3 ? a0 : a1;
                         acc = fma(-c0, nb.x, acc);
                         acc = fma(-c1, nb.y, acc);
                     }
                     y = a0 + a1;
-                    win[2 * slot + rr] = y;
+                    wins[2 * (lm * hp + 2 + j) + rr] = y;
                     yg[2 * (size_t)(lo[l] + m) + rr] = y;
                 }
                 if (l + 1 == nlev) pre = y;   // the first backward level is this one
+                lm = lm + 1 == RAS_WIN ? 0 : lm + 1;
             } else {
                 if (l > 0) pre = m < lo[l] - lo[l - 1] ? yg[2 * (size_t)(lo[l - 1] + m) + rr] : (T)0;
+                // clear the rows the slot's previous level (l + 5) covered above this level's
+                if (l + RAS_WIN < nlev && m < 3 && rr == 0) {
+                    const int jz = jmax_of(l) + 1 + m;
+                    if (jz <= jmax_of(l + RAS_WIN)) own[jz] = V2<T>{(T)0, (T)0};
+                }
                 T a0 = (T)0, a1 = (T)0;
                 if (act) {
                     a0 = cur;
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = nbv(i + upper_dx(q), j + upper_dy(q));
+                        const int dl = upper_dx(q) + 2 * upper_dy(q);      // 1..4 levels ahead
+                        const V2<T> nb = win[sb[dl] + j + upper_dy(q)];
                         const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
                         T& acc = q < 3 ? a0 : a1;
                         acc = fma(-c0, nb.x, acc);
@@ -580,7 +609,7 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 if (act) {
                     const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
                     const T zc = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
-                    win[2 * slot + rr] = zc;
+                    wins[2 * (lm * hp + 2 + j) + rr] = zc;
                     const int gc = box_cell(g, sd, i, j);
                     if (ras_type == ACAC_RAS_LEFT) {
                         if (i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)
@@ -589,6 +618,7 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                         atomicAdd(&z[(size_t)rr * N + gc], zc);
                     }
                 }
+                lm = lm == 0 ? RAS_WIN - 1 : lm - 1;
             }
             uint32_t gave_up;
             asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"

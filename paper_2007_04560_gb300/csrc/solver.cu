@@ -1124,10 +1124,12 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             // windowed apply (the last 5 levels in shared memory, the forward result in
             // global scratch) when the box vector does not fit two CTAs per SM, or on request
             L.window = p->ras_window == 1 || (p->ras_window == 0 && !full_fits2);
-            L.win_cells = h->ras_maxcnt;
+            int maxh = 0;
+            for (auto& sd : h->subs) maxh = std::max(maxh, sd.H);
+            L.win_cells = maxh + 4;   // rows per window slot
             if (L.window) {
                 // aim at three CTAs per SM with at least 4 stages each
-                const size_t win_bytes = r128((size_t)5 * h->ras_maxcnt * 2 * ks);
+                const size_t win_bytes = r128((size_t)5 * L.win_cells * 2 * ks);
                 const size_t third = 74 * 1024;
                 const size_t room = third > L.stage_off + win_bytes ? third - L.stage_off - win_bytes : 0;
                 L.nbuf = (int)std::max<size_t>(4, std::min<size_t>(RAS_MAXBUF, room / stage_bytes));
