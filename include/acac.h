@@ -126,7 +126,8 @@ void acac_default_params(acac_params *p);
  * cudaStream_t (NULL = legacy default stream).  *out receives the handle.
  * Errors: ACAC_E_ARG (sizes < 4, non-positive coefficient, periodic box that
  * would wrap onto itself, subdomain box under 4 or over 250 cells in some
- * direction, dim not 2 or 3, batch outside 1..ACAC_MAX_BATCH), ACAC_E_NOMEM,
+ * direction, a 2D cell in more than four boxes (overlap not below the owned box
+ * width), dim not 2 or 3, batch outside 1..ACAC_MAX_BATCH), ACAC_E_NOMEM,
  * ACAC_E_CUDA.
  * Ensembles (batch B > 1): the handle holds B member solvers, each with its own
  * workspace and its own CUDA stream (ordered after cuda_stream at the start of each
@@ -328,7 +329,7 @@ int acac_log(const double *x, double *y, long long n, void *cuda_stream);
 #define ACAC_K_RAS_APPLY     8    /* batched restriction, triangular sweeps, extension */
 #define ACAC_K_DOT           9    /* Gram–Schmidt block dot products                  */
 #define ACAC_K_CGS_UPDATE   10    /* Gram–Schmidt update (and norm)                   */
-#define ACAC_K_REDUCE       11    /* unused: reductions finish inside their kernels   */
+#define ACAC_K_REPACK       11    /* Jacobian rows repacked per subdomain cell        */
 #define ACAC_K_VECTOR       12    /* other vector kernels                             */
 #define ACAC_K_ENERGY       13    /* energy and mass                                  */
 #define ACAC_NKERNEL        14

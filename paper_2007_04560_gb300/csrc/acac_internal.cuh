@@ -272,6 +272,16 @@ template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
                               T* gscratch, cudaStream_t s);
+// 16 bytes of consecutive values as one vector word (bit casts, no aliasing)
+__device__ __forceinline__ uint4 pack16(const float* p) {
+    return make_uint4(__float_as_uint(p[0]), __float_as_uint(p[1]), __float_as_uint(p[2]), __float_as_uint(p[3]));
+}
+__device__ __forceinline__ uint4 pack16(const double* p) {
+    const unsigned long long a = (unsigned long long)__double_as_longlong(p[0]);
+    const unsigned long long b = (unsigned long long)__double_as_longlong(p[1]);
+    return make_uint4((unsigned)a, (unsigned)(a >> 32), (unsigned)b, (unsigned)(b >> 32));
+}
+
 // Deterministic two-stage reductions.  A reducing kernel runs at most RED_BLOCKS
 // blocks of RED_THREADS threads; each block writes one partial sum per reduced
 // quantity v to partial[v * RED_BLOCKS + block], and the block that finishes last
@@ -363,8 +373,8 @@ cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, cons
 
 // jacobian.cu
 template <typename T>
-cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J,
-                            cudaStream_t s);
+cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
+                            const int4* rec_of = nullptr);
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
 template <typename T>
@@ -409,9 +419,14 @@ cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, lon
 cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s);
 
 // ras.cu
+// Jacobian rows of every box cell, one 52-value record per box cell in the factor's
+// order (2D); rec_of[c] = the records of grid cell c (-1: unused).
+template <typename T>
+cudaError_t launch_repack(int N, const T* J, const int4* rec_of, T* Jp, cudaStream_t s);
+// J: stencil-diagonal (packed = 0) or the repacked records (packed = 1)
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
-                              const T* J, T* coef, int threads, int ring_cells, size_t smem_bytes,
+                              const T* J, int packed, T* coef, int threads, int ring_cells, size_t smem_bytes,
                               int* flags, cudaStream_t s);
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,

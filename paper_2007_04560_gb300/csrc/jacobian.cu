@@ -18,8 +18,13 @@ static int grid1(long long n, int threads) {
 }
 
 // ---------------------------------------------------------------- assembly
-template <typename T, int DIM>
-__global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<T> C, T* __restrict__ J) {
+// J is written in stencil-diagonal storage, or (PACKED, 2D) straight into the records
+// of the subdomain factorization (one 52-value record per box that contains the cell,
+// rec_of[c]; see the repack kernel of the factorization), which skips the stencil-diagonal
+// pass when nothing else reads it.
+template <typename T, int DIM, bool PACKED>
+__global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<T> C, T* __restrict__ J,
+                                                       const int4* __restrict__ rec_of) {
     constexpr int NS = nslot<DIM>();
     constexpr int NF = 2 * DIM;
     const int N = g.N;
@@ -77,6 +82,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
         Juu[0] += w * ct * hg * lapc;
     }
     const T irho = k.irho;
+    T Jvu[NS], Jvv[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
         T jvu = (T)0, jvv = (T)0;
@@ -87,19 +93,47 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
             const int f = s - 1;   // slots 1..2*DIM are the faces
             jvv = -cc * hg * eih2c[f] * irho;
         }
-        J[(size_t)(s * 4 + 0) * N + c] = (T)Juu[s];
-        J[(size_t)(s * 4 + 1) * N + c] = (T)Juv[s];
-        J[(size_t)(s * 4 + 2) * N + c] = (T)jvu;
-        J[(size_t)(s * 4 + 3) * N + c] = (T)jvv;
+        Jvu[s] = jvu;
+        Jvv[s] = jvv;
+    }
+    if (!PACKED) {
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            J[(size_t)(s * 4 + 0) * N + c] = Juu[s];
+            J[(size_t)(s * 4 + 1) * N + c] = Juv[s];
+            J[(size_t)(s * 4 + 2) * N + c] = Jvu[s];
+            J[(size_t)(s * 4 + 3) * N + c] = Jvv[s];
+        }
+        return;
+    }
+    // record: row 0 (slots x (uu, uv)), row 1 (slots x (vu, vv))
+    T out[4 * NS];
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+        out[2 * s] = Juu[s];
+        out[2 * s + 1] = Juv[s];
+        out[2 * NS + 2 * s] = Jvu[s];
+        out[2 * NS + 2 * s + 1] = Jvv[s];
+    }
+    const int4 rc = rec_of[c];
+    const int recs[4] = {rc.x, rc.y, rc.z, rc.w};
+    constexpr int PER = 16 / sizeof(T);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (recs[q] < 0) continue;
+        uint4* dst = reinterpret_cast<uint4*>(J + (size_t)recs[q] * (4 * NS));
+#pragma unroll
+        for (int kk = 0; kk < 4 * NS / PER; ++kk) dst[kk] = pack16(&out[kk * PER]);
     }
 }
 
 template <typename T>
-cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J,
-                            cudaStream_t s) {
+cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
+                            const int4* rec_of) {
     const JacK<T> kk = jac_consts<T>(k, dt);
-    if (g.dim == 3) assemble_kernel<T, 3><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J);
-    else assemble_kernel<T, 2><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J);
+    if (g.dim == 3) assemble_kernel<T, 3, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+    else if (rec_of) assemble_kernel<T, 2, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
+    else assemble_kernel<T, 2, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
     return cudaGetLastError();
 }
 
@@ -382,7 +416,7 @@ cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s) {
 
 #define INST(T)                                                                                   \
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
-                                            cudaStream_t);                                        \
+                                            cudaStream_t, const int4*);                           \
     template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
     template cudaError_t launch_jvp_g<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,      \
                                          cudaStream_t);                                           \

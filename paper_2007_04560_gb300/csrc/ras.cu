@@ -69,12 +69,70 @@ __device__ __forceinline__ int box_cell(const Geom& g, const SubInfo& sd, int i,
 // level are loaded into registers while the current level is computed.
 constexpr int FACTOR_RING = 5;
 
+// The factorization reads the Jacobian rows of a box's cells in wavefront order.  From
+// the stencil-diagonal storage those are 26 scattered values per row (at 2048^2 the
+// factorization read 9x its data in whole DRAM sectors), so the rows are first repacked
+// into one record per box cell, in the factor's order: record (box cells before the
+// box) + lo[level] + position, holding row 0 (13 slots x 2) then row 1.  One thread per
+// grid cell reads its 52 values coalesced and writes the record of every box that
+// contains the cell (up to four in 2D; rec_of[c] lists them, -1 unused).
+template <typename T>
+__global__ void __launch_bounds__(256) repack_kernel(int N, const T* __restrict__ J, const int4* __restrict__ rec_of,
+                                                     T* __restrict__ Jp) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    T v[4 * NSLOT];
+#pragma unroll
+    for (int s = 0; s < NSLOT; ++s)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) v[s * 4 + e] = J[(size_t)(s * 4 + e) * N + c];
+    // the record in the factor's order (row 0: 13 slots x 2, then row 1), stored as 16-byte
+    // vectors (a record is 208 or 416 bytes, so every record starts 16-byte aligned)
+    T out[4 * NSLOT];
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr)
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            out[rr * 2 * NSLOT + 2 * s] = v[s * 4 + 2 * rr];
+            out[rr * 2 * NSLOT + 2 * s + 1] = v[s * 4 + 2 * rr + 1];
+        }
+    const int4 rc = rec_of[c];
+    const int recs[4] = {rc.x, rc.y, rc.z, rc.w};
+    constexpr int PER = 16 / sizeof(T);          // values per 16-byte store
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (recs[q] < 0) continue;
+        uint4* dst = reinterpret_cast<uint4*>(Jp + (size_t)recs[q] * (4 * NSLOT));
+#pragma unroll
+        for (int k = 0; k < 4 * NSLOT / PER; ++k) dst[k] = pack16(&out[k * PER]);
+    }
+}
+
+template <typename T>
+cudaError_t launch_repack(int N, const T* J, const int4* rec_of, T* Jp, cudaStream_t s) {
+    repack_kernel<T><<<(N + 255) / 256, 256, 0, s>>>(N, J, rec_of, Jp);
+    return cudaGetLastError();
+}
+
+// Row rr of the Jacobian at cell m of level l: from the repacked records (packed) or
+// straight from the stencil-diagonal storage; couplings leaving the box are dropped.
 template <typename T>
 __device__ __forceinline__ void fetch_rows(const Geom& g, const SubInfo& sd, const int* lo, const T* __restrict__ J,
-                                           int l, int m, int rr, T (&dst)[NSLOT][2]) {
+                                           int packed, int l, int m, int rr, T (&dst)[NSLOT][2]) {
     const int cnt = lo[l + 1] - lo[l];
     if (m >= cnt) return;
     const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+    if (packed) {
+        const T* src = J + ((size_t)(sd.coef_base / NCOEF) + lo[l] + m) * (4 * NSLOT) + rr * 2 * NSLOT;
+#pragma unroll
+        for (int s = 0; s < NSLOT; ++s) {
+            const int ii = i + slot_dx(s), jj = j + slot_dy(s);
+            const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H;
+            dst[s][0] = in ? src[2 * s] : (T)0;
+            dst[s][1] = in ? src[2 * s + 1] : (T)0;
+        }
+        return;
+    }
     const int gc = box_cell(g, sd, i, j);
     const size_t N = (size_t)g.N;
 #pragma unroll
@@ -89,7 +147,8 @@ __device__ __forceinline__ void fetch_rows(const Geom& g, const SubInfo& sd, con
 template <typename T>
 __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                          const int* __restrict__ lev_off, const T* __restrict__ J,
-                                                         T* __restrict__ coef, int ring_cells, int* flags) {
+                                                         int packed, T* __restrict__ coef, int ring_cells,
+                                                         int* flags) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const SubInfo sd = subs[blockIdx.x];
     int* lo = reinterpret_cast<int*>(smem_raw);
@@ -100,12 +159,12 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
     const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
     int bad = 0;
     T Jn[NSLOT][2];
-    fetch_rows<T>(g, sd, lo, J, 0, m, rr, Jn);
+    fetch_rows<T>(g, sd, lo, J, packed, 0, m, rr, Jn);
     for (int l = 0; l < sd.nlev; ++l) {
         T A[NSLOT][2];
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) { A[s][0] = Jn[s][0]; A[s][1] = Jn[s][1]; }
-        if (l + 1 < sd.nlev) fetch_rows<T>(g, sd, lo, J, l + 1, m, rr, Jn);
+        if (l + 1 < sd.nlev) fetch_rows<T>(g, sd, lo, J, packed, l + 1, m, rr, Jn);
         const int cnt = lo[l + 1] - lo[l];
         const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
         const bool act = m < cnt;
@@ -171,14 +230,14 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
 
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
-                              const T* J, T* coef, int threads, int ring_cells, size_t smem_bytes, int* flags,
-                              cudaStream_t s) {
+                              const T* J, int packed, T* coef, int threads, int ring_cells, size_t smem_bytes,
+                              int* flags, cudaStream_t s) {
     static std::atomic<size_t> attr_bytes{0};
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = ensure_smem_limit((const void*)ras_factor_kernel<T>, smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
-    ras_factor_kernel<T><<<nsub, threads, smem_bytes, s>>>(g, subs, lev_off, J, coef, ring_cells, flags);
+    ras_factor_kernel<T><<<nsub, threads, smem_bytes, s>>>(g, subs, lev_off, J, packed, coef, ring_cells, flags);
     return cudaGetLastError();
 }
 
@@ -883,8 +942,9 @@ cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, cons
 }
 
 #define INST(T)                                                                                    \
+    template cudaError_t launch_repack<T>(int, const T*, const int4*, T*, cudaStream_t);              \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
-                                              T*, int, int, size_t, int*, cudaStream_t);            \
+                                              int, T*, int, int, size_t, int*, cudaStream_t);       \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, int*,       \
                                              cudaStream_t);                                           \

@@ -138,6 +138,10 @@ struct acac_handle {
     std::vector<int> cells3, pos3;   // 3D: level-ordered packed cells, position map
     SubInfo* subs_dev;
     int* lev_dev;
+    std::vector<int> rec_of;     // 2D: for every grid cell, its records in the boxes (4 per cell, -1 unused)
+    int4* rec_of_dev = nullptr;
+    void* Jp = nullptr;          // 2D: Jacobian rows repacked per box cell (52 values each)
+    bool jpacked = false;        // Jp holds the current Jacobian (assembled straight into it)
     int *cells3_dev, *pos3_dev;
     int ras_threads;
     size_t ras_smem;
@@ -398,8 +402,18 @@ int factor(acac_handle* h) {
     const int ring_cells = h->ras_maxcnt;
     const size_t smem = sizeof(int) * (size_t)(((h->ras_maxlev + 1 + 3) & ~3) + 3 & ~3) +
                         sizeof(T) * 5 * (size_t)ring_cells * CREC;
+    // the factorization reads each cell's rows: from the per-box records when the assembly
+    // wrote them; else repacked first in FP32 (the stencil-diagonal reads waste DRAM
+    // sectors), directly in FP64 (bound by the FP64 pipe, where the repack does not pay)
+    int packed = h->jpacked ? 1 : 0;
+    if (!packed && sizeof(T) == 4) {
+        KLA(ACAC_K_REPACK, (double)sizeof(T) * (52.0 * h->N + 52.0 * h->nbox), 0.0,
+            launch_repack<T>((int)h->N, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
+        packed = 1;
+    }
     KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox,
-        launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->J, (T*)h->coef,
+        launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev,
+                             packed ? (const T*)h->Jp : (const T*)h->J, packed, (T*)h->coef,
                              h->ras_threads, ring_cells, smem, h->flags, h->stream));
     h->n_factor++;
     return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
@@ -596,7 +610,16 @@ template <typename T>
 void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble) {
     set_jac<T>(h, dt);
     KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0, launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
-    if (assemble) KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0, launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
+    if (!assemble) return;
+    // with matrix-free products the assembled Jacobian feeds only the subdomain
+    // factorization: in 2D assemble it straight into the factorization's records
+    h->jpacked = h->g.dim == 2 && h->p.jac_mode == ACAC_JAC_MATFREE;
+    if (h->jpacked)
+        KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * (7.0 * h->N + 52.0 * h->nbox), 0.0,
+            launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->Jp, h->stream, h->rec_of_dev));
+    else
+        KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0,
+            launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
 }
 
 // Newton iteration from X_0 = X0 (device).  Root in h->X.
@@ -685,6 +708,7 @@ void assemble_transposed(acac_handle* h, const double* X1, double dt, int wrt_x0
     KLA(ACAC_K_ASSEMBLE, 8.0 * 59.0 * h->N, 0.0,
         launch_assemble<double>(h->g, h->k, wrt_x0 ? -dt : dt, cache_of<double>(h), J, h->stream));
     KLA(ACAC_K_VECTOR, 8.0 * 2.0 * stencil_values(h), 0.0, launch_transpose<double>(h->g, J, (double*)h->J, h->stream));
+    h->jpacked = false;
 }
 
 // One adjoint step at (X1, X0) (device, 2N each).  lam_in = lambda^{n+1}; lam_out
@@ -844,6 +868,30 @@ int build_subdomains(acac_handle* h) {
         }
     }
     h->coef_count = coef;
+    if (dim == 2) {
+        // records of every grid cell: box cells before the box + lo[level] + position
+        h->rec_of.assign((size_t)4 * p.n[0] * p.n[1], -1);
+        for (const SubInfo& sd : h->subs) {
+            const long long base = sd.coef_base / NCOEF;
+            for (int l = 0; l < sd.nlev; ++l) {
+                const int t = l - sd.W + 2;
+                const int jmin = t > 0 ? t / 2 : 0;
+                for (int j = jmin; j < sd.H; ++j) {
+                    const int i = l - 2 * j;
+                    if (i < 0) break;
+                    int gx = sd.ox + i, gy = sd.oy + j;
+                    gx = gx < 0 ? gx + p.n[0] : (gx >= p.n[0] ? gx - p.n[0] : gx);
+                    gy = gy < 0 ? gy + p.n[1] : (gy >= p.n[1] ? gy - p.n[1] : gy);
+                    const size_t gc = (size_t)gy * p.n[0] + gx;
+                    const long long rec = base + h->lev[sd.lev_base + l] + (j - jmin);
+                    int q = 0;
+                    while (q < 4 && h->rec_of[4 * gc + q] >= 0) ++q;
+                    if (q == 4 || rec > INT32_MAX) return ACAC_E_ARG;   // at most 4 boxes per cell in 2D
+                    h->rec_of[4 * gc + q] = (int)rec;
+                }
+            }
+        }
+    }
     int maxlev = 0;
     for (auto& sd : h->subs) maxlev = std::max(maxlev, sd.nlev);
     h->ras_maxlev = maxlev;
@@ -896,7 +944,7 @@ namespace {
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
-                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev};
+                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->host) cudaFreeHost(h->host);
@@ -1178,6 +1226,13 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         }
         CU(cudaMemcpy(h->subs_dev, h->subs.data(), h->subs.size() * sizeof(SubInfo), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(h->lev_dev, h->lev.data(), h->lev.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (p->dim == 2) {
+            dmalloc(&h->rec_of_dev, h->rec_of.size() * sizeof(int));
+            CU(cudaMemcpy(h->rec_of_dev, h->rec_of.data(), h->rec_of.size() * sizeof(int), cudaMemcpyHostToDevice));
+            dmalloc(&h->Jp, (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
+            h->rec_of.clear();
+            h->rec_of.shrink_to_fit();
+        }
         CU(set_taylor_constants(p->taylor_S));
     } catch (Err e) {
         free_all(h);
@@ -1292,7 +1347,7 @@ int acac_set_coeffs(acac_handle* h, int member, double alpha, double beta, doubl
 const char* acac_kernel_name(int kernel) {
     static const char* names[ACAC_NKERNEL] = {
         "residual_g", "residual_f", "linearize", "assemble", "spmv", "jvp_g", "jvp_f",
-        "ras_factor", "ras_apply", "gs_dot", "gs_update", "reduce", "vector", "energy"};
+        "ras_factor", "ras_apply", "gs_dot", "gs_update", "repack", "vector", "energy"};
     return (kernel >= 0 && kernel < ACAC_NKERNEL) ? names[kernel] : "unknown";
 }
 
@@ -1386,6 +1441,7 @@ int acac_ras_factor(acac_handle* h, const void* J) {
     try {
         const size_t bytes = (size_t)(h->g.dim == 3 ? NSLOT3 : NSLOT) * 4 * h->N * h->ksz;
         if (J != h->J) CU(cudaMemcpyAsync(h->J, J, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        h->jpacked = false;
         return h->mixed ? factor<float>(h) : factor<double>(h);
     } catch (Err e) {
         return e.code;
@@ -1416,6 +1472,7 @@ int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, co
         int gi = 0;
         double gr = 0.0;
         CU(cudaMemcpyAsync(h->b, b, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
+        h->jpacked = false;
         if (h->mixed) {
             KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
             st = factor<float>(h);
