@@ -194,6 +194,8 @@ __device__ __forceinline__ T face_weight(const Geom& g, int x, int y, int z, int
 __device__ __forceinline__ double face_ih2(const Geom& g, int f) { return f < 2 ? g.ihx2 : f < 4 ? g.ihy2 : g.ihz2; }
 // Generic stencil slots (2D: 13, 3D: 25; slot f+1 is face f in both).
 template <int DIM> __host__ __device__ constexpr int nslot() { return DIM == 2 ? NSLOT : NSLOT3; }
+// boxes that can contain one grid cell (overlap below the owned box width): 2 per axis
+template <int DIM> __host__ __device__ constexpr int rec_per_cell() { return DIM == 2 ? 4 : 8; }
 template <int DIM> __host__ __device__ constexpr int sl_dx(int s) { return DIM == 2 ? slot_dx(s) : s3_dx(s); }
 template <int DIM> __host__ __device__ constexpr int sl_dy(int s) { return DIM == 2 ? slot_dy(s) : s3_dy(s); }
 template <int DIM> __host__ __device__ constexpr int sl_dz(int s) { return DIM == 2 ? 0 : s3_dz(s); }
@@ -248,6 +250,9 @@ struct SubInfo {
 // Row pitch (in cells) of a padded box vector: W + 4, made odd so that the cells of
 // one wavefront level (row stride pitch - 2) fall into distinct shared-memory banks.
 __host__ __device__ constexpr int ras_pitch(int W) { return (W + 4) | 1; }
+// The 3D row pitch: odd for doubles (fewer bank conflicts between the cells of a level,
+// measured faster), W + 4 for floats (the larger vector then cost a CTA's stages: slower).
+__host__ __device__ constexpr int ras3_pitch(int W, int value_bytes) { return value_bytes == 8 ? (W + 4) | 1 : W + 4; }
 
 // Shared-memory plan of the Schwarz apply kernel (bytes / elements).
 struct RasLaunch {
@@ -267,11 +272,12 @@ int validate_params(const acac_params* p);
 // ---------------------------------------------------------------- kernels (launchers)
 template <typename T>
 cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                               const int* pos, const T* J, T* coef, int threads, int* flags, cudaStream_t s);
+                               const int* pos, const T* J, int packed, T* coef, int threads, int* flags,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                              const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
-                              T* gscratch, cudaStream_t s);
+                              const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
+                              int* err, cudaStream_t s);
 // 16 bytes of consecutive values as one vector word (bit casts, no aliasing)
 __device__ __forceinline__ uint4 pack16(const float* p) {
     return make_uint4(__float_as_uint(p[0]), __float_as_uint(p[1]), __float_as_uint(p[2]), __float_as_uint(p[3]));
@@ -374,7 +380,7 @@ cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, cons
 // jacobian.cu
 template <typename T>
 cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
-                            const int4* rec_of = nullptr);
+                            const int* rec_of = nullptr);
 template <typename T>
 cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
 template <typename T>
@@ -419,10 +425,10 @@ cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, lon
 cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s);
 
 // ras.cu
-// Jacobian rows of every box cell, one 52-value record per box cell in the factor's
-// order (2D); rec_of[c] = the records of grid cell c (-1: unused).
+// Jacobian rows of every box cell, one 4 x nslot-value record per box cell in the factor's
+// order; rec_of[rec_per_cell * c + q] = the records of grid cell c (-1: unused).
 template <typename T>
-cudaError_t launch_repack(int N, const T* J, const int4* rec_of, T* Jp, cudaStream_t s);
+cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s);
 // J: stencil-diagonal (packed = 0) or the repacked records (packed = 1)
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,

@@ -18,13 +18,13 @@ static int grid1(long long n, int threads) {
 }
 
 // ---------------------------------------------------------------- assembly
-// J is written in stencil-diagonal storage, or (PACKED, 2D) straight into the records
-// of the subdomain factorization (one 52-value record per box that contains the cell,
-// rec_of[c]; see the repack kernel of the factorization), which skips the stencil-diagonal
-// pass when nothing else reads it.
+// J is written in stencil-diagonal storage, or (PACKED) straight into the records of the
+// subdomain factorization (one 4 x nslot-value record per box that contains the cell,
+// rec_of[REC_PER_CELL c + q]; see the repack kernel of the factorization), which skips the
+// stencil-diagonal pass when nothing else reads it.
 template <typename T, int DIM, bool PACKED>
 __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<T> C, T* __restrict__ J,
-                                                       const int4* __restrict__ rec_of) {
+                                                       const int* __restrict__ rec_of) {
     constexpr int NS = nslot<DIM>();
     constexpr int NF = 2 * DIM;
     const int N = g.N;
@@ -115,13 +115,13 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
         out[2 * NS + 2 * s] = Jvu[s];
         out[2 * NS + 2 * s + 1] = Jvv[s];
     }
-    const int4 rc = rec_of[c];
-    const int recs[4] = {rc.x, rc.y, rc.z, rc.w};
+    constexpr int NR = rec_per_cell<DIM>();
     constexpr int PER = 16 / sizeof(T);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (recs[q] < 0) continue;
-        uint4* dst = reinterpret_cast<uint4*>(J + (size_t)recs[q] * (4 * NS));
+    for (int q = 0; q < NR; ++q) {
+        const int rec = rec_of[(size_t)NR * c + q];
+        if (rec < 0) continue;
+        uint4* dst = reinterpret_cast<uint4*>(J + (size_t)rec * (4 * NS));
 #pragma unroll
         for (int kk = 0; kk < 4 * NS / PER; ++kk) dst[kk] = pack16(&out[kk * PER]);
     }
@@ -129,11 +129,15 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
 
 template <typename T>
 cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
-                            const int4* rec_of) {
+                            const int* rec_of) {
     const JacK<T> kk = jac_consts<T>(k, dt);
-    if (g.dim == 3) assemble_kernel<T, 3, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
-    else if (rec_of) assemble_kernel<T, 2, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
-    else assemble_kernel<T, 2, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+    if (g.dim == 3) {
+        if (rec_of) assemble_kernel<T, 3, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
+        else assemble_kernel<T, 3, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+    } else {
+        if (rec_of) assemble_kernel<T, 2, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
+        else assemble_kernel<T, 2, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+    }
     return cudaGetLastError();
 }
 
@@ -416,7 +420,7 @@ cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s) {
 
 #define INST(T)                                                                                   \
     template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
-                                            cudaStream_t, const int4*);                           \
+                                            cudaStream_t, const int*);                            \
     template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
     template cudaError_t launch_jvp_g<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,      \
                                          cudaStream_t);                                           \

@@ -70,52 +70,41 @@ __device__ __forceinline__ int box_cell(const Geom& g, const SubInfo& sd, int i,
 constexpr int FACTOR_RING = 5;
 
 // The factorization reads the Jacobian rows of a box's cells in wavefront order.  From
-// the stencil-diagonal storage those are 26 scattered values per row (at 2048^2 the
-// factorization read 9x its data in whole DRAM sectors), so the rows are first repacked
-// into one record per box cell, in the factor's order: record (box cells before the
-// box) + lo[level] + position, holding row 0 (13 slots x 2) then row 1.  One thread per
-// grid cell reads its 52 values coalesced and writes the record of every box that
-// contains the cell (up to four in 2D; rec_of[c] lists them, -1 unused).
-template <typename T>
-__global__ void __launch_bounds__(256) repack_kernel(int N, const T* __restrict__ J, const int4* __restrict__ rec_of,
+// the stencil-diagonal storage those are 26 (2D) or 50 (3D) scattered values per row (at
+// 2048^2 the factorization read 9x its data in whole DRAM sectors), so the rows are first
+// repacked into one record per box cell, in the factor's order: record (box cells before
+// the box) + lo[level] + position, holding row 0 (slots x 2) then row 1.  One thread per
+// grid cell reads its values coalesced and writes the record of every box that contains
+// the cell (rec_of lists them, -1 unused).
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) repack_kernel(int N, const T* __restrict__ J, const int* __restrict__ rec_of,
                                                      T* __restrict__ Jp) {
+    constexpr int NS = nslot<DIM>(), NR = rec_per_cell<DIM>();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= N) return;
-    T v[4 * NSLOT];
+    T out[4 * NS];
 #pragma unroll
-    for (int s = 0; s < NSLOT; ++s)
+    for (int s = 0; s < NS; ++s)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) v[s * 4 + e] = J[(size_t)(s * 4 + e) * N + c];
-    // the record in the factor's order (row 0: 13 slots x 2, then row 1), stored as 16-byte
-    // vectors (a record is 208 or 416 bytes, so every record starts 16-byte aligned)
-    T out[4 * NSLOT];
+        for (int e = 0; e < 4; ++e) out[(e >> 1) * 2 * NS + 2 * s + (e & 1)] = J[(size_t)(s * 4 + e) * N + c];
+    constexpr int PER = 16 / sizeof(T);          // values per 16-byte store (records are 16-byte aligned)
 #pragma unroll
-    for (int rr = 0; rr < 2; ++rr)
+    for (int q = 0; q < NR; ++q) {
+        const int rec = rec_of[(size_t)NR * c + q];
+        if (rec < 0) continue;
+        uint4* dst = reinterpret_cast<uint4*>(Jp + (size_t)rec * (4 * NS));
 #pragma unroll
-        for (int s = 0; s < NSLOT; ++s) {
-            out[rr * 2 * NSLOT + 2 * s] = v[s * 4 + 2 * rr];
-            out[rr * 2 * NSLOT + 2 * s + 1] = v[s * 4 + 2 * rr + 1];
-        }
-    const int4 rc = rec_of[c];
-    const int recs[4] = {rc.x, rc.y, rc.z, rc.w};
-    constexpr int PER = 16 / sizeof(T);          // values per 16-byte store
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        if (recs[q] < 0) continue;
-        uint4* dst = reinterpret_cast<uint4*>(Jp + (size_t)recs[q] * (4 * NSLOT));
-#pragma unroll
-        for (int k = 0; k < 4 * NSLOT / PER; ++k) dst[k] = pack16(&out[k * PER]);
+        for (int k = 0; k < 4 * NS / PER; ++k) dst[k] = pack16(&out[k * PER]);
     }
 }
 
 template <typename T>
-cudaError_t launch_repack(int N, const T* J, const int4* rec_of, T* Jp, cudaStream_t s) {
-    repack_kernel<T><<<(N + 255) / 256, 256, 0, s>>>(N, J, rec_of, Jp);
+cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s) {
+    if (g.dim == 3) repack_kernel<T, 3><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, J, rec_of, Jp);
+    else repack_kernel<T, 2><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, J, rec_of, Jp);
     return cudaGetLastError();
 }
 
-// Row rr of the Jacobian at cell m of level l: from the repacked records (packed) or
-// straight from the stencil-diagonal storage; couplings leaving the box are dropped.
 template <typename T>
 __device__ __forceinline__ void fetch_rows(const Geom& g, const SubInfo& sd, const int* lo, const T* __restrict__ J,
                                            int packed, int l, int m, int rr, T (&dst)[NSLOT][2]) {
@@ -749,8 +738,8 @@ __device__ __forceinline__ int box_cell3(const Geom& g, const SubInfo& sd, int i
 template <typename T>
 __global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                           const int* __restrict__ lev_off, const int* __restrict__ cells,
-                                                          const int* __restrict__ pos, const T* __restrict__ J, T* coef,
-                                                          int* flags) {
+                                                          const int* __restrict__ pos, const T* __restrict__ J,
+                                                          int packed, T* coef, int* flags) {
     const SubInfo sd = subs[blockIdx.x];
     const int* lo = lev_off + sd.lev_base;
     const int* cl = cells + sd.cell_base;
@@ -767,13 +756,17 @@ __global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo*
             if (act) unpack3(cl[lo[l] + m], i, j, k);
             T A[NSLOT3][2];
             if (act) {
+                // row rr of the cell: its record (packed) or the stencil-diagonal storage
                 const int gc = box_cell3(g, sd, i, j, k);
+                const T* rec = J + ((size_t)(sd.coef_base / NCOEF3) + lo[l] + m) * (4 * NSLOT3) + rr * 2 * NSLOT3;
 #pragma unroll
                 for (int s = 0; s < NSLOT3; ++s) {
                     const int ii = i + s3_dx(s), jj = j + s3_dy(s), kk = k + s3_dz(s);
                     const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H && kk >= 0 && kk < sd.D;
-                    A[s][0] = in ? J[(size_t)(s * 4 + 2 * rr) * N + gc] : (T)0;
-                    A[s][1] = in ? J[(size_t)(s * 4 + 2 * rr + 1) * N + gc] : (T)0;
+                    const T v0 = packed ? rec[2 * s] : J[(size_t)(s * 4 + 2 * rr) * N + gc];
+                    const T v1 = packed ? rec[2 * s + 1] : J[(size_t)(s * 4 + 2 * rr + 1) * N + gc];
+                    A[s][0] = in ? v0 : (T)0;
+                    A[s][1] = in ? v1 : (T)0;
                 }
             } else {
 #pragma unroll
@@ -835,20 +828,64 @@ __global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(512) ras_apply3_kernel(Geom g, const SubInfo* __restrict__ subs,
+__global__ void __launch_bounds__(1024) ras_apply3_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                          const int* __restrict__ lev_off, const int* __restrict__ cells,
                                                          const T* __restrict__ coef, const T* __restrict__ r,
-                                                         T* __restrict__ z, int ras_type, T* gscratch) {
+                                                         T* __restrict__ z, int ras_type, T* gscratch, RasLaunch L,
+                                                         int* err) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ int s_cabort, s_pabort;
+    __shared__ int s_issued, s_consumed;
     const SubInfo sd = subs[blockIdx.x];
-    const int* lo = lev_off + sd.lev_base;
     const int* cl = cells + sd.cell_base;
     const int N = g.N;
-    const int PW = sd.W + 4, PH = sd.H + 4, PD = sd.D + 4;
+    const int PW = ras3_pitch(sd.W, sizeof(T)), PH = sd.H + 4, PD = sd.D + 4;
     const int plane = PW * PH;
-    V2<T>* yv = gscratch ? reinterpret_cast<V2<T>*>(gscratch) + sd.vec_base : reinterpret_cast<V2<T>*>(smem_raw);
+    const int nlev = sd.nlev;
+    const int nst = 2 * nlev;
+    const int nbuf = L.nbuf;
+    const int ncons = blockDim.x - 32;
+    const bool producer = threadIdx.x >= ncons;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw);
+    uint64_t* empty = full + RAS_MAXBUF;
+    int* lo = reinterpret_cast<int*>(smem_raw + 16 * RAS_MAXBUF);
+    T* stages = reinterpret_cast<T*>(smem_raw + L.stage_off);
+    V2<T>* yv = gscratch ? reinterpret_cast<V2<T>*>(gscratch) + sd.vec_base
+                         : reinterpret_cast<V2<T>*>(smem_raw + L.vec_off);
     T* ys = reinterpret_cast<T*>(yv);
-    const int rr = threadIdx.x & 1;
+    const T* cbase = coef + sd.coef_base;
+
+    for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
+    if (threadIdx.x == 0) {
+        s_cabort = 0;
+        s_pabort = 0;
+        s_issued = 0;
+        s_consumed = 0;
+        for (int b = 0; b < nbuf; ++b) {
+            mbar_init(smem_addr(&full[b]), 1);
+            mbar_init(smem_addr(&empty[b]), 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    auto issue = [&](int k) {   // stage k: the level's forward or backward records
+        const bool fwd = k < nlev;
+        const int l = fwd ? k : nst - 1 - k;
+        const int cnt = lo[l + 1] - lo[l];
+        const T* src = cbase + (long long)lo[l] * NCOEF3 + (fwd ? 0 : (long long)cnt * CREC3);
+        const uint32_t bytes = (uint32_t)(CREC3 * cnt * sizeof(T));
+        const int b = k % nbuf;
+        const uint32_t bar = smem_addr(&full[b]);
+        mbar_expect_tx(bar, bytes);
+        bulk_g2s(smem_addr(stages + (size_t)b * L.stage_elems), src, bytes, bar);
+    };
+    if (threadIdx.x == ncons) {
+        const int first = nbuf < nst ? nbuf : nst;
+        for (int k = 0; k < first; ++k) issue(k);
+        s_issued = first;
+    }
+    // restriction: the box with a zero padding of 2
     for (int idx = threadIdx.x; idx < plane * PD; idx += blockDim.x) yv[idx] = V2<T>{(T)0, (T)0};
     __syncthreads();
     const int ncell = sd.W * sd.H * sd.D;
@@ -862,44 +899,85 @@ __global__ void __launch_bounds__(512) ras_apply3_kernel(Geom g, const SubInfo* 
         yv[((k + 2) * PH + j + 2) * PW + i + 2] = val;
     }
     __syncthreads();
-    for (int pass = 0; pass < 2; ++pass) {
-        const bool fwd = pass == 0;
-        for (int s = 0; s < sd.nlev; ++s) {
-            const int l = fwd ? s : sd.nlev - 1 - s;
-            const int cnt = lo[l + 1] - lo[l];
-            const T* lvl = coef + sd.coef_base + (long long)lo[l] * NCOEF3;
-            for (int m = threadIdx.x >> 1; m < (cnt + 15) / 16 * 16; m += blockDim.x >> 1) {
-                const bool act = m < cnt;
-                int i = 0, j = 0, k = 0;
-                if (act) unpack3(cl[lo[l] + m], i, j, k);
-                const int pc = ((k + 2) * PH + j + 2) * PW + i + 2;
-                const T* rec = lvl + (long long)(fwd ? m : cnt + m) * CREC3 + (fwd ? 0 : 4) + 2 * rr;
-                T a0 = (T)0, a1 = (T)0;
-                if (act) {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) {
-                        const int off = fwd ? (l3_dz(q) * plane + l3_dy(q) * PW + l3_dx(q))
-                                            : (u3_dz(q) * plane + u3_dy(q) * PW + u3_dx(q));
-                        const V2<T> nb = yv[pc + off];
-                        T& acc = q < 6 ? a0 : a1;
-                        acc = fma(rec[4 * q], nb.x, acc);
-                        acc = fma(rec[4 * q + 1], nb.y, acc);
-                    }
+
+    if (producer) {
+        if (threadIdx.x == ncons) {
+            for (int k = nbuf; k < nst; ++k) {
+                const int b = k % nbuf;
+                if (!mbar_wait_bounded(smem_addr(&empty[b]), (uint32_t)(((k / nbuf) - 1) & 1))) {
+                    s_pabort = 1;
+                    break;
                 }
-                const T s_me = (act ? ys[2 * pc + rr] : (T)0) - (a0 + a1);
-                if (fwd) {
-                    if (act) ys[2 * pc + rr] = s_me;
-                } else {
-                    const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
-                    if (act) {
-                        const T* di = lvl + (long long)(cnt + m) * CREC3 + 2 * rr;
-                        const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
-                        ys[2 * pc + rr] = fma(di[0], sx, di[1] * sy);
-                    }
+                issue(k);
+                s_issued = k + 1;
+            }
+        }
+    } else {
+        const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+        // packed cell of position m of the next stage's level, prefetched a stage ahead
+        auto cell_at = [&](int kk) -> int {
+            if (kk >= nst) return 0;
+            const int l = kk < nlev ? kk : nst - 1 - kk;
+            return m < lo[l + 1] - lo[l] ? cl[lo[l] + m] : 0;
+        };
+        int pk = cell_at(0);
+        int k = 0;
+        for (; k < nst; ++k) {
+            const int b = k % nbuf;
+            const int cur = pk;
+            pk = cell_at(k + 1);
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
+            const bool fwd = k < nlev;
+            const int l = fwd ? k : nst - 1 - k;
+            const int cnt = lo[l + 1] - lo[l];
+            const bool act = m < cnt && landed;
+            int i = 0, j = 0, kz = 0;
+            unpack3(cur, i, j, kz);
+            const int pc = ((kz + 2) * PH + j + 2) * PW + i + 2;
+            const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC3 + (fwd ? 0 : 4) + 2 * rr;
+            T a0 = (T)0, a1 = (T)0;
+            if (act) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) {
+                    const int off = fwd ? (l3_dz(q) * plane + l3_dy(q) * PW + l3_dx(q))
+                                        : (u3_dz(q) * plane + u3_dy(q) * PW + u3_dx(q));
+                    const V2<T> nb = yv[pc + off];
+                    T& acc = q < 6 ? a0 : a1;
+                    acc = fma(rec[4 * q], nb.x, acc);
+                    acc = fma(rec[4 * q + 1], nb.y, acc);
                 }
             }
-            __syncthreads();
+            const T s_me = (act ? ys[2 * pc + rr] : (T)0) - (a0 + a1);
+            if (fwd) {
+                if (act) ys[2 * pc + rr] = s_me;
+            } else {
+                const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
+                if (act) {
+                    const T* di = stages + (size_t)b * L.stage_elems + (size_t)m * CREC3 + 2 * rr;
+                    const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
+                    ys[2 * pc + rr] = fma(di[0], sx, di[1] * sy);
+                }
+            }
+            uint32_t gave_up;
+            asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
+            if (gave_up) {
+                if (threadIdx.x == 0) s_cabort = 1;
+                break;
+            }
+            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[b]));
         }
+        if (threadIdx.x == 0) s_consumed = k;
+    }
+    __syncthreads();
+    if (s_cabort || s_pabort) {
+        if (threadIdx.x == 0) {
+            for (int kk = s_consumed; kk < s_issued; ++kk)
+                mbar_wait_bounded(smem_addr(&full[kk % nbuf]), (uint32_t)((kk / nbuf) & 1));
+            atomicOr(err, 8);
+        }
+        return;
     }
     for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
         const int i = idx % sd.W, j = (idx / sd.W) % sd.H, k = idx / (sd.W * sd.H);
@@ -918,40 +996,42 @@ __global__ void __launch_bounds__(512) ras_apply3_kernel(Geom g, const SubInfo* 
 
 template <typename T>
 cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                               const int* pos, const T* J, T* coef, int threads, int* flags, cudaStream_t s) {
-    ras_factor3_kernel<T><<<nsub, threads, 0, s>>>(g, subs, lev_off, cells, pos, J, coef, flags);
+                               const int* pos, const T* J, int packed, T* coef, int threads, int* flags,
+                               cudaStream_t s) {
+    ras_factor3_kernel<T><<<nsub, threads, 0, s>>>(g, subs, lev_off, cells, pos, J, packed, coef, flags);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                              const T* coef, const T* r, T* z, int ras_type, int threads, size_t smem_bytes,
-                              T* gscratch, cudaStream_t s) {
+                              const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
+                              int* err, cudaStream_t s) {
     static std::atomic<size_t> attr_bytes{0};
-    if (!gscratch && smem_bytes > 48 * 1024) {
-        cudaError_t e = ensure_smem_limit((const void*)ras_apply3_kernel<T>, smem_bytes, &attr_bytes);
+    {
+        cudaError_t e = ensure_smem_limit((const void*)ras_apply3_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
     if (ras_type != ACAC_RAS_LEFT) {
         cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
         if (e != cudaSuccess) return e;
     }
-    ras_apply3_kernel<T><<<nsub, threads, gscratch ? 0 : smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z,
-                                                                          ras_type, gscratch);
+    ras_apply3_kernel<T><<<nsub, L.threads, L.smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z, ras_type,
+                                                              gscratch, L, err);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                    \
-    template cudaError_t launch_repack<T>(int, const T*, const int4*, T*, cudaStream_t);              \
+    template cudaError_t launch_repack<T>(const Geom&, const T*, const int*, T*, cudaStream_t);       \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                               int, T*, int, int, size_t, int*, cudaStream_t);       \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, int*,       \
                                              cudaStream_t);                                           \
-    template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*, \
-                                               const int*, const T*, T*, int, int*, cudaStream_t);      \
-    template cudaError_t launch_ras_apply3<T>(const Geom&, int, const SubInfo*, const int*, const int*,  \
-                                              const T*, const T*, T*, int, int, size_t, T*, cudaStream_t);
+    template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*,    \
+                                               const int*, const T*, int, T*, int, int*, cudaStream_t);      \
+    template cudaError_t launch_ras_apply3<T>(const Geom&, int, const SubInfo*, const int*, const int*,     \
+                                              const T*, const T*, T*, int, const RasLaunch&, T*, int*,     \
+                                              cudaStream_t);
 INST(double)
 INST(float)
 #undef INST

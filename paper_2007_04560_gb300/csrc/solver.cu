@@ -138,9 +138,10 @@ struct acac_handle {
     std::vector<int> cells3, pos3;   // 3D: level-ordered packed cells, position map
     SubInfo* subs_dev;
     int* lev_dev;
-    std::vector<int> rec_of;     // 2D: for every grid cell, its records in the boxes (4 per cell, -1 unused)
-    int4* rec_of_dev = nullptr;
-    void* Jp = nullptr;          // 2D: Jacobian rows repacked per box cell (52 values each)
+    std::vector<int> rec_of;     // for every grid cell, its records in the boxes (4 per cell in 2D, 8 in
+                                 // 3D; -1 unused)
+    int* rec_of_dev = nullptr;
+    void* Jp = nullptr;          // Jacobian rows per box cell (52 values each in 2D, 100 in 3D)
     bool jpacked = false;        // Jp holds the current Jacobian (assembled straight into it)
     int *cells3_dev, *pos3_dev;
     int ras_threads;
@@ -377,10 +378,10 @@ void jac_action(acac_handle* h, const T* w, T* y) {
 template <typename T>
 void precond(acac_handle* h, const T* r, T* z) {
     if (h->g.dim == 3) {
-        KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (100.0 * h->nbox + 2.0 * h->N), 200.0 * h->nbox,
+        KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (104.0 * h->nbox + 4.0 * h->N), 200.0 * h->nbox,
             launch_ras_apply3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev,
-                                 (const T*)h->coef, r, z, h->p.ras_type, h->ras_threads, h->ras_smem,
-                                 (T*)h->gscratch, h->stream));
+                                 (const T*)h->coef, r, z, h->p.ras_type, h->ras_launch, (T*)h->gscratch,
+                                 h->flags + 1, h->stream));
         return;
     }
     KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
@@ -393,9 +394,16 @@ template <typename T>
 int factor(acac_handle* h) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     if (h->g.dim == 3) {
+        int packed3 = h->jpacked ? 1 : 0;
+        if (!packed3 && sizeof(T) == 4) {
+            KLA(ACAC_K_REPACK, (double)sizeof(T) * (100.0 * h->N + 100.0 * h->nbox), 0.0,
+                launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
+            packed3 = 1;
+        }
         KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 200.0 * h->nbox, 1200.0 * h->nbox,
             launch_ras_factor3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev,
-                                  (const T*)h->J, (T*)h->coef, h->ras_threads, h->flags, h->stream));
+                                  packed3 ? (const T*)h->Jp : (const T*)h->J, packed3, (T*)h->coef,
+                                  h->ras_threads, h->flags, h->stream));
         h->n_factor++;
         return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
     }
@@ -408,7 +416,7 @@ int factor(acac_handle* h) {
     int packed = h->jpacked ? 1 : 0;
     if (!packed && sizeof(T) == 4) {
         KLA(ACAC_K_REPACK, (double)sizeof(T) * (52.0 * h->N + 52.0 * h->nbox), 0.0,
-            launch_repack<T>((int)h->N, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
+            launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
         packed = 1;
     }
     KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox,
@@ -613,9 +621,9 @@ void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bo
     if (!assemble) return;
     // with matrix-free products the assembled Jacobian feeds only the subdomain
     // factorization: in 2D assemble it straight into the factorization's records
-    h->jpacked = h->g.dim == 2 && h->p.jac_mode == ACAC_JAC_MATFREE;
+    h->jpacked = h->p.jac_mode == ACAC_JAC_MATFREE;
     if (h->jpacked)
-        KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * (7.0 * h->N + 52.0 * h->nbox), 0.0,
+        KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * (7.0 * h->N + 4.0 * (h->g.dim == 3 ? NSLOT3 : NSLOT) * h->nbox), 0.0,
             launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->Jp, h->stream, h->rec_of_dev));
     else
         KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0,
@@ -860,7 +868,7 @@ int build_subdomains(acac_handle* h) {
                 h->lev.push_back(acc);
                 coef += (long long)acc * (dim == 2 ? NCOEF : NCOEF3);
                 const size_t pad = dim == 2 ? (size_t)ras_pitch(sd.W) * (sd.H + 4)
-                                            : (size_t)(sd.W + 4) * (sd.H + 4) * (sd.D + 4);
+                                            : (size_t)ras3_pitch(sd.W, (int)h->ksz) * (sd.H + 4) * (sd.D + 4);
                 vec += (long long)pad;
                 maxpad = std::max(maxpad, pad);
                 h->subs.push_back(sd);
@@ -868,6 +876,30 @@ int build_subdomains(acac_handle* h) {
         }
     }
     h->coef_count = coef;
+    if (dim == 3) {
+        // records of every grid cell: box cells before the box + lo[level] + position in the
+        // level's packed cell list (at most 8 boxes per cell)
+        const size_t ncell = (size_t)p.n[0] * p.n[1] * p.n[2];
+        h->rec_of.assign(8 * ncell, -1);
+        for (const SubInfo& sd : h->subs) {
+            const long long base = sd.coef_base / NCOEF3;
+            const size_t nbc = (size_t)sd.W * sd.H * sd.D;
+            for (size_t t = 0; t < nbc; ++t) {
+                const int pk = h->cells3[sd.cell_base + t];
+                const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
+                int gx = sd.ox + i, gy = sd.oy + j, gz = sd.oz + k;
+                gx = gx < 0 ? gx + p.n[0] : (gx >= p.n[0] ? gx - p.n[0] : gx);
+                gy = gy < 0 ? gy + p.n[1] : (gy >= p.n[1] ? gy - p.n[1] : gy);
+                gz = gz < 0 ? gz + p.n[2] : (gz >= p.n[2] ? gz - p.n[2] : gz);
+                const size_t gc = ((size_t)gz * p.n[1] + gy) * p.n[0] + gx;
+                const long long rec = base + (long long)t;   // the cell list is in level order
+                int q = 0;
+                while (q < 8 && h->rec_of[8 * gc + q] >= 0) ++q;
+                if (q == 8 || rec > INT32_MAX) return ACAC_E_ARG;
+                h->rec_of[8 * gc + q] = (int)rec;
+            }
+        }
+    }
     if (dim == 2) {
         // records of every grid cell: box cells before the box + lo[level] + position
         h->rec_of.assign((size_t)4 * p.n[0] * p.n[1], -1);
@@ -1145,10 +1177,34 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         int optin = 0;
         CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
         if (p->dim == 3) {
-            // 3D apply: the padded box vector in shared memory when it fits, else global
-            if (h->ras_smem > (size_t)optin - 2048) {
+            // 3D apply: mbarriers | level table | record stages (TMA ring) | padded box vector
+            // (shared memory when it fits, else global)
+            auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
+            RasLaunch& L = h->ras_launch;
+            L.window = 0;
+            L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
+            L.stage_elems = (CREC3 * h->ras_maxcnt + 31) / 32 * 32;
+            L.threads = 32 * ((2 * h->ras_maxcnt + 31) / 32) + 32;
+            const size_t vec_bytes = r128(h->ras_maxpad * 2 * ks);
+            const size_t stage_bytes = (size_t)L.stage_elems * ks;
+            const size_t cap = (size_t)optin - 2048, half = 113 * 1024;
+            // at least 4 stages in flight (fewer leave each level waiting on its copy): the
+            // vector in shared memory at two CTAs per SM, else at one CTA per SM, else in
+            // global scratch at two CTAs per SM
+            bool vec_in_smem = true;
+            if (L.stage_off + vec_bytes + 4 * stage_bytes <= half) {
+                L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (half - L.stage_off - vec_bytes) / stage_bytes);
+            } else if (L.stage_off + vec_bytes + 4 * stage_bytes <= cap) {
+                L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (cap - L.stage_off - vec_bytes) / stage_bytes);
+            } else {
+                vec_in_smem = false;
+                L.nbuf = (int)std::max<size_t>(2, std::min<size_t>(RAS_MAXBUF, (half - L.stage_off) / stage_bytes));
+            }
+            L.vec_off = (int)(L.stage_off + (size_t)L.nbuf * L.stage_elems * ks);
+            L.smem_bytes = L.vec_off + (vec_in_smem ? vec_bytes : 0);
+            if (!vec_in_smem) {
                 size_t tot = 0;
-                for (auto& sd : h->subs) tot += (size_t)(sd.W + 4) * (sd.H + 4) * (sd.D + 4);
+                for (auto& sd : h->subs) tot += (size_t)ras3_pitch(sd.W, (int)ks) * (sd.H + 4) * (sd.D + 4);
                 dmalloc(&h->gscratch, tot * 2 * ks);
             }
         } else {
@@ -1226,13 +1282,12 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         }
         CU(cudaMemcpy(h->subs_dev, h->subs.data(), h->subs.size() * sizeof(SubInfo), cudaMemcpyHostToDevice));
         CU(cudaMemcpy(h->lev_dev, h->lev.data(), h->lev.size() * sizeof(int), cudaMemcpyHostToDevice));
-        if (p->dim == 2) {
-            dmalloc(&h->rec_of_dev, h->rec_of.size() * sizeof(int));
-            CU(cudaMemcpy(h->rec_of_dev, h->rec_of.data(), h->rec_of.size() * sizeof(int), cudaMemcpyHostToDevice));
-            dmalloc(&h->Jp, (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
-            h->rec_of.clear();
-            h->rec_of.shrink_to_fit();
-        }
+        dmalloc(&h->rec_of_dev, h->rec_of.size() * sizeof(int));
+        CU(cudaMemcpy(h->rec_of_dev, h->rec_of.data(), h->rec_of.size() * sizeof(int), cudaMemcpyHostToDevice));
+        dmalloc(&h->Jp, p->dim == 3 ? (size_t)(h->coef_count / NCOEF3) * 4 * NSLOT3 * h->ksz
+                                    : (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
+        h->rec_of.clear();
+        h->rec_of.shrink_to_fit();
         CU(set_taylor_constants(p->taylor_S));
     } catch (Err e) {
         free_all(h);
