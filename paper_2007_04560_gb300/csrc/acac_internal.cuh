@@ -324,21 +324,45 @@ inline int red_grid(long long n) {
     return (int)(b < 1 ? 1 : (b > RED_BLOCKS ? RED_BLOCKS : b));
 }
 
-// Called by every thread of every block after the block's partials are written.
+// Sum of v over the warp, valid in lane 0.
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Called by every thread of every block after the block's partials are written.  The
+// last block sums up to eight quantities per pass: each warp adds its share of every
+// quantity's partials and leaves one value per (quantity, warp) in shared memory, then
+// one thread per quantity adds the warp values in order (two barriers per pass instead
+// of two per quantity).
 __device__ __forceinline__ void finish_reduction(const Red& r, int nv, double* sh) {
+    (void)sh;
     __shared__ int s_last;
+    __shared__ double s_w[8][32];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) s_last = atomicAdd(r.counter, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (int v = 0; v < nv; ++v) {
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x)
-            acc += __ldcg(r.partial + (size_t)v * RED_BLOCKS + i);
-        const double t = block_sum_red(acc, sh);
-        if (threadIdx.x == 0) r.out[v] = t;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = gridDim.x;
+    for (int v0 = 0; v0 < nv; v0 += 8) {
+        const int c = nv - v0 < 8 ? nv - v0 : 8;
+        for (int q = 0; q < c; ++q) {
+            const double* p = r.partial + (size_t)(v0 + q) * RED_BLOCKS;
+            double a = 0.0;
+            for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(p + i);
+            a = warp_sum(a);
+            if (lane == 0) s_w[q][warp] = a;
+        }
+        __syncthreads();
+        if ((int)threadIdx.x < c) {
+            double t = 0.0;
+            for (int k = 0; k < nw; ++k) t += s_w[threadIdx.x][k];
+            r.out[v0 + threadIdx.x] = t;
+        }
+        __syncthreads();
     }
     if (threadIdx.x == 0) *r.counter = 0u;
 }

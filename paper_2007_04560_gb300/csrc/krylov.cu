@@ -49,34 +49,59 @@ cudaError_t launch_norm2_double(const double* a, const double* b, long long n, R
 }
 
 // ---------------------------------------------------------------- V^T w
-// Vectors are processed in chunks of 8; each thread accumulates its share in the
-// Krylov precision, the block and global stages add in double.
+// Vectors are processed in chunks of up to 8, the chunk width a template parameter (a
+// predicated FP64 multiply-add still occupies the FP64 pipe, so a fixed 8-wide loop with
+// masked lanes cost 8 products per element whatever the count).  Each thread
+// accumulates its share in the Krylov precision; the block and global stages add in
+// double, the block stage with one barrier per chunk.
+template <typename T, int C>
+__device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld, const T* __restrict__ w,
+                                          long long n, double* __restrict__ partial, double (*sw)[RED_THREADS / 32]) {
+    T acc[C];
+#pragma unroll
+    for (int q = 0; q < C; ++q) acc[q] = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const T wi = w[i];
+#pragma unroll
+        for (int q = 0; q < C; ++q) acc[q] += V[(size_t)q * ld + i] * wi;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < C; ++q) {
+        const double t = warp_sum((double)acc[q]);
+        if (lane == 0) sw[q][warp] = t;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < C) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < RED_THREADS / 32; ++k) t += sw[threadIdx.x][k];
+        partial[(size_t)threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+    }
+    __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                 const T* __restrict__ w, long long n,
                                                                 Red red) {
-    __shared__ double sh[32];
+    __shared__ double sw[8][RED_THREADS / 32];
     for (int k0 = 0; k0 < nv; k0 += 8) {
-        const int cnt = nv - k0 < 8 ? nv - k0 : 8;
-        T acc[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) acc[q] = 0;
-        for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-             i += (long long)gridDim.x * blockDim.x) {
-            const T wi = w[i];
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (q < cnt) acc[q] += V[(size_t)(k0 + q) * ld + i] * wi;
-        }
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            if (q < cnt) {
-                const double t = block_sum_red((double)acc[q], sh);
-                if (threadIdx.x == 0) red.partial[(size_t)(k0 + q) * RED_BLOCKS + blockIdx.x] = t;
-            }
+        const T* Vk = V + (size_t)k0 * ld;
+        double* pk = red.partial + (size_t)k0 * RED_BLOCKS;
+        switch (nv - k0 < 8 ? nv - k0 : 8) {
+            case 1: dot_chunk<T, 1>(Vk, ld, w, n, pk, sw); break;
+            case 2: dot_chunk<T, 2>(Vk, ld, w, n, pk, sw); break;
+            case 3: dot_chunk<T, 3>(Vk, ld, w, n, pk, sw); break;
+            case 4: dot_chunk<T, 4>(Vk, ld, w, n, pk, sw); break;
+            case 5: dot_chunk<T, 5>(Vk, ld, w, n, pk, sw); break;
+            case 6: dot_chunk<T, 6>(Vk, ld, w, n, pk, sw); break;
+            case 7: dot_chunk<T, 7>(Vk, ld, w, n, pk, sw); break;
+            default: dot_chunk<T, 8>(Vk, ld, w, n, pk, sw); break;
         }
     }
-    finish_reduction(red, nv, sh);
+    finish_reduction(red, nv, nullptr);
 }
 
 template <typename T>
