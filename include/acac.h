@@ -60,6 +60,10 @@ extern "C" {
 #define ACAC_JAC_MATFREE     0    /* GMRES products by the analytic Jacobian action      */
 #define ACAC_JAC_ASSEMBLED   1    /* GMRES products by the assembled stencil matrix      */
 #define ACAC_MAX_BATCH       1024 /* largest ensemble (params.batch)                      */
+#define ACAC_SUB_ILU0        0    /* subdomain solve by ILU(0), no fill (Sec. 3.1)        */
+#define ACAC_SUB_ILU1        1    /* ILU with one level of fill (Sec. 4.2, Table 2)        */
+#define ACAC_SUB_ILU2        2    /* ILU with two levels of fill (Sec. 4.2, Table 2)       */
+#define ACAC_SUB_LU          3    /* exact LU of the subdomain matrix (Sec. 3.1, Table 2)  */
 
 /* Problem and solver settings.  Defaults: acac_default_params(). */
 typedef struct acac_params {
@@ -94,6 +98,11 @@ typedef struct acac_params {
                                    levels in shared memory (forward result in global
                                    scratch), 2 keep the whole box vector (shared memory when
                                    it fits, else global); same results                    */
+    int    subdomain_solver;    /* ACAC_SUB_*: how inv(A_k) is applied.  Levels of fill
+                                   follow the usual definition: lev = 0 on the pattern of
+                                   A_k, lev(i,j) = min(lev(i,j), lev(i,k) + lev(k,j) + 1)
+                                   in natural order, entries of lev <= p kept.  ILU(1),
+                                   ILU(2) and LU: FP64 and mixed; not with the adjoint.    */
 } acac_params;
 
 /* Per-step report. */

@@ -31,6 +31,10 @@ function that uses it:
     Neumann walls); each subdomain matrix is ordered lexicographically in the
     box's own coordinates, x fastest, u before v; ILU(0) is taken on the full
     2x2-block pattern of the radius-2 stencil.
+  * Subdomain solvers of Sec. 4.2 (Table 2): ILU(1) and ILU(2) keep the entries
+    whose level of fill is at most 1 or 2 (the usual recursive definition, in the
+    same natural order) and run the same elimination on that pattern; LU is the
+    exact solve with A_k.
 
 Parity pins for every function live in tests/test_oracle_*.py.
 """
@@ -55,6 +59,7 @@ E_DT_UNDERFLOW = -5
 
 BC_PERIODIC = 0
 BC_NEUMANN = 1
+SUB_ILU0, SUB_ILU1, SUB_ILU2, SUB_LU = 0, 1, 2, 3
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB = None
@@ -537,32 +542,106 @@ def subdomains(p):
     return out
 
 
+def fill_levels(indptr, indices, p=None):
+    """Pattern of ILU(p) for a sparse matrix given by its CSR pattern (sorted rows):
+    entries of A have level 0; eliminating row i in natural order, every entry
+    (i, k) left of the diagonal whose level is at most p, taken in increasing k,
+    gives the entries (i, j), j > k, of the upper part of row k the candidate level
+    lev(i, k) + lev(k, j) + 1, and lev(i, j) is the smallest candidate (Sec. 4.2,
+    "ILU factorizations with 0, 1 and 2 levels of fill-in").  Entries of level
+    <= p are kept; p = None keeps every fill entry (the pattern of LU).  Returns
+    (indptr, indices, levels) of the kept pattern, rows sorted."""
+    import heapq
+    n = len(indptr) - 1
+    cap = math.inf if p is None else p
+    rows = []                  # final {column: level} of each row
+    for i in range(n):
+        lev = {int(j): 0 for j in indices[indptr[i]:indptr[i + 1]]}
+        heap = [j for j in lev if j < i]
+        heapq.heapify(heap)
+        done = set()
+        while heap:
+            k = heapq.heappop(heap)
+            if k in done:
+                continue
+            done.add(k)
+            lik = lev[k]
+            for j, lkj in rows[k].items():
+                if j <= k:
+                    continue
+                cand = lik + lkj + 1
+                if cand > cap:
+                    continue
+                if j not in lev or cand < lev[j]:
+                    lev[j] = cand
+                    if j < i and j not in done:
+                        heapq.heappush(heap, j)
+        rows.append(lev)
+    out_ptr = np.zeros(n + 1, dtype=np.int64)
+    cols, levs = [], []
+    for i, lev in enumerate(rows):
+        js = sorted(lev)
+        cols.extend(js)
+        levs.extend(lev[j] for j in js)
+        out_ptr[i + 1] = len(cols)
+    return out_ptr, np.asarray(cols, dtype=np.int64), np.asarray(levs, dtype=np.int64)
+
+
+def ilu_factor(A, p=0):
+    """ILU(p) of the CSR matrix A in natural order: the IKJ elimination of ilu0.c on
+    the pattern of fill_levels(A, p) (A's values there, explicit zeros at the fill
+    entries).  Returns the factors as a CSR matrix (L strictly below the diagonal
+    with unit diagonal implied, U on and above) and the diagonal positions."""
+    A = A.tocsr()
+    A.sort_indices()
+    if p == 0:
+        ip, ind = A.indptr.astype(np.int64), A.indices.astype(np.int64)
+    else:
+        ip, ind, _ = fill_levels(A.indptr, A.indices, p)
+    n = A.shape[0]
+    data = np.zeros(ind.size)
+    for i in range(n):
+        cols = ind[ip[i]:ip[i + 1]]
+        a_cols = A.indices[A.indptr[i]:A.indptr[i + 1]]
+        pos = np.searchsorted(cols, a_cols)
+        data[ip[i] + pos] = A.data[A.indptr[i]:A.indptr[i + 1]]
+    F = sp.csr_matrix((data, ind.astype(np.int32), ip.astype(np.int32)), shape=A.shape)
+    indptr = F.indptr.astype(np.int32)
+    indices = F.indices.astype(np.int32)
+    vals = F.data.astype(np.float64).copy()
+    diag = np.zeros(n, dtype=np.int32)
+    st = _lib().oracle_ilu0_factor(n, _iptr(indptr), _iptr(indices), _dptr(vals), _iptr(diag))
+    if st != 0:
+        raise ZeroDivisionError("ILU(%d) pivot breakdown (status %d)" % (p, st))
+    return sp.csr_matrix((vals, indices, indptr), shape=A.shape), diag
+
+
 class RAS:
-    """Schwarz preconditioner of Eq. invM with ILU(0) subdomain solves.
+    """Schwarz preconditioner of Eq. invM with ILU(0), ILU(1), ILU(2) or exact LU
+    subdomain solves (p.subdomain_solver, Sec. 4.2 Table 2).
     kind: 'left' = restricted extension  sum_k R_k^0T inv(A_k) R_k^delta,
           'as'   = classical              sum_k R_k^dT inv(A_k) R_k^delta,
           'right'= restricted restriction sum_k R_k^dT inv(A_k) R_k^0."""
 
     def __init__(self, p, J, kind="left"):
         self.kind = kind
+        self.solver = getattr(p, "subdomain_solver", SUB_ILU0)
         self.subs = subdomains(p)
-        lib = _lib()
         for s in self.subs:
             s.idx = np.empty(2 * s.cells.size, dtype=np.int64)
             s.idx[0::2] = 2 * s.cells
             s.idx[1::2] = 2 * s.cells + 1
             A = J[s.idx][:, s.idx].tocsr()       # A_k = R_k J R_k^T
             A.sort_indices()
-            s.indptr = A.indptr.astype(np.int32)
-            s.indices = A.indices.astype(np.int32)
-            s.data = A.data.astype(np.float64).copy()
-            s.diag = np.zeros(A.shape[0], dtype=np.int32)
-            st = lib.oracle_ilu0_factor(A.shape[0], _iptr(s.indptr), _iptr(s.indices),
-                                        _dptr(s.data), _iptr(s.diag))
-            if st != 0:
-                raise ZeroDivisionError("ILU(0) pivot breakdown (status %d)" % st)
+            if self.solver == SUB_LU:
+                s.lu = scipy.linalg.lu_factor(A.toarray())
+                continue
+            F, s.diag = ilu_factor(A, self.solver)
+            s.indptr, s.indices, s.data = F.indptr, F.indices, F.data
 
     def solve_local(self, s, b):
+        if self.solver == SUB_LU:
+            return scipy.linalg.lu_solve(s.lu, b)
         x = np.zeros_like(b)
         _lib().oracle_ilu0_solve(b.size, _iptr(s.indptr), _iptr(s.indices), _dptr(s.data),
                                  _iptr(s.diag), _dptr(b), _dptr(x))

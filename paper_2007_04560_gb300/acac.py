@@ -45,7 +45,7 @@ class acac_params(ctypes.Structure):
         ("gmres_maxit", ctypes.c_int), ("ras_parts", ctypes.c_int * 3), ("ras_overlap", ctypes.c_int),
         ("ras_type", ctypes.c_int), ("ilu_reuse", ctypes.c_int), ("precision", ctypes.c_int),
         ("jac_mode", ctypes.c_int), ("batch", ctypes.c_int), ("cgs_refine", ctypes.c_int),
-        ("graphs", ctypes.c_int), ("ras_window", ctypes.c_int),
+        ("graphs", ctypes.c_int), ("ras_window", ctypes.c_int), ("subdomain_solver", ctypes.c_int),
     ]
 
 

@@ -28,6 +28,10 @@ PREC_FP64 = 0
 PREC_MIXED = 1
 JAC_MATFREE = 0
 JAC_ASSEMBLED = 1
+SUB_ILU0 = 0
+SUB_ILU1 = 1
+SUB_ILU2 = 2
+SUB_LU = 3
 
 
 @dataclass
@@ -66,6 +70,7 @@ class Params:
     cgs_refine: int = 1          # 1: CGS2 (two passes), 0: single classical pass
     graphs: int = 1              # 1: GMRES iterations replayed from captured CUDA graphs
     ras_window: int = 0          # 2D Schwarz apply: 0 choose, 1 level window, 2 whole box vector
+    subdomain_solver: int = SUB_ILU0   # ILU(0), ILU(1), ILU(2) or LU (Sec. 4.2, Table 2)
 
     def replace(self, **kw) -> "Params":
         return dataclasses.replace(self, **kw)
