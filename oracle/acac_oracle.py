@@ -640,7 +640,7 @@ class RAS:
             s.indptr, s.indices, s.data = F.indptr, F.indices, F.data
 
     def solve_local(self, s, b):
-        if self.solver == SUB_LU:
+        if getattr(s, "lu", None) is not None:      # exact LU of this subdomain
             return scipy.linalg.lu_solve(s.lu, b)
         x = np.zeros_like(b)
         _lib().oracle_ilu0_solve(b.size, _iptr(s.indptr), _iptr(s.indices), _dptr(s.data),
