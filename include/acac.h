@@ -365,6 +365,18 @@ int acac_kernel_stats(acac_handle *h, int kernel, long long *launches, double *t
 /* Static name of a kernel class. */
 const char *acac_kernel_name(int kernel);
 
+/* Block pattern of a subdomain factorization with fill (Sec. 4.2, Table 2), host only (no
+ * GPU, no handle): the box of W x H (x D) cells in natural order (x fastest), the radius-2
+ * stencil of dimension dim, solver ACAC_SUB_ILU1, ACAC_SUB_ILU2 or ACAC_SUB_LU.  One
+ * entry per kept 2x2 block (cell pair): row ptr[c]..ptr[c+1]-1 of col holds the kept
+ * columns (cell indices) of cell c, sorted.  ptr has n + 1 = W H D + 1 entries and col
+ * room for cap entries; *nnz receives the count.  ILU: levels of fill as described at
+ * acac_params.subdomain_solver; LU: the profile of each row, a superset of the exact
+ * factorization's fill.  ACAC_E_ARG on bad sizes or a cap below *nnz (then only *nnz is
+ * written). */
+int acac_subdomain_pattern(int dim, int W, int H, int D, int solver, int *ptr, int *col, long long cap,
+                           long long *nnz);
+
 #ifdef __cplusplus
 }
 #endif

@@ -87,6 +87,8 @@ SIGNATURES = {
     "acac_log": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_profile_mask": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "acac_subdomain_pattern": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              _PI, _PI, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),
     "acac_kernel_name": (ctypes.c_char_p, [ctypes.c_int]),
     "acac_set_coeffs": (ctypes.c_int, [_P, ctypes.c_int, _D, _D, _D, _D, _D]),
@@ -204,6 +206,22 @@ def acac_log(x, y, stream=None):
         stream = torch.cuda.current_stream()
     _check(_lib().acac_log(_dev(x, torch.float64, None, "x"), _dev(y, torch.float64, x.numel(), "y"),
                            x.numel(), ctypes.c_void_p(stream.cuda_stream)), "acac_log")
+
+
+def acac_subdomain_pattern(dim, W, H, D, solver):
+    """(ptr, col) numpy arrays of the block pattern of a subdomain factorization with fill
+    (host only; see include/acac.h)."""
+    import numpy as np
+    n = W * H * (D if dim == 3 else 1)
+    nnz = ctypes.c_longlong(0)
+    st = _lib().acac_subdomain_pattern(dim, W, H, D, solver, None, None, 0, ctypes.byref(nnz))
+    if nnz.value == 0:
+        _check(st, "acac_subdomain_pattern")
+    ptr = np.zeros(n + 1, dtype=np.int32)
+    col = np.zeros(max(1, nnz.value), dtype=np.int32)
+    _check(_lib().acac_subdomain_pattern(dim, W, H, D, solver, ptr.ctypes.data_as(_PI), col.ctypes.data_as(_PI),
+                                         nnz.value, ctypes.byref(nnz)), "acac_subdomain_pattern")
+    return ptr, col[:nnz.value]
 
 
 def acac_autotune(p, u, v, trial_steps=3, stream=None):

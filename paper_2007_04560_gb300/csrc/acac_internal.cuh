@@ -463,4 +463,44 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s);
 
+// subsolve.cu: subdomain solves with fill, ILU(1), ILU(2) and exact LU (Sec. 4.2, Table 2).
+// The box matrix A_k is stored by 2x2 blocks on a pattern over the box's cells in natural
+// order (x fastest); the pattern is that of the point factorization (the level of fill of
+// a point entry is that of its cell pair, since every 2x2 block of A_k is full).
+struct SparseShape {                 // host: symbolic factorization of one box shape
+    int dim, W, H, D, n;             // box size, cells
+    int band;                        // max |column - row| of the pattern (cells)
+    std::vector<int> ptr, col, diag; // CSR of blocks, rows sorted; position of the pivot block
+    std::vector<int> slot_pos;       // n x nslot: block of each stencil slot, -1 outside the box
+    std::vector<int> flev_ptr, flev_rows;   // forward (L) dependency levels and their rows
+    std::vector<int> blev_ptr, blev_rows;   // backward (U) dependency levels
+};
+// fill = 1 or 2: ILU(fill) by levels of fill; fill < 0: LU (every entry of the profile).
+SparseShape build_sparse_shape(int dim, int W, int H, int D, int fill);
+
+struct SparseShapeDev {              // device view of a SparseShape
+    const int *ptr, *col, *diag, *slot_pos, *flev_ptr, *flev_rows, *blev_ptr, *blev_rows;
+    int n, band, nflev, nblev;
+};
+struct SparseBox {
+    int shape;                       // index of its SparseShapeDev
+    long long blk_base;              // first 2x2 block of the box in the value array
+    long long cell_base;             // first cell of the box (pivot inverses, scratch vector)
+};
+// A_k of every box from the stencil-diagonal Jacobian J (values zeroed beforehand)
+template <typename T>
+cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
+                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s);
+// block IKJ factorization in place; D^-1 of every cell to dinv; bit 2 of *flags on a
+// singular pivot block.  smem: (threads / 32) x (2 band + 1) ints.
+template <typename T>
+cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
+                                 int* flags, int threads, size_t smem, cudaStream_t s);
+// z = sum_k E_k inv(L_k U_k) R_k r with the restrictions and extensions of ras_type; the
+// box vector in shared memory (smem > 0) or in yscratch (2 values per box cell)
+template <typename T>
+cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
+                                const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
+                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s);
+
 }  // namespace acac

@@ -144,6 +144,17 @@ struct acac_handle {
     void* Jp = nullptr;          // Jacobian rows per box cell (52 values each in 2D, 100 in 3D)
     bool jpacked = false;        // Jp holds the current Jacobian (assembled straight into it)
     int *cells3_dev, *pos3_dev;
+    // subdomain solves with fill (params.subdomain_solver != ILU(0)): patterns per box shape
+    std::vector<SparseShape> sshape;
+    SparseShapeDev* sshape_dev = nullptr;
+    SparseBox* sbox_dev = nullptr;
+    int* sint_dev = nullptr;     // every shape's integer tables
+    void* sval = nullptr;        // 2x2 blocks of every box matrix (factored in place)
+    void* sdinv = nullptr;       // inverse pivot blocks, 4 values per box cell
+    void* sy = nullptr;          // box vectors of the apply when they do not fit shared memory
+    long long sblocks = 0, scells = 0;
+    int s_threads = 32;
+    size_t s_fsmem = 0, s_asmem = 0;
     int ras_threads;
     size_t ras_smem;
     RasLaunch ras_launch;
@@ -377,6 +388,14 @@ void jac_action(acac_handle* h, const T* w, T* y) {
 
 template <typename T>
 void precond(acac_handle* h, const T* r, T* z) {
+    if (h->p.subdomain_solver != ACAC_SUB_ILU0) {
+        KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (4.0 * h->sblocks + 4.0 * h->scells + 4.0 * h->N),
+            16.0 * h->sblocks,
+            launch_sparse_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->sbox_dev, h->sshape_dev,
+                                   (const T*)h->sval, (const T*)h->sdinv, r, z, h->p.ras_type, (T*)h->sy,
+                                   h->s_threads, h->s_asmem, h->stream));
+        return;
+    }
     if (h->g.dim == 3) {
         KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (104.0 * h->nbox + 4.0 * h->N), 200.0 * h->nbox,
             launch_ras_apply3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev,
@@ -393,6 +412,20 @@ void precond(acac_handle* h, const T* r, T* z) {
 template <typename T>
 int factor(acac_handle* h) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    if (h->p.subdomain_solver != ACAC_SUB_ILU0) {
+        // A_k of every box from the stencil-diagonal Jacobian, then the block IKJ
+        // elimination on the ILU(1) / ILU(2) / LU pattern
+        CU(cudaMemsetAsync(h->sval, 0, (size_t)h->sblocks * 4 * sizeof(T), h->stream));
+        KLA(ACAC_K_REPACK, (double)sizeof(T) * (4.0 * h->sblocks + 4.0 * (h->g.dim == 3 ? NSLOT3 : NSLOT) * h->N),
+            0.0,
+            launch_sparse_init<T>(h->g, (int)h->subs.size(), h->subs_dev, h->sbox_dev, h->sshape_dev,
+                                  (const T*)h->J, (T*)h->sval, h->stream));
+        KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 8.0 * h->sblocks, 0.0,
+            launch_sparse_factor<T>((int)h->subs.size(), h->sbox_dev, h->sshape_dev, (T*)h->sval, (T*)h->sdinv,
+                                    h->flags, h->s_threads, h->s_fsmem, h->stream));
+        h->n_factor++;
+        return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+    }
     if (h->g.dim == 3) {
         int packed3 = h->jpacked ? 1 : 0;
         if (!packed3 && sizeof(T) == 4) {
@@ -621,7 +654,7 @@ void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bo
     if (!assemble) return;
     // with matrix-free products the assembled Jacobian feeds only the subdomain
     // factorization: in 2D assemble it straight into the factorization's records
-    h->jpacked = h->p.jac_mode == ACAC_JAC_MATFREE;
+    h->jpacked = h->p.jac_mode == ACAC_JAC_MATFREE && h->p.subdomain_solver == ACAC_SUB_ILU0;
     if (h->jpacked)
         KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * (7.0 * h->N + 4.0 * (h->g.dim == 3 ? NSLOT3 : NSLOT) * h->nbox), 0.0,
             launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->Jp, h->stream, h->rec_of_dev));
@@ -967,16 +1000,90 @@ int acac::validate_params(const acac_params* p) {
     if (p->batch < 1 || p->batch > ACAC_MAX_BATCH) return ACAC_E_ARG;
     if (p->graphs != 0 && p->graphs != 1) return ACAC_E_ARG;
     if (p->ras_window < 0 || p->ras_window > 2) return ACAC_E_ARG;
+    if (p->subdomain_solver < ACAC_SUB_ILU0 || p->subdomain_solver > ACAC_SUB_LU) return ACAC_E_ARG;
     return ACAC_OK;
 }
 
 namespace {
 
+// Patterns, dependency levels and device tables of the subdomain solves with fill: one
+// symbolic factorization per distinct box shape, values and pivot inverses per box.
+void build_sparse(acac_handle* h) {
+    const acac_params& p = h->p;
+    const int fill = p.subdomain_solver == ACAC_SUB_LU ? -1 : p.subdomain_solver;
+    std::vector<SparseBox> boxes;
+    std::vector<long long> keys;
+    long long blk = 0, cells = 0;
+    for (const SubInfo& sd : h->subs) {
+        const long long key = ((long long)sd.W << 40) | ((long long)sd.H << 20) | (long long)sd.D;
+        int id = (int)(std::find(keys.begin(), keys.end(), key) - keys.begin());
+        if (id == (int)keys.size()) {
+            keys.push_back(key);
+            h->sshape.push_back(build_sparse_shape(p.dim, sd.W, sd.H, sd.D, fill));
+        }
+        boxes.push_back(SparseBox{id, blk, cells});
+        blk += h->sshape[id].ptr.back();
+        cells += h->sshape[id].n;
+    }
+    h->sblocks = blk;
+    h->scells = cells;
+    // integer tables of all shapes in one device array
+    std::vector<int> ints;
+    struct Off8 { size_t o[8]; };
+    std::vector<Off8> offs;
+    int band = 0, width = 1, maxn = 0;
+    for (const SparseShape& S : h->sshape) {
+        Off8 o;
+        const std::vector<int>* parts[8] = {&S.ptr, &S.col, &S.diag, &S.slot_pos, &S.flev_ptr, &S.flev_rows,
+                                            &S.blev_ptr, &S.blev_rows};
+        for (int q = 0; q < 8; ++q) {
+            o.o[q] = ints.size();
+            ints.insert(ints.end(), parts[q]->begin(), parts[q]->end());
+            ints.resize((ints.size() + 3) & ~(size_t)3);
+        }
+        offs.push_back(o);
+        band = std::max(band, S.band);
+        maxn = std::max(maxn, S.n);
+        for (size_t l = 0; l + 1 < S.flev_ptr.size(); ++l) width = std::max(width, S.flev_ptr[l + 1] - S.flev_ptr[l]);
+        for (size_t l = 0; l + 1 < S.blev_ptr.size(); ++l) width = std::max(width, S.blev_ptr[l + 1] - S.blev_ptr[l]);
+    }
+    dmalloc(&h->sint_dev, ints.size() * sizeof(int));
+    CU(cudaMemcpy(h->sint_dev, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<SparseShapeDev> sd(h->sshape.size());
+    for (size_t t = 0; t < sd.size(); ++t) {
+        const SparseShape& S = h->sshape[t];
+        const int* b = h->sint_dev;
+        sd[t] = SparseShapeDev{b + offs[t].o[0], b + offs[t].o[1], b + offs[t].o[2], b + offs[t].o[3],
+                               b + offs[t].o[4], b + offs[t].o[5], b + offs[t].o[6], b + offs[t].o[7],
+                               S.n, S.band, (int)S.flev_ptr.size() - 1, (int)S.blev_ptr.size() - 1};
+    }
+    dmalloc(&h->sshape_dev, sd.size() * sizeof(SparseShapeDev));
+    CU(cudaMemcpy(h->sshape_dev, sd.data(), sd.size() * sizeof(SparseShapeDev), cudaMemcpyHostToDevice));
+    dmalloc(&h->sbox_dev, boxes.size() * sizeof(SparseBox));
+    CU(cudaMemcpy(h->sbox_dev, boxes.data(), boxes.size() * sizeof(SparseBox), cudaMemcpyHostToDevice));
+    dmalloc(&h->sval, (size_t)blk * 4 * h->ksz);
+    dmalloc(&h->sdinv, (size_t)cells * 4 * h->ksz);
+    // one warp per row of a dependency level, at most 8
+    h->s_threads = 32 * std::min(8, width);
+    h->s_fsmem = (size_t)(h->s_threads / 32) * (2 * band + 1) * sizeof(int);
+    const size_t vec = (size_t)maxn * 2 * h->ksz;
+    if (vec <= 96 * 1024) {
+        h->s_asmem = vec;
+    } else {
+        h->s_asmem = 0;
+        dmalloc(&h->sy, (size_t)cells * 2 * h->ksz);
+    }
+    for (SparseShape& S : h->sshape) {   // the device holds what the kernels need
+        S.col.clear(); S.col.shrink_to_fit();
+        S.slot_pos.clear(); S.slot_pos.shrink_to_fit();
+    }
+}
 
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
-                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp};
+                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
+                    h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->host) cudaFreeHost(h->host);
@@ -1288,6 +1395,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
                                     : (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
         h->rec_of.clear();
         h->rec_of.shrink_to_fit();
+        if (p->subdomain_solver != ACAC_SUB_ILU0) build_sparse(h);
         CU(set_taylor_constants(p->taylor_S));
     } catch (Err e) {
         free_all(h);
@@ -1624,7 +1732,7 @@ int acac_loss(acac_handle* h, const double* X, const double* target, double w_en
 
 int acac_adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, const double* lam1,
                       double* lam0, double* grad, double rtol, int* gmres_its) {
-    if (is_ensemble(h) || (h && h->mixed)) return ACAC_E_ARG;
+    if (is_ensemble(h) || (h && (h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0))) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !lam1 || !lam0 || !(dt > 0) || !(rtol > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1645,7 +1753,7 @@ int acac_adjoint_step(acac_handle* h, const double* X1, const double* X0, double
 int acac_adjoint(acac_handle* h, const double* u0, const double* v0, int nsteps, double dt, int checkpoint_every,
                  const double* u_target, const double* v_target, double w_energy, double w_misfit, double rtol,
                  double* loss, double* du0, double* dv0, double* grad, int* gmres_its) {
-    if (is_ensemble(h) || (h && h->mixed)) return ACAC_E_ARG;
+    if (is_ensemble(h) || (h && (h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0))) return ACAC_E_ARG;
     if (!h || !u0 || !v0 || !u_target || !v_target || !du0 || !dv0 || nsteps < 1 || !(dt > 0) ||
         checkpoint_every < 1 || !(rtol > 0))
         return ACAC_E_ARG;
@@ -1895,6 +2003,23 @@ int acac_step_host(acac_handle* h, double* u_host, double* v_host, acac_step_inf
         return st;
     } catch (Err e) {
         return e.code;
+    }
+}
+
+int acac_subdomain_pattern(int dim, int W, int H, int D, int solver, int* ptr, int* col, long long cap,
+                           long long* nnz) {
+    if ((dim != 2 && dim != 3) || W < 1 || H < 1 || (dim == 3 && D < 1) || !nnz) return ACAC_E_ARG;
+    if (solver != ACAC_SUB_ILU1 && solver != ACAC_SUB_ILU2 && solver != ACAC_SUB_LU) return ACAC_E_ARG;
+    if ((long long)W * H * (dim == 3 ? D : 1) > 250LL * 250) return ACAC_E_ARG;
+    try {
+        const SparseShape S = build_sparse_shape(dim, W, H, D, solver == ACAC_SUB_LU ? -1 : solver);
+        *nnz = (long long)S.col.size();
+        if (!ptr || !col || cap < *nnz) return ACAC_E_ARG;
+        std::copy(S.ptr.begin(), S.ptr.end(), ptr);
+        std::copy(S.col.begin(), S.col.end(), col);
+        return ACAC_OK;
+    } catch (...) {
+        return ACAC_E_NOMEM;
     }
 }
 

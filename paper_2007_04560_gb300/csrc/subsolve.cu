@@ -1,0 +1,425 @@
+// Subdomain solves with fill for the Schwarz preconditioner (Sec. 3.1, and the
+// subdomain-solver comparison of Sec. 4.2, Table 2): ILU(1), ILU(2) and exact LU of the
+// box matrices A_k, beside the fill-free wavefront ILU(0) of ras.cu.
+//
+// Every box matrix is stored by 2x2 blocks on a pattern over the box's cells in natural
+// order (x fastest, then y, then z).  Since every 2x2 block of A_k is full, the level of
+// fill of a point entry is that of its pair of cells, and the point factorization in
+// u-before-v order keeps whole blocks: the block IKJ elimination on the cell pattern
+// gives the same factors.  The pattern is built on the host once per box shape:
+//   ILU(p): levels of fill, lev = 0 on the stencil, lev(i,j) = min over the eliminated
+//           k < i of lev(i,k) + lev(k,j) + 1, entries of level <= p kept;
+//   LU:     every entry of the profile (fill never leaves the row's first stencil
+//           column on the left, nor a column's first stencil row above), a superset of
+//           the fill of the exact factorization, which keeps its values exact.
+// The factorization and the two triangular sweeps run level by level over the rows'
+// dependency levels, one CTA per box and one warp per row of a level.
+#include <algorithm>
+#include <functional>
+#include <queue>
+
+#include "acac_internal.cuh"
+
+namespace acac {
+
+// ---------------------------------------------------------------- host: symbolic
+namespace {
+struct Off { int dx, dy, dz; };
+
+std::vector<Off> stencil(int dim) {
+    std::vector<Off> o;
+    if (dim == 2)
+        for (int s = 0; s < NSLOT; ++s) o.push_back({slot_dx(s), slot_dy(s), 0});
+    else
+        for (int s = 0; s < NSLOT3; ++s) o.push_back({s3_dx(s), s3_dy(s), s3_dz(s)});
+    return o;
+}
+
+// rows' dependency levels: lev[i] = 1 + max lev over deps(i), in the given visiting order
+void levels_of(int n, const std::vector<int>& lev, std::vector<int>& ptr, std::vector<int>& rows) {
+    int nl = 0;
+    for (int i = 0; i < n; ++i) nl = std::max(nl, lev[i] + 1);
+    ptr.assign(nl + 1, 0);
+    for (int i = 0; i < n; ++i) ptr[lev[i] + 1]++;
+    for (int l = 0; l < nl; ++l) ptr[l + 1] += ptr[l];
+    rows.assign(n, 0);
+    std::vector<int> fillp(ptr.begin(), ptr.end() - 1);
+    for (int i = 0; i < n; ++i) rows[fillp[lev[i]]++] = i;
+}
+}  // namespace
+
+SparseShape build_sparse_shape(int dim, int W, int H, int D, int fill) {
+    SparseShape S;
+    S.dim = dim;
+    S.W = W;
+    S.H = H;
+    S.D = dim == 3 ? D : 1;
+    const int n = W * H * S.D;
+    S.n = n;
+    const std::vector<Off> st = stencil(dim);
+    const int ns = (int)st.size();
+    auto nb = [&](int c, const Off& o) {
+        const int i = c % W, j = (c / W) % H, k = c / (W * H);
+        const int ii = i + o.dx, jj = j + o.dy, kk = k + o.dz;
+        if (ii < 0 || ii >= W || jj < 0 || jj >= H || kk < 0 || kk >= S.D) return -1;
+        return ii + W * (jj + H * kk);
+    };
+    std::vector<std::vector<int>> cols(n);
+    if (fill < 0) {
+        // LU: the profile.  lo[i] = first stencil column of row i; the upper part of row
+        // i holds the columns j >= i whose first stencil row lo[j] (the structure is
+        // symmetric) is at most i: up to hi[i] = max{j : lo[j] <= i}
+        std::vector<int> lo(n), best(n, -1), hi(n);
+        for (int c = 0; c < n; ++c) {
+            int m = c;
+            for (const Off& o : st) {
+                const int t = nb(c, o);
+                if (t >= 0) m = std::min(m, t);
+            }
+            lo[c] = m;
+            best[m] = std::max(best[m], c);
+        }
+        int run = -1;
+        for (int i = 0; i < n; ++i) {
+            run = std::max(run, best[i]);
+            hi[i] = std::max(run, i);
+        }
+        for (int i = 0; i < n; ++i)
+            for (int j = lo[i]; j <= hi[i]; ++j) cols[i].push_back(j);
+    } else {
+        // ILU(fill): levels of fill, eliminating row i's entries left of the diagonal in
+        // increasing column order (fill entries created on the way included)
+        const int INF = 1 << 29;
+        std::vector<std::vector<std::pair<int, int>>> rows(n);   // (column, level), sorted
+        std::vector<int> lev(n, INF);
+        std::vector<int> touched;
+        for (int i = 0; i < n; ++i) {
+            touched.clear();
+            std::priority_queue<int, std::vector<int>, std::greater<int>> pq;
+            for (const Off& o : st) {
+                const int t = nb(i, o);
+                if (t < 0) continue;
+                lev[t] = 0;
+                touched.push_back(t);
+                if (t < i) pq.push(t);
+            }
+            int last = -1;
+            while (!pq.empty()) {
+                const int k = pq.top();
+                pq.pop();
+                if (k == last) continue;
+                last = k;
+                const int lik = lev[k];
+                for (const auto& e : rows[k]) {
+                    if (e.first <= k) continue;
+                    const int cand = lik + e.second + 1;
+                    if (cand > fill || cand >= lev[e.first]) continue;
+                    if (lev[e.first] == INF) {
+                        touched.push_back(e.first);
+                        if (e.first < i) pq.push(e.first);
+                    }
+                    lev[e.first] = cand;
+                }
+            }
+            std::sort(touched.begin(), touched.end());
+            for (int j : touched) {
+                rows[i].push_back({j, lev[j]});
+                cols[i].push_back(j);
+                lev[j] = INF;
+            }
+        }
+    }
+    S.ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) S.ptr[i + 1] = S.ptr[i] + (int)cols[i].size();
+    S.col.reserve(S.ptr[n]);
+    S.diag.assign(n, -1);
+    S.band = 0;
+    for (int i = 0; i < n; ++i) {
+        for (int j : cols[i]) {
+            if (j == i) S.diag[i] = (int)S.col.size();
+            S.band = std::max(S.band, std::abs(j - i));
+            S.col.push_back(j);
+        }
+    }
+    S.slot_pos.assign((size_t)n * ns, -1);
+    for (int i = 0; i < n; ++i)
+        for (int s = 0; s < ns; ++s) {
+            const int t = nb(i, st[s]);
+            if (t < 0) continue;
+            const auto b = S.col.begin() + S.ptr[i], e = S.col.begin() + S.ptr[i + 1];
+            const auto it = std::lower_bound(b, e, t);
+            S.slot_pos[(size_t)i * ns + s] = (int)(it - S.col.begin());
+        }
+    // dependency levels: forward through L (columns < i), backward through U (> i)
+    std::vector<int> fl(n, 0), bl(n, 0);
+    for (int i = 0; i < n; ++i)
+        for (int p = S.ptr[i]; p < S.diag[i]; ++p) fl[i] = std::max(fl[i], fl[S.col[p]] + 1);
+    for (int i = n - 1; i >= 0; --i)
+        for (int p = S.diag[i] + 1; p < S.ptr[i + 1]; ++p) bl[i] = std::max(bl[i], bl[S.col[p]] + 1);
+    levels_of(n, fl, S.flev_ptr, S.flev_rows);
+    levels_of(n, bl, S.blev_ptr, S.blev_rows);
+    return S;
+}
+
+// ---------------------------------------------------------------- device
+namespace {
+
+__device__ __forceinline__ int global_cell(const Geom& g, const SubInfo& sd, int c, int& i, int& j, int& k) {
+    i = c % sd.W;
+    j = (c / sd.W) % sd.H;
+    k = c / (sd.W * sd.H);
+    const bool per = g.bc == ACAC_BC_PERIODIC;
+    const int gx = wrap_or_clamp(sd.ox + i, g.nx, per), gy = wrap_or_clamp(sd.oy + j, g.ny, per);
+    const int gz = g.dim == 3 ? wrap_or_clamp(sd.oz + k, g.nz, per) : 0;
+    return (gz * g.ny + gy) * g.nx + gx;
+}
+
+__device__ __forceinline__ bool owned(const SubInfo& sd, int i, int j, int k) {
+    return i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1 && k >= sd.own_z0 && k < sd.own_z1;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sum_d(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+}  // namespace
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) sparse_init_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                          const SparseBox* __restrict__ boxes,
+                                                          const SparseShapeDev* __restrict__ shapes,
+                                                          const T* __restrict__ J, T* __restrict__ val) {
+    const SubInfo sd = subs[blockIdx.x];
+    const SparseBox bx = boxes[blockIdx.x];
+    const SparseShapeDev sh = shapes[bx.shape];
+    constexpr int NS = nslot<DIM>();
+    const size_t N = (size_t)g.N;
+    T* A = val + 4 * bx.blk_base;
+    for (int c = threadIdx.x; c < sh.n; c += blockDim.x) {
+        int i, j, k;
+        const int gc = global_cell(g, sd, c, i, j, k);
+#pragma unroll
+        for (int s = 0; s < NS; ++s) {
+            const int pos = sh.slot_pos[(size_t)c * NS + s];
+            if (pos < 0) continue;
+#pragma unroll
+            for (int e = 0; e < 4; ++e) A[4 * (size_t)pos + e] = J[(size_t)(s * 4 + e) * N + gc];
+        }
+    }
+}
+
+// Block IKJ elimination of row i, one warp per row of a dependency level:
+//   for k in L(i) ascending:  L_ik = A_ik D_k^-1;  A_ij -= L_ik U_kj  for j in U(k) kept in row i
+//   D_i = A_ii, its inverse stored.
+// The warp's map (2 band + 1 ints in shared memory) takes a column offset j - i + band
+// to the position of (i, j) in row i, -1 where row i keeps no entry (the update dropped).
+template <typename T>
+__global__ void __launch_bounds__(256) sparse_factor_kernel(const SparseBox* __restrict__ boxes,
+                                                            const SparseShapeDev* __restrict__ shapes,
+                                                            T* __restrict__ val, T* __restrict__ dinv, int* flags) {
+    extern __shared__ int smap[];
+    const SparseBox bx = boxes[blockIdx.x];
+    const SparseShapeDev sh = shapes[bx.shape];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int B = sh.band, MW = 2 * B + 1;
+    int* map = smap + (size_t)warp * MW;
+    for (int t = lane; t < MW; t += 32) map[t] = -1;
+    __syncwarp();
+    T* A = val + 4 * bx.blk_base;
+    T* Di = dinv + 4 * bx.cell_base;
+    int bad = 0;
+    for (int lv = 0; lv < sh.nflev; ++lv) {
+        for (int q = sh.flev_ptr[lv] + warp; q < sh.flev_ptr[lv + 1]; q += nw) {
+            const int i = sh.flev_rows[q];
+            const int p0 = sh.ptr[i], p1 = sh.ptr[i + 1], pd = sh.diag[i];
+            for (int p = p0 + lane; p < p1; p += 32) map[sh.col[p] - i + B] = p;
+            __syncwarp();
+            for (int p = p0; p < pd; ++p) {
+                const int k = sh.col[p];
+                const T* dk = Di + 4 * (size_t)k;
+                const T a00 = A[4 * (size_t)p], a01 = A[4 * (size_t)p + 1];
+                const T a10 = A[4 * (size_t)p + 2], a11 = A[4 * (size_t)p + 3];
+                const T l00 = a00 * dk[0] + a01 * dk[2], l01 = a00 * dk[1] + a01 * dk[3];
+                const T l10 = a10 * dk[0] + a11 * dk[2], l11 = a10 * dk[1] + a11 * dk[3];
+                __syncwarp();
+                if (lane == 0) {
+                    A[4 * (size_t)p] = l00;
+                    A[4 * (size_t)p + 1] = l01;
+                    A[4 * (size_t)p + 2] = l10;
+                    A[4 * (size_t)p + 3] = l11;
+                }
+                const int u1 = sh.ptr[k + 1];
+                for (int u = sh.diag[k] + 1 + lane; u < u1; u += 32) {
+                    const int t = map[sh.col[u] - i + B];
+                    if (t < 0) continue;
+                    const T* U = A + 4 * (size_t)u;
+                    T* X = A + 4 * (size_t)t;
+                    const T u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
+                    X[0] -= l00 * u00 + l01 * u10;
+                    X[1] -= l00 * u01 + l01 * u11;
+                    X[2] -= l10 * u00 + l11 * u10;
+                    X[3] -= l10 * u01 + l11 * u11;
+                }
+                __syncwarp();
+            }
+            if (lane == 0) {
+                const T* d = A + 4 * (size_t)pd;
+                const T det = d[0] * d[3] - d[1] * d[2];
+                if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
+                const T id = (T)1 / det;
+                T* o = Di + 4 * (size_t)i;
+                o[0] = d[3] * id;
+                o[1] = -d[1] * id;
+                o[2] = -d[2] * id;
+                o[3] = d[0] * id;
+            }
+            for (int p = p0 + lane; p < p1; p += 32) map[sh.col[p] - i + B] = -1;
+            __syncwarp();
+        }
+        __syncthreads();
+    }
+    if (bad) atomicOr(flags, 4);
+}
+
+// Restriction, forward sweep y_i = r_i - sum_{k<i} L_ik y_k, backward sweep
+// z_i = D_i^-1 (y_i - sum_{j>i} U_ij z_j), extension; one warp per row of a level, the
+// row's blocks over the lanes.
+template <typename T>
+__global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo* __restrict__ subs,
+                                                           const SparseBox* __restrict__ boxes,
+                                                           const SparseShapeDev* __restrict__ shapes,
+                                                           const T* __restrict__ val, const T* __restrict__ dinv,
+                                                           const T* __restrict__ r, T* __restrict__ z, int ras_type,
+                                                           T* yscratch, int in_smem) {
+    extern __shared__ __align__(16) unsigned char sraw[];
+    const SubInfo sd = subs[blockIdx.x];
+    const SparseBox bx = boxes[blockIdx.x];
+    const SparseShapeDev sh = shapes[bx.shape];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    T* y = in_smem ? reinterpret_cast<T*>(sraw) : yscratch + 2 * bx.cell_base;
+    const T* A = val + 4 * bx.blk_base;
+    const T* Di = dinv + 4 * bx.cell_base;
+    const size_t N = (size_t)g.N;
+    for (int c = threadIdx.x; c < sh.n; c += blockDim.x) {
+        int i, j, k;
+        const int gc = global_cell(g, sd, c, i, j, k);
+        const bool keep = ras_type != ACAC_RAS_RIGHT || owned(sd, i, j, k);
+        y[2 * c] = keep ? r[gc] : (T)0;
+        y[2 * c + 1] = keep ? r[N + gc] : (T)0;
+    }
+    __syncthreads();
+    for (int lv = 0; lv < sh.nflev; ++lv) {
+        for (int q = sh.flev_ptr[lv] + warp; q < sh.flev_ptr[lv + 1]; q += nw) {
+            const int i = sh.flev_rows[q];
+            T s0 = (T)0, s1 = (T)0;
+            for (int p = sh.ptr[i] + lane; p < sh.diag[i]; p += 32) {
+                const T* a = A + 4 * (size_t)p;
+                const int c = sh.col[p];
+                const T y0 = y[2 * c], y1 = y[2 * c + 1];
+                s0 += a[0] * y0 + a[1] * y1;
+                s1 += a[2] * y0 + a[3] * y1;
+            }
+            s0 = warp_sum_d(s0);
+            s1 = warp_sum_d(s1);
+            if (lane == 0) {
+                y[2 * i] -= s0;
+                y[2 * i + 1] -= s1;
+            }
+        }
+        __syncthreads();
+    }
+    for (int lv = 0; lv < sh.nblev; ++lv) {
+        for (int q = sh.blev_ptr[lv] + warp; q < sh.blev_ptr[lv + 1]; q += nw) {
+            const int i = sh.blev_rows[q];
+            T s0 = (T)0, s1 = (T)0;
+            for (int p = sh.diag[i] + 1 + lane; p < sh.ptr[i + 1]; p += 32) {
+                const T* a = A + 4 * (size_t)p;
+                const int c = sh.col[p];
+                const T y0 = y[2 * c], y1 = y[2 * c + 1];
+                s0 += a[0] * y0 + a[1] * y1;
+                s1 += a[2] * y0 + a[3] * y1;
+            }
+            s0 = warp_sum_d(s0);
+            s1 = warp_sum_d(s1);
+            if (lane == 0) {
+                const T t0 = y[2 * i] - s0, t1 = y[2 * i + 1] - s1;
+                const T* d = Di + 4 * (size_t)i;
+                y[2 * i] = d[0] * t0 + d[1] * t1;
+                y[2 * i + 1] = d[2] * t0 + d[3] * t1;
+            }
+        }
+        __syncthreads();
+    }
+    for (int c = threadIdx.x; c < sh.n; c += blockDim.x) {
+        int i, j, k;
+        const int gc = global_cell(g, sd, c, i, j, k);
+        if (ras_type == ACAC_RAS_LEFT) {
+            if (owned(sd, i, j, k)) {
+                z[gc] = y[2 * c];
+                z[N + gc] = y[2 * c + 1];
+            }
+        } else {
+            atomicAdd(&z[gc], y[2 * c]);
+            atomicAdd(&z[N + gc], y[2 * c + 1]);
+        }
+    }
+}
+
+template <typename T>
+cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
+                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s) {
+    if (g.dim == 3) sparse_init_kernel<T, 3><<<nbox, 256, 0, s>>>(g, subs, boxes, shapes, J, val);
+    else sparse_init_kernel<T, 2><<<nbox, 256, 0, s>>>(g, subs, boxes, shapes, J, val);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
+                                 int* flags, int threads, size_t smem, cudaStream_t s) {
+    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sparse_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    sparse_factor_kernel<T><<<nbox, threads, smem, s>>>(boxes, shapes, val, dinv, flags);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
+                                const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
+                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s) {
+    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(sparse_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (ras_type != ACAC_RAS_LEFT) {
+        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
+        if (e != cudaSuccess) return e;
+    }
+    sparse_apply_kernel<T><<<nbox, threads, smem, s>>>(g, subs, boxes, shapes, val, dinv, r, z, ras_type, yscratch,
+                                                       smem > 0 ? 1 : 0);
+    return cudaGetLastError();
+}
+
+#define INST(T)                                                                                                   \
+    template cudaError_t launch_sparse_init<T>(const Geom&, int, const SubInfo*, const SparseBox*,                 \
+                                               const SparseShapeDev*, const T*, T*, cudaStream_t);                \
+    template cudaError_t launch_sparse_factor<T>(int, const SparseBox*, const SparseShapeDev*, T*, T*, int*, int,  \
+                                                 size_t, cudaStream_t);                                           \
+    template cudaError_t launch_sparse_apply<T>(const Geom&, int, const SubInfo*, const SparseBox*,                \
+                                                const SparseShapeDev*, const T*, const T*, const T*, T*, int, T*,  \
+                                                int, size_t, cudaStream_t);
+INST(double)
+INST(float)
+#undef INST
+
+}  // namespace acac

@@ -3,7 +3,8 @@
     python -m paper_2007_04560_gb300.runs convergence --kind space [...]   (Sec. 4.1 A, Fig. 1a)
     python -m paper_2007_04560_gb300.runs convergence --kind time  [...]   (Sec. 4.1 A, Fig. 1b)
     python -m paper_2007_04560_gb300.runs long --bc neumann|periodic [...] (Sec. 4.1 A, Figs. 2-4)
-    python -m paper_2007_04560_gb300.runs schwarz [--dim 2|3] [...]        (Sec. 4.2, Tables 2-3)
+    python -m paper_2007_04560_gb300.runs schwarz [--dim 2|3] [...]        (Sec. 4.2, Table 3)
+    python -m paper_2007_04560_gb300.runs subdomain [--dim 2|3] [...]      (Sec. 4.2, Table 2)
 
 Each prints one JSON document (or, for `long`, one JSON line per step with --jsonl) with
 what the paper plots or tabulates.  Coefficients and tolerances are those of the paper's
@@ -201,6 +202,48 @@ def schwarz_table(dim=2, steps=10, dt=1e-4, seed=0, L=2.0):
             "dt": dt, "rows": rows}
 
 
+def subdomain_table(dim=2, steps=10, dt=1e-4, seed=0, L=2.0, precision=None):
+    """Sec. 4.2, Table 2: classical AS with overlap 1 and the subdomain solvers ILU(0),
+    ILU(1), ILU(2), LU (factored at every Newton iteration) and ILU(0) with reuse, on the
+    workload of schwarz_table; per solver total Newton iterations, GMRES iterations per
+    Newton and time.  precision: PREC_FP64 (default in 2D) or PREC_MIXED (default in 3D,
+    where the LU factors of the 512 boxes take ~50 GB in float)."""
+    import torch
+    from workloads import BC_NEUMANN, PREC_FP64, PREC_MIXED, SUB_ILU0, SUB_ILU1, SUB_ILU2, SUB_LU, initial_fields
+    if precision is None:
+        precision = PREC_FP64 if dim == 2 else PREC_MIXED
+    if dim == 2:
+        base = _params(n=(128, 128, 1), L=(L, L, 1.0), bc=BC_NEUMANN, dt0=dt, ras_parts=(6, 4, 1))
+    else:
+        base = _params(dim=3, n=(128, 128, 128), L=(L, L, L), bc=BC_NEUMANN, dt0=dt, ras_parts=(8, 8, 8))
+    base = base.replace(ras_type=1, ras_overlap=1, precision=precision)
+    u0, v0 = initial_fields(base, seed, 0.55, 0.05)
+    variants = [("ILU(0)", SUB_ILU0, 0), ("ILU(1)", SUB_ILU1, 0), ("ILU(2)", SUB_ILU2, 0), ("LU", SUB_LU, 0),
+                ("ILU(0)-reuse", SUB_ILU0, 1)]
+    rows = []
+    for name, solver, reuse in variants:
+        p = base.replace(subdomain_solver=solver, ilu_reuse=reuse)
+        u = torch.tensor(u0.ravel(), device="cuda")
+        v = torch.tensor(v0.ravel(), device="cuda")
+        s = _solver(p)
+        s.step(u.clone(), v.clone())          # warm-up (first-use costs), not counted
+        torch.cuda.synchronize()
+        newton = gmres = 0
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            info = s.step(u, v)
+            newton += info.newton_its
+            gmres += info.gmres_its
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        s.close()
+        rows.append({"subdomain_solver": name, "total_newton": newton, "gmres_per_newton": gmres / max(newton, 1),
+                     "seconds": el})
+    return {"dim": dim, "grid": list(base.shape[::-1]), "subdomains": list(base.ras_parts[:dim]), "steps": steps,
+            "dt": dt, "preconditioner": "classical AS, overlap 1",
+            "precision": "fp64" if precision == PREC_FP64 else "mixed", "rows": rows}
+
+
 def main(argv=None):
     from paper_2007_04560_gb300 import build
     ap = argparse.ArgumentParser()
@@ -226,6 +269,10 @@ def main(argv=None):
     sw = sub.add_parser("schwarz")
     sw.add_argument("--dim", type=int, choices=[2, 3], default=2)
     sw.add_argument("--steps", type=int, default=10)
+    sd = sub.add_parser("subdomain")
+    sd.add_argument("--dim", type=int, choices=[2, 3], default=2)
+    sd.add_argument("--steps", type=int, default=10)
+    sd.add_argument("--precision", choices=["fp64", "mixed"], default=None)
     args = ap.parse_args(argv)
     build.build()
     if args.cmd == "convergence":
@@ -234,6 +281,9 @@ def main(argv=None):
     elif args.cmd == "long":
         sink = (lambda r: print(json.dumps(r), flush=True)) if args.jsonl else None
         res = long_run(args.bc, args.n, args.t_end, args.seed, every=args.every, sink=sink, L=args.L)
+    elif args.cmd == "subdomain":
+        prec = None if args.precision is None else (0 if args.precision == "fp64" else 1)
+        res = subdomain_table(args.dim, args.steps, precision=prec)
     else:
         res = schwarz_table(args.dim, args.steps)
     print(json.dumps(res), flush=True)

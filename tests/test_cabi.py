@@ -80,7 +80,7 @@ def test_defaults_and_validation_without_gpu(lib):
     h = ctypes.c_void_p()
     # argument errors are detected before any CUDA call
     for field, bad in (("dim", 4), ("taylor_S", 0), ("gamma", -1.0), ("batch", 0), ("batch", 1025),
-                       ("gmres_restart", 99)):
+                       ("gmres_restart", 99), ("subdomain_solver", 4), ("subdomain_solver", -1)):
         q = A.acac_params()
         lib.acac_default_params(ctypes.byref(q))
         setattr(q, field, bad)
