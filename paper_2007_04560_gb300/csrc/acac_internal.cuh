@@ -470,6 +470,7 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
 struct SparseShape {                 // host: symbolic factorization of one box shape
     int dim, W, H, D, n;             // box size, cells
     int band;                        // max |column - row| of the pattern (cells)
+    int contig;                      // every row an interval of columns (the LU profile)
     std::vector<int> ptr, col, diag; // CSR of blocks, rows sorted; position of the pivot block
     std::vector<int> slot_pos;       // n x nslot: block of each stencil slot, -1 outside the box
     std::vector<int> flev_ptr, flev_rows;   // forward (L) dependency levels and their rows
@@ -480,7 +481,7 @@ SparseShape build_sparse_shape(int dim, int W, int H, int D, int fill);
 
 struct SparseShapeDev {              // device view of a SparseShape
     const int *ptr, *col, *diag, *slot_pos, *flev_ptr, *flev_rows, *blev_ptr, *blev_rows;
-    int n, band, nflev, nblev;
+    int n, band, nflev, nblev, contig;
 };
 struct SparseBox {
     int shape;                       // index of its SparseShapeDev
@@ -492,10 +493,12 @@ template <typename T>
 cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
                                const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s);
 // block IKJ factorization in place; D^-1 of every cell to dinv; bit 2 of *flags on a
-// singular pivot block.  smem: (threads / 32) x (2 band + 1) ints.
+// singular pivot block, bit 3 when a bounded wait for a row gave up.  smem: the done bits
+// ((n + 31) / 32 words, rounded up to 4) and, with use_map, (threads / 32) x (2 band + 1)
+// ints.
 template <typename T>
 cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
-                                 int* flags, int threads, size_t smem, cudaStream_t s);
+                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s);
 // z = sum_k E_k inv(L_k U_k) R_k r with the restrictions and extensions of ras_type; the
 // box vector in shared memory (smem > 0) or in yscratch (2 values per box cell)
 template <typename T>

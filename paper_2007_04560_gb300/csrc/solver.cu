@@ -153,7 +153,7 @@ struct acac_handle {
     void* sdinv = nullptr;       // inverse pivot blocks, 4 values per box cell
     void* sy = nullptr;          // box vectors of the apply when they do not fit shared memory
     long long sblocks = 0, scells = 0;
-    int s_threads = 32;
+    int s_threads = 32, s_fthreads = 512, s_use_map = 1;
     size_t s_fsmem = 0, s_asmem = 0;
     int ras_threads;
     size_t ras_smem;
@@ -422,9 +422,10 @@ int factor(acac_handle* h) {
                                   (const T*)h->J, (T*)h->sval, h->stream));
         KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 8.0 * h->sblocks, 0.0,
             launch_sparse_factor<T>((int)h->subs.size(), h->sbox_dev, h->sshape_dev, (T*)h->sval, (T*)h->sdinv,
-                                    h->flags, h->s_threads, h->s_fsmem, h->stream));
+                                    h->flags, h->s_fthreads, h->s_fsmem, h->s_use_map, h->stream));
         h->n_factor++;
-        return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+        const int f = read_flags(h);
+        return (f & 8) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
     }
     if (h->g.dim == 3) {
         int packed3 = h->jpacked ? 1 : 0;
@@ -1055,7 +1056,7 @@ void build_sparse(acac_handle* h) {
         const int* b = h->sint_dev;
         sd[t] = SparseShapeDev{b + offs[t].o[0], b + offs[t].o[1], b + offs[t].o[2], b + offs[t].o[3],
                                b + offs[t].o[4], b + offs[t].o[5], b + offs[t].o[6], b + offs[t].o[7],
-                               S.n, S.band, (int)S.flev_ptr.size() - 1, (int)S.blev_ptr.size() - 1};
+                               S.n, S.band, (int)S.flev_ptr.size() - 1, (int)S.blev_ptr.size() - 1, S.contig};
     }
     dmalloc(&h->sshape_dev, sd.size() * sizeof(SparseShapeDev));
     CU(cudaMemcpy(h->sshape_dev, sd.data(), sd.size() * sizeof(SparseShapeDev), cudaMemcpyHostToDevice));
@@ -1063,9 +1064,19 @@ void build_sparse(acac_handle* h) {
     CU(cudaMemcpy(h->sbox_dev, boxes.data(), boxes.size() * sizeof(SparseBox), cudaMemcpyHostToDevice));
     dmalloc(&h->sval, (size_t)blk * 4 * h->ksz);
     dmalloc(&h->sdinv, (size_t)cells * 4 * h->ksz);
-    // one warp per row of a dependency level, at most 8
-    h->s_threads = 32 * std::min(8, width);
-    h->s_fsmem = (size_t)(h->s_threads / 32) * (2 * band + 1) * sizeof(int);
+    // apply: 8 warps, one per row of a dependency level (the whole block on a level of a
+    // single row).  Factorization: 32 warps on the rows in natural order when positions
+    // are arithmetic, else 16 (fewer if their maps do not fit shared memory)
+    h->s_threads = 256;
+    (void)width;
+    bool contig = true;
+    for (const SparseShape& S : h->sshape) contig = contig && S.contig;
+    h->s_use_map = contig ? 0 : 1;
+    const size_t words = (size_t)((maxn + 31) / 32 + 3) / 4 * 4;
+    int fw = contig ? 32 : 16;
+    while (fw > 1 && (words + (contig ? 0 : (size_t)fw * (2 * band + 1))) * sizeof(int) > 200 * 1024) fw /= 2;
+    h->s_fthreads = 32 * fw;
+    h->s_fsmem = (words + (contig ? 0 : (size_t)fw * (2 * band + 1))) * sizeof(int);
     const size_t vec = (size_t)maxn * 2 * h->ksz;
     if (vec <= 96 * 1024) {
         h->s_asmem = vec;

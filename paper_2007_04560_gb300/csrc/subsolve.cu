@@ -12,8 +12,9 @@
 //   LU:     every entry of the profile (fill never leaves the row's first stencil
 //           column on the left, nor a column's first stencil row above), a superset of
 //           the fill of the exact factorization, which keeps its values exact.
-// The factorization and the two triangular sweeps run level by level over the rows'
-// dependency levels, one CTA per box and one warp per row of a level.
+// The factorization runs in dataflow order (rows in natural order over the warps, each
+// step waiting for the row it reads); the two triangular sweeps run level by level over
+// the rows' dependency levels, one CTA per box and one warp per row of a level.
 #include <algorithm>
 #include <functional>
 #include <queue>
@@ -158,6 +159,9 @@ SparseShape build_sparse_shape(int dim, int W, int H, int D, int fill) {
         for (int p = S.diag[i] + 1; p < S.ptr[i + 1]; ++p) bl[i] = std::max(bl[i], bl[S.col[p]] + 1);
     levels_of(n, fl, S.flev_ptr, S.flev_rows);
     levels_of(n, bl, S.blev_ptr, S.blev_rows);
+    S.contig = 1;
+    for (int i = 0; i < n && S.contig; ++i)
+        if (S.col[S.ptr[i + 1] - 1] - S.col[S.ptr[i]] != S.ptr[i + 1] - S.ptr[i] - 1) S.contig = 0;
     return S;
 }
 
@@ -213,77 +217,129 @@ __global__ void __launch_bounds__(256) sparse_init_kernel(Geom g, const SubInfo*
     }
 }
 
-// Block IKJ elimination of row i, one warp per row of a dependency level:
+// Block IKJ elimination of row i:
 //   for k in L(i) ascending:  L_ik = A_ik D_k^-1;  A_ij -= L_ik U_kj  for j in U(k) kept in row i
 //   D_i = A_ii, its inverse stored.
-// The warp's map (2 band + 1 ints in shared memory) takes a column offset j - i + band
-// to the position of (i, j) in row i, -1 where row i keeps no entry (the update dropped).
+// Dataflow order: the warps take the rows in natural order, round robin, and a warp at
+// step k first waits until row k is final (a done bit per row in shared memory, set
+// after the row's values).  Rows therefore proceed concurrently wherever their
+// dependencies allow -- under LU every dependency level holds a single row, yet
+// consecutive rows overlap on all but their last steps and read the same rows U(k)
+// at about the same time.  Every wait is bounded by the global timer; on expiry the
+// block records bit 3 of *flags and stops.
+// Positions: on a contiguous pattern (every row an interval of columns, as the LU
+// profile is) the position of (i, j) is arithmetic; otherwise the warp's map (2 band + 1
+// ints in shared memory) takes j - i + band to it, -1 where row i keeps no entry (the
+// update is dropped).
+constexpr unsigned long long SPARSE_WAIT_NS = 4000000000ull;
+
 template <typename T>
-__global__ void __launch_bounds__(256) sparse_factor_kernel(const SparseBox* __restrict__ boxes,
-                                                            const SparseShapeDev* __restrict__ shapes,
-                                                            T* __restrict__ val, T* __restrict__ dinv, int* flags) {
-    extern __shared__ int smap[];
+__global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __restrict__ boxes,
+                                                             const SparseShapeDev* __restrict__ shapes,
+                                                             T* val, T* dinv, int* flags, int use_map) {
+    extern __shared__ int smem[];
     const SparseBox bx = boxes[blockIdx.x];
     const SparseShapeDev sh = shapes[bx.shape];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int B = sh.band, MW = 2 * B + 1;
-    int* map = smap + (size_t)warp * MW;
-    for (int t = lane; t < MW; t += 32) map[t] = -1;
-    __syncwarp();
+    const int n = sh.n, B = sh.band, MW = 2 * B + 1;
+    const int nwords = (n + 31) >> 5;
+    unsigned* done = reinterpret_cast<unsigned*>(smem);
+    int* map = smem + ((nwords + 3) & ~3) + (size_t)warp * MW;
+    const bool contig = sh.contig != 0;
+    for (int t = threadIdx.x; t < nwords; t += blockDim.x) done[t] = 0u;
+    if (use_map && !contig)
+        for (int t = lane; t < MW; t += 32) map[t] = -1;
+    __syncthreads();
     T* A = val + 4 * bx.blk_base;
     T* Di = dinv + 4 * bx.cell_base;
-    int bad = 0;
-    for (int lv = 0; lv < sh.nflev; ++lv) {
-        for (int q = sh.flev_ptr[lv] + warp; q < sh.flev_ptr[lv + 1]; q += nw) {
-            const int i = sh.flev_rows[q];
-            const int p0 = sh.ptr[i], p1 = sh.ptr[i + 1], pd = sh.diag[i];
+    int bad = 0, timed_out = 0;
+    for (int i = warp; i < n && !timed_out; i += nw) {
+        const int p0 = sh.ptr[i], p1 = sh.ptr[i + 1], pd = sh.diag[i];
+        const int c0 = sh.col[p0];
+        if (!contig) {
             for (int p = p0 + lane; p < p1; p += 32) map[sh.col[p] - i + B] = p;
             __syncwarp();
-            for (int p = p0; p < pd; ++p) {
-                const int k = sh.col[p];
-                const T* dk = Di + 4 * (size_t)k;
-                const T a00 = A[4 * (size_t)p], a01 = A[4 * (size_t)p + 1];
-                const T a10 = A[4 * (size_t)p + 2], a11 = A[4 * (size_t)p + 3];
-                const T l00 = a00 * dk[0] + a01 * dk[2], l01 = a00 * dk[1] + a01 * dk[3];
-                const T l10 = a10 * dk[0] + a11 * dk[2], l11 = a10 * dk[1] + a11 * dk[3];
-                __syncwarp();
-                if (lane == 0) {
-                    A[4 * (size_t)p] = l00;
-                    A[4 * (size_t)p + 1] = l01;
-                    A[4 * (size_t)p + 2] = l10;
-                    A[4 * (size_t)p + 3] = l11;
-                }
-                const int u1 = sh.ptr[k + 1];
-                for (int u = sh.diag[k] + 1 + lane; u < u1; u += 32) {
-                    const int t = map[sh.col[u] - i + B];
-                    if (t < 0) continue;
-                    const T* U = A + 4 * (size_t)u;
-                    T* X = A + 4 * (size_t)t;
-                    const T u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
-                    X[0] -= l00 * u00 + l01 * u10;
-                    X[1] -= l00 * u01 + l01 * u11;
-                    X[2] -= l10 * u00 + l11 * u10;
-                    X[3] -= l10 * u01 + l11 * u11;
-                }
-                __syncwarp();
-            }
+        }
+        for (int p = p0; p < pd; ++p) {
+            const int k = contig ? c0 + (p - p0) : sh.col[p];
+            // row k final?  Lane 0 polls (bounded) and the warp takes its verdict
+            int ok = 1;
             if (lane == 0) {
-                const T* d = A + 4 * (size_t)pd;
-                const T det = d[0] * d[3] - d[1] * d[2];
-                if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
-                const T id = (T)1 / det;
-                T* o = Di + 4 * (size_t)i;
-                o[0] = d[3] * id;
-                o[1] = -d[1] * id;
-                o[2] = -d[2] * id;
-                o[3] = d[0] * id;
+                const volatile unsigned* dw = done + (k >> 5);
+                if (!((*dw >> (k & 31)) & 1u)) {
+                    unsigned long long t0;
+                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+                    while (!((*dw >> (k & 31)) & 1u)) {
+                        unsigned long long t1;
+                        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+                        if (t1 - t0 > SPARSE_WAIT_NS) {
+                            ok = 0;
+                            break;
+                        }
+                        __nanosleep(128);
+                    }
+                }
+                __threadfence_block();
             }
-            for (int p = p0 + lane; p < p1; p += 32) map[sh.col[p] - i + B] = -1;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                timed_out = 1;
+                break;
+            }
+            __syncwarp();
+            __threadfence_block();
+            const T* dk = Di + 4 * (size_t)k;
+            const T a00 = A[4 * (size_t)p], a01 = A[4 * (size_t)p + 1];
+            const T a10 = A[4 * (size_t)p + 2], a11 = A[4 * (size_t)p + 3];
+            const T l00 = a00 * dk[0] + a01 * dk[2], l01 = a00 * dk[1] + a01 * dk[3];
+            const T l10 = a10 * dk[0] + a11 * dk[2], l11 = a10 * dk[1] + a11 * dk[3];
+            __syncwarp();
+            if (lane == 0) {
+                A[4 * (size_t)p] = l00;
+                A[4 * (size_t)p + 1] = l01;
+                A[4 * (size_t)p + 2] = l10;
+                A[4 * (size_t)p + 3] = l11;
+            }
+            const int dk0 = sh.diag[k], u1 = sh.ptr[k + 1];
+            for (int u = dk0 + 1 + lane; u < u1; u += 32) {
+                int t;
+                if (contig) {
+                    t = p0 + (k + (u - dk0) - c0);   // column k + (u - dk0) of row i
+                } else {
+                    t = map[sh.col[u] - i + B];
+                    if (t < 0) continue;
+                }
+                const T* U = A + 4 * (size_t)u;
+                T* X = A + 4 * (size_t)t;
+                const T u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
+                X[0] -= l00 * u00 + l01 * u10;
+                X[1] -= l00 * u01 + l01 * u11;
+                X[2] -= l10 * u00 + l11 * u10;
+                X[3] -= l10 * u01 + l11 * u11;
+            }
             __syncwarp();
         }
-        __syncthreads();
+        if (timed_out) break;
+        if (lane == 0) {
+            const T* d = A + 4 * (size_t)pd;
+            const T det = d[0] * d[3] - d[1] * d[2];
+            if (!(det != (T)0) || !isfinite((double)det)) bad = 1;
+            const T id = (T)1 / det;
+            T* o = Di + 4 * (size_t)i;
+            o[0] = d[3] * id;
+            o[1] = -d[1] * id;
+            o[2] = -d[2] * id;
+            o[3] = d[0] * id;
+        }
+        if (!contig) {
+            for (int p = p0 + lane; p < p1; p += 32) map[sh.col[p] - i + B] = -1;
+        }
+        __threadfence_block();
+        __syncwarp();
+        if (lane == 0) atomicOr(done + (i >> 5), 1u << (i & 31));
     }
     if (bad) atomicOr(flags, 4);
+    if (timed_out && lane == 0) atomicOr(flags, 8);
 }
 
 // Restriction, forward sweep y_i = r_i - sum_{k<i} L_ik y_k, backward sweep
@@ -313,40 +369,71 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
         y[2 * c + 1] = keep ? r[N + gc] : (T)0;
     }
     __syncthreads();
-    for (int lv = 0; lv < sh.nflev; ++lv) {
-        for (int q = sh.flev_ptr[lv] + warp; q < sh.flev_ptr[lv + 1]; q += nw) {
-            const int i = sh.flev_rows[q];
-            T s0 = (T)0, s1 = (T)0;
-            for (int p = sh.ptr[i] + lane; p < sh.diag[i]; p += 32) {
-                const T* a = A + 4 * (size_t)p;
-                const int c = sh.col[p];
-                const T y0 = y[2 * c], y1 = y[2 * c + 1];
-                s0 += a[0] * y0 + a[1] * y1;
-                s1 += a[2] * y0 + a[3] * y1;
+    __shared__ T red[2][8];
+    // sum over positions [pa, pb) of row blocks times y, by the warp (lanes strided) or,
+    // for a level of a single row, by the whole block (threads strided)
+    auto row_dot = [&](int pa, int pb, int tid, int nt, T& s0, T& s1) {
+        s0 = (T)0;
+        s1 = (T)0;
+        for (int p = pa + tid; p < pb; p += nt) {
+            const T* a = A + 4 * (size_t)p;
+            const int c = sh.col[p];
+            const T y0 = y[2 * c], y1 = y[2 * c + 1];
+            s0 += a[0] * y0 + a[1] * y1;
+            s1 += a[2] * y0 + a[3] * y1;
+        }
+        s0 = warp_sum_d(s0);
+        s1 = warp_sum_d(s1);
+    };
+    auto block_total = [&](T& s0, T& s1) {   // after row_dot over the block: total in thread 0
+        if (lane == 0) {
+            red[0][warp] = s0;
+            red[1][warp] = s1;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            s0 = (T)0;
+            s1 = (T)0;
+            for (int w = 0; w < nw; ++w) {
+                s0 += red[0][w];
+                s1 += red[1][w];
             }
-            s0 = warp_sum_d(s0);
-            s1 = warp_sum_d(s1);
-            if (lane == 0) {
+        }
+    };
+    for (int lv = 0; lv < sh.nflev; ++lv) {
+        const int q0 = sh.flev_ptr[lv], q1 = sh.flev_ptr[lv + 1];
+        if (q1 - q0 == 1 && nw > 1) {
+            const int i = sh.flev_rows[q0];
+            T s0, s1;
+            row_dot(sh.ptr[i], sh.diag[i], threadIdx.x, blockDim.x, s0, s1);
+            block_total(s0, s1);
+            if (threadIdx.x == 0) {
                 y[2 * i] -= s0;
                 y[2 * i + 1] -= s1;
+            }
+        } else {
+            for (int q = q0 + warp; q < q1; q += nw) {
+                const int i = sh.flev_rows[q];
+                T s0, s1;
+                row_dot(sh.ptr[i], sh.diag[i], lane, 32, s0, s1);
+                if (lane == 0) {
+                    y[2 * i] -= s0;
+                    y[2 * i + 1] -= s1;
+                }
             }
         }
         __syncthreads();
     }
     for (int lv = 0; lv < sh.nblev; ++lv) {
-        for (int q = sh.blev_ptr[lv] + warp; q < sh.blev_ptr[lv + 1]; q += nw) {
+        const int q0 = sh.blev_ptr[lv], q1 = sh.blev_ptr[lv + 1];
+        const bool whole = q1 - q0 == 1 && nw > 1;
+        for (int q = q0 + (whole ? 0 : warp); q < q1; q += (whole ? 1 : nw)) {
             const int i = sh.blev_rows[q];
-            T s0 = (T)0, s1 = (T)0;
-            for (int p = sh.diag[i] + 1 + lane; p < sh.ptr[i + 1]; p += 32) {
-                const T* a = A + 4 * (size_t)p;
-                const int c = sh.col[p];
-                const T y0 = y[2 * c], y1 = y[2 * c + 1];
-                s0 += a[0] * y0 + a[1] * y1;
-                s1 += a[2] * y0 + a[3] * y1;
-            }
-            s0 = warp_sum_d(s0);
-            s1 = warp_sum_d(s1);
-            if (lane == 0) {
+            T s0, s1;
+            row_dot(sh.diag[i] + 1, sh.ptr[i + 1], whole ? (int)threadIdx.x : lane, whole ? (int)blockDim.x : 32, s0,
+                    s1);
+            if (whole) block_total(s0, s1);
+            if (whole ? threadIdx.x == 0 : lane == 0) {
                 const T t0 = y[2 * i] - s0, t1 = y[2 * i + 1] - s1;
                 const T* d = Di + 4 * (size_t)i;
                 y[2 * i] = d[0] * t0 + d[1] * t1;
@@ -380,14 +467,14 @@ cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, con
 
 template <typename T>
 cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
-                                 int* flags, int threads, size_t smem, cudaStream_t s) {
-    if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
+                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s) {
+    if (threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sparse_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sparse_factor_kernel<T><<<nbox, threads, smem, s>>>(boxes, shapes, val, dinv, flags);
+    sparse_factor_kernel<T><<<nbox, threads, smem, s>>>(boxes, shapes, val, dinv, flags, use_map);
     return cudaGetLastError();
 }
 
@@ -414,7 +501,7 @@ cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, co
     template cudaError_t launch_sparse_init<T>(const Geom&, int, const SubInfo*, const SparseBox*,                 \
                                                const SparseShapeDev*, const T*, T*, cudaStream_t);                \
     template cudaError_t launch_sparse_factor<T>(int, const SparseBox*, const SparseShapeDev*, T*, T*, int*, int,  \
-                                                 size_t, cudaStream_t);                                           \
+                                                 size_t, int, cudaStream_t);                                      \
     template cudaError_t launch_sparse_apply<T>(const Geom&, int, const SubInfo*, const SparseBox*,                \
                                                 const SparseShapeDev*, const T*, const T*, const T*, T*, int, T*,  \
                                                 int, size_t, cudaStream_t);

@@ -2,6 +2,7 @@
 
     python -m paper_2007_04560_gb300.kbench [--workload NAME] [--precision fp64|mixed]
                                              [--reps R] [--components a,b,...]
+                                             [--ras-window W] [--subdomain-solver ilu0|ilu1|ilu2|lu]
 
 Each component is one C-ABI entry point applied to seeded synthetic inputs of the
 workload's grid (a state pair near the workload's initial state, a random direction):
@@ -47,6 +48,8 @@ def main(argv=None):
     ap.add_argument("--components", default=",".join(COMPONENTS))
     ap.add_argument("--ras-window", type=int, default=None, choices=[0, 1, 2],
                     help="2D Schwarz apply variant (params.ras_window)")
+    ap.add_argument("--subdomain-solver", default=None, choices=["ilu0", "ilu1", "ilu2", "lu"],
+                    help="subdomain solve of the Schwarz preconditioner (params.subdomain_solver)")
     args = ap.parse_args(argv)
     build.build()
     w = WORKLOADS[args.workload]
@@ -55,6 +58,8 @@ def main(argv=None):
         p = p.replace(precision=PREC_MIXED if args.precision == "mixed" else PREC_FP64)
     if args.ras_window is not None:
         p = p.replace(ras_window=args.ras_window)
+    if args.subdomain_solver is not None:
+        p = p.replace(subdomain_solver=["ilu0", "ilu1", "ilu2", "lu"].index(args.subdomain_solver))
     comps = [c for c in args.components.split(",") if c]
     for c in comps:
         if c not in COMPONENTS:
