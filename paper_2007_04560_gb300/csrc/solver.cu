@@ -124,6 +124,8 @@ struct acac_handle {
     double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
     // Krylov precision buffers
     void *V, *w, *z, *kt, *jtmp, *cache, *J, *coef, *gscratch;
+    void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
+                                // solution update is Z y: no preconditioner apply per solve)
     size_t ldV;
     // reductions
     double* partial;            // RED_BLOCKS x (MAX_RESTART + 3)
@@ -471,8 +473,9 @@ void arnoldi_step(acac_handle* h, int j) {
     const long long ld = (long long)h->ldV;
     T* vj = V + (size_t)j * ld;
     T* vn = V + (size_t)(j + 1) * ld;
-    precond<T>(h, vj, (T*)h->z);
-    jac_action<T>(h, (const T*)h->z, vn);
+    T* zj = (T*)h->Zb + (size_t)j * ld;
+    precond<T>(h, vj, zj);
+    jac_action<T>(h, (const T*)zj, vn);
     const int passes = h->p.cgs_refine ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
         double* hcol = h->red + pass * (MAX_RESTART + 1);
@@ -557,7 +560,6 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
     T* V = (T*)h->V;
     const long long ld = (long long)h->ldV;
     T* w = (T*)h->w;
-    T* z = (T*)h->z;
     T* tt = (T*)h->kt;
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
     KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
@@ -615,7 +617,8 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
                 break;
             }
         }
-        // y = H(1:k,1:k)^{-1} g(1:k);  x += M^{-1} (V y)
+        // y = H(1:k,1:k)^{-1} g(1:k);  x += M^{-1} (V y) = Z y, z_j = M^{-1} v_j kept by the
+        // Arnoldi steps (the preconditioner is linear)
         for (int i = k - 1; i >= 0; --i) {
             double s = gv[i];
             for (int jj = i + 1; jj < k; ++jj) s -= Hat(i, jj) * yv[jj];
@@ -623,9 +626,8 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
         }
         memcpy(h->host, yv.data(), sizeof(double) * k);
         CU(cudaMemcpyAsync(h->red, h->host, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-        KL(ACAC_K_VECTOR, launch_lincomb<T>(V, ld, k, h->red, tt, n, h->stream));
-        precond<T>(h, tt, z);
-        KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, z, x, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_lincomb<T>((const T*)h->Zb, ld, k, h->red, tt, n, h->stream));
+        KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, tt, x, n, h->stream));
         if (done) {
             CU(cudaMemcpyAsync(h->host_flags + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
             CU(cudaStreamSynchronize(h->stream));
@@ -1091,7 +1093,7 @@ void build_sparse(acac_handle* h) {
 }
 
 void free_all(acac_handle* h) {
-    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->w, h->z,
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->Zb, h->w, h->z,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
                     h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
@@ -1285,6 +1287,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         dmalloc(&h->stage, n2 * 8);
         h->ldV = (n2 + 63) / 64 * 64;
         dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
+        dmalloc(&h->Zb, (size_t)p->gmres_restart * h->ldV * ks);
         dmalloc(&h->w, n2 * ks); dmalloc(&h->z, n2 * ks); dmalloc(&h->kt, n2 * ks);
         dmalloc(&h->jtmp, 3 * N * ks);
         dmalloc(&h->cache, 7 * N * ks);
