@@ -36,15 +36,12 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the
-# 1024^2 workload (profiles/ras_apply_2d-1024x1024.md, profiles/ras_factor_2d-1024x1024.md,
-# profiles/launches_2d-1024x1024-periodic-fp64.md: the FP64 factorization inside the time step,
-# reading the records the assembly writes).  A kernel changed after its capture must be removed
-# from this table.
+# 1024^2 workload (profiles/ras_apply_2d-1024x1024.md).  A kernel changed after its capture is
+# removed from this table (the factorization's Schur updates became two chained multiply-adds
+# after profiles/ras_factor_2d-1024x1024.md and the launch list were taken).
 TRAFFIC = {
     ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_FP64): 555.4e6,
     ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_MIXED): 282.9e6,
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_factor", PREC_FP64): 975.8e6,
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_factor", PREC_MIXED): 465.5e6,
 }
 
 

@@ -155,8 +155,8 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__
     for (int s = 0; s < nslot<DIM>(); ++s) {
         const int n = slot_nb<DIM>(g, x, yy, zz, s);
         const T wu = w[n], wv = w[N + n];
-        au += J[(size_t)(s * 4 + 0) * N + c] * wu + J[(size_t)(s * 4 + 1) * N + c] * wv;
-        av += J[(size_t)(s * 4 + 2) * N + c] * wu + J[(size_t)(s * 4 + 3) * N + c] * wv;
+        au = fma(J[(size_t)(s * 4 + 1) * N + c], wv, fma(J[(size_t)(s * 4 + 0) * N + c], wu, au));
+        av = fma(J[(size_t)(s * 4 + 3) * N + c], wv, fma(J[(size_t)(s * 4 + 2) * N + c], wu, av));
     }
     y[c] = au;
     y[N + c] = av;

@@ -177,8 +177,8 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
                         const int s2 = slot_of(dx1 + upper_dx(b), dy1 + upper_dy(b));
                         if (s2 >= 0) {
                             const T* U = kr + 4 + 4 * b;
-                            A[s2][0] -= L0 * U[0] + L1 * U[2];
-                            A[s2][1] -= L0 * U[1] + L1 * U[3];
+                            A[s2][0] = fma(-L1, U[2], fma(-L0, U[0], A[s2][0]));
+                            A[s2][1] = fma(-L1, U[3], fma(-L0, U[1], A[s2][1]));
                         }
                     }
                 }
@@ -793,8 +793,8 @@ __global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo*
                             const int s2 = slot3_of(dx1 + u3_dx(b), dy1 + u3_dy(b), dz1 + u3_dz(b));
                             if (s2 >= 0) {
                                 const T* U = kr + 4 + 4 * b;
-                                A[s2][0] -= L0 * U[0] + L1 * U[2];
-                                A[s2][1] -= L0 * U[1] + L1 * U[3];
+                                A[s2][0] = fma(-L1, U[2], fma(-L0, U[0], A[s2][0]));
+                                A[s2][1] = fma(-L1, U[3], fma(-L0, U[1], A[s2][1]));
                             }
                         }
                     }

@@ -312,10 +312,10 @@ __global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __
                 const T* U = A + 4 * (size_t)u;
                 T* X = A + 4 * (size_t)t;
                 const T u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
-                X[0] -= l00 * u00 + l01 * u10;
-                X[1] -= l00 * u01 + l01 * u11;
-                X[2] -= l10 * u00 + l11 * u10;
-                X[3] -= l10 * u01 + l11 * u11;
+                X[0] = fma(-l01, u10, fma(-l00, u00, X[0]));
+                X[1] = fma(-l01, u11, fma(-l00, u01, X[1]));
+                X[2] = fma(-l11, u10, fma(-l10, u00, X[2]));
+                X[3] = fma(-l11, u11, fma(-l10, u01, X[3]));
             }
             __syncwarp();
         }
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
             const T* a = A + 4 * (size_t)p;
             const int c = sh.col[p];
             const T y0 = y[2 * c], y1 = y[2 * c + 1];
-            s0 += a[0] * y0 + a[1] * y1;
-            s1 += a[2] * y0 + a[3] * y1;
+            s0 = fma(a[1], y1, fma(a[0], y0, s0));
+            s1 = fma(a[3], y1, fma(a[2], y0, s1));
         }
         s0 = warp_sum_d(s0);
         s1 = warp_sum_d(s1);
