@@ -66,6 +66,11 @@ struct Geom {
     int nz, dim;         // 3D: z extent (1 in 2D)
     double hz, ihz2;
     float ihz2f;
+    // 1/(2 h^2) per axis: the weight of a face average (c_i + c_n) / 2 times a face
+    // difference; no open-face test is needed with it, since a face at a Neumann wall has
+    // the cell itself as neighbour and a zero difference
+    double hihx2, hihy2, hihz2;
+    float hihx2f, hihy2f, hihz2f;
 };
 
 // ---------------------------------------------------------------- 3D stencil
@@ -192,6 +197,11 @@ __device__ __forceinline__ T face_weight(const Geom& g, int x, int y, int z, int
     return DIM == 2 ? face_w<T>(g, x, y, f) : face_w3<T>(g, x, y, z, f);
 }
 __device__ __forceinline__ double face_ih2(const Geom& g, int f) { return f < 2 ? g.ihx2 : f < 4 ? g.ihy2 : g.ihz2; }
+template <typename T>
+__device__ __forceinline__ T face_half(const Geom& g, int f) {
+    if (sizeof(T) == 8) return (T)(f < 2 ? g.hihx2 : f < 4 ? g.hihy2 : g.hihz2);
+    return (T)(f < 2 ? g.hihx2f : f < 4 ? g.hihy2f : g.hihz2f);
+}
 // Generic stencil slots (2D: 13, 3D: 25; slot f+1 is face f in both).
 template <int DIM> __host__ __device__ constexpr int nslot() { return DIM == 2 ? NSLOT : NSLOT3; }
 // boxes that can contain one grid cell (overlap below the owned box width): 2 per axis

@@ -213,8 +213,7 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, const JacK<T>* __rest
 #pragma unroll
     for (int f = 0; f < 2 * DIM; ++f) {
         const int n = face_nb<DIM>(g, x, yy, zz, f);
-        const T w_ = face_weight<DIM, T>(g, x, yy, zz, f);
-        div += w_ * ((T)0.5 * (dcc + dc[n]) * (C.Gu[n] - gc) + (T)0.5 * (cc + C.c[n]) * (dGu[n] - dgc));
+        div = fma(face_half<T>(g, f), fma(cc + C.c[n], dGu[n] - dgc, (dcc + dc[n]) * (C.Gu[n] - gc)), div);
     }
     const T idt = kp->idt, irho = kp->irho;
     y[c] = w[c] * idt - div;

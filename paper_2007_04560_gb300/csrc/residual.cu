@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho,
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) {
             const int n = face_nb<DIM>(g, x, y, z, f);
-            div += face_weight<DIM, double>(g, x, y, z, f) * 0.5 * (cc + cm[n]) * (Gu[n] - gc);
+            div = fma(face_half<double>(g, f) * (cc + cm[n]), Gu[n] - gc, div);
         }
         const double Fu = (X1[c] - a.X0[c]) * idt - div;
         const double Fv = (X1[N + c] - a.X0[N + c]) * idt + cc * Gv[c] * irho;

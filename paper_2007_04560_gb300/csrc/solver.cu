@@ -1270,6 +1270,8 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
     g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
     g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
+    g.hihx2 = 0.5 * g.ihx2; g.hihy2 = 0.5 * g.ihy2; g.hihz2 = 0.5 * g.ihz2;
+    g.hihx2f = (float)g.hihx2; g.hihy2f = (float)g.hihy2; g.hihz2f = (float)g.hihz2;
     g.vol = g.hx * g.hy * (p->dim == 3 ? g.hz : 1.0);
     h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
     h->eta = p->eta0;
