@@ -47,39 +47,49 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
         eih2c[f] = face_weight<DIM, T>(g, x, y, z, f);
         lapc += eih2c[f];
     }
-    Juu[0] = k.idt;
+    // Face f (weight w = 1/h^2 if open, else 0; neighbour n; ct = (c_c + c_n)/2;
+    // dG = G_u(n) - G_u(c)) contributes to the u row
+    //   -w/2 dG (c_u, c_v)(c)      at the centre       (mobility variation at c)
+    //   -w/2 dG (c_u, c_v)(n)      at the face slot    (mobility variation at n)
+    //   -w ct (du, xc)(n)          at the face slot    (pointwise part of dG_u(n))
+    //   +w ct hg e2(n, f2)         at n + face f2, and -w ct hg lap(n) at the face slot
+    //                              (Laplacian part of dG_u(n), lap(n) = sum_f2 e2(n, f2))
+    //   +w ct (du, xc)(c)          at the centre       (pointwise part of dG_u(c))
+    //   -w ct hg e(c, f2)          at c + face f2, +w ct hg lap(c) at the centre.
+    // The centre terms depend on f only through S1 = sum_f w dG and W = sum_f w ct, which
+    // are summed first (about half the FP64 operations of accumulating them per face).
+    T S1 = (T)0, W = (T)0;
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
         const int fx = fc_dx<DIM>(f), fy = fc_dy<DIM>(f), fz = fc_dz<DIM>(f);
         const int sf = sl_of<DIM>(fx, fy, fz);
         const int n = face_nb<DIM>(g, x, y, z, f);
         const T w = eih2c[f];
-        const T cn = C.c[n], dG = C.Gu[n] - gc, ct = half * (cc + cn);
-        // mobility variation of the face flux
-        Juu[0] -= w * half * cuc * dG;
-        Juv[0] -= w * half * cvc * dG;
-        Juu[sf] -= w * half * C.cu[n] * dG;
-        Juv[sf] -= w * half * C.cv[n] * dG;
-        // - ct * dG_u(n)/dX : pointwise part and Laplacian of the neighbour
-        Juu[sf] -= w * ct * C.du[n];
-        Juv[sf] -= w * ct * C.xc[n];
+        const T dG = C.Gu[n] - gc;
+        const T wct = w * half * (cc + C.c[n]);
+        const T t = w * half * dG;
+        S1 = fma(w, dG, S1);
+        W += wct;
         const int nx_ = x + fx, ny_ = y + fy, nz_ = z + fz;
+        const T wcth = wct * hg;
+        T lapn = (T)0;
 #pragma unroll
         for (int f2 = 0; f2 < NF; ++f2) {
             const T e2 = face_weight<DIM, T>(g, nx_, ny_, nz_, f2);
             const int s2 = sl_of<DIM>(fx + fc_dx<DIM>(f2), fy + fc_dy<DIM>(f2), fz + fc_dz<DIM>(f2));
-            Juu[s2] += w * ct * hg * e2;
-            Juu[sf] -= w * ct * hg * e2;
+            Juu[s2] = fma(wcth, e2, Juu[s2]);
+            lapn += e2;
         }
-        // + ct * dG_u(c)/dX
-        Juu[0] += w * ct * duc;
-        Juv[0] += w * ct * xcc;
+        Juu[sf] -= fma(wct, fma(hg, lapn, C.du[n]), t * C.cu[n]);
+        Juv[sf] -= fma(wct, C.xc[n], t * C.cv[n]);
+    }
+    Juu[0] += k.idt + fma(W, fma(hg, lapc, duc), -half * cuc * S1);
+    Juv[0] += fma(W, xcc, -half * cvc * S1);
+    const T hgW = hg * W;
 #pragma unroll
-        for (int f2 = 0; f2 < NF; ++f2) {
-            const int s2 = sl_of<DIM>(fc_dx<DIM>(f2), fc_dy<DIM>(f2), fc_dz<DIM>(f2));
-            Juu[s2] -= w * ct * hg * eih2c[f2];
-        }
-        Juu[0] += w * ct * hg * lapc;
+    for (int f2 = 0; f2 < NF; ++f2) {
+        const int s2 = sl_of<DIM>(fc_dx<DIM>(f2), fc_dy<DIM>(f2), fc_dz<DIM>(f2));
+        Juu[s2] = fma(-hgW, eih2c[f2], Juu[s2]);
     }
     const T irho = k.irho;
     T Jvu[NS], Jvv[NS];
