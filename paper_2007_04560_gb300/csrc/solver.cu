@@ -123,7 +123,7 @@ struct acac_handle {
     // FP64 state
     double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
     // Krylov precision buffers
-    void *V, *w, *z, *kt, *jtmp, *cache, *J, *coef, *gscratch;
+    void *V, *w, *kt, *jtmp, *cache, *J, *coef, *gscratch;
     void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
                                 // solution update is Z y: no preconditioner apply per solve)
     size_t ldV;
@@ -1093,7 +1093,7 @@ void build_sparse(acac_handle* h) {
 }
 
 void free_all(acac_handle* h) {
-    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->Zb, h->w, h->z,
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->Zb, h->w,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
                     h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
@@ -1290,7 +1290,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         h->ldV = (n2 + 63) / 64 * 64;
         dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
         dmalloc(&h->Zb, (size_t)p->gmres_restart * h->ldV * ks);
-        dmalloc(&h->w, n2 * ks); dmalloc(&h->z, n2 * ks); dmalloc(&h->kt, n2 * ks);
+        dmalloc(&h->w, n2 * ks); dmalloc(&h->kt, n2 * ks);
         dmalloc(&h->jtmp, 3 * N * ks);
         dmalloc(&h->cache, 7 * N * ks);
         dmalloc(&h->J, (size_t)(p->dim == 3 ? NSLOT3 : NSLOT) * 4 * N * ks);
