@@ -36,12 +36,13 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the
-# 1024^2 workload (profiles/ras_apply_2d-1024x1024.md).  A kernel changed after its capture is
-# removed from this table (the factorization's Schur updates became two chained multiply-adds
-# after profiles/ras_factor_2d-1024x1024.md and the launch list were taken).
+# 1024^2 workload: FP64 from the launch list of this benchmark's own run
+# (profiles/launches_2d-1024x1024-periodic-fp64.md), FP32 apply from
+# profiles/ras_apply_2d-1024x1024.md.  A kernel changed after its capture must be removed.
 TRAFFIC = {
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_FP64): 555.4e6,
+    ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_FP64): 552.4e6,
     ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_MIXED): 282.9e6,
+    ("2d-1024x1024-periodic-fp64-adaptive", "ras_factor", PREC_FP64): 975.9e6,
 }
 
 
