@@ -190,13 +190,15 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, const JacK<T>* __rest
     int x, y, z;
     decode_cell<DIM>(g, c, x, y, z);
     const T wu = w[c], wv = w[N + c];
+    // Laplacian per axis, (w_- + w_+ - 2 w) / h^2: a clamped (Neumann wall) neighbour is the
+    // cell itself and adds nothing
     T lu = 0, lv = 0;
 #pragma unroll
-    for (int f = 0; f < 2 * DIM; ++f) {
-        const int n = face_nb<DIM>(g, x, y, z, f);
-        const T ih2 = sizeof(T) == 8 ? (T)face_ih2(g, f) : (T)(f < 2 ? g.ihx2f : f < 4 ? g.ihy2f : g.ihz2f);
-        lu += (w[n] - wu) * ih2;
-        lv += (w[N + n] - wv) * ih2;
+    for (int d = 0; d < DIM; ++d) {
+        const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+        const T ih2 = sizeof(T) == 8 ? (T)face_ih2(g, 2 * d) : (T)(d == 0 ? g.ihx2f : d == 1 ? g.ihy2f : g.ihz2f);
+        lu = fma(fma((T)-2, wu, w[nm] + w[np]), ih2, lu);
+        lv = fma(fma((T)-2, wv, w[N + nm] + w[N + np]), ih2, lv);
     }
     const JacK<T> k = *kp;
     const T hg = k.hg;

@@ -19,11 +19,14 @@ __constant__ double c_rcoef[MAX_S];    // 1 / (2k+1),        k = 1..S   (its sig
 __constant__ float c_rcoef_f[MAX_S];   // the same in float, for the FP32 Jacobian of the mixed form
 
 // Table of the logarithm below: for F_j = 1 + j/128, j = 0..128, 1/F_j and ln F_j as an
-// unevaluated sum hi + lo.
+// unevaluated sum hi + lo, one 32-byte entry per j.  Global memory read through the
+// read-only cache: the lanes of a warp look up different j, which the constant cache would
+// serve one address at a time.
 constexpr int LOG_TABLE = 129;
-__constant__ double c_log_invF[LOG_TABLE];
-__constant__ double c_log_hi[LOG_TABLE];
-__constant__ double c_log_lo[LOG_TABLE];
+struct __align__(32) LogEntry {
+    double inv, hi, lo, pad;
+};
+__device__ LogEntry d_log_tab[LOG_TABLE];
 
 // The constant tables do not depend on S (S only selects how many terms a kernel
 // sums), so they are uploaded once per device; several host threads may race here.
@@ -38,13 +41,14 @@ cudaError_t set_taylor_constants(int) {
     if (g_const_ready.load(std::memory_order_acquire) & bit) return cudaSuccess;
     std::lock_guard<std::mutex> lock(g_const_mu);
     if (g_const_ready.load(std::memory_order_relaxed) & bit) return cudaSuccess;
-    double inv[LOG_TABLE], hi[LOG_TABLE], lo[LOG_TABLE];
+    LogEntry tab[LOG_TABLE];
     for (int j = 0; j < LOG_TABLE; ++j) {
         const long double F = 1.0L + (long double)j / 128.0L;
         const long double L = logl(F);
-        inv[j] = (double)(1.0L / F);
-        hi[j] = (double)L;
-        lo[j] = (double)(L - (long double)hi[j]);
+        tab[j].inv = (double)(1.0L / F);
+        tab[j].hi = (double)L;
+        tab[j].lo = (double)(L - (long double)tab[j].hi);
+        tab[j].pad = 0.0;
     }
     double a[MAX_S], b[MAX_S];
     float bf[MAX_S];
@@ -53,9 +57,7 @@ cudaError_t set_taylor_constants(int) {
         b[k - 1] = 1.0 / (2.0 * k + 1.0);
         bf[k - 1] = (float)b[k - 1];
     }
-    e = cudaMemcpyToSymbol(c_log_invF, inv, sizeof(inv));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_hi, hi, sizeof(hi));
-    if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_log_lo, lo, sizeof(lo));
+    e = cudaMemcpyToSymbol(d_log_tab, tab, sizeof(tab));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef, b, sizeof(b));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef_f, bf, sizeof(bf));
@@ -84,7 +86,9 @@ __device__ __forceinline__ double table_log(double x) {
     const double m = __longlong_as_double(mb);
     const int j = (int)((mb >> 45) & 0x7f) + (int)((mb >> 44) & 1);      // nearest j/128
     const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 45));   // 1 + j/128
-    const double u = (m - F) * c_log_invF[j];
+    const double2 t0 = __ldg(reinterpret_cast<const double2*>(&d_log_tab[j]));       // 1/F, ln F (hi)
+    const double t1 = __ldg(&d_log_tab[j].lo);
+    const double u = (m - F) * t0.x;
     const double u2 = u * u;
     // -1/2 + u (1/3 + u (-1/4 + u (1/5 + u (-1/6 + u / 7))))
     double q = fma(u, 1.0 / 7.0, -1.0 / 6.0);
@@ -95,8 +99,8 @@ __device__ __forceinline__ double table_log(double x) {
     const double ln2_hi = 6.93147180559890330187045037746429443359375e-1;   // 42 significant bits
     const double ln2_lo = 5.497923018708371174712471233040e-14;
     const double ed = (double)e;
-    const double hi = fma(ed, ln2_hi, c_log_hi[j]);
-    const double lo = fma(ed, ln2_lo, c_log_lo[j]);
+    const double hi = fma(ed, ln2_hi, t0.y);
+    const double lo = fma(ed, ln2_lo, t1);
     return hi + (u + fma(u2, q, lo));
 }
 
