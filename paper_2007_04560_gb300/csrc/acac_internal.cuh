@@ -390,8 +390,13 @@ struct ResidualArgs {
     double* F;           // residual
     Red red;             // ||F||^2 (one quantity)
     int* flags;          // bit 0: midpoint inadmissible, bit 1: trial state inadmissible
+    const double* L0 = nullptr;   // discrete Laplacians of X0's two fields (launch_laplacian), or
+                                  // null: formed from X0 in pass A
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+// L = discrete Laplacian of both fields of X (2N each): the start state's part of G3, fixed
+// over a Newton solve
+cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s);
 cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s);
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);

@@ -18,11 +18,11 @@ __constant__ double c_taylor[MAX_S];   // 1 / ((2k)(2k+1)),  k = 1..S   (Lemma 2
 __constant__ double c_rcoef[MAX_S];    // 1 / (2k+1),        k = 1..S   (its sigma/zeta derivative)
 __constant__ float c_rcoef_f[MAX_S];   // the same in float, for the FP32 Jacobian of the mixed form
 
-// Table of the logarithm below: for F_j = 1 + j/128, j = 0..128, 1/F_j and ln F_j as an
+// Table of the logarithm below: for F_j = 1 + j/1024, j = 0..1024, 1/F_j and ln F_j as an
 // unevaluated sum hi + lo, one 32-byte entry per j.  Global memory read through the
 // read-only cache: the lanes of a warp look up different j, which the constant cache would
 // serve one address at a time.
-constexpr int LOG_TABLE = 129;
+constexpr int LOG_TABLE = 1025;
 struct __align__(32) LogEntry {
     double inv, hi, lo, pad;
 };
@@ -41,9 +41,9 @@ cudaError_t set_taylor_constants(int) {
     if (g_const_ready.load(std::memory_order_acquire) & bit) return cudaSuccess;
     std::lock_guard<std::mutex> lock(g_const_mu);
     if (g_const_ready.load(std::memory_order_relaxed) & bit) return cudaSuccess;
-    LogEntry tab[LOG_TABLE];
+    std::vector<LogEntry> tab(LOG_TABLE);
     for (int j = 0; j < LOG_TABLE; ++j) {
-        const long double F = 1.0L + (long double)j / 128.0L;
+        const long double F = 1.0L + (long double)j / 1024.0L;
         const long double L = logl(F);
         tab[j].inv = (double)(1.0L / F);
         tab[j].hi = (double)L;
@@ -57,7 +57,7 @@ cudaError_t set_taylor_constants(int) {
         b[k - 1] = 1.0 / (2.0 * k + 1.0);
         bf[k - 1] = (float)b[k - 1];
     }
-    e = cudaMemcpyToSymbol(d_log_tab, tab, sizeof(tab));
+    e = cudaMemcpyToSymbol(d_log_tab, tab.data(), sizeof(LogEntry) * LOG_TABLE);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_taylor, a, sizeof(a));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef, b, sizeof(b));
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_rcoef_f, bf, sizeof(bf));
@@ -67,11 +67,12 @@ cudaError_t set_taylor_constants(int) {
 
 // Natural logarithm in double by the table-driven reduction of P. T. P. Tang, "Table-
 // driven implementation of the logarithm function in IEEE floating-point arithmetic"
-// (ACM TOMS 16, 1990), written from the mathematics: x = 2^e m, m in [1, 2); F = 1 + j/128
-// is the table point nearest to m, so f = m - F is exact and |f| <= 2^-8; with
+// (ACM TOMS 16, 1990), written from the mathematics: x = 2^e m, m in [1, 2); F = 1 + j/1024
+// is the table point nearest to m, so f = m - F is exact and |f| <= 2^-11; with
 // u = f / F (one multiplication by the tabulated 1/F),
 //     ln x = e ln 2 + ln F + ln(1 + u),
-//     ln(1 + u) = u - u^2/2 + u^3/3 - ... (terms to u^7; the next is below 2^-67 |u|).
+//     ln(1 + u) = u - u^2/2 + u^3/3 - u^4/4 + u^5/5 (the omitted terms are below 2^-57 |u|;
+//     the larger table keeps the polynomial at five terms).
 // ln 2 is split into a 42-bit head (so that e * head is exact) and a tail.  Arguments
 // that are not positive normal numbers go to the library logarithm.  The GPU tests
 // compare it with the library logarithm over the arguments the kernels use.  The range
@@ -84,16 +85,14 @@ __device__ __forceinline__ double table_log(double x) {
     const int e = (int)((bits >> 52) & 0x7ff) - 1023;
     const long long mb = (bits & 0x000fffffffffffffLL) | 0x3ff0000000000000LL;
     const double m = __longlong_as_double(mb);
-    const int j = (int)((mb >> 45) & 0x7f) + (int)((mb >> 44) & 1);      // nearest j/128
-    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 45));   // 1 + j/128
+    const int j = (int)((mb >> 42) & 0x3ff) + (int)((mb >> 41) & 1);     // nearest j/1024
+    const double F = __longlong_as_double(0x3ff0000000000000LL + ((long long)j << 42));   // 1 + j/1024
     const double2 t0 = __ldg(reinterpret_cast<const double2*>(&d_log_tab[j]));       // 1/F, ln F (hi)
     const double t1 = __ldg(&d_log_tab[j].lo);
     const double u = (m - F) * t0.x;
     const double u2 = u * u;
-    // -1/2 + u (1/3 + u (-1/4 + u (1/5 + u (-1/6 + u / 7))))
-    double q = fma(u, 1.0 / 7.0, -1.0 / 6.0);
-    q = fma(u, q, 0.2);
-    q = fma(u, q, -0.25);
+    // -1/2 + u (1/3 + u (-1/4 + u / 5))
+    double q = fma(u, 0.2, -0.25);
     q = fma(u, q, 1.0 / 3.0);
     q = fma(u, q, -0.5);
     const double ln2_hi = 6.93147180559890330187045037746429443359375e-1;   // 42 significant bits
@@ -230,7 +229,7 @@ __device__ __forceinline__ bool in_unit(double x) {
     return b > 0 && b < 0x3ff0000000000000LL;
 }
 
-template <int DIM>
+template <int DIM, bool PRE>
 __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
     const int N = g.N;
     const double* __restrict__ Xu = a.X;
@@ -250,14 +249,24 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
         const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
         // Laplacians of u1 + u0 and v1 + v0 (G3), per axis (S_- + S_+ - 2 S) / h^2; a
-        // clamped (Neumann ghost) neighbour is the cell itself and adds nothing
+        // clamped (Neumann ghost) neighbour is the cell itself and adds nothing.  With PRE
+        // the start state's Laplacians come precomputed (fixed over a Newton solve)
         double lu = 0.0, lv = 0.0;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
             const double ih2 = face_ih2(g, 2 * d);
             const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
-            lu = fma(fma(-2.0, su, (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np])), ih2, lu);
-            lv = fma(fma(-2.0, sv, (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np])), ih2, lv);
+            if (PRE) {
+                lu = fma(fma(-2.0, u1, Xu[nm] + Xu[np]), ih2, lu);
+                lv = fma(fma(-2.0, v1, Xv[nm] + Xv[np]), ih2, lv);
+            } else {
+                lu = fma(fma(-2.0, su, (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np])), ih2, lu);
+                lv = fma(fma(-2.0, sv, (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np])), ih2, lv);
+            }
+        }
+        if (PRE) {
+            lu += a.L0[cc];
+            lv += a.L0[N + cc];
         }
         // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma);
         // the increments come from the differences du, dv (exact for nearby states)
@@ -337,8 +346,41 @@ static int grid_for(long long n, int threads) {
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
-    if (g.dim == 3) g_kernel<3><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
-    else g_kernel<2><<<grid_for(g.N, 256), 256, 0, s>>>(g, k, a);
+    const int nb = grid_for(g.N, 256);
+    if (a.L0) {
+        if (g.dim == 3) g_kernel<3, true><<<nb, 256, 0, s>>>(g, k, a);
+        else g_kernel<2, true><<<nb, 256, 0, s>>>(g, k, a);
+    } else {
+        if (g.dim == 3) g_kernel<3, false><<<nb, 256, 0, s>>>(g, k, a);
+        else g_kernel<2, false><<<nb, 256, 0, s>>>(g, k, a);
+    }
+    return cudaGetLastError();
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) laplacian_kernel(Geom g, const double* __restrict__ X, double* __restrict__ L) {
+    const int N = g.N;
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
+        int x, y, z;
+        decode_cell<DIM>(g, c, x, y, z);
+        const double u = X[c], v = X[N + c];
+        double lu = 0.0, lv = 0.0;
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const double ih2 = face_ih2(g, 2 * d);
+            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+            lu = fma(fma(-2.0, u, X[nm] + X[np]), ih2, lu);
+            lv = fma(fma(-2.0, v, X[N + nm] + X[N + np]), ih2, lv);
+        }
+        L[c] = lu;
+        L[N + c] = lv;
+    }
+}
+
+cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s) {
+    const int nb = grid_for(g.N, 256);
+    if (g.dim == 3) laplacian_kernel<3><<<nb, 256, 0, s>>>(g, X, L);
+    else laplacian_kernel<2><<<nb, 256, 0, s>>>(g, X, L);
     return cudaGetLastError();
 }
 

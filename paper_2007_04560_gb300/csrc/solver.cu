@@ -122,6 +122,7 @@ struct acac_handle {
     size_t ksz;                 // sizeof Krylov element
     // FP64 state
     double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
+    double* lap0 = nullptr;     // Laplacians of X0 during a Newton solve (pass A reads them)
     // Krylov precision buffers
     void *V, *w, *kt, *jtmp, *cache, *J, *coef, *gscratch;
     void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
@@ -341,10 +342,11 @@ int read_flags(acac_handle* h) {
 
 // ||F(X)|| (or of the trial point X + lam (S + shift e_u)) and the G buffer.
 double eval_residual(acac_handle* h, const double* X, const double* S, double lam, double shift,
-                     double dt, int* flags_out) {
+                     double dt, int* flags_out, bool use_lap0 = false) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     ResidualArgs a;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
+    a.L0 = use_lap0 ? h->lap0 : nullptr;
     a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.red = red_to(h, h->red); a.flags = h->flags;
     if (S) {
         // the line search's trial state X + lam (S + shift e_u), then F there
@@ -672,8 +674,10 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
     const size_t N = h->N;
     const long long n = 2 * (long long)N;
     CU(cudaMemcpyAsync(h->X, h->X0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+    // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
+    KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream));
     int fl = 0;
-    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl);
+    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl, true);
     info->fnorm0 = info->fnorm = fnorm;
     if (fl & 1) return ACAC_E_DOMAIN;
     if (!isfinite(fnorm)) return ACAC_E_DIVERGED;
@@ -703,7 +707,7 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         const double f2 = fnorm * fnorm;
         double ft = 0.0;
         while (true) {
-            ft = eval_residual(h, h->X, h->S, lam, shift, dt, &fl);
+            ft = eval_residual(h, h->X, h->S, lam, shift, dt, &fl, true);
             if (fl == 0 && isfinite(ft) && ft * ft <= (1.0 - 2e-4 * lam) * f2) break;
             lam *= 0.5;
             h->ls_cuts++;
@@ -1093,7 +1097,7 @@ void build_sparse(acac_handle* h) {
 }
 
 void free_all(acac_handle* h) {
-    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->V, h->Zb, h->w,
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0, h->V, h->Zb, h->w,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
                     h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
@@ -1287,6 +1291,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         dmalloc(&h->Xt, n2 * 8); dmalloc(&h->F, n2 * 8); dmalloc(&h->S, n2 * 8);
         dmalloc(&h->G, 3 * N * 8); dmalloc(&h->b, n2 * 8); dmalloc(&h->r, n2 * 8); dmalloc(&h->tmpd, n2 * 8);
         dmalloc(&h->stage, n2 * 8);
+        dmalloc(&h->lap0, n2 * 8);
         h->ldV = (n2 + 63) / 64 * 64;
         dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
         dmalloc(&h->Zb, (size_t)p->gmres_restart * h->ldV * ks);
