@@ -173,6 +173,29 @@ def roofline(stats, precision, hbm_gbs, peak_src, workload, share_stats=None):
     return out
 
 
+def rank_barrier(world):
+    """Barrier over the job's ranks (no-op for one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device):
+    """Maximum of x over all ranks: the job's time is its slowest rank's."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def job_rate(world, members, steps, seconds):
+    """Whole-job throughput: every rank advances `members` problems by `steps` steps."""
+    return world * members * steps / seconds
+
+
 def run_mine(args, rank, world):
     import numpy as np
     import torch
@@ -201,17 +224,7 @@ def run_mine(args, rank, world):
         return (info[0] if isinstance(info, list) else info).as_dict()
 
     def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
-    def max_over_ranks(x):
-        if world > 1:
-            import torch.distributed as dist
-            t = torch.tensor([x], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            return float(t.item())
-        return x
+        rank_barrier(world)
 
     # ---- device-resident timed region
     s = P.Solver(p, stream)
@@ -244,7 +257,7 @@ def run_mine(args, rank, world):
     ms = e0.elapsed_time(e1)
     stats = s.kernel_stats()
     s.close()
-    ms = max_over_ranks(ms)
+    ms = max_over_ranks(ms, world, dev)
     launches = int(sum(v[0] for v in stats.values()))
 
     # ---- end to end through the C ABI with host buffers (H2D + step + D2H per step)
@@ -262,16 +275,16 @@ def run_mine(args, rank, world):
         for _ in range(args.steps):
             s2.step_host(uh, vh)
         torch.cuda.synchronize()
-        el = max_over_ranks(time.perf_counter() - t0)
+        el = max_over_ranks(time.perf_counter() - t0, world, dev)
         barrier()
         s2.close()
-        e2e = {"value": world * B * args.steps / el, "unit": "steps/s" if B == 1 else "member-steps/s",
+        e2e = {"value": job_rate(world, B, args.steps, el), "unit": "steps/s" if B == 1 else "member-steps/s",
                "h2d_bytes_per_step": 16 * N * B, "d2h_bytes_per_step": 16 * N * B}
 
     if rank != 0:
         return None
     hbm, src = peaks()
-    steps_per_s = world * B * args.steps / (ms * 1e-3)
+    steps_per_s = job_rate(world, B, args.steps, ms * 1e-3)
     out = {
         "metric": "NKS time steps/s (one accepted implicit time step per step)" if B == 1 else
                   "ensemble member time steps/s (every member takes one accepted implicit step per step)",
