@@ -365,6 +365,16 @@ int acac_kernel_stats(acac_handle *h, int kernel, long long *launches, double *t
 /* Static name of a kernel class. */
 const char *acac_kernel_name(int kernel);
 
+/* Self-check of the bounded device-side waits (the Schwarz apply's mbarrier waits,
+ * mode 0; the dataflow factorization's row waits, mode 1): one warp waits, with the
+ * production wait helper, on an mbarrier phase / a done bit that nothing completes.  The
+ * wait gives up after its limit (0.5 s / 0.2 s) and the kernel reports it.  Returns
+ * ACAC_E_TIMEOUT when the wait gave up (the expected result; the CUDA context stays
+ * usable), ACAC_OK if it completed, ACAC_E_ARG for another mode, ACAC_E_CUDA /
+ * ACAC_E_NOMEM on a runtime failure.  Enqueued on `stream` (NULL: the default stream);
+ * synchronises it. */
+int acac_wait_selftest(void *stream, int mode);
+
 /* Block pattern of a subdomain factorization with fill (Sec. 4.2, Table 2), host only (no
  * GPU, no handle): the box of W x H (x D) cells in natural order (x fastest), the radius-2
  * stencil of dimension dim, solver ACAC_SUB_ILU1, ACAC_SUB_ILU2 or ACAC_SUB_LU.  One

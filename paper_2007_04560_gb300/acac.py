@@ -87,6 +87,7 @@ SIGNATURES = {
     "acac_log": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_profile_mask": (ctypes.c_int, [_P, ctypes.c_uint]),
+    "acac_wait_selftest": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_subdomain_pattern": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               _PI, _PI, ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
     "acac_kernel_stats": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_longlong), _PD, _PD, _PD]),

@@ -478,6 +478,28 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, int* err, cudaStream_t s);
 
+// Bounded wait for bit (word_bit) of a shared-memory word set by another warp of the block:
+// true once set, false after limit_ns of the global timer (the caller then records an error
+// and leaves instead of hanging).  One lane polls; the caller broadcasts the verdict.
+__device__ __forceinline__ bool wait_bit_bounded(const volatile unsigned* word, int bit,
+                                                 unsigned long long limit_ns) {
+    if ((*word >> bit) & 1u) return true;
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!((*word >> bit) & 1u)) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        if (t1 - t0 > limit_ns) return false;
+        __nanosleep(128);
+    }
+    return true;
+}
+// The rows of the subdomain factorizations with fill wait at most this long for a row.
+constexpr unsigned long long SPARSE_WAIT_NS = 2000000000ull;
+// Self-check of the bounded waits (ras.cu): mode 0 an mbarrier phase that nothing completes,
+// mode 1 a done bit that nothing sets; *status = ACAC_E_TIMEOUT when the wait gave up.
+cudaError_t launch_wait_selftest(int mode, int* status, cudaStream_t s);
+
 // subsolve.cu: subdomain solves with fill, ILU(1), ILU(2) and exact LU (Sec. 4.2, Table 2).
 // The box matrix A_k is stored by 2x2 blocks on a pattern over the box's cells in natural
 // order (x fastest); the pattern is that of the point factorization (the level of fill of

@@ -284,6 +284,34 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
+// Self-check of the bounded waits: the waits of the production kernels, on an mbarrier
+// phase (mode 0) or a done bit (mode 1) that nothing completes.  Every lane waits; the wait
+// gives up after its limit and the kernel reports it instead of hanging.
+__global__ void wait_selftest_kernel(int mode, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned word;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        word = 0u;
+    }
+    __syncthreads();
+    bool ok;
+    if (mode == 0) {
+        ok = mbar_wait_bounded(smem_addr(&bar), 0u);     // phase 0: no arrival ever comes
+    } else {
+        int v = 1;
+        if (threadIdx.x == 0) v = wait_bit_bounded(&word, 0, 200000000ull) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, v, 0) != 0;
+    }
+    if (threadIdx.x == 0) *status = ok ? ACAC_OK : ACAC_E_TIMEOUT;
+}
+
+cudaError_t launch_wait_selftest(int mode, int* status, cudaStream_t s) {
+    wait_selftest_kernel<<<1, 32, 0, s>>>(mode, status);
+    return cudaGetLastError();
+}
+
 // Producer / consumer pipeline.  The last warp is the producer: its lane 0 streams
 // level stages into the ring (full[b] completes when a stage has landed) and reuses
 // buffer b only after the consumers released it (empty[b]).  The other warps are

@@ -2027,6 +2027,20 @@ int acac_step_host(acac_handle* h, double* u_host, double* v_host, acac_step_inf
     }
 }
 
+int acac_wait_selftest(void* stream, int mode) {
+    if (mode != 0 && mode != 1) return ACAC_E_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int* d = nullptr;
+    if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return ACAC_E_NOMEM;
+    int host = ACAC_E_CUDA, st = ACAC_E_CUDA;
+    if (cudaMemsetAsync(d, 0, sizeof(int), s) == cudaSuccess && launch_wait_selftest(mode, d, s) == cudaSuccess &&
+        cudaMemcpyAsync(&host, d, sizeof(int), cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+        cudaStreamSynchronize(s) == cudaSuccess)
+        st = host;
+    cudaFree(d);
+    return st;
+}
+
 int acac_subdomain_pattern(int dim, int W, int H, int D, int solver, int* ptr, int* col, long long cap,
                            long long* nnz) {
     if ((dim != 2 && dim != 3) || W < 1 || H < 1 || (dim == 3 && D < 1) || !nnz) return ACAC_E_ARG;

@@ -231,8 +231,6 @@ __global__ void __launch_bounds__(256) sparse_init_kernel(Geom g, const SubInfo*
 // profile is) the position of (i, j) is arithmetic; otherwise the warp's map (2 band + 1
 // ints in shared memory) takes j - i + band to it, -1 where row i keeps no entry (the
 // update is dropped).
-constexpr unsigned long long SPARSE_WAIT_NS = 4000000000ull;
-
 template <typename T>
 __global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __restrict__ boxes,
                                                              const SparseShapeDev* __restrict__ shapes,
@@ -265,20 +263,7 @@ __global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __
             // row k final?  Lane 0 polls (bounded) and the warp takes its verdict
             int ok = 1;
             if (lane == 0) {
-                const volatile unsigned* dw = done + (k >> 5);
-                if (!((*dw >> (k & 31)) & 1u)) {
-                    unsigned long long t0;
-                    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-                    while (!((*dw >> (k & 31)) & 1u)) {
-                        unsigned long long t1;
-                        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-                        if (t1 - t0 > SPARSE_WAIT_NS) {
-                            ok = 0;
-                            break;
-                        }
-                        __nanosleep(128);
-                    }
-                }
+                ok = wait_bit_bounded(done + (k >> 5), k & 31, SPARSE_WAIT_NS) ? 1 : 0;
                 __threadfence_block();
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
