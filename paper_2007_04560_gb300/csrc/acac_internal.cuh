@@ -392,6 +392,8 @@ struct ResidualArgs {
     int* flags;          // bit 0: midpoint inadmissible, bit 1: trial state inadmissible
     const double* L0 = nullptr;   // discrete Laplacians of X0's two fields (launch_laplacian), or
                                   // null: formed from X0 in pass A
+    const double* shift_sum = nullptr;   // if set, the trial shift is shift_sum[0] * shift_scale
+    double shift_scale = 0.0;            // (read on the device: no host round trip)
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 // L = discrete Laplacian of both fields of X (2N each): the start state's part of G3, fixed

@@ -297,8 +297,9 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
 // with flag bit 1 when some u+v or u-v leaves (0, 1).
 __global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
     int flag = 0;
+    const double shift = a.shift_sum ? a.shift_sum[0] * a.shift_scale : a.shift;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
-        const double u = fma(a.lam, a.S[c] + a.shift, a.X[c]);
+        const double u = fma(a.lam, a.S[c] + shift, a.X[c]);
         const double v = fma(a.lam, a.S[N + c], a.X[N + c]);
         a.Xt[c] = u;
         a.Xt[N + c] = v;

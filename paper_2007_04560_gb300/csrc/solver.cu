@@ -123,6 +123,8 @@ struct acac_handle {
     // FP64 state
     double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
     double* lap0 = nullptr;     // Laplacians of X0 during a Newton solve (pass A reads them)
+    double* shift_dev = nullptr;   // sum(u^n - u - S_u) of the current Newton direction
+    bool factor_check = false;     // a deferred factorization's flags are still to be read
     // Krylov precision buffers
     void *V, *w, *kt, *jtmp, *cache, *J, *coef, *gscratch;
     void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
@@ -342,11 +344,13 @@ int read_flags(acac_handle* h) {
 
 // ||F(X)|| (or of the trial point X + lam (S + shift e_u)) and the G buffer.
 double eval_residual(acac_handle* h, const double* X, const double* S, double lam, double shift,
-                     double dt, int* flags_out, bool use_lap0 = false) {
+                     double dt, int* flags_out, bool use_lap0 = false, const double* shift_sum = nullptr) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     ResidualArgs a;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
     a.L0 = use_lap0 ? h->lap0 : nullptr;
+    a.shift_sum = shift_sum;
+    a.shift_scale = 1.0 / (double)h->N;
     a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.red = red_to(h, h->red); a.flags = h->flags;
     if (S) {
         // the line search's trial state X + lam (S + shift e_u), then F there
@@ -356,9 +360,10 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     }
     KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 0.0, launch_residual_g(h->g, h->k, a, h->stream));
     KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
-    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double f2 = read_scalars(h, 1);
-    *flags_out = *h->host_flags;
+    // bit 3: a Schwarz apply gave up a bounded wait (sticky flag of the handle)
+    *flags_out = h->host_flags[0] | (h->host_flags[1] ? 8 : 0);
     return sqrt(f2);
 }
 
@@ -413,9 +418,20 @@ void precond(acac_handle* h, const T* r, T* z) {
                             h->stream));
 }
 
+// With defer, the pivot / timeout flags are not read here: the Newton loop's GMRES reads
+// them with its first scalar read-back (one host round trip fewer per step).
 template <typename T>
-int factor(acac_handle* h) {
+int factor(acac_handle* h, bool defer = false) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+    auto done = [&](bool timeout_bit) -> int {
+        h->n_factor++;
+        if (defer) {
+            h->factor_check = true;
+            return ACAC_OK;
+        }
+        const int f = read_flags(h);
+        return (timeout_bit && (f & 8)) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
+    };
     if (h->p.subdomain_solver != ACAC_SUB_ILU0) {
         // A_k of every box from the stencil-diagonal Jacobian, then the block IKJ
         // elimination on the ILU(1) / ILU(2) / LU pattern
@@ -427,9 +443,7 @@ int factor(acac_handle* h) {
         KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 8.0 * h->sblocks, 0.0,
             launch_sparse_factor<T>((int)h->subs.size(), h->sbox_dev, h->sshape_dev, (T*)h->sval, (T*)h->sdinv,
                                     h->flags, h->s_fthreads, h->s_fsmem, h->s_use_map, h->stream));
-        h->n_factor++;
-        const int f = read_flags(h);
-        return (f & 8) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
+        return done(true);
     }
     if (h->g.dim == 3) {
         int packed3 = h->jpacked ? 1 : 0;
@@ -442,8 +456,7 @@ int factor(acac_handle* h) {
             launch_ras_factor3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev,
                                   packed3 ? (const T*)h->Jp : (const T*)h->J, packed3, (T*)h->coef,
                                   h->ras_threads, h->flags, h->stream));
-        h->n_factor++;
-        return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+        return done(false);
     }
     const int ring_cells = h->ras_maxcnt;
     const size_t smem = sizeof(int) * (size_t)(((h->ras_maxlev + 1 + 3) & ~3) + 3 & ~3) +
@@ -461,8 +474,7 @@ int factor(acac_handle* h) {
         launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev,
                              packed ? (const T*)h->Jp : (const T*)h->J, packed, (T*)h->coef,
                              h->ras_threads, ring_cells, smem, h->flags, h->stream));
-    h->n_factor++;
-    return read_flags(h) ? ACAC_E_DIVERGED : ACAC_OK;
+    return done(false);
 }
 
 // One Arnoldi step of GMRES: v_{j+1} = J M^{-1} v_j orthogonalised against v_0..v_j
@@ -550,7 +562,7 @@ void arnoldi_step_sync(acac_handle* h, int j) {
 // Restarted GMRES for J x = b (b = h->b, double), x0 = 0, right preconditioning.
 // Returns ACAC_OK or ACAC_E_DIVERGED; x (double, 2N) receives the solution.
 template <typename T>
-int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
+int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer_timeout = false) {
     // the first call runs eagerly (it also sets the kernels' shared-memory limits);
     // later calls replay captured graphs
     struct Count {
@@ -565,7 +577,16 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
     T* tt = (T*)h->kt;
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
     KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
+    // a deferred factorization's flags come back with this read-back
+    if (h->factor_check)
+        CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double bnorm = sqrt(read_scalars(h, 1));
+    if (h->factor_check) {
+        h->factor_check = false;
+        const int f = h->host_flags[0];
+        if (f & 8) return ACAC_E_TIMEOUT;
+        if (f) return ACAC_E_DIVERGED;
+    }
     const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
     double beta = bnorm;
     int its = 0;
@@ -631,11 +652,15 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out) {
         KL(ACAC_K_VECTOR, launch_lincomb<T>((const T*)h->Zb, ld, k, h->red, tt, n, h->stream));
         KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, tt, x, n, h->stream));
         if (done) {
-            CU(cudaMemcpyAsync(h->host_flags + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-            CU(cudaStreamSynchronize(h->stream));
             *its_out = its;
             *resid_out = resid;
-            if (h->host_flags[1]) return ACAC_E_TIMEOUT;
+            // the apply's timeout flag is sticky: with defer_timeout the caller reads it at
+            // its next read-back instead of here
+            if (!defer_timeout) {
+                CU(cudaMemcpyAsync(h->host_flags + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+                CU(cudaStreamSynchronize(h->stream));
+                if (h->host_flags[1]) return ACAC_E_TIMEOUT;
+            }
             return (resid <= tol || hn == 0.0) ? ACAC_OK : ACAC_E_DIVERGED;
         }
         // restart: r = b - J x
@@ -689,7 +714,7 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         const bool refactor = (it == 0) || !h->p.ilu_reuse;
         linearize_and_maybe_assemble<T>(h, h->X, dt, refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED);
         if (refactor) {
-            int st = factor<T>(h);
+            int st = factor<T>(h, true);
             if (st != ACAC_OK) return st;
         }
         // b = -F
@@ -697,17 +722,18 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
         int gits = 0;
         double gres = 0.0;
-        int st = gmres<T>(h, h->S, &gits, &gres);
+        int st = gmres<T>(h, h->S, &gits, &gres, true);
         info->gmres_its += gits;
         if (st != ACAC_OK) return st;
-        // shift S_u by a constant so that sum(u + S_u) = sum(u^n)
-        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->red), h->stream));
-        const double shift = read_scalars(h, 1) / (double)N;
+        // shift S_u by a constant so that sum(u + S_u) = sum(u^n); the sum stays on the
+        // device, where the trial kernel reads it
+        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->shift_dev), h->stream));
         double lam = 1.0;
         const double f2 = fnorm * fnorm;
         double ft = 0.0;
         while (true) {
-            ft = eval_residual(h, h->X, h->S, lam, shift, dt, &fl, true);
+            ft = eval_residual(h, h->X, h->S, lam, 0.0, dt, &fl, true, h->shift_dev);
+            if (fl & 8) return ACAC_E_TIMEOUT;
             if (fl == 0 && isfinite(ft) && ft * ft <= (1.0 - 2e-4 * lam) * f2) break;
             lam *= 0.5;
             h->ls_cuts++;
@@ -1097,7 +1123,7 @@ void build_sparse(acac_handle* h) {
 }
 
 void free_all(acac_handle* h) {
-    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0, h->V, h->Zb, h->w,
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0, h->shift_dev, h->V, h->Zb, h->w,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
                     h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
@@ -1292,6 +1318,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         dmalloc(&h->G, 3 * N * 8); dmalloc(&h->b, n2 * 8); dmalloc(&h->r, n2 * 8); dmalloc(&h->tmpd, n2 * 8);
         dmalloc(&h->stage, n2 * 8);
         dmalloc(&h->lap0, n2 * 8);
+        dmalloc(&h->shift_dev, 16);
         h->ldV = (n2 + 63) / 64 * 64;
         dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
         dmalloc(&h->Zb, (size_t)p->gmres_restart * h->ldV * ks);
