@@ -511,8 +511,14 @@ void arnoldi_step(acac_handle* h, int j) {
 template <typename T>
 void arnoldi_step_sync(acac_handle* h, int j) {
     const bool use_graph = h->p.graphs && h->gmres_calls > 0;
+    // a deferred factorization's flags come back with this read-back
+    auto fetch_factor_flags = [&]() {
+        if (h->factor_check)
+            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    };
     if (!use_graph) {
         arnoldi_step<T>(h, j);
+        fetch_factor_flags();
         CU(cudaStreamSynchronize(h->stream));
         prof_collect(h);
         return;
@@ -555,6 +561,7 @@ void arnoldi_step_sync(acac_handle* h, int j) {
         h->kernel_flops[r.id] += r.flops;
         if (r.a) h->pending.push_back({r.id, r.a, r.b, true});
     }
+    fetch_factor_flags();
     CU(cudaStreamSynchronize(h->stream));
     prof_collect(h);
 }
@@ -562,7 +569,10 @@ void arnoldi_step_sync(acac_handle* h, int j) {
 // Restarted GMRES for J x = b (b = h->b, double), x0 = 0, right preconditioning.
 // Returns ACAC_OK or ACAC_E_DIVERGED; x (double, 2N) receives the solution.
 template <typename T>
-int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer_timeout = false) {
+// known_bnorm >= 0: ||b|| is already known to the caller (the Newton loop's b = -F has the
+// norm of its residual evaluation), so no reduction and read-back are spent on it.
+int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer_timeout = false,
+          double known_bnorm = -1.0) {
     // the first call runs eagerly (it also sets the kernels' shared-memory limits);
     // later calls replay captured graphs
     struct Count {
@@ -576,16 +586,21 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer
     T* w = (T*)h->w;
     T* tt = (T*)h->kt;
     CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
-    KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
-    // a deferred factorization's flags come back with this read-back
-    if (h->factor_check)
-        CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    const double bnorm = sqrt(read_scalars(h, 1));
-    if (h->factor_check) {
+    // a deferred factorization's flags come back with the first read-back of the solve
+    auto factor_status = [&]() -> int {
+        if (!h->factor_check) return ACAC_OK;
         h->factor_check = false;
         const int f = h->host_flags[0];
-        if (f & 8) return ACAC_E_TIMEOUT;
-        if (f) return ACAC_E_DIVERGED;
+        return (f & 8) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
+    };
+    double bnorm = known_bnorm;
+    if (bnorm < 0.0) {
+        KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
+        if (h->factor_check)
+            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        bnorm = sqrt(read_scalars(h, 1));
+        const int fs = factor_status();
+        if (fs != ACAC_OK) return fs;
     }
     const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
     double beta = bnorm;
@@ -593,7 +608,13 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer
     double resid = beta;
     *its_out = 0;
     *resid_out = beta;
-    if (beta <= tol) return ACAC_OK;
+    if (beta <= tol) {
+        if (h->factor_check) {      // no read-back happened yet in this solve
+            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+            CU(cudaStreamSynchronize(h->stream));
+        }
+        return factor_status();
+    }
     std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m + 1);
     auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
     const double* rsrc = h->b;
@@ -608,6 +629,11 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer
         for (int j = 0; j < m; ++j) {
             arnoldi_step_sync<T>(h, j);
             ++its;
+            const int fs = factor_status();
+            if (fs != ACAC_OK) {
+                *its_out = its;
+                return fs;
+            }
             const int passes = h->p.cgs_refine ? 2 : 1;
             for (int i = 0; i <= j; ++i) {
                 double hij = h->host[i];
@@ -722,7 +748,7 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
         int gits = 0;
         double gres = 0.0;
-        int st = gmres<T>(h, h->S, &gits, &gres, true);
+        int st = gmres<T>(h, h->S, &gits, &gres, true, fnorm);
         info->gmres_its += gits;
         if (st != ACAC_OK) return st;
         // shift S_u by a constant so that sum(u + S_u) = sum(u^n); the sum stays on the
