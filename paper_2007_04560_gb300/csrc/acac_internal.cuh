@@ -482,7 +482,7 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
 
 // Bounded wait for bit (word_bit) of a shared-memory word set by another warp of the block:
 // true once set, false after limit_ns of the global timer (the caller then records an error
-// and leaves instead of hanging).  One lane polls; the caller broadcasts the verdict.
+// and leaves instead of hanging).  One lane polls; the caller broadcasts the result.
 __device__ __forceinline__ bool wait_bit_bounded(const volatile unsigned* word, int bit,
                                                  unsigned long long limit_ns) {
     if ((*word >> bit) & 1u) return true;

@@ -260,7 +260,7 @@ __global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __
         }
         for (int p = p0; p < pd; ++p) {
             const int k = contig ? c0 + (p - p0) : sh.col[p];
-            // row k final?  Lane 0 polls (bounded) and the warp takes its verdict
+            // row k final?  Lane 0 polls (bounded) and the warp takes its result
             int ok = 1;
             if (lane == 0) {
                 ok = wait_bit_bounded(done + (k >> 5), k & 31, SPARSE_WAIT_NS) ? 1 : 0;
