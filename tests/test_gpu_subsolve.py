@@ -10,7 +10,7 @@ import pytest
 
 from oracle import acac_oracle as O
 from tests._helpers import dev, host, interleaved_to_soa, lib_built, need_cuda, soa, soa_to_interleaved
-from workloads import (BC_NEUMANN, BC_PERIODIC, PREC_MIXED, SUB_ILU1, SUB_ILU2, SUB_LU, Params,
+from workloads import (BC_NEUMANN, BC_PERIODIC, DT_ADAPTIVE, PREC_MIXED, SUB_ILU1, SUB_ILU2, SUB_LU, Params,
                        initial_fields, perturbed_pair, random_vector)
 
 pytestmark = pytest.mark.gpu
@@ -134,3 +134,54 @@ def test_adjoint_rejects_fill_solvers(P):
     with P.Solver(p) as s:
         with pytest.raises(AcacError):
             s.adjoint(dev(u.ravel()), dev(v.ravel()), 2, 1e-3, dev(u.ravel()), dev(v.ravel()), every=1)
+
+
+def test_apply_mixed_precision_3d(P):
+    dim, n, parts, bc, delta = CASES[2]
+    p = Params(dim=dim, n=n, bc=bc, ras_parts=parts, ras_overlap=delta, subdomain_solver=SUB_ILU2,
+               precision=PREC_MIXED)
+    z, zo = _apply_pair(P, p)
+    assert _rel(z, zo) <= 2e-4
+
+
+@pytest.mark.parametrize("solver", [SUB_ILU1, SUB_LU])
+def test_graph_replay_matches_direct_launches(P, solver):
+    """With a fill solver, GMRES iterations replayed from captured graphs give bit-identical
+    steps to direct launches."""
+    import torch
+    p = Params(n=(40, 32, 1), bc=BC_NEUMANN, ras_parts=(3, 2, 1), ras_overlap=1, dt_mode=DT_ADAPTIVE, dt0=1e-4,
+               dt_min=1e-5, dt_max=1e-1, eta0=1e4, subdomain_solver=solver)
+    u, v = initial_fields(p, 7, 0.45, 0.05)
+    out = []
+    for graphs in (0, 1):
+        ug, vg = dev(u.ravel()), dev(v.ravel())
+        with P.Solver(p.replace(graphs=graphs)) as s:
+            infos = [s.step(ug, vg) for _ in range(3)]
+        torch.cuda.synchronize()
+        out.append((host(ug), host(vg), [(i.dt, i.gmres_its, i.newton_its) for i in infos]))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+def test_ensemble_member_equals_single_handle(P):
+    """Member m of an ensemble with ILU(1) subdomain solves is bit-identical to a batch-1
+    handle stepping the same member."""
+    import torch
+    p1 = Params(n=(32, 24, 1), ras_parts=(2, 2, 1), ras_overlap=1, subdomain_solver=SUB_ILU1,
+                precision=PREC_MIXED)
+    fields = [initial_fields(p1, 40 + m, 0.45, 0.05) for m in range(2)]
+    u = np.stack([f[0] for f in fields])
+    v = np.stack([f[1] for f in fields])
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    with P.Solver(p1.replace(batch=2)) as s:
+        for _ in range(2):
+            s.step(ug, vg)
+    torch.cuda.synchronize()
+    gu, gv = host(ug).reshape(2, -1), host(vg).reshape(2, -1)
+    for m in range(2):
+        su, sv = dev(fields[m][0].ravel()), dev(fields[m][1].ravel())
+        with P.Solver(p1) as one:
+            for _ in range(2):
+                one.step(su, sv)
+        torch.cuda.synchronize()
+        assert np.array_equal(host(su), gu[m]) and np.array_equal(host(sv), gv[m]), m

@@ -60,3 +60,22 @@ def test_pattern_errors():
     # too small a cap: only the count is written
     assert A._lib().acac_subdomain_pattern(2, 5, 5, 1, SUB_ILU1, None, None, 0, ctypes.byref(nnz)) == -1
     assert nnz.value > 25
+
+
+@pytest.mark.parametrize("dim,W,H,D", [(2, 9, 7, 1), (3, 5, 4, 6)])
+def test_lu_rows_are_intervals_with_nondecreasing_ends(dim, W, H, D):
+    """The LU profile: every row an interval of columns containing the diagonal, whose last
+    column never decreases from row to row (so a row's upper part reaches every column of
+    the upper parts of the rows before it)."""
+    try:
+        A._lib()
+    except Exception as e:
+        pytest.skip("libacac not available: %s" % e)
+    ptr, col = A.acac_subdomain_pattern(dim, W, H, D, SUB_LU)
+    last = -1
+    for c in range(ptr.size - 1):
+        row = col[ptr[c]:ptr[c + 1]]
+        assert np.array_equal(row, np.arange(row[0], row[-1] + 1))
+        assert row[0] <= c <= row[-1]
+        assert row[-1] >= last
+        last = row[-1]
