@@ -102,7 +102,8 @@ typedef struct acac_params {
                                    follow the usual definition: lev = 0 on the pattern of
                                    A_k, lev(i,j) = min(lev(i,j), lev(i,k) + lev(k,j) + 1)
                                    in natural order, entries of lev <= p kept.  ILU(1),
-                                   ILU(2) and LU: FP64 and mixed; not with the adjoint.    */
+                                   ILU(2) and LU: FP64 and mixed; not with the adjoint;
+                                   boxes of at most 62,500 cells (ACAC_E_ARG otherwise).   */
 } acac_params;
 
 /* Per-step report. */

@@ -1060,6 +1060,17 @@ int acac::validate_params(const acac_params* p) {
     if (p->graphs != 0 && p->graphs != 1) return ACAC_E_ARG;
     if (p->ras_window < 0 || p->ras_window > 2) return ACAC_E_ARG;
     if (p->subdomain_solver < ACAC_SUB_ILU0 || p->subdomain_solver > ACAC_SUB_LU) return ACAC_E_ARG;
+    if (p->subdomain_solver != ACAC_SUB_ILU0) {
+        // the factorizations with fill hold a symbolic pattern per box shape on the host and a
+        // column map per warp in shared memory: the largest box (ceil(n / P) + 2 delta cells
+        // per axis, at most n) may hold 250 x 250 cells
+        long long cells = 1;
+        for (int a = 0; a < p->dim; ++a) {
+            long long w = (p->n[a] + p->ras_parts[a] - 1) / p->ras_parts[a] + 2LL * p->ras_overlap;
+            cells *= w < p->n[a] ? w : p->n[a];
+        }
+        if (cells > 250LL * 250) return ACAC_E_ARG;
+    }
     return ACAC_OK;
 }
 

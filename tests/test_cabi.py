@@ -89,6 +89,12 @@ def test_defaults_and_validation_without_gpu(lib):
     lib.acac_default_params(ctypes.byref(q))
     q.ras_parts[0] = 1                          # periodic needs >= 2 boxes per direction
     assert lib.acac_create(ctypes.byref(q), None, ctypes.byref(h)) == A.E_ARG
+    q = A.acac_params()
+    lib.acac_default_params(ctypes.byref(q))
+    q.n[0] = q.n[1] = 1024
+    q.ras_parts[0] = q.ras_parts[1] = 2          # 514 x 514-cell boxes: too large for a fill solver
+    q.subdomain_solver = 3
+    assert lib.acac_create(ctypes.byref(q), None, ctypes.byref(h)) == A.E_ARG
     assert lib.acac_kernel_name(8).decode() == "ras_apply"
 
 
