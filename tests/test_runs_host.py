@@ -25,8 +25,8 @@ def test_block_average_of_a_linear_field_is_its_value_at_the_coarse_centre(r):
 
 
 def test_relative_l2_over_both_fields():
-    u = torch.tensor([[1.0, 2.0], [3.0, 4.0]])
-    v = torch.tensor([[0.0, 1.0], [0.0, 1.0]])
+    u = torch.tensor([[1.0, 2.0], [3.0, 4.0]], dtype=torch.float64)
+    v = torch.tensor([[0.0, 1.0], [0.0, 1.0]], dtype=torch.float64)
     ur, vr = u + 0.5, v.clone()
     want = np.sqrt(4 * 0.25 / (float((ur ** 2).sum()) + float((vr ** 2).sum())))
     assert runs._rel_l2(u, v, ur, vr) == pytest.approx(want, rel=1e-15)
