@@ -152,3 +152,24 @@ def test_schwarz_with_one_box_and_lu_inverts(solver):
     else:
         z0 = O.RAS(p.replace(subdomain_solver=O.SUB_ILU0), J, "left").apply(r)
         assert err < np.linalg.norm(J @ z0 - r) / np.linalg.norm(r)
+
+
+def test_fill_lowers_oracle_gmres_iterations():
+    """Table 2's trend in the oracle itself: classical AS with overlap 1, one Newton solve on
+    a Neumann problem; the GMRES iterations per Newton iteration do not grow with the fill
+    (ILU(0) >= ILU(1) >= ILU(2) >= LU), LU needs fewer than ILU(0), and every solver reaches
+    the same root (the preconditioner changes the path, not the solution)."""
+    from workloads import initial_fields
+    base = Params(n=(24, 24, 1), bc=BC_NEUMANN, ras_parts=(2, 2, 1), ras_overlap=1, ras_type=1,
+                  newton_rtol=1e-10, gmres_rtol=1e-8)
+    U0 = initial_fields(base, 5, 0.45, 0.05)
+    its, roots = {}, {}
+    for solver in (O.SUB_ILU0, O.SUB_ILU1, O.SUB_ILU2, O.SUB_LU):
+        X, info = O.nks_solve(base.replace(subdomain_solver=solver), U0, 2e-3)
+        assert info.status == O.OK
+        its[solver] = info.gmres_its / info.newton_its
+        roots[solver] = np.concatenate([X[0].ravel(), X[1].ravel()])
+    assert its[O.SUB_LU] <= its[O.SUB_ILU2] <= its[O.SUB_ILU1] <= its[O.SUB_ILU0]
+    assert its[O.SUB_LU] < its[O.SUB_ILU0]
+    for solver in (O.SUB_ILU1, O.SUB_ILU2, O.SUB_LU):
+        assert np.linalg.norm(roots[solver] - roots[O.SUB_ILU0]) <= 1e-8 * np.linalg.norm(roots[O.SUB_ILU0])
