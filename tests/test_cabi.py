@@ -107,3 +107,20 @@ def test_binding_fails_loudly_without_library(tmp_path, monkeypatch):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         A.load()
     importlib.reload(A)
+
+
+def test_python_parameters_match_the_c_struct():
+    """Every field of acac_params has a Params field of the same name and vice versa, so no
+    setting is silently dropped or defaulted on its way to the library; and the binding
+    refuses host tensors before it reaches the library."""
+    import dataclasses
+    import paper_2007_04560_gb300.acac as A
+    from workloads import Params
+    py = {f.name for f in dataclasses.fields(Params)}
+    c = {n for n, _ in A.acac_params._fields_}
+    assert py == c
+    torch = pytest.importorskip("torch")
+    with pytest.raises(TypeError):
+        A._dev(torch.zeros(4), torch.float64, 4, "u")
+    with pytest.raises(TypeError):
+        A._dev([0.0] * 4, torch.float64, 4, "u")
