@@ -6,10 +6,15 @@ One bench step = one accepted time step (acac_step): residual, Jacobian /
 linearisation, Schwarz-ILU(0) factorization and application, GMRES, Newton line
 search, energy / mass and the adaptive-dt predictor.
 
-Default workload: 2D 1024x1024 periodic, FP64, adaptive dt from 1e-4 in
-[1e-5, 1e-1], RAS 16x16 overlap 2 ILU(0), seeded random initial fields
-(u = 0.4 + 0.05 U(-1,1), v = 0.05 U(-1,1), seed 1).  The working set (state,
-Krylov basis, ILU factors: ~1 GB) is far larger than L2, so no flush is needed.
+Default workload: 2D 2048x2048 periodic on [0,32]^2 (mesh spacing h = 1/64), adaptive
+dt from 1e-4 in [1e-5, 1e-1], RAS 16x16 overlap 2 ILU(0) (256 boxes of 132^2 cells),
+seeded random initial fields (u = 0.4 + 0.05 U(-1,1), v = 0.05 U(-1,1), seed 2),
+Newton rtol 1e-8.  `value` is the FP64 form's rate; the mixed-precision form (FP32
+Jacobian, Krylov vectors and ILU; FP64 residual, Newton update, energy and dt
+estimator) runs the same steps from the same initial state in the same process and
+is reported in the `mixed` object with its speed-up over FP64 and the relative L2
+difference of its fields from the FP64 fields.  The working set (state, Krylov basis,
+ILU factors: several GB) is far larger than L2, so no flush is needed.
 
 Prints one JSON line (rank 0).  --impl reference times the CPU FP64 oracle on the
 host instead (a bounded sample of the same workload).
@@ -29,31 +34,27 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import C2, PREC_FP64, PREC_MIXED, WORKLOADS  # noqa: E402
+from workloads import C3_FP64, PREC_FP64, PREC_MIXED, WORKLOADS, initial_fields  # noqa: E402
 
-FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
+FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flop x max SM clock
+FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on the
-# 1024^2 workload: FP64 from the launch list of this benchmark's own run
-# (profiles/launches_2d-1024x1024-periodic-fp64.md), FP32 apply from
-# profiles/ras_apply_2d-1024x1024.md.  A kernel changed after its capture must be removed.
-TRAFFIC = {
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_FP64): 552.4e6,
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_apply", PREC_MIXED): 282.9e6,
-    ("2d-1024x1024-periodic-fp64-adaptive", "ras_factor", PREC_FP64): 975.9e6,
-}
+# DRAM bytes (read + write) per launch of the dominant kernels, from one-kernel ncu captures
+# of the current kernels (profiles/).  Keyed by (kernel class, precision, box width incl.
+# overlap); the value is per box cell, so a launch's traffic is this x the box cells of
+# the launch.  A kernel changed after its capture must be removed from this table.
+TRAFFIC_PER_BOX_CELL = {}
 
 
-def peaks():
+def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return float(d["hbm_gbs"]), "measured"
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
     except Exception:
-        return FALLBACK_HBM_GBS, "fallback"
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no MEASURED_PEAKS.json)"
 
 
 class ClockSampler:
@@ -118,55 +119,155 @@ def smi_index():
     return os.environ.get("LOCAL_RANK", "0")
 
 
-def cpu_baseline(workload_name, precision, steps=1):
-    """Time the CPU oracle as it stands, single-threaded, on one time step of the
-    workload (run in a fresh process)."""
-    code = (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from workloads import WORKLOADS\n"
-        "from oracle import acac_oracle as O\n"
-        "w = WORKLOADS[%r]\n"
-        "one = hasattr(w, 'member_params')  # an ensemble: time member 0\n"
-        "p = (w.member_params(0) if one else w.params).replace(precision=0)\n"
-        "u, v = w.member_fields(0) if one else w.fields()\n"
-        "st = O.Stepper(p)\n"
-        "t = time.perf_counter()\n"
-        "for k in range(%d):\n"
-        "    X, info = st.step(u, v)\n"
-        "    u, v = X\n"
-        "el = time.perf_counter() - t\n"
-        "print(json.dumps({'seconds': el, 'steps': %d, 'newton': info.newton_its, 'gmres': info.gmres_its}))\n"
-    ) % (ROOT, workload_name, steps, steps)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=1800)
-    if r.returncode != 0:
-        return {"error": r.stderr[-400:]}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+def smi_index():
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    if vis:
+        return vis.split(",")[int(os.environ.get("LOCAL_RANK", "0"))]
+    return os.environ.get("LOCAL_RANK", "0")
 
 
-def roofline(stats, precision, hbm_gbs, peak_src, workload, share_stats=None):
+# ------------------------------------------------------------------ CPU oracle sample
+# The oracle needs about four minutes of one host core for one 2048^2 step, so it is timed on
+# a bounded piece of the same workload: a PIECE x PIECE periodic grid with the same mesh
+# spacing, coefficients, tolerances and Schwarz box geometry (boxes of the same owned width
+# and overlap, hence the same 132^2 extended boxes at 2048^2), stepped at dt = dt_min, the
+# step size of the timed GPU steps once the predictor has settled.  Its cost per step is
+# proportional to the number of cells at fixed box geometry and iteration counts, so the
+# piece's rate is scaled by piece cells / workload cells.
+PIECE = 512
+
+
+def piece_params(w):
+    p = w.params.replace(batch=1, precision=PREC_FP64)
+    n = min(PIECE, p.n[0])
+    scale = p.n[0] // n
+    h = p.L[0] / p.n[0]
+    parts = max(2, p.ras_parts[0] // scale)
+    return p.replace(n=(n, n, 1), L=(n * h, n * h, 1.0), ras_parts=(parts, parts, 1), dt_mode=0, dt0=p.dt_min)
+
+
+def oracle_worker(spec):
+    """One oracle process of the CPU sample: build the piece, print 'ready', then for every
+    'go' line on stdin take one time step from the piece's initial state and print the
+    step's monotonic start / end times and iteration counts."""
+    from oracle import acac_oracle as O
+    d = json.loads(spec)
+    w = WORKLOADS[d["workload"]]
+    p = piece_params(w)
+    u, v = initial_fields(p, int(d["seed"]), w.u_mean, w.amp)
+    O.build_lib()
+    print("ready", flush=True)
+    for line in sys.stdin:
+        if line.strip() != "go":
+            break
+        st = O.Stepper(p)
+        t0 = time.monotonic()
+        X, info = st.step(u, v)
+        t1 = time.monotonic()
+        print(json.dumps({"t0": t0, "t1": t1, "newton": info.newton_its, "gmres": info.gmres_its,
+                          "status": info.status}), flush=True)
+
+
+class OracleSample:
+    """`procs` oracle processes, each stepping its own seeded piece; one round = every
+    process takes one step at the same moment.  Piece steps per second of a round, times
+    piece cells / workload cells, is the oracle's rate in workload steps per second."""
+
+    def __init__(self, w, procs):
+        env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+                   CUDA_VISIBLE_DEVICES="")
+        self.w = w
+        self.p = piece_params(w)
+        self.procs = []
+        for i in range(procs):
+            spec = json.dumps({"workload": w.name, "seed": 1000 * w.seed + i})
+            self.procs.append(subprocess.Popen([sys.executable, os.path.abspath(__file__), "--oracle-worker", spec],
+                                               stdin=subprocess.PIPE, stdout=subprocess.PIPE, text=True, env=env))
+        for pr in self.procs:
+            if pr.stdout.readline().strip() != "ready":
+                raise RuntimeError("oracle worker failed to start")
+
+    def round(self):
+        for pr in self.procs:
+            pr.stdin.write("go\n")
+            pr.stdin.flush()
+        res = [json.loads(pr.stdout.readline()) for pr in self.procs]
+        wall = max(r["t1"] for r in res) - min(r["t0"] for r in res)
+        scale = self.p.ncells / self.w.params.ncells
+        return len(res) * scale / wall, wall, res
+
+    def close(self):
+        for pr in self.procs:
+            try:
+                pr.stdin.write("quit\n")
+                pr.stdin.flush()
+                pr.stdin.close()
+                pr.wait(timeout=30)
+            except Exception:
+                pr.kill()
+
+
+def cpu_baseline(w, repeats=3):
+    """The oracle as it stands, on the host: single-threaded, and one process per host core
+    (at most the number of pieces that tile the workload grid), median of `repeats` rounds."""
+    ncpu = os.cpu_count() or 1
+    p = piece_params(w)
+    tiles = max(1, w.params.ncells // p.ncells)
+    out = {"unit": "steps/s", "kind": "oracle", "nproc": ncpu}
+    for label, procs in (("single", 1), ("all_cores", min(ncpu, tiles))):
+        sm = OracleSample(w, procs)
+        try:
+            rounds = [sm.round() for _ in range(repeats)]
+        finally:
+            sm.close()
+        rates = sorted(r[0] for r in rounds)
+        med = rates[len(rates) // 2]
+        its = rounds[0][2][0]
+        out[label] = {"value": med, "cores": procs, "round_seconds": [round(r[1], 3) for r in rounds],
+                      "newton": its["newton"], "gmres": its["gmres"]}
+    out["value"] = out["all_cores"]["value"]
+    out["cores"] = out["all_cores"]["cores"]
+    out["sample"] = (
+        "FP64 NumPy/SciPy + C ILU(0) oracle on %dx%d periodic pieces of the workload (same h, coefficients, "
+        "tolerances and %dx%d Schwarz boxes with overlap %d), one time step at dt = dt_min = %g from seeded "
+        "initial states, scaled by piece/workload cells (1/%d); median of %d rounds.  single: one process; "
+        "all_cores: %d processes at once, one piece each (the pieces are not coupled, so this bounds a "
+        "multi-core oracle from above); nproc = %d" % (
+            p.n[0], p.n[1], p.n[0] // p.ras_parts[0] + 2 * p.ras_overlap, p.n[1] // p.ras_parts[1] + 2 * p.ras_overlap,
+            p.ras_overlap, p.dt0, tiles, repeats, out["all_cores"]["cores"], ncpu))
+    return out
+
+
+# ------------------------------------------------------------------ roofline
+def fp64_peak(probe):
+    if probe:
+        return probe, "measured: acac_peak_probe DFMA rate in this run"
+    return FP64_DERIVED_TFLOPS, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
+
+
+def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None):
     name, (n, ms, b, f) = max(stats.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
         return None
     gbs = b / (ms * 1e-3) / 1e9
     tflops = f / (ms * 1e-3) / 1e12
-    fpeak = FP64_PEAK_TFLOPS if precision == PREC_FP64 else FP32_PEAK_TFLOPS
-    traffic = TRAFFIC.get((workload, name, precision))
+    hbm_gbs, hbm_src = hbm
+    if precision == PREC_FP64:
+        fpeak, fsrc = fp64_peak(probe_fp64)
+    else:
+        fpeak, fsrc = FP32_DERIVED_TFLOPS, "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"
+    per = TRAFFIC_PER_BOX_CELL.get((name, precision, box_w))
+    traffic = per * box_cells if per is not None else None
     intensity = f / b if b > 0 else 0.0
     ridge = fpeak * 1e12 / (hbm_gbs * 1e9)
     out = {"kernel": name, "launches": n, "avg_launch_us": ms * 1e3 / n, "share_of_kernel_time": None,
-           "traffic": traffic}
+           "traffic": traffic, "bytes_per_launch": b / n, "flops_per_launch": f / n}
     if f > 0 and intensity > ridge:
-        out.update({"bound": "alu", "achieved": tflops, "peak": fpeak, "unit": "TFLOP/s",
-                    "frac": tflops / fpeak,
-                    "peak_source": "derived: 152 SMs x %s/clk x 2 flop x 2.07 GHz" %
-                                   ("2 DFMA" if precision == PREC_FP64 else "128 FFMA"),
-                    "hbm_achieved_gbs": gbs})
+        out.update({"bound": "alu", "achieved": tflops, "peak": fpeak, "unit": "TFLOP/s", "frac": tflops / fpeak,
+                    "peak_source": fsrc, "hbm_achieved_gbs": gbs})
     else:
         out.update({"bound": "hbm", "achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs,
-                    "peak_source": peak_src + " (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured"
-                    else "fallback 6.8 TB/s", "tflops_achieved": tflops})
-    # share of GPU kernel time: from a run in which every class was timed
+                    "peak_source": hbm_src, "tflops_achieved": tflops})
     src = share_stats if share_stats is not None else stats
     tot = sum(v[1] for v in src.values())
     out["share_of_kernel_time"] = src[name][1] / tot if tot > 0 else None
@@ -196,75 +297,82 @@ def job_rate(world, members, steps, seconds):
     return world * members * steps / seconds
 
 
+def twin_of(name):
+    """The workload of the other precision form, if there is one."""
+    for a, b in (("-fp64-", "-mixed-"), ("-mixed-", "-fp64-")):
+        if a in name and name.replace(a, b) in WORKLOADS:
+            return name.replace(a, b)
+    return None
+
+
 def run_mine(args, rank, world):
     import numpy as np
     import torch
     import paper_2007_04560_gb300 as P
     from paper_2007_04560_gb300 import build
+    from paper_2007_04560_gb300.acac import acac_peak_probe
 
     build.build()
     w = WORKLOADS[args.workload]
-    prec = w.params.precision if args.precision is None else (PREC_MIXED if args.precision == "mixed" else PREC_FP64)
-    p = w.params.replace(precision=prec)
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     u0, v0 = w.fields()
-    N = p.ncells
-    B = int(p.batch)                       # ensemble members (1: one problem)
+    B = int(w.params.batch)                  # ensemble members (1: one problem)
+    N = w.params.ncells
 
-    def set_member_coeffs(solver):
-        if B > 1:
-            th = w.thetas()
-            for m in range(B):
-                solver.set_coeffs(m, p.alpha, p.beta, float(th[m]), p.gamma, p.rho)
+    def barrier():
+        rank_barrier(world)
 
     def report(info):
         """Per-step report; an ensemble reports member 0's iterations and dt."""
         return (info[0] if isinstance(info, list) else info).as_dict()
 
-    def barrier():
-        rank_barrier(world)
-
-    # ---- device-resident timed region
-    s = P.Solver(p, stream)
-    set_member_coeffs(s)
-    u = torch.tensor(u0.ravel(), device=dev)
-    v = torch.tensor(v0.ravel(), device=dev)
-    for _ in range(args.warmup - 1):
+    def timed_form(wl):
+        """W warm-up steps and K timed steps of workload wl on the device (inputs resident in
+        HBM).  Returns the timing, the kernel statistics and the final fields."""
+        p = wl.params
+        s = P.Solver(p, stream)
+        if B > 1:
+            th = wl.thetas()
+            for m in range(B):
+                s.set_coeffs(m, p.alpha, p.beta, float(th[m]), p.gamma, p.rho)
+        u = torch.tensor(u0.ravel(), device=dev)
+        v = torch.tensor(v0.ravel(), device=dev)
+        for _ in range(args.warmup - 1):
+            s.step(u, v)
+        # the last warm-up step times every kernel class; the timed region then times only
+        # the class that took the most time there (two events per timed launch cost host time)
+        s.profile(True)
         s.step(u, v)
-    # the last warm-up step times every kernel class; the timed region then times only
-    # the class that took the most time there (two events per timed launch cost host
-    # time, which an ensemble's host-driven members feel)
-    s.profile(True)
-    s.step(u, v)
-    warm_stats = s.kernel_stats()
-    dominant = max(warm_stats.items(), key=lambda kv: kv[1][1])[0]
-    s.profile(True, kernels=[dominant])
-    sampler = ClockSampler(smi_index())
-    sampler.start()
-    infos = []
-    barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        infos.append(report(s.step(u, v)))
-    e1.record(stream)
-    torch.cuda.synchronize()
-    barrier()
-    clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    stats = s.kernel_stats()
-    s.close()
-    ms = max_over_ranks(ms, world, dev)
-    launches = int(sum(v[0] for v in stats.values()))
+        warm_stats = s.kernel_stats()
+        dominant = max(warm_stats.items(), key=lambda kv: kv[1][1])[0]
+        s.profile(True, kernels=[dominant])
+        infos = []
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            infos.append(report(s.step(u, v)))
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+        stats = s.kernel_stats()
+        s.close()
+        return {"ms": ms, "stats": stats, "warm_stats": warm_stats, "dominant": dominant, "infos": infos,
+                "u": u.cpu().numpy(), "v": v.cpu().numpy(), "params": p}
 
-    # ---- end to end through the C ABI with host buffers (H2D + step + D2H per step)
-    e2e = None
-    if not args.no_e2e:
+    def e2e_form(wl):
+        """Same steps through the C ABI with host buffers: H2D of the state, the step and the
+        D2H of the result inside the timed region, every step."""
+        p = wl.params
         s2 = P.Solver(p, stream)
-        set_member_coeffs(s2)
+        if B > 1:
+            th = wl.thetas()
+            for m in range(B):
+                s2.set_coeffs(m, p.alpha, p.beta, float(th[m]), p.gamma, p.rho)
         uh = torch.tensor(u0.ravel()).pin_memory()
         vh = torch.tensor(v0.ravel()).pin_memory()
         for _ in range(args.warmup):
@@ -278,13 +386,50 @@ def run_mine(args, rank, world):
         el = max_over_ranks(time.perf_counter() - t0, world, dev)
         barrier()
         s2.close()
-        e2e = {"value": job_rate(world, B, args.steps, el), "unit": "steps/s" if B == 1 else "member-steps/s",
-               "h2d_bytes_per_step": 16 * N * B, "d2h_bytes_per_step": 16 * N * B}
+        return {"value": job_rate(world, B, args.steps, el), "unit": "steps/s" if B == 1 else "member-steps/s",
+                "h2d_bytes_per_step": 16 * N * B, "d2h_bytes_per_step": 16 * N * B}
+
+    def box_geometry(p):
+        if p.dim != 2:
+            return None, None
+        wb = p.n[0] // p.ras_parts[0] + 2 * p.ras_overlap
+        hb = p.n[1] // p.ras_parts[1] + 2 * p.ras_overlap
+        return wb, wb * hb * p.ras_parts[0] * p.ras_parts[1]
+
+    def summary(res, prec):
+        infos = res["infos"]
+        nits = sum(i["newton_its"] for i in infos)
+        bw, bc = box_geometry(res["params"])
+        return {
+            "iterations": {"newton_per_step": nits / len(infos),
+                           "gmres_per_newton": sum(i["gmres_its"] for i in infos) / max(1, nits),
+                           "dt_first": infos[0]["dt"], "dt_last": infos[-1]["dt"], "t_end": infos[-1]["t"]},
+            "roofline": roofline(res["stats"], prec, hbm_peak(), probe_fp64, bc, bw, res["warm_stats"]),
+            "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
+                            "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
+                        for k, v in res["stats"].items() if v[0] > 0},
+            "kernels_timed": "timed region: events around %s launches only; last warm-up step, every class: %s" % (
+                res["dominant"], {k: round(v[1], 3) for k, v in res["warm_stats"].items() if v[0] > 0}),
+        }
+
+    sampler = ClockSampler(smi_index())
+    sampler.start()
+    probe_fp64, probe_ms = acac_peak_probe(0, 4000)
+    main = timed_form(w)
+    twin_name = None if args.no_twin else twin_of(w.name)
+    twin = timed_form(WORKLOADS[twin_name]) if twin_name else None
+    clocks = sampler.stop()
+    e2e = None if args.no_e2e else e2e_form(w)
+    twin_e2e = None if (args.no_e2e or twin is None) else e2e_form(WORKLOADS[twin_name])
 
     if rank != 0:
         return None
-    hbm, src = peaks()
-    steps_per_s = job_rate(world, B, args.steps, ms * 1e-3)
+    prec = w.params.precision
+    steps_per_s = job_rate(world, B, args.steps, main["ms"] * 1e-3)
+    launches = int(sum(v[0] for v in main["stats"].values()))
+    p = w.params
+    h = p.L[0] / p.n[0]
+    sm = summary(main, prec)
     out = {
         "metric": "NKS time steps/s (one accepted implicit time step per step)" if B == 1 else
                   "ensemble member time steps/s (every member takes one accepted implicit step per step)",
@@ -293,94 +438,108 @@ def run_mine(args, rank, world):
         "n_gpus": world,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": ms / args.steps,
+        "ms_per_step": main["ms"] / args.steps,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f64" if prec == PREC_FP64 else "f64 residual/update + f32 krylov/jacobian/ilu",
         "data": "synthetic (seeded uniform perturbation of a constant state)",
-        "config": {"workload": w.name, "grid": list(p.shape[::-1]), "bc": "periodic" if p.bc == 0 else "neumann",
+        "config": {"workload": w.name, "grid": list(p.shape[::-1]),
+                   "domain": [[0.0, float(x)] for x in p.L[:p.dim]], "h": h,
+                   "bc": "periodic" if p.bc == 0 else "neumann",
                    "precision": "fp64" if prec == PREC_FP64 else "mixed",
-                   "unknowns": 2 * N * B, "members": B, "ras": "%dx%d overlap %d ILU(0) left-RAS" % (p.ras_parts[0], p.ras_parts[1],
-                                                                                 p.ras_overlap),
+                   "unknowns": 2 * N * B, "members": B,
+                   "ras": "%s overlap %d ILU(0) left-RAS" % ("x".join(str(x) for x in p.ras_parts[:p.dim]),
+                                                           p.ras_overlap),
+                   "newton_rtol": p.newton_rtol, "gmres_rtol": p.gmres_rtol,
                    "dt_mode": "adaptive" if p.dt_mode == 1 else "fixed",
                    "l2": "inputs larger than L2 (no flush)", "parallelism": "replicas" if world > 1 else "1 GPU"},
         "unknowns_steps_per_s": steps_per_s * 2 * N,   # per member for an ensemble
-        "iterations": {"newton_per_step": sum(i["newton_its"] for i in infos) / len(infos),
-                       "gmres_per_newton": sum(i["gmres_its"] for i in infos) / max(1, sum(i["newton_its"] for i in infos)),
-                       "dt_first": infos[0]["dt"], "dt_last": infos[-1]["dt"], "t_end": infos[-1]["t"]},
+        "iterations": sm["iterations"],
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
-        "roofline": roofline(stats, prec, hbm, src, w.name, warm_stats),
-        "kernels": {k: {"launches": v[0], "ms": round(v[1], 4), "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
-                    for k, v in stats.items() if v[0] > 0},
-        "kernels_timed": "timed region: events around %s launches only; last warm-up step, every class: %s" % (
-            dominant, {k: round(v[1], 3) for k, v in warm_stats.items() if v[0] > 0}),
+        "roofline": sm["roofline"],
+        "fp64_probe": {"tflops": probe_fp64, "ms": probe_ms,
+                       "derived_tflops_at_2070mhz": FP64_DERIVED_TFLOPS},
+        "kernels": sm["kernels"],
+        "kernels_timed": sm["kernels_timed"],
     }
+    if twin is not None:
+        tp = twin["params"].precision
+        tsm = summary(twin, tp)
+        tval = job_rate(world, B, args.steps, twin["ms"] * 1e-3)
+        xf = np.concatenate([main["u"], main["v"]])
+        xt = np.concatenate([twin["u"], twin["v"]])
+        key = "mixed" if tp == PREC_MIXED else "fp64"
+        out[key] = {
+            "workload": twin_name, "value": tval, "unit": out["unit"], "ms_per_step": twin["ms"] / args.steps,
+            "ratio_vs_fp64": (tval / steps_per_s) if tp == PREC_MIXED else (steps_per_s / tval),
+            "rel_l2_vs_fp64_fields": float(np.linalg.norm(xt - xf) / np.linalg.norm(xf)),
+            "fields_compared": "after %d warm-up + %d timed steps from the same initial state" % (args.warmup,
+                                                                                               args.steps),
+            "e2e": twin_e2e,
+            "gpu_launches": int(sum(v[0] for v in twin["stats"].values())),
+            "iterations": tsm["iterations"], "roofline": tsm["roofline"], "kernels": tsm["kernels"],
+            "kernels_timed": tsm["kernels_timed"],
+        }
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
-        cb = cpu_baseline(w.name, prec, 1)
-        if "seconds" in cb:
-            out["cpu_baseline"] = {"value": cb["steps"] / cb["seconds"], "unit": "steps/s", "cores": 1,
-                                   "kind": "oracle",
-                                   "sample": "first time step of the same workload, single-threaded NumPy/SciPy + C ILU(0) "
-                                             "oracle, %.1f s" % cb["seconds"]}
-        else:
-            out["cpu_baseline"] = {"value": None, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                                   "sample": "failed: " + cb.get("error", "")[-200:]}
+        try:
+            out["cpu_baseline"] = cpu_baseline(w)
+        except Exception as e:                                   # reported, not fatal
+            out["cpu_baseline"] = {"value": None, "unit": "steps/s", "cores": 0, "kind": "oracle",
+                                   "sample": "failed: %s" % str(e)[-200:]}
     return out
 
 
 def run_reference(args, rank, world):
-    """The oracle on the host cores, on the same workload: each bench step is one
-    oracle time step; W warm-up steps are run and not timed."""
+    """The oracle on the host cores, on the same workload: each bench step is one round of
+    the bounded sample (one oracle process per host core, one piece each); the rate is the
+    mean over the timed rounds.  At most 1 warm-up and 3 timed rounds are run."""
     if rank != 0:
         return None
     w = WORKLOADS[args.workload]
-    # Bounded sample: one oracle time step of this workload takes about a minute on
-    # one host core, so at most 1 warm-up and 2 timed steps are run.
-    warm, steps = min(args.warmup, 1), min(args.steps, 2)
-    code = (
-        "import sys, time, json; sys.path.insert(0, %r)\n"
-        "from workloads import WORKLOADS\n"
-        "from oracle import acac_oracle as O\n"
-        "w = WORKLOADS[%r]\n"
-        "one = hasattr(w, 'member_params')  # an ensemble: time member 0\n"
-        "p = (w.member_params(0) if one else w.params).replace(precision=0)\n"
-        "u, v = w.member_fields(0) if one else w.fields()\n"
-        "st = O.Stepper(p)\n"
-        "for k in range(%d):\n"
-        "    X, info = st.step(u, v); u, v = X\n"
-        "t = time.perf_counter()\n"
-        "for k in range(%d):\n"
-        "    X, info = st.step(u, v); u, v = X\n"
-        "print(json.dumps({'seconds': time.perf_counter() - t}))\n"
-    ) % (ROOT, w.name, warm, steps)
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    res = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
-    if res.returncode != 0:
-        return {"impl": "reference", "unavailable": "oracle run failed: " + res.stderr[-200:].replace("\n", " ")}
-    sec = json.loads(res.stdout.strip().splitlines()[-1])["seconds"]
+    warm, steps = min(args.warmup, 1), min(args.steps, 3)
+    ncpu = os.cpu_count() or 1
+    p = piece_params(w)
+    tiles = max(1, w.params.ncells // p.ncells)
+    procs = min(ncpu, tiles)
+    try:
+        sm = OracleSample(w, procs)
+        try:
+            for _ in range(warm):
+                sm.round()
+            rounds = [sm.round() for _ in range(steps)]
+        finally:
+            sm.close()
+    except Exception as e:
+        return {"impl": "reference", "unavailable": "oracle run failed: " + str(e)[-200:].replace("\n", " ")}
+    sec = sum(1.0 / r[0] for r in rounds)          # workload-step equivalents take 1/rate each
     val = steps / sec
+    sample = ("FP64 oracle on %d concurrent %dx%d periodic pieces of the workload (same h, coefficients, tolerances "
+              "and Schwarz box geometry), one step each at dt = dt_min per round, scaled by piece/workload cells; "
+              "%d timed rounds after %d warm-up (bounded: --steps/--warmup capped at 3/1); nproc = %d" % (
+                  procs, p.n[0], p.n[1], steps, warm, ncpu))
     return {"impl": "reference", "metric": "NKS time steps/s (one accepted implicit time step per step)",
             "value": val, "unit": "steps/s", "n_gpus": world, "steps": steps, "warmup": warm,
             "ms_per_step": sec * 1e3 / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded uniform perturbation of a constant state)",
             "config": {"workload": w.name, "grid": list(w.params.shape[::-1])},
-            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                             "sample": "%d oracle time steps after %d warm-up step(s) of the same workload "
-                                       "(bounded: --steps/--warmup capped at 2/1), single-threaded" % (steps, warm)},
+            "cpu_baseline": {"value": val, "unit": "steps/s", "cores": procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": val, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
 def main():
+    if len(sys.argv) == 3 and sys.argv[1] == "--oracle-worker":
+        oracle_worker(sys.argv[2])
+        return
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
-    ap.add_argument("--workload", default=C2.name, choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default=None, choices=["fp64", "mixed"])
+    ap.add_argument("--workload", default=C3_FP64.name, choices=sorted(WORKLOADS))
+    ap.add_argument("--no-twin", action="store_true", help="skip the other precision form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()

@@ -311,9 +311,14 @@ int acac_adjoint(acac_handle *h, const double *u0, const double *v0, int nsteps,
  *   Working memory: file-scope device arrays of about 6 MB, present on every GPU
  *      that loads the library until the process exits; nothing is allocated or
  *      freed per call.
- *   The first call on a device looks up those arrays' device addresses; make it
- *      before any stream capture.  Calls share the arrays: calls whose work
- *      overlaps on the GPU race.  Synchronises cuda_stream.
+ *   The first call on a device looks up those arrays' device addresses (once per
+ *      device, cached for the life of the process); make that first call before any
+ *      stream capture.  Every call copies ||F||^2 and a flag back to the host and
+ *      synchronises cuda_stream before it returns.  Calls share the arrays: calls
+ *      whose work overlaps on the GPU (other streams, other host threads) race.
+ *      X1, X0 and F must live on the current device.  After cudaDeviceReset the
+ *      cached addresses (and the library's constant tables) are stale: the library
+ *      does not support use across a device reset.
  *   Returns ACAC_OK, ACAC_E_ARG, ACAC_E_DOMAIN (a midpoint outside the
  *      admissible set) or ACAC_E_CUDA. */
 int acac_residual_noalloc(const acac_params *p, const double *X1, const double *X0, double dt,
@@ -375,6 +380,16 @@ const char *acac_kernel_name(int kernel);
  * ACAC_E_NOMEM on a runtime failure.  Enqueued on `stream` (NULL: the default stream);
  * synchronises it. */
 int acac_wait_selftest(void *stream, int mode);
+
+/* Measured fused multiply-add rate of the device (instrumentation: the arithmetic peak that
+ * the FP64 kernels' rooflines are taken against).  A full-occupancy grid whose threads run
+ * eight independent multiply-add chains of `iters` steps each, in double (kind 0) or float
+ * (kind 1), timed with CUDA events after one warm-up launch.  *tflops receives 2 x chains x
+ * iters x threads / time in TFLOP/s, *ms the timed launch's duration (either may be NULL).
+ * Allocates and frees one small output buffer; enqueued on cuda_stream (NULL: the default
+ * stream), which it synchronises.  ACAC_E_ARG for another kind or iters < 1.  No
+ * counterpart in the paper. */
+int acac_peak_probe(int kind, int iters, double *tflops, double *ms, void *cuda_stream);
 
 /* Block pattern of a subdomain factorization with fill (Sec. 4.2, Table 2), host only (no
  * GPU, no handle): the box of W x H (x D) cells in natural order (x fastest), the radius-2

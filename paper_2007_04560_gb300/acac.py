@@ -85,6 +85,7 @@ SIGNATURES = {
     "acac_nks_solve": (ctypes.c_int, [_P, _P, _D, _P, ctypes.POINTER(acac_step_info)]),
     "acac_residual_noalloc": (ctypes.c_int, [ctypes.POINTER(acac_params), _P, _P, _D, _P, _PD, _P]),
     "acac_log": (ctypes.c_int, [_P, _P, ctypes.c_longlong, _P]),
+    "acac_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _PD, _PD, _P]),
     "acac_profile": (ctypes.c_int, [_P, ctypes.c_int]),
     "acac_profile_mask": (ctypes.c_int, [_P, ctypes.c_uint]),
     "acac_wait_selftest": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -184,12 +185,17 @@ def acac_status_string(status: int) -> str:
 
 
 def acac_residual_noalloc(p, X1, X0, dt, F, stream=None, check=True):
-    """F(X1) without a handle and without device allocation (grids up to 512x512).
-    Returns (status, ||F||)."""
+    """F(X1) without a handle and without device allocation (grids up to 512x512 cells).
+    X1, X0 and F must be on the current CUDA device.  Returns (status, ||F||)."""
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
     n = 2 * int(p.n[0]) * int(p.n[1]) * (int(p.n[2]) if p.dim == 3 else 1)
+    cur = torch.cuda.current_device()
+    for name, t in (("X1", X1), ("X0", X0), ("F", F)):
+        if isinstance(t, torch.Tensor) and t.is_cuda and t.device.index != cur:
+            raise ValueError("%s is on cuda:%d; acac_residual_noalloc runs on the current device cuda:%d"
+                             % (name, t.device.index, cur))
     cp = to_c_params(p)
     fn = ctypes.c_double()
     st = _lib().acac_residual_noalloc(ctypes.byref(cp), _dev(X1, torch.float64, n, "X1"),
@@ -207,6 +213,18 @@ def acac_log(x, y, stream=None):
         stream = torch.cuda.current_stream()
     _check(_lib().acac_log(_dev(x, torch.float64, None, "x"), _dev(y, torch.float64, x.numel(), "y"),
                            x.numel(), ctypes.c_void_p(stream.cuda_stream)), "acac_log")
+
+
+def acac_peak_probe(kind, iters, stream=None):
+    """Measured multiply-add rate of the current device: kind 0 double, 1 float.
+    Returns (TFLOP/s, ms of the timed launch)."""
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    tf, ms = ctypes.c_double(), ctypes.c_double()
+    _check(_lib().acac_peak_probe(int(kind), int(iters), ctypes.byref(tf), ctypes.byref(ms),
+                                  ctypes.c_void_p(stream.cuda_stream)), "acac_peak_probe")
+    return tf.value, ms.value
 
 
 def acac_subdomain_pattern(dim, W, H, D, solver):

@@ -278,6 +278,8 @@ struct RasLaunch {
 
 // Checks of acac_create (sizes, coefficients, partition, enumerations).
 int validate_params(const acac_params* p);
+// Grid sizes, spacings and the per-axis stencil weights of a validated parameter set.
+Geom make_geom(const acac_params* p);
 
 // ---------------------------------------------------------------- kernels (launchers)
 template <typename T>

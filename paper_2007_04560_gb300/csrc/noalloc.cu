@@ -12,9 +12,12 @@
 // process exits; the grid is limited to NOALLOC_MAX_CELLS cells.
 //
 // The first call on a device looks up the arrays' device addresses with
-// cudaGetSymbolAddress (host code cannot use the array names as device pointers);
-// make that first call before any stream capture.  All calls share the arrays, so
-// calls whose work overlaps on the GPU (other streams, other host threads) race.
+// cudaGetSymbolAddress (host code cannot use the array names as device pointers) and
+// caches them per device for the life of the process; make that first call before any
+// stream capture.  Every call reads ||F||^2 and a flag back to the host and synchronises
+// its stream.  All calls share the arrays, so calls whose work overlaps on the GPU
+// (other streams, other host threads) race.  A cudaDeviceReset invalidates the cached
+// addresses; the library does not support use across a device reset.
 #include <mutex>
 #include <string.h>
 
@@ -71,20 +74,7 @@ extern "C" int acac_residual_noalloc(const acac_params* p, const double* X1, con
     if (st != ACAC_OK) return st;
     cudaStream_t s = (cudaStream_t)cuda_stream;
 
-    Geom g;
-    memset(&g, 0, sizeof(g));
-    g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)ncell; g.bc = p->bc;
-    g.dim = p->dim;
-    g.nz = p->dim == 3 ? p->n[2] : 1;
-    g.hz = p->dim == 3 ? p->L[2] / p->n[2] : 1.0;
-    g.ihz2 = p->dim == 3 ? 1.0 / (g.hz * g.hz) : 0.0;
-    g.ihz2f = (float)g.ihz2;
-    g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
-    g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
-    g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
-    g.hihx2 = 0.5 * g.ihx2; g.hihy2 = 0.5 * g.ihy2; g.hihz2 = 0.5 * g.ihz2;
-    g.hihx2f = (float)g.hihx2; g.hihy2f = (float)g.hihy2; g.hihz2f = (float)g.hihz2;
-    g.vol = g.hx * g.hy;
+    const Geom g = make_geom(p);
     const Coef k{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
 
     // the flags accumulate with atomicOr: clear them for this call (flags[4] is the

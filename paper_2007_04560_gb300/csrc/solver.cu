@@ -1031,6 +1031,25 @@ int build_subdomains(acac_handle* h) {
 
 }  // namespace
 
+acac::Geom acac::make_geom(const acac_params* p) {
+    Geom g;
+    memset(&g, 0, sizeof(g));
+    g.nx = p->n[0]; g.ny = p->n[1]; g.bc = p->bc;
+    g.dim = p->dim;
+    g.nz = p->dim == 3 ? p->n[2] : 1;
+    g.N = g.nx * g.ny * g.nz;
+    g.hz = p->dim == 3 ? p->L[2] / p->n[2] : 1.0;
+    g.ihz2 = p->dim == 3 ? 1.0 / (g.hz * g.hz) : 0.0;
+    g.ihz2f = (float)g.ihz2;
+    g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
+    g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
+    g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
+    g.hihx2 = 0.5 * g.ihx2; g.hihy2 = 0.5 * g.ihy2; g.hihz2 = 0.5 * g.ihz2;
+    g.hihx2f = (float)g.hihx2; g.hihy2f = (float)g.hihy2; g.hihz2f = (float)g.hihz2;
+    g.vol = g.hx * g.hy * (p->dim == 3 ? g.hz : 1.0);
+    return g;
+}
+
 int acac::validate_params(const acac_params* p) {
     if (!p) return ACAC_E_ARG;
     if (p->dim != 2 && p->dim != 3) return ACAC_E_ARG;
@@ -1327,19 +1346,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     h->mixed = p->precision == ACAC_MIXED;
     h->ksz = h->mixed ? sizeof(float) : sizeof(double);
     h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
-    Geom& g = h->g;
-    g.nx = p->n[0]; g.ny = p->n[1]; g.N = (int)h->N; g.bc = p->bc;
-    g.dim = p->dim;
-    g.nz = p->dim == 3 ? p->n[2] : 1;
-    g.hz = p->dim == 3 ? p->L[2] / p->n[2] : 1.0;
-    g.ihz2 = p->dim == 3 ? 1.0 / (g.hz * g.hz) : 0.0;
-    g.ihz2f = (float)g.ihz2;
-    g.hx = p->L[0] / p->n[0]; g.hy = p->L[1] / p->n[1];
-    g.ihx2 = 1.0 / (g.hx * g.hx); g.ihy2 = 1.0 / (g.hy * g.hy);
-    g.ihx2f = (float)g.ihx2; g.ihy2f = (float)g.ihy2;
-    g.hihx2 = 0.5 * g.ihx2; g.hihy2 = 0.5 * g.ihy2; g.hihz2 = 0.5 * g.ihz2;
-    g.hihx2f = (float)g.hihx2; g.hihy2f = (float)g.hihy2; g.hihz2f = (float)g.hihz2;
-    g.vol = g.hx * g.hy * (p->dim == 3 ? g.hz : 1.0);
+    h->g = make_geom(p);
     h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
     h->eta = p->eta0;
     st = build_subdomains(h);

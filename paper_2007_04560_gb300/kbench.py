@@ -3,6 +3,8 @@
     python -m paper_2007_04560_gb300.kbench [--workload NAME] [--precision fp64|mixed]
                                              [--reps R] [--components a,b,...]
                                              [--ras-window W] [--subdomain-solver ilu0|ilu1|ilu2|lu]
+                                             [--grid NX NY] [--parts PX PY]
+    python -m paper_2007_04560_gb300.kbench --probe      (FP64 / FP32 multiply-add rates)
 
 Each component is one C-ABI entry point applied to seeded synthetic inputs of the
 workload's grid (a state pair near the workload's initial state, a random direction):
@@ -50,7 +52,20 @@ def main(argv=None):
                     help="2D Schwarz apply variant (params.ras_window)")
     ap.add_argument("--subdomain-solver", default=None, choices=["ilu0", "ilu1", "ilu2", "lu"],
                     help="subdomain solve of the Schwarz preconditioner (params.subdomain_solver)")
+    ap.add_argument("--grid", type=int, nargs=2, default=None, metavar=("NX", "NY"),
+                    help="2D grid in place of the workload's (same mesh spacing)")
+    ap.add_argument("--parts", type=int, nargs=2, default=None, metavar=("PX", "PY"),
+                    help="Schwarz boxes per direction in place of the workload's")
+    ap.add_argument("--probe", action="store_true",
+                    help="only measure the FP64 and FP32 multiply-add rates (acac_peak_probe)")
     args = ap.parse_args(argv)
+    if args.probe:
+        build.build()
+        for kind, name, iters in ((0, "fp64", 4000), (1, "fp32", 200000)):
+            for rep in range(3):
+                tf, ms = A.acac_peak_probe(kind, iters)
+                print("probe %s rep %d: %.4f TFLOP/s (%.3f ms)" % (name, rep, tf, ms))
+        return
     build.build()
     w = WORKLOADS[args.workload]
     p = w.params.replace(batch=1)
@@ -60,6 +75,11 @@ def main(argv=None):
         p = p.replace(ras_window=args.ras_window)
     if args.subdomain_solver is not None:
         p = p.replace(subdomain_solver=["ilu0", "ilu1", "ilu2", "lu"].index(args.subdomain_solver))
+    if args.grid is not None:
+        h = p.L[0] / p.n[0]
+        p = p.replace(n=(args.grid[0], args.grid[1], 1), L=(args.grid[0] * h, args.grid[1] * h, 1.0))
+    if args.parts is not None:
+        p = p.replace(ras_parts=(args.parts[0], args.parts[1], 1))
     comps = [c for c in args.components.split(",") if c]
     for c in comps:
         if c not in COMPONENTS:

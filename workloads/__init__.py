@@ -107,6 +107,53 @@ def perturbed_pair(p: Params, seed: int, u_mean: float = 0.5, amp: float = 0.05,
     return (u0 + step_amp * d[0], v0 + step_amp * d[1]), (u0, v0)
 
 
+def near_pure_pair(p: Params, seed: int, frac: float = 0.5, eps_range=(1e-8, 1e-3),
+                   ratio_max: float = 0.7):
+    """Two admissible states (U1, U0) for parity checks near pure phases and at large
+    series ratios (the regime of Lemma 2.2's series where the logarithms and the
+    truncation of the sum matter most).
+
+    Works in the variables p = u + v and q = u - v of Eq. D2-1, each of which must lie
+    in (0, 1), through their midpoints zeta and half changes sigma.  zeta: a background
+    0.45 +- 0.05; in a seeded fraction `frac` of the cells one of zeta_p, zeta_q (or
+    both) is put at eps or 1 - eps with log10(eps) uniform over eps_range, so that
+    u +- v lies within about 1e-8..1e-3 of 0 or 1 (and v near +-1/2 where p and q sit at
+    opposite ends).  sigma = r min(zeta, 1 - zeta) with r uniform over (-ratio_max,
+    ratio_max), so that max(|sigma/zeta|, |sigma/(1 - zeta)|) = |r|.  The end states
+    are zeta -+ sigma.  Returns ((u1, v1), (u0, v0)) in the shape of one field."""
+    rng = np.random.default_rng(seed)
+    shape = p.shape
+    zeta = 0.45 + 0.05 * rng.uniform(-1.0, 1.0, size=(2,) + shape)
+    pick = rng.uniform(0.0, 1.0, size=shape) < frac
+    which = rng.integers(0, 3, size=shape)                  # 0: p, 1: q, 2: both
+    lo, hi = np.log10(eps_range[0]), np.log10(eps_range[1])
+    eps = 10.0 ** rng.uniform(lo, hi, size=(2,) + shape)
+    side = rng.integers(0, 2, size=(2,) + shape)              # 0: near 0, 1: near 1
+    for a in range(2):
+        sel = pick & ((which == a) | (which == 2))
+        zeta[a] = np.where(sel, np.where(side[a] == 0, eps[a], 1.0 - eps[a]), zeta[a])
+    r = rng.uniform(-ratio_max, ratio_max, size=(2,) + shape)
+    sigma = r * np.minimum(zeta, 1.0 - zeta)
+    pq0, pq1 = zeta - sigma, zeta + sigma
+    u0, v0 = 0.5 * (pq0[0] + pq0[1]), 0.5 * (pq0[0] - pq0[1])
+    u1, v1 = 0.5 * (pq1[0] + pq1[1]), 0.5 * (pq1[0] - pq1[1])
+    return ((np.ascontiguousarray(u1), np.ascontiguousarray(v1)),
+            (np.ascontiguousarray(u0), np.ascontiguousarray(v0)))
+
+
+def near_pure_state(p: Params, seed: int, eps_p: float, eps_q: float, spread: float = 0.5,
+                    flip: bool = False):
+    """A start state close to the pure phase p = u + v -> 0, q = u - v -> 1 (so u near
+    1/2 and v near -1/2): p = eps_p exp(spread U(-1,1)), 1 - q = eps_q exp(spread U(-1,1)),
+    drawn p then q from PCG64(seed).  flip = True exchanges the roles (p near 1, q near 0,
+    v near +1/2).  Returns (u, v) in the shape of one field."""
+    rng = np.random.default_rng(seed)
+    a = eps_p * np.exp(spread * rng.uniform(-1.0, 1.0, size=p.shape))
+    b = 1.0 - eps_q * np.exp(spread * rng.uniform(-1.0, 1.0, size=p.shape))
+    pp, qq = (1.0 - a, 1.0 - b) if flip else (a, b)
+    return np.ascontiguousarray(0.5 * (pp + qq)), np.ascontiguousarray(0.5 * (pp - qq))
+
+
 def random_vector(p: Params, seed: int):
     """A seeded direction (wu, wv) with entries U(-1,1)."""
     rng = np.random.default_rng(seed)
