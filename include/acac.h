@@ -384,8 +384,10 @@ int acac_wait_selftest(void *stream, int mode);
 /* Measured fused multiply-add rate of the device (instrumentation: the arithmetic peak that
  * the FP64 kernels' rooflines are taken against).  A full-occupancy grid whose threads run
  * eight independent multiply-add chains of `iters` steps each, in double (kind 0) or float
- * (kind 1), timed with CUDA events after one warm-up launch.  *tflops receives 2 x chains x
- * iters x threads / time in TFLOP/s, *ms the timed launch's duration (either may be NULL).
+ * (kind 1), timed with CUDA events after one warm-up launch.  Kinds 2..6: double with only
+ * the first 16, 8, 4, 2 or 1 lanes of every warp working (what a partly filled warp costs
+ * the FP64 pipe).  *tflops receives 2 x chains x iters x working threads / time in TFLOP/s,
+ * *ms the timed launch's duration (either may be NULL).
  * Allocates and frees one small output buffer; enqueued on cuda_stream (NULL: the default
  * stream), which it synchronises.  ACAC_E_ARG for another kind or iters < 1.  No
  * counterpart in the paper. */

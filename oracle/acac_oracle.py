@@ -192,9 +192,11 @@ def mobility(u, v):
     return u * (1.0 - u) * (0.25 - v * v)
 
 
-def Phi(z):
-    """Phi(z) = z ln z + (1-z) ln(1-z), with 0 ln 0 = 0  (Sec. 1, Eq. 2)."""
-    return xlogy(z, z) + xlogy(1.0 - z, 1.0 - z)
+def Phi(z, omz=None):
+    """Phi(z) = z ln z + (1-z) ln(1-z), with 0 ln 0 = 0  (Sec. 1, Eq. 2).  omz: 1 - z when
+    the caller has it more accurately than 1.0 - z (near z -> 1)."""
+    omz = 1.0 - z if omz is None else omz
+    return xlogy(z, z) + xlogy(omz, omz)
 
 
 def admissible(u, v):
@@ -204,28 +206,31 @@ def admissible(u, v):
     return bool(np.all(p > 0.0) and np.all(p < 1.0) and np.all(q > 0.0) and np.all(q < 1.0))
 
 
-def phi_S(zeta, sigma, S):
+def phi_S(zeta, sigma, S, omz=None):
     """Series form of [Phi(zeta+sigma) - Phi(zeta-sigma)] / (2 sigma)  (Lemma 2.2,
     Eq. D2-1), with the sign of the printed combination corrected:
         ln zeta - ln(1-zeta) - sum_{k=1..S} [(sigma/zeta)^{2k} - (sigma/(1-zeta))^{2k}] / ((2k+1) 2k).
+    omz: 1 - zeta as formed by _pq (accurate near zeta -> 1); 1.0 - zeta when not given.
     """
+    omz = 1.0 - zeta if omz is None else omz
     a = sigma / zeta
-    b = sigma / (1.0 - zeta)
-    out = np.log(zeta) - np.log(1.0 - zeta)
+    b = sigma / omz
+    out = np.log(zeta) - np.log(omz)
     for k in range(1, S + 1):
         out = out - (a ** (2 * k) - b ** (2 * k)) / ((2 * k + 1) * (2 * k))
     return out
 
 
-def dphi_S(zeta, sigma, S):
-    """(d phi^S / d zeta, d phi^S / d sigma), differentiated term by term."""
+def dphi_S(zeta, sigma, S, omz=None):
+    """(d phi^S / d zeta, d phi^S / d sigma), differentiated term by term (omz as in phi_S)."""
+    omz = 1.0 - zeta if omz is None else omz
     a = sigma / zeta
-    b = sigma / (1.0 - zeta)
-    dz = 1.0 / zeta + 1.0 / (1.0 - zeta)
+    b = sigma / omz
+    dz = 1.0 / zeta + 1.0 / omz
     ds = np.zeros_like(zeta * sigma)
     for k in range(1, S + 1):
-        dz = dz + (a ** (2 * k) / zeta + b ** (2 * k) / (1.0 - zeta)) / (2 * k + 1)
-        ds = ds - (a ** (2 * k - 1) / zeta - b ** (2 * k - 1) / (1.0 - zeta)) / (2 * k + 1)
+        dz = dz + (a ** (2 * k) / zeta + b ** (2 * k) / omz) / (2 * k + 1)
+        ds = ds - (a ** (2 * k - 1) / zeta - b ** (2 * k - 1) / omz) / (2 * k + 1)
     return dz, ds
 
 
@@ -235,9 +240,34 @@ def exact_quotient(z1, z0):
 
 
 def _pq(u1, v1, u0, v0):
-    """zeta, sigma of p = u+v and q = u-v (Sec. 2, after Eq. D2-1)."""
+    """zeta, sigma of p = u+v and q = u-v (Sec. 2, after Eq. D2-1), and 1 - zeta of each:
+    (zeta_p, sigma_p, zeta_q, sigma_q, 1 - zeta_p, 1 - zeta_q).
+
+    zeta comes from the end values p1, p0 (each sum of u and v rounds relative to its own
+    value); 1 - zeta from the end values 1 - p and 1 - q formed by one_minus_pq, not from
+    1.0 - zeta after zeta has been rounded; sigma from the differences of whichever end
+    values lie nearer zero (p1 - p0 where zeta < 1/2, (1 - p0) - (1 - p1) above).  Near a pure
+    phase (zeta or 1 - zeta -> 0 at the edge of the admissible set) each of them then
+    keeps its relative accuracy; 1.0 - zeta would carry an absolute error of ~1e-16, a
+    relative error of ~1e-8 at 1 - zeta = 1e-8, and so would the logarithms."""
     p1, p0, q1, q0 = u1 + v1, u0 + v0, u1 - v1, u0 - v0
-    return (p1 + p0) / 2, (p1 - p0) / 2, (q1 + q0) / 2, (q1 - q0) / 2
+    mp1, mq1 = one_minus_pq(u1, v1)
+    mp0, mq0 = one_minus_pq(u0, v0)
+    zp, zq = (p1 + p0) / 2, (q1 + q0) / 2
+    # sigma from the end values nearer zero: p1 - p0 below zeta = 1/2, (1 - p0) - (1 - p1) above
+    sp_ = np.where(zp < 0.5, p1 - p0, mp0 - mp1) / 2
+    sq = np.where(zq < 0.5, q1 - q0, mq0 - mq1) / 2
+    return zp, sp_, zq, sq, (mp1 + mp0) / 2, (mq1 + mq0) / 2
+
+
+def one_minus_pq(u, v):
+    """1 - (u + v) and 1 - (u - v), each correctly rounded from the double inputs: 1 - u is
+    split into its rounded value s and the rounding error e (s + e = 1 - u exactly, the
+    two-sum of 1 and -u), and s -+ v is exact wherever the result is small (s and v then
+    lie within a factor 2 of each other), so that only the final addition of e rounds."""
+    s = 1.0 - u
+    e = -u - (s - 1.0)
+    return (s - v) + e, (s + v) + e
 
 
 def G_tilde(p, g, u1, v1, u0, v0, exact=False):
@@ -248,13 +278,13 @@ def G_tilde(p, g, u1, v1, u0, v0, exact=False):
     G1u = -0.5 * p.alpha * (u1 + u0 - 1.0)
     G1v = -0.5 * p.beta * (v1 + v0)
     # G2 from e2 = theta (Phi(u+v) + Phi(u-v))
-    zp, sp_, zq, sq = _pq(u1, v1, u0, v0)
+    zp, sp_, zq, sq, omp, omq = _pq(u1, v1, u0, v0)
     if exact:
         phi = exact_quotient(u1 + v1, u0 + v0)
         psi = exact_quotient(u1 - v1, u0 - v0)
     else:
-        phi = phi_S(zp, sp_, p.taylor_S)
-        psi = phi_S(zq, sq, p.taylor_S)
+        phi = phi_S(zp, sp_, p.taylor_S, omp)
+        psi = phi_S(zq, sq, p.taylor_S, omq)
     G2u = p.theta * (phi + psi)
     G2v = p.theta * (phi - psi)
     # G3 from e3 = gamma/2 (|grad u|^2 + |grad v|^2)
@@ -306,7 +336,8 @@ def energy_density(p, u, v):
     """Local discrete energy [e~]_ij of Eq. relations: e1 + e2 + gamma/2 sum_d
     ((D^+ phi)^2 + (D^- phi)^2)/2 for phi = u, v."""
     e = 0.5 * p.alpha * u * (1.0 - u) - 0.5 * p.beta * v * v
-    e = e + p.theta * (Phi(u + v) + Phi(u - v))
+    mp, mq = one_minus_pq(u, v)
+    e = e + p.theta * (Phi(u + v, mp) + Phi(u - v, mq))
     for phi in (u, v):
         for d in range(p.dim):
             dp, dm = _dplus_dminus(phi, p, d)
@@ -360,9 +391,9 @@ def linearization(p, X1, X0, g=None):
     cu = 0.5 * (1.0 - 2.0 * ub) * (0.25 - vb * vb)     # d c(ub, vb) / d u1
     cv = 0.5 * ub * (1.0 - ub) * (-2.0 * vb)            # d c(ub, vb) / d v1
     Gu, Gv = G_tilde(p, g, u1, v1, u0, v0)
-    zp, sp_, zq, sq = _pq(u1, v1, u0, v0)
-    dzp, dsp = dphi_S(zp, sp_, p.taylor_S)
-    dzq, dsq = dphi_S(zq, sq, p.taylor_S)
+    zp, sp_, zq, sq, omp, omq = _pq(u1, v1, u0, v0)
+    dzp, dsp = dphi_S(zp, sp_, p.taylor_S, omp)
+    dzq, dsq = dphi_S(zq, sq, p.taylor_S, omq)
     A = p.theta * 0.5 * (dzp + dsp)     # theta d phi / d p1  (zeta, sigma both move by 1/2)
     B = p.theta * 0.5 * (dzq + dsq)     # theta d psi / d q1
     return dict(c=c, cu=cu, cv=cv, Gu=Gu, Gv=Gv, A=A, B=B)

@@ -57,9 +57,9 @@ def jacobians(p, X1, X0, dt, g=None):
     cu = (0.5 * (1.0 - 2.0 * ub) * (0.25 - vb * vb)).ravel()     # dc/du1 = dc/du0
     cv = (0.5 * ub * (1.0 - ub) * (-2.0 * vb)).ravel()           # dc/dv1 = dc/dv0
     Gu, Gv = (a.ravel() for a in O.G_tilde(p, g, u1, v1, u0, v0))
-    zp, sp_, zq, sq = O._pq(u1, v1, u0, v0)
-    dzp, dsp = O.dphi_S(zp, sp_, p.taylor_S)
-    dzq, dsq = O.dphi_S(zq, sq, p.taylor_S)
+    zp, sp_, zq, sq, omp, omq = O._pq(u1, v1, u0, v0)
+    dzp, dsp = O.dphi_S(zp, sp_, p.taylor_S, omp)
+    dzq, dsq = O.dphi_S(zq, sq, p.taylor_S, omq)
     out = []
     for sgn, tsign in ((1.0, 1.0), (-1.0, -1.0)):      # X1, then X0
         A = (p.theta * 0.5 * (dzp + sgn * dsp)).ravel()   # theta d phi / d p
@@ -93,9 +93,9 @@ def dF_dparams(p, X1, X0, dt, g=None):
     u1, v1 = X1
     u0, v0 = X0
     c = O.mobility_state(u1, v1, u0, v0)
-    zp, sp_, zq, sq = O._pq(u1, v1, u0, v0)
-    phi = O.phi_S(zp, sp_, p.taylor_S)
-    psi = O.phi_S(zq, sq, p.taylor_S)
+    zp, sp_, zq, sq, omp, omq = O._pq(u1, v1, u0, v0)
+    phi = O.phi_S(zp, sp_, p.taylor_S, omp)
+    psi = O.phi_S(zq, sq, p.taylor_S, omq)
     zero = np.zeros(p.shape)
     dG = {
         "alpha": (-0.5 * (u1 + u0 - 1.0), zero),
@@ -134,8 +134,9 @@ def loss_grad(p, X, target, w_energy=1.0, w_misfit=1.0):
     ut, vt = target
     vol = g.cell_volume
     pp, qq = u + v, u - v
-    lp = np.log(pp) - np.log(1.0 - pp)
-    lq = np.log(qq) - np.log(1.0 - qq)
+    mp, mq = O.one_minus_pq(u, v)                  # 1 - p, 1 - q (accurate near p, q -> 1)
+    lp = np.log(pp) - np.log(mp)
+    lq = np.log(qq) - np.log(mq)
     dEu = 0.5 * p.alpha * (1.0 - 2.0 * u) + p.theta * (lp + lq) - p.gamma * g.lap(u)
     dEv = -p.beta * v + p.theta * (lp - lq) - p.gamma * g.lap(v)
     du = vol * (w_energy * dEu + w_misfit * (u - ut))
@@ -148,7 +149,7 @@ def loss_grad(p, X, target, w_energy=1.0, w_misfit=1.0):
     dp_ = {
         "alpha": w_energy * vol * float(np.sum(0.5 * u * (1.0 - u))),
         "beta": w_energy * vol * float(np.sum(-0.5 * v * v)),
-        "theta": w_energy * vol * float(np.sum(O.Phi(pp) + O.Phi(qq))),
+        "theta": w_energy * vol * float(np.sum(O.Phi(pp, mp) + O.Phi(qq, mq))),
         "gamma": w_energy * vol * float(np.sum(grad_terms)),
     }
     return np.concatenate([du.ravel(), dv.ravel()]), dp_

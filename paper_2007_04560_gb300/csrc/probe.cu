@@ -16,8 +16,13 @@ constexpr int PROBE_THREADS = 256;
 constexpr int PROBE_CHAINS = 8;
 
 template <typename T>
-__global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(T* __restrict__ out, int iters, T a, T b) {
+__global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(T* __restrict__ out, int iters, T a, T b,
+                                                                   int lanes) {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if ((threadIdx.x & 31) >= lanes) {   // lanes left idle: what a partly filled warp costs
+        out[t] = (T)0;
+        return;
+    }
     T x[PROBE_CHAINS];
 #pragma unroll
     for (int c = 0; c < PROBE_CHAINS; ++c) x[c] = (T)(t & 1023) * (T)1e-3 + (T)c;
@@ -32,7 +37,7 @@ __global__ void __launch_bounds__(PROBE_THREADS) fma_probe_kernel(T* __restrict_
 }
 
 template <typename T>
-int run_probe(int iters, double* tflops, double* ms_out, cudaStream_t s) {
+int run_probe(int iters, int lanes, double* tflops, double* ms_out, cudaStream_t s) {
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return ACAC_E_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return ACAC_E_CUDA;
@@ -50,9 +55,9 @@ int run_probe(int iters, double* tflops, double* ms_out, cudaStream_t s) {
     const T a = (T)0.999999, b = (T)1e-7;
     float ms = 0.f;
     if (st == ACAC_OK) {
-        fma_probe_kernel<T><<<blocks, PROBE_THREADS, 0, s>>>(out, iters, a, b);   // warm-up
+        fma_probe_kernel<T><<<blocks, PROBE_THREADS, 0, s>>>(out, iters, a, b, lanes);   // warm-up
         cudaEventRecord(e0, s);
-        fma_probe_kernel<T><<<blocks, PROBE_THREADS, 0, s>>>(out, iters, a, b);
+        fma_probe_kernel<T><<<blocks, PROBE_THREADS, 0, s>>>(out, iters, a, b, lanes);
         cudaEventRecord(e1, s);
         if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess ||
             cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
@@ -62,7 +67,7 @@ int run_probe(int iters, double* tflops, double* ms_out, cudaStream_t s) {
     if (e1) cudaEventDestroy(e1);
     cudaFree(out);
     if (st != ACAC_OK) return st;
-    const double flops = 2.0 * PROBE_CHAINS * (double)iters * (double)threads;
+    const double flops = 2.0 * PROBE_CHAINS * (double)iters * (double)threads * lanes / 32.0;
     if (tflops) *tflops = ms > 0.f ? flops / (ms * 1e-3) / 1e12 : 0.0;
     if (ms_out) *ms_out = ms;
     return ACAC_OK;
@@ -73,7 +78,8 @@ int run_probe(int iters, double* tflops, double* ms_out, cudaStream_t s) {
 extern "C" int acac_peak_probe(int kind, int iters, double* tflops, double* ms, void* cuda_stream) {
     if (iters < 1) return ACAC_E_ARG;
     cudaStream_t s = (cudaStream_t)cuda_stream;
-    if (kind == 0) return run_probe<double>(iters, tflops, ms, s);
-    if (kind == 1) return run_probe<float>(iters, tflops, ms, s);
+    if (kind == 0) return run_probe<double>(iters, 32, tflops, ms, s);
+    if (kind == 1) return run_probe<float>(iters, 32, tflops, ms, s);
+    if (kind >= 2 && kind <= 6) return run_probe<double>(iters, 32 >> (kind - 1), tflops, ms, s);
     return ACAC_E_ARG;
 }

@@ -157,12 +157,45 @@ __device__ __forceinline__ double phi_series(const SeriesArgs& s, int K) {
     return table_log(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
 }
 
+// 1 - (u + v) and 1 - (u - v), each correctly rounded from the doubles u, v: 1 - u is split
+// into its rounded value s and the rounding error e (s + e = 1 - u exactly, the two-sum of
+// 1 and -u), and s -+ v is exact wherever the result is small (s and v then lie within a
+// factor 2 of each other), so only the final addition of e rounds.
+__device__ __forceinline__ void one_minus_pq(double u, double v, double& mp, double& mq) {
+    const double s = 1.0 - u;
+    const double e = -u - (s - 1.0);
+    mp = (s - v) + e;
+    mq = (s + v) + e;
+}
+
+// Twice the midpoints zeta, 1 - zeta and half-increments sigma of p = u + v and q = u - v
+// (Eq. D2-1), formed from the end states so that each keeps its relative accuracy near a
+// pure phase: zeta from p1 + p0 (each sum of u and v rounds relative to its own, possibly
+// tiny, value), 1 - zeta from the end values 1 - p, 1 - q (one_minus_pq), sigma from the
+// differences of whichever end values lie nearer zero.  Subtracting a rounded zeta from 1, or summing u1 + u0 and v1 + v0 before adding
+// them, leaves an absolute error of ~1e-16 that swamps zeta or 1 - zeta once either falls
+// towards 1e-8.
+struct Midpoint2 {
+    double zp, omp, sp, zq, omq, sq;
+};
+__device__ __forceinline__ Midpoint2 midpoint_pq2(double u1, double v1, double u0, double v0) {
+    const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
+    double mp1, mq1, mp0, mq0;
+    one_minus_pq(u1, v1, mp1, mq1);
+    one_minus_pq(u0, v0, mp0, mq0);
+    const double zp = p1 + p0, zq = q1 + q0;
+    // sigma from the end values nearer zero: p1 - p0 below zeta = 1/2, (1-p0) - (1-p1) above
+    return Midpoint2{zp, mp1 + mp0, zp < 1.0 ? p1 - p0 : mp0 - mp1,
+                     zq, mq1 + mq0, zq < 1.0 ? q1 - q0 : mq0 - mq1};
+}
+
 // series_args for p and q with one division: 1/(zp(1-zp)) and 1/(zq(1-zq)) from the
 // reciprocal of their product (which stays far above the underflow threshold for any
 // state that is not within 1e-140 of a pure phase; such states take two divisions).
-__device__ __forceinline__ void series_args2(double zp, double sp, double zq, double sq, SeriesArgs& ap,
-                                             SeriesArgs& aq) {
-    const double omp = 1.0 - zp, omq = 1.0 - zq;
+// zeta, 1 - zeta and sigma come in separately (see midpoint_pq) and may all carry the
+// same positive factor: the ratios sigma/zeta, sigma/(1-zeta), zeta/(1-zeta) do not see it.
+__device__ __forceinline__ void series_args2(double zp, double omp, double sp, double zq, double omq, double sq,
+                                             SeriesArgs& ap, SeriesArgs& aq) {
     const double Pp = zp * omp, Pq = zq * omq;
     const double PP = Pp * Pq;
     double invp, invq;
@@ -247,7 +280,7 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         int x, y, z;
         decode_cell<DIM>(g, cc, x, y, z);
         const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
-        const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
+        const double su = u1 + u0, sv = v1 + v0;
         // Laplacians of u1 + u0 and v1 + v0 (G3), per axis (S_- + S_+ - 2 S) / h^2; a
         // clamped (Neumann ghost) neighbour is the cell itself and adds nothing.  With PRE
         // the start state's Laplacians come precomputed (fixed over a Newton solve)
@@ -268,16 +301,14 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
             lu += a.L0[cc];
             lv += a.L0[N + cc];
         }
-        // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma);
-        // the increments come from the differences du, dv (exact for nearby states)
-        // halves first (0.5 (a + b) = 0.5 a + 0.5 b exactly): ub, vb also give the mobility
-        const double ub = 0.5 * su, vb = 0.5 * sv, hdu = 0.5 * du, hdv = 0.5 * dv;
-        const double zp = ub + vb, sp = hdu + hdv;
-        const double zq = ub - vb, sq = hdu - hdv;
-        const bool ok = in_unit(zp) && in_unit(zq);
+        // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma),
+        // all three doubled (the series only sees their ratios)
+        const Midpoint2 m2 = midpoint_pq2(u1, v1, u0, v0);
+        const bool ok = m2.zp > 0.0 && m2.omp > 0.0 && m2.zq > 0.0 && m2.omq > 0.0;
         if (live && !ok) flag |= 1;
         SeriesArgs ap, aq;
-        series_args2(ok ? zp : 0.5, sp, ok ? zq : 0.5, sq, ap, aq);
+        series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
+                     aq);
         const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
         double phi = phi_series(ap, K), psi = phi_series(aq, K);
         if (!ok) { phi = 0.0; psi = 0.0; }
@@ -287,6 +318,7 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         if (live) {
             a.G[c] = Gu;
             a.G[N + c] = Gv;
+            const double ub = 0.5 * su, vb = 0.5 * sv;
             a.G[2 * N + c] = ub * (1.0 - ub) * (0.25 - vb * vb);
         }
     }
@@ -417,9 +449,11 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
         decode_cell<DIM>(g, c, x, y, z);
         const double u = U[c], v = V[c];
         const double p = u + v, q = u - v;
+        double mp, mq;                                           // 1 - p, 1 - q
+        one_minus_pq(u, v, mp, mq);
         if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) flag |= 1;
         double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v
-                 + k.theta * (xlogx(p) + xlogx(1.0 - p) + xlogx(q) + xlogx(1.0 - q));
+                 + k.theta * (xlogx(p) + xlogx(mp) + xlogx(q) + xlogx(mq));
         // gradient part gamma/2 * 1/2 * sum over D+ and D- of both fields and all axes: a
         // face's difference is the D+ of one cell and the D- of the next (both zero at a
         // Neumann wall, where the neighbour is the cell itself), so the sum over cells of
@@ -471,15 +505,13 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
         const bool live = c0 < N;
         const int c = live ? c0 : N - 1;
         const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
-        // sums and differences in double (the increments cancel), then precision T:
-        // 2 zeta_p = su + sv, 2 (1 - zeta_p) = 2 - (su + sv), 2 sigma_p = du + dv, and for q
-        // the same with -sv, -dv
-        const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
-        const double zp2 = su + sv, zq2 = su - sv;
+        // zeta, 1 - zeta and sigma of p and q in double (midpoint_pq2: accurate near the pure
+        // phases, where the increments of u and v may cancel), then precision T
+        const Midpoint2 m2 = midpoint_pq2(u1, v1, u0, v0);
+        const double su = u1 + u0, sv = v1 + v0;
         const T half = (T)0.5;
-        const T zp = half * (T)zp2, omp = half * (T)(2.0 - zp2), zq = half * (T)zq2, omq = half * (T)(2.0 - zq2);
-        const T duT = (T)du, dvT = (T)dv;
-        const T sp = half * (duT + dvT), sq = half * (duT - dvT);
+        const T zp = (T)(0.5 * m2.zp), omp = (T)(0.5 * m2.omp), zq = (T)(0.5 * m2.zq), omq = (T)(0.5 * m2.omq);
+        const T sp = (T)(0.5 * m2.sp), sq = (T)(0.5 * m2.sq);
         const T ub = half * (T)su, vb = half * (T)sv;
         const T w = (T)0.25 - vb * vb;
         // ssign = -1: derivative in the start value (phi^S is even in sigma)
@@ -545,13 +577,12 @@ __global__ void __launch_bounds__(256) param_grad_kernel(Geom g, Coef k, const d
             qu -= w * 0.5 * (c0 + cm[n]) * (mu[n] - mu_u);
         }
         const double qv = c0 * mu[N + cc] * irho;
-        const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
-        const double zp = 0.5 * (p1 + p0), sp = 0.5 * (p1 - p0);
-        const double zq = 0.5 * (q1 + q0), sq = 0.5 * (q1 - q0);
-        const bool ok = in_unit(zp) && in_unit(zq);
+        const Midpoint2 m2 = midpoint_pq2(u1, v1, u0, v0);
+        const bool ok = m2.zp > 0.0 && m2.omp > 0.0 && m2.zq > 0.0 && m2.omq > 0.0;
         if (live && !ok) flag |= 1;
         SeriesArgs ap, aq;
-        series_args2(ok ? zp : 0.5, sp, ok ? zq : 0.5, sq, ap, aq);
+        series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
+                     aq);
         const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
         const double phi = phi_series(ap, K), psi = phi_series(aq, K);
         if (live && ok) {
@@ -596,8 +627,10 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(Geom g, Coef k, const do
         decode_cell<DIM>(g, c, x, y, z);
         const double u = X[c], v = X[N + c];
         const double p = u + v, q = u - v;
+        double mp, mq;                                           // 1 - p, 1 - q
+        one_minus_pq(u, v, mp, mq);
         if (!(in_unit(p) && in_unit(q))) flag |= 1;
-        const double lp = table_log(p), lp1 = table_log(1.0 - p), lq = table_log(q), lq1 = table_log(1.0 - q);
+        const double lp = table_log(p), lp1 = table_log(mp), lq = table_log(q), lq1 = table_log(mq);
         double lapu = 0.0, lapv = 0.0, gr = 0.0;
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) {
@@ -612,7 +645,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(Geom g, Coef k, const do
         const double dEv = -k.beta * v + k.theta * ((lp - lp1) - (lq - lq1)) - k.gamma * lapv;
         lam[c] = g.vol * (wE * dEu + wM * eu);
         lam[N + c] = g.vol * (wE * dEv + wM * ev);
-        const double xl = p * lp + (1.0 - p) * lp1 + q * lq + (1.0 - q) * lq1;
+        const double xl = p * lp + mp * lp1 + q * lq + mq * lq1;
         const double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v + k.theta * xl + 0.25 * k.gamma * gr;
         acc[0] += wE * e + 0.5 * wM * (eu * eu + ev * ev);
         acc[1] += wE * 0.5 * u * (1.0 - u);

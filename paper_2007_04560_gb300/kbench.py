@@ -61,7 +61,8 @@ def main(argv=None):
     args = ap.parse_args(argv)
     if args.probe:
         build.build()
-        for kind, name, iters in ((0, "fp64", 4000), (1, "fp32", 200000)):
+        for kind, name, iters in ((0, "fp64", 4000), (1, "fp32", 200000), (2, "fp64 16 lanes", 4000),
+                                  (3, "fp64 8 lanes", 4000), (6, "fp64 1 lane", 4000)):
             for rep in range(3):
                 tf, ms = A.acac_peak_probe(kind, iters)
                 print("probe %s rep %d: %.4f TFLOP/s (%.3f ms)" % (name, rep, tf, ms))

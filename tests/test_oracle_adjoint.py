@@ -88,8 +88,11 @@ def test_loss_gradient_matches_central_differences(bc):
     x = _soa(X)
     rng = np.random.default_rng(4)
     w = rng.standard_normal(x.size)
-    fd = (L(p, x + H * w) - L(p, x - H * w)) / (2 * H)
-    assert fd == pytest.approx(float(dX @ w), rel=1e-7)
+    # fourth-order central difference at h = 1e-4: truncation ~h^4, rounding ~eps |L| / h, both
+    # far below the tolerance (a second-order difference at 1e-6 carries ~1e-6 rounding noise)
+    h = 1e-4
+    fd = (8.0 * (L(p, x + h * w) - L(p, x - h * w)) - (L(p, x + 2 * h * w) - L(p, x - 2 * h * w))) / (12.0 * h)
+    assert fd == pytest.approx(float(dX @ w), rel=1e-8)
     for name in A.PARAMS:
         val = getattr(p, name)
         fd = (L(p.replace(**{name: val + H * val}), x) - L(p.replace(**{name: val - H * val}), x)) / (2 * H * val)

@@ -77,3 +77,69 @@ def test_Phi_closed_forms():
     z = 0.2
     assert O.Phi(np.float64(z)) == pytest.approx(z * math.log(z) + (1 - z) * math.log(1 - z),
                                                 abs=1e-16)
+
+
+def _phi_S_mp(mp, z, om, s, S):
+    """phi^S of Lemma 2.2 in mpmath (z, 1 - z and sigma given exactly)."""
+    a, b = s / z, s / om
+    out = mp.log(z) - mp.log(om)
+    for k in range(1, S + 1):
+        out -= (a ** (2 * k) - b ** (2 * k)) / ((2 * k + 1) * (2 * k))
+    return out
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_series_near_pure_phases_mpmath(seed):
+    """Near the pure phases (u + v or u - v within 1e-12..1e-4 of 0 or 1) the oracle's G2
+    terms phi^S(zeta_p, sigma_p), phi^S(zeta_q, sigma_q) equal a 50-digit evaluation from
+    the exact values of the double inputs within 1e-14 of max(1, |phi|): zeta, 1 - zeta and
+    sigma each keep their relative accuracy (Sec. 2, admissible set; Eq. D2-1)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(seed)
+    n = 40
+    eps = 10.0 ** rng.uniform(-12, -4, size=(2, n))
+    side = rng.integers(0, 2, size=(2, n))
+    zeta = np.where(side == 0, eps, 1.0 - eps)             # zeta of p and q
+    r = rng.uniform(-0.7, 0.7, size=(2, n))
+    sig = r * np.minimum(zeta, 1.0 - zeta)
+    p0, p1 = zeta[0] - sig[0], zeta[0] + sig[0]
+    q0, q1 = zeta[1] - sig[1], zeta[1] + sig[1]
+    u1, v1, u0, v0 = 0.5 * (p1 + q1), 0.5 * (p1 - q1), 0.5 * (p0 + q0), 0.5 * (p0 - q0)
+    zp, sp_, zq, sq, omp, omq = O._pq(u1, v1, u0, v0)
+    phi = O.phi_S(zp, sp_, 10, omp)
+    psi = O.phi_S(zq, sq, 10, omq)
+    for i in range(n):
+        U1, V1, U0, V0 = (mp.mpf(float(x[i])) for x in (u1, v1, u0, v0))
+        for sgn, got in ((1, phi[i]), (-1, psi[i])):
+            a1, a0 = U1 + sgn * V1, U0 + sgn * V0
+            z, s = (a1 + a0) / 2, (a1 - a0) / 2
+            ref = _phi_S_mp(mp, z, 1 - z, s, 10)
+            assert abs(float(got - ref)) <= 1e-14 * max(1.0, abs(float(ref))), (i, sgn, float(got), float(ref))
+
+
+def test_series_near_pure_phases_naive_midpoints_fail():
+    """Counter-test: on the same inputs, zeta and sigma from the rounded sums p1 + p0,
+    p1 - p0 with 1 - zeta = 1.0 - zeta miss phi^S by far more than rounding (the reason
+    _pq forms 1 - zeta and sigma from the end values nearer zero)."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 50
+    rng = np.random.default_rng(0)
+    n = 40
+    eps = 10.0 ** rng.uniform(-12, -4, size=(2, n))
+    side = rng.integers(0, 2, size=(2, n))
+    zeta = np.where(side == 0, eps, 1.0 - eps)
+    r = rng.uniform(-0.7, 0.7, size=(2, n))
+    sig = r * np.minimum(zeta, 1.0 - zeta)
+    p0, p1 = zeta[0] - sig[0], zeta[0] + sig[0]
+    q0, q1 = zeta[1] - sig[1], zeta[1] + sig[1]
+    u1, v1, u0, v0 = 0.5 * (p1 + q1), 0.5 * (p1 - q1), 0.5 * (p0 + q0), 0.5 * (p0 - q0)
+    a1, a0 = u1 + v1, u0 + v0
+    naive = O.phi_S((a1 + a0) / 2, (a1 - a0) / 2, 10)
+    worst = 0.0
+    for i in range(n):
+        A1 = mp.mpf(float(u1[i])) + mp.mpf(float(v1[i]))
+        A0 = mp.mpf(float(u0[i])) + mp.mpf(float(v0[i]))
+        ref = _phi_S_mp(mp, (A1 + A0) / 2, 1 - (A1 + A0) / 2, (A1 - A0) / 2, 10)
+        worst = max(worst, abs(float(naive[i] - ref)) / max(1.0, abs(float(ref))))
+    assert worst > 1e-9
