@@ -274,6 +274,7 @@ struct RasLaunch {
     size_t smem_bytes;   // dynamic shared memory per CTA
     int window;          // 1: windowed apply (last levels in shared memory, forward result in global)
     int win_cells;       // rows per window slot (the tallest box + 4)
+    int stage_vec;       // windowed apply: element offset of the level's right-hand side in a stage
 };
 
 // Checks of acac_create (sizes, coefficients, partition, enumerations).

@@ -516,11 +516,28 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
 // rows on each side).  Every slot position that its level does not cover holds zero --
 // the stale rows a slot's previous level left are cleared when the slot is reused, and
 // the window is cleared between the sweeps -- so neighbour reads need no bounds tests.
-// The forward sweep also writes its result level-major to global scratch (coalesced),
-// where the backward sweep reads it back one level ahead; r is gathered per level, one
-// level ahead, and z written per level.  Same pipeline, barrier and bounded waits as
-// above.
+//
+// The forward sweep also writes its result level-major to global scratch (coalesced).
+// Every stage of the ring carries, next to the level's coefficient records, the level's
+// right-hand side: r gathered from the global vector (forward) or the forward result
+// read back from the scratch (backward).  The producer warp fetches it with cp.async,
+// which completes on the stage's mbarrier together with the bulk copy of the records, so
+// the consumers never wait on a global load.  A backward stage is fetched only after the
+// forward sweep has finished that level (a progress counter in shared memory).  Same
+// barrier and bounded waits as above.
 constexpr int RAS_WIN = 5;
+
+__device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, int bytes, bool zero) {
+    if (bytes == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(zero ? 0 : 8)
+                     : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(zero ? 0 : 4)
+                     : "memory");
+}
+__device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
 
 template <typename T>
 __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubInfo* __restrict__ subs,
@@ -531,6 +548,7 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;
     __shared__ int s_issued, s_consumed;
+    __shared__ volatile int s_done;             // consumer steps completed (forward result in yg)
     const SubInfo sd = subs[blockIdx.x];
     const int N = g.N;
     const int W = sd.W, H = sd.H;
@@ -556,56 +574,76 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
         s_pabort = 0;
         s_issued = 0;
         s_consumed = 0;
+        s_done = 0;
         for (int b = 0; b < nbuf; ++b) {
-            mbar_init(smem_addr(&full[b]), 1);
+            mbar_init(smem_addr(&full[b]), 33);   // the records' expect_tx + one arrival per producer lane
             mbar_init(smem_addr(&empty[b]), 1);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     __syncthreads();
-    auto issue = [&](int k) {
-        const bool fwd = k < nlev;
-        const int l = fwd ? k : nst - 1 - k;
-        const int cnt = lo[l + 1] - lo[l];
-        const T* src = cbase + (long long)lo[l] * NCOEF + (fwd ? 0 : (long long)cnt * CREC);
-        const uint32_t bytes = (uint32_t)(CREC * cnt * sizeof(T));
-        const int b = k % nbuf;
-        const uint32_t bar = smem_addr(&full[b]);
-        mbar_expect_tx(bar, bytes);
-        bulk_g2s(smem_addr(stages + (size_t)b * L.stage_elems), src, bytes, bar);
-    };
-    if (threadIdx.x == ncons) {
-        const int first = nbuf < nst ? nbuf : nst;
-        for (int k = 0; k < first; ++k) issue(k);
-        s_issued = first;
-    }
 
     if (producer) {
-        if (threadIdx.x == ncons) {
-            for (int k = nbuf; k < nst; ++k) {
-                const int b = k % nbuf;
-                if (!mbar_wait_bounded(smem_addr(&empty[b]), (uint32_t)(((k / nbuf) - 1) & 1))) {
-                    s_pabort = 1;
-                    break;
+        const int lane = threadIdx.x & 31;
+        const bool right = ras_type == ACAC_RAS_RIGHT;
+        for (int k = 0; k < nst; ++k) {
+            const int b = k % nbuf;
+            const bool fwd = k < nlev;
+            const int l = fwd ? k : nst - 1 - k;
+            int ok = 1;
+            if (lane == 0) {
+                if (k >= nbuf) ok = mbar_wait_bounded(smem_addr(&empty[b]), (uint32_t)(((k / nbuf) - 1) & 1)) ? 1 : 0;
+                if (ok && !fwd) {
+                    // the forward result of level l must be in the scratch: wait (bounded) for step l
+                    if (s_done <= l) {
+                        const uint64_t t0 = global_ns();
+                        while (s_done <= l) {
+                            if (s_cabort || global_ns() - t0 > 500000000ull) {
+                                ok = 0;
+                                break;
+                            }
+                        }
+                    }
+                    __threadfence_block();
                 }
-                issue(k);
-                s_issued = k + 1;
             }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) s_pabort = 1;
+                break;
+            }
+            __syncwarp();
+            const int cnt = lo[l + 1] - lo[l];
+            T* st = stages + (size_t)b * L.stage_elems;
+            const uint32_t bar = smem_addr(&full[b]);
+            if (lane == 0) {
+                const T* src = cbase + (long long)lo[l] * NCOEF + (fwd ? 0 : (long long)cnt * CREC);
+                const uint32_t bytes = (uint32_t)(CREC * cnt * sizeof(T));
+                mbar_expect_tx(bar, bytes);
+                bulk_g2s(smem_addr(st), src, bytes, bar);
+            }
+            T* sv = st + L.stage_vec;
+            const int jmin = level_jmin(l, W);
+            for (int e = lane; e < 2 * cnt; e += 32) {
+                const int m = e >> 1, rr = e & 1;
+                const T* src;
+                bool zero = false;
+                if (fwd) {
+                    const int j = jmin + m, i = l - 2 * j;
+                    src = r + (size_t)rr * N + box_cell(g, sd, i, j);
+                    if (right && !(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)) zero = true;
+                } else {
+                    src = yg + 2 * (size_t)(lo[l] + m) + rr;
+                }
+                cp_async_zfill(smem_addr(sv + e), src, (int)sizeof(T), zero);
+            }
+            cp_async_arrive_noinc(bar);
+            if (lane == 0) s_issued = k + 1;
         }
     } else {
         const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
         auto jmax_of = [&](int l) { const int t = l >> 1; return t < H - 1 ? t : H - 1; };
-        // this thread's row of the restricted r at cell m of level l (0 if none)
-        auto r_at = [&](int l) -> T {
-            if (l >= nlev || m >= lo[l + 1] - lo[l]) return (T)0;
-            const int j = level_jmin(l, W) + m, i = l - 2 * j;
-            if (ras_type == ACAC_RAS_RIGHT &&
-                !(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1))
-                return (T)0;
-            return r[(size_t)rr * N + box_cell(g, sd, i, j)];
-        };
-        T pre = r_at(0);   // operand prefetched for the next level: r (forward), y (backward)
         int lm = 0;        // l mod RAS_WIN
         int k = 0;
         for (; k < nst; ++k) {
@@ -623,8 +661,10 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
             const int cnt = lo[l + 1] - lo[l];
             const int jmin = level_jmin(l, W);
             const int j = jmin + m, i = l - 2 * j;
-            const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
+            const T* st = stages + (size_t)b * L.stage_elems;
+            const T* rec = st + (size_t)m * CREC;
             const bool act = m < cnt && landed;
+            const T cur = act ? st[L.stage_vec + 2 * m + rr] : (T)0;   // r (forward) or y (backward)
             // slot bases of the levels l -+ d, d = 1..4 (in V2 elements), and the row offset
             int sb[5];
 #pragma unroll
@@ -634,15 +674,12 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 sb[d] = t * hp + 2;
             }
             V2<T>* own = win + lm * hp + 2;
-            const T cur = pre;
             if (fwd) {
-                if (l + 1 < nlev) pre = r_at(l + 1);
                 // clear the rows the slot's previous level (l - 5) covered below this level's
                 if (l >= RAS_WIN && m < 3 && rr == 0) {
                     const int jz = level_jmin(l - RAS_WIN, W) + m;
                     if (jz < jmin) own[jz] = V2<T>{(T)0, (T)0};
                 }
-                T y = (T)0;
                 if (act) {
                     T a0 = cur, a1 = (T)0;
 #pragma unroll
@@ -654,14 +691,12 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                         acc = fma(-c0, nb.x, acc);
                         acc = fma(-c1, nb.y, acc);
                     }
-                    y = a0 + a1;
+                    const T y = a0 + a1;
                     wins[2 * (lm * hp + 2 + j) + rr] = y;
                     yg[2 * (size_t)(lo[l] + m) + rr] = y;
                 }
-                if (l + 1 == nlev) pre = y;   // the first backward level is this one
                 lm = lm + 1 == RAS_WIN ? 0 : lm + 1;
             } else {
-                if (l > 0) pre = m < lo[l] - lo[l - 1] ? yg[2 * (size_t)(lo[l - 1] + m) + rr] : (T)0;
                 // clear the rows the slot's previous level (l + 5) covered above this level's
                 if (l + RAS_WIN < nlev && m < 3 && rr == 0) {
                     const int jz = jmax_of(l) + 1 + m;
@@ -704,7 +739,13 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 if (threadIdx.x == 0) s_cabort = 1;
                 break;
             }
-            if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[b]));
+            if (threadIdx.x == 0) {
+                if (fwd) {
+                    __threadfence_block();   // this level's scratch writes before the count
+                    s_done = k + 1;
+                }
+                mbar_arrive(smem_addr(&empty[b]));
+            }
         }
         if (threadIdx.x == 0) s_consumed = k;
     }

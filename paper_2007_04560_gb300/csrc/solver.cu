@@ -1411,6 +1411,7 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         // stages | box vector.  Prefer a plan with two CTAs per SM.
             auto r128 = [](size_t b) { return (b + 127) / 128 * 128; };
             RasLaunch& L = h->ras_launch;
+            L.stage_vec = 0;
             L.stage_off = (int)(16 * RAS_MAXBUF + r128((size_t)(h->ras_maxlev + 1) * 4));
             L.stage_elems = (CREC * h->ras_maxcnt + 31) / 32 * 32;
             L.threads = 32 * ((2 * h->ras_maxcnt + 31) / 32) + 32;
@@ -1431,6 +1432,10 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             for (auto& sd : h->subs) maxh = std::max(maxh, sd.H);
             L.win_cells = maxh + 4;   // rows per window slot
             if (L.window) {
+                // a windowed stage also carries the level's right-hand side (2 values per cell)
+                L.stage_vec = L.stage_elems;
+                L.stage_elems += (2 * h->ras_maxcnt + 31) / 32 * 32;
+                const size_t stage_bytes = (size_t)L.stage_elems * ks;
                 // aim at three CTAs per SM with at least 4 stages each
                 const size_t win_bytes = r128((size_t)5 * L.win_cells * 2 * ks);
                 const size_t third = 74 * 1024;
