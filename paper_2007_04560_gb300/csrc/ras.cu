@@ -642,85 +642,122 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
             if (lane == 0) s_issued = k + 1;
         }
     } else {
+        // Forward then backward sweep, one level per iteration.  The stage buffer and its
+        // mbarrier parity advance incrementally, and the window slots of the levels l, l -+ 1,
+        // .., l -+ 4 (own, n1..n4, in V2 elements past the two padding rows) rotate by one
+        // per level: the bookkeeping of a level is a handful of integer operations.
         const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
-        auto jmax_of = [&](int l) { const int t = l >> 1; return t < H - 1 ? t : H - 1; };
-        int lm = 0;        // l mod RAS_WIN
+        const int rec_off = m * CREC + 2 * rr;          // this thread's row in a stage record
+        int b = 0;
+        uint32_t ph = 0u;
         int k = 0;
-        for (; k < nst; ++k) {
-            const int b = k % nbuf;
-            const bool fwd = k < nlev;
-            if (k == nlev) {
-                // between the sweeps: clear the window (the backward sweep reads only its own
-                // results and zeros), then start from the last level
-                for (int t = threadIdx.x; t < RAS_WIN * hp; t += ncons) win[t] = V2<T>{(T)0, (T)0};
-                asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
-                lm = (nlev - 1) % RAS_WIN;
+        bool aborted = false;
+        auto next_stage = [&]() {
+            if (++b == nbuf) {
+                b = 0;
+                ph ^= 1u;
             }
-            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
-            const int l = fwd ? k : nst - 1 - k;
-            const int cnt = lo[l + 1] - lo[l];
-            const int jmin = level_jmin(l, W);
-            const int j = jmin + m, i = l - 2 * j;
-            const T* st = stages + (size_t)b * L.stage_elems;
-            const T* rec = st + (size_t)m * CREC;
-            const bool act = m < cnt && landed;
-            const T cur = act ? st[L.stage_vec + 2 * m + rr] : (T)0;   // r (forward) or y (backward)
-            // slot bases of the levels l -+ d, d = 1..4 (in V2 elements), and the row offset
-            int sb[5];
-#pragma unroll
-            for (int d = 1; d <= 4; ++d) {
-                int t = fwd ? lm - d : lm + d;
-                t = t < 0 ? t + RAS_WIN : (t >= RAS_WIN ? t - RAS_WIN : t);
-                sb[d] = t * hp + 2;
+        };
+        // barrier over the consumers that also ORs "a wait gave up"; then release the stage
+        auto finish_level = [&](bool landed, bool fwd_done) -> bool {
+            uint32_t gave_up;
+            asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
+                         " selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
+            if (gave_up) {
+                if (threadIdx.x == 0) s_cabort = 1;
+                return false;
             }
-            V2<T>* own = win + lm * hp + 2;
-            if (fwd) {
+            if (threadIdx.x == 0) {
+                if (fwd_done) {
+                    __threadfence_block();   // this level's scratch writes before the count
+                    s_done = k + 1;
+                }
+                mbar_arrive(smem_addr(&empty[b]));
+            }
+            return true;
+        };
+        {   // forward: levels 0 .. nlev-1; slots of l-1 .. l-4 are 4, 3, 2, 1 at l = 0
+            int own = 2, n1 = 4 * hp + 2, n2 = 3 * hp + 2, n3 = 2 * hp + 2, n4 = hp + 2;
+            for (int l = 0; l < nlev; ++l, ++k) {
+                const bool landed = mbar_wait_bounded(smem_addr(&full[b]), ph);
+                const int cnt = lo[l + 1] - lo[l];
+                const int jmin = level_jmin(l, W);
+                const int j = jmin + m;
+                const T* st = stages + (size_t)b * L.stage_elems;
+                const bool act = m < cnt && landed;
                 // clear the rows the slot's previous level (l - 5) covered below this level's
                 if (l >= RAS_WIN && m < 3 && rr == 0) {
                     const int jz = level_jmin(l - RAS_WIN, W) + m;
-                    if (jz < jmin) own[jz] = V2<T>{(T)0, (T)0};
+                    if (jz < jmin) win[own + jz] = V2<T>{(T)0, (T)0};
                 }
                 if (act) {
-                    T a0 = cur, a1 = (T)0;
+                    const T* rec = st + rec_off;
+                    T a0 = st[L.stage_vec + 2 * m + rr], a1 = (T)0;
+                    const int off[6] = {n4 + j - 2, n3 + j - 1, n2 + j - 1, n1 + j - 1, n2 + j, n1 + j};
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        const int dl = -(lower_dx(q) + 2 * lower_dy(q));   // 1..4 levels back
-                        const V2<T> nb = win[sb[dl] + j + lower_dy(q)];
-                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
+                        const V2<T> nb = win[off[q]];
+                        const V2<T> c = *reinterpret_cast<const V2<T>*>(rec + 4 * q);
                         T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
+                        acc = fma(-c.x, nb.x, acc);
+                        acc = fma(-c.y, nb.y, acc);
                     }
                     const T y = a0 + a1;
-                    wins[2 * (lm * hp + 2 + j) + rr] = y;
+                    wins[2 * (own + j) + rr] = y;
                     yg[2 * (size_t)(lo[l] + m) + rr] = y;
                 }
-                lm = lm + 1 == RAS_WIN ? 0 : lm + 1;
-            } else {
+                if (!finish_level(landed, true)) {
+                    aborted = true;
+                    break;
+                }
+                next_stage();
+                // rotate the slots: level l+1 takes the slot of l-4
+                const int t = n4;
+                n4 = n3; n3 = n2; n2 = n1; n1 = own; own = t;
+            }
+        }
+        if (!aborted) {
+            // between the sweeps: clear the window (the backward sweep reads only its own
+            // results and zeros), then start from the last level, whose slot comes first
+            for (int t = threadIdx.x; t < RAS_WIN * hp; t += ncons) win[t] = V2<T>{(T)0, (T)0};
+            asm volatile("bar.sync 1, %0;" ::"r"(ncons) : "memory");
+            auto jmax_of = [&](int l) { const int t = l >> 1; return t < H - 1 ? t : H - 1; };
+            // slots of l, l+1 .. l+4: 0, 1 .. 4 (any fixed assignment works after the clear)
+            int own = 2, n1 = hp + 2, n2 = 2 * hp + 2, n3 = 3 * hp + 2, n4 = 4 * hp + 2;
+            for (int l = nlev - 1; l >= 0; --l, ++k) {
+                const bool landed = mbar_wait_bounded(smem_addr(&full[b]), ph);
+                const int cnt = lo[l + 1] - lo[l];
+                const int jmin = level_jmin(l, W);
+                const int j = jmin + m, i = l - 2 * j;
+                const T* st = stages + (size_t)b * L.stage_elems;
+                const bool act = m < cnt && landed;
                 // clear the rows the slot's previous level (l + 5) covered above this level's
                 if (l + RAS_WIN < nlev && m < 3 && rr == 0) {
                     const int jz = jmax_of(l) + 1 + m;
-                    if (jz <= jmax_of(l + RAS_WIN)) own[jz] = V2<T>{(T)0, (T)0};
+                    if (jz <= jmax_of(l + RAS_WIN)) win[own + jz] = V2<T>{(T)0, (T)0};
                 }
                 T a0 = (T)0, a1 = (T)0;
+                const T* rec = st + rec_off;
                 if (act) {
-                    a0 = cur;
+                    a0 = st[L.stage_vec + 2 * m + rr];
+                    const int off[6] = {n1 + j, n2 + j, n1 + j + 1, n2 + j + 1, n3 + j + 1, n4 + j + 2};
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
-                        const int dl = upper_dx(q) + 2 * upper_dy(q);      // 1..4 levels ahead
-                        const V2<T> nb = win[sb[dl] + j + upper_dy(q)];
-                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
+                        const V2<T> nb = win[off[q]];
+                        const V2<T> c = *reinterpret_cast<const V2<T>*>(rec + 4 + 4 * q);
                         T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
+                        acc = fma(-c.x, nb.x, acc);
+                        acc = fma(-c.y, nb.y, acc);
                     }
                 }
                 const T s_me = a0 + a1;
                 const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
                 if (act) {
                     const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
-                    const T zc = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
-                    wins[2 * (lm * hp + 2 + j) + rr] = zc;
+                    const V2<T> dinv = *reinterpret_cast<const V2<T>*>(rec);
+                    const T zc = fma(dinv.x, sx, dinv.y * sy);
+                    wins[2 * (own + j) + rr] = zc;
                     const int gc = box_cell(g, sd, i, j);
                     if (ras_type == ACAC_RAS_LEFT) {
                         if (i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)
@@ -729,22 +766,11 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                         atomicAdd(&z[(size_t)rr * N + gc], zc);
                     }
                 }
-                lm = lm == 0 ? RAS_WIN - 1 : lm - 1;
-            }
-            uint32_t gave_up;
-            asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
-                         " selp.u32 %0, 1, 0, p;\n}"
-                         : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
-            if (gave_up) {
-                if (threadIdx.x == 0) s_cabort = 1;
-                break;
-            }
-            if (threadIdx.x == 0) {
-                if (fwd) {
-                    __threadfence_block();   // this level's scratch writes before the count
-                    s_done = k + 1;
-                }
-                mbar_arrive(smem_addr(&empty[b]));
+                if (!finish_level(landed, false)) break;
+                next_stage();
+                // level l-1 takes the slot of l+4
+                const int t = n4;
+                n4 = n3; n3 = n2; n2 = n1; n1 = own; own = t;
             }
         }
         if (threadIdx.x == 0) s_consumed = k;
