@@ -481,7 +481,12 @@ cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, cons
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             const RasLaunch& L, T* gscratch, int* err, cudaStream_t s);
+                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s);
+// 2D windowed apply: r restricted to every box cell (right-RAS: owned cells only), written by
+// record (rec_of) into rg, two values per box cell
+template <typename T>
+cudaError_t launch_ras_gather(const Geom& g, const T* r, const int* rec_of, const unsigned char* own_of,
+                              int ras_type, T* rg, cudaStream_t s);
 
 // Bounded wait for bit (word_bit) of a shared-memory word set by another warp of the block:
 // true once set, false after limit_ns of the global timer (the caller then records an error

@@ -416,7 +416,10 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             }
         }
     } else {
+        // Forward then backward sweep, one level per iteration; the stage buffer and its
+        // mbarrier parity advance incrementally (no per-level division or modulo).
         const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+        const int rec_off = m * CREC + 2 * rr;          // this thread's row in a stage record
         // neighbour offsets in the padded box (cells)
         int offL[6], offU[6];
 #pragma unroll
@@ -424,63 +427,79 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
             offL[q] = lower_dy(q) * PW + lower_dx(q);
             offU[q] = upper_dy(q) * PW + upper_dx(q);
         }
-        int k = 0;
-        for (; k < nst; ++k) {
-            const int b = k % nbuf;
-            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), (uint32_t)((k / nbuf) & 1));
-            const bool fwd = k < nlev;
-            const int l = fwd ? k : nst - 1 - k;
-            const int cnt = lo[l + 1] - lo[l];
-            const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
-            const int pc = (j + 2) * PW + i + 2;
-            const T* rec = stages + (size_t)b * L.stage_elems + (size_t)m * CREC;
-            const bool act = m < cnt && landed;
-            if (fwd) {
-                if (act) {
-                    // row rr: y_c -= sum_lower L_c,o y_{c+o}  (two independent chains)
-                    T a0 = ys[2 * pc + rr], a1 = (T)0;
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = yv[pc + offL[q]];
-                        const T c0 = rec[4 * q + 2 * rr], c1 = rec[4 * q + 2 * rr + 1];
-                        T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
-                    }
-                    ys[2 * pc + rr] = a0 + a1;
-                }
-            } else {
-                // row rr of s = y_c - sum_upper U_c,o y_{c+o}; then y_c = D^-1 s
-                T a0 = (T)0, a1 = (T)0;
-                if (act) {
-                    a0 = ys[2 * pc + rr];
-#pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        const V2<T> nb = yv[pc + offU[q]];
-                        const T c0 = rec[4 + 4 * q + 2 * rr], c1 = rec[4 + 4 * q + 2 * rr + 1];
-                        T& acc = q < 3 ? a0 : a1;
-                        acc = fma(-c0, nb.x, acc);
-                        acc = fma(-c1, nb.y, acc);
-                    }
-                }
-                const T s_me = a0 + a1;
-                const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
-                if (act) {
-                    const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
-                    ys[2 * pc + rr] = fma(rec[2 * rr], sx, rec[2 * rr + 1] * sy);
-                }
-            }
-            // all consumers done with this level and with stage b; the barrier also
-            // ORs "a wait gave up" over the consumers so that all of them agree
+        int k = 0, b = 0;
+        uint32_t ph = 0u;
+        // all consumers done with this level and with stage b; the barrier also ORs "a wait
+        // gave up" over the consumers so that all of them agree
+        auto finish_level = [&](bool landed) -> bool {
             uint32_t gave_up;
             asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n"
                          " selp.u32 %0, 1, 0, p;\n}"
                          : "=r"(gave_up) : "r"((uint32_t)landed), "r"(ncons) : "memory");
             if (gave_up) {
                 if (threadIdx.x == 0) s_cabort = 1;
-                break;
+                return false;
             }
             if (threadIdx.x == 0) mbar_arrive(smem_addr(&empty[b]));
+            if (++b == nbuf) {
+                b = 0;
+                ph ^= 1u;
+            }
+            return true;
+        };
+        bool aborted = false;
+        for (int l = 0; l < nlev; ++l, ++k) {
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), ph);
+            const int cnt = lo[l + 1] - lo[l];
+            const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+            const int pc = (j + 2) * PW + i + 2;
+            const T* rec = stages + (size_t)b * L.stage_elems + rec_off;
+            if (m < cnt && landed) {
+                // row rr: y_c -= sum_lower L_c,o y_{c+o}  (two independent chains)
+                T a0 = ys[2 * pc + rr], a1 = (T)0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const V2<T> nb = yv[pc + offL[q]];
+                    const V2<T> c = *reinterpret_cast<const V2<T>*>(rec + 4 * q);
+                    T& acc = q < 3 ? a0 : a1;
+                    acc = fma(-c.x, nb.x, acc);
+                    acc = fma(-c.y, nb.y, acc);
+                }
+                ys[2 * pc + rr] = a0 + a1;
+            }
+            if (!finish_level(landed)) {
+                aborted = true;
+                break;
+            }
+        }
+        for (int l = nlev - 1; l >= 0 && !aborted; --l, ++k) {
+            const bool landed = mbar_wait_bounded(smem_addr(&full[b]), ph);
+            const int cnt = lo[l + 1] - lo[l];
+            const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+            const int pc = (j + 2) * PW + i + 2;
+            const T* rec = stages + (size_t)b * L.stage_elems + rec_off;
+            const bool act = m < cnt && landed;
+            // row rr of s = y_c - sum_upper U_c,o y_{c+o}; then y_c = D^-1 s
+            T a0 = (T)0, a1 = (T)0;
+            if (act) {
+                a0 = ys[2 * pc + rr];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const V2<T> nb = yv[pc + offU[q]];
+                    const V2<T> c = *reinterpret_cast<const V2<T>*>(rec + 4 + 4 * q);
+                    T& acc = q < 3 ? a0 : a1;
+                    acc = fma(-c.x, nb.x, acc);
+                    acc = fma(-c.y, nb.y, acc);
+                }
+            }
+            const T s_me = a0 + a1;
+            const T s_ot = __shfl_xor_sync(0xffffffffu, s_me, 1);
+            if (act) {
+                const T sx = rr ? s_ot : s_me, sy = rr ? s_me : s_ot;
+                const V2<T> dinv = *reinterpret_cast<const V2<T>*>(rec);
+                ys[2 * pc + rr] = fma(dinv.x, sx, dinv.y * sy);
+            }
+            if (!finish_level(landed)) break;
         }
         if (threadIdx.x == 0) s_consumed = k;
     }
@@ -517,29 +536,37 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
 // the stale rows a slot's previous level left are cleared when the slot is reused, and
 // the window is cleared between the sweeps -- so neighbour reads need no bounds tests.
 //
-// The forward sweep also writes its result level-major to global scratch (coalesced).
-// Every stage of the ring carries, next to the level's coefficient records, the level's
-// right-hand side: r gathered from the global vector (forward) or the forward result
-// read back from the scratch (backward).  The producer warp fetches it with cp.async,
-// which completes on the stage's mbarrier together with the bulk copy of the records, so
-// the consumers never wait on a global load.  A backward stage is fetched only after the
+// In float (PRE) the right-hand side r is gathered beforehand into every box cell's slot in
+// record order (ras_gather_kernel: one coalesced pass over r, restricted to owned cells for
+// right-RAS); in double the producer warp gathers it from r itself, one value per cp.async
+// (the consumers' FP64 work leaves it the time).  The forward sweep writes its result in
+// record order to global scratch.  Every
+// stage of the ring then carries, next to the level's coefficient records, the level's
+// right-hand side -- the gathered r (forward) or the forward result (backward), both
+// contiguous per level -- fetched by the producer warp in 16-byte cp.async chunks that
+// complete on the stage's mbarrier together with the bulk copy of the records, so the
+// consumers never wait on a global load.  A backward stage is fetched only after the
 // forward sweep has finished that level (a progress counter in shared memory).  Same
 // barrier and bounded waits as above.
 constexpr int RAS_WIN = 5;
 
-__device__ __forceinline__ void cp_async_zfill(uint32_t dst, const void* src, int bytes, bool zero) {
-    if (bytes == 8)
+template <typename T>
+__device__ __forceinline__ void cp_async_one(uint32_t dst, const T* src, bool zero) {
+    if (sizeof(T) == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(dst), "l"(src), "r"(zero ? 0 : 8)
                      : "memory");
     else
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(dst), "l"(src), "r"(zero ? 0 : 4)
                      : "memory");
 }
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_arrive_noinc(uint32_t bar) {
     asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
 }
 
-template <typename T>
+template <typename T, bool PRE>
 __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                             const int* __restrict__ lev_off,
                                                             const T* __restrict__ coef, const T* __restrict__ r,
@@ -564,7 +591,8 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
     T* stages = reinterpret_cast<T*>(smem_raw + L.stage_off);
     V2<T>* win = reinterpret_cast<V2<T>*>(smem_raw + L.vec_off);  // [RAS_WIN][hp]
     T* wins = reinterpret_cast<T*>(win);                            // component view
-    T* yg = gscratch + 2 * (size_t)sd.vec_base;                     // level-major forward result
+    T* yg = gscratch;                                               // forward result, by record
+    const long long rbase = sd.coef_base / NCOEF;                   // records before this box
     const T* cbase = coef + sd.coef_base;
 
     for (int l = threadIdx.x; l <= nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
@@ -586,7 +614,6 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
 
     if (producer) {
         const int lane = threadIdx.x & 31;
-        const bool right = ras_type == ACAC_RAS_RIGHT;
         for (int k = 0; k < nst; ++k) {
             const int b = k % nbuf;
             const bool fwd = k < nlev;
@@ -623,20 +650,29 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 mbar_expect_tx(bar, bytes);
                 bulk_g2s(smem_addr(st), src, bytes, bar);
             }
+            // the level's right-hand side (r gathered per box cell, or the forward result), two
+            // values per cell from element 2 (rbase + lo[l]) on, copied in 16-byte chunks from the
+            // chunk boundary below it (the consumers skip the offset)
             T* sv = st + L.stage_vec;
-            const int jmin = level_jmin(l, W);
-            for (int e = lane; e < 2 * cnt; e += 32) {
-                const int m = e >> 1, rr = e & 1;
-                const T* src;
-                bool zero = false;
-                if (fwd) {
+            constexpr int U = 16 / (int)sizeof(T);
+            if (PRE || !fwd) {
+                const T* srcv = fwd ? r : yg;
+                const long long e0 = 2 * (rbase + lo[l]);
+                const long long a = e0 & ~(long long)(U - 1);
+                const int nch = (int)((e0 - a + 2 * cnt + U - 1) / U);
+                for (int c = lane; c < nch; c += 32) cp_async16(smem_addr(sv + c * U), srcv + a + (long long)c * U);
+            } else {
+                // r straight from the global vector, one value per cp.async, at the stage's
+                // chunk offset of the level (the consumers skip it either way)
+                const int voff = (int)((2 * (rbase + lo[l])) & (U - 1));
+                const int jmin = level_jmin(l, W);
+                const bool right = ras_type == ACAC_RAS_RIGHT;
+                for (int e = lane; e < 2 * cnt; e += 32) {
+                    const int m = e >> 1, rr = e & 1;
                     const int j = jmin + m, i = l - 2 * j;
-                    src = r + (size_t)rr * N + box_cell(g, sd, i, j);
-                    if (right && !(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)) zero = true;
-                } else {
-                    src = yg + 2 * (size_t)(lo[l] + m) + rr;
+                    const bool zero = right && !(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1);
+                    cp_async_one(smem_addr(sv + voff + e), r + (size_t)rr * N + box_cell(g, sd, i, j), zero);
                 }
-                cp_async_zfill(smem_addr(sv + e), src, (int)sizeof(T), zero);
             }
             cp_async_arrive_noinc(bar);
             if (lane == 0) s_issued = k + 1;
@@ -693,7 +729,8 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 }
                 if (act) {
                     const T* rec = st + rec_off;
-                    T a0 = st[L.stage_vec + 2 * m + rr], a1 = (T)0;
+                    const int voff = (int)((2 * (rbase + lo[l])) & (16 / (int)sizeof(T) - 1));
+                    T a0 = st[L.stage_vec + voff + 2 * m + rr], a1 = (T)0;
                     const int off[6] = {n4 + j - 2, n3 + j - 1, n2 + j - 1, n1 + j - 1, n2 + j, n1 + j};
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
@@ -705,7 +742,7 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                     }
                     const T y = a0 + a1;
                     wins[2 * (own + j) + rr] = y;
-                    yg[2 * (size_t)(lo[l] + m) + rr] = y;
+                    yg[2 * (size_t)(rbase + lo[l] + m) + rr] = y;
                 }
                 if (!finish_level(landed, true)) {
                     aborted = true;
@@ -740,7 +777,8 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 T a0 = (T)0, a1 = (T)0;
                 const T* rec = st + rec_off;
                 if (act) {
-                    a0 = st[L.stage_vec + 2 * m + rr];
+                    const int voff = (int)((2 * (rbase + lo[l])) & (16 / (int)sizeof(T) - 1));
+                    a0 = st[L.stage_vec + voff + 2 * m + rr];
                     const int off[6] = {n1 + j, n2 + j, n1 + j + 1, n2 + j + 1, n3 + j + 1, n4 + j + 2};
 #pragma unroll
                     for (int q = 0; q < 6; ++q) {
@@ -786,9 +824,33 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
 }
 
 template <typename T>
+__global__ void __launch_bounds__(256) ras_gather_kernel(int N, const T* __restrict__ r, const int* __restrict__ rec_of,
+                                                         const unsigned char* __restrict__ own_of, int right,
+                                                         T* __restrict__ rg) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= N) return;
+    const V2<T> val{r[c], r[N + c]};
+    const int oq = own_of[c];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int rec = rec_of[4 * (size_t)c + q];
+        if (rec < 0) break;
+        *reinterpret_cast<V2<T>*>(rg + 2 * (size_t)rec) = (right && q != oq) ? V2<T>{(T)0, (T)0} : val;
+    }
+}
+
+template <typename T>
+cudaError_t launch_ras_gather(const Geom& g, const T* r, const int* rec_of, const unsigned char* own_of,
+                              int ras_type, T* rg, cudaStream_t s) {
+    ras_gather_kernel<T><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, r, rec_of, own_of, ras_type == ACAC_RAS_RIGHT ? 1 : 0,
+                                                         rg);
+    return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             const RasLaunch& L, T* gscratch, int* err, cudaStream_t s) {
+                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s) {
     static std::atomic<size_t> attr_bytes{0};
     if (!L.window) {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply_kernel<T>, L.smem_bytes, &attr_bytes);
@@ -799,11 +861,18 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
         if (e != cudaSuccess) return e;
     }
     if (L.window) {
-        static std::atomic<size_t> win_bytes{0};
-        cudaError_t e = ensure_smem_limit((const void*)ras_apply_win_kernel<T>, L.smem_bytes, &win_bytes);
+        static std::atomic<size_t> win_bytes{0}, win_bytes_pre{0};
+        cudaError_t e = rg ? ensure_smem_limit((const void*)ras_apply_win_kernel<T, true>, L.smem_bytes, &win_bytes_pre)
+                           : ensure_smem_limit((const void*)ras_apply_win_kernel<T, false>, L.smem_bytes, &win_bytes);
         if (e != cudaSuccess) return e;
-        ras_apply_win_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch,
-                                                                    L, err);
+        // float: r gathered beforehand (the producer keeps up only with contiguous copies);
+        // double: the producer gathers r itself (the consumers' FP64 work leaves it time)
+        if (rg)
+            ras_apply_win_kernel<T, true><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, rg, z, ras_type,
+                                                                              gscratch, L, err);
+        else
+            ras_apply_win_kernel<T, false><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type,
+                                                                               gscratch, L, err);
         return cudaGetLastError();
     }
     ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
@@ -1119,8 +1188,10 @@ cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, cons
     template cudaError_t launch_repack<T>(const Geom&, const T*, const int*, T*, cudaStream_t);       \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                               int, T*, int, int, size_t, int*, cudaStream_t);       \
+    template cudaError_t launch_ras_gather<T>(const Geom&, const T*, const int*, const unsigned char*, \
+                                              int, T*, cudaStream_t);                                   \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
-                                             const T*, T*, int, int, const RasLaunch&, T*, int*,       \
+                                             const T*, T*, int, int, const RasLaunch&, T*, const T*, int*, \
                                              cudaStream_t);                                           \
     template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*,    \
                                                const int*, const T*, int, T*, int, int*, cudaStream_t);      \

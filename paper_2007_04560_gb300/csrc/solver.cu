@@ -146,6 +146,9 @@ struct acac_handle {
     std::vector<int> rec_of;     // for every grid cell, its records in the boxes (4 per cell in 2D, 8 in
                                  // 3D; -1 unused)
     int* rec_of_dev = nullptr;
+    std::vector<unsigned char> own_of;   // 2D: for every grid cell, the slot of rec_of whose box owns it
+    unsigned char* own_of_dev = nullptr;
+    void* rg = nullptr;          // windowed apply: the right-hand side gathered per box cell, by record
     void* Jp = nullptr;          // Jacobian rows per box cell (52 values each in 2D, 100 in 3D)
     bool jpacked = false;        // Jp holds the current Jacobian (assembled straight into it)
     int *cells3_dev, *pos3_dev;
@@ -412,10 +415,13 @@ void precond(acac_handle* h, const T* r, T* z) {
                                  h->flags + 1, h->stream));
         return;
     }
+    if (h->ras_launch.window && sizeof(T) == 4)
+        KLA(ACAC_K_VECTOR, (double)sizeof(T) * (2.0 * h->N + 2.0 * h->nbox) + 17.0 * h->N, 0.0,
+            launch_ras_gather<T>(h->g, r, h->rec_of_dev, h->own_of_dev, h->p.ras_type, (T*)h->rg, h->stream));
     KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
         launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
-                            h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch, h->flags + 1,
-                            h->stream));
+                            h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch,
+                            sizeof(T) == 4 ? (const T*)h->rg : nullptr, h->flags + 1, h->stream));
 }
 
 // With defer, the pivot / timeout flags are not read here: the Newton loop's GMRES reads
@@ -995,6 +1001,7 @@ int build_subdomains(acac_handle* h) {
     if (dim == 2) {
         // records of every grid cell: box cells before the box + lo[level] + position
         h->rec_of.assign((size_t)4 * p.n[0] * p.n[1], -1);
+        h->own_of.assign((size_t)p.n[0] * p.n[1], 0);
         for (const SubInfo& sd : h->subs) {
             const long long base = sd.coef_base / NCOEF;
             for (int l = 0; l < sd.nlev; ++l) {
@@ -1012,6 +1019,8 @@ int build_subdomains(acac_handle* h) {
                     while (q < 4 && h->rec_of[4 * gc + q] >= 0) ++q;
                     if (q == 4 || rec > INT32_MAX) return ACAC_E_ARG;   // at most 4 boxes per cell in 2D
                     h->rec_of[4 * gc + q] = (int)rec;
+                    if (i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)
+                        h->own_of[gc] = (unsigned char)q;
                 }
             }
         }
@@ -1181,7 +1190,8 @@ void build_sparse(acac_handle* h) {
 void free_all(acac_handle* h) {
     void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0, h->shift_dev, h->V, h->Zb, h->w,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
-                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->Jp,
+                    h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->own_of_dev,
+                    h->rg, h->Jp,
                     h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -1432,9 +1442,13 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             for (auto& sd : h->subs) maxh = std::max(maxh, sd.H);
             L.win_cells = maxh + 4;   // rows per window slot
             if (L.window) {
-                // a windowed stage also carries the level's right-hand side (2 values per cell)
+                // a windowed stage also carries the level's right-hand side (2 values per cell,
+                // copied in 16-byte chunks from a possibly unaligned start)
                 L.stage_vec = L.stage_elems;
-                L.stage_elems += (2 * h->ras_maxcnt + 31) / 32 * 32;
+                L.stage_elems += (2 * h->ras_maxcnt + 8 + 31) / 32 * 32;
+                // float: the right-hand side gathered per box cell (in record order), read by the
+                // stages; 16 spare values for the chunked copies' overreach
+                if (ks == 4) dmalloc(&h->rg, ((size_t)(h->coef_count / NCOEF) * 2 + 16) * ks);
                 const size_t stage_bytes = (size_t)L.stage_elems * ks;
                 // aim at three CTAs per SM with at least 4 stages each
                 const size_t win_bytes = r128((size_t)5 * L.win_cells * 2 * ks);
@@ -1488,6 +1502,12 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         CU(cudaMemcpy(h->lev_dev, h->lev.data(), h->lev.size() * sizeof(int), cudaMemcpyHostToDevice));
         dmalloc(&h->rec_of_dev, h->rec_of.size() * sizeof(int));
         CU(cudaMemcpy(h->rec_of_dev, h->rec_of.data(), h->rec_of.size() * sizeof(int), cudaMemcpyHostToDevice));
+        if (!h->own_of.empty()) {
+            dmalloc(&h->own_of_dev, h->own_of.size());
+            CU(cudaMemcpy(h->own_of_dev, h->own_of.data(), h->own_of.size(), cudaMemcpyHostToDevice));
+            h->own_of.clear();
+            h->own_of.shrink_to_fit();
+        }
         dmalloc(&h->Jp, p->dim == 3 ? (size_t)(h->coef_count / NCOEF3) * 4 * NSLOT3 * h->ksz
                                     : (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
         h->rec_of.clear();
