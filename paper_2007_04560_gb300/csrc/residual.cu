@@ -178,6 +178,12 @@ __device__ __forceinline__ void one_minus_pq(double u, double v, double& mp, dou
 struct Midpoint2 {
     double zp, omp, sp, zq, omq, sq;
 };
+// true unless 0 < x2 / 2 < 1 keeps at least 2^-6 from both ends (x2 = twice a midpoint; the
+// bit pattern of a positive double orders like its value, a negative one or NaN falls outside)
+__device__ __forceinline__ bool near_pure2(double x2) {
+    const long long b = __double_as_longlong(x2);
+    return b < 0x3FA0000000000000LL || b > 0x3FFF800000000000LL;   // 2^-5, 2 - 2^-5
+}
 __device__ __forceinline__ Midpoint2 midpoint_pq2(double u1, double v1, double u0, double v0) {
     const double p1 = u1 + v1, p0 = u0 + v0, q1 = u1 - v1, q0 = u0 - v0;
     double mp1, mq1, mp0, mq0;
@@ -187,6 +193,25 @@ __device__ __forceinline__ Midpoint2 midpoint_pq2(double u1, double v1, double u
     // sigma from the end values nearer zero: p1 - p0 below zeta = 1/2, (1-p0) - (1-p1) above
     return Midpoint2{zp, mp1 + mp0, zp < 1.0 ? p1 - p0 : mp0 - mp1,
                      zq, mq1 + mq0, zq < 1.0 ? q1 - q0 : mq0 - mq1};
+}
+
+// The same quantities at the cost of the plain sums: 2 zeta = (u1 + u0) +- (v1 + v0),
+// 2 (1 - zeta) = 2 - 2 zeta, 2 sigma = (u1 - u0) +- (v1 - v0).  Far from a pure phase these
+// carry errors of a few units in the last place of u and v, i.e. of zeta and 1 - zeta (both
+// >= 2^-6 there); when a lane of the warp comes within 2^-6 of a pure phase the whole warp
+// takes midpoint_pq2 instead (one vote per warp; every lane of the warp must call it).
+__device__ __forceinline__ Midpoint2 midpoint_pq2_fast(double u1, double v1, double u0, double v0) {
+    const double su = u1 + u0, sv = v1 + v0, du = u1 - u0, dv = v1 - v0;
+    Midpoint2 m{su + sv, 0.0, du + dv, su - sv, 0.0, du - dv};
+    m.omp = 2.0 - m.zp;
+    m.omq = 2.0 - m.zq;
+    if (__any_sync(0xffffffffu, near_pure2(m.zp) || near_pure2(m.zq))) m = midpoint_pq2(u1, v1, u0, v0);
+    return m;
+}
+// positive and finite (bit-pattern test, no floating-point compare)
+__device__ __forceinline__ bool pos_bits(double x) {
+    const long long b = __double_as_longlong(x);
+    return b > 0 && b < 0x7FF0000000000000LL;
 }
 
 // series_args for p and q with one division: 1/(zp(1-zp)) and 1/(zq(1-zq)) from the
@@ -303,8 +328,8 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         }
         // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma),
         // all three doubled (the series only sees their ratios)
-        const Midpoint2 m2 = midpoint_pq2(u1, v1, u0, v0);
-        const bool ok = m2.zp > 0.0 && m2.omp > 0.0 && m2.zq > 0.0 && m2.omq > 0.0;
+        const Midpoint2 m2 = midpoint_pq2_fast(u1, v1, u0, v0);
+        const bool ok = pos_bits(m2.zp) && pos_bits(m2.omp) && pos_bits(m2.zq) && pos_bits(m2.omq);
         if (live && !ok) flag |= 1;
         SeriesArgs ap, aq;
         series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
@@ -449,8 +474,11 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
         decode_cell<DIM>(g, c, x, y, z);
         const double u = U[c], v = V[c];
         const double p = u + v, q = u - v;
-        double mp, mq;                                           // 1 - p, 1 - q
-        one_minus_pq(u, v, mp, mq);
+        // 1 - p, 1 - q: plain differences, or correctly rounded where a lane of the warp is
+        // within 2^-6 of a pure phase (the loop's trip count varies by lane: vote among the
+        // lanes still in it)
+        double mp = 1.0 - p, mq = 1.0 - q;
+        if (__any_sync(__activemask(), near_pure2(2.0 * p) || near_pure2(2.0 * q))) one_minus_pq(u, v, mp, mq);
         if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) flag |= 1;
         double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v
                  + k.theta * (xlogx(p) + xlogx(mp) + xlogx(q) + xlogx(mq));
@@ -507,11 +535,11 @@ __global__ void __launch_bounds__(256) linearize_kernel(Geom g, Coef k, const do
         const double u1 = X[c], v1 = X[N + c], u0 = X0[c], v0 = X0[N + c];
         // zeta, 1 - zeta and sigma of p and q in double (midpoint_pq2: accurate near the pure
         // phases, where the increments of u and v may cancel), then precision T
-        const Midpoint2 m2 = midpoint_pq2(u1, v1, u0, v0);
+        const Midpoint2 m2 = midpoint_pq2_fast(u1, v1, u0, v0);
         const double su = u1 + u0, sv = v1 + v0;
         const T half = (T)0.5;
-        const T zp = (T)(0.5 * m2.zp), omp = (T)(0.5 * m2.omp), zq = (T)(0.5 * m2.zq), omq = (T)(0.5 * m2.omq);
-        const T sp = (T)(0.5 * m2.sp), sq = (T)(0.5 * m2.sq);
+        const T zp = half * (T)m2.zp, omp = half * (T)m2.omp, zq = half * (T)m2.zq, omq = half * (T)m2.omq;
+        const T sp = half * (T)m2.sp, sq = half * (T)m2.sq;
         const T ub = half * (T)su, vb = half * (T)sv;
         const T w = (T)0.25 - vb * vb;
         // ssign = -1: derivative in the start value (phi^S is even in sigma)
