@@ -40,11 +40,17 @@ FP64_DERIVED_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12   # SMs x DFMA/clk/SM x 2 flo
 FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
-# DRAM bytes (read + write) per launch of the dominant kernels, from one-kernel ncu captures
-# of the current kernels (profiles/).  Keyed by (kernel class, precision, box width incl.
-# overlap); the value is per box cell, so a launch's traffic is this x the box cells of
-# the launch.  A kernel changed after its capture must be removed from this table.
-TRAFFIC_PER_BOX_CELL = {}
+# DRAM bytes (read + write) per box cell of the Schwarz kernels, from one-kernel ncu captures
+# of the current kernels on 1024^2 grids with 8x8 boxes of the same 132^2 cells as the 2048^2
+# workloads (one box per SM; profiles/ras_factor_2d-boxes132-fp64.md,
+# profiles/ras_apply_win_2d-boxes132.md): a launch's traffic is this x its box cells (the
+# traffic grows with the box cells).  Keyed by (kernel class, precision, extended box width).
+# A kernel changed after its capture must be removed from this table.
+TRAFFIC_PER_BOX_CELL = {
+    ("ras_factor", PREC_FP64, 132): 1014.398e6 / 1115136,
+    ("ras_apply", PREC_FP64, 132): 568.777e6 / 1115136,
+    ("ras_apply", PREC_MIXED, 132): 282.487e6 / 1115136,
+}
 
 
 def hbm_peak():

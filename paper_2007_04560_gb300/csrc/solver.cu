@@ -361,7 +361,10 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
         a.X = h->Xt;
         a.S = nullptr;
     }
-    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 0.0, launch_residual_g(h->g, h->k, a, h->stream));
+    // pass A: ~113 FP64 operations per cell in the formulas (midpoints, Laplacians of the new
+    // state, series arguments with one reciprocal, two table logarithms, four series of K = 4
+    // terms, G and the mobility), charged as 2 flop-equivalents each (one DFMA slot)
+    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 226.0 * h->N, launch_residual_g(h->g, h->k, a, h->stream));
     KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double f2 = read_scalars(h, 1);
