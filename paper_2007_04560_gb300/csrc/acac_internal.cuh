@@ -397,6 +397,12 @@ struct ResidualArgs {
                                   // null: formed from X0 in pass A
     const double* shift_sum = nullptr;   // if set, the trial shift is shift_sum[0] * shift_scale
     double shift_scale = 0.0;            // (read on the device: no host round trip)
+    // pass A also writes the linearisation cache at the evaluated state (the state the next
+    // Newton iteration linearises at when the line search accepts it): cache_mode 1 double
+    // (cache_d), 2 float (cache_f), 0 none
+    int cache_mode = 0;
+    Cache<double> cache_d{};
+    Cache<float> cache_f{};
 };
 cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
 // L = discrete Laplacian of both fields of X (2N each): the start state's part of G3, fixed

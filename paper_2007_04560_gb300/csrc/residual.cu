@@ -10,6 +10,8 @@
 #include <atomic>
 #include <mutex>
 
+#include <type_traits>
+
 #include "acac_internal.cuh"
 
 namespace acac {
@@ -152,6 +154,8 @@ __device__ __forceinline__ float series_R<float>(float r, int S) {
 // formed first (series_args2) so that the caller can pick the warp-uniform term count.
 struct SeriesArgs {
     double ra, rb, ratio;
+    double a, b;     // sigma / zeta, sigma / (1 - zeta)
+    double iz, io;   // 1 / zeta, 1 / (1 - zeta) divided by the common factor of the inputs
 };
 __device__ __forceinline__ double phi_series(const SeriesArgs& s, int K) {
     return table_log(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
@@ -235,8 +239,8 @@ __device__ __forceinline__ void series_args2(double zp, double omp, double sp, d
     const double tp = zp * invp, up = omp * invp;      // 1/(1-zp), 1/zp
     const double tq = zq * invq, uq = omq * invq;
     const double a1 = sp * up, b1 = sp * tp, a2 = sq * uq, b2 = sq * tq;
-    ap = SeriesArgs{a1 * a1, b1 * b1, zp * tp};
-    aq = SeriesArgs{a2 * a2, b2 * b2, zq * tq};
+    ap = SeriesArgs{a1 * a1, b1 * b1, zp * tp, a1, b1, up, tp};
+    aq = SeriesArgs{a2 * a2, b2 * b2, zq * tq, a2, b2, uq, tq};
 }
 
 // max of non-negative doubles (their bit patterns order like the values)
@@ -287,7 +291,19 @@ __device__ __forceinline__ bool in_unit(double x) {
     return b > 0 && b < 0x3ff0000000000000LL;
 }
 
-template <int DIM, bool PRE>
+// d phi^S / d(end value) from the series arguments of pass A: dphi_pair's
+//   1/2 [(1 + a^2 R(a^2) - a R(a^2)) / zeta + (1 + b^2 R(b^2) + b R(b^2)) / (1 - zeta)],
+// where pass A's inputs were doubled, so that iz = 1/(2 zeta) and io = 1/(2 (1 - zeta)) already
+// carry the 1/2; in double with pass A's warp-uniform K terms, or in float with all S terms.
+template <typename T>
+__device__ __forceinline__ T dphi_from_args(const SeriesArgs& s, int K) {
+    const T a = (T)s.a, b = (T)s.b, ra = (T)s.ra, rb = (T)s.rb;
+    const T R1 = series_R<T>(ra, K), R2 = series_R<T>(rb, K);
+    const T one = (T)1;
+    return (one + ra * R1 - a * R1) * (T)s.iz + (one + rb * R2 + b * R2) * (T)s.io;
+}
+
+template <int DIM, bool PRE, int CM>
 __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
     const int N = g.N;
     const double* __restrict__ Xu = a.X;
@@ -340,11 +356,32 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
         const double ha = 0.5 * k.alpha, hgn = -0.5 * k.gamma;
         const double Gu = fma(hgn, lu, fma(k.theta, phi + psi, fma(-ha, su, ha)));
         const double Gv = fma(hgn, lv, fma(k.theta, phi - psi, -0.5 * k.beta * sv));
+        const double ub = 0.5 * su, vb = 0.5 * sv;
+        const double cmob = ub * (1.0 - ub) * (0.25 - vb * vb);
         if (live) {
             a.G[c] = Gu;
             a.G[N + c] = Gv;
-            const double ub = 0.5 * su, vb = 0.5 * sv;
-            a.G[2 * N + c] = ub * (1.0 - ub) * (0.25 - vb * vb);
+            a.G[2 * N + c] = cmob;
+        }
+        if (CM != 0) {
+            // the linearisation cache at this state (linearize_kernel's entries, same formulas)
+            using T = typename std::conditional<CM == 1, double, float>::type;
+            const int KT = CM == 1 ? K : k.S;
+            const T dp = dphi_from_args<T>(ap, KT), dq = dphi_from_args<T>(aq, KT);
+            if (live) {
+                Cache<T> C;
+                if constexpr (CM == 1) C = a.cache_d; else C = a.cache_f;
+                const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
+                const T A = theta * dp, B = theta * dq;
+                const T ubT = (T)ub, vbT = (T)vb;
+                C.c[c] = (T)cmob;
+                C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ubT) * ((T)0.25 - vbT * vbT);
+                C.cv[c] = -ubT * ((T)1 - ubT) * vbT;
+                C.Gu[c] = (T)Gu;
+                C.Gv[c] = (T)Gv;
+                C.du[c] = -halpha + A + B;
+                C.xc[c] = A - B;
+            }
         }
     }
     if (flag) atomicOr(a.flags, flag);
@@ -405,12 +442,28 @@ cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& 
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
     const int nb = grid_for(g.N, 256);
-    if (a.L0) {
-        if (g.dim == 3) g_kernel<3, true><<<nb, 256, 0, s>>>(g, k, a);
-        else g_kernel<2, true><<<nb, 256, 0, s>>>(g, k, a);
+    auto go = [&](auto dimc, auto prec, auto cmc) {
+        g_kernel<decltype(dimc)::value, decltype(prec)::value, decltype(cmc)::value><<<nb, 256, 0, s>>>(g, k, a);
+    };
+    using I2 = std::integral_constant<int, 2>;
+    using I3 = std::integral_constant<int, 3>;
+    using PT = std::true_type;
+    using PF = std::false_type;
+    using C0 = std::integral_constant<int, 0>;
+    using C1 = std::integral_constant<int, 1>;
+    using C2 = std::integral_constant<int, 2>;
+    if (g.dim == 3) {
+        if (a.L0) {
+            if (a.cache_mode == 1) go(I3{}, PT{}, C1{}); else if (a.cache_mode == 2) go(I3{}, PT{}, C2{}); else go(I3{}, PT{}, C0{});
+        } else {
+            go(I3{}, PF{}, C0{});
+        }
     } else {
-        if (g.dim == 3) g_kernel<3, false><<<nb, 256, 0, s>>>(g, k, a);
-        else g_kernel<2, false><<<nb, 256, 0, s>>>(g, k, a);
+        if (a.L0) {
+            if (a.cache_mode == 1) go(I2{}, PT{}, C1{}); else if (a.cache_mode == 2) go(I2{}, PT{}, C2{}); else go(I2{}, PT{}, C0{});
+        } else {
+            go(I2{}, PF{}, C0{});
+        }
     }
     return cudaGetLastError();
 }

@@ -125,6 +125,7 @@ struct acac_handle {
     double* lap0 = nullptr;     // Laplacians of X0 during a Newton solve (pass A reads them)
     double* shift_dev = nullptr;   // sum(u^n - u - S_u) of the current Newton direction
     bool factor_check = false;     // a deferred factorization's flags are still to be read
+    bool cache_fresh = false;      // the last residual evaluation wrote the linearisation cache
     // Krylov precision buffers
     void *V, *w, *kt, *jtmp, *cache, *J, *coef, *gscratch;
     void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
@@ -347,9 +348,22 @@ int read_flags(acac_handle* h) {
 
 // ||F(X)|| (or of the trial point X + lam (S + shift e_u)) and the G buffer.
 double eval_residual(acac_handle* h, const double* X, const double* S, double lam, double shift,
-                     double dt, int* flags_out, bool use_lap0 = false, const double* shift_sum = nullptr) {
+                     double dt, int* flags_out, bool use_lap0 = false, const double* shift_sum = nullptr,
+                     bool fill_cache = false) {
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
     ResidualArgs a;
+    // with fill_cache pass A also writes the linearisation cache at the evaluated state, which
+    // the next Newton iteration uses if this state is accepted (the Newton loop's evaluations)
+    if (fill_cache && use_lap0) {
+        if (h->mixed) {
+            a.cache_mode = 2;
+            a.cache_f = cache_of<float>(h);
+        } else {
+            a.cache_mode = 1;
+            a.cache_d = cache_of<double>(h);
+        }
+    }
+    h->cache_fresh = a.cache_mode != 0;
     a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
     a.L0 = use_lap0 ? h->lap0 : nullptr;
     a.shift_sum = shift_sum;
@@ -364,7 +378,8 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     // pass A: ~113 FP64 operations per cell in the formulas (midpoints, Laplacians of the new
     // state, series arguments with one reciprocal, two table logarithms, four series of K = 4
     // terms, G and the mobility), charged as 2 flop-equivalents each (one DFMA slot)
-    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7, 226.0 * h->N, launch_residual_g(h->g, h->k, a, h->stream));
+    KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7 + (a.cache_mode ? 7.0 * h->ksz * h->N : 0.0), 226.0 * h->N,
+        launch_residual_g(h->g, h->k, a, h->stream));
     KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
     CU(cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     const double f2 = read_scalars(h, 1);
@@ -712,10 +727,15 @@ int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer
     }
 }
 
+// fresh: the cache already holds the linearisation at X (written by the residual evaluation
+// that produced X, see eval_residual)
 template <typename T>
-void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble) {
+void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble, bool fresh = false) {
     set_jac<T>(h, dt);
-    KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0, launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
+    if (!fresh)
+        KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0,
+            launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
+    h->cache_fresh = false;
     if (!assemble) return;
     // with matrix-free products the assembled Jacobian feeds only the subdomain
     // factorization: in 2D assemble it straight into the factorization's records
@@ -737,7 +757,7 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
     // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
     KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream));
     int fl = 0;
-    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl, true);
+    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl, true, nullptr, true);
     info->fnorm0 = info->fnorm = fnorm;
     if (fl & 1) return ACAC_E_DOMAIN;
     if (!isfinite(fnorm)) return ACAC_E_DIVERGED;
@@ -747,7 +767,8 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
     while (true) {
         if (it >= h->p.newton_maxit) return ACAC_E_DIVERGED;
         const bool refactor = (it == 0) || !h->p.ilu_reuse;
-        linearize_and_maybe_assemble<T>(h, h->X, dt, refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED);
+        linearize_and_maybe_assemble<T>(h, h->X, dt, refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED,
+                                        h->cache_fresh);
         if (refactor) {
             int st = factor<T>(h, true);
             if (st != ACAC_OK) return st;
@@ -767,7 +788,7 @@ int nks(acac_handle* h, double dt, acac_step_info* info) {
         const double f2 = fnorm * fnorm;
         double ft = 0.0;
         while (true) {
-            ft = eval_residual(h, h->X, h->S, lam, 0.0, dt, &fl, true, h->shift_dev);
+            ft = eval_residual(h, h->X, h->S, lam, 0.0, dt, &fl, true, h->shift_dev, true);
             if (fl & 8) return ACAC_E_TIMEOUT;
             if (fl == 0 && isfinite(ft) && ft * ft <= (1.0 - 2e-4 * lam) * f2) break;
             lam *= 0.5;

@@ -119,17 +119,20 @@ def convergence(kind="space", ns=(16, 32, 64), nref=128, dt=5e-5, dts=(8e-4, 4e-
 
 
 def long_run(bc="neumann", n=128, t_end=1e4, seed=0, dt_min=1e-4, dt_max=10.0, eta=1e4, dt0=1e-4,
-             max_steps=200000, parts=8, every=1, sink=None, L=2.0):
+             max_steps=200000, parts=8, every=1, sink=None, L=2.0, subdomain_solver=0, overlap=1,
+             max_seconds=None):
     """The long adaptive runs of Sec. 4.1 A (Figs. 2-4): 0.55 + U(-0.05, 0.05) /
     U(-0.05, 0.05) on n^2 cells of [0, L]^2, adaptive dt (eta, dt_min, dt_max) until t_end.
     L = 2 keeps h = 1/64 (on the unit square at 128^2 the subdomain ILU(0) does not
-    converge from the random initial state with Neumann walls).  Calls sink(record) every
-    `every` steps (and at the last); returns the summary: steps, time, dt range, energy
-    monotonicity, mass drift."""
+    converge from the random initial state with Neumann walls).  subdomain_solver / overlap:
+    the Schwarz subdomain solve (ILU(0), ILU(1), ILU(2), LU) and overlap; max_seconds stops
+    the run early.  Calls sink(record) every `every` steps (and at the last); returns the
+    summary: steps, time, dt range, energy monotonicity, mass drift."""
     import torch
     from workloads import BC_NEUMANN, BC_PERIODIC, DT_ADAPTIVE, initial_fields
     p = _params(n=(n, n, 1), L=(L, L, 1.0), bc=BC_NEUMANN if bc == "neumann" else BC_PERIODIC, dt_mode=DT_ADAPTIVE,
-                dt0=dt0, dt_min=dt_min, dt_max=dt_max, eta0=eta, ras_parts=(parts, parts, 1), ras_overlap=1)
+                dt0=dt0, dt_min=dt_min, dt_max=dt_max, eta0=eta, ras_parts=(parts, parts, 1), ras_overlap=overlap,
+                subdomain_solver=subdomain_solver)
     u0, v0 = initial_fields(p, seed, 0.55, 0.05)
     u = torch.tensor(u0.ravel(), device="cuda")
     v = torch.tensor(v0.ravel(), device="cuda")
@@ -140,7 +143,7 @@ def long_run(bc="neumann", n=128, t_end=1e4, seed=0, dt_min=1e-4, dt_max=10.0, e
     dts = []
     div = 0
     t0 = time.perf_counter()
-    while t < t_end and k < max_steps:
+    while t < t_end and k < max_steps and (max_seconds is None or time.perf_counter() - t0 < max_seconds):
         info = s.step(u, v)
         k += 1
         t = info.t
@@ -156,7 +159,9 @@ def long_run(bc="neumann", n=128, t_end=1e4, seed=0, dt_min=1e-4, dt_max=10.0, e
                   "eta": info.eta})
     torch.cuda.synchronize()
     s.close()
-    return {"bc": bc, "n": n, "steps": k, "t": t, "t_end": t_end, "seconds": time.perf_counter() - t0,
+    return {"bc": bc, "n": n, "L": L, "subdomain_solver": ["ILU(0)", "ILU(1)", "ILU(2)", "LU"][subdomain_solver],
+            "overlap": overlap, "boxes": [parts, parts], "eta0": eta, "dt_bounds": [dt_min, dt_max],
+            "steps": k, "t": t, "t_end": t_end, "seconds": time.perf_counter() - t0,
             "dt_min_seen": min(dts), "dt_max_seen": max(dts), "energy0": e0, "energy_end": e_prev,
             "energy_increases": increases, "max_relative_rise": max_rise, "mass_drift": abs(info.mass - m0) / abs(m0),
             "divergences": div}
@@ -267,6 +272,10 @@ def main(argv=None):
     lr.add_argument("--every", type=int, default=10)
     lr.add_argument("--jsonl", action="store_true")
     lr.add_argument("--L", type=float, default=2.0, help="domain [0, L]^2")
+    lr.add_argument("--subdomain-solver", choices=["ilu0", "ilu1", "ilu2", "lu"], default="ilu0")
+    lr.add_argument("--overlap", type=int, default=1)
+    lr.add_argument("--parts", type=int, default=8, help="Schwarz boxes per direction")
+    lr.add_argument("--max-seconds", type=float, default=None)
     sw = sub.add_parser("schwarz")
     sw.add_argument("--dim", type=int, choices=[2, 3], default=2)
     sw.add_argument("--steps", type=int, default=10)
@@ -281,7 +290,9 @@ def main(argv=None):
                           tuple(float(x) for x in args.dts.split(",")), args.dtref, args.T, args.n, box=args.box)
     elif args.cmd == "long":
         sink = (lambda r: print(json.dumps(r), flush=True)) if args.jsonl else None
-        res = long_run(args.bc, args.n, args.t_end, args.seed, every=args.every, sink=sink, L=args.L)
+        res = long_run(args.bc, args.n, args.t_end, args.seed, every=args.every, sink=sink, L=args.L,
+                       subdomain_solver=["ilu0", "ilu1", "ilu2", "lu"].index(args.subdomain_solver),
+                       overlap=args.overlap, parts=args.parts, max_seconds=args.max_seconds)
     elif args.cmd == "subdomain":
         prec = None if args.precision is None else (0 if args.precision == "fp64" else 1)
         res = subdomain_table(args.dim, args.steps, precision=prec)
