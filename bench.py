@@ -251,6 +251,10 @@ def fp64_peak(probe):
     return FP64_DERIVED_TFLOPS, "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz"
 
 
+# kernel classes whose arithmetic is double in both precision forms (residual, energy)
+FP64_CLASSES = {"residual_g", "residual_f", "energy"}
+
+
 def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None):
     name, (n, ms, b, f) = max(stats.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
@@ -258,7 +262,7 @@ def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=No
     gbs = b / (ms * 1e-3) / 1e9
     tflops = f / (ms * 1e-3) / 1e12
     hbm_gbs, hbm_src = hbm
-    if precision == PREC_FP64:
+    if precision == PREC_FP64 or name in FP64_CLASSES:
         fpeak, fsrc = fp64_peak(probe_fp64)
     else:
         fpeak, fsrc = FP32_DERIVED_TFLOPS, "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"
