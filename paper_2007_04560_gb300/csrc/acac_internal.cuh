@@ -136,6 +136,45 @@ struct Coef {
     int S;
 };
 
+// ---------------------------------------------------------------- ensemble members
+// An ensemble is `count` independent problems of one grid and one box decomposition,
+// solved in lockstep: every launch covers all members, member m being a grid index
+// (blockIdx.y of the cell, vector and box kernels, blockIdx.z of the 2D-tiled ones), and
+// every per-member buffer holds `count` copies at a fixed stride (elements of the buffer's
+// type).  A single problem is an ensemble of one (m = 0, strides unused).
+struct MemberK {              // per-member scalars (device array)
+    double alpha, beta, theta, gamma, rho;
+    double dt;                // time step of the member's current attempt
+    double lam;               // line-search step of the member's current trial
+    double pad;
+};
+struct Members {
+    int count = 1;
+    const int* on = nullptr;      // on[m] == 0: member m sits the launch out (nullptr: all take part)
+    const MemberK* k = nullptr;   // per-member scalars (nullptr: the launch's by-value scalars)
+    long long vs = 0;             // 2N-vectors: states, residuals, directions, Krylov vectors
+    long long gs = 0;             // 3-field buffers: G = [Gu | Gv | c], the product scratch
+    long long cs = 0;             // linearisation cache (7 fields of N)
+    long long js = 0;             // assembled stencil-diagonal Jacobian
+    long long jps = 0;            // Jacobian records per box cell
+    long long cfs = 0;            // Schwarz factors; 2x2 blocks of the fill solvers
+    long long ss = 0;             // global scratch of the Schwarz apply (box vectors)
+    long long rgs = 0;            // gathered right-hand side (windowed apply); fill solvers' inverse pivots
+    long long ps = 0;             // reduction partials
+    int rs = 0;                   // device scalars (reduction results, Hessenberg columns)
+};
+__device__ __forceinline__ bool member_off(const Members& mb, int m) { return mb.on && !mb.on[m]; }
+// Coefficients of member m (the by-value ones when the launch has no per-member scalars).
+__device__ __forceinline__ void member_coef(const Members& mb, int m, Coef& k) {
+    if (!mb.k) return;
+    const MemberK& q = mb.k[m];
+    k.alpha = q.alpha;
+    k.beta = q.beta;
+    k.theta = q.theta;
+    k.gamma = q.gamma;
+    k.rho = q.rho;
+}
+
 // Neighbour index of (x+dx, y+dy): wrapped (periodic) or clamped (Neumann; the
 // clamped value is the ghost of Sec. 2, phi_0 = phi_1).
 __device__ __forceinline__ int nb_index(const Geom& g, int x, int y, int dx, int dy) {
@@ -233,6 +272,13 @@ struct Cache {
 // or conversion per thread runs on the FP64 pipe, which on sm_103 issues at 1/64 of
 // the FP32 rate and would dominate the FP32 kernels.  The values are the correctly
 // rounded ones a kernel would form.
+// Member m's cache (the 7 fields at m * mb.cs).
+template <typename T>
+__device__ __forceinline__ Cache<T> member_cache(Cache<T> C, const Members& mb, int m) {
+    const size_t o = (size_t)m * mb.cs;
+    return Cache<T>{C.c + o, C.cu + o, C.cv + o, C.Gu + o, C.Gv + o, C.du + o, C.xc + o};
+}
+
 template <typename T>
 struct JacK {
     T idt, irho, hg, dvs;   // 1/dt, 1/rho, gamma/2, (alpha - beta)/2
@@ -282,15 +328,6 @@ int validate_params(const acac_params* p);
 // Grid sizes, spacings and the per-axis stencil weights of a validated parameter set.
 Geom make_geom(const acac_params* p);
 
-// ---------------------------------------------------------------- kernels (launchers)
-template <typename T>
-cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                               const int* pos, const T* J, int packed, T* coef, int threads, int* flags,
-                               cudaStream_t s);
-template <typename T>
-cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
-                              const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
-                              int* err, cudaStream_t s);
 // 16 bytes of consecutive values as one vector word (bit casts, no aliasing)
 __device__ __forceinline__ uint4 pack16(const float* p) {
     return make_uint4(__float_as_uint(p[0]), __float_as_uint(p[1]), __float_as_uint(p[2]), __float_as_uint(p[3]));
@@ -302,8 +339,8 @@ __device__ __forceinline__ uint4 pack16(const double* p) {
 }
 
 // Deterministic two-stage reductions.  A reducing kernel runs at most RED_BLOCKS
-// blocks of RED_THREADS threads; each block writes one partial sum per reduced
-// quantity v to partial[v * RED_BLOCKS + block], and the block that finishes last
+// blocks of RED_THREADS threads (per ensemble member); each block writes one partial sum
+// per reduced quantity v to partial[v * gridDim.x + block], and the block that finishes last
 // adds the partials of each quantity in a fixed order (so the result does not
 // depend on which block finishes when) and writes out[v].  The counter is zero
 // between launches (the last block re-arms it); kernels that share one counter must
@@ -313,6 +350,14 @@ struct Red {
     double* out;
     unsigned* counter;
 };
+
+// Member m's reduction: its partials, results and counter.
+__device__ __forceinline__ Red member_red(Red r, const Members& mb, int m) {
+    r.partial += (size_t)m * mb.ps;
+    r.out += (size_t)m * mb.rs;
+    r.counter += m;
+    return r;
+}
 
 // Sum of v over the block (blockDim.x a multiple of 32), valid in thread 0.  sh: 32 doubles.
 __device__ __forceinline__ double block_sum_red(double v, double* sh) {
@@ -363,7 +408,7 @@ __device__ __forceinline__ void finish_reduction(const Red& r, int nv, double* s
     for (int v0 = 0; v0 < nv; v0 += 8) {
         const int c = nv - v0 < 8 ? nv - v0 : 8;
         for (int q = 0; q < c; ++q) {
-            const double* p = r.partial + (size_t)(v0 + q) * RED_BLOCKS;
+            const double* p = r.partial + (size_t)(v0 + q) * nb;
             double a = 0.0;
             for (int i = threadIdx.x; i < nb; i += blockDim.x) a += __ldcg(p + i);
             a = warp_sum(a);
@@ -404,15 +449,22 @@ struct ResidualArgs {
     Cache<double> cache_d{};
     Cache<float> cache_f{};
 };
-cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
+// Launchers take the members the launch covers last (default: a single problem).  Per
+// member: X, X0, L0, Xt, S, F at stride vs; G at gs; the cache at cs; flags at 1; the
+// reduction per member_red; shift_sum at rs; coefficients, dt and lam from mb.k.
+cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s,
+                              const Members& mb = Members{});
 // L = discrete Laplacian of both fields of X (2N each): the start state's part of G3, fixed
 // over a Newton solve
-cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s);
-cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s);
-cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s);
+cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s,
+                             const Members& mb = Members{});
+cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s,
+                              const Members& mb = Members{});
+cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s, const Members& mb = Members{});
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s);
 // energy and mass: two quantities
-cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s);
+cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s,
+                          const Members& mb = Members{});
 // wrt_x0 = 0: the cache of dF/dX1; 1: of dF/dX0 (the series derivative taken with -sigma;
 // c, cu, cv, Gu, Gv are the same, and assembling with -dt gives the -1/dt diagonal).
 template <typename T>
@@ -428,71 +480,122 @@ cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, cons
                              double wM, double* lam, Red red, int* flags, cudaStream_t s);
 
 // jacobian.cu
+// The Jacobian kernels read their scalars (JacK, one per member) from device memory, written
+// whenever dt or the coefficients change, so that a captured CUDA graph of a GMRES iteration
+// stays valid across time steps.  Per member: J at js (records at jps), w, y at vs, the
+// product scratch at gs, the cache at cs.
 template <typename T>
-cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
-                            const int* rec_of = nullptr);
+cudaError_t launch_assemble(const Geom& g, const JacK<T>* kp, Cache<T> cache, T* J, cudaStream_t s,
+                            const int* rec_of = nullptr, const Members& mb = Members{});
 template <typename T>
-cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s);
+cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s);
-// The matrix-free products read their scalars (JacK) from device memory, written by
-// launch_set_jac whenever dt or the coefficients change, so that a captured CUDA
-// graph of a GMRES iteration stays valid across time steps.
 template <typename T>
-cudaError_t launch_set_jac(JacK<T>* dst, const Coef& k, double dt, cudaStream_t s);
-template <typename T>
-cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s);
+cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s,
+                            const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_jvp_g(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* tmp,
-                         cudaStream_t s);
+                         cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_jvp_f(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, const T* tmp, T* y,
-                         cudaStream_t s);
+                         cudaStream_t s, const Members& mb = Members{});
 
-// krylov.cu
+// krylov.cu (per member: vectors at vs, device scalars at rs, the reduction per member_red)
 cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
-                            cudaStream_t s);
+                            cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
-                             cudaStream_t s);
+                             cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w,
-                              long long n, int want_norm, Red red, cudaStream_t s);
+                              long long n, int want_norm, Red red, cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
-                              cudaStream_t s);
+                              cudaStream_t s, const Members& mb = Members{});
+// out = x * scale, or x / scale_dev[m * sstride] per member when scale_dev is set
 template <typename T>
-cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s);
+cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s,
+                             const Members& mb = Members{}, const double* scale_dev = nullptr, int sstride = 0);
+// out = sum_{k < nv} y_k V_k, nv = nv_dev[m] per member when nv_dev is set
 template <typename T>
 cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T* out,
-                           long long n, cudaStream_t s);
+                           long long n, cudaStream_t s, const Members& mb = Members{},
+                           const int* nv_dev = nullptr);
 template <typename T>
-cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s);
+cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s,
+                                  const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
-                                    cudaStream_t s);
+                                    cudaStream_t s, const Members& mb = Members{});
 // ||a - b||^2 (b may be NULL)
-cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s);
+cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s,
+                                const Members& mb = Members{});
+// y = x for the members that take part (vectors at vs)
+cudaError_t launch_copy_members(const double* x, double* y, long long n, cudaStream_t s, const Members& mb);
+// ensemble fields <-> member states: X[m] = [u[m] | v[m]] (to_state) or back
+cudaError_t launch_pack_members(const double* u, const double* v, double* X, long long N, int to_state,
+                                cudaStream_t s, const Members& mb);
 
-// ras.cu
+// GMRES on the device (Sec. 3.1): the Givens rotations of the Hessenberg columns, the
+// convergence test and the back substitution per member, so that a restart cycle needs
+// no host read-back per Arnoldi step.
+struct GmresHead {             // per member; written by the host at a cycle's start, read back after it
+    double beta;               // ||r|| at the cycle's start
+    double tol;                // absolute tolerance
+    double resid;              // current residual estimate |g_{k}|
+    int its, maxit;            // iterations so far (all cycles), limit
+    int k;                     // Arnoldi steps of the current cycle
+    int status;                // GMRES_RUNNING, GMRES_CONVERGED, GMRES_LIMIT, GMRES_NONFINITE
+};
+constexpr int GMRES_RUNNING = 0, GMRES_CONVERGED = 1, GMRES_LIMIT = 2, GMRES_NONFINITE = 3;
+struct GmresWork {             // per member, device only
+    double cs[MAX_RESTART], sn[MAX_RESTART], g[MAX_RESTART + 1];
+    double R[MAX_RESTART * MAX_RESTART];   // rotated Hessenberg, column j at j * MAX_RESTART
+};
+// start of a cycle for the members with on[m]: g = beta e_1, k = 0 (gon[m] = on[m])
+cudaError_t launch_gmres_start(GmresHead* head, GmresWork* work, const int* on, int* gon, int count,
+                               cudaStream_t s);
+// Arnoldi step j: column j = h0 + h1 (passes 2) or h0, subdiagonal sqrt(hn2), at red + m * rs
+// (h0 at 0, h1 at MAX_RESTART + 1, hn2 at 2 (MAX_RESTART + 1)); updates the rotations, the
+// residual estimate and gon[m] (0 once converged, at the limit or non-finite)
+cudaError_t launch_gmres_givens(GmresHead* head, GmresWork* work, const double* red, int rs, int j, int passes,
+                                int* gon, int count, cudaStream_t s);
+// y = R^-1 g over the cycle's k steps into y + m * rs, k into kcnt[m] (members with on[m])
+cudaError_t launch_gmres_solve(const GmresHead* head, const GmresWork* work, const int* on, double* y, int rs,
+                               int* kcnt, int count, cudaStream_t s);
+
+// ras.cu (per member: J at js or records at jps, factors at cfs, vectors at vs, scratch at
+// ss, the gathered right-hand side at rgs, flags and err at 1)
 // Jacobian rows of every box cell, one 4 x nslot-value record per box cell in the factor's
 // order; rec_of[rec_per_cell * c + q] = the records of grid cell c (-1: unused).
 template <typename T>
-cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s);
+cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s,
+                          const Members& mb = Members{});
 // J: stencil-diagonal (packed = 0) or the repacked records (packed = 1)
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                               const T* J, int packed, T* coef, int threads, int ring_cells, size_t smem_bytes,
-                              int* flags, cudaStream_t s);
+                              int* flags, cudaStream_t s, const Members& mb = Members{});
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s);
+                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s,
+                             const Members& mb = Members{});
 // 2D windowed apply: r restricted to every box cell (right-RAS: owned cells only), written by
 // record (rec_of) into rg, two values per box cell
 template <typename T>
 cudaError_t launch_ras_gather(const Geom& g, const T* r, const int* rec_of, const unsigned char* own_of,
-                              int ras_type, T* rg, cudaStream_t s);
+                              int ras_type, T* rg, cudaStream_t s, const Members& mb = Members{});
+
+template <typename T>
+cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                               const int* pos, const T* J, int packed, T* coef, int threads, int* flags,
+                               cudaStream_t s, const Members& mb = Members{});
+template <typename T>
+cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
+                              const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
+                              int* err, cudaStream_t s, const Members& mb = Members{});
 
 // Bounded wait for bit (word_bit) of a shared-memory word set by another warp of the block:
 // true once set, false after limit_ns of the global timer (the caller then records an error
@@ -544,19 +647,22 @@ struct SparseBox {
 // A_k of every box from the stencil-diagonal Jacobian J (values zeroed beforehand)
 template <typename T>
 cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
-                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s);
+                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s,
+                               const Members& mb = Members{});
 // block IKJ factorization in place; D^-1 of every cell to dinv; bit 2 of *flags on a
 // singular pivot block, bit 3 when a bounded wait for a row gave up.  smem: the done bits
 // ((n + 31) / 32 words, rounded up to 4) and, with use_map, (threads / 32) x (2 band + 1)
 // ints.
 template <typename T>
 cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
-                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s);
+                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s,
+                                 const Members& mb = Members{});
 // z = sum_k E_k inv(L_k U_k) R_k r with the restrictions and extensions of ras_type; the
 // box vector in shared memory (smem > 0) or in yscratch (2 values per box cell)
 template <typename T>
 cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
                                 const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
-                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s);
+                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s,
+                                const Members& mb = Members{});
 
 }  // namespace acac

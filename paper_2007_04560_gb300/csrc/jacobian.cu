@@ -23,13 +23,17 @@ static int grid1(long long n, int threads) {
 // rec_of[REC_PER_CELL c + q]; see the repack kernel of the factorization), which skips the
 // stencil-diagonal pass when nothing else reads it.
 template <typename T, int DIM, bool PACKED>
-__global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<T> C, T* __restrict__ J,
-                                                       const int* __restrict__ rec_of) {
+__global__ void __launch_bounds__(128) assemble_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
+                                                       T* __restrict__ J, const int* __restrict__ rec_of, Members mb) {
     constexpr int NS = nslot<DIM>();
     constexpr int NF = 2 * DIM;
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int m = blockIdx.y;
+    if (c >= N || member_off(mb, m)) return;
+    const JacK<T> k = kp[m];
+    C = member_cache(C, mb, m);
+    J += (size_t)m * (PACKED ? mb.jps : mb.js);
     int x, y, z;
     decode_cell<DIM>(g, c, x, y, z);
     // arithmetic in the Jacobian's precision T
@@ -138,15 +142,15 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, JacK<T> k, Cache<
 }
 
 template <typename T>
-cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> cache, T* J, cudaStream_t s,
-                            const int* rec_of) {
-    const JacK<T> kk = jac_consts<T>(k, dt);
+cudaError_t launch_assemble(const Geom& g, const JacK<T>* kp, Cache<T> cache, T* J, cudaStream_t s,
+                            const int* rec_of, const Members& mb) {
+    const dim3 grid(grid1(g.N, 128), mb.count);
     if (g.dim == 3) {
-        if (rec_of) assemble_kernel<T, 3, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
-        else assemble_kernel<T, 3, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+        if (rec_of) assemble_kernel<T, 3, true><<<grid, 128, 0, s>>>(g, kp, cache, J, rec_of, mb);
+        else assemble_kernel<T, 3, false><<<grid, 128, 0, s>>>(g, kp, cache, J, nullptr, mb);
     } else {
-        if (rec_of) assemble_kernel<T, 2, true><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, rec_of);
-        else assemble_kernel<T, 2, false><<<grid1(g.N, 128), 128, 0, s>>>(g, kk, cache, J, nullptr);
+        if (rec_of) assemble_kernel<T, 2, true><<<grid, 128, 0, s>>>(g, kp, cache, J, rec_of, mb);
+        else assemble_kernel<T, 2, false><<<grid, 128, 0, s>>>(g, kp, cache, J, nullptr, mb);
     }
     return cudaGetLastError();
 }
@@ -154,10 +158,14 @@ cudaError_t launch_assemble(const Geom& g, const Coef& k, double dt, Cache<T> ca
 // ---------------------------------------------------------------- assembled product
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__ J, const T* __restrict__ w,
-                                                   T* __restrict__ y) {
+                                                   T* __restrict__ y, Members mb) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int m = blockIdx.y;
+    if (c >= N || member_off(mb, m)) return;
+    J += (size_t)m * mb.js;
+    w += (size_t)m * mb.vs;
+    y += (size_t)m * mb.vs;
     int x, yy, zz;
     decode_cell<DIM>(g, c, x, yy, zz);
     T au = 0, av = 0;
@@ -173,9 +181,10 @@ __global__ void __launch_bounds__(256) spmv_kernel(Geom g, const T* __restrict__
 }
 
 template <typename T>
-cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s) {
-    if (g.dim == 3) spmv_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
-    else spmv_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, J, w, y);
+cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_t s, const Members& mb) {
+    const dim3 grid(grid1(g.N, 256), mb.count);
+    if (g.dim == 3) spmv_kernel<T, 3><<<grid, 256, 0, s>>>(g, J, w, y, mb);
+    else spmv_kernel<T, 2><<<grid, 256, 0, s>>>(g, J, w, y, mb);
     return cudaGetLastError();
 }
 
@@ -183,10 +192,15 @@ cudaError_t launch_spmv(const Geom& g, const T* J, const T* w, T* y, cudaStream_
 // Pass 1: dG_u, dG_v, dc per cell into tmp = [dGu | dGv | dc].
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
-                                                   const T* __restrict__ w, T* __restrict__ tmp) {
+                                                   const T* __restrict__ w, T* __restrict__ tmp, Members mb) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int m = blockIdx.y;
+    if (c >= N || member_off(mb, m)) return;
+    kp += m;
+    C = member_cache(C, mb, m);
+    w += (size_t)m * mb.vs;
+    tmp += (size_t)m * mb.gs;
     int x, y, z;
     decode_cell<DIM>(g, c, x, y, z);
     const T wu = w[c], wv = w[N + c];
@@ -211,10 +225,16 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, const JacK<T>* __rest
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
                                                    const T* __restrict__ w, const T* __restrict__ tmp,
-                                                   T* __restrict__ y) {
+                                                   T* __restrict__ y, Members mb) {
     const int N = g.N;
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int m = blockIdx.y;
+    if (c >= N || member_off(mb, m)) return;
+    kp += m;
+    C = member_cache(C, mb, m);
+    w += (size_t)m * mb.vs;
+    tmp += (size_t)m * mb.gs;
+    y += (size_t)m * mb.vs;
     int x, yy, zz;
     decode_cell<DIM>(g, c, x, yy, zz);
     const T* dGu = tmp;
@@ -233,31 +253,22 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, const JacK<T>* __rest
 }
 
 template <typename T>
-cudaError_t launch_jvp_g(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* tmp, cudaStream_t s) {
-    if (g.dim == 3) jvp1_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp);
-    else jvp1_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp);
+cudaError_t launch_jvp_g(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* tmp, cudaStream_t s,
+                         const Members& mb) {
+    const dim3 grid(grid1(g.N, 256), mb.count);
+    if (g.dim == 3) jvp1_kernel<T, 3><<<grid, 256, 0, s>>>(g, kp, cache, w, tmp, mb);
+    else jvp1_kernel<T, 2><<<grid, 256, 0, s>>>(g, kp, cache, w, tmp, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_jvp_f(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, const T* tmp, T* y,
-                         cudaStream_t s) {
-    if (g.dim == 3) jvp2_kernel<T, 3><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp, y);
-    else jvp2_kernel<T, 2><<<grid1(g.N, 256), 256, 0, s>>>(g, kp, cache, w, tmp, y);
+                         cudaStream_t s, const Members& mb) {
+    const dim3 grid(grid1(g.N, 256), mb.count);
+    if (g.dim == 3) jvp2_kernel<T, 3><<<grid, 256, 0, s>>>(g, kp, cache, w, tmp, y, mb);
+    else jvp2_kernel<T, 2><<<grid, 256, 0, s>>>(g, kp, cache, w, tmp, y, mb);
     return cudaGetLastError();
 }
-
-template <typename T>
-__global__ void set_jac_kernel(JacK<T>* dst, JacK<T> v) {
-    *dst = v;
-}
-
-template <typename T>
-cudaError_t launch_set_jac(JacK<T>* dst, const Coef& k, double dt, cudaStream_t s) {
-    set_jac_kernel<T><<<1, 1, 0, s>>>(dst, jac_consts<T>(k, dt));
-    return cudaGetLastError();
-}
-
 
 // ---------------------------------------------------------------- fused tiled product (2D)
 // y = J(X1) w in one pass over a JT_X x JT_Y tile of output cells: w is staged with a
@@ -272,7 +283,7 @@ constexpr int JT_X = 64, JT_Y = 16, JT_THREADS = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
-                                                              const T* __restrict__ w, T* __restrict__ y) {
+                                                              const T* __restrict__ w, T* __restrict__ y, Members mb) {
     constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
     constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1
     constexpr int NW = (WX * WY + JT_THREADS - 1) / JT_THREADS;
@@ -282,6 +293,12 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK
     __shared__ T sc[RY][RX], sg[RY][RX], sdg[RY][RX], sdc[RY][RX];
     __shared__ T sdgv[JT_Y][JT_X];
     const int N = g.N;
+    const int m = blockIdx.z;
+    if (member_off(mb, m)) return;
+    kp += m;
+    C = member_cache(C, mb, m);
+    w += (size_t)m * mb.vs;
+    y += (size_t)m * mb.vs;
     const int x0 = blockIdx.x * JT_X, y0 = blockIdx.y * JT_Y;
     const bool per = g.bc == ACAC_BC_PERIODIC;
     const int tid = threadIdx.x;
@@ -381,9 +398,10 @@ __global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK
 }
 
 template <typename T>
-cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s) {
-    dim3 grid((g.nx + JT_X - 1) / JT_X, (g.ny + JT_Y - 1) / JT_Y);
-    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, kp, cache, w, y);
+cudaError_t launch_jvp_tile(const Geom& g, const JacK<T>* kp, Cache<T> cache, const T* w, T* y, cudaStream_t s,
+                            const Members& mb) {
+    dim3 grid((g.nx + JT_X - 1) / JT_X, (g.ny + JT_Y - 1) / JT_Y, mb.count);
+    jvp_tile_kernel<T><<<grid, JT_THREADS, 0, s>>>(g, kp, cache, w, y, mb);
     return cudaGetLastError();
 }
 
@@ -430,16 +448,16 @@ cudaError_t launch_transpose(const Geom& g, const T* J, T* JT, cudaStream_t s) {
 }
 
 #define INST(T)                                                                                   \
-    template cudaError_t launch_assemble<T>(const Geom&, const Coef&, double, Cache<T>, T*,       \
-                                            cudaStream_t, const int*);                            \
-    template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t);       \
+    template cudaError_t launch_assemble<T>(const Geom&, const JacK<T>*, Cache<T>, T*, cudaStream_t, \
+                                            const int*, const Members&);                          \
+    template cudaError_t launch_spmv<T>(const Geom&, const T*, const T*, T*, cudaStream_t,        \
+                                        const Members&);                                          \
     template cudaError_t launch_jvp_g<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,      \
-                                         cudaStream_t);                                           \
+                                         cudaStream_t, const Members&);                           \
     template cudaError_t launch_jvp_f<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, const T*, \
-                                         T*, cudaStream_t);                                         \
+                                         T*, cudaStream_t, const Members&);                         \
     template cudaError_t launch_jvp_tile<T>(const Geom&, const JacK<T>*, Cache<T>, const T*, T*,    \
-                                            cudaStream_t);                                          \
-    template cudaError_t launch_set_jac<T>(JacK<T>*, const Coef&, double, cudaStream_t);             \
+                                            cudaStream_t, const Members&);                          \
     template cudaError_t launch_transpose<T>(const Geom&, const T*, T*, cudaStream_t);
 INST(double)
 INST(float)

@@ -1,19 +1,29 @@
 // Vector kernels of the restarted GMRES of Sec. 3.1 (Eq. hjacobi): block dot
 // products against the Arnoldi basis with warp-shuffle reductions, the classical
-// Gram–Schmidt update, norms, scaling, the basis combination V y and the
-// precision boundary between the FP64 Newton vectors and the Krylov vectors.
+// Gram–Schmidt update, norms, scaling, the basis combination V y, the precision
+// boundary between the FP64 Newton vectors and the Krylov vectors, and the small
+// per-member GMRES steps (Givens rotations, convergence test, back substitution).
 //
 // Reductions are two-stage and deterministic: every kernel writes one partial sum
-// per block (RED_BLOCKS blocks, grid-stride loops) and its last block to finish adds
-// the partials of each quantity in a fixed order (finish_reduction).
+// per block (at most RED_BLOCKS blocks per member, grid-stride loops) and the member's
+// last block to finish adds the partials of each quantity in a fixed order
+// (finish_reduction).  Member m of an ensemble is blockIdx.y; its vectors sit at
+// m * mb.vs, its device scalars at m * mb.rs.
 #include "acac_internal.cuh"
 
 namespace acac {
 
+static dim3 vgrid(long long n, const Members& mb) { return dim3(red_grid(n), mb.count); }
+
 // partial sums of (a - b - c) over n  (mass correction of the Newton direction)
 __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __restrict__ b,
-                                const double* __restrict__ c, long long n, Red red) {
+                                const double* __restrict__ c, long long n, Red red, Members mb) {
     __shared__ double sh[32];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    const size_t o = (size_t)m * mb.vs;
+    a += o; b += o; c += o;
+    red = member_red(red, mb, m);
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
@@ -24,14 +34,20 @@ __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __re
 }
 
 cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
-                            cudaStream_t s) {
-    sum_pair_kernel<<<red_grid(n), RED_THREADS, 0, s>>>(a, b, c, n, red);
+                            cudaStream_t s, const Members& mb) {
+    sum_pair_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, c, n, red, mb);
     return cudaGetLastError();
 }
 
 __global__ void norm2_double_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
-                                    Red red) {
+                                    Red red, Members mb) {
     __shared__ double sh[32];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    const size_t o = (size_t)m * mb.vs;
+    a += o;
+    if (b) b += o;
+    red = member_red(red, mb, m);
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -43,8 +59,9 @@ __global__ void norm2_double_kernel(const double* __restrict__ a, const double* 
     finish_reduction(red, 1, sh);
 }
 
-cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s) {
-    norm2_double_kernel<<<red_grid(n), RED_THREADS, 0, s>>>(a, b, n, red);
+cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s,
+                                const Members& mb) {
+    norm2_double_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, n, red, mb);
     return cudaGetLastError();
 }
 
@@ -77,7 +94,7 @@ __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld,
         double t = 0.0;
 #pragma unroll
         for (int k = 0; k < RED_THREADS / 32; ++k) t += sw[threadIdx.x][k];
-        partial[(size_t)threadIdx.x * RED_BLOCKS + blockIdx.x] = t;
+        partial[(size_t)threadIdx.x * gridDim.x + blockIdx.x] = t;
     }
     __syncthreads();
 }
@@ -85,11 +102,16 @@ __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld,
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                 const T* __restrict__ w, long long n,
-                                                                Red red) {
+                                                                Red red, Members mb) {
     __shared__ double sw[8][RED_THREADS / 32];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    V += (size_t)m * mb.vs;
+    w += (size_t)m * mb.vs;
+    red = member_red(red, mb, m);
     for (int k0 = 0; k0 < nv; k0 += 8) {
         const T* Vk = V + (size_t)k0 * ld;
-        double* pk = red.partial + (size_t)k0 * RED_BLOCKS;
+        double* pk = red.partial + (size_t)k0 * gridDim.x;
         switch (nv - k0 < 8 ? nv - k0 : 8) {
             case 1: dot_chunk<T, 1>(Vk, ld, w, n, pk, sw); break;
             case 2: dot_chunk<T, 2>(Vk, ld, w, n, pk, sw); break;
@@ -106,8 +128,8 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
 
 template <typename T>
 cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
-                             cudaStream_t s) {
-    multi_dot_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red);
+                             cudaStream_t s, const Members& mb) {
+    multi_dot_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
     return cudaGetLastError();
 }
 
@@ -115,9 +137,15 @@ cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long 
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                  const double* __restrict__ h, T* __restrict__ w,
-                                                                 long long n, int want_norm, Red red) {
+                                                                 long long n, int want_norm, Red red, Members mb) {
     __shared__ double sh[32];
     __shared__ T hs[MAX_RESTART + 1];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    V += (size_t)m * mb.vs;
+    w += (size_t)m * mb.vs;
+    h += (size_t)m * mb.rs;
+    red = member_red(red, mb, m);
     for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)h[k];
     __syncthreads();
     T acc = 0;
@@ -142,19 +170,23 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __rest
 
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w, long long n,
-                              int want_norm, Red red, cudaStream_t s) {
-    cgs_update_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red);
+                              int want_norm, Red red, cudaStream_t s, const Members& mb) {
+    cgs_update_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red, mb);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- out = w / alpha (alpha on device)
 template <typename T>
 __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restrict__ alpha,
-                                  T* __restrict__ out, long long n) {
+                                  T* __restrict__ out, long long n, Members mb) {
     // alpha holds ||w||^2; one thread per block forms 1/||w|| (an FP64 square root
     // and division per thread would cost more than the scaling itself)
     __shared__ T s_inv;
-    if (threadIdx.x == 0) s_inv = (T)(1.0 / sqrt(alpha[0]));
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    w += (size_t)m * mb.vs;
+    out += (size_t)m * mb.vs;
+    if (threadIdx.x == 0) s_inv = (T)(1.0 / sqrt(alpha[(size_t)m * mb.rs]));
     __syncthreads();
     const T inv = s_inv;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -164,30 +196,43 @@ __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restr
 
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
-                              cudaStream_t s) {
-    scale_from_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(w, alpha_dev, out, n);
+                              cudaStream_t s, const Members& mb) {
+    scale_from_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(w, alpha_dev, out, n, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* __restrict__ out,
-                                 long long n) {
+                                 long long n, Members mb, const double* __restrict__ scale_dev, int sstride) {
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    x += (size_t)m * mb.vs;
+    out += (size_t)m * mb.vs;
+    // 1/beta correctly rounded, as the host forms it for a single problem
+    if (scale_dev) scale = 1.0 / scale_dev[(size_t)m * sstride];
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         out[i] = (T)(x[i] * scale);
 }
 
 template <typename T>
-cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s) {
-    to_krylov_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(x, scale, out, n);
+cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s,
+                             const Members& mb, const double* scale_dev, int sstride) {
+    to_krylov_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, scale, out, n, mb, scale_dev, sstride);
     return cudaGetLastError();
 }
 
 // out = sum_k y_k V_k
 template <typename T>
 __global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, const double* __restrict__ y,
-                               T* __restrict__ out, long long n) {
+                               T* __restrict__ out, long long n, Members mb, const int* __restrict__ nv_dev) {
     __shared__ T ys[MAX_RESTART + 1];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    if (nv_dev) nv = nv_dev[m];
+    V += (size_t)m * mb.vs;
+    out += (size_t)m * mb.vs;
+    y += (size_t)m * mb.rs;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = (T)y[k];
     __syncthreads();
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
@@ -200,30 +245,41 @@ __global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, co
 
 template <typename T>
 cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T* out, long long n,
-                           cudaStream_t s) {
-    lincomb_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n);
+                           cudaStream_t s, const Members& mb, const int* nv_dev) {
+    lincomb_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n, mb, nv_dev);
     return cudaGetLastError();
 }
 
 template <typename T>
 __global__ void axpy_to_double_kernel(double a, const T* __restrict__ x, double* __restrict__ y,
-                                      long long n) {
+                                      long long n, Members mb) {
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    x += (size_t)m * mb.vs;
+    y += (size_t)m * mb.vs;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         y[i] = fma(a, (double)x[i], y[i]);
 }
 
 template <typename T>
-cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s) {
-    axpy_to_double_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(a, x, y, n);
+cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s,
+                                  const Members& mb) {
+    axpy_to_double_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, x, y, n, mb);
     return cudaGetLastError();
 }
 
 // r = b - Ax (double), partial sums of ||r||^2
 template <typename T>
 __global__ void residual_restart_kernel(const double* __restrict__ b, const T* __restrict__ Ax,
-                                        double* __restrict__ r, long long n, Red red) {
+                                        double* __restrict__ r, long long n, Red red, Members mb) {
     __shared__ double sh[32];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    b += (size_t)m * mb.vs;
+    Ax += (size_t)m * mb.vs;
+    r += (size_t)m * mb.vs;
+    red = member_red(red, mb, m);
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -238,23 +294,154 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
 
 template <typename T>
 cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
-                                    cudaStream_t s) {
-    residual_restart_kernel<T><<<red_grid(n), RED_THREADS, 0, s>>>(b, Ax, r, n, red);
+                                    cudaStream_t s, const Members& mb) {
+    residual_restart_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- member copies
+__global__ void copy_members_kernel(const double* __restrict__ x, double* __restrict__ y, long long n, Members mb) {
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    x += (size_t)m * mb.vs;
+    y += (size_t)m * mb.vs;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i];
+}
+
+cudaError_t launch_copy_members(const double* x, double* y, long long n, cudaStream_t s, const Members& mb) {
+    copy_members_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, y, n, mb);
+    return cudaGetLastError();
+}
+
+// u, v: the ensemble's fields (member m at m * N); X: member states [u | v] at m * vs
+__global__ void pack_members_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                    double* __restrict__ X, long long N, int to_state, Members mb) {
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    double* Xm = X + (size_t)m * mb.vs;
+    double* um = const_cast<double*>(u) + (size_t)m * N;
+    double* vm = const_cast<double*>(v) + (size_t)m * N;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
+         i += (long long)gridDim.x * blockDim.x) {
+        if (to_state) {
+            Xm[i] = um[i];
+            Xm[N + i] = vm[i];
+        } else {
+            um[i] = Xm[i];
+            vm[i] = Xm[N + i];
+        }
+    }
+}
+
+cudaError_t launch_pack_members(const double* u, const double* v, double* X, long long N, int to_state,
+                                cudaStream_t s, const Members& mb) {
+    pack_members_kernel<<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, N, to_state, mb);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- GMRES steps per member
+// One thread per member: the steps are O(j) scalar operations, negligible beside the
+// vector kernels of the Arnoldi step, and run on the device so that the host launches a
+// whole restart cycle without reading anything back in between.
+__global__ void gmres_start_kernel(GmresHead* __restrict__ head, GmresWork* __restrict__ work,
+                                   const int* __restrict__ on, int* __restrict__ gon, int count) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const int o = on ? on[m] : 1;
+    gon[m] = o;
+    if (o) work[m].g[0] = head[m].beta;
+}
+
+cudaError_t launch_gmres_start(GmresHead* head, GmresWork* work, const int* on, int* gon, int count,
+                               cudaStream_t s) {
+    gmres_start_kernel<<<(count + 127) / 128, 128, 0, s>>>(head, work, on, gon, count);
+    return cudaGetLastError();
+}
+
+// Column j of the Hessenberg matrix: rotated by the previous rotations, then the new
+// rotation zeroes its subdiagonal entry; the rotated right-hand side g gives the residual
+// norm |g_{j+1}| of the minimiser over the j + 1 directions.
+__global__ void gmres_givens_kernel(GmresHead* __restrict__ head, GmresWork* __restrict__ work,
+                                    const double* __restrict__ red, int rs, int j, int passes,
+                                    int* __restrict__ gon, int count) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count || !gon[m]) return;
+    const double* r = red + (size_t)m * rs;
+    GmresWork& W = work[m];
+    GmresHead& H = head[m];
+    double* R = W.R + (size_t)j * MAX_RESTART;
+    for (int i = 0; i <= j; ++i) R[i] = passes == 2 ? r[i] + r[(MAX_RESTART + 1) + i] : r[i];
+    const double hn = sqrt(r[2 * (MAX_RESTART + 1)]);
+    for (int i = 0; i < j; ++i) {
+        const double a = R[i], b = R[i + 1];
+        R[i] = W.cs[i] * a + W.sn[i] * b;
+        R[i + 1] = -W.sn[i] * a + W.cs[i] * b;
+    }
+    const double rho = hypot(R[j], hn);
+    W.cs[j] = R[j] / rho;
+    W.sn[j] = hn / rho;
+    R[j] = rho;
+    W.g[j + 1] = -W.sn[j] * W.g[j];
+    W.g[j] = W.cs[j] * W.g[j];
+    const double resid = fabs(W.g[j + 1]);
+    H.resid = resid;
+    H.its += 1;
+    H.k = j + 1;
+    if (!(resid == resid) || !isfinite(rho)) {
+        H.status = GMRES_NONFINITE;
+        gon[m] = 0;
+    } else if (resid <= H.tol || H.its >= H.maxit || hn == 0.0) {
+        H.status = (resid <= H.tol || hn == 0.0) ? GMRES_CONVERGED : GMRES_LIMIT;
+        gon[m] = 0;
+    }
+}
+
+cudaError_t launch_gmres_givens(GmresHead* head, GmresWork* work, const double* red, int rs, int j, int passes,
+                                int* gon, int count, cudaStream_t s) {
+    gmres_givens_kernel<<<(count + 127) / 128, 128, 0, s>>>(head, work, red, rs, j, passes, gon, count);
+    return cudaGetLastError();
+}
+
+// y = R(0:k, 0:k)^-1 g(0:k) by back substitution
+__global__ void gmres_solve_kernel(const GmresHead* __restrict__ head, const GmresWork* __restrict__ work,
+                                   const int* __restrict__ on, double* __restrict__ y, int rs,
+                                   int* __restrict__ kcnt, int count) {
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (m >= count || (on && !on[m])) return;
+    const int k = head[m].k;
+    const GmresWork& W = work[m];
+    double* yv = y + (size_t)m * rs;
+    kcnt[m] = k;
+    for (int i = k - 1; i >= 0; --i) {
+        double s = W.g[i];
+        for (int jj = i + 1; jj < k; ++jj) s -= W.R[(size_t)jj * MAX_RESTART + i] * yv[jj];
+        yv[i] = s / W.R[(size_t)i * MAX_RESTART + i];
+    }
+}
+
+cudaError_t launch_gmres_solve(const GmresHead* head, const GmresWork* work, const int* on, double* y, int rs,
+                               int* kcnt, int count, cudaStream_t s) {
+    gmres_solve_kernel<<<(count + 127) / 128, 128, 0, s>>>(head, work, on, y, rs, kcnt, count);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                     \
     template cudaError_t launch_multi_dot<T>(const T*, long long, int, const T*, long long, Red,    \
-                                             cudaStream_t);                                         \
+                                             cudaStream_t, const Members&);                         \
     template cudaError_t launch_cgs_update<T>(const T*, long long, int, const double*, T*, long long, \
-                                              int, Red, cudaStream_t);                              \
-    template cudaError_t launch_scale_from<T>(const T*, const double*, T*, long long, cudaStream_t); \
-    template cudaError_t launch_to_krylov<T>(const double*, double, T*, long long, cudaStream_t);   \
+                                              int, Red, cudaStream_t, const Members&);              \
+    template cudaError_t launch_scale_from<T>(const T*, const double*, T*, long long, cudaStream_t, \
+                                              const Members&);                                      \
+    template cudaError_t launch_to_krylov<T>(const double*, double, T*, long long, cudaStream_t,    \
+                                             const Members&, const double*, int);                   \
     template cudaError_t launch_lincomb<T>(const T*, long long, int, const double*, T*, long long,  \
-                                           cudaStream_t);                                           \
-    template cudaError_t launch_axpy_to_double<T>(double, const T*, double*, long long, cudaStream_t); \
+                                           cudaStream_t, const Members&, const int*);               \
+    template cudaError_t launch_axpy_to_double<T>(double, const T*, double*, long long, cudaStream_t, \
+                                                  const Members&);                                  \
     template cudaError_t launch_residual_restart<T>(const double*, const T*, double*, long long,    \
-                                                    Red, cudaStream_t);
+                                                    Red, cudaStream_t, const Members&);
 INST(double)
 INST(float)
 #undef INST

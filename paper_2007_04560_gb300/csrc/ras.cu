@@ -78,10 +78,13 @@ constexpr int FACTOR_RING = 5;
 // the cell (rec_of lists them, -1 unused).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) repack_kernel(int N, const T* __restrict__ J, const int* __restrict__ rec_of,
-                                                     T* __restrict__ Jp) {
+                                                     T* __restrict__ Jp, Members mb) {
     constexpr int NS = nslot<DIM>(), NR = rec_per_cell<DIM>();
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int mem = blockIdx.y;
+    if (c >= N || member_off(mb, mem)) return;
+    J += (size_t)mem * mb.js;
+    Jp += (size_t)mem * mb.jps;
     T out[4 * NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s)
@@ -99,9 +102,10 @@ __global__ void __launch_bounds__(256) repack_kernel(int N, const T* __restrict_
 }
 
 template <typename T>
-cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s) {
-    if (g.dim == 3) repack_kernel<T, 3><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, J, rec_of, Jp);
-    else repack_kernel<T, 2><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, J, rec_of, Jp);
+cudaError_t launch_repack(const Geom& g, const T* J, const int* rec_of, T* Jp, cudaStream_t s, const Members& mb) {
+    const dim3 grid((g.N + 255) / 256, mb.count);
+    if (g.dim == 3) repack_kernel<T, 3><<<grid, 256, 0, s>>>(g.N, J, rec_of, Jp, mb);
+    else repack_kernel<T, 2><<<grid, 256, 0, s>>>(g.N, J, rec_of, Jp, mb);
     return cudaGetLastError();
 }
 
@@ -137,8 +141,13 @@ template <typename T>
 __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                          const int* __restrict__ lev_off, const T* __restrict__ J,
                                                          int packed, T* __restrict__ coef, int ring_cells,
-                                                         int* flags) {
+                                                         int* flags, Members mb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    J += (size_t)mem * (packed ? mb.jps : mb.js);
+    coef += (size_t)mem * mb.cfs;
+    flags += mem;
     const SubInfo sd = subs[blockIdx.x];
     int* lo = reinterpret_cast<int*>(smem_raw);
     const int lev_words = (sd.nlev + 1 + 3) & ~3;
@@ -220,13 +229,14 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
 template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                               const T* J, int packed, T* coef, int threads, int ring_cells, size_t smem_bytes,
-                              int* flags, cudaStream_t s) {
+                              int* flags, cudaStream_t s, const Members& mb) {
     static std::atomic<size_t> attr_bytes{0};
     if (smem_bytes > 48 * 1024) {
         cudaError_t e = ensure_smem_limit((const void*)ras_factor_kernel<T>, smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
-    ras_factor_kernel<T><<<nsub, threads, smem_bytes, s>>>(g, subs, lev_off, J, packed, coef, ring_cells, flags);
+    ras_factor_kernel<T><<<dim3(nsub, mb.count), threads, smem_bytes, s>>>(g, subs, lev_off, J, packed, coef,
+                                                                          ring_cells, flags, mb);
     return cudaGetLastError();
 }
 
@@ -322,10 +332,17 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
                                                         const int* __restrict__ lev_off,
                                                         const T* __restrict__ coef, const T* __restrict__ r,
                                                         T* __restrict__ z, int ras_type, T* gscratch,
-                                                        RasLaunch L, int* err) {
+                                                        RasLaunch L, int* err, Members mb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;   // consumer / producer gave up on a wait
     __shared__ int s_issued, s_consumed;
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    coef += (size_t)mem * mb.cfs;
+    r += (size_t)mem * mb.vs;
+    z += (size_t)mem * mb.vs;
+    if (gscratch) gscratch += (size_t)mem * mb.ss;
+    err += mem;
     const SubInfo sd = subs[blockIdx.x];
     const int N = g.N;
     const int PW = ras_pitch(sd.W), PH = sd.H + 4;
@@ -571,11 +588,18 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                                                             const int* __restrict__ lev_off,
                                                             const T* __restrict__ coef, const T* __restrict__ r,
                                                             T* __restrict__ z, int ras_type, T* __restrict__ gscratch,
-                                                            RasLaunch L, int* err) {
+                                                            RasLaunch L, int* err, Members mb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;
     __shared__ int s_issued, s_consumed;
     __shared__ volatile int s_done;             // consumer steps completed (forward result in yg)
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    coef += (size_t)mem * mb.cfs;
+    r += (size_t)mem * (PRE ? mb.rgs : mb.vs);   // PRE: r is the gathered right-hand side
+    z += (size_t)mem * mb.vs;
+    gscratch += (size_t)mem * mb.ss;
+    err += mem;
     const SubInfo sd = subs[blockIdx.x];
     const int N = g.N;
     const int W = sd.W, H = sd.H;
@@ -826,9 +850,12 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
 template <typename T>
 __global__ void __launch_bounds__(256) ras_gather_kernel(int N, const T* __restrict__ r, const int* __restrict__ rec_of,
                                                          const unsigned char* __restrict__ own_of, int right,
-                                                         T* __restrict__ rg) {
+                                                         T* __restrict__ rg, Members mb) {
     const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= N) return;
+    const int mem = blockIdx.y;
+    if (c >= N || member_off(mb, mem)) return;
+    r += (size_t)mem * mb.vs;
+    rg += (size_t)mem * mb.rgs;
     const V2<T> val{r[c], r[N + c]};
     const int oq = own_of[c];
 #pragma unroll
@@ -841,23 +868,25 @@ __global__ void __launch_bounds__(256) ras_gather_kernel(int N, const T* __restr
 
 template <typename T>
 cudaError_t launch_ras_gather(const Geom& g, const T* r, const int* rec_of, const unsigned char* own_of,
-                              int ras_type, T* rg, cudaStream_t s) {
-    ras_gather_kernel<T><<<(g.N + 255) / 256, 256, 0, s>>>(g.N, r, rec_of, own_of, ras_type == ACAC_RAS_RIGHT ? 1 : 0,
-                                                         rg);
+                              int ras_type, T* rg, cudaStream_t s, const Members& mb) {
+    ras_gather_kernel<T><<<dim3((g.N + 255) / 256, mb.count), 256, 0, s>>>(
+        g.N, r, rec_of, own_of, ras_type == ACAC_RAS_RIGHT ? 1 : 0, rg, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
-                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s) {
+                             const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s,
+                             const Members& mb) {
     static std::atomic<size_t> attr_bytes{0};
+    const dim3 grid(nsub, mb.count);
     if (!L.window) {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
     if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
+        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
         if (e != cudaSuccess) return e;
     }
     if (L.window) {
@@ -868,15 +897,15 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
         // float: r gathered beforehand (the producer keeps up only with contiguous copies);
         // double: the producer gathers r itself (the consumers' FP64 work leaves it time)
         if (rg)
-            ras_apply_win_kernel<T, true><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, rg, z, ras_type,
-                                                                              gscratch, L, err);
+            ras_apply_win_kernel<T, true><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, rg, z, ras_type,
+                                                                              gscratch, L, err, mb);
         else
-            ras_apply_win_kernel<T, false><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type,
-                                                                               gscratch, L, err);
+            ras_apply_win_kernel<T, false><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type,
+                                                                               gscratch, L, err, mb);
         return cudaGetLastError();
     }
-    ras_apply_kernel<T><<<nsub, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
-                                                            err);
+    ras_apply_kernel<T><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
+                                                            err, mb);
     return cudaGetLastError();
 }
 
@@ -903,7 +932,12 @@ template <typename T>
 __global__ void __launch_bounds__(512) ras_factor3_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                           const int* __restrict__ lev_off, const int* __restrict__ cells,
                                                           const int* __restrict__ pos, const T* __restrict__ J,
-                                                          int packed, T* coef, int* flags) {
+                                                          int packed, T* coef, int* flags, Members mb) {
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    J += (size_t)mem * (packed ? mb.jps : mb.js);
+    coef += (size_t)mem * mb.cfs;
+    flags += mem;
     const SubInfo sd = subs[blockIdx.x];
     const int* lo = lev_off + sd.lev_base;
     const int* cl = cells + sd.cell_base;
@@ -996,10 +1030,17 @@ __global__ void __launch_bounds__(1024) ras_apply3_kernel(Geom g, const SubInfo*
                                                          const int* __restrict__ lev_off, const int* __restrict__ cells,
                                                          const T* __restrict__ coef, const T* __restrict__ r,
                                                          T* __restrict__ z, int ras_type, T* gscratch, RasLaunch L,
-                                                         int* err) {
+                                                         int* err, Members mb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;
     __shared__ int s_issued, s_consumed;
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    coef += (size_t)mem * mb.cfs;
+    r += (size_t)mem * mb.vs;
+    z += (size_t)mem * mb.vs;
+    if (gscratch) gscratch += (size_t)mem * mb.ss;
+    err += mem;
     const SubInfo sd = subs[blockIdx.x];
     const int* cl = cells + sd.cell_base;
     const int N = g.N;
@@ -1161,43 +1202,45 @@ __global__ void __launch_bounds__(1024) ras_apply3_kernel(Geom g, const SubInfo*
 template <typename T>
 cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                                const int* pos, const T* J, int packed, T* coef, int threads, int* flags,
-                               cudaStream_t s) {
-    ras_factor3_kernel<T><<<nsub, threads, 0, s>>>(g, subs, lev_off, cells, pos, J, packed, coef, flags);
+                               cudaStream_t s, const Members& mb) {
+    ras_factor3_kernel<T><<<dim3(nsub, mb.count), threads, 0, s>>>(g, subs, lev_off, cells, pos, J, packed, coef,
+                                                                   flags, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
-                              int* err, cudaStream_t s) {
+                              int* err, cudaStream_t s, const Members& mb) {
     static std::atomic<size_t> attr_bytes{0};
     {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply3_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
     if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
+        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
         if (e != cudaSuccess) return e;
     }
-    ras_apply3_kernel<T><<<nsub, L.threads, L.smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z, ras_type,
-                                                              gscratch, L, err);
+    ras_apply3_kernel<T><<<dim3(nsub, mb.count), L.threads, L.smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z,
+                                                                              ras_type, gscratch, L, err, mb);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                    \
-    template cudaError_t launch_repack<T>(const Geom&, const T*, const int*, T*, cudaStream_t);       \
+    template cudaError_t launch_repack<T>(const Geom&, const T*, const int*, T*, cudaStream_t, const Members&); \
     template cudaError_t launch_ras_factor<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
-                                              int, T*, int, int, size_t, int*, cudaStream_t);       \
+                                              int, T*, int, int, size_t, int*, cudaStream_t, const Members&); \
     template cudaError_t launch_ras_gather<T>(const Geom&, const T*, const int*, const unsigned char*, \
-                                              int, T*, cudaStream_t);                                   \
+                                              int, T*, cudaStream_t, const Members&);                   \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, const T*, int*, \
-                                             cudaStream_t);                                           \
+                                             cudaStream_t, const Members&);                           \
     template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*,    \
-                                               const int*, const T*, int, T*, int, int*, cudaStream_t);      \
+                                               const int*, const T*, int, T*, int, int*, cudaStream_t,      \
+                                               const Members&);                                             \
     template cudaError_t launch_ras_apply3<T>(const Geom&, int, const SubInfo*, const int*, const int*,     \
                                               const T*, const T*, T*, int, const RasLaunch&, T*, int*,     \
-                                              cudaStream_t);
+                                              cudaStream_t, const Members&);
 INST(double)
 INST(float)
 #undef INST

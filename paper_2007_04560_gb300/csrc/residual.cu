@@ -304,8 +304,25 @@ __device__ __forceinline__ T dphi_from_args(const SeriesArgs& s, int K) {
 }
 
 template <int DIM, bool PRE, int CM>
-__global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) {
+__global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, Members mb) {
     const int N = g.N;
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    member_coef(mb, m, k);
+    a.X += (size_t)m * mb.vs;
+    a.X0 += (size_t)m * mb.vs;
+    if (PRE) a.L0 += (size_t)m * mb.vs;
+    a.G += (size_t)m * mb.gs;
+    a.flags += m;
+    if (CM == 1) {
+        const size_t o = (size_t)m * mb.cs;
+        a.cache_d = Cache<double>{a.cache_d.c + o, a.cache_d.cu + o, a.cache_d.cv + o, a.cache_d.Gu + o,
+                                  a.cache_d.Gv + o, a.cache_d.du + o, a.cache_d.xc + o};
+    } else if (CM == 2) {
+        const size_t o = (size_t)m * mb.cs;
+        a.cache_f = Cache<float>{a.cache_f.c + o, a.cache_f.cu + o, a.cache_f.cv + o, a.cache_f.Gu + o,
+                                 a.cache_f.Gv + o, a.cache_f.du + o, a.cache_f.xc + o};
+    }
     const double* __restrict__ Xu = a.X;
     const double* __restrict__ Xv = a.X + N;
     const double* __restrict__ Pu = a.X0;
@@ -389,9 +406,16 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a) 
 
 // Trial state of the line search: Xt_u = X_u + lam (S_u + shift), Xt_v = X_v + lam S_v,
 // with flag bit 1 when some u+v or u-v leaves (0, 1).
-__global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
+__global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a, Members mb) {
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    a.X += (size_t)m * mb.vs;
+    a.S += (size_t)m * mb.vs;
+    a.Xt += (size_t)m * mb.vs;
+    a.flags += m;
+    if (mb.k) a.lam = mb.k[m].lam;
     int flag = 0;
-    const double shift = a.shift_sum ? a.shift_sum[0] * a.shift_scale : a.shift;
+    const double shift = a.shift_sum ? a.shift_sum[(size_t)m * mb.rs] * a.shift_scale : a.shift;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         const double u = fma(a.lam, a.S[c] + shift, a.X[c]);
         const double v = fma(a.lam, a.S[N + c], a.X[N + c]);
@@ -404,9 +428,21 @@ __global__ void __launch_bounds__(256) trial_kernel(int N, ResidualArgs a) {
 
 // ---------------------------------------------------------------- pass B
 template <int DIM>
-__global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho, ResidualArgs a) {
+__global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho, ResidualArgs a, Members mb) {
     __shared__ double sh[32];
     const int N = g.N;
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    if (mb.k) {
+        // correctly rounded, as the host forms them for the by-value arguments
+        idt = 1.0 / mb.k[m].dt;
+        irho = 1.0 / mb.k[m].rho;
+    }
+    a.X += (size_t)m * mb.vs;
+    a.X0 += (size_t)m * mb.vs;
+    a.G += (size_t)m * mb.gs;
+    a.F += (size_t)m * mb.vs;
+    a.red = member_red(a.red, mb, m);
     const double* __restrict__ X1 = a.X;
     const double* __restrict__ Gu = a.G;
     const double* __restrict__ Gv = a.G + N;
@@ -438,12 +474,14 @@ static int grid_for(long long n, int threads) {
     return (int)(b < RED_BLOCKS ? (b < 1 ? 1 : b) : RED_BLOCKS);
 }
 
-cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
+cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s,
+                              const Members& mb) {
     cudaError_t e = set_taylor_constants(k.S);
     if (e != cudaSuccess) return e;
     const int nb = grid_for(g.N, 256);
     auto go = [&](auto dimc, auto prec, auto cmc) {
-        g_kernel<decltype(dimc)::value, decltype(prec)::value, decltype(cmc)::value><<<nb, 256, 0, s>>>(g, k, a);
+        g_kernel<decltype(dimc)::value, decltype(prec)::value, decltype(cmc)::value><<<dim3(nb, mb.count), 256, 0, s>>>(
+            g, k, a, mb);
     };
     using I2 = std::integral_constant<int, 2>;
     using I3 = std::integral_constant<int, 3>;
@@ -469,8 +507,13 @@ cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& 
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(256) laplacian_kernel(Geom g, const double* __restrict__ X, double* __restrict__ L) {
+__global__ void __launch_bounds__(256) laplacian_kernel(Geom g, const double* __restrict__ X, double* __restrict__ L,
+                                                        Members mb) {
     const int N = g.N;
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    X += (size_t)m * mb.vs;
+    L += (size_t)m * mb.vs;
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < N; c += gridDim.x * blockDim.x) {
         int x, y, z;
         decode_cell<DIM>(g, c, x, y, z);
@@ -488,23 +531,25 @@ __global__ void __launch_bounds__(256) laplacian_kernel(Geom g, const double* __
     }
 }
 
-cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s) {
-    const int nb = grid_for(g.N, 256);
-    if (g.dim == 3) laplacian_kernel<3><<<nb, 256, 0, s>>>(g, X, L);
-    else laplacian_kernel<2><<<nb, 256, 0, s>>>(g, X, L);
+cudaError_t launch_laplacian(const Geom& g, const double* X, double* L, cudaStream_t s, const Members& mb) {
+    const dim3 nb(grid_for(g.N, 256), mb.count);
+    if (g.dim == 3) laplacian_kernel<3><<<nb, 256, 0, s>>>(g, X, L, mb);
+    else laplacian_kernel<2><<<nb, 256, 0, s>>>(g, X, L, mb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s) {
-    trial_kernel<<<grid_for(g.N, 256), 256, 0, s>>>(g.N, a);
+cudaError_t launch_trial(const Geom& g, const ResidualArgs& a, cudaStream_t s, const Members& mb) {
+    trial_kernel<<<dim3(grid_for(g.N, 256), mb.count), 256, 0, s>>>(g.N, a, mb);
     return cudaGetLastError();
 }
 
-cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s) {
+cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& a, cudaStream_t s,
+                              const Members& mb) {
     // 1/dt and 1/rho on the host (correctly rounded, as a kernel division would be)
     const double idt = 1.0 / a.dt, irho = 1.0 / k.rho;
-    if (g.dim == 3) f_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, idt, irho, a);
-    else f_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, idt, irho, a);
+    const dim3 nb(red_grid(g.N), mb.count);
+    if (g.dim == 3) f_kernel<3><<<nb, RED_THREADS, 0, s>>>(g, idt, irho, a, mb);
+    else f_kernel<2><<<nb, RED_THREADS, 0, s>>>(g, idt, irho, a, mb);
     return cudaGetLastError();
 }
 
@@ -515,9 +560,15 @@ __device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_l
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
 template <int DIM>
 __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const double* __restrict__ X,
-                                                     Red red, int* flags) {
+                                                     Red red, int* flags, Members mb) {
     __shared__ double sh[32];
     const int N = g.N;
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    member_coef(mb, m, k);
+    X += (size_t)m * mb.vs;
+    flags += m;
+    red = member_red(red, mb, m);
     const double* __restrict__ U = X;
     const double* __restrict__ V = X + N;
     double e_acc = 0.0, m_acc = 0.0;
@@ -554,13 +605,15 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
     double t = block_sum_red(e_acc, sh);
     if (threadIdx.x == 0) red.partial[blockIdx.x] = t * g.vol;
     t = block_sum_red(m_acc, sh);
-    if (threadIdx.x == 0) red.partial[RED_BLOCKS + blockIdx.x] = t * g.vol;
+    if (threadIdx.x == 0) red.partial[gridDim.x + blockIdx.x] = t * g.vol;
     finish_reduction(red, 2, sh);
 }
 
-cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s) {
-    if (g.dim == 3) energy_kernel<3><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, red, flags);
-    else energy_kernel<2><<<red_grid(g.N), RED_THREADS, 0, s>>>(g, k, X, red, flags);
+cudaError_t launch_energy(const Geom& g, const Coef& k, const double* X, Red red, int* flags, cudaStream_t s,
+                          const Members& mb) {
+    const dim3 nb(red_grid(g.N), mb.count);
+    if (g.dim == 3) energy_kernel<3><<<nb, RED_THREADS, 0, s>>>(g, k, X, red, flags, mb);
+    else energy_kernel<2><<<nb, RED_THREADS, 0, s>>>(g, k, X, red, flags, mb);
     return cudaGetLastError();
 }
 
@@ -677,7 +730,7 @@ __global__ void __launch_bounds__(256) param_grad_kernel(Geom g, Coef k, const d
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
         const double t = block_sum_red(acc[v], sh);
-        if (threadIdx.x == 0) red.partial[(size_t)v * RED_BLOCKS + blockIdx.x] = t;
+        if (threadIdx.x == 0) red.partial[(size_t)v * gridDim.x + blockIdx.x] = t;
     }
     finish_reduction(red, 4, sh);
 }
@@ -738,7 +791,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(Geom g, Coef k, const do
 #pragma unroll
     for (int v = 0; v < 5; ++v) {
         const double t = block_sum_red(acc[v], sh);
-        if (threadIdx.x == 0) red.partial[(size_t)v * RED_BLOCKS + blockIdx.x] = t * g.vol;
+        if (threadIdx.x == 0) red.partial[(size_t)v * gridDim.x + blockIdx.x] = t * g.vol;
     }
     finish_reduction(red, 5, sh);
 }

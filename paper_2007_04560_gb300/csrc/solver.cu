@@ -1,99 +1,32 @@
 // Host side of the acac C ABI: handle and workspace, the inexact Newton iteration
 // with line search (Sec. 3.1, Eq. newton), restarted right-preconditioned GMRES
-// (Sec. 3.1, Eq. hjacobi; Hessenberg and Givens rotations on the host in double),
-// the subdomain tables of the Schwarz preconditioner, and the adaptive time step
-// of Sec. 3.2 (Eq. sencondt, with retry on divergence and eta doubling).
+// (Sec. 3.1, Eq. hjacobi), the subdomain tables of the Schwarz preconditioner, and the
+// adaptive time step of Sec. 3.2 (Eq. sencondt, with retry on divergence and eta
+// doubling).
+//
+// A handle holds B >= 1 independent problems (ensemble members) of one grid and one box
+// decomposition and solves them in lockstep: every kernel launch covers all members
+// (a grid dimension indexes the member), and per-member masks on the device say which
+// members take part (those still iterating in Newton, in the line search, in the GMRES
+// cycle).  The Givens rotations, the convergence test and the back substitution of
+// GMRES run on the device, so a restart cycle is launched without a host read-back per
+// Arnoldi step.  A single problem is the case B = 1.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
-#include <atomic>
 #include <chrono>
-#include <condition_variable>
-#include <functional>
-#include <mutex>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "acac_internal.cuh"
 
 using namespace acac;
 
-// Fixed set of host threads that runs fn(0..count-1) concurrently (the calling thread
-// takes part).  The members of an ensemble each drive their own solve from the host
-// (Newton control, GMRES Givens rotations, scalar read-backs), so stepping them from
-// separate threads lets their kernels, issued on separate streams, share the GPU.
-class MemberPool {
-public:
-    MemberPool(int nthreads, int device) : device_(device) {
-        for (int i = 0; i < nthreads; ++i) threads_.emplace_back([this] { worker(); });
-    }
-    ~MemberPool() {
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            stop_ = true;
-        }
-        cv_.notify_all();
-        for (auto& t : threads_) t.join();
-    }
-    void run(int count, const std::function<void(int)>& fn) {
-        {
-            std::lock_guard<std::mutex> lock(mu_);
-            fn_ = &fn;
-            count_ = count;
-            next_.store(0);
-            busy_ = (int)threads_.size();
-            ++gen_;
-        }
-        cv_.notify_all();
-        drain(fn, count);
-        std::unique_lock<std::mutex> lock(mu_);
-        done_cv_.wait(lock, [this] { return busy_ == 0; });
-        fn_ = nullptr;
-    }
-
-private:
-    void drain(const std::function<void(int)>& fn, int count) {
-        for (int i = next_.fetch_add(1); i < count; i = next_.fetch_add(1)) fn(i);
-    }
-    void worker() {
-        cudaSetDevice(device_);
-        long seen = 0;
-        while (true) {
-            const std::function<void(int)>* fn;
-            int count;
-            {
-                std::unique_lock<std::mutex> lock(mu_);
-                cv_.wait(lock, [&] { return stop_ || gen_ != seen; });
-                if (stop_) return;
-                seen = gen_;
-                fn = fn_;
-                count = count_;
-            }
-            drain(*fn, count);
-            {
-                std::lock_guard<std::mutex> lock(mu_);
-                --busy_;
-            }
-            done_cv_.notify_all();
-        }
-    }
-    int device_;
-    std::vector<std::thread> threads_;
-    std::mutex mu_;
-    std::condition_variable cv_, done_cv_;
-    const std::function<void(int)>* fn_ = nullptr;
-    int count_ = 0;
-    std::atomic<int> next_{0};
-    int busy_ = 0;
-    long gen_ = 0;
-    bool stop_ = false;
-};
-
 // One captured GMRES (Arnoldi) iteration: the graph and, per kernel node, the
-// launch accounting (and, when profiling, the event pair recorded around it).
+// launch accounting (per member taking part) and, when profiling, the event pair
+// recorded around it.
 struct GraphRec {
     int id;
     double bytes, flops;
@@ -104,14 +37,42 @@ struct IterGraph {
     std::vector<GraphRec> recs;
 };
 
+// Per-member device scalars (stride RS doubles): the two Gram-Schmidt passes' Hessenberg
+// columns, ||w||^2, the GMRES combination y, the mass-correction shift, and a few slots
+// for other reductions (their results land at offset 0).
+constexpr int RS_H0 = 0;
+constexpr int RS_H1 = MAX_RESTART + 1;
+constexpr int RS_NRM = 2 * (MAX_RESTART + 1);
+constexpr int RS_Y = 3 * (MAX_RESTART + 1);
+constexpr int RS_SHIFT = 4 * (MAX_RESTART + 1);
+constexpr int RS = 4 * (MAX_RESTART + 1) + 8;
+static_assert(sizeof(GmresHead) == 5 * sizeof(double), "GmresHead holds 5 doubles");
+
+// Masks (B ints each on the device): the members a launch covers.
+enum { MK_NEWTON = 0, MK_LS, MK_CYC, MK_GON, MK_RESTART, MK_AUX, MK_COUNT };
+
 struct acac_handle {
     acac_params p;
     Geom g;
-    Coef k;
+    Coef k;                     // member 0's coefficients (the by-value scalars of single-problem calls)
+    int B = 1;                  // members
+    Members mb;                 // member strides and per-member scalars (mb.on set per launch)
     cudaStream_t stream;        // private stream of all the handle's work
     cudaStream_t user_stream;   // the caller's stream (ordered with `stream` at entry and exit)
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-    void* jk_dev = nullptr;     // JacK<T> of the current linearisation
+    void* jk_dev = nullptr;     // JacK<T> per member of the current linearisation
+    MemberK* mk_dev = nullptr;  // per-member coefficients, dt, line-search step
+    std::vector<MemberK> mk;    // host copy
+    int* masks = nullptr;       // MK_COUNT x B
+    std::vector<int> mask_host[MK_COUNT];
+    int mask_count[MK_COUNT] = {0};
+    int nact = 1;               // members taking part in the launch being issued
+    int ncyc = 1;               // members in the current GMRES cycle
+    GmresHead* ghead_dev = nullptr;
+    GmresWork* gwork_dev = nullptr;
+    int* kcnt_dev = nullptr;    // Arnoldi steps of each member's last cycle
+    std::vector<GmresHead> ghead;
+    int gm_hint = 0;            // steps the previous GMRES cycle took (where to look first)
     // CUDA graphs of the Arnoldi iterations (index j), captured on first use
     std::vector<IterGraph> graphs;
     unsigned graphs_prof = 0;   // timing mask the graphs were captured with
@@ -120,24 +81,26 @@ struct acac_handle {
     bool mixed;
     size_t N;
     size_t ksz;                 // sizeof Krylov element
-    // FP64 state
+    // FP64 state (B members at stride mb.vs)
     double *X, *X0, *Xprev, *Xt, *F, *S, *G, *b, *r, *tmpd, *stage;
     double* lap0 = nullptr;     // Laplacians of X0 during a Newton solve (pass A reads them)
-    double* shift_dev = nullptr;   // sum(u^n - u - S_u) of the current Newton direction
     bool factor_check = false;     // a deferred factorization's flags are still to be read
     bool cache_fresh = false;      // the last residual evaluation wrote the linearisation cache
     // Krylov precision buffers
     void *V, *w, *kt, *jtmp, *cache, *J, *coef, *gscratch;
     void* Zb = nullptr;         // preconditioned basis z_j = M^-1 v_j, restart x ldV (the
                                 // solution update is Z y: no preconditioner apply per solve)
-    size_t ldV;
+    size_t ldV;                 // Krylov basis stride: B members x mb.vs
     // reductions
-    double* partial;            // RED_BLOCKS x (MAX_RESTART + 3)
-    double* red;                // device results
-    double* host;               // pinned host mirror of red
-    int* flags;
-    int* host_flags;
-    unsigned* counter;          // reduction counter (zero between launches)
+    double* partial;            // per member: (MAX_RESTART + 3) quantities x blocks
+    double* red;                // device results, RS per member
+    double* host;               // pinned host mirror of per-member results
+    int* flags;                 // [0, B): per-member flags; [B, 2B): sticky apply timeouts
+    int* host_flags;            // pinned, 2B
+    unsigned* counter;          // reduction counters, one per member (zero between launches)
+    // per-member results of the last residual evaluation
+    std::vector<double> fn;
+    std::vector<int> fl;
     // Schwarz tables
     std::vector<SubInfo> subs;
     std::vector<int> lev;
@@ -171,12 +134,10 @@ struct acac_handle {
     double nbox;                // cells of all subdomain boxes (overlap counted)
     int ras_maxlev, ras_maxcnt;
     size_t ras_maxpad;
-    // time stepping
-    double t, dt_prev, eta;
-    int nstep;
-    bool have_prev;
-    // counters of the current solve
-    int ls_cuts, n_factor;
+    // time stepping, per member
+    std::vector<double> t, dt_prev, eta;
+    std::vector<int> nstep;
+    std::vector<char> have_prev;
     // kernel launch counts and (when enabled) CUDA-event timings per kernel
     bool prof_on;
     unsigned prof_mask = 0;     // kernel classes timed with events (bit = ACAC_K_*)
@@ -191,13 +152,6 @@ struct acac_handle {
     // and one stencil matrix in the Krylov precision
     double* adj = nullptr;
     void* adjJ = nullptr;
-    // ensemble (batch > 1): independent member problems, each a batch-1 handle on its
-    // own stream; this handle then only owns them, the staging buffer and the pool
-    std::vector<acac_handle*> members;
-    std::vector<cudaStream_t> member_streams;
-    std::vector<cudaEvent_t> member_done;
-    cudaEvent_t member_start = nullptr;
-    MemberPool* member_pool = nullptr;
 };
 
 namespace {
@@ -242,15 +196,16 @@ void prof_collect(acac_handle* h) {
     h->pending.clear();
 }
 
-// Brackets one kernel launch: counts it and, when profiling, records CUDA events
-// around it on the handle's stream.
+// Brackets one kernel launch: counts it (bytes and flops per member taking part) and,
+// when profiling, records CUDA events around it on the handle's stream.
 struct KScope {
     acac_handle* h;
     cudaEvent_t b;
     KScope(acac_handle* h_, int id, double bytes = 0.0, double flops = 0.0) : h(h_), b(nullptr) {
         if (h->capture) {
-            // inside a graph capture: the accounting happens at every replay, and the
-            // events (when profiling) become event-record nodes of the graph
+            // inside a graph capture: the accounting happens at every replay (scaled by the
+            // members of the cycle then), and the events (when profiling) become
+            // event-record nodes of the graph
             GraphRec r{id, bytes, flops, nullptr, nullptr};
             if (h->prof_on && (h->prof_mask >> id & 1u)) {
                 // events come from the pool, stocked before the capture began
@@ -266,8 +221,8 @@ struct KScope {
             return;
         }
         h->launches[id]++;
-        h->kernel_bytes[id] += bytes;
-        h->kernel_flops[id] += flops;
+        h->kernel_bytes[id] += bytes * h->nact;
+        h->kernel_flops[id] += flops * h->nact;
         if (h->prof_on && (h->prof_mask >> id & 1u)) {
             cudaEvent_t a = take_event(h);
             b = take_event(h);
@@ -283,8 +238,7 @@ struct KScope {
 };
 
 // Orders the handle's private stream after the caller's stream on entry to a C-ABI
-// call and the caller's stream after the private stream on exit.  (An ensemble
-// handle works on the caller's stream itself and has no join events.)
+// call and the caller's stream after the private stream on exit.
 struct Join {
     acac_handle* h;
     explicit Join(acac_handle* h_) : h(h_) {
@@ -315,13 +269,14 @@ void free_graphs(acac_handle* h) {
         KScope ks_(h, id);           \
         CU(call);                    \
     } while (0)
-// Same, with the launch's algorithmic HBM bytes and floating-point operations.
+// Same, with the launch's algorithmic HBM bytes and floating-point operations per member.
 #define KLA(id, bytes, flops, call)          \
     do {                                     \
         KScope ks_(h, id, (bytes), (flops)); \
         CU(call);                            \
     } while (0)
 
+// Member 0's cache fields; member m's are at m * mb.cs (member_cache).
 template <typename T>
 Cache<T> cache_of(acac_handle* h) {
     T* base = (T*)h->cache;
@@ -329,9 +284,73 @@ Cache<T> cache_of(acac_handle* h) {
     return Cache<T>{base, base + N, base + 2 * N, base + 3 * N, base + 4 * N, base + 5 * N, base + 6 * N};
 }
 
-// Reduction target: partials at h->partial + poff, results at out.
-Red red_to(acac_handle* h, double* out, size_t poff = 0) { return Red{h->partial + poff, out, h->counter}; }
+// Reduction target: partials, member results at out (+ m * RS), counters.
+Red red_to(acac_handle* h, double* out) { return Red{h->partial, out, h->counter}; }
 
+// ---------------------------------------------------------------- members
+// Every member takes part (single-problem calls, whole-ensemble work).
+Members all_members(acac_handle* h) {
+    h->nact = h->B;
+    return h->mb;
+}
+
+// The members of mask `slot`.
+Members on_mask(acac_handle* h, int slot) {
+    Members mb = h->mb;
+    mb.on = h->masks + (size_t)slot * h->B;
+    h->nact = slot == MK_GON ? h->ncyc : h->mask_count[slot];
+    return mb;
+}
+
+// Writes mask `slot` (when it changed: the copy from pageable memory is staged at once, so
+// the host vector may change right after).
+void set_mask(acac_handle* h, int slot, const std::vector<int>& v) {
+    int cnt = 0;
+    for (int x : v) cnt += x ? 1 : 0;
+    h->mask_count[slot] = cnt;
+    if (h->mask_host[slot] == v) return;
+    h->mask_host[slot] = v;
+    CU(cudaMemcpyAsync(h->masks + (size_t)slot * h->B, h->mask_host[slot].data(), sizeof(int) * h->B,
+                       cudaMemcpyHostToDevice, h->stream));
+}
+
+int any_of(const std::vector<int>& v) {
+    for (int x : v)
+        if (x) return 1;
+    return 0;
+}
+
+// Per-member scalars to the device: coefficients, dt and line-search step, and the
+// Jacobian scalars formed from them.
+template <typename T>
+void write_members(acac_handle* h) {
+    CU(cudaMemcpyAsync(h->mk_dev, h->mk.data(), sizeof(MemberK) * h->B, cudaMemcpyHostToDevice, h->stream));
+    std::vector<JacK<T>> jk(h->B);
+    for (int m = 0; m < h->B; ++m) {
+        const MemberK& q = h->mk[m];
+        jk[m] = jac_consts<T>(Coef{q.alpha, q.beta, q.theta, q.gamma, q.rho, h->p.taylor_S}, q.dt);
+    }
+    CU(cudaMemcpyAsync(h->jk_dev, jk.data(), sizeof(JacK<T>) * h->B, cudaMemcpyHostToDevice, h->stream));
+}
+void write_members_any(acac_handle* h) {
+    if (h->mixed) write_members<float>(h);
+    else write_members<double>(h);
+}
+// A single problem's dt (member 0), for the component entry points.
+void set_dt0(acac_handle* h, double dt) {
+    for (auto& q : h->mk) q.dt = dt;
+    write_members_any(h);
+}
+
+// n scalars of every member from red + off into host[m * n + i]; synchronises.
+void read_member_scalars(acac_handle* h, size_t off, int n) {
+    CU(cudaMemcpy2DAsync(h->host, sizeof(double) * n, h->red + off, sizeof(double) * RS, sizeof(double) * n,
+                         h->B, cudaMemcpyDeviceToHost, h->stream));
+    CU(cudaStreamSynchronize(h->stream));
+    prof_collect(h);
+}
+
+// Member 0's first scalars (single-problem helpers).
 double read_scalars(acac_handle* h, int n) {
     CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
     CU(cudaStreamSynchronize(h->stream));
@@ -339,21 +358,23 @@ double read_scalars(acac_handle* h, int n) {
     return h->host[0];
 }
 
-int read_flags(acac_handle* h) {
-    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    CU(cudaStreamSynchronize(h->stream));
-    prof_collect(h);
-    return *h->host_flags;
+// Per-member flags (both halves) to host_flags; the caller synchronises.
+void fetch_flags(acac_handle* h) {
+    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int) * 2 * h->B, cudaMemcpyDeviceToHost, h->stream));
 }
 
-// ||F(X)|| (or of the trial point X + lam (S + shift e_u)) and the G buffer.
-double eval_residual(acac_handle* h, const double* X, const double* S, double lam, double shift,
-                     double dt, int* flags_out, bool use_lap0 = false, const double* shift_sum = nullptr,
-                     bool fill_cache = false) {
-    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+// F at the members of mask `slot` (slot < 0: every member): at X, or (trial) at the
+// line-search state X + lam (S + shift e_u) with lam and the shift per member on the
+// device.  With fill_cache pass A also writes the linearisation cache at the evaluated
+// state, which the next Newton iteration uses if the line search accepts that state.
+// Sets h->fn[m] = ||F|| and h->fl[m] (bit 0: a midpoint left the admissible set, bit 1:
+// the trial state did, bit 3: a Schwarz apply gave up a bounded wait, sticky) for the
+// members of the mask.
+void eval_residual(acac_handle* h, int slot, const double* X, bool trial, bool use_lap0 = false,
+                   bool fill_cache = false) {
+    const Members mb = slot < 0 ? all_members(h) : on_mask(h, slot);
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int) * h->B, h->stream));
     ResidualArgs a;
-    // with fill_cache pass A also writes the linearisation cache at the evaluated state, which
-    // the next Newton iteration uses if this state is accepted (the Newton loop's evaluations)
     if (fill_cache && use_lap0) {
         if (h->mixed) {
             a.cache_mode = 2;
@@ -364,14 +385,13 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
         }
     }
     h->cache_fresh = a.cache_mode != 0;
-    a.X = X; a.S = S; a.lam = lam; a.shift = shift; a.X0 = h->X0; a.dt = dt;
+    a.X = X; a.S = trial ? h->S : nullptr; a.lam = 0.0; a.shift = 0.0; a.X0 = h->X0; a.dt = h->mk[0].dt;
     a.L0 = use_lap0 ? h->lap0 : nullptr;
-    a.shift_sum = shift_sum;
+    a.shift_sum = trial ? h->red + RS_SHIFT : nullptr;
     a.shift_scale = 1.0 / (double)h->N;
     a.Xt = h->Xt; a.G = h->G; a.F = h->F; a.red = red_to(h, h->red); a.flags = h->flags;
-    if (S) {
-        // the line search's trial state X + lam (S + shift e_u), then F there
-        KLA(ACAC_K_VECTOR, 40.0 * h->N, 0.0, launch_trial(h->g, a, h->stream));
+    if (trial) {
+        KLA(ACAC_K_VECTOR, 40.0 * h->N, 0.0, launch_trial(h->g, a, h->stream, mb));
         a.X = h->Xt;
         a.S = nullptr;
     }
@@ -379,107 +399,109 @@ double eval_residual(acac_handle* h, const double* X, const double* S, double la
     // state, series arguments with one reciprocal, two table logarithms, four series of K = 4
     // terms, G and the mobility), charged as 2 flop-equivalents each (one DFMA slot)
     KLA(ACAC_K_RESIDUAL_G, 8.0 * h->N * 7 + (a.cache_mode ? 7.0 * h->ksz * h->N : 0.0), 226.0 * h->N,
-        launch_residual_g(h->g, h->k, a, h->stream));
-    KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream));
-    CU(cudaMemcpyAsync(h->host_flags, h->flags, 2 * sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    const double f2 = read_scalars(h, 1);
-    // bit 3: a Schwarz apply gave up a bounded wait (sticky flag of the handle)
-    *flags_out = h->host_flags[0] | (h->host_flags[1] ? 8 : 0);
-    return sqrt(f2);
-}
-
-// Scalars of the Jacobian action for the current (dt, coefficients), on the device.
-template <typename T>
-void set_jac(acac_handle* h, double dt) {
-    KL(ACAC_K_VECTOR, launch_set_jac<T>((JacK<T>*)h->jk_dev, h->k, dt, h->stream));
+        launch_residual_g(h->g, h->k, a, h->stream, mb));
+    KLA(ACAC_K_RESIDUAL_F, 8.0 * h->N * 9, 30.0 * h->N, launch_residual_f(h->g, h->k, a, h->stream, mb));
+    fetch_flags(h);
+    read_member_scalars(h, 0, 1);
+    for (int m = 0; m < h->B; ++m) {
+        h->fn[m] = sqrt(h->host[m]);
+        h->fl[m] = h->host_flags[m] | (h->host_flags[h->B + m] ? 8 : 0);
+    }
 }
 
 template <typename T>
-void jvp_action(acac_handle* h, const T* w, T* y) {
+void jvp_action(acac_handle* h, const Members& mb, const T* w, T* y) {
     const JacK<T>* kp = (const JacK<T>*)h->jk_dev;
     if (h->g.dim == 2 && sizeof(T) == 4) {
         // FP32: one tiled pass (HBM bound); FP64 keeps the two passes (FP64-pipe bound,
         // no halo recomputation)
         KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 11, 80.0 * h->N,
-            launch_jvp_tile<T>(h->g, kp, cache_of<T>(h), w, y, h->stream));
+            launch_jvp_tile<T>(h->g, kp, cache_of<T>(h), w, y, h->stream, mb));
         return;
     }
-    KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N, launch_jvp_g<T>(h->g, kp, cache_of<T>(h), w, (T*)h->jtmp, h->stream));
-    KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N, launch_jvp_f<T>(h->g, kp, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream));
+    KLA(ACAC_K_JVP_G, (double)sizeof(T) * h->N * 9, 32.0 * h->N,
+        launch_jvp_g<T>(h->g, kp, cache_of<T>(h), w, (T*)h->jtmp, h->stream, mb));
+    KLA(ACAC_K_JVP_F, (double)sizeof(T) * h->N * 10, 48.0 * h->N,
+        launch_jvp_f<T>(h->g, kp, cache_of<T>(h), w, (const T*)h->jtmp, y, h->stream, mb));
 }
 
 template <typename T>
-void jac_action(acac_handle* h, const T* w, T* y) {
+void jac_action(acac_handle* h, const Members& mb, const T* w, T* y) {
     if (h->p.jac_mode == ACAC_JAC_ASSEMBLED)
-        KLA(ACAC_K_SPMV, (double)sizeof(T) * h->N * 56, 104.0 * h->N, launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream));
+        KLA(ACAC_K_SPMV, (double)sizeof(T) * h->N * 56, 104.0 * h->N,
+            launch_spmv<T>(h->g, (const T*)h->J, w, y, h->stream, mb));
     else
-        jvp_action<T>(h, w, y);
+        jvp_action<T>(h, mb, w, y);
 }
 
 template <typename T>
-void precond(acac_handle* h, const T* r, T* z) {
+void precond(acac_handle* h, const Members& mb, const T* r, T* z) {
+    int* err = h->flags + h->B;   // sticky timeout flags
     if (h->p.subdomain_solver != ACAC_SUB_ILU0) {
         KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (4.0 * h->sblocks + 4.0 * h->scells + 4.0 * h->N),
             16.0 * h->sblocks,
             launch_sparse_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->sbox_dev, h->sshape_dev,
                                    (const T*)h->sval, (const T*)h->sdinv, r, z, h->p.ras_type, (T*)h->sy,
-                                   h->s_threads, h->s_asmem, h->stream));
+                                   h->s_threads, h->s_asmem, h->stream, mb));
         return;
     }
     if (h->g.dim == 3) {
         KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (104.0 * h->nbox + 4.0 * h->N), 200.0 * h->nbox,
             launch_ras_apply3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev,
                                  (const T*)h->coef, r, z, h->p.ras_type, h->ras_launch, (T*)h->gscratch,
-                                 h->flags + 1, h->stream));
+                                 err, h->stream, mb));
         return;
     }
     if (h->ras_launch.window && sizeof(T) == 4)
         KLA(ACAC_K_VECTOR, (double)sizeof(T) * (2.0 * h->N + 2.0 * h->nbox) + 17.0 * h->N, 0.0,
-            launch_ras_gather<T>(h->g, r, h->rec_of_dev, h->own_of_dev, h->p.ras_type, (T*)h->rg, h->stream));
+            launch_ras_gather<T>(h->g, r, h->rec_of_dev, h->own_of_dev, h->p.ras_type, (T*)h->rg, h->stream, mb));
     KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
         launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
                             h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch,
-                            sizeof(T) == 4 ? (const T*)h->rg : nullptr, h->flags + 1, h->stream));
+                            sizeof(T) == 4 ? (const T*)h->rg : nullptr, err, h->stream, mb));
 }
 
-// With defer, the pivot / timeout flags are not read here: the Newton loop's GMRES reads
-// them with its first scalar read-back (one host round trip fewer per step).
+// Subdomain factorizations of the members in mb.  With defer, the pivot / timeout flags
+// are read with the next GMRES read-back (one host round trip fewer per Newton step) and
+// ACAC_OK is returned; without, member 0's status.
 template <typename T>
-int factor(acac_handle* h, bool defer = false) {
-    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
+int factor(acac_handle* h, const Members& mb, bool defer = false) {
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int) * h->B, h->stream));
     auto done = [&](bool timeout_bit) -> int {
-        h->n_factor++;
         if (defer) {
             h->factor_check = true;
             return ACAC_OK;
         }
-        const int f = read_flags(h);
+        fetch_flags(h);
+        CU(cudaStreamSynchronize(h->stream));
+        prof_collect(h);
+        const int f = h->host_flags[0];
         return (timeout_bit && (f & 8)) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
     };
     if (h->p.subdomain_solver != ACAC_SUB_ILU0) {
         // A_k of every box from the stencil-diagonal Jacobian, then the block IKJ
         // elimination on the ILU(1) / ILU(2) / LU pattern
-        CU(cudaMemsetAsync(h->sval, 0, (size_t)h->sblocks * 4 * sizeof(T), h->stream));
+        CU(cudaMemsetAsync(h->sval, 0, (size_t)h->mb.cfs * h->B * sizeof(T), h->stream));
         KLA(ACAC_K_REPACK, (double)sizeof(T) * (4.0 * h->sblocks + 4.0 * (h->g.dim == 3 ? NSLOT3 : NSLOT) * h->N),
             0.0,
             launch_sparse_init<T>(h->g, (int)h->subs.size(), h->subs_dev, h->sbox_dev, h->sshape_dev,
-                                  (const T*)h->J, (T*)h->sval, h->stream));
+                                  (const T*)h->J, (T*)h->sval, h->stream, mb));
         KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 8.0 * h->sblocks, 0.0,
             launch_sparse_factor<T>((int)h->subs.size(), h->sbox_dev, h->sshape_dev, (T*)h->sval, (T*)h->sdinv,
-                                    h->flags, h->s_fthreads, h->s_fsmem, h->s_use_map, h->stream));
+                                    h->flags, h->s_fthreads, h->s_fsmem, h->s_use_map, h->stream, mb));
         return done(true);
     }
     if (h->g.dim == 3) {
         int packed3 = h->jpacked ? 1 : 0;
         if (!packed3 && sizeof(T) == 4) {
             KLA(ACAC_K_REPACK, (double)sizeof(T) * (100.0 * h->N + 100.0 * h->nbox), 0.0,
-                launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
+                launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream, mb));
             packed3 = 1;
         }
         KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 200.0 * h->nbox, 1200.0 * h->nbox,
             launch_ras_factor3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev,
                                   packed3 ? (const T*)h->Jp : (const T*)h->J, packed3, (T*)h->coef,
-                                  h->ras_threads, h->flags, h->stream));
+                                  h->ras_threads, h->flags, h->stream, mb));
         return done(false);
     }
     const int ring_cells = h->ras_maxcnt;
@@ -491,60 +513,54 @@ int factor(acac_handle* h, bool defer = false) {
     int packed = h->jpacked ? 1 : 0;
     if (!packed && sizeof(T) == 4) {
         KLA(ACAC_K_REPACK, (double)sizeof(T) * (52.0 * h->N + 52.0 * h->nbox), 0.0,
-            launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream));
+            launch_repack<T>(h->g, (const T*)h->J, h->rec_of_dev, (T*)h->Jp, h->stream, mb));
         packed = 1;
     }
     KLA(ACAC_K_RAS_FACTOR, (double)sizeof(T) * 104.0 * h->nbox, 528.0 * h->nbox,
         launch_ras_factor<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev,
                              packed ? (const T*)h->Jp : (const T*)h->J, packed, (T*)h->coef,
-                             h->ras_threads, ring_cells, smem, h->flags, h->stream));
+                             h->ras_threads, ring_cells, smem, h->flags, h->stream, mb));
     return done(false);
 }
 
-// One Arnoldi step of GMRES: v_{j+1} = J M^{-1} v_j orthogonalised against v_0..v_j
-// by classical Gram–Schmidt (twice when cgs_refine) and normalised; the Hessenberg
-// column and ||w||^2 are copied to h->host.  The caller synchronises.
+// One Arnoldi step of GMRES for the members still iterating (mask MK_GON): v_{j+1} =
+// J M^{-1} v_j orthogonalised against v_0..v_j by classical Gram–Schmidt (twice when
+// cgs_refine) and normalised, then the member's Givens step on the device (which clears
+// its MK_GON entry once it has converged or stopped).
 template <typename T>
 void arnoldi_step(acac_handle* h, int j) {
     const long long n = 2 * (long long)h->N;
+    const Members mb = on_mask(h, MK_GON);
     T* V = (T*)h->V;
     const long long ld = (long long)h->ldV;
     T* vj = V + (size_t)j * ld;
     T* vn = V + (size_t)(j + 1) * ld;
     T* zj = (T*)h->Zb + (size_t)j * ld;
-    precond<T>(h, vj, zj);
-    jac_action<T>(h, (const T*)zj, vn);
+    precond<T>(h, mb, vj, zj);
+    jac_action<T>(h, mb, (const T*)zj, vn);
     const int passes = h->p.cgs_refine ? 2 : 1;
     for (int pass = 0; pass < passes; ++pass) {
-        double* hcol = h->red + pass * (MAX_RESTART + 1);
+        double* hcol = h->red + (pass ? RS_H1 : RS_H0);
         KLA(ACAC_K_DOT, (double)sizeof(T) * n * (j + 2), 2.0 * n * (j + 1),
-            launch_multi_dot<T>(V, ld, j + 1, vn, n, red_to(h, hcol), h->stream));
+            launch_multi_dot<T>(V, ld, j + 1, vn, n, red_to(h, hcol), h->stream, mb));
         const bool last = pass == passes - 1;
         KLA(ACAC_K_CGS_UPDATE, (double)sizeof(T) * n * (j + 3), 2.0 * n * (j + 2),
-            launch_cgs_update<T>(V, ld, j + 1, hcol, vn, n, last ? 1 : 0,
-                                 red_to(h, h->red + 2 * (MAX_RESTART + 1)), h->stream));
+            launch_cgs_update<T>(V, ld, j + 1, hcol, vn, n, last ? 1 : 0, red_to(h, h->red + RS_NRM), h->stream,
+                                 mb));
     }
-    KL(ACAC_K_VECTOR, launch_scale_from<T>(vn, h->red + 2 * (MAX_RESTART + 1), vn, n, h->stream));
-    CU(cudaMemcpyAsync(h->host, h->red, sizeof(double) * 3 * (MAX_RESTART + 1), cudaMemcpyDeviceToHost,
-                       h->stream));
+    KL(ACAC_K_VECTOR, launch_scale_from<T>(vn, h->red + RS_NRM, vn, n, h->stream, mb));
+    KL(ACAC_K_VECTOR, launch_gmres_givens(h->ghead_dev, h->gwork_dev, h->red, RS, j, passes,
+                                          h->masks + (size_t)MK_GON * h->B, h->B, h->stream));
 }
 
 // arnoldi_step(j), replayed from a CUDA graph captured on its first use (one graph per
-// j; every pointer and scalar the step's kernels take is fixed for the handle's
-// lifetime), or launched directly.  Synchronises and collects timings.
+// j; every pointer the step's kernels take is fixed for the handle's lifetime and their
+// scalars live on the device), or launched directly.  Does not synchronise.
 template <typename T>
-void arnoldi_step_sync(acac_handle* h, int j) {
+void arnoldi_launch(acac_handle* h, int j) {
     const bool use_graph = h->p.graphs && h->gmres_calls > 0;
-    // a deferred factorization's flags come back with this read-back
-    auto fetch_factor_flags = [&]() {
-        if (h->factor_check)
-            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    };
     if (!use_graph) {
         arnoldi_step<T>(h, j);
-        fetch_factor_flags();
-        CU(cudaStreamSynchronize(h->stream));
-        prof_collect(h);
         return;
     }
     const unsigned timing = h->prof_on ? h->prof_mask : 0u;
@@ -581,236 +597,419 @@ void arnoldi_step_sync(acac_handle* h, int j) {
     CU(cudaGraphLaunch(G.exec, h->stream));
     for (const GraphRec& r : G.recs) {
         h->launches[r.id]++;
-        h->kernel_bytes[r.id] += r.bytes;
-        h->kernel_flops[r.id] += r.flops;
+        // counted for every member of the cycle (those that have already converged
+        // return at once)
+        h->kernel_bytes[r.id] += r.bytes * h->ncyc;
+        h->kernel_flops[r.id] += r.flops * h->ncyc;
         if (r.a) h->pending.push_back({r.id, r.a, r.b, true});
     }
-    fetch_factor_flags();
-    CU(cudaStreamSynchronize(h->stream));
-    prof_collect(h);
 }
 
-// Restarted GMRES for J x = b (b = h->b, double), x0 = 0, right preconditioning.
-// Returns ACAC_OK or ACAC_E_DIVERGED; x (double, 2N) receives the solution.
+// Restarted GMRES for J x = b (b = h->b), x0 = 0, right preconditioning, for the members
+// in `want`.  x (device, member stride mb.vs) receives the solutions; per member gst
+// (ACAC_OK, ACAC_E_DIVERGED or ACAC_E_TIMEOUT), gits (iterations) and gres (residual
+// estimate).  bnorm: ||b|| per member when already known (the Newton loop's b = -F has
+// the norm of its residual evaluation; no reduction and read-back are spent on it), else
+// null.  With defer_timeout the apply's sticky timeout flags are left to the caller's
+// next read-back.
 template <typename T>
-// known_bnorm >= 0: ||b|| is already known to the caller (the Newton loop's b = -F has the
-// norm of its residual evaluation), so no reduction and read-back are spent on it.
-int gmres(acac_handle* h, double* x, int* its_out, double* resid_out, bool defer_timeout = false,
-          double known_bnorm = -1.0) {
-    // the first call runs eagerly (it also sets the kernels' shared-memory limits);
-    // later calls replay captured graphs
+void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<int>& gst, std::vector<int>& gits,
+           std::vector<double>& gres, const std::vector<double>* bnorm, bool defer_timeout = false) {
+    // the first call runs eagerly (it also sets the kernels' shared-memory limits); later
+    // calls replay captured graphs
     struct Count {
         acac_handle* h;
         ~Count() { h->gmres_calls++; }
     } count{h};
+    const int B = h->B;
     const long long n = 2 * (long long)h->N;
-    const int m = h->p.gmres_restart;
-    T* V = (T*)h->V;
+    const int mres = h->p.gmres_restart;
     const long long ld = (long long)h->ldV;
-    T* w = (T*)h->w;
     T* tt = (T*)h->kt;
-    CU(cudaMemsetAsync(x, 0, sizeof(double) * n, h->stream));
+    T* w = (T*)h->w;
+    int* gon_host = h->host_flags + 2 * B;
+    gst.assign(B, ACAC_OK);
+    gits.assign(B, 0);
+    gres.assign(B, 0.0);
+    CU(cudaMemsetAsync(x, 0, sizeof(double) * h->mb.vs * B, h->stream));
     // a deferred factorization's flags come back with the first read-back of the solve
-    auto factor_status = [&]() -> int {
-        if (!h->factor_check) return ACAC_OK;
-        h->factor_check = false;
-        const int f = h->host_flags[0];
-        return (f & 8) ? ACAC_E_TIMEOUT : f ? ACAC_E_DIVERGED : ACAC_OK;
+    bool flags_pending = h->factor_check;
+    h->factor_check = false;
+    auto factor_flags = [&]() {   // after a synchronised fetch_flags
+        if (!flags_pending) return;
+        flags_pending = false;
+        for (int m = 0; m < B; ++m) {
+            if (!want[m]) continue;
+            const int f = h->host_flags[m];
+            if (f & 8) gst[m] = ACAC_E_TIMEOUT;
+            else if (f) gst[m] = ACAC_E_DIVERGED;
+        }
     };
-    double bnorm = known_bnorm;
-    if (bnorm < 0.0) {
-        KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream));
-        if (h->factor_check)
-            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-        bnorm = sqrt(read_scalars(h, 1));
-        const int fs = factor_status();
-        if (fs != ACAC_OK) return fs;
+    std::vector<double> beta(B, 0.0), tol(B, 0.0);
+    if (bnorm) {
+        beta = *bnorm;
+    } else {
+        set_mask(h, MK_AUX, want);
+        KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream, on_mask(h, MK_AUX)));
+        if (flags_pending) fetch_flags(h);
+        read_member_scalars(h, 0, 1);
+        for (int m = 0; m < B; ++m) beta[m] = sqrt(h->host[m]);
+        factor_flags();
     }
-    const double tol = std::max(h->p.gmres_rtol * bnorm, h->p.gmres_atol);
-    double beta = bnorm;
-    int its = 0;
-    double resid = beta;
-    *its_out = 0;
-    *resid_out = beta;
-    if (beta <= tol) {
-        if (h->factor_check) {      // no read-back happened yet in this solve
-            CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-            CU(cudaStreamSynchronize(h->stream));
-        }
-        return factor_status();
+    std::vector<int> act(B, 0);
+    for (int m = 0; m < B; ++m) {
+        if (!want[m]) continue;
+        tol[m] = std::max(h->p.gmres_rtol * beta[m], h->p.gmres_atol);
+        gres[m] = beta[m];
+        act[m] = gst[m] == ACAC_OK && beta[m] > tol[m];
     }
-    std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m + 1);
-    auto Hat = [&](int i, int j) -> double& { return H[(size_t)i * m + j]; };
     const double* rsrc = h->b;
-    while (true) {
-        KL(ACAC_K_VECTOR, launch_to_krylov<T>(rsrc, 1.0 / beta, V, n, h->stream));
-        std::fill(H.begin(), H.end(), 0.0);
-        std::fill(gv.begin(), gv.end(), 0.0);
-        gv[0] = beta;
-        int k = 0;
-        bool done = false;
-        double hn = 0.0;
-        for (int j = 0; j < m; ++j) {
-            arnoldi_step_sync<T>(h, j);
-            ++its;
-            const int fs = factor_status();
-            if (fs != ACAC_OK) {
-                *its_out = its;
-                return fs;
-            }
-            const int passes = h->p.cgs_refine ? 2 : 1;
-            for (int i = 0; i <= j; ++i) {
-                double hij = h->host[i];
-                if (passes == 2) hij += h->host[(MAX_RESTART + 1) + i];
-                Hat(i, j) = hij;
-            }
-            hn = sqrt(h->host[2 * (MAX_RESTART + 1)]);
-            Hat(j + 1, j) = hn;
-            for (int i = 0; i < j; ++i) {
-                const double t0 = cs[i] * Hat(i, j) + sn[i] * Hat(i + 1, j);
-                Hat(i + 1, j) = -sn[i] * Hat(i, j) + cs[i] * Hat(i + 1, j);
-                Hat(i, j) = t0;
-            }
-            const double rho = hypot(Hat(j, j), Hat(j + 1, j));
-            cs[j] = Hat(j, j) / rho;
-            sn[j] = Hat(j + 1, j) / rho;
-            Hat(j, j) = rho;
-            Hat(j + 1, j) = 0.0;
-            gv[j + 1] = -sn[j] * gv[j];
-            gv[j] = cs[j] * gv[j];
-            resid = fabs(gv[j + 1]);
-            k = j + 1;
-            if (!(resid == resid) || !isfinite(rho)) {
-                *its_out = its;
-                *resid_out = resid;
-                return ACAC_E_DIVERGED;
-            }
-            if (resid <= tol || its >= h->p.gmres_maxit || hn == 0.0) {
-                done = true;
-                break;
-            }
+    h->ghead.resize(B);
+    while (any_of(act)) {
+        // cycle start: v_0 = r / beta, g = beta e_1
+        for (int m = 0; m < B; ++m)
+            h->ghead[m] = GmresHead{beta[m], tol[m], beta[m], gits[m], h->p.gmres_maxit, 0, GMRES_RUNNING};
+        CU(cudaMemcpyAsync(h->ghead_dev, h->ghead.data(), sizeof(GmresHead) * B, cudaMemcpyHostToDevice, h->stream));
+        set_mask(h, MK_CYC, act);
+        h->ncyc = h->mask_count[MK_CYC];
+        int* cyc = h->masks + (size_t)MK_CYC * B;
+        KL(ACAC_K_VECTOR, launch_gmres_start(h->ghead_dev, h->gwork_dev, cyc, h->masks + (size_t)MK_GON * B, B,
+                                             h->stream));
+        KL(ACAC_K_VECTOR, launch_to_krylov<T>(rsrc, 1.0, (T*)h->V, n, h->stream, on_mask(h, MK_CYC),
+                                              (const double*)h->ghead_dev, (int)(sizeof(GmresHead) / sizeof(double))));
+        // Arnoldi steps without read-backs: the first look at the members' progress comes
+        // after as many steps as the previous cycle took, then one after every step
+        int j = 0;
+        int next = std::max(1, std::min(mres, h->gm_hint));
+        while (j < mres) {
+            arnoldi_launch<T>(h, j);
+            ++j;
+            if (j >= mres || j < next) continue;
+            if (flags_pending) fetch_flags(h);
+            CU(cudaMemcpyAsync(gon_host, h->masks + (size_t)MK_GON * B, sizeof(int) * B, cudaMemcpyDeviceToHost,
+                               h->stream));
+            CU(cudaStreamSynchronize(h->stream));
+            prof_collect(h);
+            factor_flags();
+            bool any = false;
+            for (int m = 0; m < B; ++m) any = any || gon_host[m];
+            if (!any) break;
+            next = j + 1;
         }
-        // y = H(1:k,1:k)^{-1} g(1:k);  x += M^{-1} (V y) = Z y, z_j = M^{-1} v_j kept by the
-        // Arnoldi steps (the preconditioner is linear)
-        for (int i = k - 1; i >= 0; --i) {
-            double s = gv[i];
-            for (int jj = i + 1; jj < k; ++jj) s -= Hat(i, jj) * yv[jj];
-            yv[i] = s / Hat(i, i);
+        // y = R^-1 g and x += Z y (z_j = M^-1 v_j kept by the Arnoldi steps: the
+        // preconditioner is linear) for the members of the cycle
+        KL(ACAC_K_VECTOR, launch_gmres_solve(h->ghead_dev, h->gwork_dev, cyc, h->red + RS_Y, RS, h->kcnt_dev, B,
+                                             h->stream));
+        const Members mc = on_mask(h, MK_CYC);
+        KL(ACAC_K_VECTOR, launch_lincomb<T>((const T*)h->Zb, ld, mres, h->red + RS_Y, tt, n, h->stream, mc,
+                                            h->kcnt_dev));
+        KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, tt, x, n, h->stream, mc));
+        CU(cudaMemcpyAsync(h->ghead.data(), h->ghead_dev, sizeof(GmresHead) * B, cudaMemcpyDeviceToHost, h->stream));
+        if (flags_pending) fetch_flags(h);
+        CU(cudaStreamSynchronize(h->stream));
+        prof_collect(h);
+        factor_flags();
+        int hint = 0;
+        std::vector<int> rst(B, 0);
+        for (int m = 0; m < B; ++m) {
+            if (!act[m]) continue;
+            const GmresHead& H = h->ghead[m];
+            gits[m] = H.its;
+            gres[m] = H.resid;
+            hint = std::max(hint, H.k);
+            act[m] = 0;
+            if (gst[m] != ACAC_OK) continue;
+            if (H.status == GMRES_LIMIT || H.status == GMRES_NONFINITE) gst[m] = ACAC_E_DIVERGED;
+            else if (H.status == GMRES_RUNNING) rst[m] = 1;
         }
-        memcpy(h->host, yv.data(), sizeof(double) * k);
-        CU(cudaMemcpyAsync(h->red, h->host, sizeof(double) * k, cudaMemcpyHostToDevice, h->stream));
-        KL(ACAC_K_VECTOR, launch_lincomb<T>((const T*)h->Zb, ld, k, h->red, tt, n, h->stream));
-        KL(ACAC_K_VECTOR, launch_axpy_to_double<T>(1.0, tt, x, n, h->stream));
-        if (done) {
-            *its_out = its;
-            *resid_out = resid;
-            // the apply's timeout flag is sticky: with defer_timeout the caller reads it at
-            // its next read-back instead of here
-            if (!defer_timeout) {
-                CU(cudaMemcpyAsync(h->host_flags + 1, h->flags + 1, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-                CU(cudaStreamSynchronize(h->stream));
-                if (h->host_flags[1]) return ACAC_E_TIMEOUT;
-            }
-            return (resid <= tol || hn == 0.0) ? ACAC_OK : ACAC_E_DIVERGED;
-        }
+        h->gm_hint = hint;
+        if (!any_of(rst)) break;
         // restart: r = b - J x
-        KL(ACAC_K_VECTOR, launch_to_krylov<T>(x, 1.0, tt, n, h->stream));
-        jac_action<T>(h, tt, w);
-        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, red_to(h, h->red), h->stream));
-        beta = sqrt(read_scalars(h, 1));
-        rsrc = h->r;
-        if (beta <= tol) {
-            *its_out = its;
-            *resid_out = beta;
-            return ACAC_OK;
+        set_mask(h, MK_RESTART, rst);
+        const Members mr = on_mask(h, MK_RESTART);
+        KL(ACAC_K_VECTOR, launch_to_krylov<T>(x, 1.0, tt, n, h->stream, mr));
+        jac_action<T>(h, mr, tt, w);
+        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, red_to(h, h->red), h->stream, mr));
+        read_member_scalars(h, 0, 1);
+        for (int m = 0; m < B; ++m) {
+            if (!rst[m]) continue;
+            beta[m] = sqrt(h->host[m]);
+            if (beta[m] <= tol[m]) gres[m] = beta[m];
+            else act[m] = 1;
         }
+        rsrc = h->r;
+    }
+    if (flags_pending || !defer_timeout) {
+        fetch_flags(h);
+        CU(cudaStreamSynchronize(h->stream));
+        prof_collect(h);
+        factor_flags();
+        if (!defer_timeout)
+            for (int m = 0; m < B; ++m)
+                if (want[m] && gst[m] == ACAC_OK && h->host_flags[B + m]) gst[m] = ACAC_E_TIMEOUT;
     }
 }
 
 // fresh: the cache already holds the linearisation at X (written by the residual evaluation
 // that produced X, see eval_residual)
 template <typename T>
-void linearize_and_maybe_assemble(acac_handle* h, const double* X, double dt, bool assemble, bool fresh = false) {
-    set_jac<T>(h, dt);
-    if (!fresh)
+void linearize_and_maybe_assemble(acac_handle* h, const Members& mb, const double* X, bool assemble,
+                                  bool fresh = false) {
+    if (!fresh) {
+        // single problems only: the Newton loop's evaluations always leave the cache fresh
+        if (h->B != 1) throw Err{ACAC_E_ARG};
         KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 7.0 * sizeof(T) * h->N, 0.0,
             launch_linearize<T>(h->g, h->k, X, h->X0, h->G, cache_of<T>(h), h->stream));
+    }
     h->cache_fresh = false;
     if (!assemble) return;
+    const JacK<T>* kp = (const JacK<T>*)h->jk_dev;
     // with matrix-free products the assembled Jacobian feeds only the subdomain
     // factorization: in 2D assemble it straight into the factorization's records
     h->jpacked = h->p.jac_mode == ACAC_JAC_MATFREE && h->p.subdomain_solver == ACAC_SUB_ILU0;
     if (h->jpacked)
         KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * (7.0 * h->N + 4.0 * (h->g.dim == 3 ? NSLOT3 : NSLOT) * h->nbox), 0.0,
-            launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->Jp, h->stream, h->rec_of_dev));
+            launch_assemble<T>(h->g, kp, cache_of<T>(h), (T*)h->Jp, h->stream, h->rec_of_dev, mb));
     else
         KLA(ACAC_K_ASSEMBLE, (double)sizeof(T) * 59.0 * h->N, 0.0,
-            launch_assemble<T>(h->g, h->k, dt, cache_of<T>(h), (T*)h->J, h->stream));
+            launch_assemble<T>(h->g, kp, cache_of<T>(h), (T*)h->J, h->stream, nullptr, mb));
 }
 
-// Newton iteration from X_0 = X0 (device).  Root in h->X.
+// The line-search steps (and the rest of the per-member scalars) to the device.
+void write_lam(acac_handle* h) {
+    CU(cudaMemcpyAsync(h->mk_dev, h->mk.data(), sizeof(MemberK) * h->B, cudaMemcpyHostToDevice, h->stream));
+}
+
+// Newton iteration (Sec. 3.1) from X_0 = X0 for the members in `want`, each with its own
+// dt (h->mk, already on the device).  Roots in h->X; st[m] per member; info[m] accumulates
+// the member's iteration counts.
 template <typename T>
-int nks(acac_handle* h, double dt, acac_step_info* info) {
+void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, acac_step_info* info) {
+    const int B = h->B;
     const size_t N = h->N;
     const long long n = 2 * (long long)N;
-    CU(cudaMemcpyAsync(h->X, h->X0, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
-    // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
-    KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream));
-    int fl = 0;
-    double fnorm = eval_residual(h, h->X, nullptr, 0.0, 0.0, dt, &fl, true, nullptr, true);
-    info->fnorm0 = info->fnorm = fnorm;
-    if (fl & 1) return ACAC_E_DOMAIN;
-    if (!isfinite(fnorm)) return ACAC_E_DIVERGED;
-    const double stop = std::max(h->p.newton_rtol * fnorm, h->p.newton_atol);
-    if (fnorm <= stop) return ACAC_OK;
-    int it = 0;
-    while (true) {
-        if (it >= h->p.newton_maxit) return ACAC_E_DIVERGED;
+    st.assign(B, ACAC_OK);
+    std::vector<int> act = want;
+    std::vector<double> fnorm(B, 0.0), stop(B, 0.0);
+    std::vector<double*> root(B, nullptr);
+    set_mask(h, MK_NEWTON, act);
+    {
+        const Members mn = on_mask(h, MK_NEWTON);
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->X0, h->X, n, h->stream, mn));
+        // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream, mn));
+    }
+    eval_residual(h, MK_NEWTON, h->X, false, true, true);
+    for (int m = 0; m < B; ++m) {
+        if (!want[m]) continue;
+        info[m].fnorm0 = info[m].fnorm = fnorm[m] = h->fn[m];
+        if (h->fl[m] & 1) {
+            st[m] = ACAC_E_DOMAIN;
+            act[m] = 0;
+        } else if (!isfinite(fnorm[m])) {
+            st[m] = ACAC_E_DIVERGED;
+            act[m] = 0;
+        } else {
+            stop[m] = std::max(h->p.newton_rtol * fnorm[m], h->p.newton_atol);
+            if (fnorm[m] <= stop[m]) {
+                act[m] = 0;
+                root[m] = h->X;
+            }
+        }
+    }
+    std::vector<int> gst, gits;
+    std::vector<double> gres;
+    for (int it = 0; any_of(act); ++it) {
+        if (it >= h->p.newton_maxit) {
+            for (int m = 0; m < B; ++m)
+                if (act[m]) st[m] = ACAC_E_DIVERGED;
+            break;
+        }
+        set_mask(h, MK_NEWTON, act);
         const bool refactor = (it == 0) || !h->p.ilu_reuse;
-        linearize_and_maybe_assemble<T>(h, h->X, dt, refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED,
-                                        h->cache_fresh);
+        linearize_and_maybe_assemble<T>(h, on_mask(h, MK_NEWTON), h->X,
+                                        refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED, h->cache_fresh);
         if (refactor) {
-            int st = factor<T>(h, true);
-            if (st != ACAC_OK) return st;
+            factor<T>(h, on_mask(h, MK_NEWTON), true);
+            for (int m = 0; m < B; ++m) info[m].ilu_factorizations += act[m];
         }
         // b = -F
-        CU(cudaMemsetAsync(h->b, 0, sizeof(double) * n, h->stream));
-        KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream));
-        int gits = 0;
-        double gres = 0.0;
-        int st = gmres<T>(h, h->S, &gits, &gres, true, fnorm);
-        info->gmres_its += gits;
-        if (st != ACAC_OK) return st;
-        // shift S_u by a constant so that sum(u + S_u) = sum(u^n); the sum stays on the
-        // device, where the trial kernel reads it
-        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->shift_dev), h->stream));
-        double lam = 1.0;
-        const double f2 = fnorm * fnorm;
-        double ft = 0.0;
-        while (true) {
-            ft = eval_residual(h, h->X, h->S, lam, 0.0, dt, &fl, true, h->shift_dev, true);
-            if (fl & 8) return ACAC_E_TIMEOUT;
-            if (fl == 0 && isfinite(ft) && ft * ft <= (1.0 - 2e-4 * lam) * f2) break;
-            lam *= 0.5;
-            h->ls_cuts++;
-            if (lam < 1.0 / 1024.0) return ACAC_E_DIVERGED;
+        CU(cudaMemsetAsync(h->b, 0, sizeof(double) * h->mb.vs * B, h->stream));
+        KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream, on_mask(h, MK_NEWTON)));
+        gmres<T>(h, act, h->S, gst, gits, gres, &fnorm, true);
+        for (int m = 0; m < B; ++m) {
+            if (!act[m]) continue;
+            info[m].gmres_its += gits[m];
+            if (gst[m] != ACAC_OK) {
+                st[m] = gst[m];
+                act[m] = 0;
+            }
         }
+        if (!any_of(act)) break;
+        set_mask(h, MK_NEWTON, act);
+        // shift S_u by a constant so that sum(u + S_u) = sum(u^n); the sums stay on the
+        // device, where the trial kernel reads them
+        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->red + RS_SHIFT), h->stream,
+                                          on_mask(h, MK_NEWTON)));
+        std::vector<int> ls = act;
+        std::vector<double> lam(B, 1.0), ft(B, 0.0);
+        while (any_of(ls)) {
+            for (int m = 0; m < B; ++m) h->mk[m].lam = lam[m];
+            write_lam(h);
+            set_mask(h, MK_LS, ls);
+            eval_residual(h, MK_LS, h->X, true, true, true);
+            for (int m = 0; m < B; ++m) {
+                if (!ls[m]) continue;
+                const double f = h->fn[m];
+                if (h->fl[m] & 8) {
+                    st[m] = ACAC_E_TIMEOUT;
+                    act[m] = ls[m] = 0;
+                } else if (h->fl[m] == 0 && isfinite(f) && f * f <= (1.0 - 2e-4 * lam[m]) * fnorm[m] * fnorm[m]) {
+                    ft[m] = f;
+                    ls[m] = 0;
+                } else {
+                    lam[m] *= 0.5;
+                    info[m].line_search_cuts++;
+                    if (lam[m] < 1.0 / 1024.0) {
+                        st[m] = ACAC_E_DIVERGED;
+                        act[m] = ls[m] = 0;
+                    }
+                }
+            }
+        }
+        // the accepted states of the members still iterating are in Xt; members that
+        // finished earlier keep their roots where they were (root[m])
         std::swap(h->X, h->Xt);
-        fnorm = ft;
-        ++it;
-        info->newton_its = it;
-        info->fnorm = fnorm;
-        if (fnorm <= stop) return ACAC_OK;
+        for (int m = 0; m < B; ++m) {
+            if (!act[m]) continue;
+            fnorm[m] = ft[m];
+            info[m].newton_its = it + 1;
+            info[m].fnorm = fnorm[m];
+            if (fnorm[m] <= stop[m]) {
+                act[m] = 0;
+                root[m] = h->X;
+            }
+        }
+    }
+    // roots left in the other buffer by later swaps
+    std::vector<int> fix(B, 0);
+    for (int m = 0; m < B; ++m) fix[m] = want[m] && st[m] == ACAC_OK && root[m] != h->X;
+    if (any_of(fix)) {
+        set_mask(h, MK_AUX, fix);
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->Xt, h->X, n, h->stream, on_mask(h, MK_AUX)));
     }
 }
 
-int nks_dispatch(acac_handle* h, double dt, acac_step_info* info) {
-    h->ls_cuts = 0;
-    h->n_factor = 0;
-    int st = h->mixed ? nks<float>(h, dt, info) : nks<double>(h, dt, info);
-    info->line_search_cuts += h->ls_cuts;
-    info->ilu_factorizations += h->n_factor;
-    return st;
+void nks_dispatch(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, acac_step_info* info) {
+    if (h->mixed) nks<float>(h, want, st, info);
+    else nks<double>(h, want, st, info);
+}
+
+// Energy and mass (Eqs. relations, freeenergy) of the members of mask `slot` (slot < 0:
+// all) at X; bad[m] != 0 when some u + v or u - v of the member lies outside [0, 1].
+void energy_members(acac_handle* h, int slot, const double* X, std::vector<double>& e, std::vector<double>& ms,
+                    std::vector<int>& bad) {
+    const Members mb = slot < 0 ? all_members(h) : on_mask(h, slot);
+    CU(cudaMemsetAsync(h->flags, 0, sizeof(int) * h->B, h->stream));
+    KLA(ACAC_K_ENERGY, 16.0 * h->N, 0.0, launch_energy(h->g, h->k, X, red_to(h, h->red), h->flags, h->stream, mb));
+    fetch_flags(h);
+    read_member_scalars(h, 0, 2);
+    e.resize(h->B);
+    ms.resize(h->B);
+    bad.resize(h->B);
+    for (int m = 0; m < h->B; ++m) {
+        e[m] = h->host[2 * m];
+        ms[m] = h->host[2 * m + 1];
+        bad[m] = h->host_flags[m];
+    }
+}
+
+// One accepted time step of every member (fields u, v: member m at m * N), with the
+// adaptive step of Sec. 3.2: the predictor of Eq. sencondt from the last two states, and
+// on divergence dt / sqrt(2) and eta doubled, retried until it converges or dt drops
+// below dt_min.  The members retry independently (those done wait); info[m] per member.
+// Returns the first failing status in member order.
+int step_members(acac_handle* h, double* u, double* v, acac_step_info* info_out) {
+    const int B = h->B;
+    const size_t N = h->N;
+    const long long n2 = 2 * (long long)N;
+    std::vector<acac_step_info> info(B);
+    memset(info.data(), 0, sizeof(acac_step_info) * B);
+    KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_pack_members(u, v, h->X0, (long long)N, 1, h->stream, all_members(h)));
+    const bool adaptive = h->p.dt_mode == ACAC_DT_ADAPTIVE;
+    std::vector<double> dt(B, h->p.dt0);
+    if (adaptive) {
+        std::vector<int> prev(B);
+        for (int m = 0; m < B; ++m) prev[m] = h->have_prev[m];
+        if (any_of(prev)) {
+            set_mask(h, MK_AUX, prev);
+            KL(ACAC_K_VECTOR, launch_norm2_double(h->X0, h->Xprev, n2, red_to(h, h->red), h->stream,
+                                                  on_mask(h, MK_AUX)));
+            read_member_scalars(h, 0, 1);
+            for (int m = 0; m < B; ++m) {
+                if (!prev[m]) continue;
+                const double xd = sqrt(h->host[m]) / h->dt_prev[m];
+                dt[m] = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta[m] * xd * xd));
+            }
+        }
+    }
+    std::vector<int> pending(B, 1), stv(B, ACAC_OK), st;
+    std::vector<double> e, ms;
+    std::vector<int> bad;
+    while (any_of(pending)) {
+        for (int m = 0; m < B; ++m) {
+            h->mk[m].dt = dt[m];
+            h->mk[m].lam = 1.0;
+        }
+        write_members_any(h);
+        nks_dispatch(h, pending, st, info.data());
+        std::vector<int> ok(B, 0);
+        for (int m = 0; m < B; ++m) {
+            if (!pending[m]) continue;
+            if (st[m] == ACAC_OK) {
+                ok[m] = 1;
+                pending[m] = 0;
+            } else if (st[m] == ACAC_E_DIVERGED && adaptive) {
+                info[m].divergences++;
+                dt[m] = dt[m] / sqrt(2.0);
+                h->eta[m] *= 2.0;
+                if (dt[m] < h->p.dt_min) {
+                    stv[m] = ACAC_E_DT_UNDERFLOW;
+                    pending[m] = 0;
+                }
+            } else {
+                if (st[m] == ACAC_E_DIVERGED) info[m].divergences++;
+                stv[m] = st[m];
+                pending[m] = 0;
+            }
+        }
+        if (!any_of(ok)) continue;
+        // accepted members: U^{n+1} out, U^n kept for the next predictor, energy and mass
+        set_mask(h, MK_AUX, ok);
+        const Members ma = on_mask(h, MK_AUX);
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->X0, h->Xprev, n2, h->stream, ma));
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_pack_members(u, v, h->X, (long long)N, 0, h->stream, ma));
+        energy_members(h, MK_AUX, h->X, e, ms, bad);
+        for (int m = 0; m < B; ++m) {
+            if (!ok[m]) continue;
+            h->dt_prev[m] = dt[m];
+            h->t[m] += dt[m];
+            h->nstep[m]++;
+            h->have_prev[m] = 1;
+            info[m].energy = e[m];
+            info[m].mass = ms[m];
+            info[m].dt = dt[m];
+            info[m].t = h->t[m];
+        }
+    }
+    int first = ACAC_OK;
+    for (int m = 0; m < B; ++m) {
+        info[m].eta = h->eta[m];
+        info[m].status = stv[m];
+        if (first == ACAC_OK && stv[m] != ACAC_OK) first = stv[m];
+    }
+    if (info_out) memcpy(info_out, info.data(), sizeof(acac_step_info) * B);
+    return first;
 }
 
 // ---------------------------------------------------------------- adjoint
@@ -835,8 +1034,10 @@ void assemble_transposed(acac_handle* h, const double* X1, double dt, int wrt_x0
     KLA(ACAC_K_LINEARIZE, 56.0 * h->N + 56.0 * h->N, 0.0,
         launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream, wrt_x0));
     // -dt puts -1/dt on the diagonal of dF/dX0
+    set_dt0(h, wrt_x0 ? -dt : dt);
     KLA(ACAC_K_ASSEMBLE, 8.0 * 59.0 * h->N, 0.0,
-        launch_assemble<double>(h->g, h->k, wrt_x0 ? -dt : dt, cache_of<double>(h), J, h->stream));
+        launch_assemble<double>(h->g, (const JacK<double>*)h->jk_dev, cache_of<double>(h), J, h->stream));
+    set_dt0(h, dt);
     KLA(ACAC_K_VECTOR, 8.0 * 2.0 * stencil_values(h), 0.0, launch_transpose<double>(h->g, J, (double*)h->J, h->stream));
     h->jpacked = false;
 }
@@ -848,12 +1049,12 @@ int adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, 
     const long long n2 = 2 * (long long)h->N;
     double* mu = h->adj;
     CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
-    int fl = 0;
-    eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
-    if (fl & 1) return ACAC_E_DOMAIN;
+    set_dt0(h, dt);
+    eval_residual(h, -1, X1, false);
+    if (h->fl[0] & 1) return ACAC_E_DOMAIN;
     // J1^T mu = lambda^{n+1}
     assemble_transposed(h, X1, dt, 0);
-    int st = factor<double>(h);
+    int st = factor<double>(h, all_members(h));
     if (st != ACAC_OK) return st;
     CU(cudaMemcpyAsync(h->b, lam_in, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
     const acac_params saved = h->p;
@@ -861,16 +1062,17 @@ int adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, 
     h->p.graphs = 0;                      // the captured iterations use the forward product
     h->p.gmres_rtol = rtol;
     h->p.gmres_atol = 0.0;
-    int gi = 0;
-    double gr = 0.0;
+    std::vector<int> gst, gits;
+    std::vector<double> gres;
     try {
-        st = gmres<double>(h, mu, &gi, &gr);
+        gmres<double>(h, std::vector<int>(1, 1), mu, gst, gits, gres, nullptr);
     } catch (Err e) {
         h->p = saved;
         throw;
     }
     h->p = saved;
-    if (its) *its += gi;
+    st = gst[0];
+    if (its) *its += gits[0];
     if (st != ACAC_OK) return st;
     // -mu^T dF/dp
     CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
@@ -1183,8 +1385,11 @@ void build_sparse(acac_handle* h) {
     CU(cudaMemcpy(h->sshape_dev, sd.data(), sd.size() * sizeof(SparseShapeDev), cudaMemcpyHostToDevice));
     dmalloc(&h->sbox_dev, boxes.size() * sizeof(SparseBox));
     CU(cudaMemcpy(h->sbox_dev, boxes.data(), boxes.size() * sizeof(SparseBox), cudaMemcpyHostToDevice));
-    dmalloc(&h->sval, (size_t)blk * 4 * h->ksz);
-    dmalloc(&h->sdinv, (size_t)cells * 4 * h->ksz);
+    auto r64 = [](long long e) { return (e + 63) / 64 * 64; };
+    h->mb.cfs = r64(blk * 4);
+    h->mb.rgs = r64(cells * 4);
+    dmalloc(&h->sval, (size_t)h->mb.cfs * h->B * h->ksz);
+    dmalloc(&h->sdinv, (size_t)h->mb.rgs * h->B * h->ksz);
     // apply: 8 warps, one per row of a dependency level (the whole block on a level of a
     // single row).  Factorization: 32 warps on the rows in natural order when positions
     // are arithmetic, else 16 (fewer if their maps do not fit shared memory)
@@ -1203,7 +1408,8 @@ void build_sparse(acac_handle* h) {
         h->s_asmem = vec;
     } else {
         h->s_asmem = 0;
-        dmalloc(&h->sy, (size_t)cells * 2 * h->ksz);
+        h->mb.ss = r64(cells * 2);
+        dmalloc(&h->sy, (size_t)h->mb.ss * h->B * h->ksz);
     }
     for (SparseShape& S : h->sshape) {   // the device holds what the kernels need
         S.col.clear(); S.col.shrink_to_fit();
@@ -1212,7 +1418,8 @@ void build_sparse(acac_handle* h) {
 }
 
 void free_all(acac_handle* h) {
-    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0, h->shift_dev, h->V, h->Zb, h->w,
+    void* bufs[] = {h->X, h->X0, h->Xprev, h->Xt, h->F, h->S, h->G, h->b, h->r, h->tmpd, h->stage, h->lap0,
+                    h->mk_dev, h->masks, h->ghead_dev, h->gwork_dev, h->kcnt_dev, h->V, h->Zb, h->w,
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->own_of_dev,
                     h->rg, h->Jp,
@@ -1231,96 +1438,6 @@ void free_all(acac_handle* h) {
 
 }  // namespace
 
-// ---------------------------------------------------------------- ensembles
-extern "C" int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out);
-extern "C" void acac_destroy(acac_handle* h);
-
-namespace {
-
-void destroy_ensemble(acac_handle* h) {
-    cudaStreamSynchronize(h->stream);
-    delete h->member_pool;
-    for (acac_handle* m : h->members)
-        if (m) acac_destroy(m);
-    for (cudaStream_t s : h->member_streams) cudaStreamDestroy(s);
-    for (cudaEvent_t e : h->member_done) cudaEventDestroy(e);
-    if (h->member_start) cudaEventDestroy(h->member_start);
-    if (h->stage) cudaFree(h->stage);
-    delete h;
-}
-
-int create_ensemble(const acac_params* p, void* cuda_stream, acac_handle** out) {
-    acac_handle* h = new (std::nothrow) acac_handle();
-    if (!h) return ACAC_E_NOMEM;
-    h->p = *p;
-    h->stream = h->user_stream = (cudaStream_t)cuda_stream;
-    h->mixed = p->precision == ACAC_MIXED;
-    h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
-    acac_params q = *p;
-    q.batch = 1;
-    const int B = p->batch;
-    int st = ACAC_OK;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) st = ACAC_E_CUDA;
-    h->members.assign(B, nullptr);
-    for (int m = 0; m < B && st == ACAC_OK; ++m) {
-        cudaStream_t s = nullptr;
-        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
-            st = ACAC_E_CUDA;
-            break;
-        }
-        h->member_streams.push_back(s);
-        cudaEvent_t e = nullptr;
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            st = ACAC_E_CUDA;
-            break;
-        }
-        h->member_done.push_back(e);
-        st = acac_create(&q, s, &h->members[m]);
-    }
-    if (st == ACAC_OK && cudaEventCreateWithFlags(&h->member_start, cudaEventDisableTiming) != cudaSuccess)
-        st = ACAC_E_CUDA;
-    if (st == ACAC_OK && cudaMalloc((void**)&h->stage, 2 * h->N * B * sizeof(double)) != cudaSuccess)
-        st = ACAC_E_NOMEM;
-    if (st != ACAC_OK) {
-        destroy_ensemble(h);
-        return st;
-    }
-    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
-    const int workers = std::min<int>(B, (int)hw) - 1;   // the calling thread takes part
-    try {
-        h->member_pool = new MemberPool(std::max(0, workers), dev);
-    } catch (...) {
-        destroy_ensemble(h);
-        return ACAC_E_NOMEM;
-    }
-    *out = h;
-    return ACAC_OK;
-}
-
-// Runs fn(member) for every member concurrently, with the members' streams ordered
-// after the caller's stream on entry and before it on exit.  Returns the first
-// failing status in member order.
-int for_members(acac_handle* h, const std::function<int(int)>& fn) {
-    const int B = (int)h->members.size();
-    if (cudaEventRecord(h->member_start, h->stream) != cudaSuccess) return ACAC_E_CUDA;
-    for (int m = 0; m < B; ++m)
-        if (cudaStreamWaitEvent(h->member_streams[m], h->member_start, 0) != cudaSuccess) return ACAC_E_CUDA;
-    std::vector<int> st(B, ACAC_OK);
-    h->member_pool->run(B, [&](int m) { st[m] = fn(m); });
-    int first = ACAC_OK;
-    for (int m = 0; m < B; ++m) {
-        if (cudaEventRecord(h->member_done[m], h->member_streams[m]) != cudaSuccess ||
-            cudaStreamWaitEvent(h->stream, h->member_done[m], 0) != cudaSuccess)
-            return ACAC_E_CUDA;
-        if (first == ACAC_OK && st[m] != ACAC_OK) first = st[m];
-    }
-    return first;
-}
-
-bool is_ensemble(const acac_handle* h) { return h && !h->members.empty(); }
-
-}  // namespace
 
 // ====================================================================== C ABI
 extern "C" {
@@ -1368,7 +1485,6 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     *out = nullptr;
     int st = validate_params(p);
     if (st != ACAC_OK) return st;
-    if (p->batch > 1) return create_ensemble(p, cuda_stream, out);
     acac_handle* h = new (std::nothrow) acac_handle();
     if (!h) return ACAC_E_NOMEM;
     h->p = *p;
@@ -1382,7 +1498,16 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
     h->N = (size_t)p->n[0] * p->n[1] * (p->dim == 3 ? p->n[2] : 1);
     h->g = make_geom(p);
     h->k = Coef{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->taylor_S};
-    h->eta = p->eta0;
+    const int B = h->B = p->batch;
+    h->mk.assign(B, MemberK{p->alpha, p->beta, p->theta, p->gamma, p->rho, p->dt0, 1.0, 0.0});
+    h->t.assign(B, 0.0);
+    h->dt_prev.assign(B, 0.0);
+    h->eta.assign(B, p->eta0);
+    h->nstep.assign(B, 0);
+    h->have_prev.assign(B, 0);
+    h->fn.assign(B, 0.0);
+    h->fl.assign(B, 0);
+    for (auto& v : h->mask_host) v.assign(B, -1);   // nothing written yet
     st = build_subdomains(h);
     if (st != ACAC_OK) {
         cudaStreamDestroy(h->stream);
@@ -1390,21 +1515,40 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         return st;
     }
     try {
-        const size_t N = h->N, n2 = 2 * N, ks = h->ksz;
-        dmalloc(&h->X, n2 * 8); dmalloc(&h->X0, n2 * 8); dmalloc(&h->Xprev, n2 * 8);
-        dmalloc(&h->Xt, n2 * 8); dmalloc(&h->F, n2 * 8); dmalloc(&h->S, n2 * 8);
-        dmalloc(&h->G, 3 * N * 8); dmalloc(&h->b, n2 * 8); dmalloc(&h->r, n2 * 8); dmalloc(&h->tmpd, n2 * 8);
-        dmalloc(&h->stage, n2 * 8);
-        dmalloc(&h->lap0, n2 * 8);
-        dmalloc(&h->shift_dev, 16);
-        h->ldV = (n2 + 63) / 64 * 64;
+        const size_t N = h->N, n2 = 2 * N, ks = h->ksz, Bz = (size_t)B;
+        // per-member strides, 64 elements aligned (256 bytes for doubles): every member's
+        // buffers start where the single-problem kernels expect their alignment
+        auto r64 = [](long long e) { return (e + 63) / 64 * 64; };
+        Members& mb = h->mb;
+        mb.count = B;
+        mb.vs = r64((long long)n2);
+        mb.gs = r64(3LL * (long long)N);
+        mb.cs = r64(7LL * (long long)N);
+        mb.js = r64((long long)(p->dim == 3 ? NSLOT3 : NSLOT) * 4 * (long long)N);
+        mb.jps = r64(p->dim == 3 ? (h->coef_count / NCOEF3) * 4 * NSLOT3 : (h->coef_count / NCOEF) * 4 * NSLOT);
+        mb.cfs = r64(h->coef_count);
+        mb.rs = RS;
+        mb.ps = (long long)(MAX_RESTART + 3) * red_grid((long long)n2);
+        const size_t vz = (size_t)mb.vs * Bz;
+        dmalloc(&h->X, vz * 8); dmalloc(&h->X0, vz * 8); dmalloc(&h->Xprev, vz * 8);
+        dmalloc(&h->Xt, vz * 8); dmalloc(&h->F, vz * 8); dmalloc(&h->S, vz * 8);
+        dmalloc(&h->G, (size_t)mb.gs * Bz * 8); dmalloc(&h->b, vz * 8); dmalloc(&h->r, vz * 8);
+        dmalloc(&h->tmpd, vz * 8);
+        dmalloc(&h->stage, n2 * Bz * 8);
+        dmalloc(&h->lap0, vz * 8);
+        dmalloc(&h->mk_dev, sizeof(MemberK) * Bz);
+        dmalloc(&h->masks, sizeof(int) * MK_COUNT * Bz);
+        dmalloc(&h->ghead_dev, sizeof(GmresHead) * Bz);
+        dmalloc(&h->gwork_dev, sizeof(GmresWork) * Bz);
+        dmalloc(&h->kcnt_dev, sizeof(int) * Bz);
+        h->ldV = vz;
         dmalloc(&h->V, (size_t)(p->gmres_restart + 1) * h->ldV * ks);
         dmalloc(&h->Zb, (size_t)p->gmres_restart * h->ldV * ks);
-        dmalloc(&h->w, n2 * ks); dmalloc(&h->kt, n2 * ks);
-        dmalloc(&h->jtmp, 3 * N * ks);
-        dmalloc(&h->cache, 7 * N * ks);
-        dmalloc(&h->J, (size_t)(p->dim == 3 ? NSLOT3 : NSLOT) * 4 * N * ks);
-        dmalloc(&h->coef, (size_t)h->coef_count * ks);
+        dmalloc(&h->w, vz * ks); dmalloc(&h->kt, vz * ks);
+        dmalloc(&h->jtmp, (size_t)mb.gs * Bz * ks);
+        dmalloc(&h->cache, (size_t)mb.cs * Bz * ks);
+        dmalloc(&h->J, (size_t)mb.js * Bz * ks);
+        dmalloc(&h->coef, (size_t)(p->subdomain_solver == ACAC_SUB_ILU0 ? mb.cfs * Bz : 1) * ks);
         int dev = 0;
         CU(cudaGetDevice(&dev));
         int optin = 0;
@@ -1438,7 +1582,8 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             if (!vec_in_smem) {
                 size_t tot = 0;
                 for (auto& sd : h->subs) tot += (size_t)ras3_pitch(sd.W, (int)ks) * (sd.H + 4) * (sd.D + 4);
-                dmalloc(&h->gscratch, tot * 2 * ks);
+                mb.ss = r64((long long)tot * 2);
+                dmalloc(&h->gscratch, (size_t)mb.ss * Bz * ks);
             }
         } else {
         // shared-memory plan of the Schwarz apply: mbarriers | level table | coefficient
@@ -1472,7 +1617,8 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
                 L.stage_elems += (2 * h->ras_maxcnt + 8 + 31) / 32 * 32;
                 // float: the right-hand side gathered per box cell (in record order), read by the
                 // stages; 16 spare values for the chunked copies' overreach
-                if (ks == 4) dmalloc(&h->rg, ((size_t)(h->coef_count / NCOEF) * 2 + 16) * ks);
+                mb.rgs = r64((h->coef_count / NCOEF) * 2 + 16);
+                if (ks == 4) dmalloc(&h->rg, (size_t)mb.rgs * Bz * ks);
                 const size_t stage_bytes = (size_t)L.stage_elems * ks;
                 // aim at three CTAs per SM with at least 4 stages each
                 const size_t win_bytes = r128((size_t)5 * L.win_cells * 2 * ks);
@@ -1483,7 +1629,8 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
                 L.smem_bytes = L.vec_off + win_bytes;
                 size_t tot = 0;
                 for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
-                dmalloc(&h->gscratch, tot * 2 * ks);
+                mb.ss = r64((long long)tot * 2);
+                dmalloc(&h->gscratch, (size_t)mb.ss * Bz * ks);
             } else if (L.stage_off + vec_bytes + 3 * stage_bytes <= half) {
                 L.nbuf = (int)std::min<size_t>(RAS_MAXBUF, (half - L.stage_off - vec_bytes) / stage_bytes);
                 vec_in_smem = true;
@@ -1499,21 +1646,23 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
                 if (!vec_in_smem) {
                     size_t tot = 0;
                     for (auto& sd : h->subs) tot += (size_t)ras_pitch(sd.W) * (sd.H + 4);
-                    dmalloc(&h->gscratch, tot * 2 * ks);
+                    mb.ss = r64((long long)tot * 2);
+                dmalloc(&h->gscratch, (size_t)mb.ss * Bz * ks);
                 }
             }
         }
-        dmalloc(&h->partial, (size_t)RED_BLOCKS * (MAX_RESTART + 3) * 8);
-        dmalloc(&h->red, (size_t)3 * (MAX_RESTART + 1) * 8);
-        dmalloc(&h->flags, 16);
-        CU(cudaMemset(h->flags, 0, 16));
-        dmalloc(&h->counter, 16);
-        CU(cudaMemset(h->counter, 0, 16));
-        dmalloc(&h->jk_dev, sizeof(JacK<double>));
+        dmalloc(&h->partial, (size_t)mb.ps * Bz * 8);
+        dmalloc(&h->red, (size_t)RS * Bz * 8);
+        dmalloc(&h->flags, sizeof(int) * 2 * Bz);
+        CU(cudaMemset(h->flags, 0, sizeof(int) * 2 * Bz));
+        dmalloc(&h->counter, sizeof(unsigned) * Bz);
+        CU(cudaMemset(h->counter, 0, sizeof(unsigned) * Bz));
+        dmalloc(&h->jk_dev, sizeof(JacK<double>) * Bz);
+        mb.k = h->mk_dev;
         CU(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         CU(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
-        CU(cudaMallocHost((void**)&h->host, (size_t)3 * (MAX_RESTART + 1) * 8));
-        CU(cudaMallocHost((void**)&h->host_flags, 16));
+        CU(cudaMallocHost((void**)&h->host, (size_t)RS * Bz * 8));
+        CU(cudaMallocHost((void**)&h->host_flags, sizeof(int) * 3 * Bz));
         dmalloc(&h->subs_dev, h->subs.size() * sizeof(SubInfo));
         dmalloc(&h->lev_dev, h->lev.size() * sizeof(int));
         dmalloc(&h->cells3_dev, std::max<size_t>(1, h->cells3.size()) * sizeof(int));
@@ -1532,12 +1681,15 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
             h->own_of.clear();
             h->own_of.shrink_to_fit();
         }
-        dmalloc(&h->Jp, p->dim == 3 ? (size_t)(h->coef_count / NCOEF3) * 4 * NSLOT3 * h->ksz
-                                    : (size_t)(h->coef_count / NCOEF) * 4 * NSLOT * h->ksz);
+        dmalloc(&h->Jp, (size_t)mb.jps * Bz * h->ksz);
         h->rec_of.clear();
         h->rec_of.shrink_to_fit();
         if (p->subdomain_solver != ACAC_SUB_ILU0) build_sparse(h);
         CU(set_taylor_constants(p->taylor_S));
+        std::vector<int> ones(B, 1);
+        set_mask(h, MK_NEWTON, ones);
+        write_members_any(h);
+        CU(cudaStreamSynchronize(h->stream));
     } catch (Err e) {
         free_all(h);
         delete h;
@@ -1549,10 +1701,6 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
 
 void acac_destroy(acac_handle* h) {
     if (!h) return;
-    if (!h->members.empty()) {
-        destroy_ensemble(h);
-        return;
-    }
     cudaStreamSynchronize(h->stream);
     for (auto& p : h->pending) {
         if (p.owned_by_graph) continue;
@@ -1575,13 +1723,6 @@ int acac_profile(acac_handle* h, int enable) { return acac_profile_mask(h, enabl
 
 int acac_profile_mask(acac_handle* h, unsigned mask) {
     if (!h) return ACAC_E_ARG;
-    if (is_ensemble(h)) {
-        for (acac_handle* m : h->members) {
-            const int st = acac_profile_mask(m, mask);
-            if (st != ACAC_OK) return st;
-        }
-        return ACAC_OK;
-    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
     try {
         prof_collect(h);
@@ -1602,24 +1743,6 @@ int acac_profile_mask(acac_handle* h, unsigned mask) {
 int acac_kernel_stats(acac_handle* h, int kernel, long long* launches, double* total_ms, double* bytes,
                       double* flops) {
     if (!h || kernel < 0 || kernel >= ACAC_NKERNEL) return ACAC_E_ARG;
-    if (is_ensemble(h)) {
-        // sums over the members (their kernels overlap in time: the sum of the
-        // durations exceeds the wall time)
-        long long n = 0;
-        double ms = 0.0, b = 0.0, f = 0.0;
-        for (acac_handle* m : h->members) {
-            long long n1 = 0;
-            double ms1 = 0.0, b1 = 0.0, f1 = 0.0;
-            const int st = acac_kernel_stats(m, kernel, &n1, &ms1, &b1, &f1);
-            if (st != ACAC_OK) return st;
-            n += n1; ms += ms1; b += b1; f += f1;
-        }
-        if (launches) *launches = n;
-        if (total_ms) *total_ms = ms;
-        if (bytes) *bytes = b;
-        if (flops) *flops = f;
-        return ACAC_OK;
-    }
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return ACAC_E_CUDA;
     try {
         prof_collect(h);
@@ -1637,14 +1760,15 @@ int acac_set_coeffs(acac_handle* h, int member, double alpha, double beta, doubl
                     double rho) {
     if (!h) return ACAC_E_ARG;
     if (!(alpha > 0 && beta > 0 && theta > 0 && gamma > 0 && rho > 0)) return ACAC_E_ARG;
-    if (is_ensemble(h)) {
-        if (member < 0 || member >= (int)h->members.size()) return ACAC_E_ARG;
-        h = h->members[member];
-    } else if (member != 0) {
-        return ACAC_E_ARG;
+    if (member < 0 || member >= h->B) return ACAC_E_ARG;
+    MemberK& q = h->mk[member];
+    q.alpha = alpha; q.beta = beta; q.theta = theta; q.gamma = gamma; q.rho = rho;
+    if (member == 0) {
+        h->p.alpha = alpha; h->p.beta = beta; h->p.theta = theta; h->p.gamma = gamma; h->p.rho = rho;
+        h->k = Coef{alpha, beta, theta, gamma, rho, h->p.taylor_S};
     }
-    h->p.alpha = alpha; h->p.beta = beta; h->p.theta = theta; h->p.gamma = gamma; h->p.rho = rho;
-    h->k = Coef{alpha, beta, theta, gamma, rho, h->p.taylor_S};
+    // on the device with the next step (write_members); single-problem calls write them
+    // with their dt
     return ACAC_OK;
 }
 
@@ -1656,18 +1780,18 @@ const char* acac_kernel_name(int kernel) {
 }
 
 int acac_residual(acac_handle* h, const double* X1, const double* X0, double dt, double* F, double* fnorm) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !F || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
         const size_t n2 = 2 * h->N;
         CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
-        int fl = 0;
-        double fn = eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
+        set_dt0(h, dt);
+        eval_residual(h, -1, X1, false);
         CU(cudaMemcpyAsync(F, h->F, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
         CU(cudaStreamSynchronize(h->stream));
-        if (fnorm) *fnorm = fn;
-        return (fl & 1) ? ACAC_E_DOMAIN : ACAC_OK;
+        if (fnorm) *fnorm = h->fn[0];
+        return (h->fl[0] & 1) ? ACAC_E_DOMAIN : ACAC_OK;
     } catch (Err e) {
         return e.code;
     }
@@ -1677,30 +1801,29 @@ int acac_residual(acac_handle* h, const double* X1, const double* X0, double dt,
 static int linearize_at(acac_handle* h, const double* X1, const double* X0, double dt) {
     const size_t n2 = 2 * h->N;
     CU(cudaMemcpyAsync(h->X0, X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
-    int fl = 0;
-    eval_residual(h, X1, nullptr, 0.0, 0.0, dt, &fl);
-    if (fl & 1) return ACAC_E_DOMAIN;
-    if (h->mixed) {
-        set_jac<float>(h, dt);
+    set_dt0(h, dt);
+    eval_residual(h, -1, X1, false);
+    if (h->fl[0] & 1) return ACAC_E_DOMAIN;
+    if (h->mixed)
         KL(ACAC_K_LINEARIZE, launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream));
-    } else {
-        set_jac<double>(h, dt);
+    else
         KL(ACAC_K_LINEARIZE, launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream));
-    }
     return ACAC_OK;
 }
 
 int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt, void* J) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !J || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
         if (h->mixed)
-            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, (const JacK<float>*)h->jk_dev, cache_of<float>(h),
+                                                       (float*)J, h->stream));
         else
-            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)J, h->stream));
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, (const JacK<double>*)h->jk_dev, cache_of<double>(h),
+                                                        (double*)J, h->stream));
         CU(cudaStreamSynchronize(h->stream));
         return ACAC_OK;
     } catch (Err e) {
@@ -1709,7 +1832,7 @@ int acac_jacobian(acac_handle* h, const double* X1, const double* X0, double dt,
 }
 
 int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !J || !w || !y) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1724,14 +1847,14 @@ int acac_spmv(acac_handle* h, const void* J, const void* w, void* y) {
 }
 
 int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, const void* w, void* y) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !w || !y || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
-        if (h->mixed) jvp_action<float>(h, (const float*)w, (float*)y);
-        else jvp_action<double>(h, (const double*)w, (double*)y);
+        if (h->mixed) jvp_action<float>(h, all_members(h), (const float*)w, (float*)y);
+        else jvp_action<double>(h, all_members(h), (const double*)w, (double*)y);
         return ACAC_OK;
     } catch (Err e) {
         return e.code;
@@ -1739,26 +1862,26 @@ int acac_jvp(acac_handle* h, const double* X1, const double* X0, double dt, cons
 }
 
 int acac_ras_factor(acac_handle* h, const void* J) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !J) return ACAC_E_ARG;
     Join join(h);
     try {
         const size_t bytes = (size_t)(h->g.dim == 3 ? NSLOT3 : NSLOT) * 4 * h->N * h->ksz;
         if (J != h->J) CU(cudaMemcpyAsync(h->J, J, bytes, cudaMemcpyDeviceToDevice, h->stream));
         h->jpacked = false;
-        return h->mixed ? factor<float>(h) : factor<double>(h);
+        return h->mixed ? factor<float>(h, all_members(h)) : factor<double>(h, all_members(h));
     } catch (Err e) {
         return e.code;
     }
 }
 
 int acac_ras_apply(acac_handle* h, const void* r, void* z) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !r || !z) return ACAC_E_ARG;
     Join join(h);
     try {
-        if (h->mixed) precond<float>(h, (const float*)r, (float*)z);
-        else precond<double>(h, (const double*)r, (double*)z);
+        if (h->mixed) precond<float>(h, all_members(h), (const float*)r, (float*)z);
+        else precond<double>(h, all_members(h), (const double*)r, (double*)z);
         return ACAC_OK;
     } catch (Err e) {
         return e.code;
@@ -1767,27 +1890,31 @@ int acac_ras_apply(acac_handle* h, const void* r, void* z) {
 
 int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, const double* b, double* x,
                int* its, double* resid) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !b || !x || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
         int st = linearize_at(h, X1, X0, dt);
         if (st != ACAC_OK) return st;
-        int gi = 0;
-        double gr = 0.0;
         CU(cudaMemcpyAsync(h->b, b, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
         h->jpacked = false;
+        const std::vector<int> one(1, 1);
+        std::vector<int> gst(1, ACAC_OK), gits(1, 0);
+        std::vector<double> gres(1, 0.0);
         if (h->mixed) {
-            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, dt, cache_of<float>(h), (float*)h->J, h->stream));
-            st = factor<float>(h);
-            if (st == ACAC_OK) st = gmres<float>(h, x, &gi, &gr);
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, (const JacK<float>*)h->jk_dev, cache_of<float>(h),
+                                                       (float*)h->J, h->stream));
+            st = factor<float>(h, all_members(h));
+            if (st == ACAC_OK) gmres<float>(h, one, x, gst, gits, gres, nullptr);
         } else {
-            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, dt, cache_of<double>(h), (double*)h->J, h->stream));
-            st = factor<double>(h);
-            if (st == ACAC_OK) st = gmres<double>(h, x, &gi, &gr);
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, (const JacK<double>*)h->jk_dev, cache_of<double>(h),
+                                                        (double*)h->J, h->stream));
+            st = factor<double>(h, all_members(h));
+            if (st == ACAC_OK) gmres<double>(h, one, x, gst, gits, gres, nullptr);
         }
-        if (its) *its = gi;
-        if (resid) *resid = gr;
+        if (st == ACAC_OK) st = gst[0];
+        if (its) *its = gits[0];
+        if (resid) *resid = gres[0];
         return st;
     } catch (Err e) {
         return e.code;
@@ -1795,7 +1922,7 @@ int acac_gmres(acac_handle* h, const double* X1, const double* X0, double dt, co
 }
 
 int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac_step_info* info) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !U0 || !U1 || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     acac_step_info local;
@@ -1803,7 +1930,10 @@ int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac
     int st;
     try {
         CU(cudaMemcpyAsync(h->X0, U0, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
-        st = nks_dispatch(h, dt, &local);
+        set_dt0(h, dt);
+        std::vector<int> sv;
+        nks_dispatch(h, std::vector<int>(1, 1), sv, &local);
+        st = sv[0];
         if (st == ACAC_OK) CU(cudaMemcpyAsync(U1, h->X, 2 * h->N * 8, cudaMemcpyDeviceToDevice, h->stream));
         CU(cudaStreamSynchronize(h->stream));
     } catch (Err e) {
@@ -1816,7 +1946,7 @@ int acac_nks_solve(acac_handle* h, const double* U0, double dt, double* U1, acac
 }
 
 int acac_jacobian_x0(acac_handle* h, const double* X1, const double* X0, double dt, void* J) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !J || !(dt > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1824,10 +1954,14 @@ int acac_jacobian_x0(acac_handle* h, const double* X1, const double* X0, double 
         if (st != ACAC_OK) return st;
         if (h->mixed) {
             KL(ACAC_K_LINEARIZE, launch_linearize<float>(h->g, h->k, X1, h->X0, h->G, cache_of<float>(h), h->stream, 1));
-            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, h->k, -dt, cache_of<float>(h), (float*)J, h->stream));
+            set_dt0(h, -dt);
+            KL(ACAC_K_ASSEMBLE, launch_assemble<float>(h->g, (const JacK<float>*)h->jk_dev, cache_of<float>(h),
+                                                       (float*)J, h->stream));
         } else {
             KL(ACAC_K_LINEARIZE, launch_linearize<double>(h->g, h->k, X1, h->X0, h->G, cache_of<double>(h), h->stream, 1));
-            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, h->k, -dt, cache_of<double>(h), (double*)J, h->stream));
+            set_dt0(h, -dt);
+            KL(ACAC_K_ASSEMBLE, launch_assemble<double>(h->g, (const JacK<double>*)h->jk_dev, cache_of<double>(h),
+                                                        (double*)J, h->stream));
         }
         CU(cudaStreamSynchronize(h->stream));
         return ACAC_OK;
@@ -1837,7 +1971,7 @@ int acac_jacobian_x0(acac_handle* h, const double* X1, const double* X0, double 
 }
 
 int acac_spmv_t(acac_handle* h, const void* J, const void* w, void* y) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !J || !w || !y) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1857,7 +1991,7 @@ int acac_spmv_t(acac_handle* h, const void* J, const void* w, void* y) {
 
 int acac_loss(acac_handle* h, const double* X, const double* target, double w_energy, double w_misfit,
               double* loss, double* dX, double* grad) {
-    if (is_ensemble(h)) return ACAC_E_ARG;
+    if (h && h->B > 1) return ACAC_E_ARG;
     if (!h || !X || !target || !dX) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1873,7 +2007,7 @@ int acac_loss(acac_handle* h, const double* X, const double* target, double w_en
 
 int acac_adjoint_step(acac_handle* h, const double* X1, const double* X0, double dt, const double* lam1,
                       double* lam0, double* grad, double rtol, int* gmres_its) {
-    if (is_ensemble(h) || (h && (h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0))) return ACAC_E_ARG;
+    if (h && (h->B > 1 || h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0)) return ACAC_E_ARG;
     if (!h || !X1 || !X0 || !lam1 || !lam0 || !(dt > 0) || !(rtol > 0)) return ACAC_E_ARG;
     Join join(h);
     try {
@@ -1894,7 +2028,7 @@ int acac_adjoint_step(acac_handle* h, const double* X1, const double* X0, double
 int acac_adjoint(acac_handle* h, const double* u0, const double* v0, int nsteps, double dt, int checkpoint_every,
                  const double* u_target, const double* v_target, double w_energy, double w_misfit, double rtol,
                  double* loss, double* du0, double* dv0, double* grad, int* gmres_its) {
-    if (is_ensemble(h) || (h && (h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0))) return ACAC_E_ARG;
+    if (h && (h->B > 1 || h->mixed || h->p.subdomain_solver != ACAC_SUB_ILU0)) return ACAC_E_ARG;
     if (!h || !u0 || !v0 || !u_target || !v_target || !du0 || !dv0 || nsteps < 1 || !(dt > 0) ||
         checkpoint_every < 1 || !(rtol > 0))
         return ACAC_E_ARG;
@@ -1923,7 +2057,10 @@ int acac_adjoint(acac_handle* h, const double* u0, const double* v0, int nsteps,
         int its = 0;
         auto step_from_X0 = [&](acac_step_info* info) {
             memset(info, 0, sizeof(*info));
-            return nks_dispatch(h, dt, info);
+            set_dt0(h, dt);
+            std::vector<int> sv;
+            nks_dispatch(h, std::vector<int>(1, 1), sv, info);
+            return sv[0];
         };
         for (int k = 0; k < nsteps; ++k) {
             if (k % every == 0)
@@ -2036,31 +2173,23 @@ int acac_autotune(const acac_params* p, const double* u, const double* v, int tr
     return rc;
 }
 
-static int energy_of(acac_handle* h, const double* X, double* e, double* m) {
-    CU(cudaMemsetAsync(h->flags, 0, sizeof(int), h->stream));
-    KLA(ACAC_K_ENERGY, 16.0 * h->N, 0.0, launch_energy(h->g, h->k, X, red_to(h, h->red), h->flags, h->stream));
-    CU(cudaMemcpyAsync(h->host_flags, h->flags, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
-    read_scalars(h, 2);
-    if (e) *e = h->host[0];
-    if (m) *m = h->host[1];
-    return *h->host_flags ? ACAC_E_DOMAIN : ACAC_OK;
-}
-
 int acac_energy(acac_handle* h, const double* u, const double* v, double* energy, double* mass) {
     if (!h || !u || !v) return ACAC_E_ARG;
-    if (is_ensemble(h)) {
-        const size_t N = h->N;
-        return for_members(h, [&](int m) {
-            return acac_energy(h->members[m], u + m * N, v + m * N, energy ? energy + m : nullptr,
-                               mass ? mass + m : nullptr);
-        });
-    }
     Join join(h);
     try {
         const size_t N = h->N;
-        CU(cudaMemcpyAsync(h->tmpd, u, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-        CU(cudaMemcpyAsync(h->tmpd + N, v, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-        return energy_of(h, h->tmpd, energy, mass);
+        // member states [u | v] in tmpd, then one launch over the members
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_pack_members(u, v, h->tmpd, (long long)N, 1, h->stream, all_members(h)));
+        std::vector<double> e, ms;
+        std::vector<int> bad;
+        energy_members(h, -1, h->tmpd, e, ms, bad);
+        int st = ACAC_OK;
+        for (int m = 0; m < h->B; ++m) {
+            if (energy) energy[m] = e[m];
+            if (mass) mass[m] = ms[m];
+            if (bad[m] && st == ACAC_OK) st = ACAC_E_DOMAIN;
+        }
+        return st;
     } catch (Err e) {
         return e.code;
     }
@@ -2068,78 +2197,34 @@ int acac_energy(acac_handle* h, const double* u, const double* v, double* energy
 
 int acac_step(acac_handle* h, double* u, double* v, acac_step_info* info) {
     if (!h || !u || !v) return ACAC_E_ARG;
-    if (is_ensemble(h)) {
-        const size_t N = h->N;
-        return for_members(h, [&](int m) {
-            return acac_step(h->members[m], u + m * N, v + m * N, info ? info + m : nullptr);
-        });
-    }
     Join join(h);
-    acac_step_info local;
-    memset(&local, 0, sizeof(local));
-    int st = ACAC_OK;
     try {
-        const size_t N = h->N;
-        const long long n2 = 2 * (long long)N;
-        CU(cudaMemcpyAsync(h->X0, u, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-        CU(cudaMemcpyAsync(h->X0 + N, v, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-        // predictor of Eq. sencondt
-        double dt = h->p.dt0;
-        if (h->p.dt_mode == ACAC_DT_ADAPTIVE && h->have_prev) {
-            KL(ACAC_K_VECTOR, launch_norm2_double(h->X0, h->Xprev, n2, red_to(h, h->red), h->stream));
-            const double xd = sqrt(read_scalars(h, 1)) / h->dt_prev;
-            dt = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta * xd * xd));
-        }
-        while (true) {
-            st = nks_dispatch(h, dt, &local);
-            if (st == ACAC_OK) break;
-            if (st != ACAC_E_DIVERGED) break;
-            local.divergences++;
-            if (h->p.dt_mode == ACAC_DT_FIXED) break;
-            dt = dt / sqrt(2.0);
-            h->eta *= 2.0;
-            if (dt < h->p.dt_min) {
-                st = ACAC_E_DT_UNDERFLOW;
-                break;
-            }
-        }
-        if (st == ACAC_OK) {
-            CU(cudaMemcpyAsync(h->Xprev, h->X0, n2 * 8, cudaMemcpyDeviceToDevice, h->stream));
-            CU(cudaMemcpyAsync(u, h->X, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-            CU(cudaMemcpyAsync(v, h->X + N, N * 8, cudaMemcpyDeviceToDevice, h->stream));
-            h->dt_prev = dt;
-            h->t += dt;
-            h->nstep++;
-            h->have_prev = true;
-            double e = 0.0, m = 0.0;
-            energy_of(h, h->X, &e, &m);
-            local.energy = e;
-            local.mass = m;
-            local.dt = dt;
-            local.t = h->t;
-        }
-        local.eta = h->eta;
+        return step_members(h, u, v, info);
     } catch (Err e) {
-        st = e.code;
+        if (info)
+            for (int m = 0; m < h->B; ++m) info[m].status = e.code;
+        return e.code;
     }
-    local.status = st;
-    if (info) *info = local;
-    return st;
 }
 
 int acac_step_host(acac_handle* h, double* u_host, double* v_host, acac_step_info* info) {
     if (!h || !u_host || !v_host) return ACAC_E_ARG;
     Join join(h);
     try {
-        const size_t N = h->N * (is_ensemble(h) ? h->members.size() : 1);
+        const size_t N = h->N * h->B;
         CU(cudaMemcpyAsync(h->stage, u_host, N * 8, cudaMemcpyHostToDevice, h->stream));
         CU(cudaMemcpyAsync(h->stage + N, v_host, N * 8, cudaMemcpyHostToDevice, h->stream));
-        int st = acac_step(h, h->stage, h->stage + N, info);
-        // an ensemble copies every member back: a failed member's fields are unchanged
-        if (st == ACAC_OK || is_ensemble(h)) {
-            CU(cudaMemcpyAsync(u_host, h->stage, N * 8, cudaMemcpyDeviceToHost, h->stream));
-            CU(cudaMemcpyAsync(v_host, h->stage + N, N * 8, cudaMemcpyDeviceToHost, h->stream));
+        int st;
+        try {
+            st = step_members(h, h->stage, h->stage + N, info);
+        } catch (Err e) {
+            if (info)
+                for (int m = 0; m < h->B; ++m) info[m].status = e.code;
+            st = e.code;
         }
+        // every member is copied back: a failed member's fields are unchanged
+        CU(cudaMemcpyAsync(u_host, h->stage, N * 8, cudaMemcpyDeviceToHost, h->stream));
+        CU(cudaMemcpyAsync(v_host, h->stage + N, N * 8, cudaMemcpyDeviceToHost, h->stream));
         CU(cudaStreamSynchronize(h->stream));
         return st;
     } catch (Err e) {

@@ -197,7 +197,11 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(256) sparse_init_kernel(Geom g, const SubInfo* __restrict__ subs,
                                                           const SparseBox* __restrict__ boxes,
                                                           const SparseShapeDev* __restrict__ shapes,
-                                                          const T* __restrict__ J, T* __restrict__ val) {
+                                                          const T* __restrict__ J, T* __restrict__ val, Members mb) {
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    J += (size_t)mem * mb.js;
+    val += (size_t)mem * mb.cfs;
     const SubInfo sd = subs[blockIdx.x];
     const SparseBox bx = boxes[blockIdx.x];
     const SparseShapeDev sh = shapes[bx.shape];
@@ -234,8 +238,13 @@ __global__ void __launch_bounds__(256) sparse_init_kernel(Geom g, const SubInfo*
 template <typename T>
 __global__ void __launch_bounds__(1024) sparse_factor_kernel(const SparseBox* __restrict__ boxes,
                                                              const SparseShapeDev* __restrict__ shapes,
-                                                             T* val, T* dinv, int* flags, int use_map) {
+                                                             T* val, T* dinv, int* flags, int use_map, Members mb) {
     extern __shared__ int smem[];
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    val += (size_t)mem * mb.cfs;
+    dinv += (size_t)mem * mb.rgs;
+    flags += mem;
     const SparseBox bx = boxes[blockIdx.x];
     const SparseShapeDev sh = shapes[bx.shape];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -336,8 +345,15 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
                                                            const SparseShapeDev* __restrict__ shapes,
                                                            const T* __restrict__ val, const T* __restrict__ dinv,
                                                            const T* __restrict__ r, T* __restrict__ z, int ras_type,
-                                                           T* yscratch, int in_smem) {
+                                                           T* yscratch, int in_smem, Members mb) {
     extern __shared__ __align__(16) unsigned char sraw[];
+    const int mem = blockIdx.y;
+    if (member_off(mb, mem)) return;
+    val += (size_t)mem * mb.cfs;
+    dinv += (size_t)mem * mb.rgs;
+    r += (size_t)mem * mb.vs;
+    z += (size_t)mem * mb.vs;
+    if (yscratch) yscratch += (size_t)mem * mb.ss;
     const SubInfo sd = subs[blockIdx.x];
     const SparseBox bx = boxes[blockIdx.x];
     const SparseShapeDev sh = shapes[bx.shape];
@@ -444,29 +460,32 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
 
 template <typename T>
 cudaError_t launch_sparse_init(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
-                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s) {
-    if (g.dim == 3) sparse_init_kernel<T, 3><<<nbox, 256, 0, s>>>(g, subs, boxes, shapes, J, val);
-    else sparse_init_kernel<T, 2><<<nbox, 256, 0, s>>>(g, subs, boxes, shapes, J, val);
+                               const SparseShapeDev* shapes, const T* J, T* val, cudaStream_t s, const Members& mb) {
+    const dim3 grid(nbox, mb.count);
+    if (g.dim == 3) sparse_init_kernel<T, 3><<<grid, 256, 0, s>>>(g, subs, boxes, shapes, J, val, mb);
+    else sparse_init_kernel<T, 2><<<grid, 256, 0, s>>>(g, subs, boxes, shapes, J, val, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_sparse_factor(int nbox, const SparseBox* boxes, const SparseShapeDev* shapes, T* val, T* dinv,
-                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s) {
+                                 int* flags, int threads, size_t smem, int use_map, cudaStream_t s,
+                                 const Members& mb) {
     if (threads < 32 || threads > 1024 || threads % 32) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sparse_factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    sparse_factor_kernel<T><<<nbox, threads, smem, s>>>(boxes, shapes, val, dinv, flags, use_map);
+    sparse_factor_kernel<T><<<dim3(nbox, mb.count), threads, smem, s>>>(boxes, shapes, val, dinv, flags, use_map, mb);
     return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
                                 const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
-                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s) {
+                                int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s,
+                                const Members& mb) {
     if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sparse_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -474,22 +493,22 @@ cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, co
         if (e != cudaSuccess) return e;
     }
     if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * 2 * (size_t)g.N, s);
+        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
         if (e != cudaSuccess) return e;
     }
-    sparse_apply_kernel<T><<<nbox, threads, smem, s>>>(g, subs, boxes, shapes, val, dinv, r, z, ras_type, yscratch,
-                                                       smem > 0 ? 1 : 0);
+    sparse_apply_kernel<T><<<dim3(nbox, mb.count), threads, smem, s>>>(g, subs, boxes, shapes, val, dinv, r, z,
+                                                                       ras_type, yscratch, smem > 0 ? 1 : 0, mb);
     return cudaGetLastError();
 }
 
 #define INST(T)                                                                                                   \
     template cudaError_t launch_sparse_init<T>(const Geom&, int, const SubInfo*, const SparseBox*,                 \
-                                               const SparseShapeDev*, const T*, T*, cudaStream_t);                \
+                                               const SparseShapeDev*, const T*, T*, cudaStream_t, const Members&); \
     template cudaError_t launch_sparse_factor<T>(int, const SparseBox*, const SparseShapeDev*, T*, T*, int*, int,  \
-                                                 size_t, int, cudaStream_t);                                      \
+                                                 size_t, int, cudaStream_t, const Members&);                      \
     template cudaError_t launch_sparse_apply<T>(const Geom&, int, const SubInfo*, const SparseBox*,                \
                                                 const SparseShapeDev*, const T*, const T*, const T*, T*, int, T*,  \
-                                                int, size_t, cudaStream_t);
+                                                int, size_t, cudaStream_t, const Members&);
 INST(double)
 INST(float)
 #undef INST

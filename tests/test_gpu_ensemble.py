@@ -195,3 +195,97 @@ def test_autotune_picks_a_valid_partition():
     (uo, vo), _ = O.Stepper(p).step(u, v)
     xo = soa(uo, vo)
     assert np.linalg.norm(soa(host(ug), host(vg)) - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_ensemble_one_launch_per_kernel():
+    """The members are solved in lockstep: one Schwarz apply launch per Arnoldi step for
+    the whole ensemble (not one per member), so an eight-member step launches the apply
+    about as often as its slowest member iterates, far fewer times than the members'
+    iterations summed."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    p1 = Params(n=(64, 48, 1), ras_parts=(4, 3, 1), ras_overlap=2, precision=PREC_MIXED, dt0=1e-3)
+    B = 8
+    fields = _members(p1, tuple(range(50, 50 + B)))
+    u, v = _stack(fields)
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    with P.Solver(p1.replace(batch=B)) as s:
+        for m in range(B):
+            s.set_coeffs(m, p1.alpha, p1.beta, 0.25 + 0.01 * m, p1.gamma, p1.rho)
+        s.step(ug, vg)
+        s.profile(True)
+        infos = s.step(ug, vg)
+        stats = s.kernel_stats()
+        s.profile(False)
+    torch.cuda.synchronize()
+    its = [i.gmres_its for i in infos]
+    newton = max(i.newton_its for i in infos)
+    applies = stats["ras_apply"][0]
+    assert min(its) >= 2
+    # the Arnoldi steps of the slowest member, plus at most a restart length of steps
+    # launched past convergence per Newton iteration before the host looks
+    assert applies <= max(its) + newton * p1.gmres_restart
+    assert applies < sum(its) / 2, (applies, its)
+
+
+def test_ensemble_3d_member_equals_single_handle():
+    """3D Neumann members with uneven boxes (17 cells split 2 ways, overlap 2), mixed
+    precision: member m of a two-member ensemble is bit-identical to a batch-1 handle."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    from workloads import BC_NEUMANN
+    p1 = Params(dim=3, n=(17, 16, 15), bc=BC_NEUMANN, ras_parts=(2, 2, 2), ras_overlap=2, precision=PREC_MIXED,
+                dt0=1e-3)
+    fields = _members(p1, (71, 72))
+    u, v = _stack(fields)
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    thetas = (0.27, 0.33)
+    with P.Solver(p1.replace(batch=2)) as s:
+        for m, t in enumerate(thetas):
+            s.set_coeffs(m, p1.alpha, p1.beta, t, p1.gamma, p1.rho)
+        ens = [s.step(ug, vg) for _ in range(2)]
+    torch.cuda.synchronize()
+    gu, gv = host(ug).reshape(2, -1), host(vg).reshape(2, -1)
+    for m in range(2):
+        su, sv = dev(fields[m][0].ravel()), dev(fields[m][1].ravel())
+        with P.Solver(p1.replace(theta=thetas[m])) as one:
+            solo = [one.step(su, sv) for _ in range(2)]
+        torch.cuda.synchronize()
+        assert np.array_equal(host(su), gu[m]) and np.array_equal(host(sv), gv[m]), m
+        assert [i.gmres_its for i in solo] == [e[m].gmres_its for e in ens]
+
+
+def test_ensemble_member_retry_matches_single_handle():
+    """Adaptive steps where the members' Newton solves diverge at different times (a very
+    large dt0 and dt_max with theta spread): each member retries with its own dt while the
+    others wait, and still equals a batch-1 handle bit for bit, dt and divergence count
+    included."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    p1 = Params(n=(48, 40, 1), ras_parts=(3, 2, 1), ras_overlap=1, dt_mode=DT_ADAPTIVE, dt0=5.0, dt_min=1e-6,
+                dt_max=5.0, eta0=1.0, newton_maxit=4)
+    thetas = (0.22, 0.3, 0.38)
+    B = len(thetas)
+    fields = _members(p1, (81, 82, 83))
+    u, v = _stack(fields)
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    with P.Solver(p1.replace(batch=B)) as s:
+        for m, t in enumerate(thetas):
+            s.set_coeffs(m, p1.alpha, p1.beta, t, p1.gamma, p1.rho)
+        ens = [s.step(ug, vg, check=False) for _ in range(2)]
+    torch.cuda.synchronize()
+    gu, gv = host(ug).reshape(B, -1), host(vg).reshape(B, -1)
+    for m in range(B):
+        su, sv = dev(fields[m][0].ravel()), dev(fields[m][1].ravel())
+        with P.Solver(p1.replace(theta=thetas[m])) as one:
+            solo = [one.step(su, sv, check=False) for _ in range(2)]
+        torch.cuda.synchronize()
+        assert np.array_equal(host(su), gu[m]) and np.array_equal(host(sv), gv[m]), m
+        for k in range(2):
+            a, b = solo[k], ens[k][m]
+            assert (a.status, a.dt, a.divergences, a.gmres_its, a.newton_its) == \
+                   (b.status, b.dt, b.divergences, b.gmres_its, b.newton_its), (m, k)
+    assert sum(e.divergences for e in ens[0]) > 0   # the retry path was taken
