@@ -139,11 +139,13 @@ void acac_default_params(acac_params *p);
  * direction, a 2D cell in more than four boxes (overlap not below the owned box
  * width), dim not 2 or 3, batch outside 1..ACAC_MAX_BATCH), ACAC_E_NOMEM,
  * ACAC_E_CUDA.
- * Ensembles (batch B > 1): the handle holds B member solvers, each with its own
- * workspace and its own CUDA stream (ordered after cuda_stream at the start of each
- * call and before it at the end), and a pool of host threads that drives the
- * members' solves concurrently so that their kernels share the GPU.  Every member
- * starts with the coefficients of *p. */
+ * Ensembles (batch B > 1): the handle holds B independent problems of this grid and
+ * box decomposition and solves them in lockstep: every kernel launch covers all
+ * members, per-member masks on the device say which members take part, and every
+ * per-member buffer is B copies at a fixed stride (device memory grows about B-fold).
+ * The handle's work runs on a private stream ordered after cuda_stream at the start
+ * of each call and before it at the end.  Every member starts with the coefficients
+ * of *p. */
 int acac_create(const acac_params *p, void *cuda_stream, acac_handle **out);
 
 /* Coefficients alpha, beta, theta, gamma, rho (all > 0, Eq. 2 and Eq. 1) of ensemble
@@ -218,7 +220,9 @@ int acac_jvp(acac_handle *h, const double *X1, const double *X0, double dt,
 int acac_ras_factor(acac_handle *h, const void *J);
 
 /* z = H^{-1} r with the Schwarz preconditioner of params.ras_type and the factors
- * of the last acac_ras_factor (Krylov precision, device). */
+ * of the last acac_ras_factor (Krylov precision, device).  Deterministic for every
+ * ras_type: where boxes overlap (AS, right-RAS) their values are added per cell in a
+ * fixed order. */
 int acac_ras_apply(acac_handle *h, const void *r, void *z);
 
 /* Solve J(X1) x = b by restarted right-preconditioned GMRES (Sec. 3.1, Eq.
@@ -245,10 +249,11 @@ int acac_nks_solve(acac_handle *h, const double *U0, double dt, double *U1,
  * 96, 128, 192 or 240 cells per direction, each with overlap 1 and 2, that acac_create
  * accepts.  The box shape trades the preconditioner's strength (GMRES iterations)
  * against the length of the triangular sweeps and the parallelism across boxes, so
- * each candidate is timed end to end: one untimed step from (u, v) (device, N doubles
- * each, not modified), then trial_steps timed steps continuing from it.
- * *best_ms_per_step and *ncandidates (host, may be NULL) report the best time and
- * the number of candidates tried.  ACAC_E_ARG on bad arguments or batch != 1,
+ * each candidate is timed end to end: one untimed step from (u, v) (device, B*N
+ * doubles each for an ensemble of batch B, not modified), then trial_steps timed steps
+ * continuing from it (an ensemble is timed as a whole, every member with the
+ * coefficients of *p).  *best_ms_per_step and *ncandidates (host, may be NULL) report
+ * the best time and the number of candidates tried.  ACAC_E_ARG on bad arguments,
  * ACAC_E_DIVERGED when no candidate completes its steps.  Synchronises. */
 int acac_autotune(const acac_params *p, const double *u, const double *v, int trial_steps,
                   void *cuda_stream, acac_params *best, double *best_ms_per_step,

@@ -252,7 +252,7 @@ def acac_autotune(p, u, v, trial_steps=3, stream=None):
     import torch
     if stream is None:
         stream = torch.cuda.current_stream()
-    n = int(p.n[0]) * int(p.n[1]) * (int(p.n[2]) if p.dim == 3 else 1)
+    n = int(p.n[0]) * int(p.n[1]) * (int(p.n[2]) if p.dim == 3 else 1) * int(getattr(p, "batch", 1))
     cp = to_c_params(p)
     best = acac_params()
     ms, nc = ctypes.c_double(), ctypes.c_int()

@@ -160,6 +160,7 @@ struct Members {
     long long cfs = 0;            // Schwarz factors; 2x2 blocks of the fill solvers
     long long ss = 0;             // global scratch of the Schwarz apply (box vectors)
     long long rgs = 0;            // gathered right-hand side (windowed apply); fill solvers' inverse pivots
+    long long zs = 0;             // box-cell results of the additive extensions (AS, right-RAS)
     long long ps = 0;             // reduction partials
     int rs = 0;                   // device scalars (reduction results, Hessenberg columns)
 };
@@ -577,11 +578,17 @@ template <typename T>
 cudaError_t launch_ras_factor(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                               const T* J, int packed, T* coef, int threads, int ring_cells, size_t smem_bytes,
                               int* flags, cudaStream_t s, const Members& mb = Members{});
+// ras_type AS / right-RAS: every box writes its cells' values by record into zb (2 values per
+// box cell, member stride zs), then z is formed per grid cell from its records (rec_of) in a
+// fixed order: launch_ext_gather.  Left-RAS writes the owned cells of z directly.
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s,
-                             const Members& mb = Members{});
+                             const Members& mb = Members{}, const int* rec_of = nullptr, T* zb = nullptr);
+template <typename T>
+cudaError_t launch_ext_gather(const Geom& g, const int* rec_of, const T* zb, T* z, cudaStream_t s,
+                              const Members& mb = Members{});
 // 2D windowed apply: r restricted to every box cell (right-RAS: owned cells only), written by
 // record (rec_of) into rg, two values per box cell
 template <typename T>
@@ -595,7 +602,8 @@ cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, con
 template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
-                              int* err, cudaStream_t s, const Members& mb = Members{});
+                              int* err, cudaStream_t s, const Members& mb = Members{}, const int* rec_of = nullptr,
+                              T* zb = nullptr);
 
 // Bounded wait for bit (word_bit) of a shared-memory word set by another warp of the block:
 // true once set, false after limit_ns of the global timer (the caller then records an error
@@ -663,6 +671,6 @@ template <typename T>
 cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
                                 const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
                                 int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s,
-                                const Members& mb = Members{});
+                                const Members& mb = Members{}, const int* rec_of = nullptr, T* zb = nullptr);
 
 }  // namespace acac

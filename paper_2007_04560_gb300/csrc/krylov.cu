@@ -9,13 +9,67 @@
 // last block to finish adds the partials of each quantity in a fixed order
 // (finish_reduction).  Member m of an ensemble is blockIdx.y; its vectors sit at
 // m * mb.vs, its device scalars at m * mb.rs.
+#include <stdint.h>
+#include <string.h>
+
 #include "acac_internal.cuh"
 
 namespace acac {
 
 static dim3 vgrid(long long n, const Members& mb) { return dim3(red_grid(n), mb.count); }
 
+// Element packs.  A thread takes P = 4 consecutive elements per step, loaded with 16-byte
+// vector loads when every pointer of the launch is 16-byte aligned (the handle's buffers
+// and member strides are), so that more bytes are in flight per thread; otherwise (P = 1)
+// element by element.  Elements past the last whole pack are taken one by one.
+template <typename T, int P>
+struct Pk {
+    T v[P];
+};
+template <typename T, int P>
+__device__ __forceinline__ Pk<T, P> ldp(const T* __restrict__ p, long long i) {
+    Pk<T, P> r;
+    if constexpr (P * sizeof(T) % 16 == 0) {
+        const uint4* q = reinterpret_cast<const uint4*>(p + i * P);
+#pragma unroll
+        for (int k = 0; k < (int)(P * sizeof(T) / 16); ++k) {
+            const uint4 u = q[k];
+            memcpy(&r.v[k * (16 / sizeof(T))], &u, 16);
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) r.v[k] = p[i * P + k];
+    }
+    return r;
+}
+template <typename T, int P>
+__device__ __forceinline__ void stp(T* __restrict__ p, long long i, const Pk<T, P>& r) {
+    if constexpr (P * sizeof(T) % 16 == 0) {
+        uint4* q = reinterpret_cast<uint4*>(p + i * P);
+#pragma unroll
+        for (int k = 0; k < (int)(P * sizeof(T) / 16); ++k) {
+            uint4 u;
+            memcpy(&u, &r.v[k * (16 / sizeof(T))], 16);
+            q[k] = u;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < P; ++k) p[i * P + k] = r.v[k];
+    }
+}
+// Runs f(pack index) over the whole packs and g(element index) over the remaining elements,
+// grid-stride within the member's blocks.
+template <int P, typename F, typename G>
+__device__ __forceinline__ void over_packs(long long n, F f, G g) {
+    const long long np = n / P;
+    const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
+    for (long long i = t0; i < np; i += st) f(i);
+    for (long long i = np * P + t0; i < n; i += st) g(i);
+}
+static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
 // partial sums of (a - b - c) over n  (mass correction of the Newton direction)
+template <int P>
 __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __restrict__ b,
                                 const double* __restrict__ c, long long n, Red red, Members mb) {
     __shared__ double sh[32];
@@ -25,9 +79,11 @@ __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __re
     a += o; b += o; c += o;
     red = member_red(red, mb, m);
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        acc += (a[i] - b[i]) - c[i];
+    over_packs<P>(n, [&](long long i) {
+        const Pk<double, P> x = ldp<double, P>(a, i), y = ldp<double, P>(b, i), z = ldp<double, P>(c, i);
+#pragma unroll
+        for (int k = 0; k < P; ++k) acc += (x.v[k] - y.v[k]) - z.v[k];
+    }, [&](long long i) { acc += (a[i] - b[i]) - c[i]; });
     const double t = block_sum_red(acc, sh);
     if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
     finish_reduction(red, 1, sh);
@@ -35,10 +91,12 @@ __global__ void sum_pair_kernel(const double* __restrict__ a, const double* __re
 
 cudaError_t launch_sum_pair(const double* a, const double* b, const double* c, long long n, Red red,
                             cudaStream_t s, const Members& mb) {
-    sum_pair_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, c, n, red, mb);
+    if (al16(a) && al16(b) && al16(c)) sum_pair_kernel<4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, c, n, red, mb);
+    else sum_pair_kernel<1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, c, n, red, mb);
     return cudaGetLastError();
 }
 
+template <int P>
 __global__ void norm2_double_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
                                     Red red, Members mb) {
     __shared__ double sh[32];
@@ -49,11 +107,20 @@ __global__ void norm2_double_kernel(const double* __restrict__ a, const double* 
     if (b) b += o;
     red = member_red(red, mb, m);
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    over_packs<P>(n, [&](long long i) {
+        const Pk<double, P> x = ldp<double, P>(a, i);
+        if (b) {
+            const Pk<double, P> y = ldp<double, P>(b, i);
+#pragma unroll
+            for (int k = 0; k < P; ++k) acc = fma(x.v[k] - y.v[k], x.v[k] - y.v[k], acc);
+        } else {
+#pragma unroll
+            for (int k = 0; k < P; ++k) acc = fma(x.v[k], x.v[k], acc);
+        }
+    }, [&](long long i) {
         const double x = b ? a[i] - b[i] : a[i];
         acc = fma(x, x, acc);
-    }
+    });
     const double t = block_sum_red(acc, sh);
     if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
     finish_reduction(red, 1, sh);
@@ -61,7 +128,8 @@ __global__ void norm2_double_kernel(const double* __restrict__ a, const double* 
 
 cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s,
                                 const Members& mb) {
-    norm2_double_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, n, red, mb);
+    if (al16(a) && (!b || al16(b))) norm2_double_kernel<4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, n, red, mb);
+    else norm2_double_kernel<1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, b, n, red, mb);
     return cudaGetLastError();
 }
 
@@ -71,18 +139,25 @@ cudaError_t launch_norm2_double(const double* a, const double* b, long long n, R
 // masked lanes cost 8 products per element whatever the count).  Each thread
 // accumulates its share in the Krylov precision; the block and global stages add in
 // double, the block stage with one barrier per chunk.
-template <typename T, int C>
+template <typename T, int C, int P>
 __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld, const T* __restrict__ w,
                                           long long n, double* __restrict__ partial, double (*sw)[RED_THREADS / 32]) {
     T acc[C];
 #pragma unroll
     for (int q = 0; q < C; ++q) acc[q] = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    over_packs<P>(n, [&](long long i) {
+        const Pk<T, P> wi = ldp<T, P>(w, i);
+#pragma unroll
+        for (int q = 0; q < C; ++q) {
+            const Pk<T, P> vq = ldp<T, P>(V + (size_t)q * ld, i);
+#pragma unroll
+            for (int k = 0; k < P; ++k) acc[q] += vq.v[k] * wi.v[k];
+        }
+    }, [&](long long i) {
         const T wi = w[i];
 #pragma unroll
         for (int q = 0; q < C; ++q) acc[q] += V[(size_t)q * ld + i] * wi;
-    }
+    });
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < C; ++q) {
@@ -99,7 +174,7 @@ __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld,
     __syncthreads();
 }
 
-template <typename T>
+template <typename T, int P>
 __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                 const T* __restrict__ w, long long n,
                                                                 Red red, Members mb) {
@@ -113,14 +188,14 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
         const T* Vk = V + (size_t)k0 * ld;
         double* pk = red.partial + (size_t)k0 * gridDim.x;
         switch (nv - k0 < 8 ? nv - k0 : 8) {
-            case 1: dot_chunk<T, 1>(Vk, ld, w, n, pk, sw); break;
-            case 2: dot_chunk<T, 2>(Vk, ld, w, n, pk, sw); break;
-            case 3: dot_chunk<T, 3>(Vk, ld, w, n, pk, sw); break;
-            case 4: dot_chunk<T, 4>(Vk, ld, w, n, pk, sw); break;
-            case 5: dot_chunk<T, 5>(Vk, ld, w, n, pk, sw); break;
-            case 6: dot_chunk<T, 6>(Vk, ld, w, n, pk, sw); break;
-            case 7: dot_chunk<T, 7>(Vk, ld, w, n, pk, sw); break;
-            default: dot_chunk<T, 8>(Vk, ld, w, n, pk, sw); break;
+            case 1: dot_chunk<T, 1, P>(Vk, ld, w, n, pk, sw); break;
+            case 2: dot_chunk<T, 2, P>(Vk, ld, w, n, pk, sw); break;
+            case 3: dot_chunk<T, 3, P>(Vk, ld, w, n, pk, sw); break;
+            case 4: dot_chunk<T, 4, P>(Vk, ld, w, n, pk, sw); break;
+            case 5: dot_chunk<T, 5, P>(Vk, ld, w, n, pk, sw); break;
+            case 6: dot_chunk<T, 6, P>(Vk, ld, w, n, pk, sw); break;
+            case 7: dot_chunk<T, 7, P>(Vk, ld, w, n, pk, sw); break;
+            default: dot_chunk<T, 8, P>(Vk, ld, w, n, pk, sw); break;
         }
     }
     finish_reduction(red, nv, nullptr);
@@ -129,12 +204,15 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
 template <typename T>
 cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
                              cudaStream_t s, const Members& mb) {
-    multi_dot_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
+    if (al16(V) && al16(w) && (ld * sizeof(T)) % 16 == 0)
+        multi_dot_kernel<T, 16 / sizeof(T)><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
+    else
+        multi_dot_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- w -= V h  (+ ||w||^2)
-template <typename T>
+template <typename T, int P>
 __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __restrict__ V, long long ld, int nv,
                                                                  const double* __restrict__ h, T* __restrict__ w,
                                                                  long long n, int want_norm, Red red, Members mb) {
@@ -149,18 +227,30 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __rest
     for (int k = threadIdx.x; k < nv; k += blockDim.x) hs[k] = (T)h[k];
     __syncthreads();
     T acc = 0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    over_packs<P>(n, [&](long long i) {
+        Pk<T, P> s;
+#pragma unroll
+        for (int e = 0; e < P; ++e) s.v[e] = 0;
+        for (int k = 0; k < nv; ++k) {
+            const Pk<T, P> vk = ldp<T, P>(V + (size_t)k * ld, i);
+            const T hk = hs[k];
+#pragma unroll
+            for (int e = 0; e < P; ++e) s.v[e] += hk * vk.v[e];
+        }
+        Pk<T, P> wi = ldp<T, P>(w, i);
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            wi.v[e] -= s.v[e];
+            acc += wi.v[e] * wi.v[e];
+        }
+        stp<T, P>(w, i, wi);
+    }, [&](long long i) {
         T s = 0;
-        int k = 0;
-        for (; k + 4 <= nv; k += 4)
-            s += hs[k] * V[(size_t)k * ld + i] + hs[k + 1] * V[(size_t)(k + 1) * ld + i]
-               + hs[k + 2] * V[(size_t)(k + 2) * ld + i] + hs[k + 3] * V[(size_t)(k + 3) * ld + i];
-        for (; k < nv; ++k) s += hs[k] * V[(size_t)k * ld + i];
+        for (int k = 0; k < nv; ++k) s += hs[k] * V[(size_t)k * ld + i];
         const T wn = w[i] - s;
         w[i] = wn;
         acc += wn * wn;
-    }
+    });
     if (want_norm) {
         const double t = block_sum_red((double)acc, sh);
         if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
@@ -171,12 +261,15 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_update_kernel(const T* __rest
 template <typename T>
 cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h, T* w, long long n,
                               int want_norm, Red red, cudaStream_t s, const Members& mb) {
-    cgs_update_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red, mb);
+    if (al16(V) && al16(w) && (ld * sizeof(T)) % 16 == 0)
+        cgs_update_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red, mb);
+    else
+        cgs_update_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, h, w, n, want_norm, red, mb);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- out = w / alpha (alpha on device)
-template <typename T>
+template <typename T, int P>
 __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restrict__ alpha,
                                   T* __restrict__ out, long long n, Members mb) {
     // alpha holds ||w||^2; one thread per block forms 1/||w|| (an FP64 square root
@@ -189,19 +282,23 @@ __global__ void scale_from_kernel(const T* __restrict__ w, const double* __restr
     if (threadIdx.x == 0) s_inv = (T)(1.0 / sqrt(alpha[(size_t)m * mb.rs]));
     __syncthreads();
     const T inv = s_inv;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        out[i] = w[i] * inv;
+    over_packs<P>(n, [&](long long i) {
+        Pk<T, P> x = ldp<T, P>(w, i);
+#pragma unroll
+        for (int e = 0; e < P; ++e) x.v[e] *= inv;
+        stp<T, P>(out, i, x);
+    }, [&](long long i) { out[i] = w[i] * inv; });
 }
 
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
                               cudaStream_t s, const Members& mb) {
-    scale_from_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(w, alpha_dev, out, n, mb);
+    if (al16(w) && al16(out)) scale_from_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(w, alpha_dev, out, n, mb);
+    else scale_from_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(w, alpha_dev, out, n, mb);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int P>
 __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* __restrict__ out,
                                  long long n, Members mb, const double* __restrict__ scale_dev, int sstride) {
     const int m = blockIdx.y;
@@ -210,20 +307,27 @@ __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* 
     out += (size_t)m * mb.vs;
     // 1/beta correctly rounded, as the host forms it for a single problem
     if (scale_dev) scale = 1.0 / scale_dev[(size_t)m * sstride];
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        out[i] = (T)(x[i] * scale);
+    over_packs<P>(n, [&](long long i) {
+        const Pk<double, P> a = ldp<double, P>(x, i);
+        Pk<T, P> r;
+#pragma unroll
+        for (int e = 0; e < P; ++e) r.v[e] = (T)(a.v[e] * scale);
+        stp<T, P>(out, i, r);
+    }, [&](long long i) { out[i] = (T)(x[i] * scale); });
 }
 
 template <typename T>
 cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s,
                              const Members& mb, const double* scale_dev, int sstride) {
-    to_krylov_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, scale, out, n, mb, scale_dev, sstride);
+    if (al16(x) && al16(out))
+        to_krylov_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, scale, out, n, mb, scale_dev, sstride);
+    else
+        to_krylov_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, scale, out, n, mb, scale_dev, sstride);
     return cudaGetLastError();
 }
 
 // out = sum_k y_k V_k
-template <typename T>
+template <typename T, int P>
 __global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, const double* __restrict__ y,
                                T* __restrict__ out, long long n, Members mb, const int* __restrict__ nv_dev) {
     __shared__ T ys[MAX_RESTART + 1];
@@ -235,42 +339,59 @@ __global__ void lincomb_kernel(const T* __restrict__ V, long long ld, int nv, co
     y += (size_t)m * mb.rs;
     for (int k = threadIdx.x; k < nv; k += blockDim.x) ys[k] = (T)y[k];
     __syncthreads();
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    over_packs<P>(n, [&](long long i) {
+        Pk<T, P> s;
+#pragma unroll
+        for (int e = 0; e < P; ++e) s.v[e] = 0;
+        for (int k = 0; k < nv; ++k) {
+            const Pk<T, P> vk = ldp<T, P>(V + (size_t)k * ld, i);
+#pragma unroll
+            for (int e = 0; e < P; ++e) s.v[e] += ys[k] * vk.v[e];
+        }
+        stp<T, P>(out, i, s);
+    }, [&](long long i) {
         T s = 0;
         for (int k = 0; k < nv; ++k) s += ys[k] * V[(size_t)k * ld + i];
         out[i] = s;
-    }
+    });
 }
 
 template <typename T>
 cudaError_t launch_lincomb(const T* V, long long ld, int nv, const double* y, T* out, long long n,
                            cudaStream_t s, const Members& mb, const int* nv_dev) {
-    lincomb_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n, mb, nv_dev);
+    if (al16(V) && al16(out) && (ld * sizeof(T)) % 16 == 0)
+        lincomb_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n, mb, nv_dev);
+    else
+        lincomb_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, y, out, n, mb, nv_dev);
     return cudaGetLastError();
 }
 
-template <typename T>
+template <typename T, int P>
 __global__ void axpy_to_double_kernel(double a, const T* __restrict__ x, double* __restrict__ y,
                                       long long n, Members mb) {
     const int m = blockIdx.y;
     if (member_off(mb, m)) return;
     x += (size_t)m * mb.vs;
     y += (size_t)m * mb.vs;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        y[i] = fma(a, (double)x[i], y[i]);
+    over_packs<P>(n, [&](long long i) {
+        const Pk<T, P> xi = ldp<T, P>(x, i);
+        Pk<double, P> yi = ldp<double, P>(y, i);
+#pragma unroll
+        for (int e = 0; e < P; ++e) yi.v[e] = fma(a, (double)xi.v[e], yi.v[e]);
+        stp<double, P>(y, i, yi);
+    }, [&](long long i) { y[i] = fma(a, (double)x[i], y[i]); });
 }
 
 template <typename T>
 cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s,
                                   const Members& mb) {
-    axpy_to_double_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, x, y, n, mb);
+    if (al16(x) && al16(y)) axpy_to_double_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, x, y, n, mb);
+    else axpy_to_double_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(a, x, y, n, mb);
     return cudaGetLastError();
 }
 
 // r = b - Ax (double), partial sums of ||r||^2
-template <typename T>
+template <typename T, int P>
 __global__ void residual_restart_kernel(const double* __restrict__ b, const T* __restrict__ Ax,
                                         double* __restrict__ r, long long n, Red red, Members mb) {
     __shared__ double sh[32];
@@ -281,12 +402,21 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
     r += (size_t)m * mb.vs;
     red = member_red(red, mb, m);
     double acc = 0.0;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
+    over_packs<P>(n, [&](long long i) {
+        const Pk<double, P> bi = ldp<double, P>(b, i);
+        const Pk<T, P> ai = ldp<T, P>(Ax, i);
+        Pk<double, P> ri;
+#pragma unroll
+        for (int e = 0; e < P; ++e) {
+            ri.v[e] = bi.v[e] - (double)ai.v[e];
+            acc = fma(ri.v[e], ri.v[e], acc);
+        }
+        stp<double, P>(r, i, ri);
+    }, [&](long long i) {
         const double ri = b[i] - (double)Ax[i];
         r[i] = ri;
         acc = fma(ri, ri, acc);
-    }
+    });
     const double t = block_sum_red(acc, sh);
     if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
     finish_reduction(red, 1, sh);
@@ -295,23 +425,26 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
 template <typename T>
 cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
                                     cudaStream_t s, const Members& mb) {
-    residual_restart_kernel<T><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
+    if (al16(b) && al16(Ax) && al16(r))
+        residual_restart_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
+    else
+        residual_restart_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
     return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- member copies
+template <int P>
 __global__ void copy_members_kernel(const double* __restrict__ x, double* __restrict__ y, long long n, Members mb) {
     const int m = blockIdx.y;
     if (member_off(mb, m)) return;
     x += (size_t)m * mb.vs;
     y += (size_t)m * mb.vs;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        y[i] = x[i];
+    over_packs<P>(n, [&](long long i) { stp<double, P>(y, i, ldp<double, P>(x, i)); }, [&](long long i) { y[i] = x[i]; });
 }
 
 cudaError_t launch_copy_members(const double* x, double* y, long long n, cudaStream_t s, const Members& mb) {
-    copy_members_kernel<<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, y, n, mb);
+    if (al16(x) && al16(y)) copy_members_kernel<4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, y, n, mb);
+    else copy_members_kernel<1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(x, y, n, mb);
     return cudaGetLastError();
 }
 

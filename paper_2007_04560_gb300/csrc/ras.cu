@@ -332,7 +332,7 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
                                                         const int* __restrict__ lev_off,
                                                         const T* __restrict__ coef, const T* __restrict__ r,
                                                         T* __restrict__ z, int ras_type, T* gscratch,
-                                                        RasLaunch L, int* err, Members mb) {
+                                                        RasLaunch L, int* err, Members mb, T* __restrict__ zb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;   // consumer / producer gave up on a wait
     __shared__ int s_issued, s_consumed;
@@ -342,6 +342,7 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
     r += (size_t)mem * mb.vs;
     z += (size_t)mem * mb.vs;
     if (gscratch) gscratch += (size_t)mem * mb.ss;
+    if (zb) zb += (size_t)mem * mb.zs;
     err += mem;
     const SubInfo sd = subs[blockIdx.x];
     const int N = g.N;
@@ -530,17 +531,24 @@ __global__ void __launch_bounds__(1024) ras_apply_kernel(Geom g, const SubInfo* 
         }
         return;
     }
-    // extension
+    // extension: left-RAS writes the owned cells of z; the additive extensions (AS,
+    // right-RAS) write every box cell's values by record, summed per grid cell afterwards in
+    // a fixed order (ext_gather_kernel: no atomics, the same sums run to run)
+    const long long rbase = sd.coef_base / NCOEF;
     for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
         const int i = idx % sd.W, j = idx / sd.W;
         const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1;
-        const int gc = box_cell(g, sd, i, j);
         const V2<T> val = yv[(j + 2) * PW + i + 2];
         if (ras_type == ACAC_RAS_LEFT) {
-            if (own) { z[gc] = val.x; z[N + gc] = val.y; }
+            if (own) {
+                const int gc = box_cell(g, sd, i, j);
+                z[gc] = val.x;
+                z[N + gc] = val.y;
+            }
         } else {
-            atomicAdd(&z[gc], val.x);
-            atomicAdd(&z[N + gc], val.y);
+            const int l = i + 2 * j;
+            const size_t rec = (size_t)(rbase + lo[l] + (j - level_jmin(l, sd.W)));
+            *reinterpret_cast<V2<T>*>(zb + 2 * rec) = val;
         }
     }
 }
@@ -588,13 +596,14 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                                                             const int* __restrict__ lev_off,
                                                             const T* __restrict__ coef, const T* __restrict__ r,
                                                             T* __restrict__ z, int ras_type, T* __restrict__ gscratch,
-                                                            RasLaunch L, int* err, Members mb) {
+                                                            RasLaunch L, int* err, Members mb, T* __restrict__ zb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;
     __shared__ int s_issued, s_consumed;
     __shared__ volatile int s_done;             // consumer steps completed (forward result in yg)
     const int mem = blockIdx.y;
     if (member_off(mb, mem)) return;
+    if (zb) zb += (size_t)mem * mb.zs;
     coef += (size_t)mem * mb.cfs;
     r += (size_t)mem * (PRE ? mb.rgs : mb.vs);   // PRE: r is the gathered right-hand side
     z += (size_t)mem * mb.vs;
@@ -820,12 +829,11 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                     const V2<T> dinv = *reinterpret_cast<const V2<T>*>(rec);
                     const T zc = fma(dinv.x, sx, dinv.y * sy);
                     wins[2 * (own + j) + rr] = zc;
-                    const int gc = box_cell(g, sd, i, j);
                     if (ras_type == ACAC_RAS_LEFT) {
                         if (i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1)
-                            z[(size_t)rr * N + gc] = zc;
+                            z[(size_t)rr * N + box_cell(g, sd, i, j)] = zc;
                     } else {
-                        atomicAdd(&z[(size_t)rr * N + gc], zc);
+                        zb[2 * (size_t)(rbase + lo[l] + m) + rr] = zc;   // summed by ext_gather_kernel
                     }
                 }
                 if (!finish_level(landed, false)) break;
@@ -874,19 +882,50 @@ cudaError_t launch_ras_gather(const Geom& g, const T* r, const int* rec_of, cons
     return cudaGetLastError();
 }
 
+// The additive extensions (AS, right-RAS): z at grid cell c = the sum of the values of its
+// box cells (rec_of[rpc c + q], q in increasing order, -1 ends the list), written by record
+// into zb by the apply kernels.  A fixed order: the same sums run to run.
+template <typename T, int RPC>
+__global__ void __launch_bounds__(256) ext_gather_kernel(int N, const int* __restrict__ rec_of,
+                                                         const T* __restrict__ zb, T* __restrict__ z, Members mb) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int mem = blockIdx.y;
+    if (c >= N || member_off(mb, mem)) return;
+    zb += (size_t)mem * mb.zs;
+    z += (size_t)mem * mb.vs;
+    T sx = (T)0, sy = (T)0;
+#pragma unroll
+    for (int q = 0; q < RPC; ++q) {
+        const int rec = rec_of[(size_t)RPC * c + q];
+        if (rec < 0) break;
+        const V2<T> v = *reinterpret_cast<const V2<T>*>(zb + 2 * (size_t)rec);
+        sx += v.x;
+        sy += v.y;
+    }
+    z[c] = sx;
+    z[N + c] = sy;
+}
+
+template <typename T>
+cudaError_t launch_ext_gather(const Geom& g, const int* rec_of, const T* zb, T* z, cudaStream_t s,
+                              const Members& mb) {
+    const dim3 grid((g.N + 255) / 256, mb.count);
+    if (g.dim == 3) ext_gather_kernel<T, 8><<<grid, 256, 0, s>>>(g.N, rec_of, zb, z, mb);
+    else ext_gather_kernel<T, 4><<<grid, 256, 0, s>>>(g.N, rec_of, zb, z, mb);
+    return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off,
                              const T* coef, const T* r, T* z, int ras_type, int threads,
                              const RasLaunch& L, T* gscratch, const T* rg, int* err, cudaStream_t s,
-                             const Members& mb) {
+                             const Members& mb, const int* rec_of, T* zb) {
     static std::atomic<size_t> attr_bytes{0};
     const dim3 grid(nsub, mb.count);
+    const bool additive = ras_type != ACAC_RAS_LEFT;
+    if (additive && (!rec_of || !zb)) return cudaErrorInvalidValue;
     if (!L.window) {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply_kernel<T>, L.smem_bytes, &attr_bytes);
-        if (e != cudaSuccess) return e;
-    }
-    if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
         if (e != cudaSuccess) return e;
     }
     if (L.window) {
@@ -898,15 +937,17 @@ cudaError_t launch_ras_apply(const Geom& g, int nsub, const SubInfo* subs, const
         // double: the producer gathers r itself (the consumers' FP64 work leaves it time)
         if (rg)
             ras_apply_win_kernel<T, true><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, rg, z, ras_type,
-                                                                              gscratch, L, err, mb);
+                                                                              gscratch, L, err, mb, zb);
         else
             ras_apply_win_kernel<T, false><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type,
-                                                                               gscratch, L, err, mb);
-        return cudaGetLastError();
+                                                                               gscratch, L, err, mb, zb);
+    } else {
+        ras_apply_kernel<T><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
+                                                                err, mb, zb);
     }
-    ras_apply_kernel<T><<<grid, threads, L.smem_bytes, s>>>(g, subs, lev_off, coef, r, z, ras_type, gscratch, L,
-                                                            err, mb);
-    return cudaGetLastError();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !additive) return e;
+    return launch_ext_gather<T>(g, rec_of, zb, z, s, mb);
 }
 
 
@@ -1030,12 +1071,13 @@ __global__ void __launch_bounds__(1024) ras_apply3_kernel(Geom g, const SubInfo*
                                                          const int* __restrict__ lev_off, const int* __restrict__ cells,
                                                          const T* __restrict__ coef, const T* __restrict__ r,
                                                          T* __restrict__ z, int ras_type, T* gscratch, RasLaunch L,
-                                                         int* err, Members mb) {
+                                                         int* err, Members mb, T* __restrict__ zb) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ int s_cabort, s_pabort;
     __shared__ int s_issued, s_consumed;
     const int mem = blockIdx.y;
     if (member_off(mb, mem)) return;
+    if (zb) zb += (size_t)mem * mb.zs;
     coef += (size_t)mem * mb.cfs;
     r += (size_t)mem * mb.vs;
     z += (size_t)mem * mb.vs;
@@ -1184,17 +1226,25 @@ __global__ void __launch_bounds__(1024) ras_apply3_kernel(Geom g, const SubInfo*
         }
         return;
     }
-    for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
-        const int i = idx % sd.W, j = (idx / sd.W) % sd.H, k = idx / (sd.W * sd.H);
-        const bool own = i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1 &&
-                         k >= sd.own_z0 && k < sd.own_z1;
-        const int gc = box_cell3(g, sd, i, j, k);
-        const V2<T> val = yv[((k + 2) * PH + j + 2) * PW + i + 2];
-        if (ras_type == ACAC_RAS_LEFT) {
-            if (own) { z[gc] = val.x; z[N + gc] = val.y; }
-        } else {
-            atomicAdd(&z[gc], val.x);
-            atomicAdd(&z[N + gc], val.y);
+    if (ras_type == ACAC_RAS_LEFT) {
+        for (int idx = threadIdx.x; idx < ncell; idx += blockDim.x) {
+            const int i = idx % sd.W, j = (idx / sd.W) % sd.H, k = idx / (sd.W * sd.H);
+            if (!(i >= sd.own_x0 && i < sd.own_x1 && j >= sd.own_y0 && j < sd.own_y1 && k >= sd.own_z0 &&
+                  k < sd.own_z1))
+                continue;
+            const int gc = box_cell3(g, sd, i, j, k);
+            const V2<T> val = yv[((k + 2) * PH + j + 2) * PW + i + 2];
+            z[gc] = val.x;
+            z[N + gc] = val.y;
+        }
+    } else {
+        // additive extensions: every box cell's values by record (the level-ordered cell list),
+        // summed per grid cell in a fixed order by ext_gather_kernel
+        const long long rbase = sd.coef_base / NCOEF3;
+        for (int t = threadIdx.x; t < ncell; t += blockDim.x) {
+            const int pk = cl[t];
+            const int i = pk & 1023, j = (pk >> 10) & 1023, k = pk >> 20;
+            *reinterpret_cast<V2<T>*>(zb + 2 * (size_t)(rbase + t)) = yv[((k + 2) * PH + j + 2) * PW + i + 2];
         }
     }
 }
@@ -1211,19 +1261,19 @@ cudaError_t launch_ras_factor3(const Geom& g, int nsub, const SubInfo* subs, con
 template <typename T>
 cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, const int* lev_off, const int* cells,
                               const T* coef, const T* r, T* z, int ras_type, const RasLaunch& L, T* gscratch,
-                              int* err, cudaStream_t s, const Members& mb) {
+                              int* err, cudaStream_t s, const Members& mb, const int* rec_of, T* zb) {
     static std::atomic<size_t> attr_bytes{0};
+    const bool additive = ras_type != ACAC_RAS_LEFT;
+    if (additive && (!rec_of || !zb)) return cudaErrorInvalidValue;
     {
         cudaError_t e = ensure_smem_limit((const void*)ras_apply3_kernel<T>, L.smem_bytes, &attr_bytes);
         if (e != cudaSuccess) return e;
     }
-    if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
-        if (e != cudaSuccess) return e;
-    }
     ras_apply3_kernel<T><<<dim3(nsub, mb.count), L.threads, L.smem_bytes, s>>>(g, subs, lev_off, cells, coef, r, z,
-                                                                              ras_type, gscratch, L, err, mb);
-    return cudaGetLastError();
+                                                                              ras_type, gscratch, L, err, mb, zb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !additive) return e;
+    return launch_ext_gather<T>(g, rec_of, zb, z, s, mb);
 }
 
 #define INST(T)                                                                                    \
@@ -1234,13 +1284,15 @@ cudaError_t launch_ras_apply3(const Geom& g, int nsub, const SubInfo* subs, cons
                                               int, T*, cudaStream_t, const Members&);                   \
     template cudaError_t launch_ras_apply<T>(const Geom&, int, const SubInfo*, const int*, const T*, \
                                              const T*, T*, int, int, const RasLaunch&, T*, const T*, int*, \
-                                             cudaStream_t, const Members&);                           \
+                                             cudaStream_t, const Members&, const int*, T*);           \
+    template cudaError_t launch_ext_gather<T>(const Geom&, const int*, const T*, T*, cudaStream_t,     \
+                                              const Members&);                                        \
     template cudaError_t launch_ras_factor3<T>(const Geom&, int, const SubInfo*, const int*, const int*,    \
                                                const int*, const T*, int, T*, int, int*, cudaStream_t,      \
                                                const Members&);                                             \
     template cudaError_t launch_ras_apply3<T>(const Geom&, int, const SubInfo*, const int*, const int*,     \
                                               const T*, const T*, T*, int, const RasLaunch&, T*, int*,     \
-                                              cudaStream_t, const Members&);
+                                              cudaStream_t, const Members&, const int*, T*);
 INST(double)
 INST(float)
 #undef INST

@@ -124,6 +124,8 @@ struct acac_handle {
     void* sval = nullptr;        // 2x2 blocks of every box matrix (factored in place)
     void* sdinv = nullptr;       // inverse pivot blocks, 4 values per box cell
     void* sy = nullptr;          // box vectors of the apply when they do not fit shared memory
+    int* srec_of_dev = nullptr;  // fill solvers: the box cells (natural order) of every grid cell
+    void* zb = nullptr;          // additive extensions (AS, right-RAS): box-cell results by record
     long long sblocks = 0, scells = 0;
     int s_threads = 32, s_fthreads = 512, s_use_map = 1;
     size_t s_fsmem = 0, s_asmem = 0;
@@ -442,14 +444,14 @@ void precond(acac_handle* h, const Members& mb, const T* r, T* z) {
             16.0 * h->sblocks,
             launch_sparse_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->sbox_dev, h->sshape_dev,
                                    (const T*)h->sval, (const T*)h->sdinv, r, z, h->p.ras_type, (T*)h->sy,
-                                   h->s_threads, h->s_asmem, h->stream, mb));
+                                   h->s_threads, h->s_asmem, h->stream, mb, h->srec_of_dev, (T*)h->zb));
         return;
     }
     if (h->g.dim == 3) {
         KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (104.0 * h->nbox + 4.0 * h->N), 200.0 * h->nbox,
             launch_ras_apply3<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, h->cells3_dev,
                                  (const T*)h->coef, r, z, h->p.ras_type, h->ras_launch, (T*)h->gscratch,
-                                 err, h->stream, mb));
+                                 err, h->stream, mb, h->rec_of_dev, (T*)h->zb));
         return;
     }
     if (h->ras_launch.window && sizeof(T) == 4)
@@ -458,7 +460,8 @@ void precond(acac_handle* h, const Members& mb, const T* r, T* z) {
     KLA(ACAC_K_RAS_APPLY, (double)sizeof(T) * (54.0 * h->nbox + 2.0 * h->N), 104.0 * h->nbox,
         launch_ras_apply<T>(h->g, (int)h->subs.size(), h->subs_dev, h->lev_dev, (const T*)h->coef, r, z,
                             h->p.ras_type, h->ras_launch.threads, h->ras_launch, (T*)h->gscratch,
-                            sizeof(T) == 4 ? (const T*)h->rg : nullptr, err, h->stream, mb));
+                            sizeof(T) == 4 ? (const T*)h->rg : nullptr, err, h->stream, mb, h->rec_of_dev,
+                            (T*)h->zb));
 }
 
 // Subdomain factorizations of the members in mb.  With defer, the pivot / timeout flags
@@ -1411,6 +1414,36 @@ void build_sparse(acac_handle* h) {
         h->mb.ss = r64(cells * 2);
         dmalloc(&h->sy, (size_t)h->mb.ss * h->B * h->ksz);
     }
+    if (p.ras_type != ACAC_RAS_LEFT) {
+        // the box cells of every grid cell (natural order within each box), for the additive
+        // extensions' fixed-order sums
+        const int rpc = p.dim == 3 ? 8 : 4;
+        const size_t ncell = h->N;
+        std::vector<int> map(rpc * ncell, -1);
+        for (size_t bi = 0; bi < h->subs.size(); ++bi) {
+            const SubInfo& sd = h->subs[bi];
+            const long long base = boxes[bi].cell_base;
+            const int D = p.dim == 3 ? sd.D : 1;
+            for (int k = 0; k < D; ++k)
+                for (int j = 0; j < sd.H; ++j)
+                    for (int i = 0; i < sd.W; ++i) {
+                        auto wrap = [&](int x, int n) {
+                            return p.bc == ACAC_BC_PERIODIC ? (x < 0 ? x + n : (x >= n ? x - n : x))
+                                                            : (x < 0 ? 0 : (x >= n ? n - 1 : x));
+                        };
+                        const int gx = wrap(sd.ox + i, p.n[0]), gy = wrap(sd.oy + j, p.n[1]);
+                        const int gz = p.dim == 3 ? wrap(sd.oz + k, p.n[2]) : 0;
+                        const size_t gc = ((size_t)gz * p.n[1] + gy) * p.n[0] + gx;
+                        const long long rec = base + ((long long)k * sd.H + j) * sd.W + i;
+                        int q = 0;
+                        while (q < rpc && map[rpc * gc + q] >= 0) ++q;
+                        if (q == rpc || rec > INT32_MAX) throw Err{ACAC_E_ARG};
+                        map[rpc * gc + q] = (int)rec;
+                    }
+        }
+        dmalloc(&h->srec_of_dev, map.size() * sizeof(int));
+        CU(cudaMemcpy(h->srec_of_dev, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice));
+    }
     for (SparseShape& S : h->sshape) {   // the device holds what the kernels need
         S.col.clear(); S.col.shrink_to_fit();
         S.slot_pos.clear(); S.slot_pos.shrink_to_fit();
@@ -1423,7 +1456,7 @@ void free_all(acac_handle* h) {
                     h->kt, h->jtmp, h->cache, h->J, h->coef, h->gscratch, h->partial, h->red, h->flags,
                     h->counter, h->subs_dev, h->lev_dev, h->cells3_dev, h->pos3_dev, h->rec_of_dev, h->own_of_dev,
                     h->rg, h->Jp,
-                    h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy};
+                    h->sshape_dev, h->sbox_dev, h->sint_dev, h->sval, h->sdinv, h->sy, h->srec_of_dev, h->zb};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (h->host) cudaFreeHost(h->host);
@@ -1685,6 +1718,13 @@ int acac_create(const acac_params* p, void* cuda_stream, acac_handle** out) {
         h->rec_of.clear();
         h->rec_of.shrink_to_fit();
         if (p->subdomain_solver != ACAC_SUB_ILU0) build_sparse(h);
+        if (p->ras_type != ACAC_RAS_LEFT) {
+            // additive extensions: every box cell's two values, summed per grid cell afterwards
+            const long long bcells = p->subdomain_solver != ACAC_SUB_ILU0 ? h->scells
+                                   : h->coef_count / (p->dim == 3 ? NCOEF3 : NCOEF);
+            mb.zs = r64(2 * bcells);
+            dmalloc(&h->zb, (size_t)mb.zs * Bz * ks);
+        }
         CU(set_taylor_constants(p->taylor_S));
         std::vector<int> ones(B, 1);
         set_mask(h, MK_NEWTON, ones);
@@ -2111,9 +2151,8 @@ int acac_autotune(const acac_params* p, const double* u, const double* v, int tr
     if (!p || !u || !v || !best || trial_steps < 1) return ACAC_E_ARG;
     int st = validate_params(p);
     if (st != ACAC_OK) return st;
-    if (p->batch != 1) return ACAC_E_ARG;
     const int dim = p->dim;
-    const size_t N = (size_t)p->n[0] * p->n[1] * (dim == 3 ? p->n[2] : 1);
+    const size_t N = (size_t)p->n[0] * p->n[1] * (dim == 3 ? p->n[2] : 1) * p->batch;   // all members
     // candidates: the given partition, and near-cubic boxes of owned width W in every
     // direction for W in a ladder, each with overlap 1 and 2
     std::vector<acac_params> cand;

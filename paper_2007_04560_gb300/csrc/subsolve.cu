@@ -345,10 +345,11 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
                                                            const SparseShapeDev* __restrict__ shapes,
                                                            const T* __restrict__ val, const T* __restrict__ dinv,
                                                            const T* __restrict__ r, T* __restrict__ z, int ras_type,
-                                                           T* yscratch, int in_smem, Members mb) {
+                                                           T* yscratch, int in_smem, Members mb, T* __restrict__ zb) {
     extern __shared__ __align__(16) unsigned char sraw[];
     const int mem = blockIdx.y;
     if (member_off(mb, mem)) return;
+    if (zb) zb += (size_t)mem * mb.zs;
     val += (size_t)mem * mb.cfs;
     dinv += (size_t)mem * mb.rgs;
     r += (size_t)mem * mb.vs;
@@ -452,8 +453,10 @@ __global__ void __launch_bounds__(256) sparse_apply_kernel(Geom g, const SubInfo
                 z[N + gc] = y[2 * c + 1];
             }
         } else {
-            atomicAdd(&z[gc], y[2 * c]);
-            atomicAdd(&z[N + gc], y[2 * c + 1]);
+            // additive extensions: by box cell (natural order within the box), summed per grid
+            // cell in a fixed order afterwards (launch_ext_gather)
+            zb[2 * (size_t)(bx.cell_base + c)] = y[2 * c];
+            zb[2 * (size_t)(bx.cell_base + c) + 1] = y[2 * c + 1];
         }
     }
 }
@@ -485,20 +488,20 @@ template <typename T>
 cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, const SparseBox* boxes,
                                 const SparseShapeDev* shapes, const T* val, const T* dinv, const T* r, T* z,
                                 int ras_type, T* yscratch, int threads, size_t smem, cudaStream_t s,
-                                const Members& mb) {
+                                const Members& mb, const int* rec_of, T* zb) {
+    const bool additive = ras_type != ACAC_RAS_LEFT;
+    if (additive && (!rec_of || !zb)) return cudaErrorInvalidValue;
     if (threads < 32 || threads > 256 || threads % 32) return cudaErrorInvalidValue;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(sparse_apply_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem);
         if (e != cudaSuccess) return e;
     }
-    if (ras_type != ACAC_RAS_LEFT) {
-        cudaError_t e = cudaMemsetAsync(z, 0, sizeof(T) * ((size_t)(mb.count - 1) * mb.vs + 2 * (size_t)g.N), s);
-        if (e != cudaSuccess) return e;
-    }
     sparse_apply_kernel<T><<<dim3(nbox, mb.count), threads, smem, s>>>(g, subs, boxes, shapes, val, dinv, r, z,
-                                                                       ras_type, yscratch, smem > 0 ? 1 : 0, mb);
-    return cudaGetLastError();
+                                                                       ras_type, yscratch, smem > 0 ? 1 : 0, mb, zb);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !additive) return e;
+    return launch_ext_gather<T>(g, rec_of, zb, z, s, mb);
 }
 
 #define INST(T)                                                                                                   \
@@ -508,7 +511,7 @@ cudaError_t launch_sparse_apply(const Geom& g, int nbox, const SubInfo* subs, co
                                                  size_t, int, cudaStream_t, const Members&);                      \
     template cudaError_t launch_sparse_apply<T>(const Geom&, int, const SubInfo*, const SparseBox*,                \
                                                 const SparseShapeDev*, const T*, const T*, const T*, T*, int, T*,  \
-                                                int, size_t, cudaStream_t, const Members&);
+                                                int, size_t, cudaStream_t, const Members&, const int*, T*);
 INST(double)
 INST(float)
 #undef INST

@@ -76,23 +76,38 @@ def _rel_l2(u, v, ur, vr):
 
 
 def convergence(kind="space", ns=(16, 32, 64), nref=128, dt=5e-5, dts=(8e-4, 4e-4, 2e-4, 1e-4),
-                dtref=2.5e-5, T=3.2e-3, n=64, newton_rtol=1e-10, box=8):
+                dtref=2.5e-5, T=3.2e-3, n=64, newton_rtol=1e-10, box=8, ref_solver=0, ref_overlap=1,
+                ref_box=None, ref_newton_atol=None):
     """Relative l2 errors against the reference run and the observed orders (Fig. 1).
 
     space: grids ns at fixed dt, reference grid nref, all to time T;
-    time:  grid n, time steps dts, reference time step dtref, all to time T."""
+    time:  grid n, time steps dts, reference time step dtref, all to time T.
+    The space reference may take its own subdomain solver, overlap and box size (ILU(0)
+    boxes do not converge on the paper's 1024^2 reference) and an absolute Newton
+    tolerance (the rounding floor of F grows with 1/dt and the cell count)."""
     from workloads import BC_PERIODIC, sinusoidal_fields
     out = {"kind": kind, "T": T, "coefficients": "Sec. 4.1", "newton_rtol": newton_rtol, "rows": []}
     t0 = time.perf_counter()
     if kind == "space":
         steps = int(round(T / dt))
-        pr = _params(n=(nref, nref, 1), bc=BC_PERIODIC, dt0=dt, ras_parts=(_parts(nref, box), _parts(nref, box), 1),
-                     newton_rtol=newton_rtol)
+        rb = ref_box or box
+        pr = _params(n=(nref, nref, 1), bc=BC_PERIODIC, dt0=dt, ras_parts=(_parts(nref, rb), _parts(nref, rb), 1),
+                     newton_rtol=newton_rtol, subdomain_solver=ref_solver, ras_overlap=ref_overlap)
+        if ref_newton_atol is not None:
+            pr = pr.replace(newton_atol=ref_newton_atol)
+        t1 = time.perf_counter()
         ur, vr, _ = _fixed_run(pr, *sinusoidal_fields(pr), steps)
+        out["reference"] = {"n": nref, "subdomain_solver": ref_solver, "overlap": ref_overlap, "box": rb,
+                            "newton_atol": pr.newton_atol, "seconds": time.perf_counter() - t1}
+        base = _params(n=(nref, nref, 1), bc=BC_PERIODIC, dt0=dt, newton_rtol=newton_rtol)
         prev = None
         for m in ns:
-            p = pr.replace(n=(m, m, 1), ras_parts=(_parts(m, box), _parts(m, box), 1))
-            u, v, info = _fixed_run(p, *sinusoidal_fields(p), steps)
+            p = base.replace(n=(m, m, 1), ras_parts=(_parts(m, box), _parts(m, box), 1))
+            try:
+                u, v, info = _fixed_run(p, *sinusoidal_fields(p), steps)
+            except Exception as exc:   # a coarse grid that fails keeps the (costly) reference's rows
+                out["rows"].append({"n": m, "error": str(exc)})
+                continue
             r = nref // m
             e = _rel_l2(u, v, _block_average(ur, r), _block_average(vr, r))
             row = {"n": m, "l2": e, "newton_last_step": info.newton_its}
@@ -264,6 +279,11 @@ def main(argv=None):
     c.add_argument("--dtref", type=float, default=2.5e-5)
     c.add_argument("--T", type=float, default=3.2e-3)
     c.add_argument("--box", type=int, default=8, help="owned cells per subdomain box and direction")
+    c.add_argument("--ref-solver", choices=["ilu0", "ilu1", "ilu2", "lu"], default="ilu0",
+                   help="subdomain solver of the space reference run")
+    c.add_argument("--ref-overlap", type=int, default=1)
+    c.add_argument("--ref-box", type=int, default=None)
+    c.add_argument("--ref-newton-atol", type=float, default=None)
     lr = sub.add_parser("long")
     lr.add_argument("--bc", choices=["neumann", "periodic"], default="neumann")
     lr.add_argument("--n", type=int, default=128)
@@ -286,8 +306,11 @@ def main(argv=None):
     args = ap.parse_args(argv)
     build.build()
     if args.cmd == "convergence":
+        solvers = {"ilu0": 0, "ilu1": 1, "ilu2": 2, "lu": 3}
         res = convergence(args.kind, tuple(int(x) for x in args.ns.split(",")), args.nref, args.dt,
-                          tuple(float(x) for x in args.dts.split(",")), args.dtref, args.T, args.n, box=args.box)
+                          tuple(float(x) for x in args.dts.split(",")), args.dtref, args.T, args.n, box=args.box,
+                          ref_solver=solvers[args.ref_solver], ref_overlap=args.ref_overlap, ref_box=args.ref_box,
+                          ref_newton_atol=args.ref_newton_atol)
     elif args.cmd == "long":
         sink = (lambda r: print(json.dumps(r), flush=True)) if args.jsonl else None
         res = long_run(args.bc, args.n, args.t_end, args.seed, every=args.every, sink=sink, L=args.L,

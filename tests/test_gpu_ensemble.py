@@ -289,3 +289,23 @@ def test_ensemble_member_retry_matches_single_handle():
             assert (a.status, a.dt, a.divergences, a.gmres_its, a.newton_its) == \
                    (b.status, b.dt, b.divergences, b.gmres_its, b.newton_its), (m, k)
     assert sum(e.divergences for e in ens[0]) > 0   # the retry path was taken
+
+
+def test_autotune_ensemble():
+    """acac_autotune on an ensemble: times the whole ensemble per candidate, returns a
+    partition acac_create accepts, and leaves the members' fields unchanged."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    from paper_2007_04560_gb300.acac import acac_autotune
+    p1 = Params(n=(64, 48, 1), ras_parts=(2, 2, 1), ras_overlap=1, precision=PREC_MIXED, dt0=1e-3, batch=3)
+    fields = _members(p1, (91, 92, 93))
+    u, v = _stack(fields)
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    best, ms, nc = acac_autotune(p1, ug, vg, trial_steps=1)
+    torch.cuda.synchronize()
+    assert nc >= 2 and ms > 0 and best.batch == 3
+    assert np.array_equal(host(ug), u.ravel()) and np.array_equal(host(vg), v.ravel())
+    with P.Solver(best) as s:
+        infos = s.step(ug, vg)
+    assert [i.status for i in infos] == [0, 0, 0]

@@ -358,3 +358,38 @@ def test_window_apply_steps_match_whole_box(P, precision):
         out.append((host(ug), host(vg), [(i.dt, i.gmres_its) for i in infos]))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("ras_type", [1, 2])
+@pytest.mark.parametrize("case", ["2d-box", "2d-window", "3d", "2d-ilu1", "3d-float"])
+def test_additive_extension_is_deterministic(P, ras_type, case):
+    """AS and right-RAS add the values of the overlapping boxes per grid cell in a fixed order
+    (the apply writes them by box cell, one pass sums them): repeated applies of one
+    factorization give bit-identical results, in every apply kernel."""
+    import torch
+    from workloads import SUB_ILU1
+    kw = dict(ras_type=ras_type)
+    if case.startswith("3d"):
+        p = Params(dim=3, n=(18, 16, 14), bc=BC_NEUMANN, ras_parts=(2, 2, 2), ras_overlap=2,
+                   precision=PREC_MIXED if case == "3d-float" else 0, **kw)
+    else:
+        p = Params(n=(64, 48, 1), bc=BC_PERIODIC, ras_parts=(4, 3, 1), ras_overlap=2,
+                   ras_window=1 if case == "2d-window" else 2, subdomain_solver=SUB_ILU1 if case == "2d-ilu1" else 0,
+                   **kw)
+    X1, X0 = perturbed_pair(p, 23, u_mean=0.45, amp=0.05, step_amp=2e-3)
+    dt = 2e-3
+    ft = torch.float32 if p.precision == PREC_MIXED else torch.float64
+    nslot = 25 if p.dim == 3 else 13
+    with P.Solver(p) as s:
+        J = torch.empty(nslot * 4 * p.ncells, dtype=ft, device="cuda")
+        s.jacobian(dev(soa(*X1)), dev(soa(*X0)), dt, J)
+        s.ras_factor(J)
+        r = dev(soa(*random_vector(p, 29)), ft)
+        outs = []
+        for _ in range(3):
+            z = torch.empty(2 * p.ncells, dtype=ft, device="cuda")
+            s.ras_apply(r, z)
+            outs.append(host(z))
+        torch.cuda.synchronize()
+    assert np.all(np.isfinite(outs[0])) and np.abs(outs[0]).max() > 0
+    assert all(np.array_equal(outs[0], o) for o in outs[1:])

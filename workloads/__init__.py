@@ -283,12 +283,13 @@ class EnsembleWorkload(Workload):
 
 
 # 32 members of 256^2 periodic (h = 1/64, so [0, 4]^2), theta ~ U(0.25, 0.35) per member,
-# FP64 residual with FP32 Krylov / Jacobian / ILU, adaptive dt from 1e-4.  RAS 22x22 boxes
-# (12-cell boxes) with overlap 2: the partition acac_autotune picks for one member.
+# FP64 residual with FP32 Krylov / Jacobian / ILU, adaptive dt from 1e-4.  RAS 3x3 boxes
+# (85-86 owned cells per direction) with overlap 1: the partition acac_autotune picks for the
+# whole ensemble, all members solved in lockstep.
 E32 = EnsembleWorkload(
     "2d-ensemble-32x256x256-periodic-mixed-adaptive",
     Params(dim=2, n=(256, 256, 1), L=(256 * H64, 256 * H64, 1.0), bc=BC_PERIODIC, dt_mode=DT_ADAPTIVE,
-           dt0=1e-4, dt_min=1e-5, dt_max=1e-1, eta0=1e4, ras_parts=(22, 22, 1), ras_overlap=2,
+           dt0=1e-4, dt_min=1e-5, dt_max=1e-1, eta0=1e4, ras_parts=(3, 3, 1), ras_overlap=1,
            precision=PREC_MIXED, batch=32, **_COEF),
     steps=50, seed=3, u_mean=0.4, amp=0.05)
 
