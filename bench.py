@@ -7,7 +7,8 @@ linearisation, Schwarz-ILU(0) factorization and application, GMRES, Newton line
 search, energy / mass and the adaptive-dt predictor.
 
 Default workload: 2D 2048x2048 periodic on [0,32]^2 (mesh spacing h = 1/64), adaptive
-dt from 1e-4 in [1e-5, 1e-1], RAS 16x16 overlap 2 ILU(0) (256 boxes of 132^2 cells),
+dt from 1e-4 in [1e-5, 1e-1], RAS 17x17 overlap 2 ILU(0) (289 boxes of 124-125 cells per
+direction),
 seeded random initial fields (u = 0.4 + 0.05 U(-1,1), v = 0.05 U(-1,1), seed 2),
 Newton rtol 1e-8.  `value` is the FP64 form's rate; the mixed-precision form (FP32
 Jacobian, Krylov vectors and ILU; FP64 residual, Newton update, energy and dt

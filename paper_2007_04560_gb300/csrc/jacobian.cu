@@ -282,7 +282,7 @@ cudaError_t launch_jvp_f(const Geom& g, const JacK<T>* kp, Cache<T> cache, const
 constexpr int JT_X = 64, JT_Y = 16, JT_THREADS = 256;
 
 template <typename T>
-__global__ void __launch_bounds__(JT_THREADS) jvp_tile_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
+__global__ void __launch_bounds__(JT_THREADS, 4) jvp_tile_kernel(Geom g, const JacK<T>* __restrict__ kp, Cache<T> C,
                                                               const T* __restrict__ w, T* __restrict__ y, Members mb) {
     constexpr int WX = JT_X + 4, WY = JT_Y + 4;     // w with halo 2
     constexpr int RX = JT_X + 2, RY = JT_Y + 2;     // ring with halo 1

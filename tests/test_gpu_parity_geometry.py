@@ -3,11 +3,13 @@ workloads, on full-size grids (the oracle takes about a minute per solve here).
 
 * 1024^2 periodic with 16 x 16 boxes and overlap 2 (68^2 extended boxes, the whole-box
   apply kernel): one FP64 time step of the 1024^2 workload from its seeded initial state.
-* 1024^2 periodic with 8 x 8 boxes and overlap 2: extended boxes of 132^2 cells, the boxes
-  of the 2048^2 workload (16 x 16 boxes of 128^2 owned cells), for which the launch plan
-  picks the level-window apply kernel in both precisions (the whole box vector needs
-  296 KB in double, 148 KB in float: more than two CTAs per SM can hold).  One Newton
-  solve in FP64 and one in the mixed form against the same oracle root.
+* 1024^2 periodic with 8 x 8 boxes and overlap 2: extended boxes of 132^2 cells, for which
+  the launch plan picks the level-window apply kernel in both precisions (the whole box
+  vector needs 296 KB in double, 148 KB in float: more than two CTAs per SM can hold).
+  One Newton solve in FP64 and one in the mixed form against the same oracle root.
+* 964^2 periodic with 8 x 8 boxes and overlap 2: extended boxes of 124 and 125 cells per
+  direction, exactly the boxes of the 2048^2 workload (17 x 17 boxes of 120-121 owned
+  cells), again with the level-window apply; the same two solves.
 * Three mixed-precision time steps of the 64^2 workload against the FP64 oracle's steps.
 
 Tolerances: FP64 roots within 1e-9 relative L2 (both sides iterate Newton to rtol 1e-12
@@ -34,6 +36,13 @@ def P():
 def _boxes132():
     """1024^2 on [0,16]^2 (h = 1/64), 8 x 8 boxes of 128^2 owned cells, overlap 2."""
     return C3.params.replace(n=(1024, 1024, 1), L=(1024 * H64, 1024 * H64, 1.0), ras_parts=(8, 8, 1),
+                             ras_overlap=2, dt_mode=0, dt0=1e-4)
+
+
+def _boxes124():
+    """964^2 on [0, 964/64]^2 (h = 1/64), 8 x 8 boxes of 120-121 owned cells, overlap 2: the
+    extended boxes (124 and 125 cells per direction) of the 2048^2 workload's 17 x 17 boxes."""
+    return C3.params.replace(n=(964, 964, 1), L=(964 * H64, 964 * H64, 1.0), ras_parts=(8, 8, 1),
                              ras_overlap=2, dt_mode=0, dt0=1e-4)
 
 
@@ -74,6 +83,29 @@ def test_nks_1024_boxes132(P, precision):
     p = _boxes132()
     U0 = initial_fields(p, C3.seed, C3.u_mean, C3.amp)
     xo, io = _oracle_root("boxes132", p, U0, p.dt0)
+    pg = p.replace(precision=precision, newton_rtol=1e-12 if precision == PREC_FP64 else 1e-8)
+    with P.Solver(pg) as s:
+        U1 = torch.empty(2 * p.ncells, dtype=torch.float64, device="cuda")
+        ig = s.nks_solve(dev(soa(*U0)), p.dt0, U1)
+        xg = host(U1)
+    assert ig.status == 0
+    tol = 1e-9 if precision == PREC_FP64 else 1e-8
+    assert np.linalg.norm(xg - xo) <= tol * np.linalg.norm(xo)
+    if precision == PREC_FP64:
+        assert ig.newton_its == io.newton_its
+    else:
+        assert ig.fnorm <= 1e-8 * ig.fnorm0
+
+
+@pytest.mark.parametrize("precision", [PREC_FP64, PREC_MIXED])
+def test_nks_964_boxes124(P, precision):
+    """One Newton solve at dt = 1e-4 with the 2048^2 workload's box shapes (124 / 125 cells
+    per direction, the level-window apply): FP64 within 1e-9 of the oracle root, the mixed
+    form (Newton rtol 1e-8) within 1e-8."""
+    import torch
+    p = _boxes124()
+    U0 = initial_fields(p, C3.seed, C3.u_mean, C3.amp)
+    xo, io = _oracle_root("boxes124", p, U0, p.dt0)
     pg = p.replace(precision=precision, newton_rtol=1e-12 if precision == PREC_FP64 else 1e-8)
     with P.Solver(pg) as s:
         U1 = torch.empty(2 * p.ncells, dtype=torch.float64, device="cuda")
