@@ -145,11 +145,14 @@ PIECE = 512
 
 
 def piece_params(w):
+    """A square periodic piece of about PIECE^2 cells with the workload's mesh spacing and
+    its Schwarz boxes: an integer number of the workload's owned box widths per side, so
+    the piece's extended boxes have the workload's sizes."""
     p = w.params.replace(batch=1, precision=PREC_FP64)
-    n = min(PIECE, p.n[0])
-    scale = p.n[0] // n
+    own = p.n[0] / p.ras_parts[0]                       # owned box width of the workload
+    parts = max(2, min(p.ras_parts[0], int(round(min(PIECE, p.n[0]) / own))))
+    n = int(round(parts * own))
     h = p.L[0] / p.n[0]
-    parts = max(2, p.ras_parts[0] // scale)
     return p.replace(n=(n, n, 1), L=(n * h, n * h, 1.0), ras_parts=(parts, parts, 1), dt_mode=0, dt0=p.dt_min)
 
 
@@ -236,12 +239,13 @@ def cpu_baseline(w, repeats=3):
     out["cores"] = out["all_cores"]["cores"]
     out["sample"] = (
         "FP64 NumPy/SciPy + C ILU(0) oracle on %dx%d periodic pieces of the workload (same h, coefficients, "
-        "tolerances and %dx%d Schwarz boxes with overlap %d), one time step at dt = dt_min = %g from seeded "
-        "initial states, scaled by piece/workload cells (1/%d); median of %d rounds.  single: one process; "
+        "tolerances and Schwarz boxes of %d to %d cells per side with overlap %d), one time step at dt = dt_min = %g from seeded "
+        "initial states, scaled by piece/workload cells (1/%.2f); median of %d rounds.  single: one process; "
         "all_cores: %d processes at once, one piece each (the pieces are not coupled, so this bounds a "
         "multi-core oracle from above); nproc = %d" % (
-            p.n[0], p.n[1], p.n[0] // p.ras_parts[0] + 2 * p.ras_overlap, p.n[1] // p.ras_parts[1] + 2 * p.ras_overlap,
-            p.ras_overlap, p.dt0, tiles, repeats, out["all_cores"]["cores"], ncpu))
+            p.n[0], p.n[1], p.n[0] // p.ras_parts[0] + 2 * p.ras_overlap,
+            -(-p.n[1] // p.ras_parts[1]) + 2 * p.ras_overlap,
+            p.ras_overlap, p.dt0, w.params.ncells / p.ncells, repeats, out["all_cores"]["cores"], ncpu))
     return out
 
 
@@ -401,11 +405,15 @@ def run_mine(args, rank, world):
                 "h2d_bytes_per_step": 16 * N * B, "d2h_bytes_per_step": 16 * N * B}
 
     def box_geometry(p):
+        """(extended width of the narrowest box, cells of all boxes): per axis the owned
+        widths add up to n and every box adds the overlap on each side (not on a wall's
+        side, with Neumann walls)."""
         if p.dim != 2:
             return None, None
         wb = p.n[0] // p.ras_parts[0] + 2 * p.ras_overlap
-        hb = p.n[1] // p.ras_parts[1] + 2 * p.ras_overlap
-        return wb, wb * hb * p.ras_parts[0] * p.ras_parts[1]
+        ends = 0 if p.bc == 0 else 1     # periodic: every box overlaps on both sides
+        ext = [p.n[a] + 2 * p.ras_overlap * (p.ras_parts[a] - ends) for a in (0, 1)]
+        return wb, ext[0] * ext[1]
 
     def summary(res, prec):
         infos = res["infos"]
@@ -494,6 +502,8 @@ def run_mine(args, rank, world):
             "iterations": tsm["iterations"], "roofline": tsm["roofline"], "kernels": tsm["kernels"],
             "kernels_timed": tsm["kernels_timed"],
         }
+    if not args.no_extras and world == 1:
+        out["other_workloads"] = other_workloads(P, stream, dev, args.extra_steps)
     if not args.no_cpu_baseline and world == 1 or (not args.no_cpu_baseline and rank == 0):
         try:
             out["cpu_baseline"] = cpu_baseline(w)
@@ -501,6 +511,72 @@ def run_mine(args, rank, world):
             out["cpu_baseline"] = {"value": None, "unit": "steps/s", "cores": 0, "kind": "oracle",
                                    "sample": "failed: %s" % str(e)[-200:]}
     return out
+
+
+def other_workloads(P, stream, dev, steps):
+    """The other configurations, briefly (device-timed, inputs resident in HBM, 3 warm-up
+    steps then `steps` timed ones): 3D 128^3 Neumann in both precision forms, the 32 x 256^2
+    ensemble, and one gradient of the 512^2 adjoint workload (20 steps forward and back)."""
+    import torch
+    from workloads import C4, C4_FP64, C5, E32
+    res = []
+
+    def stepped(w):
+        p = w.params
+        s = P.Solver(p, stream)
+        if p.batch > 1:
+            th = w.thetas()
+            for m in range(p.batch):
+                s.set_coeffs(m, p.alpha, p.beta, float(th[m]), p.gamma, p.rho)
+        u0, v0 = w.fields()
+        u = torch.tensor(u0.ravel(), device=dev)
+        v = torch.tensor(v0.ravel(), device=dev)
+        for _ in range(3):
+            s.step(u, v)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos = [s.step(u, v) for _ in range(steps)]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        s.close()
+        ms = e0.elapsed_time(e1) / steps
+        first = [i[0] if isinstance(i, list) else i for i in infos]
+        B = int(p.batch)
+        return {"workload": w.name, "value": 1000.0 * B / ms, "unit": "steps/s" if B == 1 else "member-steps/s",
+                "ms_per_step": ms, "steps": steps, "warmup": 3,
+                "ras": "%s overlap %d" % ("x".join(str(x) for x in p.ras_parts[:p.dim]), p.ras_overlap),
+                "newton_per_step": sum(i.newton_its for i in first) / steps,
+                "gmres_per_step": sum(i.gmres_its for i in first) / steps,
+                "dt_last": first[-1].dt}
+
+    for w in (C4, C4_FP64, E32):
+        try:
+            res.append(stepped(w))
+        except Exception as e:                                   # reported, not fatal
+            res.append({"workload": w.name, "error": str(e)[-200:]})
+    try:
+        p = C5.params
+        u0, v0 = C5.fields()
+        ut, vt = C5.target()
+        t = lambda a: torch.tensor(a.ravel(), device=dev)
+        with P.Solver(p, stream) as s:
+            s.adjoint(t(u0), t(v0), C5.steps, p.dt0, t(ut), t(vt), C5.w_energy, C5.w_misfit, C5.every)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            L, _, _, g, its = s.adjoint(t(u0), t(v0), C5.steps, p.dt0, t(ut), t(vt), C5.w_energy, C5.w_misfit,
+                                        C5.every)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        res.append({"workload": C5.name, "value": 1000.0 / ms, "unit": "gradients/s", "ms_per_gradient": ms,
+                    "gradient": "loss after %d fixed-dt steps w.r.t. u0, v0, alpha, beta, theta, gamma "
+                                "(checkpoint every %d)" % (C5.steps, C5.every),
+                    "adjoint_gmres_its": its, "loss": L})
+    except Exception as e:
+        res.append({"workload": C5.name, "error": str(e)[-200:]})
+    return res
 
 
 def run_reference(args, rank, world):
@@ -553,6 +629,8 @@ def main():
     ap.add_argument("--no-twin", action="store_true", help="skip the other precision form")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the other workloads' brief timings")
+    ap.add_argument("--extra-steps", type=int, default=10)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

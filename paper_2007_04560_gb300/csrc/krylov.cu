@@ -58,13 +58,20 @@ __device__ __forceinline__ void stp(T* __restrict__ p, long long i, const Pk<T, 
     }
 }
 // Runs f(pack index) over the whole packs and g(element index) over the remaining elements,
-// grid-stride within the member's blocks.
-template <int P, typename F, typename G>
+// grid-stride within the member's blocks; with U = 2 two packs per trip, so that the loads
+// of both are issued before either is used (twice the bytes in flight per thread).
+template <int P, int U = 2, typename F, typename G>
 __device__ __forceinline__ void over_packs(long long n, F f, G g) {
     const long long np = n / P;
     const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x, st = (long long)gridDim.x * blockDim.x;
-    for (long long i = t0; i < np; i += st) f(i);
-    for (long long i = np * P + t0; i < n; i += st) g(i);
+    long long i = t0;
+    if (U == 2)
+        for (; i + st < np; i += 2 * st) {
+            f(i);
+            f(i + st);
+        }
+    for (; i < np; i += st) f(i);
+    for (long long e = np * P + t0; e < n; e += st) g(e);
 }
 static bool al16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
@@ -134,9 +141,9 @@ cudaError_t launch_norm2_double(const double* a, const double* b, long long n, R
 }
 
 // ---------------------------------------------------------------- V^T w
-// Vectors are processed in chunks of up to 8, the chunk width a template parameter (a
-// predicated FP64 multiply-add still occupies the FP64 pipe, so a fixed 8-wide loop with
-// masked lanes cost 8 products per element whatever the count).  Each thread
+// Vectors are processed in chunks of up to 4, the chunk width a template parameter (a
+// predicated multiply-add still occupies its pipe, so a fixed-width loop with masked
+// lanes would cost the full width per element whatever the count).  Each thread
 // accumulates its share in the Krylov precision; the block and global stages add in
 // double, the block stage with one barrier per chunk.
 template <typename T, int C, int P>
@@ -145,7 +152,7 @@ __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld,
     T acc[C];
 #pragma unroll
     for (int q = 0; q < C; ++q) acc[q] = 0;
-    over_packs<P>(n, [&](long long i) {
+    over_packs<P, (C <= 2 ? 2 : 1)>(n, [&](long long i) {
         const Pk<T, P> wi = ldp<T, P>(w, i);
 #pragma unroll
         for (int q = 0; q < C; ++q) {
@@ -174,8 +181,11 @@ __device__ __forceinline__ void dot_chunk(const T* __restrict__ V, long long ld,
     __syncthreads();
 }
 
-template <typename T, int P>
-__global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld, int nv,
+// One launch per chunk of up to four vectors, the width a template parameter: the kernel
+// keeps only that chunk's packs in registers (it is bound by the bytes in flight, i.e. by
+// the resident warps), and chunks of one or two vectors take two packs per trip.
+template <typename T, int P, int C>
+__global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restrict__ V, long long ld,
                                                                 const T* __restrict__ w, long long n,
                                                                 Red red, Members mb) {
     __shared__ double sw[8][RED_THREADS / 32];
@@ -184,31 +194,38 @@ __global__ void __launch_bounds__(RED_THREADS) multi_dot_kernel(const T* __restr
     V += (size_t)m * mb.vs;
     w += (size_t)m * mb.vs;
     red = member_red(red, mb, m);
-    for (int k0 = 0; k0 < nv; k0 += 8) {
-        const T* Vk = V + (size_t)k0 * ld;
-        double* pk = red.partial + (size_t)k0 * gridDim.x;
-        switch (nv - k0 < 8 ? nv - k0 : 8) {
-            case 1: dot_chunk<T, 1, P>(Vk, ld, w, n, pk, sw); break;
-            case 2: dot_chunk<T, 2, P>(Vk, ld, w, n, pk, sw); break;
-            case 3: dot_chunk<T, 3, P>(Vk, ld, w, n, pk, sw); break;
-            case 4: dot_chunk<T, 4, P>(Vk, ld, w, n, pk, sw); break;
-            case 5: dot_chunk<T, 5, P>(Vk, ld, w, n, pk, sw); break;
-            case 6: dot_chunk<T, 6, P>(Vk, ld, w, n, pk, sw); break;
-            case 7: dot_chunk<T, 7, P>(Vk, ld, w, n, pk, sw); break;
-            default: dot_chunk<T, 8, P>(Vk, ld, w, n, pk, sw); break;
-        }
-    }
-    finish_reduction(red, nv, nullptr);
+    dot_chunk<T, C, P>(V, ld, w, n, red.partial, sw);
+    finish_reduction(red, C, nullptr);
 }
 
+template <typename T, int P>
+static void multi_dot_chunk(const T* V, long long ld, int c, const T* w, long long n, Red red, cudaStream_t s,
+                            const Members& mb) {
+    const dim3 g = vgrid(n, mb);
+    switch (c) {
+        case 1: multi_dot_kernel<T, P, 1><<<g, RED_THREADS, 0, s>>>(V, ld, w, n, red, mb); break;
+        case 2: multi_dot_kernel<T, P, 2><<<g, RED_THREADS, 0, s>>>(V, ld, w, n, red, mb); break;
+        case 3: multi_dot_kernel<T, P, 3><<<g, RED_THREADS, 0, s>>>(V, ld, w, n, red, mb); break;
+        default: multi_dot_kernel<T, P, 4><<<g, RED_THREADS, 0, s>>>(V, ld, w, n, red, mb); break;
+    }
+}
+
+// h[k] = V_k . w for k < nv: the chunks' results land at red.out + k0 (the launches run in
+// stream order and share the partials and the counter)
 template <typename T>
 cudaError_t launch_multi_dot(const T* V, long long ld, int nv, const T* w, long long n, Red red,
                              cudaStream_t s, const Members& mb) {
-    if (al16(V) && al16(w) && (ld * sizeof(T)) % 16 == 0)
-        multi_dot_kernel<T, 16 / sizeof(T)><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
-    else
-        multi_dot_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(V, ld, nv, w, n, red, mb);
-    return cudaGetLastError();
+    const bool vec = al16(V) && al16(w) && (ld * sizeof(T)) % 16 == 0;
+    for (int k0 = 0; k0 < nv; k0 += 4) {
+        Red r = red;
+        r.out += k0;
+        const int c = nv - k0 < 4 ? nv - k0 : 4;
+        if (vec) multi_dot_chunk<T, 16 / sizeof(T)>(V + (size_t)k0 * ld, ld, c, w, n, r, s, mb);
+        else multi_dot_chunk<T, 1>(V + (size_t)k0 * ld, ld, c, w, n, r, s, mb);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 // ---------------------------------------------------------------- w -= V h  (+ ||w||^2)

@@ -43,6 +43,12 @@ __device__ __forceinline__ int level_jmin(int l, int W) {
     return t > 0 ? t / 2 : 0;
 }
 
+// (i + dx, j + dy) inside a W x H box, for a cell (i, j) inside it: with dx, dy known at
+// compile time only the sides the offset can cross are tested.
+__device__ __forceinline__ bool in_box(int i, int j, int dx, int dy, int W, int H) {
+    return (dx >= 0 || i + dx >= 0) && (dx <= 0 || i + dx < W) && (dy >= 0 || j + dy >= 0) && (dy <= 0 || j + dy < H);
+}
+
 // Global cell of box-local (i, j).
 __device__ __forceinline__ int box_cell(const Geom& g, const SubInfo& sd, int i, int j) {
     int gx = sd.ox + i, gy = sd.oy + j;
@@ -119,10 +125,10 @@ __device__ __forceinline__ void fetch_rows(const Geom& g, const SubInfo& sd, con
         const T* src = J + ((size_t)(sd.coef_base / NCOEF) + lo[l] + m) * (4 * NSLOT) + rr * 2 * NSLOT;
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) {
-            const int ii = i + slot_dx(s), jj = j + slot_dy(s);
-            const bool in = ii >= 0 && ii < sd.W && jj >= 0 && jj < sd.H;
-            dst[s][0] = in ? src[2 * s] : (T)0;
-            dst[s][1] = in ? src[2 * s + 1] : (T)0;
+            V2<T> v{(T)0, (T)0};
+            if (in_box(i, j, slot_dx(s), slot_dy(s), sd.W, sd.H)) v = *reinterpret_cast<const V2<T>*>(src + 2 * s);
+            dst[s][0] = v.x;
+            dst[s][1] = v.y;
         }
         return;
     }
@@ -155,47 +161,56 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
     for (int l = threadIdx.x; l <= sd.nlev; l += blockDim.x) lo[l] = lev_off[sd.lev_base + l];
     __syncthreads();
     const int m = threadIdx.x >> 1, rr = threadIdx.x & 1;
+    const int W = sd.W;
     int bad = 0;
     T Jn[NSLOT][2];
     fetch_rows<T>(g, sd, lo, J, packed, 0, m, rr, Jn);
+    // ring slots (element offsets) of the levels l, l-1 .. l-4, rotated by one per level (the
+    // slot of level l is l mod FACTOR_RING), and the first rows of those levels
+    const int rstride = ring_cells * CREC;
+    int sl0 = 0, sl1 = 4 * rstride, sl2 = 3 * rstride, sl3 = 2 * rstride, sl4 = rstride;
     for (int l = 0; l < sd.nlev; ++l) {
         T A[NSLOT][2];
 #pragma unroll
         for (int s = 0; s < NSLOT; ++s) { A[s][0] = Jn[s][0]; A[s][1] = Jn[s][1]; }
         if (l + 1 < sd.nlev) fetch_rows<T>(g, sd, lo, J, packed, l + 1, m, rr, Jn);
         const int cnt = lo[l + 1] - lo[l];
-        const int j = level_jmin(l, sd.W) + m, i = l - 2 * j;
+        const int jm0 = level_jmin(l, W), jm1 = level_jmin(l - 1, W), jm2 = level_jmin(l - 2, W);
+        const int jm3 = level_jmin(l - 3, W), jm4 = level_jmin(l - 4, W);
+        const int j = jm0 + m, i = l - 2 * j;
         const bool act = m < cnt;
         T* fw = coef + sd.coef_base + (long long)lo[l] * NCOEF + (long long)m * CREC;
         T* bw = fw + (long long)cnt * CREC;
-        T* rb = ring + ((size_t)(l % FACTOR_RING) * ring_cells + m) * CREC;
+        T* rb = ring + sl0 + m * CREC;
         if (act) {
 #pragma unroll
             for (int a = 0; a < 6; ++a) {
                 const int dx1 = lower_dx(a), dy1 = lower_dy(a);
-                const int ki = i + dx1, kj = j + dy1;
+                const int d = -(dx1 + 2 * dy1);           // the neighbour's level is l - d (1..4)
                 T L0 = (T)0, L1 = (T)0;
-                if (ki >= 0 && ki < sd.W && kj >= 0 && kj < sd.H) {
-                    const int lk = l + dx1 + 2 * dy1;
-                    const T* kr = ring + ((size_t)(lk % FACTOR_RING) * ring_cells + (kj - level_jmin(lk, sd.W))) * CREC;
+                if (in_box(i, j, dx1, dy1, W, sd.H)) {
+                    const int sb = d == 1 ? sl1 : d == 2 ? sl2 : d == 3 ? sl3 : sl4;
+                    const int jb = d == 1 ? jm1 : d == 2 ? jm2 : d == 3 ? jm3 : jm4;
+                    const T* kr = ring + sb + (j + dy1 - jb) * CREC;
                     const T* As = A[slot_of(dx1, dy1)];
-                    L0 = As[0] * kr[0] + As[1] * kr[2];
-                    L1 = As[0] * kr[1] + As[1] * kr[3];
+                    const V2<T> p0 = *reinterpret_cast<const V2<T>*>(kr);       // kr[0], kr[1]
+                    const V2<T> p1 = *reinterpret_cast<const V2<T>*>(kr + 2);   // kr[2], kr[3]
+                    L0 = As[0] * p0.x + As[1] * p1.x;
+                    L1 = As[0] * p0.y + As[1] * p1.y;
 #pragma unroll
                     for (int b = 0; b < 6; ++b) {
                         const int s2 = slot_of(dx1 + upper_dx(b), dy1 + upper_dy(b));
                         if (s2 >= 0) {
-                            const T* U = kr + 4 + 4 * b;
-                            A[s2][0] = fma(-L1, U[2], fma(-L0, U[0], A[s2][0]));
-                            A[s2][1] = fma(-L1, U[3], fma(-L0, U[1], A[s2][1]));
+                            const V2<T> u0 = *reinterpret_cast<const V2<T>*>(kr + 4 + 4 * b);   // U[0], U[1]
+                            const V2<T> u1 = *reinterpret_cast<const V2<T>*>(kr + 6 + 4 * b);   // U[2], U[3]
+                            A[s2][0] = fma(-L1, u1.x, fma(-L0, u0.x, A[s2][0]));
+                            A[s2][1] = fma(-L1, u1.y, fma(-L0, u0.y, A[s2][1]));
                         }
                     }
                 }
-                fw[4 * a + 2 * rr] = L0;
-                fw[4 * a + 2 * rr + 1] = L1;
+                *reinterpret_cast<V2<T>*>(fw + 4 * a + 2 * rr) = V2<T>{L0, L1};
             }
-            fw[24 + 2 * rr] = (T)0;
-            fw[25 + 2 * rr] = (T)0;
+            *reinterpret_cast<V2<T>*>(fw + 24 + 2 * rr) = V2<T>{(T)0, (T)0};
         }
         // pivot block D = A[0]: row rr here, the other row in the partner lane
         const T o0 = __shfl_xor_sync(0xffffffffu, A[0][0], 1);
@@ -208,20 +223,19 @@ __global__ void __launch_bounds__(256) ras_factor_kernel(Geom g, const SubInfo* 
             const T id = (T)1 / det;
             const T i0 = rr ? -d10 * id : d11 * id;    // row rr of D^-1
             const T i1 = rr ? d00 * id : -d01 * id;
-            bw[2 * rr] = i0;
-            bw[2 * rr + 1] = i1;
-            rb[2 * rr] = i0;
-            rb[2 * rr + 1] = i1;
+            *reinterpret_cast<V2<T>*>(bw + 2 * rr) = V2<T>{i0, i1};
+            *reinterpret_cast<V2<T>*>(rb + 2 * rr) = V2<T>{i0, i1};
 #pragma unroll
             for (int b = 0; b < 6; ++b) {
-                const int s = slot_of(upper_dx(b), upper_dy(b));
-                bw[4 + 4 * b + 2 * rr] = A[s][0];
-                bw[4 + 4 * b + 2 * rr + 1] = A[s][1];
-                rb[4 + 4 * b + 2 * rr] = A[s][0];
-                rb[4 + 4 * b + 2 * rr + 1] = A[s][1];
+                const int sx = slot_of(upper_dx(b), upper_dy(b));
+                *reinterpret_cast<V2<T>*>(bw + 4 + 4 * b + 2 * rr) = V2<T>{A[sx][0], A[sx][1]};
+                *reinterpret_cast<V2<T>*>(rb + 4 + 4 * b + 2 * rr) = V2<T>{A[sx][0], A[sx][1]};
             }
         }
         __syncthreads();
+        // level l+1 takes the slot of l-4
+        const int t = sl4;
+        sl4 = sl3; sl3 = sl2; sl2 = sl1; sl1 = sl0; sl0 = t;
     }
     if (bad) atomicOr(flags, 4);
 }

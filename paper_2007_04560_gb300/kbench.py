@@ -32,7 +32,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-COMPONENTS = ("residual", "jacobian", "spmv", "jvp", "ras_factor", "ras_apply", "energy")
+COMPONENTS = ("residual", "jacobian", "spmv", "jvp", "ras_factor", "ras_apply", "energy", "nks")
 
 
 def main(argv=None):
@@ -106,6 +106,9 @@ def main(argv=None):
         "ras_factor": lambda: s.ras_factor(J),
         "ras_apply": lambda: s.ras_apply(wv, y),
         "energy": lambda: s.energy(x1[:N], x1[N:]),
+        # one Newton solve from X0 at dt (every kernel of the step's solve, including pass A
+        # writing the linearisation cache and the Gram-Schmidt kernels)
+        "nks": lambda: s.nks_solve(x0, dt, F),
     }
     print("workload %s, %s, %d cells, %d reps" % (w.name, "mixed" if p.precision == PREC_MIXED else "fp64", N,
                                                   args.reps))
