@@ -42,16 +42,21 @@ FP32_DERIVED_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 
 # DRAM bytes (read + write) per box cell of the Schwarz kernels, from one-kernel ncu captures
-# of the current kernels on 1024^2 grids with 8x8 boxes of the same 132^2 cells as the 2048^2
-# workloads (one box per SM; profiles/ras_factor_2d-boxes132-fp64.md,
-# profiles/ras_apply_win_2d-boxes132.md): a launch's traffic is this x its box cells (the
-# traffic grows with the box cells).  Keyed by (kernel class, precision, extended box width).
-# A kernel changed after its capture must be removed from this table.
+# of the current kernels on a 964^2 grid with 8x8 boxes of the same 124-125 cells as the 2048^2
+# workloads (one box per SM; profiles/ras_factor_2d-boxes124.md,
+# profiles/ras_apply_win_2d-boxes124.md): a launch's traffic is this x its box cells (the
+# traffic grows with the box cells).  Keyed by (kernel class, precision, width of the
+# narrowest extended box).  A kernel changed after its capture must be removed from this table.
 TRAFFIC_PER_BOX_CELL = {
-    ("ras_factor", PREC_FP64, 132): 1014.398e6 / 1115136,
-    ("ras_apply", PREC_FP64, 132): 568.777e6 / 1115136,
-    ("ras_apply", PREC_MIXED, 132): 282.487e6 / 1115136,
+    ("ras_factor", PREC_FP64, 124): 866.94e6 / 992016,
+    ("ras_factor", PREC_MIXED, 124): 381.76e6 / 992016,
+    ("ras_apply", PREC_FP64, 124): 505.17e6 / 992016,
+    ("ras_apply", PREC_MIXED, 124): 249.47e6 / 992016,
 }
+# DRAM bytes per grid cell of cell kernels, from captures at the 2048^2 grid itself (or, where
+# that held too much on the device, at the workload's mesh on a smaller grid whose traffic per
+# cell matches): keyed by (kernel class, precision).
+TRAFFIC_PER_CELL = {}
 
 
 def hbm_peak():
@@ -260,7 +265,7 @@ def fp64_peak(probe):
 FP64_CLASSES = {"residual_g", "residual_f", "energy"}
 
 
-def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None):
+def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None, cells=None):
     name, (n, ms, b, f) = max(stats.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
         return None
@@ -273,6 +278,8 @@ def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=No
         fpeak, fsrc = FP32_DERIVED_TFLOPS, "derived: 152 SMs x 128 FFMA/clk x 2 flop x 2.07 GHz"
     per = TRAFFIC_PER_BOX_CELL.get((name, precision, box_w))
     traffic = per * box_cells if per is not None else None
+    if traffic is None and cells and (name, precision) in TRAFFIC_PER_CELL:
+        traffic = TRAFFIC_PER_CELL[(name, precision)] * cells
     intensity = f / b if b > 0 else 0.0
     ridge = fpeak * 1e12 / (hbm_gbs * 1e9)
     out = {"kernel": name, "launches": n, "avg_launch_us": ms * 1e3 / n, "share_of_kernel_time": None,
@@ -423,7 +430,8 @@ def run_mine(args, rank, world):
             "iterations": {"newton_per_step": nits / len(infos),
                            "gmres_per_newton": sum(i["gmres_its"] for i in infos) / max(1, nits),
                            "dt_first": infos[0]["dt"], "dt_last": infos[-1]["dt"], "t_end": infos[-1]["t"]},
-            "roofline": roofline(res["stats"], prec, hbm_peak(), probe_fp64, bc, bw, res["warm_stats"]),
+            "roofline": roofline(res["stats"], prec, hbm_peak(), probe_fp64, bc, bw, res["warm_stats"],
+                                 res["params"].ncells * int(res["params"].batch)),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
                             "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
                         for k, v in res["stats"].items() if v[0] > 0},
