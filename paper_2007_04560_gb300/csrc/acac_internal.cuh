@@ -136,6 +136,49 @@ struct Coef {
     int S;
 };
 
+// ---------------------------------------------------------------- conversions
+// Conversions between double and float, and from int to double, on the integer units: on
+// this GPU a conversion instruction takes an FP64-pipe slot (it issues at the FP64
+// multiply-add rate, 1/64 of the FP32 rate), and the FP64 pipe bounds the kernels that
+// convert.  The results equal the conversion instructions' bit for bit (round to nearest
+// even); operands whose result is not a normal number take the instruction.
+__device__ __forceinline__ float dbl2flt(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long a = b & 0x7fffffffffffffffULL;
+    // |x| in [2^-126, 2^128): exponent field 897..1150
+    if (a - 0x3810000000000000ULL >= 0x0FE0000000000000ULL) return __double2float_rn(x);
+    unsigned int f = (unsigned int)((a >> 29) - (896ULL << 23));    // rebiased exponent, top 23 bits
+    const unsigned long long r = a & 0x1FFFFFFFULL;                  // the 29 bits dropped
+    f += (unsigned int)((r > 0x10000000ULL) | ((r == 0x10000000ULL) & (f & 1u)));   // a carry may reach the exponent
+    return __uint_as_float(f | ((unsigned int)(b >> 32) & 0x80000000u));
+}
+__device__ __forceinline__ double flt2dbl(float x) {
+    const unsigned int b = __float_as_uint(x);
+    const unsigned int a = b & 0x7fffffffu;
+    if (a - 0x00800000u >= 0x7f000000u) return (double)x;            // zero, subnormal, inf, NaN
+    const unsigned long long d = ((unsigned long long)a << 29) + (896ULL << 52);
+    return __longlong_as_double((long long)(d | ((unsigned long long)(b & 0x80000000u) << 32)));
+}
+__device__ __forceinline__ double int2dbl(int i) {
+    if (i == 0) return 0.0;
+    const unsigned int a = i < 0 ? 0u - (unsigned int)i : (unsigned int)i;
+    const int p = 31 - __clz(a);                                     // a in [2^p, 2^(p+1))
+    const unsigned long long m = ((unsigned long long)a << (52 - p)) & 0x000FFFFFFFFFFFFFULL;
+    const unsigned long long sgn = i < 0 ? 0x8000000000000000ULL : 0ULL;
+    return __longlong_as_double((long long)(sgn | ((unsigned long long)(1023 + p) << 52) | m));
+}
+// double -> Krylov precision T, and back
+template <typename T>
+__device__ __forceinline__ T from_dbl(double x) {
+    if constexpr (sizeof(T) == 4) return dbl2flt(x);
+    else return x;
+}
+template <typename T>
+__device__ __forceinline__ double to_dbl(T x) {
+    if constexpr (sizeof(T) == 4) return flt2dbl(x);
+    else return x;
+}
+
 // ---------------------------------------------------------------- ensemble members
 // An ensemble is `count` independent problems of one grid and one box decomposition,
 // solved in lockstep: every launch covers all members, member m being a grid index

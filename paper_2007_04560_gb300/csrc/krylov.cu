@@ -328,9 +328,9 @@ __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* 
         const Pk<double, P> a = ldp<double, P>(x, i);
         Pk<T, P> r;
 #pragma unroll
-        for (int e = 0; e < P; ++e) r.v[e] = (T)(a.v[e] * scale);
+        for (int e = 0; e < P; ++e) r.v[e] = from_dbl<T>(a.v[e] * scale);
         stp<T, P>(out, i, r);
-    }, [&](long long i) { out[i] = (T)(x[i] * scale); });
+    }, [&](long long i) { out[i] = from_dbl<T>(x[i] * scale); });
 }
 
 template <typename T>
@@ -394,9 +394,9 @@ __global__ void axpy_to_double_kernel(double a, const T* __restrict__ x, double*
         const Pk<T, P> xi = ldp<T, P>(x, i);
         Pk<double, P> yi = ldp<double, P>(y, i);
 #pragma unroll
-        for (int e = 0; e < P; ++e) yi.v[e] = fma(a, (double)xi.v[e], yi.v[e]);
+        for (int e = 0; e < P; ++e) yi.v[e] = fma(a, to_dbl<T>(xi.v[e]), yi.v[e]);
         stp<double, P>(y, i, yi);
-    }, [&](long long i) { y[i] = fma(a, (double)x[i], y[i]); });
+    }, [&](long long i) { y[i] = fma(a, to_dbl<T>(x[i]), y[i]); });
 }
 
 template <typename T>
@@ -425,12 +425,12 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
         Pk<double, P> ri;
 #pragma unroll
         for (int e = 0; e < P; ++e) {
-            ri.v[e] = bi.v[e] - (double)ai.v[e];
+            ri.v[e] = bi.v[e] - to_dbl<T>(ai.v[e]);
             acc = fma(ri.v[e], ri.v[e], acc);
         }
         stp<double, P>(r, i, ri);
     }, [&](long long i) {
-        const double ri = b[i] - (double)Ax[i];
+        const double ri = b[i] - to_dbl<T>(Ax[i]);
         r[i] = ri;
         acc = fma(ri, ri, acc);
     });

@@ -99,7 +99,7 @@ __device__ __forceinline__ double table_log(double x) {
     q = fma(u, q, -0.5);
     const double ln2_hi = 6.93147180559890330187045037746429443359375e-1;   // 42 significant bits
     const double ln2_lo = 5.497923018708371174712471233040e-14;
-    const double ed = (double)e;
+    const double ed = int2dbl(e);
     const double hi = fma(ed, ln2_hi, t0.y);
     const double lo = fma(ed, ln2_lo, t1);
     return hi + (u + fma(u2, q, lo));
@@ -129,7 +129,7 @@ __device__ __forceinline__ int series_terms_bits(float rmax_lane, int S, float b
     return K < 1 ? 1 : (K > S ? S : K);
 }
 __device__ __forceinline__ int series_terms(double rmax_lane, int S) {
-    return series_terms_bits((float)rmax_lane, S, 60.0f);
+    return series_terms_bits(dbl2flt(rmax_lane), S, 60.0f);
 }
 // sum_{k=1..S} r^(k-1) / (2k+1), Horner form (in the precision T of the Jacobian).
 template <typename T>
@@ -297,10 +297,10 @@ __device__ __forceinline__ bool in_unit(double x) {
 // carry the 1/2; in double with pass A's warp-uniform K terms, or in float with all S terms.
 template <typename T>
 __device__ __forceinline__ T dphi_from_args(const SeriesArgs& s, int K) {
-    const T a = (T)s.a, b = (T)s.b, ra = (T)s.ra, rb = (T)s.rb;
+    const T a = from_dbl<T>(s.a), b = from_dbl<T>(s.b), ra = from_dbl<T>(s.ra), rb = from_dbl<T>(s.rb);
     const T R1 = series_R<T>(ra, K), R2 = series_R<T>(rb, K);
     const T one = (T)1;
-    return (one + ra * R1 - a * R1) * (T)s.iz + (one + rb * R2 + b * R2) * (T)s.io;
+    return (one + ra * R1 - a * R1) * from_dbl<T>(s.iz) + (one + rb * R2 + b * R2) * from_dbl<T>(s.io);
 }
 
 template <int DIM, bool PRE, int CM>
@@ -388,14 +388,14 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
             if (live) {
                 Cache<T> C;
                 if constexpr (CM == 1) C = a.cache_d; else C = a.cache_f;
-                const T theta = (T)k.theta, halpha = (T)(0.5 * k.alpha);
+                const T theta = from_dbl<T>(k.theta), halpha = from_dbl<T>(0.5 * k.alpha);
                 const T A = theta * dp, B = theta * dq;
-                const T ubT = (T)ub, vbT = (T)vb;
-                C.c[c] = (T)cmob;
+                const T ubT = from_dbl<T>(ub), vbT = from_dbl<T>(vb);
+                C.c[c] = from_dbl<T>(cmob);
                 C.cu[c] = (T)0.5 * ((T)1 - (T)2 * ubT) * ((T)0.25 - vbT * vbT);
                 C.cv[c] = -ubT * ((T)1 - ubT) * vbT;
-                C.Gu[c] = (T)Gu;
-                C.Gv[c] = (T)Gv;
+                C.Gu[c] = from_dbl<T>(Gu);
+                C.Gv[c] = from_dbl<T>(Gv);
                 C.du[c] = -halpha + A + B;
                 C.xc[c] = A - B;
             }
