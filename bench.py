@@ -56,7 +56,13 @@ TRAFFIC_PER_BOX_CELL = {
 # DRAM bytes per grid cell of cell kernels, from captures at the 2048^2 grid itself (or, where
 # that held too much on the device, at the workload's mesh on a smaller grid whose traffic per
 # cell matches): keyed by (kernel class, precision).
-TRAFFIC_PER_CELL = {}
+TRAFFIC_PER_CELL = {
+    # residual pass A writing the linearisation cache (the Newton loop's evaluations):
+    # profiles/residual_g_jvp_tile_2d-2048x2048.md; float cache at 2048^2 itself, double cache
+    # at 1448^2 (part of its writes was still in L2 when the kernel ended)
+    ("residual_g", PREC_MIXED): 378.26e6 / 4194304,
+    ("residual_g", PREC_FP64): 215.60e6 / 2096704,
+}
 
 
 def hbm_peak():

@@ -752,8 +752,12 @@ __global__ void __launch_bounds__(1024) ras_apply_win_kernel(Geom g, const SubIn
                 return false;
             }
             if (threadIdx.x == 0) {
-                if (fwd_done) {
-                    __threadfence_block();   // this level's scratch writes before the count
+                // the backward sweep starts at the last level, whose right-hand side is the
+                // forward sweep's last result: the producer needs the whole forward result
+                // before its first backward stage, so the count is published once, after the
+                // last forward level (a fence per level would sit on every level's path)
+                if (fwd_done && k + 1 == nlev) {
+                    __threadfence_block();   // the forward results in the scratch before the count
                     s_done = k + 1;
                 }
                 mbar_arrive(smem_addr(&empty[b]));

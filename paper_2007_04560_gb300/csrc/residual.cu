@@ -80,6 +80,10 @@ cudaError_t set_taylor_constants(int) {
 // compare it with the library logarithm over the arguments the kernels use.  The range
 // test and F are formed on the bit patterns (integer instructions): on this GPU every
 // FP64 instruction costs an FP64-pipe slot, and those bound the kernels that call this.
+// IEXP: the exponent's conversion to double on the integer units (int2dbl) or by the
+// conversion instruction; the first is faster in every kernel measured but pass A with the
+// FP64 cache (2.9% slower there).
+template <bool IEXP = true>
 __device__ __forceinline__ double table_log(double x) {
     const long long bits = __double_as_longlong(x);
     // positive normal numbers: bits in [bits(DBL_MIN), bits(DBL_MAX)]
@@ -99,7 +103,7 @@ __device__ __forceinline__ double table_log(double x) {
     q = fma(u, q, -0.5);
     const double ln2_hi = 6.93147180559890330187045037746429443359375e-1;   // 42 significant bits
     const double ln2_lo = 5.497923018708371174712471233040e-14;
-    const double ed = int2dbl(e);
+    const double ed = IEXP ? int2dbl(e) : (double)e;
     const double hi = fma(ed, ln2_hi, t0.y);
     const double lo = fma(ed, ln2_lo, t1);
     return hi + (u + fma(u2, q, lo));
@@ -157,8 +161,9 @@ struct SeriesArgs {
     double a, b;     // sigma / zeta, sigma / (1 - zeta)
     double iz, io;   // 1 / zeta, 1 / (1 - zeta) divided by the common factor of the inputs
 };
+template <bool IEXP = true>
 __device__ __forceinline__ double phi_series(const SeriesArgs& s, int K) {
-    return table_log(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
+    return table_log<IEXP>(s.ratio) - (series_P(s.ra, K) - series_P(s.rb, K));
 }
 
 // 1 - (u + v) and 1 - (u - v), each correctly rounded from the doubles u, v: 1 - u is split
@@ -368,7 +373,7 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
         series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
                      aq);
         const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
-        double phi = phi_series(ap, K), psi = phi_series(aq, K);
+        double phi = phi_series<CM != 1>(ap, K), psi = phi_series<CM != 1>(aq, K);
         if (!ok) { phi = 0.0; psi = 0.0; }
         const double ha = 0.5 * k.alpha, hgn = -0.5 * k.gamma;
         const double Gu = fma(hgn, lu, fma(k.theta, phi + psi, fma(-ha, su, ha)));
@@ -554,7 +559,7 @@ cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& 
 }
 
 // ---------------------------------------------------------------- energy / mass
-__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_log(z) : 0.0; }
+__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_log<>(z) : 0.0; }
 
 // E~ = sum [e1 + e2 + gamma/2 sum_d ((D+ phi)^2 + (D- phi)^2)/2] dx dy (Eqs. relations,
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
@@ -718,7 +723,7 @@ __global__ void __launch_bounds__(256) param_grad_kernel(Geom g, Coef k, const d
         series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
                      aq);
         const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
-        const double phi = phi_series(ap, K), psi = phi_series(aq, K);
+        const double phi = phi_series<>(ap, K), psi = phi_series<>(aq, K);
         if (live && ok) {
             acc[0] += 0.5 * (su - 1.0) * qu;
             acc[1] += 0.5 * sv * qv;
@@ -764,7 +769,7 @@ __global__ void __launch_bounds__(256) loss_grad_kernel(Geom g, Coef k, const do
         double mp, mq;                                           // 1 - p, 1 - q
         one_minus_pq(u, v, mp, mq);
         if (!(in_unit(p) && in_unit(q))) flag |= 1;
-        const double lp = table_log(p), lp1 = table_log(mp), lq = table_log(q), lq1 = table_log(mq);
+        const double lp = table_log<>(p), lp1 = table_log<>(mp), lq = table_log<>(q), lq1 = table_log<>(mq);
         double lapu = 0.0, lapv = 0.0, gr = 0.0;
 #pragma unroll
         for (int f = 0; f < 2 * DIM; ++f) {
@@ -806,7 +811,7 @@ cudaError_t launch_loss_grad(const Geom& g, const Coef& k, const double* X, cons
 }
 __global__ void table_log_kernel(const double* __restrict__ x, double* __restrict__ y, long long n) {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        y[i] = table_log(x[i]);
+        y[i] = table_log<>(x[i]);
 }
 
 cudaError_t launch_table_log(const double* x, double* y, long long n, cudaStream_t s) {

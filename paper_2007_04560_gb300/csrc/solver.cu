@@ -836,9 +836,8 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
             factor<T>(h, on_mask(h, MK_NEWTON), true);
             for (int m = 0; m < B; ++m) info[m].ilu_factorizations += act[m];
         }
-        // b = -F
-        CU(cudaMemsetAsync(h->b, 0, sizeof(double) * h->mb.vs * B, h->stream));
-        KL(ACAC_K_VECTOR, launch_axpy_to_double<double>(-1.0, h->F, h->b, n, h->stream, on_mask(h, MK_NEWTON)));
+        // b = -F (one pass: the scaled copy of the Krylov-boundary kernel, in double)
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_to_krylov<double>(h->F, -1.0, h->b, n, h->stream, on_mask(h, MK_NEWTON)));
         gmres<T>(h, act, h->S, gst, gits, gres, &fnorm, true);
         for (int m = 0; m < B; ++m) {
             if (!act[m]) continue;
