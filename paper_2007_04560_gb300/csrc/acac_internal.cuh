@@ -557,7 +557,7 @@ cudaError_t launch_cgs_update(const T* V, long long ld, int nv, const double* h,
 template <typename T>
 cudaError_t launch_scale_from(const T* w, const double* alpha_dev, T* out, long long n,
                               cudaStream_t s, const Members& mb = Members{});
-// out = x * scale, or x / scale_dev[m * sstride] per member when scale_dev is set
+// out = x * scale, or x * scale * (1 / scale_dev[m * sstride]) per member when scale_dev is set
 template <typename T>
 cudaError_t launch_to_krylov(const double* x, double scale, T* out, long long n, cudaStream_t s,
                              const Members& mb = Members{}, const double* scale_dev = nullptr, int sstride = 0);
@@ -570,7 +570,7 @@ template <typename T>
 cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, cudaStream_t s,
                                   const Members& mb = Members{});
 template <typename T>
-cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
+cudaError_t launch_residual_restart(const double* b, double bsign, const T* Ax, double* r, long long n, Red red,
                                     cudaStream_t s, const Members& mb = Members{});
 // ||a - b||^2 (b may be NULL)
 cudaError_t launch_norm2_double(const double* a, const double* b, long long n, Red red, cudaStream_t s,
@@ -578,6 +578,10 @@ cudaError_t launch_norm2_double(const double* a, const double* b, long long n, R
 // y = x for the members that take part (vectors at vs)
 cudaError_t launch_copy_members(const double* x, double* y, long long n, cudaStream_t s, const Members& mb);
 // ensemble fields <-> member states: X[m] = [u[m] | v[m]] (to_state) or back
+// X = [u | v] per member (u, v of member m at m * N) and, when Xp is set, ||X - Xp||^2 per
+// member through red
+cudaError_t launch_pack_state(const double* u, const double* v, double* X, const double* Xp, long long N, Red red,
+                              cudaStream_t s, const Members& mb);
 cudaError_t launch_pack_members(const double* u, const double* v, double* X, long long N, int to_state,
                                 cudaStream_t s, const Members& mb);
 

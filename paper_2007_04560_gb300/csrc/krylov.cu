@@ -322,8 +322,9 @@ __global__ void to_krylov_kernel(const double* __restrict__ x, double scale, T* 
     if (member_off(mb, m)) return;
     x += (size_t)m * mb.vs;
     out += (size_t)m * mb.vs;
-    // 1/beta correctly rounded, as the host forms it for a single problem
-    if (scale_dev) scale = 1.0 / scale_dev[(size_t)m * sstride];
+    // scale / beta with 1/beta correctly rounded, as the host forms it for a single problem
+    // (scale is +-1 there: an exact sign)
+    if (scale_dev) scale *= 1.0 / scale_dev[(size_t)m * sstride];
     over_packs<P>(n, [&](long long i) {
         const Pk<double, P> a = ldp<double, P>(x, i);
         Pk<T, P> r;
@@ -407,9 +408,9 @@ cudaError_t launch_axpy_to_double(double a, const T* x, double* y, long long n, 
     return cudaGetLastError();
 }
 
-// r = b - Ax (double), partial sums of ||r||^2
+// r = bsign b - Ax (double; bsign = +-1, an exact sign), partial sums of ||r||^2
 template <typename T, int P>
-__global__ void residual_restart_kernel(const double* __restrict__ b, const T* __restrict__ Ax,
+__global__ void residual_restart_kernel(const double* __restrict__ b, double bsign, const T* __restrict__ Ax,
                                         double* __restrict__ r, long long n, Red red, Members mb) {
     __shared__ double sh[32];
     const int m = blockIdx.y;
@@ -425,12 +426,12 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
         Pk<double, P> ri;
 #pragma unroll
         for (int e = 0; e < P; ++e) {
-            ri.v[e] = bi.v[e] - to_dbl<T>(ai.v[e]);
+            ri.v[e] = bsign * bi.v[e] - to_dbl<T>(ai.v[e]);
             acc = fma(ri.v[e], ri.v[e], acc);
         }
         stp<double, P>(r, i, ri);
     }, [&](long long i) {
-        const double ri = b[i] - to_dbl<T>(Ax[i]);
+        const double ri = bsign * b[i] - to_dbl<T>(Ax[i]);
         r[i] = ri;
         acc = fma(ri, ri, acc);
     });
@@ -440,12 +441,12 @@ __global__ void residual_restart_kernel(const double* __restrict__ b, const T* _
 }
 
 template <typename T>
-cudaError_t launch_residual_restart(const double* b, const T* Ax, double* r, long long n, Red red,
+cudaError_t launch_residual_restart(const double* b, double bsign, const T* Ax, double* r, long long n, Red red,
                                     cudaStream_t s, const Members& mb) {
     if (al16(b) && al16(Ax) && al16(r))
-        residual_restart_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
+        residual_restart_kernel<T, 4><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, bsign, Ax, r, n, red, mb);
     else
-        residual_restart_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, Ax, r, n, red, mb);
+        residual_restart_kernel<T, 1><<<vgrid(n, mb), RED_THREADS, 0, s>>>(b, bsign, Ax, r, n, red, mb);
     return cudaGetLastError();
 }
 
@@ -466,6 +467,7 @@ cudaError_t launch_copy_members(const double* x, double* y, long long n, cudaStr
 }
 
 // u, v: the ensemble's fields (member m at m * N); X: member states [u | v] at m * vs
+template <int P>
 __global__ void pack_members_kernel(const double* __restrict__ u, const double* __restrict__ v,
                                     double* __restrict__ X, long long N, int to_state, Members mb) {
     const int m = blockIdx.y;
@@ -473,21 +475,83 @@ __global__ void pack_members_kernel(const double* __restrict__ u, const double* 
     double* Xm = X + (size_t)m * mb.vs;
     double* um = const_cast<double*>(u) + (size_t)m * N;
     double* vm = const_cast<double*>(v) + (size_t)m * N;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < N;
-         i += (long long)gridDim.x * blockDim.x) {
-        if (to_state) {
+    if (to_state)
+        over_packs<P>(N, [&](long long i) {
+            stp<double, P>(Xm, i, ldp<double, P>(um, i));
+            stp<double, P>(Xm + N, i, ldp<double, P>(vm, i));
+        }, [&](long long i) {
             Xm[i] = um[i];
             Xm[N + i] = vm[i];
-        } else {
+        });
+    else
+        over_packs<P>(N, [&](long long i) {
+            stp<double, P>(um, i, ldp<double, P>(Xm, i));
+            stp<double, P>(vm, i, ldp<double, P>(Xm + N, i));
+        }, [&](long long i) {
             um[i] = Xm[i];
             vm[i] = Xm[N + i];
-        }
-    }
+        });
 }
 
 cudaError_t launch_pack_members(const double* u, const double* v, double* X, long long N, int to_state,
                                 cudaStream_t s, const Members& mb) {
-    pack_members_kernel<<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, N, to_state, mb);
+    if (al16(u) && al16(v) && al16(X) && N % 2 == 0 && mb.vs % 2 == 0)
+        pack_members_kernel<4><<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, N, to_state, mb);
+    else
+        pack_members_kernel<1><<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, N, to_state, mb);
+    return cudaGetLastError();
+}
+
+// X = [u | v] per member and, when Xp is set, partial sums of ||X - Xp||^2 (the step
+// predictor's change of state, Sec. 3.2): one pass over the new state instead of a copy
+// followed by a norm.  P = 4 needs every pointer 16-byte aligned and N even (member and
+// field offsets of N doubles).
+template <int P>
+__global__ void pack_state_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                  double* __restrict__ X, const double* __restrict__ Xp, long long N, Red red,
+                                  Members mb) {
+    __shared__ double sh[32];
+    const int m = blockIdx.y;
+    if (member_off(mb, m)) return;
+    u += (size_t)m * N;
+    v += (size_t)m * N;
+    X += (size_t)m * mb.vs;
+    if (Xp) Xp += (size_t)m * mb.vs;
+    double acc = 0.0;
+    over_packs<P>(N, [&](long long i) {
+        const Pk<double, P> a = ldp<double, P>(u, i), b = ldp<double, P>(v, i);
+        stp<double, P>(X, i, a);
+        stp<double, P>(X + N, i, b);
+        if (Xp) {
+            const Pk<double, P> pa = ldp<double, P>(Xp, i), pb = ldp<double, P>(Xp + N, i);
+#pragma unroll
+            for (int k = 0; k < P; ++k) {
+                acc = fma(a.v[k] - pa.v[k], a.v[k] - pa.v[k], acc);
+                acc = fma(b.v[k] - pb.v[k], b.v[k] - pb.v[k], acc);
+            }
+        }
+    }, [&](long long i) {
+        const double a = u[i], b = v[i];
+        X[i] = a;
+        X[N + i] = b;
+        if (Xp) {
+            acc = fma(a - Xp[i], a - Xp[i], acc);
+            acc = fma(b - Xp[N + i], b - Xp[N + i], acc);
+        }
+    });
+    if (!Xp) return;   // uniform over the grid
+    red = member_red(red, mb, m);
+    const double t = block_sum_red(acc, sh);
+    if (threadIdx.x == 0) red.partial[blockIdx.x] = t;
+    finish_reduction(red, 1, sh);
+}
+
+cudaError_t launch_pack_state(const double* u, const double* v, double* X, const double* Xp, long long N, Red red,
+                              cudaStream_t s, const Members& mb) {
+    if (al16(u) && al16(v) && al16(X) && (!Xp || al16(Xp)) && N % 2 == 0 && mb.vs % 2 == 0)
+        pack_state_kernel<4><<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, Xp, N, red, mb);
+    else
+        pack_state_kernel<1><<<vgrid(N, mb), RED_THREADS, 0, s>>>(u, v, X, Xp, N, red, mb);
     return cudaGetLastError();
 }
 
@@ -590,7 +654,7 @@ cudaError_t launch_gmres_solve(const GmresHead* head, const GmresWork* work, con
                                            cudaStream_t, const Members&, const int*);               \
     template cudaError_t launch_axpy_to_double<T>(double, const T*, double*, long long, cudaStream_t, \
                                                   const Members&);                                  \
-    template cudaError_t launch_residual_restart<T>(const double*, const T*, double*, long long,    \
+    template cudaError_t launch_residual_restart<T>(const double*, double, const T*, double*, long long, \
                                                     Red, cudaStream_t, const Members&);
 INST(double)
 INST(float)

@@ -608,16 +608,19 @@ void arnoldi_launch(acac_handle* h, int j) {
     }
 }
 
-// Restarted GMRES for J x = b (b = h->b), x0 = 0, right preconditioning, for the members
-// in `want`.  x (device, member stride mb.vs) receives the solutions; per member gst
-// (ACAC_OK, ACAC_E_DIVERGED or ACAC_E_TIMEOUT), gits (iterations) and gres (residual
-// estimate).  bnorm: ||b|| per member when already known (the Newton loop's b = -F has
-// the norm of its residual evaluation; no reduction and read-back are spent on it), else
-// null.  With defer_timeout the apply's sticky timeout flags are left to the caller's
-// next read-back.
+// Restarted GMRES for J x = b, b = bsign * bsrc (bsrc = h->b when null; bsign = +-1, an
+// exact sign: the Newton loop's b = -F is read from F itself), x0 = 0, right
+// preconditioning, for the members in `want`.  x (device, member stride mb.vs) receives the
+// solutions; per member gst (ACAC_OK, ACAC_E_DIVERGED or ACAC_E_TIMEOUT), gits (iterations)
+// and gres (residual estimate).  bnorm: ||b|| per member when already known (the Newton
+// loop's b = -F has the norm of its residual evaluation; no reduction and read-back are
+// spent on it), else null.  With defer_timeout the apply's sticky timeout flags are left to
+// the caller's next read-back.
 template <typename T>
 void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<int>& gst, std::vector<int>& gits,
-           std::vector<double>& gres, const std::vector<double>* bnorm, bool defer_timeout = false) {
+           std::vector<double>& gres, const std::vector<double>* bnorm, bool defer_timeout = false,
+           const double* bsrc = nullptr, double bsign = 1.0) {
+    if (!bsrc) bsrc = h->b;
     // the first call runs eagerly (it also sets the kernels' shared-memory limits); later
     // calls replay captured graphs
     struct Count {
@@ -653,7 +656,7 @@ void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<
         beta = *bnorm;
     } else {
         set_mask(h, MK_AUX, want);
-        KL(ACAC_K_VECTOR, launch_norm2_double(h->b, nullptr, n, red_to(h, h->red), h->stream, on_mask(h, MK_AUX)));
+        KL(ACAC_K_VECTOR, launch_norm2_double(bsrc, nullptr, n, red_to(h, h->red), h->stream, on_mask(h, MK_AUX)));
         if (flags_pending) fetch_flags(h);
         read_member_scalars(h, 0, 1);
         for (int m = 0; m < B; ++m) beta[m] = sqrt(h->host[m]);
@@ -666,7 +669,8 @@ void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<
         gres[m] = beta[m];
         act[m] = gst[m] == ACAC_OK && beta[m] > tol[m];
     }
-    const double* rsrc = h->b;
+    const double* rsrc = bsrc;
+    double rsign = bsign;
     h->ghead.resize(B);
     while (any_of(act)) {
         // cycle start: v_0 = r / beta, g = beta e_1
@@ -678,7 +682,7 @@ void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<
         int* cyc = h->masks + (size_t)MK_CYC * B;
         KL(ACAC_K_VECTOR, launch_gmres_start(h->ghead_dev, h->gwork_dev, cyc, h->masks + (size_t)MK_GON * B, B,
                                              h->stream));
-        KL(ACAC_K_VECTOR, launch_to_krylov<T>(rsrc, 1.0, (T*)h->V, n, h->stream, on_mask(h, MK_CYC),
+        KL(ACAC_K_VECTOR, launch_to_krylov<T>(rsrc, rsign, (T*)h->V, n, h->stream, on_mask(h, MK_CYC),
                                               (const double*)h->ghead_dev, (int)(sizeof(GmresHead) / sizeof(double))));
         // Arnoldi steps without read-backs: the first look at the members' progress comes
         // after as many steps as the previous cycle took, then one after every step
@@ -732,7 +736,7 @@ void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<
         const Members mr = on_mask(h, MK_RESTART);
         KL(ACAC_K_VECTOR, launch_to_krylov<T>(x, 1.0, tt, n, h->stream, mr));
         jac_action<T>(h, mr, tt, w);
-        KL(ACAC_K_VECTOR, launch_residual_restart<T>(h->b, w, h->r, n, red_to(h, h->red), h->stream, mr));
+        KL(ACAC_K_VECTOR, launch_residual_restart<T>(bsrc, bsign, w, h->r, n, red_to(h, h->red), h->stream, mr));
         read_member_scalars(h, 0, 1);
         for (int m = 0; m < B; ++m) {
             if (!rst[m]) continue;
@@ -741,6 +745,7 @@ void gmres(acac_handle* h, const std::vector<int>& want, double* x, std::vector<
             else act[m] = 1;
         }
         rsrc = h->r;
+        rsign = 1.0;
     }
     if (flags_pending || !defer_timeout) {
         fetch_flags(h);
@@ -794,15 +799,14 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
     st.assign(B, ACAC_OK);
     std::vector<int> act = want;
     std::vector<double> fnorm(B, 0.0), stop(B, 0.0);
-    std::vector<double*> root(B, nullptr);
+    std::vector<const double*> root(B, nullptr);
     set_mask(h, MK_NEWTON, act);
-    {
-        const Members mn = on_mask(h, MK_NEWTON);
-        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->X0, h->X, n, h->stream, mn));
-        // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
-        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream, mn));
-    }
-    eval_residual(h, MK_NEWTON, h->X, false, true, true);
+    // X0 stays fixed over the solve: its Laplacians once, for every pass A of the solve
+    KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_laplacian(h->g, h->X0, h->lap0, h->stream, on_mask(h, MK_NEWTON)));
+    // the current iterate: the start state X0 itself (read in place), then the accepted
+    // trial states, which alternate between the buffers X and Xt
+    const double* cur = h->X0;
+    eval_residual(h, MK_NEWTON, cur, false, true, true);
     for (int m = 0; m < B; ++m) {
         if (!want[m]) continue;
         info[m].fnorm0 = info[m].fnorm = fnorm[m] = h->fn[m];
@@ -816,7 +820,7 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
             stop[m] = std::max(h->p.newton_rtol * fnorm[m], h->p.newton_atol);
             if (fnorm[m] <= stop[m]) {
                 act[m] = 0;
-                root[m] = h->X;
+                root[m] = cur;
             }
         }
     }
@@ -830,15 +834,14 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
         }
         set_mask(h, MK_NEWTON, act);
         const bool refactor = (it == 0) || !h->p.ilu_reuse;
-        linearize_and_maybe_assemble<T>(h, on_mask(h, MK_NEWTON), h->X,
+        linearize_and_maybe_assemble<T>(h, on_mask(h, MK_NEWTON), cur,
                                         refactor || h->p.jac_mode == ACAC_JAC_ASSEMBLED, h->cache_fresh);
         if (refactor) {
             factor<T>(h, on_mask(h, MK_NEWTON), true);
             for (int m = 0; m < B; ++m) info[m].ilu_factorizations += act[m];
         }
-        // b = -F (one pass: the scaled copy of the Krylov-boundary kernel, in double)
-        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_to_krylov<double>(h->F, -1.0, h->b, n, h->stream, on_mask(h, MK_NEWTON)));
-        gmres<T>(h, act, h->S, gst, gits, gres, &fnorm, true);
+        // b = -F, read from F with the sign folded into GMRES's first basis vector
+        gmres<T>(h, act, h->S, gst, gits, gres, &fnorm, true, h->F, -1.0);
         for (int m = 0; m < B; ++m) {
             if (!act[m]) continue;
             info[m].gmres_its += gits[m];
@@ -851,7 +854,7 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
         set_mask(h, MK_NEWTON, act);
         // shift S_u by a constant so that sum(u + S_u) = sum(u^n); the sums stay on the
         // device, where the trial kernel reads them
-        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, h->X, h->S, (long long)N, red_to(h, h->red + RS_SHIFT), h->stream,
+        KL(ACAC_K_VECTOR, launch_sum_pair(h->X0, cur, h->S, (long long)N, red_to(h, h->red + RS_SHIFT), h->stream,
                                           on_mask(h, MK_NEWTON)));
         std::vector<int> ls = act;
         std::vector<double> lam(B, 1.0), ft(B, 0.0);
@@ -859,7 +862,7 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
             for (int m = 0; m < B; ++m) h->mk[m].lam = lam[m];
             write_lam(h);
             set_mask(h, MK_LS, ls);
-            eval_residual(h, MK_LS, h->X, true, true, true);
+            eval_residual(h, MK_LS, cur, true, true, true);
             for (int m = 0; m < B; ++m) {
                 if (!ls[m]) continue;
                 const double f = h->fn[m];
@@ -882,6 +885,7 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
         // the accepted states of the members still iterating are in Xt; members that
         // finished earlier keep their roots where they were (root[m])
         std::swap(h->X, h->Xt);
+        cur = h->X;
         for (int m = 0; m < B; ++m) {
             if (!act[m]) continue;
             fnorm[m] = ft[m];
@@ -889,16 +893,17 @@ void nks(acac_handle* h, const std::vector<int>& want, std::vector<int>& st, aca
             info[m].fnorm = fnorm[m];
             if (fnorm[m] <= stop[m]) {
                 act[m] = 0;
-                root[m] = h->X;
+                root[m] = cur;
             }
         }
     }
-    // roots left in the other buffer by later swaps
-    std::vector<int> fix(B, 0);
-    for (int m = 0; m < B; ++m) fix[m] = want[m] && st[m] == ACAC_OK && root[m] != h->X;
-    if (any_of(fix)) {
+    // roots elsewhere than X: left in Xt by later swaps, or the start state itself
+    for (const double* src : {(const double*)h->Xt, (const double*)h->X0}) {
+        std::vector<int> fix(B, 0);
+        for (int m = 0; m < B; ++m) fix[m] = want[m] && st[m] == ACAC_OK && root[m] == src;
+        if (!any_of(fix)) continue;
         set_mask(h, MK_AUX, fix);
-        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->Xt, h->X, n, h->stream, on_mask(h, MK_AUX)));
+        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(src, h->X, n, h->stream, on_mask(h, MK_AUX)));
     }
 }
 
@@ -937,22 +942,21 @@ int step_members(acac_handle* h, double* u, double* v, acac_step_info* info_out)
     const long long n2 = 2 * (long long)N;
     std::vector<acac_step_info> info(B);
     memset(info.data(), 0, sizeof(acac_step_info) * B);
-    KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_pack_members(u, v, h->X0, (long long)N, 1, h->stream, all_members(h)));
     const bool adaptive = h->p.dt_mode == ACAC_DT_ADAPTIVE;
     std::vector<double> dt(B, h->p.dt0);
-    if (adaptive) {
-        std::vector<int> prev(B);
-        for (int m = 0; m < B; ++m) prev[m] = h->have_prev[m];
-        if (any_of(prev)) {
-            set_mask(h, MK_AUX, prev);
-            KL(ACAC_K_VECTOR, launch_norm2_double(h->X0, h->Xprev, n2, red_to(h, h->red), h->stream,
-                                                  on_mask(h, MK_AUX)));
-            read_member_scalars(h, 0, 1);
-            for (int m = 0; m < B; ++m) {
-                if (!prev[m]) continue;
-                const double xd = sqrt(h->host[m]) / h->dt_prev[m];
-                dt[m] = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta[m] * xd * xd));
-            }
+    std::vector<int> prev(B);
+    for (int m = 0; m < B; ++m) prev[m] = adaptive && h->have_prev[m];
+    // U^n into X0 and, for the predictor, ||U^n - U^{n-1}||^2 in the same pass (members
+    // without a previous state get a sum they do not read)
+    KLA(ACAC_K_VECTOR, (any_of(prev) ? 48.0 : 32.0) * N, 0.0,
+        launch_pack_state(u, v, h->X0, any_of(prev) ? h->Xprev : nullptr, (long long)N, red_to(h, h->red),
+                          h->stream, all_members(h)));
+    if (any_of(prev)) {
+        read_member_scalars(h, 0, 1);
+        for (int m = 0; m < B; ++m) {
+            if (!prev[m]) continue;
+            const double xd = sqrt(h->host[m]) / h->dt_prev[m];
+            dt[m] = std::max(h->p.dt_min, h->p.dt_max / sqrt(1.0 + h->eta[m] * xd * xd));
         }
     }
     std::vector<int> pending(B, 1), stv(B, ACAC_OK), st;
@@ -989,7 +993,10 @@ int step_members(acac_handle* h, double* u, double* v, acac_step_info* info_out)
         // accepted members: U^{n+1} out, U^n kept for the next predictor, energy and mass
         set_mask(h, MK_AUX, ok);
         const Members ma = on_mask(h, MK_AUX);
-        KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->X0, h->Xprev, n2, h->stream, ma));
+        // U^n becomes the predictor's previous state: when every member is accepted in this
+        // round the buffers trade places (X0 is refilled by the next step), else a copy
+        if (std::all_of(ok.begin(), ok.end(), [](int o) { return o != 0; })) std::swap(h->X0, h->Xprev);
+        else KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_copy_members(h->X0, h->Xprev, n2, h->stream, ma));
         KLA(ACAC_K_VECTOR, 32.0 * N, 0.0, launch_pack_members(u, v, h->X, (long long)N, 0, h->stream, ma));
         energy_members(h, MK_AUX, h->X, e, ms, bad);
         for (int m = 0; m < B; ++m) {
