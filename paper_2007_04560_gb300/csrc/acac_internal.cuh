@@ -71,6 +71,9 @@ struct Geom {
     // the cell itself as neighbour and a zero difference
     double hihx2, hihy2, hihz2;
     float hihx2f, hihy2f, hihz2f;
+    // 1 when every axis has the same spacing: a Laplacian then sums its neighbours first and
+    // scales once by 1/h^2 (fewer FP64 operations than one scaling per axis)
+    int iso;
 };
 
 // ---------------------------------------------------------------- 3D stencil

@@ -207,12 +207,26 @@ __global__ void __launch_bounds__(256) jvp1_kernel(Geom g, const JacK<T>* __rest
     // Laplacian per axis, (w_- + w_+ - 2 w) / h^2: a clamped (Neumann wall) neighbour is the
     // cell itself and adds nothing
     T lu = 0, lv = 0;
+    if (g.iso) {
+        // equal spacing: the neighbour sums first, one scaling by 1/h^2
+        T nu = 0, nv = 0;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) {
-        const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
-        const T ih2 = sizeof(T) == 8 ? (T)face_ih2(g, 2 * d) : (T)(d == 0 ? g.ihx2f : d == 1 ? g.ihy2f : g.ihz2f);
-        lu = fma(fma((T)-2, wu, w[nm] + w[np]), ih2, lu);
-        lv = fma(fma((T)-2, wv, w[N + nm] + w[N + np]), ih2, lv);
+        for (int d = 0; d < DIM; ++d) {
+            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+            nu = d == 0 ? w[nm] + w[np] : nu + (w[nm] + w[np]);
+            nv = d == 0 ? w[N + nm] + w[N + np] : nv + (w[N + nm] + w[N + np]);
+        }
+        const T ih2 = sizeof(T) == 8 ? (T)g.ihx2 : (T)g.ihx2f;
+        lu = fma((T)(-2 * DIM), wu, nu) * ih2;
+        lv = fma((T)(-2 * DIM), wv, nv) * ih2;
+    } else {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+            const T ih2 = sizeof(T) == 8 ? (T)face_ih2(g, 2 * d) : (T)(d == 0 ? g.ihx2f : d == 1 ? g.ihy2f : g.ihz2f);
+            lu = fma(fma((T)-2, wu, w[nm] + w[np]), ih2, lu);
+            lv = fma(fma((T)-2, wv, w[N + nm] + w[N + np]), ih2, lv);
+        }
     }
     const JacK<T> k = *kp;
     const T hg = k.hg;
@@ -242,10 +256,22 @@ __global__ void __launch_bounds__(256) jvp2_kernel(Geom g, const JacK<T>* __rest
     const T* dc = tmp + 2 * N;
     const T cc = C.c[c], gc = C.Gu[c], dgc = dGu[c], dcc = dc[c];
     T div = 0;
+    if (g.iso) {
+        // equal spacing: every face has the weight 1/(2 h^2), applied once to the sum
+        T t = 0;
 #pragma unroll
-    for (int f = 0; f < 2 * DIM; ++f) {
-        const int n = face_nb<DIM>(g, x, yy, zz, f);
-        div = fma(face_half<T>(g, f), fma(cc + C.c[n], dGu[n] - dgc, (dcc + dc[n]) * (C.Gu[n] - gc)), div);
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, yy, zz, f);
+            t = f == 0 ? (dcc + dc[n]) * (C.Gu[n] - gc) : fma(dcc + dc[n], C.Gu[n] - gc, t);
+            t = fma(cc + C.c[n], dGu[n] - dgc, t);
+        }
+        div = face_half<T>(g, 0) * t;
+    } else {
+#pragma unroll
+        for (int f = 0; f < 2 * DIM; ++f) {
+            const int n = face_nb<DIM>(g, x, yy, zz, f);
+            div = fma(face_half<T>(g, f), fma(cc + C.c[n], dGu[n] - dgc, (dcc + dc[n]) * (C.Gu[n] - gc)), div);
+        }
     }
     const T idt = kp->idt, irho = kp->irho;
     y[c] = w[c] * idt - div;

@@ -233,7 +233,8 @@ __device__ __forceinline__ void series_args2(double zp, double omp, double sp, d
     const double Pp = zp * omp, Pq = zq * omq;
     const double PP = Pp * Pq;
     double invp, invq;
-    if (PP > 1e-280) {
+    // PP > 1e-280 on the bit patterns (PP >= 0 here: the callers pass positive midpoints)
+    if (__double_as_longlong(PP) > __double_as_longlong(1e-280)) {
         const double D = 1.0 / PP;
         invp = Pq * D;
         invq = Pp * D;
@@ -348,21 +349,43 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
         // clamped (Neumann ghost) neighbour is the cell itself and adds nothing.  With PRE
         // the start state's Laplacians come precomputed (fixed over a Newton solve)
         double lu = 0.0, lv = 0.0;
+        if (g.iso) {
+            // equal spacing: the neighbour sums first, one scaling by 1/h^2 (with PRE the
+            // start state's Laplacians enter as the addend of that scaling)
+            double nu = 0.0, nv = 0.0;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const double ih2 = face_ih2(g, 2 * d);
-            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
-            if (PRE) {
-                lu = fma(fma(-2.0, u1, Xu[nm] + Xu[np]), ih2, lu);
-                lv = fma(fma(-2.0, v1, Xv[nm] + Xv[np]), ih2, lv);
-            } else {
-                lu = fma(fma(-2.0, su, (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np])), ih2, lu);
-                lv = fma(fma(-2.0, sv, (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np])), ih2, lv);
+            for (int d = 0; d < DIM; ++d) {
+                const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+                const double tu = PRE ? Xu[nm] + Xu[np] : (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np]);
+                const double tv = PRE ? Xv[nm] + Xv[np] : (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np]);
+                nu = d == 0 ? tu : nu + tu;
+                nv = d == 0 ? tv : nv + tv;
             }
-        }
-        if (PRE) {
-            lu += a.L0[cc];
-            lv += a.L0[N + cc];
+            const double c2 = -2.0 * DIM, ih2 = g.ihx2;
+            if (PRE) {
+                lu = fma(fma(c2, u1, nu), ih2, a.L0[cc]);
+                lv = fma(fma(c2, v1, nv), ih2, a.L0[N + cc]);
+            } else {
+                lu = fma(c2, su, nu) * ih2;
+                lv = fma(c2, sv, nv) * ih2;
+            }
+        } else {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const double ih2 = face_ih2(g, 2 * d);
+                const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+                if (PRE) {
+                    lu = fma(fma(-2.0, u1, Xu[nm] + Xu[np]), ih2, lu);
+                    lv = fma(fma(-2.0, v1, Xv[nm] + Xv[np]), ih2, lv);
+                } else {
+                    lu = fma(fma(-2.0, su, (Xu[nm] + Pu[nm]) + (Xu[np] + Pu[np])), ih2, lu);
+                    lv = fma(fma(-2.0, sv, (Xv[nm] + Pv[nm]) + (Xv[np] + Pv[np])), ih2, lv);
+                }
+            }
+            if (PRE) {
+                lu += a.L0[cc];
+                lv += a.L0[N + cc];
+            }
         }
         // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma),
         // all three doubled (the series only sees their ratios)
@@ -457,11 +480,25 @@ __global__ void __launch_bounds__(256) f_kernel(Geom g, double idt, double irho,
         int x, y, z;
         decode_cell<DIM>(g, c, x, y, z);
         const double gc = Gu[c], cc = cm[c];
+        // the faces of an axis (of every axis, with equal spacing) share the weight 1/(2 h^2),
+        // applied once to their sum (a Neumann wall's neighbour is the cell itself: its
+        // difference is exactly zero)
         double div = 0.0;
+        if (g.iso) {
+            double t = 0.0;
 #pragma unroll
-        for (int f = 0; f < 2 * DIM; ++f) {
-            const int n = face_nb<DIM>(g, x, y, z, f);
-            div = fma(face_half<double>(g, f) * (cc + cm[n]), Gu[n] - gc, div);
+            for (int f = 0; f < 2 * DIM; ++f) {
+                const int n = face_nb<DIM>(g, x, y, z, f);
+                t = f == 0 ? (cc + cm[n]) * (Gu[n] - gc) : fma(cc + cm[n], Gu[n] - gc, t);
+            }
+            div = g.hihx2 * t;
+        } else {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+                const double t = fma(cc + cm[np], Gu[np] - gc, (cc + cm[nm]) * (Gu[nm] - gc));
+                div = fma(face_half<double>(g, 2 * d), t, div);
+            }
         }
         const double Fu = (X1[c] - a.X0[c]) * idt - div;
         const double Fv = (X1[N + c] - a.X0[N + c]) * idt + cc * Gv[c] * irho;
@@ -524,12 +561,24 @@ __global__ void __launch_bounds__(256) laplacian_kernel(Geom g, const double* __
         decode_cell<DIM>(g, c, x, y, z);
         const double u = X[c], v = X[N + c];
         double lu = 0.0, lv = 0.0;
+        if (g.iso) {
+            double nu = 0.0, nv = 0.0;
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-            const double ih2 = face_ih2(g, 2 * d);
-            const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
-            lu = fma(fma(-2.0, u, X[nm] + X[np]), ih2, lu);
-            lv = fma(fma(-2.0, v, X[N + nm] + X[N + np]), ih2, lv);
+            for (int d = 0; d < DIM; ++d) {
+                const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+                nu = d == 0 ? X[nm] + X[np] : nu + (X[nm] + X[np]);
+                nv = d == 0 ? X[N + nm] + X[N + np] : nv + (X[N + nm] + X[N + np]);
+            }
+            lu = fma(-2.0 * DIM, u, nu) * g.ihx2;
+            lv = fma(-2.0 * DIM, v, nv) * g.ihx2;
+        } else {
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+                const double ih2 = face_ih2(g, 2 * d);
+                const int nm = face_nb<DIM>(g, x, y, z, 2 * d), np = face_nb<DIM>(g, x, y, z, 2 * d + 1);
+                lu = fma(fma(-2.0, u, X[nm] + X[np]), ih2, lu);
+                lv = fma(fma(-2.0, v, X[N + nm] + X[N + np]), ih2, lv);
+            }
         }
         L[c] = lu;
         L[N + c] = lv;
@@ -559,7 +608,14 @@ cudaError_t launch_residual_f(const Geom& g, const Coef& k, const ResidualArgs& 
 }
 
 // ---------------------------------------------------------------- energy / mass
-__device__ __forceinline__ double xlogx(double z) { return z > 0.0 ? z * table_log<>(z) : 0.0; }
+// z ln z for positive finite z, else 0 (the test on the bit pattern: an FP64 comparison
+// would take an FP64-pipe slot)
+__device__ __forceinline__ double xlogx(double z) { return pos_bits(z) ? z * table_log<>(z) : 0.0; }
+// 0 <= x <= 1 on the bit pattern (-0 included, NaN excluded)
+__device__ __forceinline__ bool in_closed_unit(double x) {
+    const long long b = __double_as_longlong(x);
+    return (unsigned long long)b <= 0x3ff0000000000000ULL || b == (long long)0x8000000000000000ULL;
+}
 
 // E~ = sum [e1 + e2 + gamma/2 sum_d ((D+ phi)^2 + (D- phi)^2)/2] dx dy (Eqs. relations,
 // freeenergy) and sum u dx dy, as per-block partials [energy | mass].
@@ -588,7 +644,7 @@ __global__ void __launch_bounds__(256) energy_kernel(Geom g, Coef k, const doubl
         // lanes still in it)
         double mp = 1.0 - p, mq = 1.0 - q;
         if (__any_sync(__activemask(), near_pure2(2.0 * p) || near_pure2(2.0 * q))) one_minus_pq(u, v, mp, mq);
-        if (!(p >= 0.0 && p <= 1.0 && q >= 0.0 && q <= 1.0)) flag |= 1;
+        if (!(in_closed_unit(p) && in_closed_unit(q))) flag |= 1;
         double e = 0.5 * k.alpha * u * (1.0 - u) - 0.5 * k.beta * v * v
                  + k.theta * (xlogx(p) + xlogx(mp) + xlogx(q) + xlogx(mq));
         // gradient part gamma/2 * 1/2 * sum over D+ and D- of both fields and all axes: a

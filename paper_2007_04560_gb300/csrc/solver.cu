@@ -1291,6 +1291,7 @@ acac::Geom acac::make_geom(const acac_params* p) {
     g.hihx2 = 0.5 * g.ihx2; g.hihy2 = 0.5 * g.ihy2; g.hihz2 = 0.5 * g.ihz2;
     g.hihx2f = (float)g.hihx2; g.hihy2f = (float)g.hihy2; g.hihz2f = (float)g.hihz2;
     g.vol = g.hx * g.hy * (p->dim == 3 ? g.hz : 1.0);
+    g.iso = g.ihx2 == g.ihy2 && (p->dim == 2 || g.ihz2 == g.ihx2);
     return g;
 }
 

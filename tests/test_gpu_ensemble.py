@@ -7,7 +7,7 @@ import pytest
 
 from oracle import acac_oracle as O
 from tests._helpers import dev, host, lib_built, need_cuda, soa
-from workloads import DT_ADAPTIVE, E32, PREC_MIXED, Params, initial_fields
+from workloads import DT_ADAPTIVE, E32, PREC_FP64, PREC_MIXED, Params, initial_fields
 
 pytestmark = pytest.mark.gpu
 
@@ -289,6 +289,47 @@ def test_ensemble_member_retry_matches_single_handle():
             assert (a.status, a.dt, a.divergences, a.gmres_its, a.newton_its) == \
                    (b.status, b.dt, b.divergences, b.gmres_its, b.newton_its), (m, k)
     assert sum(e.divergences for e in ens[0]) > 0   # the retry path was taken
+
+
+@pytest.mark.parametrize("precision", [PREC_FP64, PREC_MIXED])
+def test_stationary_member_keeps_its_state(precision):
+    """A uniform state u = 1/2, v = 0 is a fixed point of the scheme (F(X0) = 0 exactly: G is
+    uniform and p = q), so its Newton solve ends before the first iteration and the root is
+    the start state itself.  Beside a member that iterates (adaptive steps, so the
+    predictor's change of state is 0 for one member and not for the other) the stationary
+    member keeps its fields bit for bit with zero Newton iterations, the other matches a
+    batch-1 handle bit for bit, and a batch-1 handle on the stationary state agrees."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    p1 = Params(n=(48, 40, 1), ras_parts=(3, 2, 1), ras_overlap=1, dt_mode=DT_ADAPTIVE, dt0=1e-3, dt_min=1e-5,
+                dt_max=1e-1, eta0=1e4, precision=precision)
+    uf, vf = initial_fields(p1, 31, 0.4, 0.05)
+    uc, vc = np.full_like(uf, 0.5), np.zeros_like(vf)
+    u, v = _stack([(uc, vc), (uf, vf)])
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    with P.Solver(p1.replace(batch=2)) as s:
+        ens = [s.step(ug, vg) for _ in range(3)]
+    torch.cuda.synchronize()
+    gu, gv = host(ug).reshape(2, -1), host(vg).reshape(2, -1)
+    assert np.array_equal(gu[0], uc.ravel()) and np.array_equal(gv[0], vc.ravel())
+    assert all(e[0].newton_its == 0 and e[0].status == 0 for e in ens)
+    assert ens[-1][0].dt == pytest.approx(p1.dt_max)            # no change of state: the largest dt
+    assert ens[0][0].energy == pytest.approx(O.energy(p1, uc, vc), rel=1e-12)
+    assert all(e[1].newton_its >= 1 for e in ens)
+    su, sv = dev(uf.ravel()), dev(vf.ravel())
+    with P.Solver(p1) as one:
+        solo = [one.step(su, sv) for _ in range(3)]
+    torch.cuda.synchronize()
+    assert np.array_equal(host(su), gu[1]) and np.array_equal(host(sv), gv[1])
+    assert [(a.dt, a.newton_its, a.gmres_its) for a in solo] == [(e[1].dt, e[1].newton_its, e[1].gmres_its)
+                                                               for e in ens]
+    cu, cv = dev(uc.ravel()), dev(vc.ravel())
+    with P.Solver(p1) as one:
+        infos = [one.step(cu, cv) for _ in range(2)]
+    torch.cuda.synchronize()
+    assert np.array_equal(host(cu), uc.ravel()) and np.array_equal(host(cv), vc.ravel())
+    assert [i.newton_its for i in infos] == [0, 0]
 
 
 def test_autotune_ensemble():

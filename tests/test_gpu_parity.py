@@ -16,7 +16,7 @@ import pytest
 from oracle import acac_oracle as O
 from tests._helpers import (dev, host, interleaved_to_soa, lib_built, need_cuda, soa,
                             soa_to_interleaved, stencil_J_to_csr)
-from workloads import (BC_NEUMANN, BC_PERIODIC, C1, DT_ADAPTIVE, PREC_MIXED, Params,
+from workloads import (BC_NEUMANN, BC_PERIODIC, C1, DT_ADAPTIVE, PREC_FP64, PREC_MIXED, Params,
                        initial_fields, perturbed_pair, random_vector)
 
 pytestmark = pytest.mark.gpu
@@ -233,6 +233,32 @@ def test_steps_match_oracle_tight():
             assert abs(ig.mass - M0) <= 1e-12 * abs(M0)
             assert ig.energy == pytest.approx(io.energy, rel=1e-12)
             E0 = ig.energy
+
+
+@pytest.mark.parametrize("precision,tol", [(PREC_FP64, 1e-9), (PREC_MIXED, 1e-8)])
+def test_steps_with_gmres_restarts_match_oracle(precision, tol):
+    """C1 at dt = 1e-2 with GMRES restarted every 4 iterations (about 60 iterations per
+    Newton step, so every solve restarts many times from r = b - J x with b = -F): each step's
+    fields within 1e-9 (FP64) / 1e-8 (mixed) relative L2 of the oracle's at Newton rtol 1e-12,
+    with the oracle's Newton iteration count."""
+    need_cuda()
+    P = lib_built()
+    import torch
+    p = C1.params.replace(dt0=1e-2, gmres_restart=4, newton_rtol=1e-12, precision=precision)
+    u, v = C1.fields()
+    st = O.Stepper(p)
+    uo, vo = u.copy(), v.copy()
+    ug, vg = dev(u.ravel()), dev(v.ravel())
+    with P.Solver(p) as s:
+        for k in range(2):
+            Xo, io = st.step(uo, vo)
+            uo, vo = Xo
+            ig = s.step(ug, vg)
+            torch.cuda.synchronize()
+            xg, xo = soa(host(ug), host(vg)), soa(uo, vo)
+            assert np.linalg.norm(xg - xo) <= tol * np.linalg.norm(xo), k
+            assert ig.newton_its == io.newton_its
+            assert ig.gmres_its > 8 * ig.newton_its    # restarts taken
 
 
 def test_steps_match_oracle_config_tolerance():

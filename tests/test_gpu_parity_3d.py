@@ -11,8 +11,12 @@ from workloads import BC_NEUMANN, BC_PERIODIC, Params, initial_fields, perturbed
 
 pytestmark = pytest.mark.gpu
 
-# periodic boxes must not wrap onto themselves: width <= N - 2
-CASES = [(BC_PERIODIC, (12, 11, 10), (2, 2, 2)), (BC_NEUMANN, (10, 9, 11), (2, 2, 3))]
+# periodic boxes must not wrap onto themselves: width <= N - 2.  The first two have a
+# different spacing per axis, the last two equal spacing (the kernels' one-scaling form of
+# the Laplacians and face sums)
+ANISO, CUBE = (1.0, 0.9, 1.1), (1.0, 1.0, 1.0)
+CASES = [(BC_PERIODIC, (12, 11, 10), (2, 2, 2), ANISO), (BC_NEUMANN, (10, 9, 11), (2, 2, 3), ANISO),
+         (BC_PERIODIC, (12, 12, 12), (2, 2, 2), CUBE), (BC_NEUMANN, (10, 10, 10), (2, 2, 2), CUBE)]
 
 
 @pytest.fixture(scope="module")
@@ -25,14 +29,14 @@ def _rel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
 
 
-def _p(bc, n, parts, **kw):
-    return Params(dim=3, n=n, L=(1.0, 0.9, 1.1), bc=bc, ras_parts=parts, ras_overlap=1, **kw)
+def _p(bc, n, parts, L=ANISO, **kw):
+    return Params(dim=3, n=n, L=L, bc=bc, ras_parts=parts, ras_overlap=1, **kw)
 
 
-@pytest.mark.parametrize("bc,n,parts", CASES)
-def test_residual_energy_3d(P, bc, n, parts):
+@pytest.mark.parametrize("bc,n,parts,L", CASES)
+def test_residual_energy_3d(P, bc, n, parts, L):
     import torch
-    p = _p(bc, n, parts)
+    p = _p(bc, n, parts, L)
     X1, X0 = perturbed_pair(p, 5, u_mean=0.45, amp=0.05, step_amp=2e-3)
     dt = 2e-3
     Fo = soa(*O.residual(p, X1, X0, dt))
@@ -47,10 +51,10 @@ def test_residual_energy_3d(P, bc, n, parts):
     assert m == pytest.approx(O.mass(p, X1[0]), rel=1e-14)
 
 
-@pytest.mark.parametrize("bc,n,parts", CASES)
-def test_jacobian_spmv_jvp_3d(P, bc, n, parts):
+@pytest.mark.parametrize("bc,n,parts,L", CASES)
+def test_jacobian_spmv_jvp_3d(P, bc, n, parts, L):
     import torch
-    p = _p(bc, n, parts)
+    p = _p(bc, n, parts, L)
     X1, X0 = perturbed_pair(p, 7, u_mean=0.45, amp=0.05, step_amp=2e-3)
     dt = 2e-3
     Jo = O.jacobian(p, X1, X0, dt)
@@ -72,10 +76,10 @@ def test_jacobian_spmv_jvp_3d(P, bc, n, parts):
 
 
 @pytest.mark.parametrize("ras_type", [0, 1, 2])
-@pytest.mark.parametrize("bc,n,parts", CASES)
-def test_ras_apply_3d(P, bc, n, parts, ras_type):
+@pytest.mark.parametrize("bc,n,parts,L", CASES)
+def test_ras_apply_3d(P, bc, n, parts, L, ras_type):
     import torch
-    p = _p(bc, n, parts, ras_type=ras_type)
+    p = _p(bc, n, parts, L, ras_type=ras_type)
     X1, X0 = perturbed_pair(p, 13, u_mean=0.45, amp=0.05, step_amp=2e-3)
     dt = 2e-3
     Jo = O.jacobian(p, X1, X0, dt)
@@ -92,10 +96,10 @@ def test_ras_apply_3d(P, bc, n, parts, ras_type):
     assert _rel(host(z), zo) <= 1e-10
 
 
-@pytest.mark.parametrize("bc,n,parts", CASES)
-def test_nks_root_and_steps_3d(P, bc, n, parts):
+@pytest.mark.parametrize("bc,n,parts,L", CASES)
+def test_nks_root_and_steps_3d(P, bc, n, parts, L):
     import torch
-    p = _p(bc, n, parts, newton_rtol=1e-12, gmres_rtol=1e-8, dt0=2e-3)
+    p = _p(bc, n, parts, L, newton_rtol=1e-12, gmres_rtol=1e-8, dt0=2e-3)
     u, v = initial_fields(p, 3, 0.45, 0.05)
     st = O.Stepper(p)
     uo, vo = u.copy(), v.copy()
