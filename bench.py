@@ -56,13 +56,10 @@ TRAFFIC_PER_BOX_CELL = {
 # DRAM bytes per grid cell of cell kernels, from captures at the 2048^2 grid itself (or, where
 # that held too much on the device, at the workload's mesh on a smaller grid whose traffic per
 # cell matches): keyed by (kernel class, precision).
-TRAFFIC_PER_CELL = {
-    # residual pass A writing the linearisation cache (the Newton loop's evaluations):
-    # profiles/residual_g_jvp_tile_2d-2048x2048.md; float cache at 2048^2 itself, double cache
-    # at 1448^2 (part of its writes was still in L2 when the kernel ended)
-    ("residual_g", PREC_MIXED): 378.26e6 / 4194304,
-    ("residual_g", PREC_FP64): 215.60e6 / 2096704,
-}
+# Residual pass A has no entry: its class now mixes two forms (the first evaluation of a
+# Newton solve at the start state reads and computes less than the trial evaluations), and
+# the captures in profiles/ predate that split.
+TRAFFIC_PER_CELL = {}
 
 
 def hbm_peak():

@@ -301,6 +301,13 @@ template <int DIM> __host__ __device__ constexpr int sl_of(int dx, int dy, int d
 template <int DIM> __host__ __device__ constexpr int fc_dx(int f) { return DIM == 2 ? face_dx(f) : f3_dx(f); }
 template <int DIM> __host__ __device__ constexpr int fc_dy(int f) { return DIM == 2 ? face_dy(f) : f3_dy(f); }
 template <int DIM> __host__ __device__ constexpr int fc_dz(int f) { return DIM == 2 ? 0 : f3_dz(f); }
+// face f of cell (x, y, z) is open: periodic, or its neighbour lies inside the grid
+template <int DIM>
+__device__ __forceinline__ bool face_open(const Geom& g, int x, int y, int z, int f) {
+    if (g.bc == ACAC_BC_PERIODIC) return true;
+    const int xx = x + fc_dx<DIM>(f), yy = y + fc_dy<DIM>(f), zz = z + fc_dz<DIM>(f);
+    return xx >= 0 && xx < g.nx && yy >= 0 && yy < g.ny && (DIM == 2 || (zz >= 0 && zz < g.nz));
+}
 template <int DIM>
 __device__ __forceinline__ int slot_nb(const Geom& g, int x, int y, int z, int s) {
     return DIM == 2 ? nb_index(g, x, y, slot_dx(s), slot_dy(s)) : nb_index3(g, x, y, z, s3_dx(s), s3_dy(s), s3_dz(s));
@@ -495,6 +502,10 @@ struct ResidualArgs {
     int cache_mode = 0;
     Cache<double> cache_d{};
     Cache<float> cache_f{};
+    // 1: X is X0 itself (the first evaluation of a Newton solve, with L0 set): the midpoint is
+    // the start state and sigma = 0, so pass A takes its shorter form (no series, no Laplacian
+    // of X beyond 2 L0)
+    int same = 0;
 };
 // Launchers take the members the launch covers last (default: a single problem).  Per
 // member: X, X0, L0, Xt, S, F at stride vs; G at gs; the cache at cs; flags at 1; the

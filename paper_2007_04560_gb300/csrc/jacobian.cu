@@ -44,11 +44,14 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, const JacK<T>* __
     for (int s = 0; s < NS; ++s) { Juu[s] = (T)0; Juv[s] = (T)0; }
     const T cc = C.c[c], cuc = C.cu[c], cvc = C.cv[c], gc = C.Gu[c], gvc = C.Gv[c];
     const T duc = C.du[c], xcc = C.xc[c];
+    const bool per = g.bc == ACAC_BC_PERIODIC;
     T lapc = (T)0;   // sum of open faces / h^2 at c
-    T eih2c[NF];
+    T eih2c[NF], ehc[NF];   // 1/h^2 and 1/(2 h^2) of the open faces, 0 for closed ones
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-        eih2c[f] = face_weight<DIM, T>(g, x, y, z, f);
+        const bool o = face_open<DIM>(g, x, y, z, f);
+        eih2c[f] = o ? (sizeof(T) == 8 ? (T)face_ih2(g, f) : (T)(f < 2 ? g.ihx2f : f < 4 ? g.ihy2f : g.ihz2f)) : (T)0;
+        ehc[f] = o ? face_half<T>(g, f) : (T)0;
         lapc += eih2c[f];
     }
     // Face f (weight w = 1/h^2 if open, else 0; neighbour n; ct = (c_c + c_n)/2;
@@ -68,22 +71,25 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, const JacK<T>* __
         const int fx = fc_dx<DIM>(f), fy = fc_dy<DIM>(f), fz = fc_dz<DIM>(f);
         const int sf = sl_of<DIM>(fx, fy, fz);
         const int n = face_nb<DIM>(g, x, y, z, f);
-        const T w = eih2c[f];
+        const T w = eih2c[f], hw = ehc[f];
         const T dG = C.Gu[n] - gc;
-        const T wct = w * half * (cc + C.c[n]);
-        const T t = w * half * dG;
+        const T wct = hw * (cc + C.c[n]);
+        const T t = hw * dG;
         S1 = fma(w, dG, S1);
         W += wct;
         const int nx_ = x + fx, ny_ = y + fy, nz_ = z + fz;
         const T wcth = wct * hg;
+        // lap(n); on a periodic grid every face is open and lap(n) = lap(c) (the same
+        // weights summed in the same order)
         T lapn = (T)0;
 #pragma unroll
         for (int f2 = 0; f2 < NF; ++f2) {
             const T e2 = face_weight<DIM, T>(g, nx_, ny_, nz_, f2);
             const int s2 = sl_of<DIM>(fx + fc_dx<DIM>(f2), fy + fc_dy<DIM>(f2), fz + fc_dz<DIM>(f2));
             Juu[s2] = fma(wcth, e2, Juu[s2]);
-            lapn += e2;
+            if (!per) lapn += e2;
         }
+        if (per) lapn = lapc;
         Juu[sf] -= fma(wct, fma(hg, lapn, C.du[n]), t * C.cu[n]);
         Juv[sf] -= fma(wct, C.xc[n], t * C.cv[n]);
     }
@@ -96,6 +102,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, const JacK<T>* __
         Juu[s2] = fma(-hgW, eih2c[f2], Juu[s2]);
     }
     const T irho = k.irho;
+    const T cgi = -cc * hg * irho;   // face entries of the v row: -c gamma/2 w / rho
     T Jvu[NS], Jvv[NS];
 #pragma unroll
     for (int s = 0; s < NS; ++s) {
@@ -105,7 +112,7 @@ __global__ void __launch_bounds__(128) assemble_kernel(Geom g, const JacK<T>* __
             jvv = k.idt + (cvc * gvc + cc * (duc + dvshift + hg * lapc)) * irho;
         } else if (s <= NF) {
             const int f = s - 1;   // slots 1..2*DIM are the faces
-            jvv = -cc * hg * eih2c[f] * irho;
+            jvv = cgi * eih2c[f];
         }
         Jvu[s] = jvu;
         Jvv[s] = jvv;

@@ -217,6 +217,16 @@ __device__ __forceinline__ Midpoint2 midpoint_pq2_fast(double u1, double v1, dou
     if (__any_sync(0xffffffffu, near_pure2(m.zp) || near_pure2(m.zq))) m = midpoint_pq2(u1, v1, u0, v0);
     return m;
 }
+// midpoint_pq2_fast for equal end states (u1 = u0 = u, v1 = v0 = v): the same values,
+// sigma = +0, without the differences
+__device__ __forceinline__ Midpoint2 midpoint_pq2_same(double u, double v) {
+    const double su = u + u, sv = v + v;
+    Midpoint2 m{su + sv, 0.0, 0.0, su - sv, 0.0, 0.0};
+    m.omp = 2.0 - m.zp;
+    m.omq = 2.0 - m.zq;
+    if (__any_sync(0xffffffffu, near_pure2(m.zp) || near_pure2(m.zq))) m = midpoint_pq2(u, v, u, v);
+    return m;
+}
 // positive and finite (bit-pattern test, no floating-point compare)
 __device__ __forceinline__ bool pos_bits(double x) {
     const long long b = __double_as_longlong(x);
@@ -247,6 +257,27 @@ __device__ __forceinline__ void series_args2(double zp, double omp, double sp, d
     const double a1 = sp * up, b1 = sp * tp, a2 = sq * uq, b2 = sq * tq;
     ap = SeriesArgs{a1 * a1, b1 * b1, zp * tp, a1, b1, up, tp};
     aq = SeriesArgs{a2 * a2, b2 * b2, zq * tq, a2, b2, uq, tq};
+}
+
+// series_args2 for sigma = 0: the series arguments vanish and only the log argument and the
+// reciprocals remain (the values series_args2 gives for sp = sq = +0)
+__device__ __forceinline__ void series_args2_same(double zp, double omp, double zq, double omq, SeriesArgs& ap,
+                                                  SeriesArgs& aq) {
+    const double Pp = zp * omp, Pq = zq * omq;
+    const double PP = Pp * Pq;
+    double invp, invq;
+    if (__double_as_longlong(PP) > __double_as_longlong(1e-280)) {
+        const double D = 1.0 / PP;
+        invp = Pq * D;
+        invq = Pp * D;
+    } else {
+        invp = 1.0 / Pp;
+        invq = 1.0 / Pq;
+    }
+    const double tp = zp * invp, up = omp * invp;
+    const double tq = zq * invq, uq = omq * invq;
+    ap = SeriesArgs{0.0, 0.0, zp * tp, 0.0, 0.0, up, tp};
+    aq = SeriesArgs{0.0, 0.0, zq * tq, 0.0, 0.0, uq, tq};
 }
 
 // max of non-negative doubles (their bit patterns order like the values)
@@ -309,7 +340,9 @@ __device__ __forceinline__ T dphi_from_args(const SeriesArgs& s, int K) {
     return (one + ra * R1 - a * R1) * from_dbl<T>(s.iz) + (one + rb * R2 + b * R2) * from_dbl<T>(s.io);
 }
 
-template <int DIM, bool PRE, int CM>
+// SAME (with PRE): X is X0 itself, so u1 = u0, the Laplacian of X1 + X0 is 2 L0, sigma = 0
+// and phi^S = ln(zeta / (1 - zeta)) (the series of K = 1 terms at sigma = 0 adds exactly 0).
+template <int DIM, bool PRE, int CM, bool SAME = false>
 __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, Members mb) {
     const int N = g.N;
     const int m = blockIdx.y;
@@ -343,13 +376,16 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
         const int cc = live ? c : N - 1;
         int x, y, z;
         decode_cell<DIM>(g, cc, x, y, z);
-        const double u1 = Xu[cc], v1 = Xv[cc], u0 = Pu[cc], v0 = Pv[cc];
+        const double u1 = Xu[cc], v1 = Xv[cc], u0 = SAME ? u1 : Pu[cc], v0 = SAME ? v1 : Pv[cc];
         const double su = u1 + u0, sv = v1 + v0;
         // Laplacians of u1 + u0 and v1 + v0 (G3), per axis (S_- + S_+ - 2 S) / h^2; a
         // clamped (Neumann ghost) neighbour is the cell itself and adds nothing.  With PRE
         // the start state's Laplacians come precomputed (fixed over a Newton solve)
         double lu = 0.0, lv = 0.0;
-        if (g.iso) {
+        if (SAME) {
+            lu = 2.0 * a.L0[cc];
+            lv = 2.0 * a.L0[N + cc];
+        } else if (g.iso) {
             // equal spacing: the neighbour sums first, one scaling by 1/h^2 (with PRE the
             // start state's Laplacians enter as the addend of that scaling)
             double nu = 0.0, nv = 0.0;
@@ -389,14 +425,23 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
         }
         // G2^S on p = u+v and q = u-v at the midpoint (zeta) with half-increment (sigma),
         // all three doubled (the series only sees their ratios)
-        const Midpoint2 m2 = midpoint_pq2_fast(u1, v1, u0, v0);
+        const Midpoint2 m2 = SAME ? midpoint_pq2_same(u1, v1) : midpoint_pq2_fast(u1, v1, u0, v0);
         const bool ok = pos_bits(m2.zp) && pos_bits(m2.omp) && pos_bits(m2.zq) && pos_bits(m2.omq);
         if (live && !ok) flag |= 1;
         SeriesArgs ap, aq;
-        series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq, ap,
-                     aq);
-        const int K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
-        double phi = phi_series<CM != 1>(ap, K), psi = phi_series<CM != 1>(aq, K);
+        int K = 1;
+        double phi, psi;
+        if (SAME) {
+            series_args2_same(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, ap, aq);
+            phi = table_log<CM != 1>(ap.ratio);
+            psi = table_log<CM != 1>(aq.ratio);
+        } else {
+            series_args2(ok ? m2.zp : 1.0, ok ? m2.omp : 1.0, m2.sp, ok ? m2.zq : 1.0, ok ? m2.omq : 1.0, m2.sq,
+                         ap, aq);
+            K = series_terms(max_nonneg(ap.ra, ap.rb, aq.ra, aq.rb), k.S);
+            phi = phi_series<CM != 1>(ap, K);
+            psi = phi_series<CM != 1>(aq, K);
+        }
         if (!ok) { phi = 0.0; psi = 0.0; }
         const double ha = 0.5 * k.alpha, hgn = -0.5 * k.gamma;
         const double Gu = fma(hgn, lu, fma(k.theta, phi + psi, fma(-ha, su, ha)));
@@ -412,7 +457,10 @@ __global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, 
             // the linearisation cache at this state (linearize_kernel's entries, same formulas)
             using T = typename std::conditional<CM == 1, double, float>::type;
             const int KT = CM == 1 ? K : k.S;
-            const T dp = dphi_from_args<T>(ap, KT), dq = dphi_from_args<T>(aq, KT);
+            // sigma = 0: both series factors are exactly 1, the derivative is 1/zeta + 1/(1-zeta)
+            // (halved through the doubled inputs)
+            const T dp = SAME ? from_dbl<T>(ap.iz) + from_dbl<T>(ap.io) : dphi_from_args<T>(ap, KT);
+            const T dq = SAME ? from_dbl<T>(aq.iz) + from_dbl<T>(aq.io) : dphi_from_args<T>(aq, KT);
             if (live) {
                 Cache<T> C;
                 if constexpr (CM == 1) C = a.cache_d; else C = a.cache_f;
@@ -522,8 +570,15 @@ cudaError_t launch_residual_g(const Geom& g, const Coef& k, const ResidualArgs& 
     if (e != cudaSuccess) return e;
     const int nb = grid_for(g.N, 256);
     auto go = [&](auto dimc, auto prec, auto cmc) {
-        g_kernel<decltype(dimc)::value, decltype(prec)::value, decltype(cmc)::value><<<dim3(nb, mb.count), 256, 0, s>>>(
-            g, k, a, mb);
+        constexpr int D = decltype(dimc)::value, C = decltype(cmc)::value;
+        constexpr bool P = decltype(prec)::value;
+        if constexpr (P) {
+            if (a.same) {
+                g_kernel<D, true, C, true><<<dim3(nb, mb.count), 256, 0, s>>>(g, k, a, mb);
+                return;
+            }
+        }
+        g_kernel<D, P, C, false><<<dim3(nb, mb.count), 256, 0, s>>>(g, k, a, mb);
     };
     using I2 = std::integral_constant<int, 2>;
     using I3 = std::integral_constant<int, 3>;
