@@ -56,10 +56,15 @@ TRAFFIC_PER_BOX_CELL = {
 # DRAM bytes per grid cell of cell kernels, from captures at the 2048^2 grid itself (or, where
 # that held too much on the device, at the workload's mesh on a smaller grid whose traffic per
 # cell matches): keyed by (kernel class, precision).
-# Residual pass A has no entry: its class now mixes two forms (the first evaluation of a
-# Newton solve at the start state reads and computes less than the trial evaluations), and
-# the captures in profiles/ predate that split.
 TRAFFIC_PER_CELL = {}
+# Residual pass A has two forms in one kernel class: the first evaluation of each Newton solve
+# (at the start state) and the trial evaluations.  DRAM bytes per cell of each, (first, trial),
+# from one ncu capture of both at 2048^2 (profiles/residual_g_forms_2d-2048x2048-mixed.md); a
+# launch's traffic is the mix of the two over the timed launches (one first evaluation per
+# Newton solve).
+TRAFFIC_PASS_A = {
+    PREC_MIXED: (296.11e6 / 4194304, 377.58e6 / 4194304),
+}
 
 
 def hbm_peak():
@@ -268,7 +273,7 @@ def fp64_peak(probe):
 FP64_CLASSES = {"residual_g", "residual_f", "energy"}
 
 
-def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None, cells=None):
+def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=None, cells=None, n_first=None):
     name, (n, ms, b, f) = max(stats.items(), key=lambda kv: kv[1][1])
     if n == 0 or ms <= 0:
         return None
@@ -283,6 +288,10 @@ def roofline(stats, precision, hbm, probe_fp64, box_cells, box_w, share_stats=No
     traffic = per * box_cells if per is not None else None
     if traffic is None and cells and (name, precision) in TRAFFIC_PER_CELL:
         traffic = TRAFFIC_PER_CELL[(name, precision)] * cells
+    if traffic is None and cells and name == "residual_g" and precision in TRAFFIC_PASS_A and n_first:
+        first, trial = TRAFFIC_PASS_A[precision]
+        k = min(n_first, n)
+        traffic = cells * (k * first + (n - k) * trial) / n
     intensity = f / b if b > 0 else 0.0
     ridge = fpeak * 1e12 / (hbm_gbs * 1e9)
     out = {"kernel": name, "launches": n, "avg_launch_us": ms * 1e3 / n, "share_of_kernel_time": None,
@@ -433,8 +442,10 @@ def run_mine(args, rank, world):
             "iterations": {"newton_per_step": nits / len(infos),
                            "gmres_per_newton": sum(i["gmres_its"] for i in infos) / max(1, nits),
                            "dt_first": infos[0]["dt"], "dt_last": infos[-1]["dt"], "t_end": infos[-1]["t"]},
+            # one first evaluation of pass A per Newton solve: per step, plus one per retry
             "roofline": roofline(res["stats"], prec, hbm_peak(), probe_fp64, bc, bw, res["warm_stats"],
-                                 res["params"].ncells * int(res["params"].batch)),
+                                 res["params"].ncells * int(res["params"].batch),
+                                 len(infos) + sum(i["divergences"] for i in infos)),
             "kernels": {k: {"launches": v[0], "ms": round(v[1], 4),
                             "gbs": (v[2] / (v[1] * 1e-3) / 1e9) if v[1] > 0 else None}
                         for k, v in res["stats"].items() if v[0] > 0},
