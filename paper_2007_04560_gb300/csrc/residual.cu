@@ -342,8 +342,11 @@ __device__ __forceinline__ T dphi_from_args(const SeriesArgs& s, int K) {
 
 // SAME (with PRE): X is X0 itself, so u1 = u0, the Laplacian of X1 + X0 is 2 L0, sigma = 0
 // and phi^S = ln(zeta / (1 - zeta)) (the series of K = 1 terms at sigma = 0 adds exactly 0).
+// Three blocks per SM: without a minimum the compiler held the float-cache form to 64
+// registers with a spill; at 78 registers (24 resident warps, enough for the FP64 pipe) its
+// trial evaluations run 4% faster.
 template <int DIM, bool PRE, int CM, bool SAME = false>
-__global__ void __launch_bounds__(256) g_kernel(Geom g, Coef k, ResidualArgs a, Members mb) {
+__global__ void __launch_bounds__(256, 3) g_kernel(Geom g, Coef k, ResidualArgs a, Members mb) {
     const int N = g.N;
     const int m = blockIdx.y;
     if (member_off(mb, m)) return;
