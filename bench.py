@@ -61,7 +61,8 @@ TRAFFIC_PER_CELL = {}
 # (at the start state) and the trial evaluations.  DRAM bytes per cell of each, (first, trial),
 # from one ncu capture of both at 2048^2 (profiles/residual_g_forms_2d-2048x2048-mixed.md); a
 # launch's traffic is the mix of the two over the timed launches (one first evaluation per
-# Newton solve).
+# Newton solve).  The capture predates the kernel's launch bound (three blocks per SM), which
+# changed its register allocation only (the float-cache form no longer spills 8 bytes).
 TRAFFIC_PASS_A = {
     PREC_MIXED: (296.11e6 / 4194304, 377.58e6 / 4194304),
 }
